@@ -1,0 +1,261 @@
+"""FP64 CPU oracle of the 2D3V PIC + Thomas-BMT step (test infrastructure).
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the benchmark's
+CPU-baseline leg are the only users.  It does not import, link or share code
+with the CUDA library.
+
+The arithmetic is plain C (``pic_oracle.c``); this module builds it with gcc,
+derives the oracle's own units from a workload (length c/omega0, time
+1/omega0, dt = cfl / sqrt(1/dx^2 + 1/dy^2)) and holds the state in float64
+numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+# a prebuilt oracle library to load instead (the mutation tests point it at
+# deliberately broken copies)
+_LIB_OVERRIDE = os.environ.get("PIC_ORACLE_LIB")
+_lib = None
+
+MEC2_MEV = 0.51099895
+BC = {"open": 0, "periodic": 1}
+POL = {"none": 0, "lp-y": 1, "cp": 2}
+
+
+def build(force: bool = False) -> str:
+    """Compile pic_oracle.c into liboracle.so next to it (gcc, FP64, no FMA contraction)."""
+    src = os.path.join(_HERE, "pic_oracle.c")
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(src),
+                                                   os.path.getmtime(os.path.join(_HERE, "pic_oracle.h")))):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+                           src, "-o", tmp, "-lm"])
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("dx", C.c_double), ("dy", C.c_double),
+                ("dt", C.c_double), ("bc_x", C.c_int), ("pol", C.c_int), ("a0", C.c_double),
+                ("w0", C.c_double), ("tau", C.c_double), ("t_peak", C.c_double)]
+
+
+class Spec(C.Structure):
+    _fields_ = [("q", C.c_double), ("m", C.c_double), ("a", C.c_double)]
+
+
+_DP = C.POINTER(C.c_double)
+_IP = C.POINTER(C.c_int)
+
+
+class Fields(C.Structure):
+    _fields_ = [(k, _DP) for k in ("ex", "ey", "ez", "bx", "by", "bz", "jx", "jy", "jz", "byL", "bzL")]
+
+
+class Parts(C.Structure):
+    _fields_ = [("n", C.c_long)] + [(k, _DP) for k in
+                                    ("x", "y", "ux", "uy", "uz", "sx", "sy", "sz", "w")] + [("alive", _IP)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if _LIB_OVERRIDE:
+            L = C.CDLL(_LIB_OVERRIDE)
+        else:
+            build()
+            L = C.CDLL(_LIB_PATH)
+        G, S, F, P = C.POINTER(Grid), C.POINTER(Spec), C.POINTER(Fields), C.POINTER(Parts)
+        sig = {
+            "or_gather": (None, [G, F, C.c_double, C.c_double, _DP, _DP]),
+            "or_boris": (None, [C.c_double, C.c_double, _DP, _DP, _DP]),
+            "or_omega": (None, [C.c_double, C.c_double, _DP, _DP, _DP, _DP]),
+            "or_spin_rotate": (None, [_DP, C.c_double, _DP]),
+            "or_deposit_one": (None, [G, F, C.c_double, C.c_double, C.c_double, C.c_double,
+                                      C.c_double, C.c_double]),
+            "or_push": (None, [G, S, P, F, _DP, _DP, _DP]),
+            "or_deposit": (None, [G, S, P, _DP, _DP, _DP, F]),
+            "or_field_update": (None, [G, F, C.c_long]),
+            "or_laser": (None, [G, C.c_double, C.c_double, C.c_int, _DP]),
+            "or_step": (None, [G, S, P, _IP, C.c_int, F, C.c_long]),
+            "or_rho": (None, [G, S, P, _DP]),
+            "or_div_e": (None, [G, F, _DP]),
+            "or_div_b": (None, [G, F, _DP]),
+            "or_moments": (None, [S, P, C.c_double, C.c_double, _DP]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_DP)
+
+
+def _v3(x):
+    return (C.c_double * 3)(*[float(v) for v in x])
+
+
+# ---------------------------------------------------------------------------
+# single-particle parts, for closed-form tests
+# ---------------------------------------------------------------------------
+def boris(qm, dt, E, B, u):
+    uu = _v3(u)
+    lib().or_boris(qm, dt, _v3(E), _v3(B), uu)
+    return np.array(uu[:])
+
+
+def omega(qm, a, ubar, E, B):
+    out = _v3((0, 0, 0))
+    lib().or_omega(qm, a, _v3(ubar), _v3(E), _v3(B), out)
+    return np.array(out[:])
+
+
+def spin_rotate(Om, dt, s):
+    ss = _v3(s)
+    lib().or_spin_rotate(_v3(Om), dt, ss)
+    return np.array(ss[:])
+
+
+def derive_grid(wl) -> Grid:
+    """The oracle's own units: lengths in c/omega0 (lambda = 2 pi), time in 1/omega0."""
+    two_pi = 2.0 * math.pi
+    dx, dy = wl.dx_lambda * two_pi, wl.dy_lambda * two_pi
+    dt = wl.cfl / math.sqrt(1.0 / dx ** 2 + 1.0 / dy ** 2)
+    tau = wl.fwhm_periods * two_pi / math.sqrt(2.0 * math.log(2.0))
+    return Grid(nx=wl.nx, ny=wl.ny, dx=dx, dy=dy, dt=dt, bc_x=BC[wl.bc_x],
+                pol=POL[wl.pol] if wl.bc_x == "open" else 0, a0=wl.a0,
+                w0=wl.waist_lambda * two_pi, tau=tau, t_peak=wl.t_peak_periods * two_pi)
+
+
+class OracleSim:
+    """State of one oracle simulation: float64 mesh and particle arrays.
+
+    ``particles`` is the per-species list of dicts from
+    ``workloads.generate_particles``; positions become global cell coordinates
+    x = ix + ox, y = iy + oy.
+    """
+
+    FIELD_KEYS = ("ex", "ey", "ez", "bx", "by", "bz", "jx", "jy", "jz")
+
+    def __init__(self, wl, particles, fields=None, step=0):
+        self.wl = wl
+        self.grid = derive_grid(wl)
+        ny, nx = wl.ny, wl.nx
+        self.f = {k: np.zeros((ny, nx)) for k in self.FIELD_KEYS}
+        self.f["byL"] = np.zeros(ny)
+        self.f["bzL"] = np.zeros(ny)
+        if fields is not None:
+            for k, v in fields.items():
+                self.f[k][...] = np.asarray(v, dtype=np.float64)
+        self.spec = [Spec(q=s.q, m=s.m, a=s.a) for s in wl.species]
+        self.mobile = np.array([1 if s.mobile else 0 for s in wl.species], dtype=np.int32)
+        self.p = []
+        for d in particles:
+            self.p.append(dict(
+                x=d["ix"].astype(np.float64) + d["ox"].astype(np.float64),
+                y=d["iy"].astype(np.float64) + d["oy"].astype(np.float64),
+                ux=d["ux"].astype(np.float64), uy=d["uy"].astype(np.float64),
+                uz=d["uz"].astype(np.float64), sx=d["sx"].astype(np.float64),
+                sy=d["sy"].astype(np.float64), sz=d["sz"].astype(np.float64),
+                w=d["w"].astype(np.float64), alive=np.ones(len(d["ix"]), np.int32),
+                id=d["id"].copy()))
+        self.step_index = step
+        self.rho_bg = np.zeros((ny, nx))
+        if wl.neutralizing_background:
+            self.rho_bg = -self.rho()
+
+    # ctypes views --------------------------------------------------------
+    def _fields(self):
+        return Fields(**{k: _dp(self.f[k]) for k in self.f})
+
+    def _parts(self, s):
+        d = self.p[s]
+        kw = {k: _dp(d[k]) for k in ("x", "y", "ux", "uy", "uz", "sx", "sy", "sz", "w")}
+        return Parts(n=len(d["x"]), alive=d["alive"].ctypes.data_as(_IP), **kw)
+
+    # method parts ----------------------------------------------------------
+    def push(self, s):
+        """a1-a4 for species s; returns (x_old, y_old, vz) for the deposit."""
+        n = len(self.p[s]["x"])
+        xo, yo, vz = np.zeros(n), np.zeros(n), np.zeros(n)
+        pp = self._parts(s)
+        lib().or_push(C.byref(self.grid), C.byref(self.spec[s]), C.byref(pp),
+                      C.byref(self._fields()), _dp(xo), _dp(yo), _dp(vz))
+        return xo, yo, vz
+
+    def deposit(self, s, xo, yo, vz):
+        """a5 for species s (adds into J)."""
+        pp = self._parts(s)
+        lib().or_deposit(C.byref(self.grid), C.byref(self.spec[s]), C.byref(pp),
+                         _dp(xo), _dp(yo), _dp(vz), C.byref(self._fields()))
+
+    def zero_current(self):
+        for k in ("jx", "jy", "jz"):
+            self.f[k][...] = 0.0
+
+    def field_update(self):
+        """a6 at the current step index (does not advance it)."""
+        lib().or_field_update(C.byref(self.grid), C.byref(self._fields()), self.step_index)
+
+    def step(self, nsteps=1):
+        """Whole steps: zero J, push and deposit every mobile species, a6."""
+        nsp = len(self.p)
+        for _ in range(nsteps):
+            parts = (Parts * nsp)(*[self._parts(s) for s in range(nsp)])
+            specs = (Spec * nsp)(*self.spec)
+            lib().or_step(C.byref(self.grid), specs, parts,
+                          self.mobile.ctypes.data_as(_IP), nsp, C.byref(self._fields()),
+                          self.step_index)
+            self.step_index += 1
+
+    # diagnostics -------------------------------------------------------------
+    def rho(self):
+        r = np.zeros((self.wl.ny, self.wl.nx))
+        for s in range(len(self.p)):
+            pp = self._parts(s)
+            lib().or_rho(C.byref(self.grid), C.byref(self.spec[s]), C.byref(pp), _dp(r))
+        return r
+
+    def div_e(self):
+        d = np.zeros((self.wl.ny, self.wl.nx))
+        lib().or_div_e(C.byref(self.grid), C.byref(self._fields()), _dp(d))
+        return d
+
+    def div_b(self):
+        d = np.zeros((self.wl.ny, self.wl.nx))
+        lib().or_div_b(C.byref(self.grid), C.byref(self._fields()), _dp(d))
+        return d
+
+    def gauss_residual(self):
+        """div E - rho - rho_background on nodes; interior nodes only with open x
+        (nodes 0..2 and nx-3..nx-1 see the removal of particles)."""
+        r = self.div_e() - self.rho() - self.rho_bg
+        if self.wl.bc_x == "open":
+            r = r[:, 3:self.wl.nx - 3]
+        return r
+
+    def moments(self, s, emin=-np.inf, emax=np.inf):
+        out = (C.c_double * 7)()
+        pp = self._parts(s)
+        lib().or_moments(C.byref(self.spec[s]), C.byref(pp), float(emin), float(emax), out)
+        return np.array(out[:])
+
+    def laser(self, t, y, comp):
+        v = C.c_double()
+        lib().or_laser(C.byref(self.grid), t, y, comp, C.byref(v))
+        return v.value

@@ -1,0 +1,165 @@
+"""Seeded synthetic workloads shared by the CUDA path and the oracle.
+
+This module holds data only: the workload parameters (the paper's setup of
+Sec. 2 scaled to the 2D3V cases built here) and seeded random draws of the
+initial particle state and, for single-step tests, of random mesh fields.  It
+contains none of the method's arithmetic; both the oracle and the CUDA
+library derive their own time step, units and boundary handling from these
+parameters.
+
+Particle state of one species (all arrays of length n):
+  ix, iy   int32   cell indices (node i sits at x = i dx)
+  ox, oy   float32 offsets inside the cell, in [0, 1)
+  ux,uy,uz float32 momentum u = p / (m c)
+  sx,sy,sz float32 unit spin
+  w        float32 density carried by the macro-particle [n_c]
+  id       int32   particle identity (index at creation)
+Every float is drawn as a float32 value, so the oracle's float64 copy of the
+state is exactly the state the GPU holds.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = ["Species", "Workload", "CONFIG1", "CONFIG3", "generate_particles",
+           "random_fields", "small_case", "scaled"]
+
+
+@dataclass(frozen=True)
+class Species:
+    name: str
+    q: float            # charge [e]
+    m: float            # mass [m_e]
+    a: float            # gyromagnetic anomaly
+    n0: float           # density [n_c]
+    ppc: int            # macro-particles per cell
+    u_th: float         # thermal spread of each momentum component [m c]
+    s0: tuple           # initial spin (unit vector)
+    mobile: bool = True
+    colocate_with: int = -1   # reuse the positions of this species (a neutral start)
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    nx: int
+    ny: int
+    dx_lambda: float          # cell size in laser wavelengths
+    dy_lambda: float
+    cfl: float                # dt = cfl / sqrt(1/dx^2 + 1/dy^2)
+    steps: int
+    species: tuple
+    a0: float = 0.0
+    waist_lambda: float = 4.0
+    fwhm_periods: float = 10.0   # FWHM of the intensity, in laser periods
+    t_peak_periods: float = 15.0
+    pol: str = "lp-y"            # "lp-y", "cp" or "none"
+    bc_x: str = "open"           # "open" (laser enters at x_min) or "periodic"
+    neutralizing_background: bool = False  # immobile ions = -rho_e at t = 0
+    seed: int = 1
+    lambda_um: float = 0.8
+
+
+ELECTRON = dict(q=-1.0, m=1.0, a=0.00116)
+PROTON = dict(q=1.0, m=1836.0, a=1.793)
+
+# 2D3V uniform electron plasma with immobile ions, LP laser a0 = 4 (131,072 electrons).
+CONFIG1 = Workload(
+    name="2d3v-256x128-ppc4-lp-a0_4",
+    nx=256, ny=128, dx_lambda=1 / 16, dy_lambda=1 / 16, cfl=0.95, steps=400,
+    species=(Species("electron", n0=0.01, ppc=4, u_th=1e-3, s0=(0.0, 1.0, 0.0), **ELECTRON),),
+    a0=4.0, waist_lambda=4.0, fwhm_periods=10.0, t_peak_periods=15.0, pol="lp-y",
+    bc_x="open", neutralizing_background=True, seed=1)
+
+# 2D3V high-density pre-polarised hydrogen: 8 ppc electrons + 8 ppc protons
+# (67,043,328 particles: every cell but the two-cell vacuum margins at x_min and
+# x_max; 67,108,864 with all cells filled), spins +x, CP laser a0 = 60.
+CONFIG3 = Workload(
+    name="2d3v-4096x1024-e8p8-cp-a0_60",
+    nx=4096, ny=1024, dx_lambda=1 / 32, dy_lambda=1 / 32, cfl=0.95, steps=5000,
+    species=(Species("electron", n0=0.2, ppc=8, u_th=1e-3, s0=(1.0, 0.0, 0.0), **ELECTRON),
+             Species("proton", n0=0.2, ppc=8, u_th=1e-3 * math.sqrt(1 / 1836.0),
+                     s0=(1.0, 0.0, 0.0), colocate_with=0, **PROTON)),
+    a0=60.0, waist_lambda=8.0, fwhm_periods=10.0, t_peak_periods=15.0, pol="cp",
+    bc_x="open", neutralizing_background=False, seed=3)
+
+
+def scaled(wl: Workload, **kw) -> Workload:
+    """A copy of a workload with some fields replaced."""
+    return dataclasses.replace(wl, **kw)
+
+
+def small_case(nx=40, ny=24, ppc=2, bc_x="open", seed=11, pol="lp-y", a0=4.0,
+               two_species=False, u_th=0.05) -> Workload:
+    """Few-tile test workload; nx, ny need not be tile multiples (ragged edges)."""
+    sp = [Species("electron", n0=0.05, ppc=ppc, u_th=u_th, s0=(0.0, 1.0, 0.0), **ELECTRON)]
+    if two_species:
+        sp.append(Species("proton", n0=0.05, ppc=ppc, u_th=u_th / 20, s0=(1.0, 0.0, 0.0),
+                          colocate_with=0, **PROTON))
+    return Workload(name=f"small-{nx}x{ny}", nx=nx, ny=ny, dx_lambda=1 / 16, dy_lambda=1 / 16,
+                    cfl=0.95, steps=10, species=tuple(sp), a0=a0, waist_lambda=1.0,
+                    fwhm_periods=2.0, t_peak_periods=1.0, pol=pol, bc_x=bc_x,
+                    neutralizing_background=not two_species, seed=seed)
+
+
+def _region_x(wl: Workload):
+    """Cells that hold plasma along x: all of them when x is periodic, else a
+    two-cell vacuum margin at each end (particles live in [2, nx-2))."""
+    if wl.bc_x == "periodic":
+        return 0, wl.nx
+    return 2, wl.nx - 2
+
+
+def generate_particles(wl: Workload, seed: int | None = None):
+    """Initial particles of every species: uniform random positions inside
+    each cell, Gaussian thermal momenta, equal spins and weights.
+
+    Order is ppc-major (all cells for the first macro-particle of each cell,
+    then the second, ...), so neighbouring entries sit in neighbouring cells.
+    Returns a list with one dict of arrays per species.
+    """
+    rng = np.random.default_rng(wl.seed if seed is None else seed)
+    x0, x1 = _region_x(wl)
+    ncx = x1 - x0
+    gy, gx = np.meshgrid(np.arange(wl.ny, dtype=np.int32),
+                         np.arange(x0, x1, dtype=np.int32), indexing="ij")
+    out = []
+    for s, sp in enumerate(wl.species):
+        n = sp.ppc * ncx * wl.ny
+        if sp.colocate_with >= 0:
+            ref = out[sp.colocate_with]
+            if len(ref["ix"]) != n:
+                raise ValueError("co-located species need the same particle count")
+            ix, iy, ox, oy = ref["ix"], ref["iy"], ref["ox"], ref["oy"]
+        else:
+            ix = np.tile(gx.ravel(), sp.ppc)
+            iy = np.tile(gy.ravel(), sp.ppc)
+            ox = rng.random(n, dtype=np.float32)
+            oy = rng.random(n, dtype=np.float32)
+        uth = np.float32(sp.u_th)
+        ux = rng.standard_normal(n, dtype=np.float32) * uth
+        uy = rng.standard_normal(n, dtype=np.float32) * uth
+        uz = rng.standard_normal(n, dtype=np.float32) * uth
+        s0 = np.asarray(sp.s0, dtype=np.float32)
+        out.append(dict(
+            ix=ix, iy=iy, ox=ox, oy=oy, ux=ux, uy=uy, uz=uz,
+            sx=np.full(n, s0[0], np.float32), sy=np.full(n, s0[1], np.float32),
+            sz=np.full(n, s0[2], np.float32),
+            w=np.full(n, np.float32(sp.n0 / sp.ppc), np.float32),
+            id=np.arange(n, dtype=np.int32)))
+    return out
+
+
+def random_fields(wl: Workload, seed: int, e_amp: float = 0.5, b_amp: float = 0.5):
+    """Random mesh fields (float32, [ny][nx]) for single-step tests."""
+    rng = np.random.default_rng(seed)
+    shape = (wl.ny, wl.nx)
+    f = {}
+    for k, amp in (("ex", e_amp), ("ey", e_amp), ("ez", e_amp),
+                   ("bx", b_amp), ("by", b_amp), ("bz", b_amp)):
+        f[k] = (rng.standard_normal(shape, dtype=np.float32) * np.float32(amp))
+    return f
