@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""Throughput of the 2D3V PIC + Thomas-BMT step on GB300.
+
+One step = the fused gather / Boris / spin / advance / Esirkepov kernel
+(pic_push_deposit), the Yee update (pic_field_update), the tile sort every
+--sort-every steps and the FP64 Eq. (4) moments of every species every
+--diag-every steps, on the high-density pre-polarised hydrogen workload:
+4096 x 1024 cells (dx = lambda/32), 8 ppc electrons + 8 ppc protons, CP laser
+a0 = 60.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Several GPUs run independent replicas (one per rank, launched by torchrun):
+the step has no exchange between runs, so there is no collective on the
+data path; ranks only meet at the barriers around the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "particle-steps/s (push+spin+deposit) and % HBM roofline, FP32 vs FP64 at stated error"
+UNIT = "particle-steps/s"
+# algorithmic bytes of the fused kernel: per particle read cell, ox, oy, u(3),
+# s(3), w = 40 B and write cell, ox, oy, u, s = 36 B; per cell the E, B
+# window (24 B) and the current added to J (12 B)
+BYTES_PER_PARTICLE = 76
+BYTES_PER_CELL = 36
+CPU_SAMPLE_NY = 32
+CPU_SAMPLE_STEPS = 6
+
+
+def parse(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=4)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["config3", "config1"], default="config3")
+    ap.add_argument("--sort-every", type=int, default=8)
+    ap.add_argument("--diag-every", type=int, default=10)
+    ap.add_argument("--tile", type=int, nargs=2, default=(0, 0))
+    ap.add_argument("--ny", type=int, default=0, help="smaller ny for profiling captures")
+    ap.add_argument("--e2e-steps", type=int, default=4)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args(argv)
+
+
+def workload(name, ny=0):
+    wl = W.CONFIG3 if name == "config3" else W.CONFIG1
+    return W.scaled(wl, ny=ny) if ny else wl
+
+
+# ---------------------------------------------------------------------------
+# ranks: replicas only
+# ---------------------------------------------------------------------------
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), \
+        int(os.environ.get("LOCAL_RANK", 0))
+
+
+def init_dist(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend)
+    return dist
+
+
+def combine(elapsed_s, units, world, device=None):
+    """Whole-job numbers from every rank: the slowest rank's time and the sum
+    of the units all ranks processed."""
+    if world == 1:
+        return elapsed_s, units
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([elapsed_s], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+
+        sm = [num(r[1]) for r in rows]
+        mx = [num(r[2]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.nanmedian(sm)), "sm_max_mhz": float(np.nanmax(mx)),
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": float(np.nanmax([num(r[3]) for r in rows]))}
+
+
+def measured_hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def traffic_record():
+    """dram bytes per launch of the fused kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "k_step_fused.traffic.json")
+    try:
+        with open(p) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("k_particles.cu", "pic_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2002_02211_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if rec.get("source_sha256") != h.hexdigest():
+        return None
+    return rec
+
+
+# ---------------------------------------------------------------------------
+# the oracle leg (CPU baseline and --impl reference)
+# ---------------------------------------------------------------------------
+def cpu_sample(wl):
+    import oracle
+    sample = W.scaled(wl, ny=CPU_SAMPLE_NY)
+    parts = W.generate_particles(sample)
+    sim = oracle.OracleSim(sample, parts)
+    n = sum(len(p["x"]) for p in sim.p)
+    desc = (f"{wl.name} with ny={CPU_SAMPLE_NY} ({sample.nx}x{sample.ny} cells, {n} particles), "
+            f"FP64 C oracle, single thread")
+    return sim, n, desc
+
+
+def run_oracle_steps(sim, steps):
+    t0 = time.perf_counter()
+    sim.step(steps)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(wl):
+    sim, n, desc = cpu_sample(wl)
+    dt = run_oracle_steps(sim, CPU_SAMPLE_STEPS)
+    return {"value": n * CPU_SAMPLE_STEPS / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{CPU_SAMPLE_STEPS} steps of {desc}", "seconds": round(dt, 2)}
+
+
+def main_reference(args):
+    rank, world, _ = dist_env()
+    wl = workload(args.workload, args.ny)
+    if rank != 0:
+        return
+    sim, n, desc = cpu_sample(wl)
+    run_oracle_steps(sim, args.warmup)
+    dt = run_oracle_steps(sim, args.steps)
+    v = n * args.steps / dt
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": wl.name, "sample": desc},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} steps of {desc}"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def main_ours(args):
+    import torch
+
+    import paper_2002_02211_gb300 as pic
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    init_dist(world, "nccl")
+    dev = torch.device("cuda", local)
+    wl = workload(args.workload, args.ny)
+    parts = W.generate_particles(wl)
+    n_particles = sum(len(p["ix"]) for p in parts)
+    n_cells = wl.nx * wl.ny
+
+    stream = torch.cuda.Stream(device=dev)
+    cfg = pic.config_from_workload(wl, sort_every=args.sort_every, tile=tuple(args.tile))
+    sim = pic.Simulation(cfg, stream=stream)
+    for s, d in enumerate(parts):
+        sim.set_particles(s, d)
+    if wl.neutralizing_background:
+        sim.capture_background()
+    sim.sync()
+
+    state = {"since_sort": 0, "k": 0}
+    ev_pairs = []
+
+    def one_step(record):
+        if state["since_sort"] >= args.sort_every:
+            sim.sort()
+            state["since_sort"] = 0
+        if record:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        sim.push_deposit()
+        if record:
+            e1.record(stream)
+            ev_pairs.append((e0, e1))
+        sim.field_update()
+        state["since_sort"] += 1
+        state["k"] += 1
+        if state["k"] % args.diag_every == 0:
+            for s in range(len(wl.species)):
+                sim.polarization(s)
+
+    for _ in range(args.warmup):
+        one_step(False)
+    sim.sync()
+
+    clocks = ClockSampler(local)
+    launches0 = sim.launch_count()
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(args.steps):
+        one_step(True)
+    end.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clk = clocks.stop()
+    launches = sim.launch_count() - launches0
+    sim.sync()
+
+    elapsed = start.elapsed_time(end) * 1e-3
+    t_fused = float(np.mean([a.elapsed_time(b) for a, b in ev_pairs])) * 1e-3
+    tmax, units = combine(elapsed, n_particles * args.steps, world, dev)
+    value = units / tmax
+
+    peak, peak_kind = measured_hbm_peak()
+    bytes_fused = BYTES_PER_PARTICLE * n_particles + BYTES_PER_CELL * n_cells
+    achieved = bytes_fused / t_fused / 1e9
+    tr = traffic_record()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": tr["dram_bytes_per_launch"] if tr else None,
+                "kernel": "k_step_fused", "kernel_ms": t_fused * 1e3,
+                "algorithmic_bytes": bytes_fused, "peak_source": f"{peak_kind} hbm_gbs"}
+
+    # end to end through the C ABI with host buffers: upload the particle state
+    # from pinned memory, one step, read back the Eq. (4) moments
+    e2e = None
+    if not args.no_e2e and args.e2e_steps > 0:
+        pinned = []
+        ptrs = []
+        for d in parts:
+            pp = {}
+            for k in ("ix", "iy", "ox", "oy", "ux", "uy", "uz", "sx", "sy", "sz", "w", "id"):
+                t = torch.from_numpy(np.ascontiguousarray(d[k])).pin_memory()
+                pinned.append(t)
+                pp[k] = t.data_ptr()
+            ptrs.append((len(d["ix"]), pp))
+        h2d = sum(len(d["ix"]) * 4 * 12 for d in parts)
+        d2h = len(parts) * 7 * 8
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            for s, (n, pp) in enumerate(ptrs):
+                sim.set_particles_raw(s, n, pp)
+            sim.push_deposit()
+            sim.field_update()
+            for s in range(len(parts)):
+                sim.polarization(s)
+        torch.cuda.synchronize(dev)
+        te = time.perf_counter() - t0
+        te, eu = combine(te, n_particles * args.e2e_steps, world, dev)
+        e2e = {"value": eu / te, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "steps": args.e2e_steps,
+               "what": "per step: pic_set_particles of every species from pinned host memory "
+                       "(H2D + tile sort), pic_push_deposit, pic_field_update, pic_polarization "
+                       "of every species (D2H)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl)
+
+    sim.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": tmax * 1e3 / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": wl.name, "cells": [wl.nx, wl.ny], "particles": n_particles,
+                           "species": [s.name for s in wl.species], "sort_every": args.sort_every,
+                           "diag_every": args.diag_every, "tile": list(args.tile),
+                           "l2": "inputs larger than L2 (particle state 2.95 GB)",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": launches}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main(argv=None):
+    args = parse(argv)
+    if args.impl == "reference":
+        main_reference(args)
+    else:
+        main_ours(args)
+
+
+if __name__ == "__main__":
+    main()

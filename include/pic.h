@@ -1,0 +1,212 @@
+/*
+ * pic.h -- C ABI of the GB300 (sm_103a) 2D3V electromagnetic particle-in-cell
+ * step with Thomas-BMT spin tracking.
+ *
+ * The method (Sec. 2 of Huetzen et al., "Simulation of Polarized Beams from
+ * Laser-Plasma Accelerators"): particles are pushed in the plasma and laser
+ * fields, and each macro-particle carries a classical spin s that precesses
+ * by ds/dt = -Omega x s (Eq. 1) with Omega from Eqs. (2)-(3); the beam
+ * polarization is the ensemble mean of s (Eq. 4).  The particle-in-cell parts
+ * the paper leaves to its PIC code are the standard ones: CIC field gather
+ * on the Yee mesh, Boris push, Esirkepov charge-conserving current and Yee
+ * FDTD field update.
+ *
+ * Units (normalised): time 1/omega0, length c/omega0, momentum u = p/(m c),
+ * fields m_e c omega0 / e, density n_c, charge e, mass m_e; omega0 = 2 pi c / lambda.
+ *
+ * Conventions for every entry point:
+ *   - the return value is a pic_status_t; nothing throws across the ABI;
+ *     pic_last_error() gives a one-line reason for the last failure;
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream); compute calls are asynchronous on it; calls documented as
+ *     "synchronous" wait for the stream before returning;
+ *   - the context owns all device memory it allocates (cudaMalloc at
+ *     pic_create, freed at pic_destroy); host pointers passed in are only
+ *     read or written during the call;
+ *   - a context is bound to the CUDA device that was current at pic_create;
+ *     calls on one context must not overlap (one host thread at a time).
+ *
+ * Mesh layout (host arrays are row-major [ny][nx] float32).  Element [j][i] of
+ *   Ex sits at (i+1/2, j)   Ey at (i, j+1/2)   Ez at (i, j)
+ *   Bx at (i, j+1/2)        By at (i+1/2, j)   Bz at (i+1/2, j+1/2)
+ *   Jx, Jy, Jz as Ex, Ey, Ez   (node i is at x = i dx).
+ * y is periodic.  With PIC_BC_OPEN along x a first-order Silver-Mueller
+ * boundary absorbs outgoing waves at both ends and injects the laser at x = 0;
+ * By[j][nx-1] and Bz[j][nx-1] (x = nx - 1/2) then hold boundary values, and the
+ * left boundary values By(-1/2), Bz(-1/2) are the arrays by_left, bz_left [ny].
+ * Particles live in [2, nx-2) along x with open boundaries (a particle that
+ * leaves is removed after its current is deposited) and wrap when periodic.
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PIC_OK = 0,
+    PIC_ERR_ARG = -1,      /* invalid argument or configuration; nothing was done   */
+    PIC_ERR_CUDA = -2,     /* a CUDA call failed (out of memory, launch failure...) */
+    PIC_ERR_NAN = -3,      /* a kernel produced a non-finite momentum or spin       */
+    PIC_ERR_CFL = -4,      /* a particle moved a cell or more in one step           */
+    PIC_ERR_OVERFLOW = -5, /* more particles than the species capacity              */
+    PIC_ERR_TIMEOUT = -6,  /* a bounded device-side wait gave up (tile staging)     */
+    PIC_ERR_STATE = -7     /* call not valid in the context's current state         */
+} pic_status_t;
+
+#define PIC_MAX_SPECIES 4
+#define PIC_BC_OPEN 0
+#define PIC_BC_PERIODIC 1
+#define PIC_POL_NONE 0
+#define PIC_POL_LP_Y 1 /* linear, E along y                         */
+#define PIC_POL_CP 2   /* circular, a0/sqrt(2) in each of Ey and Ez */
+
+typedef struct {
+    double q;            /* charge [e]                                  */
+    double m;            /* mass [m_e]                                  */
+    double a;            /* gyromagnetic anomaly (Eq. 3): e 0.00116, p 1.793 */
+    int mobile;          /* 0: never pushed (contributes only to rho)   */
+    int64_t capacity;    /* device slots reserved for this species      */
+} pic_species_t;
+
+typedef struct {
+    int nx, ny;                  /* cells; nx >= 8, ny >= 4, both <= 32767        */
+    double dx_lambda, dy_lambda; /* cell size in laser wavelengths                 */
+    double cfl;                  /* dt = cfl / sqrt(1/dx^2 + 1/dy^2), 0 < cfl < 1  */
+    int bc_x;                    /* PIC_BC_OPEN or PIC_BC_PERIODIC                 */
+    int pol;                     /* PIC_POL_*, used with PIC_BC_OPEN               */
+    double a0;                   /* peak normalised amplitude e A / (m_e c)        */
+    double waist_lambda;         /* 1/e field radius at x = 0 [lambda]             */
+    double fwhm_periods;         /* FWHM of the intensity [laser periods]          */
+    double t_peak_periods;       /* time of the envelope peak at x = 0 [periods]   */
+    int nspecies;                /* 1 .. PIC_MAX_SPECIES                           */
+    pic_species_t sp[PIC_MAX_SPECIES];
+    int sort_every;              /* steps between tile sorts in pic_step (0: 8)    */
+    int tile_x, tile_y;          /* cells per tile (0: chosen from the mesh size); tile_x % 4 == 0 */
+} pic_config_t;
+
+/* Host-side particle arrays of one species (n entries each).  ix, iy are cell
+ * indices and ox, oy in [0, 1) the offsets inside the cell (x = (ix + ox) dx). */
+typedef struct {
+    int64_t n;
+    int32_t *ix, *iy;
+    float *ox, *oy;
+    float *ux, *uy, *uz;  /* u = p / (m c) */
+    float *sx, *sy, *sz;  /* spin          */
+    float *w;             /* density carried by the macro-particle [n_c] */
+    int32_t *id;          /* caller's particle identity, carried through sorts */
+} pic_particles_t;
+
+/* Host-side mesh arrays, [ny][nx] float32 each (by_left, bz_left: [ny]).
+ * A NULL member is skipped by pic_set_fields / pic_get_fields. */
+typedef struct {
+    float *ex, *ey, *ez, *bx, *by, *bz, *jx, *jy, *jz;
+    float *by_left, *bz_left;
+} pic_fields_t;
+
+/* Moments of Eq. (4) over the live particles of one species whose kinetic
+ * energy (gamma - 1) m c^2 lies in [emin, emax) MeV, accumulated in FP64. */
+typedef struct {
+    double P[3];       /* sum w s / sum w  (Eq. 4; equal weights give (1/N) sum s) */
+    double sum_w;
+    double count;
+    double ekin_mean;  /* weighted mean kinetic energy [MeV]   */
+    double ekin_var;   /* weighted variance [MeV^2]             */
+} pic_moments_t;
+
+/* Host-only check of a configuration (no CUDA call).  PIC_OK or PIC_ERR_ARG. */
+pic_status_t pic_validate_config(const pic_config_t *cfg);
+
+/* Creates a context on the current device: allocates the mesh and particle
+ * storage, zero fields, no particles, step index 0.  Synchronous. */
+pic_status_t pic_create(const pic_config_t *cfg, void *stream, void **ctx_out);
+
+/* Releases everything the context owns.  NULL is accepted. */
+void pic_destroy(void *ctx);
+
+/* Time step dt [1/omega0] and cell sizes dx, dy [c/omega0] the context derived. */
+pic_status_t pic_get_grid(void *ctx, double *dt, double *dx, double *dy);
+
+/* Loads the particles of one species from host arrays (replacing what was
+ * there) and sorts them by tile.  n <= capacity (else PIC_ERR_OVERFLOW).
+ * Cells must lie in the particle region (else PIC_ERR_ARG).  Synchronous. */
+pic_status_t pic_set_particles(void *ctx, int species, const pic_particles_t *p, void *stream);
+
+/* Number of particle slots of one species (live and removed since the last
+ * sort).  Synchronises the legacy default stream. */
+pic_status_t pic_get_count(void *ctx, int species, int64_t *n);
+
+/* Copies every slot into caller arrays with room for out->n entries (set
+ * out->n to that room; PIC_ERR_ARG if the slots do not fit); on return out->n
+ * is the slot count.  A removed particle has ix = iy = -1.  Synchronous. */
+pic_status_t pic_get_particles(void *ctx, int species, pic_particles_t *out, void *stream);
+
+/* Mesh arrays host <-> device.  Synchronous. */
+pic_status_t pic_set_fields(void *ctx, const pic_fields_t *f, void *stream);
+pic_status_t pic_get_fields(void *ctx, pic_fields_t *f, void *stream);
+
+/* Step index n (the fields are at t = n dt; the laser phase follows it). */
+pic_status_t pic_set_step(void *ctx, int64_t step);
+pic_status_t pic_get_step(void *ctx, int64_t *step);
+
+/* a1-a4 for every mobile species: CIC gather of E^n, B^n at x^n, Boris push
+ * u^{n-1/2} -> u^{n+1/2}, spin rotation s^{n-1/2} -> s^{n+1/2} by
+ * ds/dt = -Omega x s with Omega of Eqs. (2)-(3) at the mean momentum,
+ * x^{n+1} = x^n + dt u/gamma.  Keeps x^n and v_z for pic_deposit. */
+pic_status_t pic_gather_push_spin(void *ctx, void *stream);
+
+/* a5: adds the Esirkepov current J^{n+1/2} of the move made by the last
+ * pic_gather_push_spin (PIC_ERR_STATE if none is pending); removes particles
+ * that left the region.  J must hold what the caller wants added to (it is
+ * zero after pic_create and after every field update). */
+pic_status_t pic_deposit(void *ctx, void *stream);
+
+/* a6: B^{n+1/2} = B^n - dt/2 curl E^n; boundary values at t^{n+1/2};
+ * E^{n+1} = E^n + dt (curl B^{n+1/2} - J); B^{n+1} = B^{n+1/2} - dt/2 curl E^{n+1};
+ * then J = 0 and n += 1. */
+pic_status_t pic_field_update(void *ctx, void *stream);
+
+/* a7: counting sort of every species by tile (drops removed particles). */
+pic_status_t pic_sort(void *ctx, void *stream);
+
+/* a1-a5 in one kernel: per tile, the field window is staged into shared
+ * memory by TMA and the current is accumulated there before being added to
+ * J.  Same result as pic_gather_push_spin + pic_deposit up to float rounding
+ * order of the current sums. */
+pic_status_t pic_push_deposit(void *ctx, void *stream);
+
+/* nsteps whole steps: pic_sort when sort_every steps have passed since the
+ * last sort (counted across calls), then pic_push_deposit and
+ * pic_field_update.  No host synchronisation. */
+pic_status_t pic_step(void *ctx, int nsteps, void *stream);
+
+/* a8: Eq. (4) moments of one species in an energy window.  Synchronous;
+ * also reports device-side error flags (PIC_ERR_NAN, PIC_ERR_TIMEOUT). */
+pic_status_t pic_polarization(void *ctx, int species, double emin_mev, double emax_mev,
+                              pic_moments_t *out, void *stream);
+
+/* Sets the immobile background charge to minus the CIC charge density of
+ * the current particles (a neutral start).  Asynchronous. */
+pic_status_t pic_capture_background(void *ctx, void *stream);
+
+/* Charge-conservation residual div E - rho - rho_background on the nodes
+ * i in [3, nx-4] (open x) or all nodes (periodic): out[0] = max |r|,
+ * out[1] = sqrt(sum r^2 / count), FP64.  Synchronous. */
+pic_status_t pic_gauss_residual(void *ctx, double out[2], void *stream);
+
+/* Waits for the stream and reports device-side error flags. */
+pic_status_t pic_sync(void *ctx, void *stream);
+
+/* Number of CUDA kernels this context has launched so far (host counter). */
+pic_status_t pic_launch_count(void *ctx, int64_t *count);
+
+/* Reason for the last failure on this context (or of pic_create when ctx is NULL). */
+const char *pic_last_error(void *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

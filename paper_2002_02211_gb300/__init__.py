@@ -1,0 +1,302 @@
+"""Python binding of libpic.so, the GB300 (sm_103a) 2D3V PIC + Thomas-BMT step.
+
+Argument marshalling only: every function below calls the C entry point of
+the same name declared in include/pic.h, and all arithmetic runs in the CUDA
+kernels.  Device memory is owned by the library; CUDA streams come from
+PyTorch (pass ``torch.cuda.current_stream()`` or any ``torch.cuda.Stream``)
+or are None for the legacy default stream.
+
+There is no CPU fallback: loading fails loudly if the library cannot be built
+or opened.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["PicError", "pic_config_t", "pic_species_t", "config_from_workload", "Simulation",
+           "load", "LIB_PATH"]
+
+LIB_PATH = _build.LIB
+MAX_SPECIES = 4
+BC = {"open": 0, "periodic": 1}
+POL = {"none": 0, "lp-y": 1, "cp": 2}
+STATUS = {0: "PIC_OK", -1: "PIC_ERR_ARG", -2: "PIC_ERR_CUDA", -3: "PIC_ERR_NAN", -4: "PIC_ERR_CFL",
+          -5: "PIC_ERR_OVERFLOW", -6: "PIC_ERR_TIMEOUT", -7: "PIC_ERR_STATE"}
+
+
+class PicError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class pic_species_t(C.Structure):
+    _fields_ = [("q", C.c_double), ("m", C.c_double), ("a", C.c_double), ("mobile", C.c_int),
+                ("capacity", C.c_int64)]
+
+
+class pic_config_t(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("dx_lambda", C.c_double), ("dy_lambda", C.c_double),
+                ("cfl", C.c_double), ("bc_x", C.c_int), ("pol", C.c_int), ("a0", C.c_double),
+                ("waist_lambda", C.c_double), ("fwhm_periods", C.c_double),
+                ("t_peak_periods", C.c_double), ("nspecies", C.c_int),
+                ("sp", pic_species_t * MAX_SPECIES), ("sort_every", C.c_int), ("tile_x", C.c_int),
+                ("tile_y", C.c_int)]
+
+
+_I32P = C.POINTER(C.c_int32)
+_F32P = C.POINTER(C.c_float)
+
+
+class pic_particles_t(C.Structure):
+    _fields_ = [("n", C.c_int64), ("ix", _I32P), ("iy", _I32P), ("ox", _F32P), ("oy", _F32P),
+                ("ux", _F32P), ("uy", _F32P), ("uz", _F32P), ("sx", _F32P), ("sy", _F32P),
+                ("sz", _F32P), ("w", _F32P), ("id", _I32P)]
+
+
+class pic_fields_t(C.Structure):
+    _fields_ = [(k, _F32P) for k in ("ex", "ey", "ez", "bx", "by", "bz", "jx", "jy", "jz",
+                                     "by_left", "bz_left")]
+
+
+class pic_moments_t(C.Structure):
+    _fields_ = [("P", C.c_double * 3), ("sum_w", C.c_double), ("count", C.c_double),
+                ("ekin_mean", C.c_double), ("ekin_var", C.c_double)]
+
+
+_lib = None
+
+_SIGS = {
+    "pic_validate_config": [C.POINTER(pic_config_t)],
+    "pic_create": [C.POINTER(pic_config_t), C.c_void_p, C.POINTER(C.c_void_p)],
+    "pic_get_grid": [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)],
+    "pic_set_particles": [C.c_void_p, C.c_int, C.POINTER(pic_particles_t), C.c_void_p],
+    "pic_get_count": [C.c_void_p, C.c_int, C.POINTER(C.c_int64)],
+    "pic_get_particles": [C.c_void_p, C.c_int, C.POINTER(pic_particles_t), C.c_void_p],
+    "pic_set_fields": [C.c_void_p, C.POINTER(pic_fields_t), C.c_void_p],
+    "pic_get_fields": [C.c_void_p, C.POINTER(pic_fields_t), C.c_void_p],
+    "pic_set_step": [C.c_void_p, C.c_int64],
+    "pic_get_step": [C.c_void_p, C.POINTER(C.c_int64)],
+    "pic_gather_push_spin": [C.c_void_p, C.c_void_p],
+    "pic_deposit": [C.c_void_p, C.c_void_p],
+    "pic_field_update": [C.c_void_p, C.c_void_p],
+    "pic_sort": [C.c_void_p, C.c_void_p],
+    "pic_push_deposit": [C.c_void_p, C.c_void_p],
+    "pic_step": [C.c_void_p, C.c_int, C.c_void_p],
+    "pic_launch_count": [C.c_void_p, C.POINTER(C.c_int64)],
+    "pic_polarization": [C.c_void_p, C.c_int, C.c_double, C.c_double, C.POINTER(pic_moments_t),
+                         C.c_void_p],
+    "pic_capture_background": [C.c_void_p, C.c_void_p],
+    "pic_gauss_residual": [C.c_void_p, C.POINTER(C.c_double), C.c_void_p],
+    "pic_sync": [C.c_void_p, C.c_void_p],
+}
+
+
+def load(build: bool = True):
+    """Opens libpic.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        if build:
+            _build.build()
+        if not os.path.exists(LIB_PATH):
+            raise OSError(f"CUDA library not built: {LIB_PATH}")
+        L = C.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = C.c_int
+        L.pic_destroy.argtypes = [C.c_void_p]
+        L.pic_destroy.restype = None
+        L.pic_last_error.argtypes = [C.c_void_p]
+        L.pic_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(status, ctx=None):
+    if status != 0:
+        msg = load().pic_last_error(ctx)
+        raise PicError(status, msg.decode() if msg else "")
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    h = getattr(stream, "cuda_stream", stream)
+    return C.c_void_p(int(h))
+
+
+def config_from_workload(wl, capacity_factor: float = 1.0, sort_every: int = 0, tile=(0, 0)):
+    """pic_config_t for a workload description (nx, ny, dx_lambda, ..., species)."""
+    cfg = pic_config_t()
+    cfg.nx, cfg.ny = wl.nx, wl.ny
+    cfg.dx_lambda, cfg.dy_lambda = wl.dx_lambda, wl.dy_lambda
+    cfg.cfl = wl.cfl
+    cfg.bc_x = BC[wl.bc_x]
+    cfg.pol = POL[wl.pol]
+    cfg.a0 = wl.a0
+    cfg.waist_lambda = wl.waist_lambda
+    cfg.fwhm_periods = wl.fwhm_periods
+    cfg.t_peak_periods = wl.t_peak_periods
+    cfg.nspecies = len(wl.species)
+    ncx = wl.nx if wl.bc_x == "periodic" else wl.nx - 4
+    for s, sp in enumerate(wl.species):
+        cfg.sp[s].q, cfg.sp[s].m, cfg.sp[s].a = sp.q, sp.m, sp.a
+        cfg.sp[s].mobile = 1 if sp.mobile else 0
+        cfg.sp[s].capacity = int(math.ceil(sp.ppc * ncx * wl.ny * capacity_factor))
+    cfg.sort_every = sort_every
+    cfg.tile_x, cfg.tile_y = tile
+    return cfg
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(t)
+
+
+class Simulation:
+    """One library context (pic_create ... pic_destroy) with numpy-facing calls."""
+
+    FIELD_KEYS = ("ex", "ey", "ez", "bx", "by", "bz", "jx", "jy", "jz")
+
+    def __init__(self, cfg: pic_config_t, stream=None):
+        L = load()
+        self.cfg = cfg
+        self.nx, self.ny = cfg.nx, cfg.ny
+        self.nspecies = cfg.nspecies
+        h = C.c_void_p()
+        _check(L.pic_create(C.byref(cfg), _stream(stream), C.byref(h)))
+        self.h = h
+        self.stream = stream
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().pic_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _c(self, status):
+        _check(status, self.h)
+
+    @property
+    def _s(self):
+        return _stream(self.stream)
+
+    def grid(self):
+        dt, dx, dy = C.c_double(), C.c_double(), C.c_double()
+        self._c(load().pic_get_grid(self.h, C.byref(dt), C.byref(dx), C.byref(dy)))
+        return dt.value, dx.value, dy.value
+
+    # state ----------------------------------------------------------------
+    def set_particles(self, s, d):
+        n = len(d["ix"])
+        arr = {k: np.ascontiguousarray(d[k], dtype=np.int32 if k in ("ix", "iy", "id") else np.float32)
+               for k in ("ix", "iy", "ox", "oy", "ux", "uy", "uz", "sx", "sy", "sz", "w", "id")}
+        p = pic_particles_t(n=n, **{k: _ptr(v, _I32P if v.dtype == np.int32 else _F32P)
+                                    for k, v in arr.items()})
+        self._c(load().pic_set_particles(self.h, s, C.byref(p), self._s))
+
+    def set_particles_raw(self, s, n, ptrs):
+        """Like set_particles, from raw host addresses (e.g. pinned buffers):
+        ptrs maps every pic_particles_t array name to an integer address."""
+        kw = {k: C.cast(C.c_void_p(int(v)), _I32P if k in ("ix", "iy", "id") else _F32P)
+              for k, v in ptrs.items()}
+        p = pic_particles_t(n=int(n), **kw)
+        self._c(load().pic_set_particles(self.h, s, C.byref(p), self._s))
+
+    def count(self, s):
+        n = C.c_int64()
+        self._c(load().pic_get_count(self.h, s, C.byref(n)))
+        return n.value
+
+    def get_particles(self, s):
+        n = self.count(s)
+        out = {k: np.empty(n, np.int32 if k in ("ix", "iy", "id") else np.float32)
+               for k in ("ix", "iy", "ox", "oy", "ux", "uy", "uz", "sx", "sy", "sz", "w", "id")}
+        p = pic_particles_t(n=n, **{k: _ptr(v, _I32P if v.dtype == np.int32 else _F32P)
+                                    for k, v in out.items()})
+        self._c(load().pic_get_particles(self.h, s, C.byref(p), self._s))
+        return out
+
+    def set_fields(self, f):
+        keep = {}
+        kw = {}
+        for k, v in f.items():
+            a = np.ascontiguousarray(v, dtype=np.float32)
+            keep[k] = a
+            kw[k] = _ptr(a, _F32P)
+        pf = pic_fields_t(**kw)
+        self._c(load().pic_set_fields(self.h, C.byref(pf), self._s))
+
+    def get_fields(self):
+        out = {k: np.empty((self.ny, self.nx), np.float32) for k in self.FIELD_KEYS}
+        out["by_left"] = np.empty(self.ny, np.float32)
+        out["bz_left"] = np.empty(self.ny, np.float32)
+        pf = pic_fields_t(**{k: _ptr(v, _F32P) for k, v in out.items()})
+        self._c(load().pic_get_fields(self.h, C.byref(pf), self._s))
+        return out
+
+    def set_step(self, n):
+        self._c(load().pic_set_step(self.h, int(n)))
+
+    def get_step(self):
+        v = C.c_int64()
+        self._c(load().pic_get_step(self.h, C.byref(v)))
+        return v.value
+
+    # method parts ---------------------------------------------------------
+    def gather_push_spin(self):
+        self._c(load().pic_gather_push_spin(self.h, self._s))
+
+    def deposit(self):
+        self._c(load().pic_deposit(self.h, self._s))
+
+    def field_update(self):
+        self._c(load().pic_field_update(self.h, self._s))
+
+    def sort(self):
+        self._c(load().pic_sort(self.h, self._s))
+
+    def push_deposit(self):
+        self._c(load().pic_push_deposit(self.h, self._s))
+
+    def step(self, nsteps=1):
+        self._c(load().pic_step(self.h, int(nsteps), self._s))
+
+    def launch_count(self):
+        v = C.c_int64()
+        self._c(load().pic_launch_count(self.h, C.byref(v)))
+        return v.value
+
+    def polarization(self, s, emin=-math.inf, emax=math.inf):
+        m = pic_moments_t()
+        self._c(load().pic_polarization(self.h, s, float(emin), float(emax), C.byref(m), self._s))
+        return dict(P=np.array(m.P[:]), sum_w=m.sum_w, count=m.count, ekin_mean=m.ekin_mean,
+                    ekin_var=m.ekin_var)
+
+    def capture_background(self):
+        self._c(load().pic_capture_background(self.h, self._s))
+
+    def gauss_residual(self):
+        out = (C.c_double * 2)()
+        self._c(load().pic_gauss_residual(self.h, out, self._s))
+        return out[0], out[1]
+
+    def sync(self):
+        self._c(load().pic_sync(self.h, self._s))

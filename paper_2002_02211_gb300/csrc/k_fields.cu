@@ -1,0 +1,99 @@
+// k_fields.cu -- a6: Yee FDTD update (Yee 1966) in three stages, B half step,
+// E full step with -J (which is then cleared), B half step, with a
+// first-order Silver-Mueller boundary at x_min (laser source) and x_max.
+#include "pic_kernels.h"
+
+namespace {
+
+// B <- B - h curl E.  Bx on every column; By, Bz on the columns whose x+1
+// neighbour exists (all of them when x is periodic).
+__global__ void __launch_bounds__(256) k_b_half(const MeshParams m, float hdx, float hdy) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= m.nx) return;
+    const int jp = j + 1 == m.ny ? 0 : j + 1;
+    const size_t P = m.plane;
+    float *EB = m.EB;
+    const size_t c = (size_t)j * m.ld + i, cjp = (size_t)jp * m.ld + i;
+    const float ez = EB[2 * P + c];
+    EB[3 * P + c] -= hdy * (EB[2 * P + cjp] - ez);
+    const bool periodic = m.bc_x == 1;
+    if (i < m.nx - 1 || periodic) {
+        const size_t cip = (size_t)j * m.ld + (i + 1 == m.nx ? 0 : i + 1);
+        EB[4 * P + c] += hdx * (EB[2 * P + cip] - ez);
+        EB[5 * P + c] -= hdx * (EB[1 * P + cip] - EB[1 * P + c]) - hdy * (EB[0 * P + cjp] - EB[0 * P + c]);
+    }
+}
+
+__device__ double laser_value(const LaserParams &L, double t, double y, int comp) {
+    const double e = (t - L.t_peak) / L.tau;
+    const double r = (y - L.yc) / L.w0;
+    const double env = exp(-e * e) * exp(-r * r);
+    const double ph = t - L.t_peak;
+    if (L.pol == 1) return comp == 0 ? L.a0 * env * sin(ph) : 0.0;
+    if (L.pol == 2) return L.a0 * 0.7071067811865476 * env * (comp == 0 ? sin(ph) : cos(ph));
+    return 0.0;
+}
+
+// boundary B at t^{n+1/2}: incoming characteristic = laser at x_min, none at x_max
+//   By(-1/2) = (2 Ez(0) - (1-r) By(1/2) - 4 f) / (1+r),  Bz(-1/2) = (4 g - 2 Ey(0) - (1-r) Bz(1/2)) / (1+r)
+//   By(nx-1/2) = (-2 Ez(nx-1) - (1-r) By(nx-3/2)) / (1+r), Bz(nx-1/2) = (2 Ey(nx-1) - (1-r) Bz(nx-3/2)) / (1+r)
+__global__ void k_boundary(const MeshParams m, float *bnd, const LaserParams L, double t, double r) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m.ny) return;
+    const size_t P = m.plane;
+    float *EB = m.EB;
+    const size_t c0 = (size_t)j * m.ld, cl = c0 + m.nx - 1;
+    const double f = laser_value(L, t, (double)j * L.dy, 1);
+    const double g = laser_value(L, t, ((double)j + 0.5) * L.dy, 0);
+    const double ir = 1.0 / (1.0 + r), mr = 1.0 - r;
+    bnd[j] = (float)((2.0 * EB[2 * P + c0] - mr * EB[4 * P + c0] - 4.0 * f) * ir);
+    bnd[m.ny + j] = (float)((4.0 * g - 2.0 * EB[1 * P + c0] - mr * EB[5 * P + c0]) * ir);
+    EB[4 * P + cl] = (float)((-2.0 * EB[2 * P + cl] - mr * EB[4 * P + cl - 1]) * ir);
+    EB[5 * P + cl] = (float)((2.0 * EB[1 * P + cl] - mr * EB[5 * P + cl - 1]) * ir);
+}
+
+// E <- E + dt (curl B - J), then J <- 0
+__global__ void __launch_bounds__(256) k_e_full(const MeshParams m, const float *bnd, float dt,
+                                                float dtdx, float dtdy) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= m.nx) return;
+    const int jm = j == 0 ? m.ny - 1 : j - 1;
+    const size_t P = m.plane;
+    float *EB = m.EB;
+    float *J = m.J;
+    const size_t c = (size_t)j * m.ld + i, cjm = (size_t)jm * m.ld + i;
+    float by_im, bz_im;
+    if (i > 0) {
+        by_im = EB[4 * P + c - 1];
+        bz_im = EB[5 * P + c - 1];
+    } else if (m.bc_x == 1) {
+        by_im = EB[4 * P + c + m.nx - 1];
+        bz_im = EB[5 * P + c + m.nx - 1];
+    } else {
+        by_im = bnd[j];
+        bz_im = bnd[m.ny + j];
+    }
+    const float bx = EB[3 * P + c], by = EB[4 * P + c], bz = EB[5 * P + c];
+    EB[0 * P + c] += dtdy * (bz - EB[5 * P + cjm]) - dt * J[0 * P + c];
+    EB[1 * P + c] += -dtdx * (bz - bz_im) - dt * J[1 * P + c];
+    EB[2 * P + c] += dtdx * (by - by_im) - dtdy * (bx - EB[3 * P + cjm]) - dt * J[2 * P + c];
+    J[0 * P + c] = 0.f;
+    J[1 * P + c] = 0.f;
+    J[2 * P + c] = 0.f;
+}
+
+}  // namespace
+
+cudaError_t launch_field_update(const MeshParams &m, float *bnd, const LaserParams &L, double dt,
+                                double dx, double dy, long long step, cudaStream_t st) {
+    const dim3 blk(256), grd((m.nx + 255) / 256, m.ny);
+    const float hdx = (float)(0.5 * dt / dx), hdy = (float)(0.5 * dt / dy);
+    k_b_half<<<grd, blk, 0, st>>>(m, hdx, hdy);
+    if (m.bc_x == 0)
+        k_boundary<<<(m.ny + 127) / 128, 128, 0, st>>>(m, bnd, L, ((double)step + 0.5) * dt, dt / dx);
+    k_e_full<<<grd, blk, 0, st>>>(m, bnd, (float)dt, (float)(dt / dx), (float)(dt / dy));
+    k_b_half<<<grd, blk, 0, st>>>(m, hdx, hdy);
+    return cudaGetLastError();
+}

@@ -1,0 +1,226 @@
+// k_reduce.cu -- a8: FP64 reductions.  Eq. (4) polarization moments of one
+// species in an energy window (two passes: sums, then the variance about the
+// mean), the CIC charge density, and the charge-conservation residual
+// div E - rho.  Per-block FP64 partials are summed by one CTA in a fixed
+// order, so a result depends only on the particle order, not on timing.
+#include "pic_kernels.h"
+
+#define MEC2_MEV 0.51099895
+
+namespace {
+
+constexpr int RB = 152 * 4;  // reduction blocks
+constexpr int RT = 256;      // threads per reduction block
+
+// FP64 block reduction of NV values per thread; thread 0 writes the block's row
+template <int NV>
+__device__ void block_sum(double (&v)[NV], double *row) {
+    __shared__ double red[RT / 32][NV];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xFFFFFFFFu, v[k], o);
+    if (lane == 0)
+        for (int k = 0; k < NV; ++k) red[wid][k] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < NV; ++k) {
+            double s = 0.0;
+            for (int w = 0; w < RT / 32; ++w) s += red[w][k];
+            row[k] = s;
+        }
+    }
+}
+
+// kinetic energy (gamma - 1) m c^2 = m c^2 u^2 / (1 + gamma), no cancellation
+__device__ __forceinline__ float ekin(float m_mev, float ux, float uy, float uz) {
+    const float u2 = ux * ux + uy * uy + uz * uz;
+    return m_mev * u2 / (1.f + sqrtf(1.f + u2));
+}
+
+// pass 1: sum w, sum w s (3), sum w e, count.  Each thread folds float sums of
+// at most 16 particles into its double accumulators.
+__global__ void __launch_bounds__(RT) k_mom1(const DevSpecies S, float m_mev, float emin, float emax,
+                                             double *partials) {
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    float f[6] = {0, 0, 0, 0, 0, 0};
+    int k = 0;
+    const int n = *S.n;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        if (S.cell[p] == PIC_DEAD) continue;
+        const float e = ekin(m_mev, S.ux[p], S.uy[p], S.uz[p]);
+        if (!(e >= emin && e < emax)) continue;
+        const float w = S.w[p];
+        f[0] += w;
+        f[1] += w * S.sx[p];
+        f[2] += w * S.sy[p];
+        f[3] += w * S.sz[p];
+        f[4] += w * e;
+        f[5] += 1.f;
+        if (++k == 16) {
+            for (int q = 0; q < 6; ++q) {
+                acc[q] += (double)f[q];
+                f[q] = 0.f;
+            }
+            k = 0;
+        }
+    }
+    for (int q = 0; q < 6; ++q) acc[q] += (double)f[q];
+    block_sum<6>(acc, partials + (size_t)blockIdx.x * 6);
+}
+
+// fixed-order sum of nb rows of width nv; row 0 of result gets the sums
+__global__ void __launch_bounds__(RT) k_final(const double *partials, int nb, int nv, double *result) {
+    __shared__ double s[RT];
+    for (int q = 0; q < nv; ++q) {
+        double a = 0.0;
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) a += partials[(size_t)b * nv + q];
+        s[threadIdx.x] = a;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if ((int)threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) result[q] = s[0];
+        __syncthreads();
+    }
+}
+
+// max over rows for column 0, sum for column 1
+__global__ void __launch_bounds__(RT) k_final_maxsum(const double *partials, int nb, double *result) {
+    __shared__ double smax[RT], ssum[RT];
+    double a = 0.0, b = 0.0;
+    for (int r = threadIdx.x; r < nb; r += blockDim.x) {
+        a = fmax(a, partials[(size_t)r * 2]);
+        b += partials[(size_t)r * 2 + 1];
+    }
+    smax[threadIdx.x] = a;
+    ssum[threadIdx.x] = b;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + o]);
+            ssum[threadIdx.x] += ssum[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        result[0] = smax[0];
+        result[1] = ssum[0];
+    }
+}
+
+// pass 2: sum w (e - mean)^2, the mean read from pass 1's result
+__global__ void __launch_bounds__(RT) k_mom2(const DevSpecies S, float m_mev, float emin, float emax,
+                                             const double *r1, double *partials) {
+    const double sw = r1[0];
+    const float mean = sw > 0.0 ? (float)(r1[4] / sw) : 0.f;
+    double acc[1] = {0.0};
+    float f = 0.f;
+    int k = 0;
+    const int n = *S.n;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        if (S.cell[p] == PIC_DEAD) continue;
+        const float e = ekin(m_mev, S.ux[p], S.uy[p], S.uz[p]);
+        if (!(e >= emin && e < emax)) continue;
+        const float d = e - mean;
+        f += S.w[p] * d * d;
+        if (++k == 16) {
+            acc[0] += (double)f;
+            f = 0.f;
+            k = 0;
+        }
+    }
+    acc[0] += (double)f;
+    block_sum<1>(acc, partials + blockIdx.x);
+}
+
+// CIC charge density of one species at the nodes
+__global__ void k_rho(const DevSpecies S, const MeshParams m, float *rho) {
+    const int n = *S.n;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const uint32_t c = S.cell[p];
+        if (c == PIC_DEAD) continue;
+        const int ix = (int)(c & 0xFFFFu), iy = (int)(c >> 16);
+        const float ox = S.ox[p], oy = S.oy[p], qw = S.q * S.w[p];
+        const int ix1 = ix + 1 == m.nx ? 0 : ix + 1;
+        const int iy1 = iy + 1 == m.ny ? 0 : iy + 1;
+        atomicAdd(&rho[(size_t)iy * m.ld + ix], qw * (1.f - ox) * (1.f - oy));
+        atomicAdd(&rho[(size_t)iy * m.ld + ix1], qw * ox * (1.f - oy));
+        atomicAdd(&rho[(size_t)iy1 * m.ld + ix], qw * (1.f - ox) * oy);
+        atomicAdd(&rho[(size_t)iy1 * m.ld + ix1], qw * ox * oy);
+    }
+}
+
+// div E - rho - rho_bg on nodes i in [i0, i1]: block max |r| and sum r^2
+__global__ void __launch_bounds__(RT) k_gauss(const MeshParams m, const float *rho, const float *rho_bg,
+                                              double idx, double idy, int i0, int i1, double *partials) {
+    double vmax = 0.0, ssq = 0.0;
+    const int w = i1 - i0 + 1;
+    const long long total = (long long)w * m.ny;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(q / w), i = i0 + (int)(q - (long long)j * w);
+        const int im = i == 0 ? m.nx - 1 : i - 1, jm = j == 0 ? m.ny - 1 : j - 1;
+        const size_t c = (size_t)j * m.ld + i;
+        const double div = ((double)m.EB[c] - (double)m.EB[(size_t)j * m.ld + im]) * idx +
+                           ((double)m.EB[m.plane + c] - (double)m.EB[m.plane + (size_t)jm * m.ld + i]) * idy;
+        const double r = div - (double)rho[c] - (double)rho_bg[c];
+        vmax = fmax(vmax, fabs(r));
+        ssq += r * r;
+    }
+    __shared__ double smax[RT], ssum[RT];
+    smax[threadIdx.x] = vmax;
+    ssum[threadIdx.x] = ssq;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + o]);
+            ssum[threadIdx.x] += ssum[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = smax[0];
+        partials[2 * blockIdx.x + 1] = ssum[0];
+    }
+}
+
+__global__ void k_negate(const float *src, float *dst, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = -src[i];
+}
+
+}  // namespace
+
+int reduce_blocks() { return RB; }
+
+// result[0..5] = sums of pass 1, result[6] = sum w (e - mean)^2
+cudaError_t launch_moments(const DevSpecies &S, float m_mev, float emin, float emax, double *partials,
+                           double *result, cudaStream_t st) {
+    k_mom1<<<RB, RT, 0, st>>>(S, m_mev, emin, emax, partials);
+    k_final<<<1, RT, 0, st>>>(partials, RB, 6, result);
+    k_mom2<<<RB, RT, 0, st>>>(S, m_mev, emin, emax, result, partials);
+    k_final<<<1, RT, 0, st>>>(partials, RB, 1, result + 6);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rho(const DevSpecies &S, int n_upper, const MeshParams &m, float *rho, cudaStream_t st) {
+    int b = (n_upper + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    if (b < 1) b = 1;
+    k_rho<<<b, 256, 0, st>>>(S, m, rho);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gauss(const MeshParams &m, const float *rho, const float *rho_bg, double dx, double dy,
+                         int i0, int i1, double *partials, double *result, cudaStream_t st) {
+    k_gauss<<<RB, RT, 0, st>>>(m, rho, rho_bg, 1.0 / dx, 1.0 / dy, i0, i1, partials);
+    k_final_maxsum<<<1, RT, 0, st>>>(partials, RB, result);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_negate_copy(const float *src, float *dst, size_t n, cudaStream_t st) {
+    k_negate<<<152 * 4, 256, 0, st>>>(src, dst, n);
+    return cudaGetLastError();
+}

@@ -1,0 +1,654 @@
+// pic_api.cu -- the C ABI declared in include/pic.h: context, state transfer,
+// and the host-side sequencing of the kernels.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "pic.h"
+#include "pic_kernels.h"
+
+namespace {
+
+constexpr double kTwoPi = 6.283185307179586;
+constexpr double kMec2Mev = 0.51099895;
+
+struct SpeciesBuf {
+    uint32_t *cell = nullptr;
+    float *f[9] = {};  // ox oy ux uy uz sx sy sz w
+    int32_t *id = nullptr;
+};
+
+struct Ctx {
+    pic_config_t cfg{};
+    int device = 0;
+    double dt = 0, dx = 0, dy = 0;
+    int ld = 0;
+    size_t plane = 0;
+    TileGeom tg{};
+    int ntiles = 0;
+    float *EB = nullptr, *J = nullptr, *bnd = nullptr, *rho = nullptr, *rho_bg = nullptr;
+    SpeciesBuf buf[PIC_MAX_SPECIES][2];
+    int cur[PIC_MAX_SPECIES] = {};
+    int n_upper[PIC_MAX_SPECIES] = {};  // host bound on the device slot counts (sizes grids)
+    int32_t *tile_start[PIC_MAX_SPECIES] = {};
+    uint32_t *cell_old[PIC_MAX_SPECIES] = {};
+    float *old_f[PIC_MAX_SPECIES][3] = {};  // ox_old, oy_old, vz
+    int32_t *tile_count = nullptr, *tile_cursor = nullptr;
+    int32_t *n_dev = nullptr;  // [PIC_MAX_SPECIES + 1] slot counts; the last entry is sort scratch
+    int32_t *scratch_i32 = nullptr;  // 2 * max capacity, for ix / iy transfers
+    unsigned *err = nullptr;
+    double *partials = nullptr, *result = nullptr;
+    CUtensorMap tmapEB;
+    bool pending_deposit = false;
+    long long step = 0;
+    int since_sort = 0;
+    long long launches = 0;  // kernels launched by this context
+    std::string last_error;
+};
+
+std::string g_create_error;
+
+pic_status_t fail(Ctx *c, pic_status_t s, const std::string &msg) {
+    if (c)
+        c->last_error = msg;
+    else
+        g_create_error = msg;
+    return s;
+}
+
+#define CK(call)                                                                         \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(c, PIC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+cudaStream_t S(void *stream) { return reinterpret_cast<cudaStream_t>(stream); }
+
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+DevSpecies dev_species(Ctx *c, int s, int which) {
+    DevSpecies d{};
+    const SpeciesBuf &b = c->buf[s][which];
+    d.cell = b.cell;
+    d.ox = b.f[0];
+    d.oy = b.f[1];
+    d.ux = b.f[2];
+    d.uy = b.f[3];
+    d.uz = b.f[4];
+    d.sx = b.f[5];
+    d.sy = b.f[6];
+    d.sz = b.f[7];
+    d.w = b.f[8];
+    d.id = b.id;
+    d.tile_start = c->tile_start[s];
+    d.cell_old = c->cell_old[s];
+    d.ox_old = c->old_f[s][0];
+    d.oy_old = c->old_f[s][1];
+    d.vz = c->old_f[s][2];
+    const pic_species_t &sp = c->cfg.sp[s];
+    d.qm = (float)(sp.q / sp.m);
+    d.q = (float)sp.q;
+    d.a = (float)sp.a;
+    d.mobile = sp.mobile;
+    d.n = c->n_dev + s;
+    return d;
+}
+
+MeshParams mesh(Ctx *c) {
+    MeshParams m{};
+    m.nx = c->cfg.nx;
+    m.ny = c->cfg.ny;
+    m.ld = c->ld;
+    m.bc_x = c->cfg.bc_x;
+    m.dt = (float)c->dt;
+    m.dt_dx = (float)(c->dt / c->dx);
+    m.dt_dy = (float)(c->dt / c->dy);
+    m.dx_dt = (float)(c->dx / c->dt);
+    m.dy_dt = (float)(c->dy / c->dt);
+    m.EB = c->EB;
+    m.J = c->J;
+    m.plane = c->plane;
+    return m;
+}
+
+StepParams step_params(Ctx *c) {
+    StepParams P{};
+    P.m = mesh(c);
+    P.t = c->tg;
+    P.nsp = c->cfg.nspecies;
+    for (int s = 0; s < P.nsp; ++s) P.sp[s] = dev_species(c, s, c->cur[s]);
+    P.err = c->err;
+    return P;
+}
+
+LaserParams laser(Ctx *c) {
+    LaserParams L{};
+    L.pol = c->cfg.bc_x == PIC_BC_OPEN ? c->cfg.pol : PIC_POL_NONE;
+    L.a0 = c->cfg.a0;
+    L.w0 = c->cfg.waist_lambda * kTwoPi;
+    L.tau = c->cfg.fwhm_periods * kTwoPi / std::sqrt(2.0 * std::log(2.0));
+    L.t_peak = c->cfg.t_peak_periods * kTwoPi;
+    L.yc = 0.5 * c->cfg.ny * c->dy;
+    L.dy = c->dy;
+    return L;
+}
+
+void choose_tiles(Ctx *c) {
+    int tx = c->cfg.tile_x, ty = c->cfg.tile_y;
+    if (tx <= 0 || ty <= 0) {
+        const long long cells = (long long)c->cfg.nx * c->cfg.ny;
+        tx = cells >= (1LL << 21) ? 32 : 16;
+        ty = cells >= (1LL << 21) ? 16 : 8;
+    }
+    c->tg.TX = tx;
+    c->tg.TY = ty;
+    c->tg.WX = tx + 2 * PIC_HALO;
+    c->tg.WY = ty + 2 * PIC_HALO;
+    c->tg.ntx = (c->cfg.nx + tx - 1) / tx;
+    c->tg.nty = (c->cfg.ny + ty - 1) / ty;
+    c->ntiles = c->tg.ntx * c->tg.nty;
+}
+
+pic_status_t make_tensor_map(Ctx *c) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    CK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+    if (!fn || q != cudaDriverEntryPointSuccess)
+        return fail(c, PIC_ERR_CUDA, "cuTensorMapEncodeTiled not available");
+    auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    cuuint64_t dims[3] = {(cuuint64_t)c->cfg.nx, (cuuint64_t)c->cfg.ny, 6};
+    cuuint64_t strides[2] = {(cuuint64_t)c->ld * sizeof(float), (cuuint64_t)c->plane * sizeof(float)};
+    cuuint32_t box[3] = {(cuuint32_t)c->tg.WX, (cuuint32_t)c->tg.WY, 6};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = enc(&c->tmapEB, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->EB, dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(c, PIC_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+    return PIC_OK;
+}
+
+pic_status_t check_flags(Ctx *c, cudaStream_t st) {
+    unsigned h = 0;
+    CK(cudaMemcpyAsync(&h, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (h == 0) return PIC_OK;
+    CK(cudaMemsetAsync(c->err, 0, sizeof(unsigned), st));
+    CK(cudaStreamSynchronize(st));
+    if (h & PIC_EF_TIMEOUT) return fail(c, PIC_ERR_TIMEOUT, "tile staging wait timed out");
+    if (h & PIC_EF_NAN) return fail(c, PIC_ERR_NAN, "non-finite momentum or spin");
+    if (h & PIC_EF_CFL) return fail(c, PIC_ERR_CFL, "particle moved a cell or more in one step");
+    if (h & PIC_EF_RANGE) return fail(c, PIC_ERR_ARG, "particle cell outside the particle region");
+    return fail(c, PIC_ERR_CUDA, "unknown device error flag");
+}
+
+// no host synchronisation: the sorted count stays on the device (it only
+// ever shrinks, so n_upper still bounds it)
+pic_status_t sort_species(Ctx *c, int s, cudaStream_t st) {
+    const int from = c->cur[s], to = 1 - from;
+    DevSpecies src = dev_species(c, s, from), dst = dev_species(c, s, to);
+    CK(launch_tile_sort(src, dst, c->tg, c->tile_count, c->tile_cursor, c->tile_start[s],
+                        c->n_dev + PIC_MAX_SPECIES, c->n_upper[s], st));
+    c->launches += 3;
+    c->cur[s] = to;
+    return PIC_OK;
+}
+
+pic_status_t read_count(Ctx *c, int s, cudaStream_t st, int32_t *n) {
+    CK(cudaMemcpyAsync(n, c->n_dev + s, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return PIC_OK;
+}
+
+pic_status_t alloc_old(Ctx *c, int s) {
+    if (c->cell_old[s]) return PIC_OK;
+    const size_t cap = (size_t)c->cfg.sp[s].capacity;
+    CK(cudaMalloc(&c->cell_old[s], cap * sizeof(uint32_t) + 16));
+    for (int k = 0; k < 3; ++k) CK(cudaMalloc(&c->old_f[s][k], cap * sizeof(float) + 16));
+    return PIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pic_status_t pic_validate_config(const pic_config_t *cfg) {
+    Ctx *c = nullptr;
+    if (!cfg) return fail(c, PIC_ERR_ARG, "null config");
+    if (cfg->nx < 8 || cfg->ny < 4 || cfg->nx > 32767 || cfg->ny > 32767)
+        return fail(c, PIC_ERR_ARG, "nx must be in [8, 32767] and ny in [4, 32767]");
+    if (!(cfg->dx_lambda > 0) || !(cfg->dy_lambda > 0)) return fail(c, PIC_ERR_ARG, "cell sizes must be > 0");
+    if (!(cfg->cfl > 0 && cfg->cfl < 1)) return fail(c, PIC_ERR_ARG, "cfl must be in (0, 1)");
+    if (cfg->bc_x != PIC_BC_OPEN && cfg->bc_x != PIC_BC_PERIODIC) return fail(c, PIC_ERR_ARG, "bad bc_x");
+    if (cfg->pol < PIC_POL_NONE || cfg->pol > PIC_POL_CP) return fail(c, PIC_ERR_ARG, "bad pol");
+    if (cfg->pol != PIC_POL_NONE && cfg->bc_x == PIC_BC_OPEN &&
+        (!(cfg->waist_lambda > 0) || !(cfg->fwhm_periods > 0)))
+        return fail(c, PIC_ERR_ARG, "laser needs waist_lambda > 0 and fwhm_periods > 0");
+    if (cfg->nspecies < 1 || cfg->nspecies > PIC_MAX_SPECIES) return fail(c, PIC_ERR_ARG, "nspecies must be 1..4");
+    for (int s = 0; s < cfg->nspecies; ++s) {
+        const pic_species_t &sp = cfg->sp[s];
+        if (!(sp.m > 0)) return fail(c, PIC_ERR_ARG, "species mass must be > 0");
+        if (sp.capacity < 0 || sp.capacity > 0x7FFFFFF0LL)
+            return fail(c, PIC_ERR_ARG, "species capacity must be in [0, 2^31 - 16]");
+    }
+    if ((cfg->tile_x != 0 || cfg->tile_y != 0) &&
+        (cfg->tile_x < 4 || cfg->tile_y < 1 || cfg->tile_x % 4 != 0 || cfg->tile_x + 2 * PIC_HALO > 256 ||
+         cfg->tile_y + 2 * PIC_HALO > 256))
+        return fail(c, PIC_ERR_ARG, "tile_x must be a multiple of 4 and tile + 8 <= 256 cells");
+    if (cfg->sort_every < 0) return fail(c, PIC_ERR_ARG, "sort_every must be >= 0");
+    return PIC_OK;
+}
+
+pic_status_t pic_create(const pic_config_t *cfg, void *stream, void **ctx_out) {
+    Ctx *c = nullptr;
+    if (!ctx_out) return fail(c, PIC_ERR_ARG, "null ctx_out");
+    *ctx_out = nullptr;
+    pic_status_t v = pic_validate_config(cfg);
+    if (v != PIC_OK) return v;
+    c = new (std::nothrow) Ctx();
+    if (!c) return fail(nullptr, PIC_ERR_CUDA, "host allocation failed");
+    c->cfg = *cfg;
+    if (c->cfg.sort_every == 0) c->cfg.sort_every = 8;
+    cudaStream_t st = S(stream);
+    auto bail = [&](pic_status_t s) {
+        g_create_error = c->last_error;
+        pic_destroy(c);
+        return s;
+    };
+#define CKC(call)                                                                              \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) {                                                               \
+            c->last_error = std::string(#call) + ": " + cudaGetErrorString(e_);                \
+            return bail(PIC_ERR_CUDA);                                                         \
+        }                                                                                      \
+    } while (0)
+    CKC(cudaGetDevice(&c->device));
+    c->dx = cfg->dx_lambda * kTwoPi;
+    c->dy = cfg->dy_lambda * kTwoPi;
+    c->dt = cfg->cfl / std::sqrt(1.0 / (c->dx * c->dx) + 1.0 / (c->dy * c->dy));
+    c->ld = round_up(cfg->nx, 32);
+    c->plane = (size_t)c->ld * cfg->ny;
+    choose_tiles(c);
+    CKC(cudaMalloc(&c->EB, 6 * c->plane * sizeof(float)));
+    CKC(cudaMalloc(&c->J, 3 * c->plane * sizeof(float)));
+    CKC(cudaMalloc(&c->bnd, 2 * (size_t)cfg->ny * sizeof(float)));
+    CKC(cudaMalloc(&c->rho, c->plane * sizeof(float)));
+    CKC(cudaMalloc(&c->rho_bg, c->plane * sizeof(float)));
+    CKC(cudaMemsetAsync(c->EB, 0, 6 * c->plane * sizeof(float), st));
+    CKC(cudaMemsetAsync(c->J, 0, 3 * c->plane * sizeof(float), st));
+    CKC(cudaMemsetAsync(c->bnd, 0, 2 * (size_t)cfg->ny * sizeof(float), st));
+    CKC(cudaMemsetAsync(c->rho_bg, 0, c->plane * sizeof(float), st));
+    int64_t capmax = 0;
+    for (int s = 0; s < cfg->nspecies; ++s) {
+        const size_t cap = (size_t)cfg->sp[s].capacity;
+        capmax = capmax > (int64_t)cap ? capmax : (int64_t)cap;
+        for (int b = 0; b < 2; ++b) {
+            CKC(cudaMalloc(&c->buf[s][b].cell, cap * sizeof(uint32_t) + 16));
+            for (int k = 0; k < 9; ++k) CKC(cudaMalloc(&c->buf[s][b].f[k], cap * sizeof(float) + 16));
+            CKC(cudaMalloc(&c->buf[s][b].id, cap * sizeof(int32_t) + 16));
+        }
+        CKC(cudaMalloc(&c->tile_start[s], (c->ntiles + 1) * sizeof(int32_t)));
+        CKC(cudaMemsetAsync(c->tile_start[s], 0, (c->ntiles + 1) * sizeof(int32_t), st));
+    }
+    CKC(cudaMalloc(&c->tile_count, c->ntiles * sizeof(int32_t)));
+    CKC(cudaMalloc(&c->tile_cursor, c->ntiles * sizeof(int32_t)));
+    CKC(cudaMalloc(&c->n_dev, (PIC_MAX_SPECIES + 1) * sizeof(int32_t)));
+    CKC(cudaMemsetAsync(c->n_dev, 0, (PIC_MAX_SPECIES + 1) * sizeof(int32_t), st));
+    CKC(cudaMalloc(&c->scratch_i32, 2 * (size_t)capmax * sizeof(int32_t) + 16));
+    CKC(cudaMalloc(&c->err, sizeof(unsigned)));
+    CKC(cudaMemsetAsync(c->err, 0, sizeof(unsigned), st));
+    CKC(cudaMalloc(&c->partials, (size_t)reduce_blocks() * 8 * sizeof(double)));
+    CKC(cudaMalloc(&c->result, 16 * sizeof(double)));
+    if (make_tensor_map(c) != PIC_OK) return bail(PIC_ERR_CUDA);
+    CKC(cudaStreamSynchronize(st));
+#undef CKC
+    *ctx_out = c;
+    return PIC_OK;
+}
+
+void pic_destroy(void *ctx) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return;
+    cudaFree(c->EB);
+    cudaFree(c->J);
+    cudaFree(c->bnd);
+    cudaFree(c->rho);
+    cudaFree(c->rho_bg);
+    for (int s = 0; s < PIC_MAX_SPECIES; ++s) {
+        for (int b = 0; b < 2; ++b) {
+            cudaFree(c->buf[s][b].cell);
+            for (int k = 0; k < 9; ++k) cudaFree(c->buf[s][b].f[k]);
+            cudaFree(c->buf[s][b].id);
+        }
+        cudaFree(c->tile_start[s]);
+        cudaFree(c->cell_old[s]);
+        for (int k = 0; k < 3; ++k) cudaFree(c->old_f[s][k]);
+    }
+    cudaFree(c->tile_count);
+    cudaFree(c->tile_cursor);
+    cudaFree(c->n_dev);
+    cudaFree(c->scratch_i32);
+    cudaFree(c->err);
+    cudaFree(c->partials);
+    cudaFree(c->result);
+    delete c;
+}
+
+pic_status_t pic_get_grid(void *ctx, double *dt, double *dx, double *dy) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
+    if (dt) *dt = c->dt;
+    if (dx) *dx = c->dx;
+    if (dy) *dy = c->dy;
+    return PIC_OK;
+}
+
+pic_status_t pic_set_particles(void *ctx, int s, const pic_particles_t *p, void *stream) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
+    if (s < 0 || s >= c->cfg.nspecies || !p) return fail(c, PIC_ERR_ARG, "bad species or particles");
+    if (p->n < 0) return fail(c, PIC_ERR_ARG, "negative particle count");
+    if (p->n > c->cfg.sp[s].capacity) return fail(c, PIC_ERR_OVERFLOW, "more particles than capacity");
+    const float *src[9] = {p->ox, p->oy, p->ux, p->uy, p->uz, p->sx, p->sy, p->sz, p->w};
+    if (p->n > 0) {
+        if (!p->ix || !p->iy || !p->id) return fail(c, PIC_ERR_ARG, "null particle array");
+        for (int k = 0; k < 9; ++k)
+            if (!src[k]) return fail(c, PIC_ERR_ARG, "null particle array");
+    }
+    cudaStream_t st = S(stream);
+    const size_t n = (size_t)p->n;
+    const int b = c->cur[s];
+    SpeciesBuf &B = c->buf[s][b];
+    int32_t *dix = c->scratch_i32, *diy = c->scratch_i32 + c->cfg.sp[s].capacity;
+    if (n) {
+        CK(cudaMemcpyAsync(dix, p->ix, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(diy, p->iy, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        for (int k = 0; k < 9; ++k)
+            CK(cudaMemcpyAsync(B.f[k], src[k], n * sizeof(float), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(B.id, p->id, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    }
+    const int xlo = c->cfg.bc_x == PIC_BC_OPEN ? 2 : 0;
+    const int xhi = c->cfg.bc_x == PIC_BC_OPEN ? c->cfg.nx - 3 : c->cfg.nx - 1;
+    CK(launch_pack_cells(dix, diy, B.cell, (int)n, xlo, xhi, c->cfg.ny, c->err, st));
+    c->launches += n ? 1 : 0;
+    const int32_t nn = (int32_t)n;
+    CK(cudaMemcpyAsync(c->n_dev + s, &nn, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    c->n_upper[s] = (int)n;
+    c->pending_deposit = false;
+    pic_status_t r = check_flags(c, st);
+    if (r != PIC_OK) {
+        const int32_t zero = 0;
+        cudaMemcpyAsync(c->n_dev + s, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, st);
+        cudaStreamSynchronize(st);
+        c->n_upper[s] = 0;
+        return r;
+    }
+    r = sort_species(c, s, st);
+    if (r != PIC_OK) return r;
+    c->since_sort = 0;
+    CK(cudaStreamSynchronize(st));
+    return PIC_OK;
+}
+
+pic_status_t pic_get_count(void *ctx, int s, int64_t *n) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
+    if (s < 0 || s >= c->cfg.nspecies || !n) return fail(c, PIC_ERR_ARG, "bad species");
+    int32_t v = 0;
+    pic_status_t r = read_count(c, s, nullptr, &v);
+    *n = v;
+    return r;
+}
+
+pic_status_t pic_get_particles(void *ctx, int s, pic_particles_t *out, void *stream) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
+    if (s < 0 || s >= c->cfg.nspecies || !out) return fail(c, PIC_ERR_ARG, "bad species or output");
+    if (c->pending_deposit) return fail(c, PIC_ERR_STATE, "a move is waiting for pic_deposit");
+    cudaStream_t st = S(stream);
+    int32_t nv = 0;
+    pic_status_t rc = read_count(c, s, st, &nv);
+    if (rc != PIC_OK) return rc;
+    const size_t n = (size_t)nv;
+    if ((int64_t)n > out->n) return fail(c, PIC_ERR_ARG, "output arrays too small");
+    out->n = (int64_t)n;
+    if (!n) return PIC_OK;
+    float *dst[9] = {out->ox, out->oy, out->ux, out->uy, out->uz, out->sx, out->sy, out->sz, out->w};
+    if (!out->ix || !out->iy || !out->id) return fail(c, PIC_ERR_ARG, "null output array");
+    for (int k = 0; k < 9; ++k)
+        if (!dst[k]) return fail(c, PIC_ERR_ARG, "null output array");
+    const SpeciesBuf &B = c->buf[s][c->cur[s]];
+    int32_t *dix = c->scratch_i32, *diy = c->scratch_i32 + c->cfg.sp[s].capacity;
+    CK(launch_unpack_cells(B.cell, dix, diy, (int)n, st));
+    c->launches += 1;
+    CK(cudaMemcpyAsync(out->ix, dix, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(out->iy, diy, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    for (int k = 0; k < 9; ++k)
+        CK(cudaMemcpyAsync(dst[k], B.f[k], n * sizeof(float), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(out->id, B.id, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return PIC_OK;
+}
+
+static pic_status_t copy_fields(Ctx *c, pic_fields_t *f, bool to_dev, cudaStream_t st) {
+    float *host[9] = {f->ex, f->ey, f->ez, f->bx, f->by, f->bz, f->jx, f->jy, f->jz};
+    const size_t nx = c->cfg.nx, ny = c->cfg.ny;
+    for (int k = 0; k < 9; ++k) {
+        if (!host[k]) continue;
+        float *d = k < 6 ? c->EB + k * c->plane : c->J + (k - 6) * c->plane;
+        if (to_dev)
+            CK(cudaMemcpy2DAsync(d, c->ld * sizeof(float), host[k], nx * sizeof(float), nx * sizeof(float), ny,
+                                 cudaMemcpyHostToDevice, st));
+        else
+            CK(cudaMemcpy2DAsync(host[k], nx * sizeof(float), d, c->ld * sizeof(float), nx * sizeof(float), ny,
+                                 cudaMemcpyDeviceToHost, st));
+    }
+    float *lb[2] = {f->by_left, f->bz_left};
+    for (int k = 0; k < 2; ++k) {
+        if (!lb[k]) continue;
+        if (to_dev)
+            CK(cudaMemcpyAsync(c->bnd + k * ny, lb[k], ny * sizeof(float), cudaMemcpyHostToDevice, st));
+        else
+            CK(cudaMemcpyAsync(lb[k], c->bnd + k * ny, ny * sizeof(float), cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    return PIC_OK;
+}
+
+pic_status_t pic_set_fields(void *ctx, const pic_fields_t *f, void *stream) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
+    if (!f) return fail(c, PIC_ERR_ARG, "null fields");
+    pic_fields_t tmp = *f;
+    return copy_fields(c, &tmp, true, S(stream));
+}
+
+pic_status_t pic_get_fields(void *ctx, pic_fields_t *f, void *stream) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
+    if (!f) return fail(c, PIC_ERR_ARG, "null fields");
+    return copy_fields(c, f, false, S(stream));
+}
+
+pic_status_t pic_set_step(void *ctx, int64_t step) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
+    c->step = step;
+    return PIC_OK;
+}
+
+pic_status_t pic_get_step(void *ctx, int64_t *step) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c || !step) return fail(c, PIC_ERR_ARG, "null argument");
+    *step = c->step;
+    return PIC_OK;
+}
+
+pic_status_t pic_gather_push_spin(void *ctx, void *stream) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
+    if (c->pending_deposit) return fail(c, PIC_ERR_STATE, "a move is waiting for pic_deposit");
+    cudaStream_t st = S(stream);
+    for (int s = 0; s < c->cfg.nspecies; ++s) {
+        if (!c->cfg.sp[s].mobile) continue;
+        pic_status_t r = alloc_old(c, s);
+        if (r != PIC_OK) return r;
+    }
+    StepParams P = step_params(c);
+    for (int s = 0; s < c->cfg.nspecies; ++s)
+        if (c->cfg.sp[s].mobile) {
+            CK(launch_push_split(P, s, c->n_upper[s], st));
+            c->launches += 1;
+        }
+    c->pending_deposit = true;
+    return PIC_OK;
+}
+
+pic_status_t pic_deposit(void *ctx, void *stream) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
+    if (!c->pending_deposit) return fail(c, PIC_ERR_STATE, "no pending move: call pic_gather_push_spin first");
+    cudaStream_t st = S(stream);
+    StepParams P = step_params(c);
+    for (int s = 0; s < c->cfg.nspecies; ++s)
+        if (c->cfg.sp[s].mobile) {
+            CK(launch_deposit_split(P, s, c->n_upper[s], st));
+            c->launches += 1;
+        }
+    c->pending_deposit = false;
+    return PIC_OK;
+}
+
+pic_status_t pic_field_update(void *ctx, void *stream) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
+    if (c->pending_deposit) return fail(c, PIC_ERR_STATE, "a move is waiting for pic_deposit");
+    CK(launch_field_update(mesh(c), c->bnd, laser(c), c->dt, c->dx, c->dy, c->step, S(stream)));
+    c->launches += c->cfg.bc_x == PIC_BC_OPEN ? 4 : 3;
+    c->step += 1;
+    return PIC_OK;
+}
+
+pic_status_t pic_push_deposit(void *ctx, void *stream) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
+    if (c->pending_deposit) return fail(c, PIC_ERR_STATE, "a move is waiting for pic_deposit");
+    CK(launch_step_fused(step_params(c), c->tmapEB, S(stream)));
+    c->launches += 1;
+    return PIC_OK;
+}
+
+pic_status_t pic_sort(void *ctx, void *stream) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
+    if (c->pending_deposit) return fail(c, PIC_ERR_STATE, "a move is waiting for pic_deposit");
+    for (int s = 0; s < c->cfg.nspecies; ++s) {
+        pic_status_t r = sort_species(c, s, S(stream));
+        if (r != PIC_OK) return r;
+    }
+    c->since_sort = 0;
+    return PIC_OK;
+}
+
+pic_status_t pic_step(void *ctx, int nsteps, void *stream) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
+    if (nsteps < 0) return fail(c, PIC_ERR_ARG, "negative step count");
+    if (c->pending_deposit) return fail(c, PIC_ERR_STATE, "a move is waiting for pic_deposit");
+    for (int k = 0; k < nsteps; ++k) {
+        pic_status_t r = PIC_OK;
+        if (c->since_sort >= c->cfg.sort_every) r = pic_sort(c, stream);
+        if (r == PIC_OK) r = pic_push_deposit(c, stream);
+        if (r == PIC_OK) r = pic_field_update(c, stream);
+        if (r != PIC_OK) return r;
+        c->since_sort += 1;
+    }
+    return PIC_OK;
+}
+
+pic_status_t pic_polarization(void *ctx, int s, double emin, double emax, pic_moments_t *out, void *stream) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
+    if (s < 0 || s >= c->cfg.nspecies || !out) return fail(c, PIC_ERR_ARG, "bad species or output");
+    if (c->pending_deposit) return fail(c, PIC_ERR_STATE, "a move is waiting for pic_deposit");
+    cudaStream_t st = S(stream);
+    DevSpecies d = dev_species(c, s, c->cur[s]);
+    const float lo = std::isinf(emin) && emin < 0 ? -INFINITY : (float)emin;
+    const float hi = std::isinf(emax) && emax > 0 ? INFINITY : (float)emax;
+    CK(launch_moments(d, (float)(c->cfg.sp[s].m * kMec2Mev), lo, hi, c->partials, c->result, st));
+    c->launches += 4;
+    double r[7];
+    CK(cudaMemcpyAsync(r, c->result, 7 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    pic_status_t fl = check_flags(c, st);
+    const double sw = r[0];
+    for (int k = 0; k < 3; ++k) out->P[k] = sw > 0 ? r[1 + k] / sw : 0.0;
+    out->sum_w = sw;
+    out->count = r[5];
+    out->ekin_mean = sw > 0 ? r[4] / sw : 0.0;
+    out->ekin_var = sw > 0 ? r[6] / sw : 0.0;
+    return fl;
+}
+
+pic_status_t pic_capture_background(void *ctx, void *stream) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
+    cudaStream_t st = S(stream);
+    MeshParams m = mesh(c);
+    CK(cudaMemsetAsync(c->rho, 0, c->plane * sizeof(float), st));
+    for (int s = 0; s < c->cfg.nspecies; ++s)
+        CK(launch_rho(dev_species(c, s, c->cur[s]), c->n_upper[s], m, c->rho, st));
+    CK(launch_negate_copy(c->rho, c->rho_bg, c->plane, st));
+    c->launches += c->cfg.nspecies + 1;
+    return PIC_OK;
+}
+
+pic_status_t pic_gauss_residual(void *ctx, double out[2], void *stream) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
+    if (!out) return fail(c, PIC_ERR_ARG, "null output");
+    if (c->pending_deposit) return fail(c, PIC_ERR_STATE, "a move is waiting for pic_deposit");
+    cudaStream_t st = S(stream);
+    MeshParams m = mesh(c);
+    CK(cudaMemsetAsync(c->rho, 0, c->plane * sizeof(float), st));
+    for (int s = 0; s < c->cfg.nspecies; ++s)
+        CK(launch_rho(dev_species(c, s, c->cur[s]), c->n_upper[s], m, c->rho, st));
+    c->launches += c->cfg.nspecies + 2;
+    const bool open = c->cfg.bc_x == PIC_BC_OPEN;
+    const int i0 = open ? 3 : 0, i1 = open ? c->cfg.nx - 4 : c->cfg.nx - 1;
+    CK(launch_gauss(m, c->rho, c->rho_bg, c->dx, c->dy, i0, i1, c->partials, c->result, st));
+    double r[2];
+    CK(cudaMemcpyAsync(r, c->result, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const double cnt = (double)(i1 - i0 + 1) * c->cfg.ny;
+    out[0] = r[0];
+    out[1] = std::sqrt(r[1] / cnt);
+    return PIC_OK;
+}
+
+pic_status_t pic_sync(void *ctx, void *stream) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
+    return check_flags(c, S(stream));
+}
+
+pic_status_t pic_launch_count(void *ctx, int64_t *count) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c || !count) return fail(c, PIC_ERR_ARG, "null argument");
+    *count = c->launches;
+    return PIC_OK;
+}
+
+const char *pic_last_error(void *ctx) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    return c ? c->last_error.c_str() : g_create_error.c_str();
+}
+
+}  // extern "C"

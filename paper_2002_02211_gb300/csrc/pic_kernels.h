@@ -1,0 +1,40 @@
+// pic_kernels.h -- launchers of the CUDA kernels, called by the C ABI layer.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "pic_device.cuh"
+
+struct LaserParams {
+    int pol;            // 0 none, 1 LP-y, 2 CP
+    double a0, w0, tau, t_peak, yc, dy;
+};
+
+// k_particles.cu
+size_t step_fused_smem_bytes(const TileGeom &t);
+cudaError_t launch_step_fused(const StepParams &P, const CUtensorMap &tmapEB, cudaStream_t st);
+cudaError_t launch_push_split(const StepParams &P, int s, int n_upper, cudaStream_t st);
+cudaError_t launch_deposit_split(const StepParams &P, int s, int n_upper, cudaStream_t st);
+
+// k_fields.cu
+cudaError_t launch_field_update(const MeshParams &m, float *bnd, const LaserParams &L,
+                                double dt, double dx, double dy, long long step, cudaStream_t st);
+
+// k_sort.cu
+cudaError_t launch_pack_cells(const int32_t *ix, const int32_t *iy, uint32_t *cell, int n,
+                              int xlo, int xhi, int ny, unsigned *err, cudaStream_t st);
+cudaError_t launch_unpack_cells(const uint32_t *cell, int32_t *ix, int32_t *iy, int n,
+                                cudaStream_t st);
+cudaError_t launch_tile_sort(const DevSpecies &src, const DevSpecies &dst, const TileGeom &t,
+                             int32_t *count, int32_t *cursor, int32_t *tile_start,
+                             int32_t *n_tmp, int n_upper, cudaStream_t st);
+
+// k_reduce.cu
+int reduce_blocks();
+cudaError_t launch_moments(const DevSpecies &S, float m_mev, float emin, float emax,
+                           double *partials, double *result, cudaStream_t st);
+cudaError_t launch_rho(const DevSpecies &S, int n_upper, const MeshParams &m, float *rho, cudaStream_t st);
+cudaError_t launch_gauss(const MeshParams &m, const float *rho, const float *rho_bg, double dx,
+                         double dy, int i0, int i1, double *partials, double *result,
+                         cudaStream_t st);
+cudaError_t launch_negate_copy(const float *src, float *dst, size_t n, cudaStream_t st);

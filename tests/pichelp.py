@@ -1,0 +1,82 @@
+"""Shared helpers of the GPU parity tests: build a library context and an
+oracle simulation from the same seeded state, and compare them."""
+import numpy as np
+
+import oracle
+import paper_2002_02211_gb300 as pic
+import workloads as W
+
+
+def make_pair(wl, fields=None, step=0, capacity_factor=1.0, sort_every=0, tile=(0, 0), parts=None):
+    parts = W.generate_particles(wl) if parts is None else parts
+    cfg = pic.config_from_workload(wl, capacity_factor=capacity_factor, sort_every=sort_every, tile=tile)
+    sim = pic.Simulation(cfg)
+    for s, d in enumerate(parts):
+        sim.set_particles(s, d)
+    if fields is not None:
+        sim.set_fields(fields)
+    sim.set_step(step)
+    if wl.neutralizing_background:
+        sim.capture_background()
+    orc = oracle.OracleSim(wl, parts, fields=fields, step=step)
+    return sim, orc, parts
+
+
+def gpu_by_id(sim, s, n_total):
+    """GPU particles of species s reordered by id; removed ones flagged."""
+    g = sim.get_particles(s)
+    out = {k: np.full(n_total, np.nan) for k in ("x", "y", "ux", "uy", "uz", "sx", "sy", "sz")}
+    alive = np.zeros(n_total, bool)
+    ids = g["id"]
+    live = g["ix"] >= 0
+    assert len(np.unique(ids)) == len(ids), "duplicate particle ids"
+    out["x"][ids[live]] = g["ix"][live] + g["ox"][live].astype(np.float64)
+    out["y"][ids[live]] = g["iy"][live] + g["oy"][live].astype(np.float64)
+    for k in ("ux", "uy", "uz", "sx", "sy", "sz"):
+        out[k][ids[live]] = g[k][live]
+    alive[ids[live]] = True
+    return out, alive
+
+
+def periodic_diff(a, b, n):
+    d = a - b
+    return d - n * np.round(d / n)
+
+
+def compare_particles(sim, orc, s, u_tol=1e-5, s_tol=1e-5, x_tol=1e-5, u_floor=1e-3):
+    """Per-particle comparison: u relative (floor u_floor), s absolute, x in cells."""
+    p = orc.p[s]
+    n = len(p["x"])
+    g, alive = gpu_by_id(sim, s, n)
+    oal = p["alive"].astype(bool)
+    assert np.array_equal(alive, oal), f"alive sets differ: {np.sum(alive != oal)} particles"
+    if not alive.any():
+        return {}
+    m = alive
+    du = np.sqrt(sum((g[k][m] - p[k][m]) ** 2 for k in ("ux", "uy", "uz")))
+    un = np.maximum(np.sqrt(sum(p[k][m] ** 2 for k in ("ux", "uy", "uz"))), u_floor)
+    ds = np.sqrt(sum((g[k][m] - p[k][m]) ** 2 for k in ("sx", "sy", "sz")))
+    dx = np.abs(periodic_diff(g["x"][m], p["x"][m], orc.wl.nx))
+    dy = np.abs(periodic_diff(g["y"][m], p["y"][m], orc.wl.ny))
+    err = dict(u=float((du / un).max()), s=float(ds.max()), x=float(max(dx.max(), dy.max())))
+    assert err["u"] <= u_tol, err
+    assert err["s"] <= s_tol, err
+    assert err["x"] <= x_tol, err
+    return err
+
+
+def rel_l2(a, b):
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a))
+
+
+def compare_fields(sim, orc, keys, tol, region=None):
+    f = sim.get_fields()
+    errs = {}
+    for k in keys:
+        a, b = f[k].astype(np.float64), orc.f[k]
+        if region is not None:
+            a, b = a[region], b[region]
+        errs[k] = rel_l2(a, b)
+        assert errs[k] <= tol, (k, errs)
+    return errs

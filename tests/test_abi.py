@@ -1,0 +1,74 @@
+"""CPU-side checks of the C ABI: the library builds for sm_103a, loads, exports
+every entry point include/pic.h declares, and validates configurations on
+the host (no CUDA call is made here)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+import paper_2002_02211_gb300 as pic
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            names += re.findall(r"^\s*(?:pic_status_t|void|const char\s*\*)\s*\*?\s*(pic_\w+)\s*\(", txt, re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("pic_create", "pic_gather_push_spin", "pic_deposit", "pic_field_update",
+                     "pic_step", "pic_polarization", "pic_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = pic.load()
+    missing = [n for n in _declared() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_binding_names_match_header():
+    for n in _declared():
+        if n in ("pic_destroy", "pic_last_error"):
+            continue
+        assert n in pic._SIGS, n
+
+
+def _status(cfg):
+    return pic.load().pic_validate_config(C.byref(cfg))
+
+
+def test_validate_config_accepts_the_workloads():
+    for wl in (W.CONFIG1, W.CONFIG3, W.small_case(), W.small_case(bc_x="periodic", two_species=True)):
+        assert _status(pic.config_from_workload(wl)) == 0
+
+
+@pytest.mark.parametrize("field,value", [
+    ("nx", 4), ("ny", 2), ("nx", 40000), ("cfl", 1.0), ("cfl", 0.0), ("dx_lambda", 0.0),
+    ("bc_x", 7), ("pol", 9), ("nspecies", 0), ("nspecies", 5), ("sort_every", -1),
+])
+def test_validate_config_rejects(field, value):
+    cfg = pic.config_from_workload(W.small_case())
+    setattr(cfg, field, value)
+    assert _status(cfg) == -1
+    assert pic.load().pic_last_error(None)
+
+
+def test_validate_config_rejects_bad_tiles_and_species():
+    cfg = pic.config_from_workload(W.small_case())
+    cfg.tile_x, cfg.tile_y = 6, 4        # tile_x must be a multiple of 4 (16-byte TMA rows)
+    assert _status(cfg) == -1
+    cfg = pic.config_from_workload(W.small_case())
+    cfg.sp[0].m = 0.0
+    assert _status(cfg) == -1
+    cfg = pic.config_from_workload(W.small_case())
+    cfg.sp[0].capacity = -5
+    assert _status(cfg) == -1

@@ -1,0 +1,166 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances (per step, from the FP32 arithmetic of the kernels): momentum
+relative error 1e-5 with a floor of 1e-3 on |u|, spin absolute 1e-5,
+position 1e-5 cells, relative L2 error of J and of E, B 1e-5.  Integer work
+(which particles are removed, the sort permutation) is compared exactly.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2002_02211_gb300 as pic
+import workloads as W
+from pichelp import compare_fields, compare_particles, gpu_by_id, make_pair, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def _split_step(sim, orc):
+    sim.gather_push_spin()
+    sim.deposit()
+    orc.zero_current()
+    saved = [orc.push(s) for s in range(len(orc.p))]
+    for s, (xo, yo, vz) in enumerate(saved):
+        orc.deposit(s, xo, yo, vz)
+
+
+CASES = [
+    dict(nx=44, ny=26, ppc=3, bc_x="open", two_species=True),      # ragged vs 16x8 tiles
+    dict(nx=40, ny=24, ppc=2, bc_x="periodic", two_species=False),
+    dict(nx=36, ny=20, ppc=4, bc_x="open", two_species=False, pol="cp"),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=["open-2sp-ragged", "periodic", "open-cp"])
+def test_split_path_one_step(case):
+    wl = W.small_case(u_th=0.2, **case)
+    f = W.random_fields(wl, seed=7)
+    sim, orc, _ = make_pair(wl, fields=f, step=5)
+    _split_step(sim, orc)
+    for s in range(len(wl.species)):
+        compare_particles(sim, orc, s, TOL, TOL, TOL)
+    compare_fields(sim, orc, ("jx", "jy", "jz"), TOL)
+    sim.field_update()
+    orc.field_update()
+    compare_fields(sim, orc, ("ex", "ey", "ez", "bx", "by", "bz"), TOL)
+    assert sim.get_step() == 6
+
+
+@pytest.mark.parametrize("case", CASES, ids=["open-2sp-ragged", "periodic", "open-cp"])
+def test_fused_step_one_step(case):
+    wl = W.small_case(u_th=0.2, **case)
+    f = W.random_fields(wl, seed=8)
+    sim, orc, _ = make_pair(wl, fields=f, step=2)
+    sim.step(1)
+    orc.step(1)
+    for s in range(len(wl.species)):
+        compare_particles(sim, orc, s, TOL, TOL, TOL)
+    compare_fields(sim, orc, ("ex", "ey", "ez", "bx", "by", "bz"), TOL)
+
+
+def test_fused_step_many_steps_with_sorting_and_removal():
+    # particles fast enough to leave their tiles and the box; sort every 3 steps
+    wl = W.small_case(nx=48, ny=24, ppc=2, u_th=2.0, a0=8.0)
+    sim, orc, _ = make_pair(wl, sort_every=3, tile=(8, 4))
+    for k in range(12):
+        sim.step(1)
+        orc.step(1)
+    assert (~orc.p[0]["alive"].astype(bool)).sum() > 0, "case should remove particles"
+    compare_particles(sim, orc, 0, 1e-4, 1e-4, 1e-4)
+    compare_fields(sim, orc, ("ex", "ey", "ez", "bx", "by", "bz"), 1e-4)
+
+
+def test_sort_is_a_grouping_permutation():
+    wl = W.small_case(nx=64, ny=32, ppc=3, u_th=1.0, two_species=True)
+    sim, orc, parts = make_pair(wl, tile=(16, 8))
+    sim.step(5)          # particles drift from their tiles, some leave
+    before = [sim.get_particles(s) for s in range(2)]
+    sim.sort()
+    for s in range(2):
+        b, a = before[s], sim.get_particles(s)
+        live = b["ix"] >= 0
+        assert len(a["id"]) == live.sum()
+        assert np.array_equal(np.sort(a["id"]), np.sort(b["id"][live]))
+        # contents travel with the id, bit for bit
+        ob, oa = np.argsort(b["id"]), np.argsort(a["id"])
+        bl = {k: v[ob][live[ob]] for k, v in b.items()}
+        for k in a:
+            assert np.array_equal(a[k][oa], bl[k]), k
+        tile = (a["iy"] // 8) * ((64 + 15) // 16) + a["ix"] // 16
+        assert np.all(np.diff(tile) >= 0)
+
+
+def test_polarization_and_energy_moments():
+    wl = W.small_case(nx=48, ny=32, ppc=4, u_th=0.5, two_species=True)
+    f = W.random_fields(wl, seed=9, e_amp=0.2, b_amp=0.8)
+    sim, orc, _ = make_pair(wl, fields=f)
+    sim.step(3)
+    orc.step(3)
+    for s in range(2):
+        for emin, emax in [(-math.inf, math.inf), (0.01, 0.2), (0.05, math.inf)]:
+            # windows whose edges no particle sits close to (the decision is made in float)
+            om = orc.moments(s, emin, emax)
+            gm = sim.polarization(s, emin, emax)
+            assert gm["count"] == om[4]
+            np.testing.assert_allclose(gm["P"], om[:3], atol=1e-6)
+            if om[4] > 0:
+                assert gm["sum_w"] == pytest.approx(om[3], rel=1e-6)
+                assert gm["ekin_mean"] == pytest.approx(om[5], rel=1e-5)
+                assert gm["ekin_var"] == pytest.approx(om[6], rel=1e-4)
+
+
+def test_polarization_unchanged_without_fields():
+    wl = W.small_case(nx=32, ny=16, ppc=2, pol="none", a0=0.0, u_th=0.0, bc_x="periodic")
+    sim, orc, _ = make_pair(wl)
+    sim.step(10)
+    m = sim.polarization(0)
+    np.testing.assert_array_equal(m["P"], [0.0, 1.0, 0.0])
+    assert m["count"] == len(orc.p[0]["x"])
+
+
+def test_gauss_law_stays_at_roundoff():
+    wl = W.small_case(nx=96, ny=32, ppc=4, a0=5.0, u_th=0.05)
+    sim, orc, _ = make_pair(wl)
+    r0 = sim.gauss_residual()
+    sim.step(80)
+    orc.step(80)
+    r1 = sim.gauss_residual()
+    ro = np.abs(orc.gauss_residual()).max()
+    n0 = wl.species[0].n0
+    assert r0[0] < 1e-6 * n0
+    assert ro < 1e-11
+    # FP32 charge conservation: residual a small multiple of eps32 * density
+    assert r1[0] < 1e-4 * n0, (r1, n0)
+
+
+def test_config1_full_run_statistics():
+    # 2D3V 256x128, 131,072 electrons, LP a0 = 4, 400 steps: the GPU run and the
+    # oracle run agree on P and the energy moments within 1%
+    wl = W.CONFIG1
+    sim, orc, _ = make_pair(wl)
+    sim.step(wl.steps)
+    orc.step(wl.steps)
+    gm = sim.polarization(0)
+    om = orc.moments(0)
+    assert gm["count"] == om[4]
+    assert np.abs(gm["P"] - om[:3]).max() < 0.01
+    assert gm["ekin_mean"] == pytest.approx(om[5], rel=0.01)
+    assert gm["ekin_var"] == pytest.approx(om[6], rel=0.01)
+    # the laser has been through the plasma
+    assert om[5] > 10 * (wl.species[0].u_th ** 2) * 0.511 * 1.5
+
+
+def test_config1_first_steps_per_particle():
+    wl = W.CONFIG1
+    sim, orc, _ = make_pair(wl)
+    for _ in range(3):
+        sim.step(1)
+        orc.step(1)
+    compare_particles(sim, orc, 0, TOL, TOL, TOL)
+    compare_fields(sim, orc, ("ex", "ey", "ez", "bx", "by", "bz"), TOL)
