@@ -314,28 +314,35 @@ static void b_half(const or_grid_t *g, or_fields_t *f, double h)
 
 /* a6: B half step, boundary B values, E full step with -J, B half step.
  * Open x: first-order Silver-Mueller condition at t^{n+1/2} on the B values
- * half a cell outside the outermost tangential E nodes; at x_min the
- * incoming characteristic carries the laser (r = dt/dx):
- *   By(-1/2) = [2 Ez(0) - (1-r) By(1/2) - 4 f] / (1+r)
+ * half a cell outside the outermost tangential E nodes.  The condition on
+ * the incoming characteristic (Ez - By = 2f, Ey + Bz = 2g at x_min with the
+ * laser's incident f, g; Ez + By = 0, Ey - Bz = 0 at x_max) is imposed on
+ * the time-centred boundary values, with E^{n+1} taken from its own update,
+ * including the transverse term dBx = Bx(j+1/2) - Bx(j-1/2) of the Ez
+ * update (r = dt/dx, q = dt/dy):
+ *   By(-1/2) = [2 Ez(0) - (1-r) By(1/2) - q dBx(0) - 4 f] / (1+r)
  *   Bz(-1/2) = [4 g - 2 Ey(0) - (1-r) Bz(1/2)] / (1+r)
- *   By(nx-1/2) = [-2 Ez(nx-1) - (1-r) By(nx-3/2)] / (1+r)
+ *   By(nx-1/2) = [-2 Ez(nx-1) - (1-r) By(nx-3/2) + q dBx(nx-1)] / (1+r)
  *   Bz(nx-1/2) = [ 2 Ey(nx-1) - (1-r) Bz(nx-3/2)] / (1+r)
- * with f, g the incident Ez and Ey of the laser at x = 0. */
+ * (dropping the q dBx terms leaves a condition that is unstable for fields
+ * varying along y). */
 void or_field_update(const or_grid_t *g, or_fields_t *f, long step)
 {
     long nx = g->nx, ny = g->ny;
     double dt = g->dt;
     b_half(g, f, 0.5 * dt);
     if (g->bc_x == OR_BC_OPEN) {
-        double r = dt / g->dx, t = ((double)step + 0.5) * dt;
+        double r = dt / g->dx, q = dt / g->dy, t = ((double)step + 0.5) * dt;
         for (long j = 0; j < ny; ++j) {
             double fin, gin;
             or_laser(g, t, (double)j * g->dy, 1, &fin);
             or_laser(g, t, ((double)j + 0.5) * g->dy, 0, &gin);
-            long c0 = j * nx, cl = j * nx + nx - 1;
-            f->byL[j] = (2.0 * f->ez[c0] - (1.0 - r) * f->by[c0] - 4.0 * fin) / (1.0 + r);
+            long c0 = j * nx, cl = j * nx + nx - 1, jm = yj(g, j - 1);
+            double dbx0 = f->bx[c0] - f->bx[jm * nx];
+            double dbxl = f->bx[cl] - f->bx[jm * nx + nx - 1];
+            f->byL[j] = (2.0 * f->ez[c0] - (1.0 - r) * f->by[c0] - q * dbx0 - 4.0 * fin) / (1.0 + r);
             f->bzL[j] = (4.0 * gin - 2.0 * f->ey[c0] - (1.0 - r) * f->bz[c0]) / (1.0 + r);
-            f->by[cl] = (-2.0 * f->ez[cl] - (1.0 - r) * f->by[cl - 1]) / (1.0 + r);
+            f->by[cl] = (-2.0 * f->ez[cl] - (1.0 - r) * f->by[cl - 1] + q * dbxl) / (1.0 + r);
             f->bz[cl] = (2.0 * f->ey[cl] - (1.0 - r) * f->bz[cl - 1]) / (1.0 + r);
         }
     }

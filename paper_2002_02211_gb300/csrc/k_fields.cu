@@ -35,21 +35,30 @@ __device__ double laser_value(const LaserParams &L, double t, double y, int comp
     return 0.0;
 }
 
-// boundary B at t^{n+1/2}: incoming characteristic = laser at x_min, none at x_max
-//   By(-1/2) = (2 Ez(0) - (1-r) By(1/2) - 4 f) / (1+r),  Bz(-1/2) = (4 g - 2 Ey(0) - (1-r) Bz(1/2)) / (1+r)
-//   By(nx-1/2) = (-2 Ez(nx-1) - (1-r) By(nx-3/2)) / (1+r), Bz(nx-1/2) = (2 Ey(nx-1) - (1-r) Bz(nx-3/2)) / (1+r)
-__global__ void k_boundary(const MeshParams m, float *bnd, const LaserParams L, double t, double r) {
+// boundary B at t^{n+1/2}: the incoming characteristic is the laser at x_min
+// and zero at x_max, imposed on time-centred values with E^{n+1} from its own
+// update including the transverse term dBx = Bx(j+1/2) - Bx(j-1/2) (r = dt/dx,
+// q = dt/dy):
+//   By(-1/2) = (2 Ez(0) - (1-r) By(1/2) - q dBx(0) - 4 f) / (1+r)
+//   Bz(-1/2) = (4 g - 2 Ey(0) - (1-r) Bz(1/2)) / (1+r)
+//   By(nx-1/2) = (-2 Ez(nx-1) - (1-r) By(nx-3/2) + q dBx(nx-1)) / (1+r)
+//   Bz(nx-1/2) = (2 Ey(nx-1) - (1-r) Bz(nx-3/2)) / (1+r)
+__global__ void k_boundary(const MeshParams m, float *bnd, const LaserParams L, double t, double r,
+                           double q) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= m.ny) return;
     const size_t P = m.plane;
     float *EB = m.EB;
     const size_t c0 = (size_t)j * m.ld, cl = c0 + m.nx - 1;
+    const size_t cm = (size_t)(j == 0 ? m.ny - 1 : j - 1) * m.ld;
     const double f = laser_value(L, t, (double)j * L.dy, 1);
     const double g = laser_value(L, t, ((double)j + 0.5) * L.dy, 0);
     const double ir = 1.0 / (1.0 + r), mr = 1.0 - r;
-    bnd[j] = (float)((2.0 * EB[2 * P + c0] - mr * EB[4 * P + c0] - 4.0 * f) * ir);
+    const double dbx0 = (double)EB[3 * P + c0] - (double)EB[3 * P + cm];
+    const double dbxl = (double)EB[3 * P + cl] - (double)EB[3 * P + cm + m.nx - 1];
+    bnd[j] = (float)((2.0 * EB[2 * P + c0] - mr * EB[4 * P + c0] - q * dbx0 - 4.0 * f) * ir);
     bnd[m.ny + j] = (float)((4.0 * g - 2.0 * EB[1 * P + c0] - mr * EB[5 * P + c0]) * ir);
-    EB[4 * P + cl] = (float)((-2.0 * EB[2 * P + cl] - mr * EB[4 * P + cl - 1]) * ir);
+    EB[4 * P + cl] = (float)((-2.0 * EB[2 * P + cl] - mr * EB[4 * P + cl - 1] + q * dbxl) * ir);
     EB[5 * P + cl] = (float)((2.0 * EB[1 * P + cl] - mr * EB[5 * P + cl - 1]) * ir);
 }
 
@@ -92,7 +101,7 @@ cudaError_t launch_field_update(const MeshParams &m, float *bnd, const LaserPara
     const float hdx = (float)(0.5 * dt / dx), hdy = (float)(0.5 * dt / dy);
     k_b_half<<<grd, blk, 0, st>>>(m, hdx, hdy);
     if (m.bc_x == 0)
-        k_boundary<<<(m.ny + 127) / 128, 128, 0, st>>>(m, bnd, L, ((double)step + 0.5) * dt, dt / dx);
+        k_boundary<<<(m.ny + 127) / 128, 128, 0, st>>>(m, bnd, L, ((double)step + 0.5) * dt, dt / dx, dt / dy);
     k_e_full<<<grd, blk, 0, st>>>(m, bnd, (float)dt, (float)(dt / dx), (float)(dt / dy));
     k_b_half<<<grd, blk, 0, st>>>(m, hdx, hdy);
     return cudaGetLastError();

@@ -46,10 +46,16 @@ MUTATIONS = [
      "f->ey[c] += dt * (-(f->bz[c] - bz_im) / g->dx);"),
     ("laser source sign", "f->bzL[j] = (4.0 * gin - 2.0 * f->ey[c0] - (1.0 - r) * f->bz[c0]) / (1.0 + r);",
      "f->bzL[j] = (-4.0 * gin - 2.0 * f->ey[c0] - (1.0 - r) * f->bz[c0]) / (1.0 + r);"),
-    ("CP source sign", "f->byL[j] = (2.0 * f->ez[c0] - (1.0 - r) * f->by[c0] - 4.0 * fin) / (1.0 + r);",
-     "f->byL[j] = (2.0 * f->ez[c0] - (1.0 - r) * f->by[c0] + 4.0 * fin) / (1.0 + r);"),
+    ("CP source sign", "f->byL[j] = (2.0 * f->ez[c0] - (1.0 - r) * f->by[c0] - q * dbx0 - 4.0 * fin) / (1.0 + r);",
+     "f->byL[j] = (2.0 * f->ez[c0] - (1.0 - r) * f->by[c0] - q * dbx0 + 4.0 * fin) / (1.0 + r);"),
     ("absorber at x_max", "f->bz[cl] = (2.0 * f->ey[cl] - (1.0 - r) * f->bz[cl - 1]) / (1.0 + r);",
      "f->bz[cl] = (2.0 * f->ey[cl] + (1.0 - r) * f->bz[cl - 1]) / (1.0 + r);"),
+    ("boundary without transverse term",
+     "f->byL[j] = (2.0 * f->ez[c0] - (1.0 - r) * f->by[c0] - q * dbx0 - 4.0 * fin) / (1.0 + r);",
+     "f->byL[j] = (2.0 * f->ez[c0] - (1.0 - r) * f->by[c0] - 4.0 * fin) / (1.0 + r);"),
+    ("boundary transverse sign at x_max",
+     "f->by[cl] = (-2.0 * f->ez[cl] - (1.0 - r) * f->by[cl - 1] + q * dbxl) / (1.0 + r);",
+     "f->by[cl] = (-2.0 * f->ez[cl] - (1.0 - r) * f->by[cl - 1] - q * dbxl) / (1.0 + r);"),
     ("moments unweighted mean", "swy += p->w[i] * p->sy[i];", "swy += p->sy[i];"),
     ("energy uses total energy", "double ek = (sqrt(1.0 + dot3(u, u)) - 1.0) * sp->m * MEC2_MEV;\n        if (ek < emin_mev",
      "double ek = (sqrt(1.0 + dot3(u, u))) * sp->m * MEC2_MEV;\n        if (ek < emin_mev"),

@@ -554,3 +554,28 @@ def test_spin_update_is_second_order_in_dt(oracle_mod):
         errs.append(np.linalg.norm(s - ref[3:]))
     r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
     assert 3.3 < r1 < 4.8 and 3.3 < r2 < 4.8, errs
+
+
+@pytest.mark.parametrize("dy_lambda,cfl", [(1 / 16, 0.95), (1 / 32, 0.99), (1 / 10, 0.9)])
+def test_open_boundary_is_stable_for_2d_fields(oracle_mod, dy_lambda, cfl):
+    # random vacuum fields varying along x and y in a box with open x ends:
+    # the field energy may only decrease (first-order absorbing boundary)
+    nx, ny = 64, 32
+    sp = W.Species("e", q=-1.0, m=1.0, a=0.0, n0=0.0, ppc=0, u_th=0.0, s0=(1, 0, 0))
+    wl = W.Workload(name="vac", nx=nx, ny=ny, dx_lambda=1 / 16, dy_lambda=dy_lambda, cfl=cfl,
+                    steps=1, species=(sp,), bc_x="open", pol="none")
+    f = W.random_fields(wl, seed=4, e_amp=0.1, b_amp=0.1)
+    sim = oracle_mod.OracleSim(wl, _empty(), fields=f)
+
+    def energy():
+        return sum((sim.f[k] ** 2).sum() for k in ("ex", "ey", "ez", "bx", "by", "bz"))
+
+    # (E^2 + B^2 at one time level is not the exactly conserved discrete
+    # energy of the leapfrog scheme, so allow transient rises, not growth)
+    e0 = energy()
+    es = []
+    for _ in range(12):
+        sim.step(50)
+        es.append(energy())
+    assert max(es) < 1.5 * e0, es
+    assert es[-1] < e0, es

@@ -124,19 +124,27 @@ def test_polarization_unchanged_without_fields():
     assert m["count"] == len(orc.p[0]["x"])
 
 
-def test_gauss_law_stays_at_roundoff():
-    wl = W.small_case(nx=96, ny=32, ppc=4, a0=5.0, u_th=0.05)
+@pytest.mark.parametrize("a0", [0.0, 5.0], ids=["plasma-only", "laser"])
+def test_gauss_law_stays_at_roundoff(a0):
+    # Esirkepov + Yee conserve div E - rho exactly in exact arithmetic; in FP32
+    # the residual is the rounding of the stored E (eps32 |E| per update,
+    # differenced over a cell) accumulating as a random walk over the steps
+    wl = W.small_case(nx=96, ny=32, ppc=4, a0=a0, u_th=0.05, pol="lp-y" if a0 else "none")
+    steps = 80
     sim, orc, _ = make_pair(wl)
     r0 = sim.gauss_residual()
-    sim.step(80)
-    orc.step(80)
+    sim.step(steps)
+    orc.step(steps)
     r1 = sim.gauss_residual()
     ro = np.abs(orc.gauss_residual()).max()
     n0 = wl.species[0].n0
+    dt, dx, dy = sim.grid()
+    f = sim.get_fields()
+    emax = max(np.abs(f["ex"]).max(), np.abs(f["ey"]).max())
+    bound = 4 * np.finfo(np.float32).eps * (emax / min(dx, dy) + n0) * math.sqrt(steps)
     assert r0[0] < 1e-6 * n0
     assert ro < 1e-11
-    # FP32 charge conservation: residual a small multiple of eps32 * density
-    assert r1[0] < 1e-4 * n0, (r1, n0)
+    assert r1[0] < bound, (r1, bound, emax)
 
 
 def test_config1_full_run_statistics():
