@@ -85,7 +85,8 @@ typedef struct {
     int nspecies;                /* 1 .. PIC_MAX_SPECIES                           */
     pic_species_t sp[PIC_MAX_SPECIES];
     int sort_every;              /* steps between tile sorts in pic_step (0: 8)    */
-    int tile_x, tile_y;          /* cells per tile (0: chosen from the mesh size); tile_x % 4 == 0 */
+    int tile_x, tile_y;          /* cells per tile: 8x4, 16x8, 32x8, 32x16 or 64x16 (0, 0: chosen
+                                    from the mesh size)                            */
 } pic_config_t;
 
 /* Host-side particle arrays of one species (n entries each).  ix, iy are cell

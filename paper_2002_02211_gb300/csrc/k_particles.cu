@@ -69,104 +69,200 @@ __device__ __forceinline__ bool finish_move(const MeshParams &m, int &ix1, int &
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// Fused step kernel.  CTA = one tile.  Thread 0 stages the 6-component field
-// window [tile - 4, tile + 4) x [tile - 4, tile + 4) with one 3D TMA load
-// (zero fill outside the mesh); the CTA then runs a1-a5 for every particle
-// of the tile's slot range, gathering from and depositing into shared
-// memory when the particle's 4x4 stencil lies inside the window and the mesh
-// (no wrap), otherwise through global memory; finally the current window is
-// added to J with 16-byte vector atomics.
+// Fused step kernel.  CTA = one tile of TX x TY cells (compile-time, so every
+// shared-memory offset below is an immediate).  Thread 0 stages the
+// 6-component field window [tile - 4, tile + 4) in x and y with one 3D TMA
+// load (zero fill outside the mesh).  Particle records of the tile (both
+// species, one slot range after the other) stream through a two-deep
+// cp.async ring in shared memory: while a thread computes one record it has
+// the next one in flight.  Each record runs a1-a5, gathering from and
+// depositing into shared memory when the particle's 4x4 stencil lies inside
+// the window and the mesh (no wrap), otherwise through global memory.  The
+// current window is finally added to J with 16-byte vector atomics.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_step_fused(const StepParams P,
-                                                    const __grid_constant__ CUtensorMap tmapEB) {
+constexpr int kFusedThreads = 256;
+#ifndef PIC_FUSED_MINB
+#define PIC_FUSED_MINB 4  // resident CTAs per SM the register budget is sized for
+#endif
+constexpr int kRec = 10;  // staged words per particle: cell ox oy ux uy uz sx sy sz w
+
+template <int TX, int TY>
+struct TileConst {
+    static constexpr int WX = TX + 2 * PIC_HALO, WY = TY + 2 * PIC_HALO, WA = WX * WY;
+    static constexpr size_t smem_bytes = (size_t)(9 * WA + 2 * kRec * kFusedThreads) * sizeof(float);
+};
+
+template <int WX, int WA>
+struct SmemMeshT {
+    const float *F;
+    float *Jw;
+    __device__ __forceinline__ float f(int c, int x, int y) const { return F[c * WA + y * WX + x]; }
+    __device__ __forceinline__ void j(int c, int x, int y, float v) const { atomicAdd(&Jw[c * WA + y * WX + x], v); }
+};
+
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+template <int TX, int TY>
+__global__ void __launch_bounds__(kFusedThreads, PIC_FUSED_MINB)
+    k_step_fused(const StepParams P, const __grid_constant__ CUtensorMap tmapEB) {
+    using TC = TileConst<TX, TY>;
+    constexpr int WX = TC::WX, WY = TC::WY, WA = TC::WA;
     extern __shared__ __align__(1024) unsigned char dsm[];
     __shared__ __align__(8) uint64_t bar;
-    const MeshParams &m = P.m;
-    const TileGeom &T = P.t;
-    const int WX = T.WX, WY = T.WY, WA = WX * WY;
     float *sF = reinterpret_cast<float *>(dsm);
     float *sJ = sF + 6 * WA;
+    float *ring = sJ + 3 * WA;  // [2][kRec][kFusedThreads]
+    const MeshParams &m = P.m;
 
     const int tile = blockIdx.x;
-    const int ty = tile / T.ntx, tx = tile - ty * T.ntx;
-    const int wx0 = tx * T.TX - PIC_HALO, wy0 = ty * T.TY - PIC_HALO;
+    const int ty = tile / P.t.ntx, tx = tile - ty * P.t.ntx;
+    const int wx0 = tx * TX - PIC_HALO, wy0 = ty * TY - PIC_HALO;
+    const int tid = threadIdx.x;
 
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
         mbar_expect_tx(&bar, (unsigned)(6 * WA * sizeof(float)));
         tma_load_3d(sF, &tmapEB, &bar, wx0, wy0, 0);
     }
-    for (int i = threadIdx.x; i < 3 * WA; i += blockDim.x) sJ[i] = 0.f;
+
+    // the tile's records: species 0 slots [b0, b0 + l0), then species 1, ...
+    // (scalars, not arrays, so nothing is indexed at run time)
+    int b0 = 0, b1 = 0, b2 = 0, b3 = 0, l0 = 0, l1 = 0, l2 = 0, l3 = 0;
+    auto range = [&](int s, int &b, int &l) {
+        if (s < P.nsp && P.sp[s].mobile) {
+            b = P.sp[s].tile_start[tile];
+            l = P.sp[s].tile_start[tile + 1] - b;
+        }
+    };
+    range(0, b0, l0);
+    range(1, b1, l1);
+    range(2, b2, l2);
+    range(3, b3, l3);
+    const int total = l0 + l1 + l2 + l3;
+    // record k (k < total) -> species and slot
+    auto locate = [&](int k, int &sp, int &slot) {
+        if (k < l0) {
+            sp = 0;
+            slot = b0 + k;
+        } else if (k < l0 + l1) {
+            sp = 1;
+            slot = b1 + k - l0;
+        } else if (k < l0 + l1 + l2) {
+            sp = 2;
+            slot = b2 + k - l0 - l1;
+        } else {
+            sp = 3;
+            slot = b3 + k - l0 - l1 - l2;
+        }
+    };
+    auto prefetch = [&](int k, int buf) {
+        if (k < total) {
+            int sp, slot;
+            locate(k, sp, slot);
+            const DevSpecies &S = P.sp[sp];
+            float *r = ring + buf * kRec * kFusedThreads + tid;
+            cp_async4(r + 0 * kFusedThreads, S.cell + slot);
+            cp_async4(r + 1 * kFusedThreads, S.ox + slot);
+            cp_async4(r + 2 * kFusedThreads, S.oy + slot);
+            cp_async4(r + 3 * kFusedThreads, S.ux + slot);
+            cp_async4(r + 4 * kFusedThreads, S.uy + slot);
+            cp_async4(r + 5 * kFusedThreads, S.uz + slot);
+            cp_async4(r + 6 * kFusedThreads, S.sx + slot);
+            cp_async4(r + 7 * kFusedThreads, S.sy + slot);
+            cp_async4(r + 8 * kFusedThreads, S.sz + slot);
+            cp_async4(r + 9 * kFusedThreads, S.w + slot);
+        }
+        cp_async_commit();
+    };
+
+    prefetch(tid, 0);
+    for (int i = tid; i < 3 * WA; i += kFusedThreads) sJ[i] = 0.f;
     __syncthreads();
     if (!mbar_wait_bounded(&bar, 0)) {
-        if (threadIdx.x == 0) atomicOr(P.err, PIC_EF_TIMEOUT);
+        if (tid == 0) atomicOr(P.err, PIC_EF_TIMEOUT);
+        cp_async_wait0();
         return;
     }
 
-    const SmemMesh sm{sF, sJ, WX, WY};
+    const SmemMeshT<WX, WA> sm{sF, sJ};
     const GlobalMesh gm{m.EB, m.J, m.nx, m.ny, m.ld, m.bc_x == 1, m.plane, P.err};
     // window interior where a whole stencil [i-1, i+2] fits, intersected with the mesh
     const int xlo = max(wx0 + 1, 1), xhi = min(wx0 + WX - 3, m.nx - 3);
     const int ylo = max(wy0 + 1, 1), yhi = min(wy0 + WY - 3, m.ny - 3);
-    unsigned bad = 0;
+    bool bad = false;
 
-    for (int s = 0; s < P.nsp; ++s) {
-        const DevSpecies &S = P.sp[s];
-        if (!S.mobile) continue;
-        const int p0 = S.tile_start[tile], p1 = S.tile_start[tile + 1];
-        const float qm = S.qm, a = S.a, q = S.q;
-        for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-            const uint32_t c = S.cell[p];
-            if (c == PIC_DEAD) continue;
-            const int ix = (int)(c & 0xFFFFu), iy = (int)(c >> 16);
-            const float ox = S.ox[p], oy = S.oy[p], w = S.w[p];
-            float u[3] = {S.ux[p], S.uy[p], S.uz[p]};
-            float sp[3] = {S.sx[p], S.sy[p], S.sz[p]};
-            const bool fast = ix >= xlo && ix <= xhi && iy >= ylo && iy <= yhi;
-            float E[3], B[3];
-            if (fast)
-                gather_eb(sm, ix - wx0, iy - wy0, ox, oy, E, B);
-            else
-                gather_eb(gm, ix, iy, ox, oy, E, B);
-            push_spin(qm, a, m.dt, E, B, u, sp);
-            const float gi = rsqrtf(1.f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-            int ix1 = ix, iy1 = iy;
-            float ox1 = ox, oy1 = oy;
-            advance_axis(ix1, ox1, u[0] * gi * m.dt_dx);
-            advance_axis(iy1, oy1, u[1] * gi * m.dt_dy);
-            const float qw = q * w, vz = u[2] * gi;
-            if (fast)
-                deposit_esirkepov(sm, ix - wx0, iy - wy0, ox, oy, ix1 - wx0, iy1 - wy0, ox1, oy1,
-                                  qw, vz, m.dx_dt, m.dy_dt);
-            else
-                deposit_esirkepov(gm, ix, iy, ox, oy, ix1, iy1, ox1, oy1, qw, vz, m.dx_dt, m.dy_dt);
-            const bool alive = finish_move(m, ix1, iy1);
-            if (!finite3(u) || !finite3(sp)) bad |= PIC_EF_NAN;
-            S.cell[p] = alive ? pack_cell(ix1, iy1) : PIC_DEAD;
-            S.ox[p] = ox1;
-            S.oy[p] = oy1;
-            S.ux[p] = u[0];
-            S.uy[p] = u[1];
-            S.uz[p] = u[2];
-            S.sx[p] = sp[0];
-            S.sy[p] = sp[1];
-            S.sz[p] = sp[2];
+    int buf = 0;
+    for (int k0 = 0; k0 < total; k0 += kFusedThreads) {
+        const int k = k0 + tid;
+        prefetch(k + kFusedThreads, buf ^ 1);
+        cp_async_wait1();
+        if (k < total) {
+            const float *r = ring + buf * kRec * kFusedThreads + tid;
+            int sp, slot;
+            locate(k, sp, slot);
+            const DevSpecies &S = P.sp[sp];
+            const uint32_t c = __float_as_uint(r[0]);
+            if (c != PIC_DEAD) {
+                const int ix = (int)(c & 0xFFFFu), iy = (int)(c >> 16);
+                const float ox = r[1 * kFusedThreads], oy = r[2 * kFusedThreads];
+                float u[3] = {r[3 * kFusedThreads], r[4 * kFusedThreads], r[5 * kFusedThreads]};
+                float spn[3] = {r[6 * kFusedThreads], r[7 * kFusedThreads], r[8 * kFusedThreads]};
+                const float w = r[9 * kFusedThreads];
+                const bool fast = ix >= xlo && ix <= xhi && iy >= ylo && iy <= yhi;
+                float E[3], B[3];
+                if (fast)
+                    gather_eb(sm, ix - wx0, iy - wy0, ox, oy, E, B);
+                else
+                    gather_eb(gm, ix, iy, ox, oy, E, B);
+                push_spin(S.qm, S.a, m.dt, E, B, u, spn);
+                const float gi = rsqrtf(1.f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                int ix1 = ix, iy1 = iy;
+                float ox1 = ox, oy1 = oy;
+                advance_axis(ix1, ox1, u[0] * gi * m.dt_dx);
+                advance_axis(iy1, oy1, u[1] * gi * m.dt_dy);
+                const float qw = S.q * w, vz = u[2] * gi;
+                if (fast)
+                    deposit_esirkepov(sm, ix - wx0, iy - wy0, ox, oy, ix1 - wx0, iy1 - wy0, ox1, oy1, qw, vz,
+                                      m.dx_dt, m.dy_dt);
+                else
+                    deposit_esirkepov(gm, ix, iy, ox, oy, ix1, iy1, ox1, oy1, qw, vz, m.dx_dt, m.dy_dt);
+                const bool alive = finish_move(m, ix1, iy1);
+                const float chk = u[0] * u[0] + u[1] * u[1] + u[2] * u[2] + spn[0] * spn[0] +
+                                  spn[1] * spn[1] + spn[2] * spn[2];
+                bad |= !isfinite(chk);
+                S.cell[slot] = alive ? pack_cell(ix1, iy1) : PIC_DEAD;
+                S.ox[slot] = ox1;
+                S.oy[slot] = oy1;
+                S.ux[slot] = u[0];
+                S.uy[slot] = u[1];
+                S.uz[slot] = u[2];
+                S.sx[slot] = spn[0];
+                S.sy[slot] = spn[1];
+                S.sz[slot] = spn[2];
+            }
         }
+        buf ^= 1;
     }
-    if (bad) atomicOr(P.err, bad);
+    cp_async_wait0();
+    if (bad) atomicOr(P.err, PIC_EF_NAN);
     __syncthreads();
 
     // flush the current window: 16-byte quads, skipping all-zero ones and
     // rows / columns outside the mesh (nothing is deposited there)
-    const int WQ = WX >> 2;
-    for (int qd = threadIdx.x; qd < 3 * WY * WQ; qd += blockDim.x) {
+    constexpr int WQ = WX / 4;
+    for (int qd = tid; qd < 3 * WY * WQ; qd += kFusedThreads) {
         const int c = qd / (WY * WQ);
-        const int r = qd - c * WY * WQ;
-        const int y = r / WQ, xq = r - y * WQ;
+        const int rr = qd - c * WY * WQ;
+        const int y = rr / WQ, xq = rr - y * WQ;
         const int gy = wy0 + y, gx = wx0 + 4 * xq;
         if (gy < 0 || gy >= m.ny || gx < 0 || gx >= m.ld) continue;
-        const float4 v = *reinterpret_cast<const float4 *>(&sJ[(c * WY + y) * WX + 4 * xq]);
+        const float4 v = *reinterpret_cast<const float4 *>(&sJ[c * WA + y * WX + 4 * xq]);
         if (v.x == 0.f && v.y == 0.f && v.z == 0.f && v.w == 0.f) continue;
         atomicAdd(reinterpret_cast<float4 *>(&m.J[c * m.plane + (size_t)gy * m.ld + gx]), v);
     }
@@ -240,22 +336,33 @@ __global__ void __launch_bounds__(256) k_deposit_split(const StepParams P, int s
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-size_t step_fused_smem_bytes(const TileGeom &t) {
-    return (size_t)9 * t.WX * t.WY * sizeof(float);
+template <int TX, int TY>
+static cudaError_t launch_fused_t(const StepParams &P, const CUtensorMap &tmapEB, cudaStream_t st) {
+    constexpr size_t smem = TileConst<TX, TY>::smem_bytes;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_step_fused<TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    k_step_fused<TX, TY><<<P.t.ntx * P.t.nty, kFusedThreads, smem, st>>>(P, tmapEB);
+    return cudaGetLastError();
+}
+
+bool fused_tile_supported(int tx, int ty) {
+    return (tx == 8 && ty == 4) || (tx == 16 && ty == 8) || (tx == 32 && ty == 8) ||
+           (tx == 32 && ty == 16) || (tx == 64 && ty == 16);
 }
 
 cudaError_t launch_step_fused(const StepParams &P, const CUtensorMap &tmapEB, cudaStream_t st) {
-    const size_t smem = step_fused_smem_bytes(P.t);
-    static size_t configured = 0;
-    if (smem > 48 * 1024 && smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_step_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = smem;
-    }
-    const int ntiles = P.t.ntx * P.t.nty;
-    k_step_fused<<<ntiles, 256, smem, st>>>(P, tmapEB);
-    return cudaGetLastError();
+    const int tx = P.t.TX, ty = P.t.TY;
+    if (tx == 8 && ty == 4) return launch_fused_t<8, 4>(P, tmapEB, st);
+    if (tx == 16 && ty == 8) return launch_fused_t<16, 8>(P, tmapEB, st);
+    if (tx == 32 && ty == 8) return launch_fused_t<32, 8>(P, tmapEB, st);
+    if (tx == 32 && ty == 16) return launch_fused_t<32, 16>(P, tmapEB, st);
+    if (tx == 64 && ty == 16) return launch_fused_t<64, 16>(P, tmapEB, st);
+    return cudaErrorInvalidValue;
 }
 
 static int blocks_for(int n) {

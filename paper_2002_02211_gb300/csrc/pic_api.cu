@@ -148,6 +148,7 @@ void choose_tiles(Ctx *c) {
         tx = cells >= (1LL << 21) ? 32 : 16;
         ty = cells >= (1LL << 21) ? 16 : 8;
     }
+    // tile shapes the fused kernel is compiled for (pic_validate_config checks)
     c->tg.TX = tx;
     c->tg.TY = ty;
     c->tg.WX = tx + 2 * PIC_HALO;
@@ -238,10 +239,8 @@ pic_status_t pic_validate_config(const pic_config_t *cfg) {
         if (sp.capacity < 0 || sp.capacity > 0x7FFFFFF0LL)
             return fail(c, PIC_ERR_ARG, "species capacity must be in [0, 2^31 - 16]");
     }
-    if ((cfg->tile_x != 0 || cfg->tile_y != 0) &&
-        (cfg->tile_x < 4 || cfg->tile_y < 1 || cfg->tile_x % 4 != 0 || cfg->tile_x + 2 * PIC_HALO > 256 ||
-         cfg->tile_y + 2 * PIC_HALO > 256))
-        return fail(c, PIC_ERR_ARG, "tile_x must be a multiple of 4 and tile + 8 <= 256 cells");
+    if ((cfg->tile_x != 0 || cfg->tile_y != 0) && !fused_tile_supported(cfg->tile_x, cfg->tile_y))
+        return fail(c, PIC_ERR_ARG, "tile must be one of 8x4, 16x8, 32x8, 32x16, 64x16 cells");
     if (cfg->sort_every < 0) return fail(c, PIC_ERR_ARG, "sort_every must be >= 0");
     return PIC_OK;
 }

@@ -148,6 +148,7 @@ __device__ __forceinline__ void gather_eb(const M &m, int ix, int iy, float ox, 
 //   s' = s + (sin th / th) w x s + ((1 - cos th) / th^2) w x (w x s),  th = |w|.
 // Below th = 0.03 the two factors use their Taylor series to second order
 // (truncation below 1e-9, under float rounding); above, sincosf of th/2.
+// Divisions use the fast reciprocal (2 ulp), well inside the 1e-5 budget.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void push_spin(float qm, float a, float dt, const float E[3],
                                           const float B[3], float u[3], float s[3]) {
@@ -155,7 +156,7 @@ __device__ __forceinline__ void push_spin(float qm, float a, float dt, const flo
     const float umx = u[0] + h * E[0], umy = u[1] + h * E[1], umz = u[2] + h * E[2];
     const float gi = rsqrtf(1.f + umx * umx + umy * umy + umz * umz);
     const float tx = h * B[0] * gi, ty = h * B[1] * gi, tz = h * B[2] * gi;
-    const float f = 2.f / (1.f + tx * tx + ty * ty + tz * tz);
+    const float f = __fdividef(2.f, 1.f + tx * tx + ty * ty + tz * tz);
     const float upx = umx + (umy * tz - umz * ty);
     const float upy = umy + (umz * tx - umx * tz);
     const float upz = umz + (umx * ty - umy * tx);
@@ -170,7 +171,7 @@ __device__ __forceinline__ void push_spin(float qm, float a, float dt, const flo
     const float gbi = rsqrtf(g2);
     const float gb = g2 * gbi;
     const float vx = bx * gbi, vy = by * gbi, vz = bz * gbi;
-    const float ip1 = 1.f / (1.f + gb);
+    const float ip1 = __fdividef(1.f, 1.f + gb);
     const float omB = a + gbi;               // Eq. (3)
     const float omv = a * gb * ip1;          // Eq. (3)
     const float omE = a + ip1;               // Eq. (3)
@@ -189,11 +190,11 @@ __device__ __forceinline__ void push_spin(float qm, float a, float dt, const flo
         A = 1.f - th2 * (1.f / 6.f);
         C = 0.5f - th2 * (1.f / 24.f);
     } else {
-        const float th = sqrtf(th2);
+        const float rth = rsqrtf(th2);
         float sh, ch;
-        sincosf(0.5f * th, &sh, &ch);
-        A = 2.f * sh * ch / th;
-        C = 2.f * sh * sh / th2;
+        sincosf(0.5f * th2 * rth, &sh, &ch);
+        A = 2.f * sh * ch * rth;
+        C = 2.f * sh * sh * rth * rth;
     }
     const float s0 = s[0], s1 = s[1], s2 = s[2];
     const float c0 = wy * s2 - wz * s1, c1 = wz * s0 - wx * s2, c2 = wx * s1 - wy * s0;  // w x s
@@ -255,10 +256,38 @@ __device__ __forceinline__ int shape3(int i, float o, int i1, float o1, float S0
 // Rows / columns that only hold zeros when the particle stays in its cell
 // are skipped.
 // ---------------------------------------------------------------------------
+// Move that stays inside its cell (the common case): with the offsets d, e
+// of the move and the midpoint (xm, ym) = (ox + d/2, oy + e/2) the weights
+// above reduce to
+//   Jx(i+1/2, j) = q w d dx/dt (1 - ym),  Jx(i+1/2, j+1) = q w d dx/dt ym,
+//   Jy(i, j+1/2) = q w e dy/dt (1 - xm),  Jy(i+1, j+1/2) = q w e dy/dt xm,
+//   Jz = q w vz [(1-xm)(1-ym) + de/12, xm(1-ym) - de/12, (1-xm) ym - de/12, xm ym + de/12].
+template <class M>
+__device__ __forceinline__ void deposit_in_cell(const M &m, int ix, int iy, float ox, float oy,
+                                                float ox1, float oy1, float qw, float vz,
+                                                float dx_dt, float dy_dt) {
+    const float d = ox1 - ox, e = oy1 - oy;
+    const float xm = ox + 0.5f * d, ym = oy + 0.5f * e;
+    const float jx = qw * dx_dt * d, jy = qw * dy_dt * e, cz = qw * vz;
+    const float de = d * e * (1.f / 12.f);
+    m.j(0, ix, iy, jx * (1.f - ym));
+    m.j(0, ix, iy + 1, jx * ym);
+    m.j(1, ix, iy, jy * (1.f - xm));
+    m.j(1, ix + 1, iy, jy * xm);
+    m.j(2, ix, iy, cz * ((1.f - xm) * (1.f - ym) + de));
+    m.j(2, ix + 1, iy, cz * (xm * (1.f - ym) - de));
+    m.j(2, ix, iy + 1, cz * ((1.f - xm) * ym - de));
+    m.j(2, ix + 1, iy + 1, cz * (xm * ym + de));
+}
+
 template <class M>
 __device__ __forceinline__ void deposit_esirkepov(const M &m, int ix, int iy, float ox, float oy,
                                                   int ix1, int iy1, float ox1, float oy1,
                                                   float qw, float vz, float dx_dt, float dy_dt) {
+    if (ix1 == ix && iy1 == iy) {
+        deposit_in_cell(m, ix, iy, ox, oy, ox1, oy1, qw, vz, dx_dt, dy_dt);
+        return;
+    }
     float S0x[3], dSx[3], S0y[3], dSy[3];
     const int gx = shape3(ix, ox, ix1, ox1, S0x, dSx);
     const int gy = shape3(iy, oy, iy1, oy1, S0y, dSy);

@@ -11,7 +11,7 @@ struct LaserParams {
 };
 
 // k_particles.cu
-size_t step_fused_smem_bytes(const TileGeom &t);
+bool fused_tile_supported(int tx, int ty);
 cudaError_t launch_step_fused(const StepParams &P, const CUtensorMap &tmapEB, cudaStream_t st);
 cudaError_t launch_push_split(const StepParams &P, int s, int n_upper, cudaStream_t st);
 cudaError_t launch_deposit_split(const StepParams &P, int s, int n_upper, cudaStream_t st);

@@ -64,8 +64,10 @@ def test_validate_config_rejects(field, value):
 
 def test_validate_config_rejects_bad_tiles_and_species():
     cfg = pic.config_from_workload(W.small_case())
-    cfg.tile_x, cfg.tile_y = 6, 4        # tile_x must be a multiple of 4 (16-byte TMA rows)
+    cfg.tile_x, cfg.tile_y = 6, 4        # not a compiled tile shape
     assert _status(cfg) == -1
+    cfg.tile_x, cfg.tile_y = 32, 16
+    assert _status(cfg) == 0
     cfg = pic.config_from_workload(W.small_case())
     cfg.sp[0].m = 0.0
     assert _status(cfg) == -1
