@@ -51,7 +51,7 @@ def parse(argv=None):
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["config3", "config1"], default="config3")
-    ap.add_argument("--sort-every", type=int, default=8)
+    ap.add_argument("--sort-every", type=int, default=32)
     ap.add_argument("--diag-every", type=int, default=10)
     ap.add_argument("--tile", type=int, nargs=2, default=(0, 0))
     ap.add_argument("--ny", type=int, default=0, help="smaller ny for profiling captures")

@@ -84,7 +84,7 @@ typedef struct {
     double t_peak_periods;       /* time of the envelope peak at x = 0 [periods]   */
     int nspecies;                /* 1 .. PIC_MAX_SPECIES                           */
     pic_species_t sp[PIC_MAX_SPECIES];
-    int sort_every;              /* steps between tile sorts in pic_step (0: 8)    */
+    int sort_every;              /* steps between tile sorts in pic_step (0: 32)   */
     int tile_x, tile_y;          /* cells per tile: 8x4, 16x8, 32x8, 32x16 or 64x16 (0, 0: chosen
                                     from the mesh size)                            */
 } pic_config_t;

@@ -71,7 +71,8 @@ __device__ __forceinline__ bool finish_move(const MeshParams &m, int &ix1, int &
 // ---------------------------------------------------------------------------
 // Fused step kernel.  CTA = one tile of TX x TY cells (compile-time, so every
 // shared-memory offset below is an immediate).  Thread 0 stages the
-// 6-component field window [tile - 4, tile + 4) in x and y with one 3D TMA
+// 6-component field window (4 cells of margin before the tile in x and y,
+// at least 4 after, rows padded to a multiple of 32 floats) with one 3D TMA
 // load (zero fill outside the mesh).  Particle records of the tile (both
 // species, one slot range after the other) stream through a two-deep
 // cp.async ring in shared memory: while a thread computes one record it has
@@ -88,7 +89,7 @@ constexpr int kRec = 10;  // staged words per particle: cell ox oy ux uy uz sx s
 
 template <int TX, int TY>
 struct TileConst {
-    static constexpr int WX = TX + 2 * PIC_HALO, WY = TY + 2 * PIC_HALO, WA = WX * WY;
+    static constexpr int WX = window_wx(TX), WY = window_wy(TY), WA = WX * WY;
     static constexpr size_t smem_bytes = (size_t)(9 * WA + 2 * kRec * kFusedThreads) * sizeof(float);
 };
 
@@ -339,6 +340,7 @@ __global__ void __launch_bounds__(256) k_deposit_split(const StepParams P, int s
 template <int TX, int TY>
 static cudaError_t launch_fused_t(const StepParams &P, const CUtensorMap &tmapEB, cudaStream_t st) {
     constexpr size_t smem = TileConst<TX, TY>::smem_bytes;
+    if (P.t.WX != TileConst<TX, TY>::WX || P.t.WY != TileConst<TX, TY>::WY) return cudaErrorInvalidValue;
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(k_step_fused<TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -146,13 +146,13 @@ void choose_tiles(Ctx *c) {
     if (tx <= 0 || ty <= 0) {
         const long long cells = (long long)c->cfg.nx * c->cfg.ny;
         tx = cells >= (1LL << 21) ? 32 : 16;
-        ty = cells >= (1LL << 21) ? 16 : 8;
+        ty = 8;
     }
     // tile shapes the fused kernel is compiled for (pic_validate_config checks)
     c->tg.TX = tx;
     c->tg.TY = ty;
-    c->tg.WX = tx + 2 * PIC_HALO;
-    c->tg.WY = ty + 2 * PIC_HALO;
+    c->tg.WX = window_wx(tx);
+    c->tg.WY = window_wy(ty);
     c->tg.ntx = (c->cfg.nx + tx - 1) / tx;
     c->tg.nty = (c->cfg.ny + ty - 1) / ty;
     c->ntiles = c->tg.ntx * c->tg.nty;
@@ -254,7 +254,7 @@ pic_status_t pic_create(const pic_config_t *cfg, void *stream, void **ctx_out) {
     c = new (std::nothrow) Ctx();
     if (!c) return fail(nullptr, PIC_ERR_CUDA, "host allocation failed");
     c->cfg = *cfg;
-    if (c->cfg.sort_every == 0) c->cfg.sort_every = 8;
+    if (c->cfg.sort_every == 0) c->cfg.sort_every = 32;
     cudaStream_t st = S(stream);
     auto bail = [&](pic_status_t s) {
         g_create_error = c->last_error;

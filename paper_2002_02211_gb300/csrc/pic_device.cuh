@@ -49,9 +49,13 @@ struct MeshParams {
 
 struct TileGeom {
     int TX, TY;                    // tile size in cells
-    int WX, WY;                    // window = tile + 2 * PIC_HALO
+    int WX, WY;                    // window: x row stride (tile + 2 * PIC_HALO rounded up to
+                                   // 32 floats, so a row shift never changes a bank), y rows
     int ntx, nty;                  // tiles along x and y
 };
+
+__host__ __device__ constexpr int window_wx(int tx) { return (tx + 2 * PIC_HALO + 31) / 32 * 32; }
+__host__ __device__ constexpr int window_wy(int ty) { return ty + 2 * PIC_HALO; }
 
 struct StepParams {
     MeshParams m;
