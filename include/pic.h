@@ -204,6 +204,35 @@ pic_status_t pic_sync(void *ctx, void *stream);
 /* Number of CUDA kernels this context has launched so far (host counter). */
 pic_status_t pic_launch_count(void *ctx, int64_t *count);
 
+/* Eq. (4) moments, as pic_polarization computes them, of n particles held in
+ * caller-owned device arrays (the layout of the library's own buffers: cell
+ * words with 0xFFFFFFFF marking a removed particle, float32 u, s and w), for
+ * a species of mass mass_me [m_e] and the kinetic-energy window [emin, emax)
+ * MeV.  The result is written to the caller's device memory *out_dev.
+ *
+ * This entry point allocates no device memory: it is meant for callers that
+ * cannot, e.g. code being captured into a CUDA graph, callers whose device
+ * memory all comes from their own pool, or loops that cannot afford the
+ * device-wide synchronisation of cudaMalloc.  The reduction's per-block
+ * partial sums live in one fixed array of about 29 KB that the library
+ * declares at file scope; every GPU that loads the library holds it until the
+ * process exits.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents
+ * (every slot is rewritten before it is read, so nothing needs clearing);
+ * calls that overlap on the GPU (different streams, or different host
+ * threads) race on it and must be ordered by the caller.
+ *
+ * n must be in [0, PIC_NOALLOC_MAX_PARTICLES] (else PIC_ERR_ARG, with the
+ * reason in pic_last_error(NULL)); the pointers must be device pointers of
+ * the current device.  Asynchronous on `stream`.  No counterpart in the
+ * paper: this is an interface variant, not part of the method. */
+#define PIC_NOALLOC_MAX_PARTICLES 2147483647LL
+pic_status_t pic_moments_noalloc(int64_t n, const uint32_t *cell, const float *ux, const float *uy,
+                                 const float *uz, const float *sx, const float *sy, const float *sz,
+                                 const float *w, double mass_me, double emin_mev, double emax_mev,
+                                 pic_moments_t *out_dev, void *stream);
+
 /* Reason for the last failure on this context (or of pic_create when ctx is NULL). */
 const char *pic_last_error(void *ctx);
 

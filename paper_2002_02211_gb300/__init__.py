@@ -95,6 +95,8 @@ _SIGS = {
     "pic_capture_background": [C.c_void_p, C.c_void_p],
     "pic_gauss_residual": [C.c_void_p, C.POINTER(C.c_double), C.c_void_p],
     "pic_sync": [C.c_void_p, C.c_void_p],
+    "pic_moments_noalloc": [C.c_int64] + [C.c_void_p] * 8 + [C.c_double, C.c_double, C.c_double,
+                                                              C.c_void_p, C.c_void_p],
 }
 
 
@@ -130,6 +132,13 @@ def _stream(stream):
         return None
     h = getattr(stream, "cuda_stream", stream)
     return C.c_void_p(int(h))
+
+
+def moments_noalloc(n, cell, ux, uy, uz, sx, sy, sz, w, mass_me, emin, emax, out_dev, stream=None):
+    """pic_moments_noalloc: every array argument is a device address (int)."""
+    ptrs = [C.c_void_p(int(a)) for a in (cell, ux, uy, uz, sx, sy, sz, w)]
+    _check(load().pic_moments_noalloc(int(n), *ptrs, float(mass_me), float(emin), float(emax),
+                                      C.c_void_p(int(out_dev)), _stream(stream)))
 
 
 def config_from_workload(wl, capacity_factor: float = 1.0, sort_every: int = 0, tile=(0, 0)):

@@ -218,6 +218,8 @@ pic_status_t alloc_old(Ctx *c, int s) {
 
 }  // namespace
 
+void set_global_error(const std::string &msg) { g_create_error = msg; }
+
 extern "C" {
 
 pic_status_t pic_validate_config(const pic_config_t *cfg) {

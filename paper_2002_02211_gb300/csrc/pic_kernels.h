@@ -3,6 +3,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <string>
+
 #include "pic_device.cuh"
 
 struct LaserParams {
@@ -38,3 +40,6 @@ cudaError_t launch_gauss(const MeshParams &m, const float *rho, const float *rho
                          double dy, int i0, int i1, double *partials, double *result,
                          cudaStream_t st);
 cudaError_t launch_negate_copy(const float *src, float *dst, size_t n, cudaStream_t st);
+
+// pic_api.cu: the message pic_last_error(NULL) returns
+void set_global_error(const std::string &msg);
