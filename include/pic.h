@@ -184,6 +184,19 @@ pic_status_t pic_push_deposit(void *ctx, void *stream);
  * pic_field_update.  No host synchronisation. */
 pic_status_t pic_step(void *ctx, int nsteps, void *stream);
 
+/* a8 inside the step: every `every` steps (0 turns it off) pic_push_deposit,
+ * and so pic_step, also accumulates the Eq. (4) moments of every species over
+ * the particles it has just moved (u, s at n+1/2, x at n+1; live particles
+ * whose kinetic energy lies in [emin[s], emax[s]) MeV; NULL arrays mean no
+ * window).  The sums are float per thread over a few particles, FP64 per CTA
+ * and across CTAs; the variance is taken about the previous diagnostic's
+ * mean.  No extra pass over the particles and no host synchronisation. */
+pic_status_t pic_set_diagnostics(void *ctx, int every, const double *emin_mev, const double *emax_mev);
+
+/* The moments of the last in-step diagnostic (out[nspecies]) and the step
+ * index they belong to (-1 if none yet).  Synchronous. */
+pic_status_t pic_get_diagnostics(void *ctx, pic_moments_t *out, int64_t *step, void *stream);
+
 /* a8: Eq. (4) moments of one species in an energy window.  Synchronous;
  * also reports device-side error flags (PIC_ERR_NAN, PIC_ERR_TIMEOUT). */
 pic_status_t pic_polarization(void *ctx, int species, double emin_mev, double emax_mev,

@@ -95,6 +95,8 @@ _SIGS = {
     "pic_capture_background": [C.c_void_p, C.c_void_p],
     "pic_gauss_residual": [C.c_void_p, C.POINTER(C.c_double), C.c_void_p],
     "pic_sync": [C.c_void_p, C.c_void_p],
+    "pic_set_diagnostics": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
+    "pic_get_diagnostics": [C.c_void_p, C.c_void_p, C.POINTER(C.c_int64), C.c_void_p],
     "pic_moments_noalloc": [C.c_int64] + [C.c_void_p] * 8 + [C.c_double, C.c_double, C.c_double,
                                                               C.c_void_p, C.c_void_p],
 }
@@ -298,6 +300,19 @@ class Simulation:
         self._c(load().pic_polarization(self.h, s, float(emin), float(emax), C.byref(m), self._s))
         return dict(P=np.array(m.P[:]), sum_w=m.sum_w, count=m.count, ekin_mean=m.ekin_mean,
                     ekin_var=m.ekin_var)
+
+    def set_diagnostics(self, every, emin=None, emax=None):
+        n = self.nspecies
+        lo = (C.c_double * n)(*([-math.inf] * n if emin is None else emin))
+        hi = (C.c_double * n)(*([math.inf] * n if emax is None else emax))
+        self._c(load().pic_set_diagnostics(self.h, int(every), lo, hi))
+
+    def get_diagnostics(self):
+        out = (pic_moments_t * self.nspecies)()
+        st = C.c_int64()
+        self._c(load().pic_get_diagnostics(self.h, out, C.byref(st), self._s))
+        return st.value, [dict(P=np.array(m.P[:]), sum_w=m.sum_w, count=m.count, ekin_mean=m.ekin_mean,
+                               ekin_var=m.ekin_var) for m in out]
 
     def capture_background(self):
         self._c(load().pic_capture_background(self.h, self._s))

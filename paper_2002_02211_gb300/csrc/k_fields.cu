@@ -1,6 +1,8 @@
 // k_fields.cu -- a6: Yee FDTD update (Yee 1966) in three stages, B half step,
 // E full step with -J (which is then cleared), B half step, with a
 // first-order Silver-Mueller boundary at x_min (laser source) and x_max.
+#include <cmath>
+
 #include "pic_kernels.h"
 
 namespace {
@@ -25,16 +27,6 @@ __global__ void __launch_bounds__(256) k_b_half(const MeshParams m, float hdx, f
     }
 }
 
-__device__ double laser_value(const LaserParams &L, double t, double y, int comp) {
-    const double e = (t - L.t_peak) / L.tau;
-    const double r = (y - L.yc) / L.w0;
-    const double env = exp(-e * e) * exp(-r * r);
-    const double ph = t - L.t_peak;
-    if (L.pol == 1) return comp == 0 ? L.a0 * env * sin(ph) : 0.0;
-    if (L.pol == 2) return L.a0 * 0.7071067811865476 * env * (comp == 0 ? sin(ph) : cos(ph));
-    return 0.0;
-}
-
 // boundary B at t^{n+1/2}: the incoming characteristic is the laser at x_min
 // and zero at x_max, imposed on time-centred values with E^{n+1} from its own
 // update including the transverse term dBx = Bx(j+1/2) - Bx(j-1/2) (r = dt/dx,
@@ -43,16 +35,19 @@ __device__ double laser_value(const LaserParams &L, double t, double y, int comp
 //   Bz(-1/2) = (4 g - 2 Ey(0) - (1-r) Bz(1/2)) / (1+r)
 //   By(nx-1/2) = (-2 Ez(nx-1) - (1-r) By(nx-3/2) + q dBx(nx-1)) / (1+r)
 //   Bz(nx-1/2) = (2 Ey(nx-1) - (1-r) Bz(nx-3/2)) / (1+r)
-__global__ void k_boundary(const MeshParams m, float *bnd, const LaserParams L, double t, double r,
-                           double q) {
+__global__ void k_boundary(const MeshParams m, float *bnd, const double *prof, double fz, double fy,
+                           double r, double q) {
+    // incident Ez (f) and Ey (g) at t^{n+1/2}: the time factor fz, fy (envelope x
+    // carrier, one number per step) times the transverse profile prof[j] at y_j
+    // and prof[ny + j] at y_{j+1/2}
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= m.ny) return;
     const size_t P = m.plane;
     float *EB = m.EB;
     const size_t c0 = (size_t)j * m.ld, cl = c0 + m.nx - 1;
     const size_t cm = (size_t)(j == 0 ? m.ny - 1 : j - 1) * m.ld;
-    const double f = laser_value(L, t, (double)j * L.dy, 1);
-    const double g = laser_value(L, t, ((double)j + 0.5) * L.dy, 0);
+    const double f = fz * prof[j];
+    const double g = fy * prof[m.ny + j];
     const double ir = 1.0 / (1.0 + r), mr = 1.0 - r;
     const double dbx0 = (double)EB[3 * P + c0] - (double)EB[3 * P + cm];
     const double dbxl = (double)EB[3 * P + cl] - (double)EB[3 * P + cm + m.nx - 1];
@@ -95,14 +90,42 @@ __global__ void __launch_bounds__(256) k_e_full(const MeshParams m, const float 
 
 }  // namespace
 
-cudaError_t launch_field_update(const MeshParams &m, float *bnd, const LaserParams &L, double dt,
-                                double dx, double dy, long long step, cudaStream_t st) {
+// laser time factors at t: the incident Ez (comp 1) and Ey (comp 0) on the
+// axis, i.e. without the transverse profile
+static void laser_time_factors(const LaserParams &L, double t, double *fz, double *fy) {
+    const double e = (t - L.t_peak) / L.tau;
+    const double env = std::exp(-e * e);
+    const double ph = t - L.t_peak;
+    *fz = *fy = 0.0;
+    if (L.pol == 1) {
+        *fy = L.a0 * env * std::sin(ph);
+    } else if (L.pol == 2) {
+        *fy = L.a0 * 0.7071067811865476 * env * std::sin(ph);
+        *fz = L.a0 * 0.7071067811865476 * env * std::cos(ph);
+    }
+}
+
+cudaError_t launch_field_update(const MeshParams &m, float *bnd, const double *prof, const LaserParams &L,
+                                double dt, double dx, double dy, long long step, cudaStream_t st) {
     const dim3 blk(256), grd((m.nx + 255) / 256, m.ny);
     const float hdx = (float)(0.5 * dt / dx), hdy = (float)(0.5 * dt / dy);
     k_b_half<<<grd, blk, 0, st>>>(m, hdx, hdy);
-    if (m.bc_x == 0)
-        k_boundary<<<(m.ny + 127) / 128, 128, 0, st>>>(m, bnd, L, ((double)step + 0.5) * dt, dt / dx, dt / dy);
+    if (m.bc_x == 0) {
+        double fz, fy;
+        laser_time_factors(L, ((double)step + 0.5) * dt, &fz, &fy);
+        k_boundary<<<(m.ny + 127) / 128, 128, 0, st>>>(m, bnd, prof, fz, fy, dt / dx, dt / dy);
+    }
     k_e_full<<<grd, blk, 0, st>>>(m, bnd, (float)dt, (float)(dt / dx), (float)(dt / dy));
     k_b_half<<<grd, blk, 0, st>>>(m, hdx, hdy);
     return cudaGetLastError();
+}
+
+// transverse laser profile exp(-((y - yc)/w0)^2) at y_j (first ny) and y_{j+1/2}
+void laser_profile(const LaserParams &L, int ny, double *host) {
+    for (int j = 0; j < ny; ++j) {
+        const double a = ((double)j * L.dy - L.yc) / L.w0;
+        const double b = (((double)j + 0.5) * L.dy - L.yc) / L.w0;
+        host[j] = std::exp(-a * a);
+        host[ny + j] = std::exp(-b * b);
+    }
 }

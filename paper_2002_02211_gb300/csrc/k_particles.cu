@@ -132,42 +132,11 @@ __global__ void __launch_bounds__(kFusedThreads, PIC_FUSED_MINB)
         tma_load_3d(sF, &tmapEB, &bar, wx0, wy0, 0);
     }
 
-    // the tile's records: species 0 slots [b0, b0 + l0), then species 1, ...
-    // (scalars, not arrays, so nothing is indexed at run time)
-    int b0 = 0, b1 = 0, b2 = 0, b3 = 0, l0 = 0, l1 = 0, l2 = 0, l3 = 0;
-    auto range = [&](int s, int &b, int &l) {
-        if (s < P.nsp && P.sp[s].mobile) {
-            b = P.sp[s].tile_start[tile];
-            l = P.sp[s].tile_start[tile + 1] - b;
-        }
-    };
-    range(0, b0, l0);
-    range(1, b1, l1);
-    range(2, b2, l2);
-    range(3, b3, l3);
-    const int total = l0 + l1 + l2 + l3;
-    // record k (k < total) -> species and slot
-    auto locate = [&](int k, int &sp, int &slot) {
-        if (k < l0) {
-            sp = 0;
-            slot = b0 + k;
-        } else if (k < l0 + l1) {
-            sp = 1;
-            slot = b1 + k - l0;
-        } else if (k < l0 + l1 + l2) {
-            sp = 2;
-            slot = b2 + k - l0 - l1;
-        } else {
-            sp = 3;
-            slot = b3 + k - l0 - l1 - l2;
-        }
-    };
-    auto prefetch = [&](int k, int buf) {
-        if (k < total) {
-            int sp, slot;
-            locate(k, sp, slot);
-            const DevSpecies &S = P.sp[sp];
-            float *r = ring + buf * kRec * kFusedThreads + tid;
+    float *ring0 = ring + tid;
+    // particle record `slot` of species S into ring stage `buf`
+    auto prefetch = [&](const DevSpecies &S, int slot, bool live, int buf) {
+        if (live) {
+            float *r = ring0 + buf * kRec * kFusedThreads;
             cp_async4(r + 0 * kFusedThreads, S.cell + slot);
             cp_async4(r + 1 * kFusedThreads, S.ox + slot);
             cp_async4(r + 2 * kFusedThreads, S.oy + slot);
@@ -182,7 +151,20 @@ __global__ void __launch_bounds__(kFusedThreads, PIC_FUSED_MINB)
         cp_async_commit();
     };
 
-    prefetch(tid, 0);
+    // Eq. (4) diagnostic sums of one species: float per thread (at most
+    // total/256 particles each), then double across the CTA
+    __shared__ double sdiag[kFusedThreads / 32][8];
+    const bool diag = P.diag.on != 0;
+
+    // the first record of the first mobile species is requested before the
+    // window wait, so both latencies overlap
+    int first = -1;
+    for (int sp = 0; sp < P.nsp && first < 0; ++sp)
+        if (P.sp[sp].mobile) first = sp;
+    if (first >= 0) {
+        const int beg = P.sp[first].tile_start[tile];
+        prefetch(P.sp[first], beg + tid, tid < P.sp[first].tile_start[tile + 1] - beg, 0);
+    }
     for (int i = tid; i < 3 * WA; i += kFusedThreads) sJ[i] = 0.f;
     __syncthreads();
     if (!mbar_wait_bounded(&bar, 0)) {
@@ -198,59 +180,101 @@ __global__ void __launch_bounds__(kFusedThreads, PIC_FUSED_MINB)
     const int ylo = max(wy0 + 1, 1), yhi = min(wy0 + WY - 3, m.ny - 3);
     bool bad = false;
 
-    int buf = 0;
-    for (int k0 = 0; k0 < total; k0 += kFusedThreads) {
-        const int k = k0 + tid;
-        prefetch(k + kFusedThreads, buf ^ 1);
-        cp_async_wait1();
-        if (k < total) {
-            const float *r = ring + buf * kRec * kFusedThreads + tid;
-            int sp, slot;
-            locate(k, sp, slot);
-            const DevSpecies &S = P.sp[sp];
-            const uint32_t c = __float_as_uint(r[0]);
-            if (c != PIC_DEAD) {
-                const int ix = (int)(c & 0xFFFFu), iy = (int)(c >> 16);
-                const float ox = r[1 * kFusedThreads], oy = r[2 * kFusedThreads];
-                float u[3] = {r[3 * kFusedThreads], r[4 * kFusedThreads], r[5 * kFusedThreads]};
-                float spn[3] = {r[6 * kFusedThreads], r[7 * kFusedThreads], r[8 * kFusedThreads]};
-                const float w = r[9 * kFusedThreads];
-                const bool fast = ix >= xlo && ix <= xhi && iy >= ylo && iy <= yhi;
-                float E[3], B[3];
-                if (fast)
-                    gather_eb(sm, ix - wx0, iy - wy0, ox, oy, E, B);
-                else
-                    gather_eb(gm, ix, iy, ox, oy, E, B);
-                push_spin(S.qm, S.a, m.dt, E, B, u, spn);
-                const float gi = rsqrtf(1.f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-                int ix1 = ix, iy1 = iy;
-                float ox1 = ox, oy1 = oy;
-                advance_axis(ix1, ox1, u[0] * gi * m.dt_dx);
-                advance_axis(iy1, oy1, u[1] * gi * m.dt_dy);
-                const float qw = S.q * w, vz = u[2] * gi;
-                if (fast)
-                    deposit_esirkepov(sm, ix - wx0, iy - wy0, ox, oy, ix1 - wx0, iy1 - wy0, ox1, oy1, qw, vz,
-                                      m.dx_dt, m.dy_dt);
-                else
-                    deposit_esirkepov(gm, ix, iy, ox, oy, ix1, iy1, ox1, oy1, qw, vz, m.dx_dt, m.dy_dt);
-                const bool alive = finish_move(m, ix1, iy1);
-                const float chk = u[0] * u[0] + u[1] * u[1] + u[2] * u[2] + spn[0] * spn[0] +
-                                  spn[1] * spn[1] + spn[2] * spn[2];
-                bad |= !isfinite(chk);
-                S.cell[slot] = alive ? pack_cell(ix1, iy1) : PIC_DEAD;
-                S.ox[slot] = ox1;
-                S.oy[slot] = oy1;
-                S.ux[slot] = u[0];
-                S.uy[slot] = u[1];
-                S.uz[slot] = u[2];
-                S.sx[slot] = spn[0];
-                S.sy[slot] = spn[1];
-                S.sz[slot] = spn[2];
-            }
+    for (int sp = 0; sp < P.nsp; ++sp) {
+        const DevSpecies &S = P.sp[sp];
+        if (!S.mobile) continue;
+        const int beg = S.tile_start[tile], len = S.tile_start[tile + 1] - beg;
+        const float qm = S.qm, a = S.a, q = S.q;
+        float dacc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float dlo = 0.f, dhi = 0.f, dm = 0.f, dshift = 0.f;
+        if (diag) {
+            dlo = P.diag.lo[sp];
+            dhi = P.diag.hi[sp];
+            dm = P.diag.m_mev[sp];
+            dshift = (float)P.diag.shift[sp];
         }
-        buf ^= 1;
+        int buf = 0;
+        if (sp != first) prefetch(S, beg + tid, tid < len, 0);
+        for (int k0 = 0; k0 < len; k0 += kFusedThreads) {
+            const int k = k0 + tid;
+            prefetch(S, beg + k + kFusedThreads, k + kFusedThreads < len, buf ^ 1);
+            cp_async_wait1();
+            if (k < len) {
+                const int slot = beg + k;
+                const float *r = ring0 + buf * kRec * kFusedThreads;
+                const uint32_t c = __float_as_uint(r[0]);
+                if (c != PIC_DEAD) {
+                    const int ix = (int)(c & 0xFFFFu), iy = (int)(c >> 16);
+                    const float ox = r[1 * kFusedThreads], oy = r[2 * kFusedThreads];
+                    float u[3] = {r[3 * kFusedThreads], r[4 * kFusedThreads], r[5 * kFusedThreads]};
+                    float spn[3] = {r[6 * kFusedThreads], r[7 * kFusedThreads], r[8 * kFusedThreads]};
+                    const float w = r[9 * kFusedThreads];
+                    const bool fast = ix >= xlo && ix <= xhi && iy >= ylo && iy <= yhi;
+                    float E[3], B[3];
+                    if (fast)
+                        gather_eb(sm, ix - wx0, iy - wy0, ox, oy, E, B);
+                    else
+                        gather_eb(gm, ix, iy, ox, oy, E, B);
+                    push_spin(qm, a, m.dt, E, B, u, spn);
+                    const float gi = rsqrtf(1.f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                    int ix1 = ix, iy1 = iy;
+                    float ox1 = ox, oy1 = oy;
+                    advance_axis(ix1, ox1, u[0] * gi * m.dt_dx);
+                    advance_axis(iy1, oy1, u[1] * gi * m.dt_dy);
+                    const float qw = q * w, vz = u[2] * gi;
+                    if (fast)
+                        deposit_esirkepov(sm, ix - wx0, iy - wy0, ox, oy, ix1 - wx0, iy1 - wy0, ox1, oy1, qw,
+                                          vz, m.dx_dt, m.dy_dt);
+                    else
+                        deposit_esirkepov(gm, ix, iy, ox, oy, ix1, iy1, ox1, oy1, qw, vz, m.dx_dt, m.dy_dt);
+                    const bool alive = finish_move(m, ix1, iy1);
+                    const float chk = u[0] * u[0] + u[1] * u[1] + u[2] * u[2] + spn[0] * spn[0] +
+                                      spn[1] * spn[1] + spn[2] * spn[2];
+                    bad |= !isfinite(chk);
+                    if (diag && alive) {
+                        const float e = ekin_mev(dm, u[0], u[1], u[2]);
+                        if (e >= dlo && e < dhi) {
+                            const float ep = e - dshift;
+                            dacc[0] += w;
+                            dacc[1] += w * spn[0];
+                            dacc[2] += w * spn[1];
+                            dacc[3] += w * spn[2];
+                            dacc[4] += w * ep;
+                            dacc[5] += w * ep * ep;
+                            dacc[6] += 1.f;
+                        }
+                    }
+                    S.cell[slot] = alive ? pack_cell(ix1, iy1) : PIC_DEAD;
+                    S.ox[slot] = ox1;
+                    S.oy[slot] = oy1;
+                    S.ux[slot] = u[0];
+                    S.uy[slot] = u[1];
+                    S.uz[slot] = u[2];
+                    S.sx[slot] = spn[0];
+                    S.sy[slot] = spn[1];
+                    S.sz[slot] = spn[2];
+                }
+            }
+            buf ^= 1;
+        }
+        cp_async_wait0();
+        if (diag) {
+            // converged here: warp shuffles in double, then one row per CTA
+            const int lane = tid & 31, wid = tid >> 5;
+            for (int qd = 0; qd < 7; ++qd) {
+                double v = (double)dacc[qd];
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+                if (lane == 0) sdiag[wid][qd] = v;
+            }
+            __syncthreads();
+            if (tid < 7) {
+                double t = 0.0;
+                for (int w8 = 0; w8 < kFusedThreads / 32; ++w8) t += sdiag[w8][tid];
+                P.diag.rows[((size_t)blockIdx.x * PIC_MAXSP + sp) * 8 + tid] = t;
+            }
+            __syncthreads();
+        }
     }
-    cp_async_wait0();
     if (bad) atomicOr(P.err, PIC_EF_NAN);
     __syncthreads();
 

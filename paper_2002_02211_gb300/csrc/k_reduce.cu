@@ -32,10 +32,8 @@ __device__ void block_sum(double (&v)[NV], double *row) {
     }
 }
 
-// kinetic energy (gamma - 1) m c^2 = m c^2 u^2 / (1 + gamma), no cancellation
 __device__ __forceinline__ float ekin(float m_mev, float ux, float uy, float uz) {
-    const float u2 = ux * ux + uy * uy + uz * uz;
-    return m_mev * u2 / (1.f + sqrtf(1.f + u2));
+    return ekin_mev(m_mev, ux, uy, uz);
 }
 
 // pass 1: sum w, sum w s (3), sum w e, count.  Each thread folds float sums of
@@ -191,9 +189,50 @@ __global__ void k_negate(const float *src, float *dst, size_t n) {
         dst[i] = -src[i];
 }
 
+// Fixed-order sum of the per-CTA diagnostic rows [nrows][PIC_MAXSP][8] into
+// the moments of each species; the new mean becomes the next shift.
+__global__ void __launch_bounds__(RT) k_diag_final(const double *rows, int nrows, int nsp, double *shift,
+                                                   pic_moments_dev *out) {
+    __shared__ double s[RT];
+    __shared__ double tot[8];
+    for (int sp = 0; sp < nsp; ++sp) {
+        for (int q = 0; q < 7; ++q) {
+            double a = 0.0;
+            for (int r = threadIdx.x; r < nrows; r += blockDim.x) a += rows[((size_t)r * PIC_MAXSP + sp) * 8 + q];
+            s[threadIdx.x] = a;
+            __syncthreads();
+            for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+                if ((int)threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) tot[q] = s[0];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            const double sw = tot[0], sh = shift[sp];
+            pic_moments_dev m;
+            for (int k = 0; k < 3; ++k) m.P[k] = sw > 0 ? tot[1 + k] / sw : 0.0;
+            const double d = sw > 0 ? tot[4] / sw : 0.0;
+            m.sum_w = sw;
+            m.count = tot[6];
+            m.ekin_mean = sw > 0 ? sh + d : 0.0;
+            m.ekin_var = sw > 0 ? fmax(tot[5] / sw - d * d, 0.0) : 0.0;
+            out[sp] = m;
+            if (sw > 0) shift[sp] = sh + d;
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 int reduce_blocks() { return RB; }
+
+cudaError_t launch_diag_final(const double *rows, int nrows, int nsp, double *shift, pic_moments_dev *out,
+                              cudaStream_t st) {
+    k_diag_final<<<1, RT, 0, st>>>(rows, nrows, nsp, shift, out);
+    return cudaGetLastError();
+}
 
 // result[0..5] = sums of pass 1, result[6] = sum w (e - mean)^2
 cudaError_t launch_moments(const DevSpecies &S, float m_mev, float emin, float emax, double *partials,

@@ -45,6 +45,13 @@ struct Ctx {
     int32_t *scratch_i32 = nullptr;  // 2 * max capacity, for ix / iy transfers
     unsigned *err = nullptr;
     double *partials = nullptr, *result = nullptr;
+    double *laser_prof = nullptr;  // [2][ny] transverse profile at y_j, y_{j+1/2}
+    // in-step Eq. (4) diagnostics
+    int diag_every = 0;
+    float diag_lo[PIC_MAX_SPECIES] = {}, diag_hi[PIC_MAX_SPECIES] = {};
+    double *diag_rows = nullptr, *diag_shift = nullptr;
+    pic_moments_dev *diag_out = nullptr;
+    long long diag_step = -1;
     CUtensorMap tmapEB;
     bool pending_deposit = false;
     long long step = 0;
@@ -308,6 +315,18 @@ pic_status_t pic_create(const pic_config_t *cfg, void *stream, void **ctx_out) {
     CKC(cudaMemsetAsync(c->err, 0, sizeof(unsigned), st));
     CKC(cudaMalloc(&c->partials, (size_t)reduce_blocks() * 8 * sizeof(double)));
     CKC(cudaMalloc(&c->result, 16 * sizeof(double)));
+    CKC(cudaMalloc(&c->diag_rows, (size_t)c->ntiles * PIC_MAX_SPECIES * 8 * sizeof(double)));
+    CKC(cudaMalloc(&c->diag_shift, PIC_MAX_SPECIES * sizeof(double)));
+    CKC(cudaMemsetAsync(c->diag_shift, 0, PIC_MAX_SPECIES * sizeof(double), st));
+    CKC(cudaMalloc(&c->diag_out, PIC_MAX_SPECIES * sizeof(pic_moments_dev)));
+    CKC(cudaMemsetAsync(c->diag_out, 0, PIC_MAX_SPECIES * sizeof(pic_moments_dev), st));
+    {
+        std::vector<double> prof(2 * (size_t)cfg->ny);
+        laser_profile(laser(c), cfg->ny, prof.data());
+        CKC(cudaMalloc(&c->laser_prof, prof.size() * sizeof(double)));
+        CKC(cudaMemcpyAsync(c->laser_prof, prof.data(), prof.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        CKC(cudaStreamSynchronize(st));
+    }
     if (make_tensor_map(c) != PIC_OK) return bail(PIC_ERR_CUDA);
     CKC(cudaStreamSynchronize(st));
 #undef CKC
@@ -340,6 +359,10 @@ void pic_destroy(void *ctx) {
     cudaFree(c->err);
     cudaFree(c->partials);
     cudaFree(c->result);
+    cudaFree(c->diag_rows);
+    cudaFree(c->diag_shift);
+    cudaFree(c->diag_out);
+    cudaFree(c->laser_prof);
     delete c;
 }
 
@@ -532,7 +555,7 @@ pic_status_t pic_field_update(void *ctx, void *stream) {
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
     if (c->pending_deposit) return fail(c, PIC_ERR_STATE, "a move is waiting for pic_deposit");
-    CK(launch_field_update(mesh(c), c->bnd, laser(c), c->dt, c->dx, c->dy, c->step, S(stream)));
+    CK(launch_field_update(mesh(c), c->bnd, c->laser_prof, laser(c), c->dt, c->dx, c->dy, c->step, S(stream)));
     c->launches += c->cfg.bc_x == PIC_BC_OPEN ? 4 : 3;
     c->step += 1;
     return PIC_OK;
@@ -542,9 +565,59 @@ pic_status_t pic_push_deposit(void *ctx, void *stream) {
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
     if (c->pending_deposit) return fail(c, PIC_ERR_STATE, "a move is waiting for pic_deposit");
-    CK(launch_step_fused(step_params(c), c->tmapEB, S(stream)));
+    StepParams P = step_params(c);
+    const bool diag = c->diag_every > 0 && (c->step + 1) % c->diag_every == 0;
+    if (diag) {
+        P.diag.on = 1;
+        for (int s = 0; s < c->cfg.nspecies; ++s) {
+            P.diag.lo[s] = c->diag_lo[s];
+            P.diag.hi[s] = c->diag_hi[s];
+            P.diag.m_mev[s] = (float)(c->cfg.sp[s].m * kMec2Mev);
+        }
+        P.diag.shift = c->diag_shift;
+        P.diag.rows = c->diag_rows;
+    }
+    CK(launch_step_fused(P, c->tmapEB, S(stream)));
     c->launches += 1;
+    if (diag) {
+        CK(launch_diag_final(c->diag_rows, c->ntiles, c->cfg.nspecies, c->diag_shift, c->diag_out, S(stream)));
+        c->launches += 1;
+        c->diag_step = c->step + 1;
+    }
     return PIC_OK;
+}
+
+pic_status_t pic_set_diagnostics(void *ctx, int every, const double *emin_mev, const double *emax_mev) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
+    if (every < 0) return fail(c, PIC_ERR_ARG, "every must be >= 0");
+    for (int s = 0; s < c->cfg.nspecies; ++s) {
+        const double lo = emin_mev ? emin_mev[s] : -INFINITY, hi = emax_mev ? emax_mev[s] : INFINITY;
+        if (!(lo < hi)) return fail(c, PIC_ERR_ARG, "energy window must have emin < emax");
+        c->diag_lo[s] = std::isinf(lo) && lo < 0 ? -INFINITY : (float)lo;
+        c->diag_hi[s] = std::isinf(hi) && hi > 0 ? INFINITY : (float)hi;
+    }
+    c->diag_every = every;
+    return PIC_OK;
+}
+
+pic_status_t pic_get_diagnostics(void *ctx, pic_moments_t *out, int64_t *step, void *stream) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
+    if (!out) return fail(c, PIC_ERR_ARG, "null output");
+    cudaStream_t st = S(stream);
+    pic_moments_dev h[PIC_MAX_SPECIES];
+    CK(cudaMemcpyAsync(h, c->diag_out, sizeof(h), cudaMemcpyDeviceToHost, st));
+    pic_status_t fl = check_flags(c, st);
+    for (int s = 0; s < c->cfg.nspecies; ++s) {
+        for (int k = 0; k < 3; ++k) out[s].P[k] = h[s].P[k];
+        out[s].sum_w = h[s].sum_w;
+        out[s].count = h[s].count;
+        out[s].ekin_mean = h[s].ekin_mean;
+        out[s].ekin_var = h[s].ekin_var;
+    }
+    if (step) *step = c->diag_step;
+    return fl;
 }
 
 pic_status_t pic_sort(void *ctx, void *stream) {

@@ -57,13 +57,32 @@ struct TileGeom {
 __host__ __device__ constexpr int window_wx(int tx) { return (tx + 2 * PIC_HALO + 31) / 32 * 32; }
 __host__ __device__ constexpr int window_wy(int ty) { return ty + 2 * PIC_HALO; }
 
+// Eq. (4) moments accumulated inside the fused kernel on diagnostic steps:
+// per species and CTA the sums w, w s (3), w e', w e'^2, count over live
+// particles with kinetic energy e in [lo, hi), where e' = e - shift and shift
+// is the mean of the previous diagnostic (a one-pass variance that stays
+// well conditioned).
+struct DiagParams {
+    int on;
+    float lo[PIC_MAXSP], hi[PIC_MAXSP], m_mev[PIC_MAXSP];
+    const double *shift;           // [PIC_MAXSP] device
+    double *rows;                  // [gridDim][PIC_MAXSP][8] per-CTA sums
+};
+
 struct StepParams {
     MeshParams m;
     TileGeom t;
     int nsp;
     DevSpecies sp[PIC_MAXSP];
     unsigned *err;
+    DiagParams diag;
 };
+
+// kinetic energy (gamma - 1) m c^2 = m c^2 u^2 / (1 + gamma), no cancellation
+__device__ __forceinline__ float ekin_mev(float m_mev, float ux, float uy, float uz) {
+    const float u2 = ux * ux + uy * uy + uz * uz;
+    return m_mev * u2 / (1.f + sqrtf(1.f + u2));
+}
 
 // ---------------------------------------------------------------------------
 // mesh accessors: a window staged in shared memory (local coordinates) or the

@@ -7,6 +7,12 @@
 
 #include "pic_device.cuh"
 
+// device-side copy of pic_moments_t (same layout: seven doubles)
+struct pic_moments_dev {
+    double P[3];
+    double sum_w, count, ekin_mean, ekin_var;
+};
+
 struct LaserParams {
     int pol;            // 0 none, 1 LP-y, 2 CP
     double a0, w0, tau, t_peak, yc, dy;
@@ -19,8 +25,9 @@ cudaError_t launch_push_split(const StepParams &P, int s, int n_upper, cudaStrea
 cudaError_t launch_deposit_split(const StepParams &P, int s, int n_upper, cudaStream_t st);
 
 // k_fields.cu
-cudaError_t launch_field_update(const MeshParams &m, float *bnd, const LaserParams &L,
+cudaError_t launch_field_update(const MeshParams &m, float *bnd, const double *prof, const LaserParams &L,
                                 double dt, double dx, double dy, long long step, cudaStream_t st);
+void laser_profile(const LaserParams &L, int ny, double *host);
 
 // k_sort.cu
 cudaError_t launch_pack_cells(const int32_t *ix, const int32_t *iy, uint32_t *cell, int n,
@@ -40,6 +47,8 @@ cudaError_t launch_gauss(const MeshParams &m, const float *rho, const float *rho
                          double dy, int i0, int i1, double *partials, double *result,
                          cudaStream_t st);
 cudaError_t launch_negate_copy(const float *src, float *dst, size_t n, cudaStream_t st);
+cudaError_t launch_diag_final(const double *rows, int nrows, int nsp, double *shift, pic_moments_dev *out,
+                              cudaStream_t st);
 
 // pic_api.cu: the message pic_last_error(NULL) returns
 void set_global_error(const std::string &msg);

@@ -115,6 +115,30 @@ def test_polarization_and_energy_moments():
                 assert gm["ekin_var"] == pytest.approx(om[6], rel=1e-4)
 
 
+def test_in_step_diagnostics_match_polarization():
+    # the Eq. (4) moments accumulated inside the fused step against the
+    # two-pass reduction over the same particles
+    wl = W.small_case(nx=64, ny=32, ppc=4, u_th=0.5, two_species=True)
+    f = W.random_fields(wl, seed=12, e_amp=0.2, b_amp=0.8)
+    sim, orc, _ = make_pair(wl, fields=f)
+    windows = [(-math.inf, math.inf), (0.01, math.inf)]
+    for emin, emax in windows:
+        sim.set_diagnostics(1, [emin, emin], [emax, emax])
+        for _ in range(3):          # the variance shift comes from the previous call
+            sim.step(1)
+            step, diag = sim.get_diagnostics()
+            assert step == sim.get_step()
+            for s in range(2):
+                ref = sim.polarization(s, emin, emax)
+                d = diag[s]
+                assert d["count"] == ref["count"]
+                np.testing.assert_allclose(d["P"], ref["P"], atol=1e-6)
+                assert d["sum_w"] == pytest.approx(ref["sum_w"], rel=1e-6)
+                assert d["ekin_mean"] == pytest.approx(ref["ekin_mean"], rel=1e-5)
+                assert d["ekin_var"] == pytest.approx(ref["ekin_var"], rel=1e-3)
+    sim.set_diagnostics(0)
+
+
 def test_polarization_unchanged_without_fields():
     wl = W.small_case(nx=32, ny=16, ppc=2, pol="none", a0=0.0, u_th=0.0, bc_x="periodic")
     sim, orc, _ = make_pair(wl)
