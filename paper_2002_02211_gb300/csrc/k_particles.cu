@@ -83,7 +83,7 @@ __device__ __forceinline__ bool finish_move(const MeshParams &m, int &ix1, int &
 // ---------------------------------------------------------------------------
 constexpr int kFusedThreads = 256;
 #ifndef PIC_FUSED_MINB
-#define PIC_FUSED_MINB 4  // resident CTAs per SM the register budget is sized for
+#define PIC_FUSED_MINB 3  // resident CTAs per SM the register budget is sized for
 #endif
 constexpr int kRec = 10;  // staged words per particle: cell ox oy ux uy uz sx sy sz w
 
@@ -179,6 +179,24 @@ __global__ void __launch_bounds__(kFusedThreads, PIC_FUSED_MINB)
     const int xlo = max(wx0 + 1, 1), xhi = min(wx0 + WX - 3, m.nx - 3);
     const int ylo = max(wy0 + 1, 1), yhi = min(wy0 + WY - 3, m.ny - 3);
     bool bad = false;
+    // In-cell moves (the common case) of consecutive particles of the same
+    // cell are summed in registers and added to the shared window once, at
+    // the next change of cell: with the layered tile order each thread meets
+    // the same cell on every pass through the layers.
+    int acc_key = -1;  // window offset of the accumulated cell
+    float acc[8];
+    auto acc_flush = [&]() {
+        if (acc_key >= 0) {
+            atomicAdd(&sJ[acc_key], acc[0]);
+            atomicAdd(&sJ[acc_key + WX], acc[1]);
+            atomicAdd(&sJ[WA + acc_key], acc[2]);
+            atomicAdd(&sJ[WA + acc_key + 1], acc[3]);
+            atomicAdd(&sJ[2 * WA + acc_key], acc[4]);
+            atomicAdd(&sJ[2 * WA + acc_key + 1], acc[5]);
+            atomicAdd(&sJ[2 * WA + acc_key + WX], acc[6]);
+            atomicAdd(&sJ[2 * WA + acc_key + WX + 1], acc[7]);
+        }
+    };
 
     for (int sp = 0; sp < P.nsp; ++sp) {
         const DevSpecies &S = P.sp[sp];
@@ -222,11 +240,31 @@ __global__ void __launch_bounds__(kFusedThreads, PIC_FUSED_MINB)
                     advance_axis(ix1, ox1, u[0] * gi * m.dt_dx);
                     advance_axis(iy1, oy1, u[1] * gi * m.dt_dy);
                     const float qw = q * w, vz = u[2] * gi;
-                    if (fast)
+                    if (fast && ix1 == ix && iy1 == iy) {
+                        // in-cell Esirkepov weights (see deposit_in_cell), summed per cell
+                        const int key = (iy - wy0) * WX + (ix - wx0);
+                        const float d = ox1 - ox, e = oy1 - oy;
+                        const float xm = ox + 0.5f * d, ym = oy + 0.5f * e;
+                        const float jx = qw * m.dx_dt * d, jy = qw * m.dy_dt * e, cz = qw * vz;
+                        const float de = d * e * (1.f / 12.f);
+                        const float v[8] = {jx * (1.f - ym), jx * ym, jy * (1.f - xm), jy * xm,
+                                            cz * ((1.f - xm) * (1.f - ym) + de), cz * (xm * (1.f - ym) - de),
+                                            cz * ((1.f - xm) * ym - de), cz * (xm * ym + de)};
+                        if (key != acc_key) {
+                            acc_flush();
+                            acc_key = key;
+#pragma unroll
+                            for (int q8 = 0; q8 < 8; ++q8) acc[q8] = v[q8];
+                        } else {
+#pragma unroll
+                            for (int q8 = 0; q8 < 8; ++q8) acc[q8] += v[q8];
+                        }
+                    } else if (fast) {
                         deposit_esirkepov(sm, ix - wx0, iy - wy0, ox, oy, ix1 - wx0, iy1 - wy0, ox1, oy1, qw,
                                           vz, m.dx_dt, m.dy_dt);
-                    else
+                    } else {
                         deposit_esirkepov(gm, ix, iy, ox, oy, ix1, iy1, ox1, oy1, qw, vz, m.dx_dt, m.dy_dt);
+                    }
                     const bool alive = finish_move(m, ix1, iy1);
                     const float chk = u[0] * u[0] + u[1] * u[1] + u[2] * u[2] + spn[0] * spn[0] +
                                       spn[1] * spn[1] + spn[2] * spn[2];
@@ -275,6 +313,7 @@ __global__ void __launch_bounds__(kFusedThreads, PIC_FUSED_MINB)
             __syncthreads();
         }
     }
+    acc_flush();
     if (bad) atomicOr(P.err, PIC_EF_NAN);
     __syncthreads();
 

@@ -41,6 +41,7 @@ struct Ctx {
     uint32_t *cell_old[PIC_MAX_SPECIES] = {};
     float *old_f[PIC_MAX_SPECIES][3] = {};  // ox_old, oy_old, vz
     int32_t *tile_count = nullptr, *tile_cursor = nullptr;
+    int32_t *cell_count = nullptr, *cell_off = nullptr, *tile_R = nullptr;
     int32_t *n_dev = nullptr;  // [PIC_MAX_SPECIES + 1] slot counts; the last entry is sort scratch
     int32_t *scratch_i32 = nullptr;  // 2 * max capacity, for ix / iy transfers
     unsigned *err = nullptr;
@@ -202,9 +203,9 @@ pic_status_t check_flags(Ctx *c, cudaStream_t st) {
 pic_status_t sort_species(Ctx *c, int s, cudaStream_t st) {
     const int from = c->cur[s], to = 1 - from;
     DevSpecies src = dev_species(c, s, from), dst = dev_species(c, s, to);
-    CK(launch_tile_sort(src, dst, c->tg, c->tile_count, c->tile_cursor, c->tile_start[s],
-                        c->n_dev + PIC_MAX_SPECIES, c->n_upper[s], st));
-    c->launches += 3;
+    SortScratch w{c->cell_count, c->cell_off, c->tile_R, c->tile_count, c->tile_cursor, c->scratch_i32};
+    CK(launch_tile_sort(src, dst, c->tg, w, c->tile_start[s], c->n_dev + PIC_MAX_SPECIES, c->n_upper[s], st));
+    c->launches += 4;
     c->cur[s] = to;
     return PIC_OK;
 }
@@ -307,6 +308,9 @@ pic_status_t pic_create(const pic_config_t *cfg, void *stream, void **ctx_out) {
         CKC(cudaMemsetAsync(c->tile_start[s], 0, (c->ntiles + 1) * sizeof(int32_t), st));
     }
     CKC(cudaMalloc(&c->tile_count, c->ntiles * sizeof(int32_t)));
+    CKC(cudaMalloc(&c->cell_count, (size_t)c->ntiles * c->tg.TX * c->tg.TY * sizeof(int32_t)));
+    CKC(cudaMalloc(&c->cell_off, (size_t)c->ntiles * c->tg.TX * c->tg.TY * sizeof(int32_t)));
+    CKC(cudaMalloc(&c->tile_R, c->ntiles * sizeof(int32_t)));
     CKC(cudaMalloc(&c->tile_cursor, c->ntiles * sizeof(int32_t)));
     CKC(cudaMalloc(&c->n_dev, (PIC_MAX_SPECIES + 1) * sizeof(int32_t)));
     CKC(cudaMemsetAsync(c->n_dev, 0, (PIC_MAX_SPECIES + 1) * sizeof(int32_t), st));
@@ -353,6 +357,9 @@ void pic_destroy(void *ctx) {
         for (int k = 0; k < 3; ++k) cudaFree(c->old_f[s][k]);
     }
     cudaFree(c->tile_count);
+    cudaFree(c->cell_count);
+    cudaFree(c->cell_off);
+    cudaFree(c->tile_R);
     cudaFree(c->tile_cursor);
     cudaFree(c->n_dev);
     cudaFree(c->scratch_i32);

@@ -34,9 +34,15 @@ cudaError_t launch_pack_cells(const int32_t *ix, const int32_t *iy, uint32_t *ce
                               int xlo, int xhi, int ny, unsigned *err, cudaStream_t st);
 cudaError_t launch_unpack_cells(const uint32_t *cell, int32_t *ix, int32_t *iy, int n,
                                 cudaStream_t st);
+struct SortScratch {
+    int32_t *cell_count, *cell_off;  // [ntiles * TX * TY]
+    int32_t *tile_R, *tile_total;    // [ntiles]
+    int32_t *cursor;                 // [ntiles]
+    int32_t *rank;                   // [n]
+};
 cudaError_t launch_tile_sort(const DevSpecies &src, const DevSpecies &dst, const TileGeom &t,
-                             int32_t *count, int32_t *cursor, int32_t *tile_start,
-                             int32_t *n_tmp, int n_upper, cudaStream_t st);
+                             const SortScratch &w, int32_t *tile_start, int32_t *n_tmp, int n_upper,
+                             cudaStream_t st);
 
 // k_reduce.cu
 int reduce_blocks();
