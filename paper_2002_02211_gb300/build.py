@@ -67,7 +67,9 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if errors:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
     tmp = LIB + f".{os.getpid()}.tmp"
-    subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
+    # --no-undefined: a missing definition fails here, not at dlopen on the GPU machine
+    subprocess.check_call([nvcc, *ARCH, "-shared", "-Xlinker", "--no-undefined", "-o", tmp, *objs,
+                           "-lpthread", "-ldl", "-lrt"])
     os.replace(tmp, LIB)
     return LIB
 

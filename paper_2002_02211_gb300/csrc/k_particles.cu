@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(kFusedThreads, PIC_FUSED_MINB)
     // the next change of cell: with the layered tile order each thread meets
     // the same cell on every pass through the layers.
     int acc_key = -1;  // window offset of the accumulated cell
-    float acc[8];
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     auto acc_flush = [&]() {
         if (acc_key >= 0) {
             atomicAdd(&sJ[acc_key], acc[0]);
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(kFusedThreads, PIC_FUSED_MINB)
             if (tid < 7) {
                 double t = 0.0;
                 for (int w8 = 0; w8 < kFusedThreads / 32; ++w8) t += sdiag[w8][tid];
-                P.diag.rows[((size_t)blockIdx.x * PIC_MAXSP + sp) * 8 + tid] = t;
+                P.diag.rows[((size_t)sp * 8 + tid) * gridDim.x + blockIdx.x] = t;
             }
             __syncthreads();
         }

@@ -189,39 +189,37 @@ __global__ void k_negate(const float *src, float *dst, size_t n) {
         dst[i] = -src[i];
 }
 
-// Fixed-order sum of the per-CTA diagnostic rows [nrows][PIC_MAXSP][8] into
-// the moments of each species; the new mean becomes the next shift.
-__global__ void __launch_bounds__(RT) k_diag_final(const double *rows, int nrows, int nsp, double *shift,
-                                                   pic_moments_dev *out) {
+// Fixed-order sum of each column of the per-CTA diagnostic sums
+// [PIC_MAXSP][8][nrows]: one block per (species, quantity) column.
+__global__ void __launch_bounds__(RT) k_diag_cols(const double *rows, int nrows, double *tot) {
     __shared__ double s[RT];
-    __shared__ double tot[8];
-    for (int sp = 0; sp < nsp; ++sp) {
-        for (int q = 0; q < 7; ++q) {
-            double a = 0.0;
-            for (int r = threadIdx.x; r < nrows; r += blockDim.x) a += rows[((size_t)r * PIC_MAXSP + sp) * 8 + q];
-            s[threadIdx.x] = a;
-            __syncthreads();
-            for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-                if ((int)threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
-                __syncthreads();
-            }
-            if (threadIdx.x == 0) tot[q] = s[0];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            const double sw = tot[0], sh = shift[sp];
-            pic_moments_dev m;
-            for (int k = 0; k < 3; ++k) m.P[k] = sw > 0 ? tot[1 + k] / sw : 0.0;
-            const double d = sw > 0 ? tot[4] / sw : 0.0;
-            m.sum_w = sw;
-            m.count = tot[6];
-            m.ekin_mean = sw > 0 ? sh + d : 0.0;
-            m.ekin_var = sw > 0 ? fmax(tot[5] / sw - d * d, 0.0) : 0.0;
-            out[sp] = m;
-            if (sw > 0) shift[sp] = sh + d;
-        }
+    const double *col = rows + (size_t)blockIdx.x * nrows;
+    double a = 0.0;
+    for (int r = threadIdx.x; r < nrows; r += blockDim.x) a += col[r];
+    s[threadIdx.x] = a;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
         __syncthreads();
     }
+    if (threadIdx.x == 0) tot[blockIdx.x] = s[0];
+}
+
+// moments of each species from the column sums; the new mean becomes the next shift
+__global__ void k_diag_moments(const double *tot, int nsp, double *shift, pic_moments_dev *out) {
+    const int sp = threadIdx.x;
+    if (sp >= nsp) return;
+    const double *t = tot + sp * 8;
+    const double sw = t[0], sh = shift[sp];
+    pic_moments_dev m;
+    for (int k = 0; k < 3; ++k) m.P[k] = sw > 0 ? t[1 + k] / sw : 0.0;
+    const double d = sw > 0 ? t[4] / sw : 0.0;
+    m.sum_w = sw;
+    m.count = t[6];
+    m.ekin_mean = sw > 0 ? sh + d : 0.0;
+    m.ekin_var = sw > 0 ? fmax(t[5] / sw - d * d, 0.0) : 0.0;
+    out[sp] = m;
+    if (sw > 0) shift[sp] = sh + d;
 }
 
 }  // namespace
@@ -229,10 +227,12 @@ __global__ void __launch_bounds__(RT) k_diag_final(const double *rows, int nrows
 int reduce_blocks() { return RB; }
 
 cudaError_t launch_diag_final(const double *rows, int nrows, int nsp, double *shift, pic_moments_dev *out,
-                              cudaStream_t st) {
-    k_diag_final<<<1, RT, 0, st>>>(rows, nrows, nsp, shift, out);
+                              double *tot, cudaStream_t st) {
+    k_diag_cols<<<nsp * 8, RT, 0, st>>>(rows, nrows, tot);
+    k_diag_moments<<<1, 32, 0, st>>>(tot, nsp, shift, out);
     return cudaGetLastError();
 }
+
 
 // result[0..5] = sums of pass 1, result[6] = sum w (e - mean)^2
 cudaError_t launch_moments(const DevSpecies &S, float m_mev, float emin, float emax, double *partials,

@@ -153,7 +153,7 @@ void choose_tiles(Ctx *c) {
     int tx = c->cfg.tile_x, ty = c->cfg.tile_y;
     if (tx <= 0 || ty <= 0) {
         const long long cells = (long long)c->cfg.nx * c->cfg.ny;
-        tx = cells >= (1LL << 21) ? 32 : 16;
+        tx = cells >= (1LL << 19) ? 32 : 16;
         ty = 8;
     }
     // tile shapes the fused kernel is compiled for (pic_validate_config checks)
@@ -318,7 +318,7 @@ pic_status_t pic_create(const pic_config_t *cfg, void *stream, void **ctx_out) {
     CKC(cudaMalloc(&c->err, sizeof(unsigned)));
     CKC(cudaMemsetAsync(c->err, 0, sizeof(unsigned), st));
     CKC(cudaMalloc(&c->partials, (size_t)reduce_blocks() * 8 * sizeof(double)));
-    CKC(cudaMalloc(&c->result, 16 * sizeof(double)));
+    CKC(cudaMalloc(&c->result, 64 * sizeof(double)));  // moments results and diagnostic column sums
     CKC(cudaMalloc(&c->diag_rows, (size_t)c->ntiles * PIC_MAX_SPECIES * 8 * sizeof(double)));
     CKC(cudaMalloc(&c->diag_shift, PIC_MAX_SPECIES * sizeof(double)));
     CKC(cudaMemsetAsync(c->diag_shift, 0, PIC_MAX_SPECIES * sizeof(double), st));
@@ -587,8 +587,9 @@ pic_status_t pic_push_deposit(void *ctx, void *stream) {
     CK(launch_step_fused(P, c->tmapEB, S(stream)));
     c->launches += 1;
     if (diag) {
-        CK(launch_diag_final(c->diag_rows, c->ntiles, c->cfg.nspecies, c->diag_shift, c->diag_out, S(stream)));
-        c->launches += 1;
+        CK(launch_diag_final(c->diag_rows, c->ntiles, c->cfg.nspecies, c->diag_shift, c->diag_out, c->result,
+                             S(stream)));
+        c->launches += 2;
         c->diag_step = c->step + 1;
     }
     return PIC_OK;

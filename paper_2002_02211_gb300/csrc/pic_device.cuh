@@ -66,7 +66,7 @@ struct DiagParams {
     int on;
     float lo[PIC_MAXSP], hi[PIC_MAXSP], m_mev[PIC_MAXSP];
     const double *shift;           // [PIC_MAXSP] device
-    double *rows;                  // [gridDim][PIC_MAXSP][8] per-CTA sums
+    double *rows;                  // [PIC_MAXSP][8][gridDim] per-CTA sums (columns contiguous)
 };
 
 struct StepParams {

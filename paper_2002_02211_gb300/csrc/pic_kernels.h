@@ -54,7 +54,7 @@ cudaError_t launch_gauss(const MeshParams &m, const float *rho, const float *rho
                          cudaStream_t st);
 cudaError_t launch_negate_copy(const float *src, float *dst, size_t n, cudaStream_t st);
 cudaError_t launch_diag_final(const double *rows, int nrows, int nsp, double *shift, pic_moments_dev *out,
-                              cudaStream_t st);
+                              double *tot, cudaStream_t st);
 
 // pic_api.cu: the message pic_last_error(NULL) returns
 void set_global_error(const std::string &msg);
