@@ -56,6 +56,7 @@ def parse(argv=None):
     ap.add_argument("--diag-every", type=int, default=10)
     ap.add_argument("--tile", type=int, nargs=2, default=(0, 0))
     ap.add_argument("--ny", type=int, default=0, help="smaller ny for profiling captures")
+    ap.add_argument("--precision", type=int, choices=[32, 64], default=32)
     ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -253,7 +254,8 @@ def main_ours(args):
     n_cells = wl.nx * wl.ny
 
     stream = torch.cuda.Stream(device=dev)
-    cfg = pic.config_from_workload(wl, sort_every=args.sort_every, tile=tuple(args.tile))
+    cfg = pic.config_from_workload(wl, sort_every=args.sort_every, tile=tuple(args.tile),
+                                   precision=args.precision)
     sim = pic.Simulation(cfg, stream=stream)
     for s, d in enumerate(parts):
         sim.set_particles(s, d)
@@ -309,7 +311,8 @@ def main_ours(args):
     value = units / tmax
 
     peak, peak_kind = measured_hbm_peak()
-    bytes_fused = BYTES_PER_PARTICLE * n_particles + BYTES_PER_CELL * n_cells
+    wb = args.precision // 32  # algorithmic bytes scale with the real width (the cell word stays 4 B)
+    bytes_fused = (4 + (BYTES_PER_PARTICLE - 4) * wb) * n_particles + BYTES_PER_CELL * wb * n_cells
     achieved = bytes_fused / t_fused / 1e9
     tr = traffic_record()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -359,7 +362,8 @@ def main_ours(args):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": tmax * 1e3 / args.steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if args.precision == 32 else "f64",
                 "data": "synthetic",
                 "config": {"workload": wl.name, "cells": [wl.nx, wl.ny], "particles": n_particles,
                            "species": [s.name for s in wl.species], "sort_every": args.sort_every,

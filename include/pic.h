@@ -87,6 +87,10 @@ typedef struct {
     int sort_every;              /* steps between tile sorts in pic_step (0: 32)   */
     int tile_x, tile_y;          /* cells per tile: 8x4, 16x8, 32x8, 32x16 or 64x16 (0, 0: chosen
                                     from the mesh size)                            */
+    int precision;               /* arithmetic of particles and mesh: 32 (the
+                                    production path) or 64 (the FP64 instantiation
+                                    of the same kernels); 0 means 32.  Reductions
+                                    are FP64 in both.                              */
 } pic_config_t;
 
 /* Host-side particle arrays of one species (n entries each).  ix, iy are cell
@@ -101,12 +105,28 @@ typedef struct {
     int32_t *id;          /* caller's particle identity, carried through sorts */
 } pic_particles_t;
 
+/* The same with float64 arrays (read-back of either precision at full width). */
+typedef struct {
+    int64_t n;
+    int32_t *ix, *iy;
+    double *ox, *oy;
+    double *ux, *uy, *uz;
+    double *sx, *sy, *sz;
+    double *w;
+    int32_t *id;
+} pic_particles_f64_t;
+
 /* Host-side mesh arrays, [ny][nx] float32 each (by_left, bz_left: [ny]).
  * A NULL member is skipped by pic_set_fields / pic_get_fields. */
 typedef struct {
     float *ex, *ey, *ez, *bx, *by, *bz, *jx, *jy, *jz;
     float *by_left, *bz_left;
 } pic_fields_t;
+
+typedef struct {
+    double *ex, *ey, *ez, *bx, *by, *bz, *jx, *jy, *jz;
+    double *by_left, *bz_left;
+} pic_fields_f64_t;
 
 /* Moments of Eq. (4) over the live particles of one species whose kinetic
  * energy (gamma - 1) m c^2 lies in [emin, emax) MeV, accumulated in FP64. */
@@ -131,8 +151,8 @@ void pic_destroy(void *ctx);
 /* Time step dt [1/omega0] and cell sizes dx, dy [c/omega0] the context derived. */
 pic_status_t pic_get_grid(void *ctx, double *dt, double *dx, double *dy);
 
-/* Loads the particles of one species from host arrays (replacing what was
- * there) and sorts them by tile.  n <= capacity (else PIC_ERR_OVERFLOW).
+/* Loads the particles of one species from host float32 arrays (widened
+ * exactly with precision 64; replacing what was there) and sorts them by tile.  n <= capacity (else PIC_ERR_OVERFLOW).
  * Cells must lie in the particle region (else PIC_ERR_ARG).  Synchronous. */
 pic_status_t pic_set_particles(void *ctx, int species, const pic_particles_t *p, void *stream);
 
@@ -142,12 +162,17 @@ pic_status_t pic_get_count(void *ctx, int species, int64_t *n);
 
 /* Copies every slot into caller arrays with room for out->n entries (set
  * out->n to that room; PIC_ERR_ARG if the slots do not fit); on return out->n
- * is the slot count.  A removed particle has ix = iy = -1.  Synchronous. */
+ * is the slot count.  A removed particle has ix = iy = -1.  Synchronous.
+ * With precision 64 the values are rounded to float32; pic_get_particles_f64
+ * returns them at full width (and widens float32 state exactly). */
 pic_status_t pic_get_particles(void *ctx, int species, pic_particles_t *out, void *stream);
+pic_status_t pic_get_particles_f64(void *ctx, int species, pic_particles_f64_t *out, void *stream);
 
-/* Mesh arrays host <-> device.  Synchronous. */
+/* Mesh arrays host <-> device (float32 host arrays for either precision;
+ * pic_get_fields_f64 reads back at full width).  Synchronous. */
 pic_status_t pic_set_fields(void *ctx, const pic_fields_t *f, void *stream);
 pic_status_t pic_get_fields(void *ctx, pic_fields_t *f, void *stream);
+pic_status_t pic_get_fields_f64(void *ctx, pic_fields_f64_t *f, void *stream);
 
 /* Step index n (the fields are at t = n dt; the laser phase follows it). */
 pic_status_t pic_set_step(void *ctx, int64_t step);
@@ -217,8 +242,9 @@ pic_status_t pic_sync(void *ctx, void *stream);
 /* Number of CUDA kernels this context has launched so far (host counter). */
 pic_status_t pic_launch_count(void *ctx, int64_t *count);
 
-/* Eq. (4) moments, as pic_polarization computes them, of n particles held in
- * caller-owned device arrays (the layout of the library's own buffers: cell
+/* Eq. (4) moments, as pic_polarization computes them for precision 32, of n
+ * particles held in caller-owned device arrays (the layout of the library's
+ * own float32 buffers: cell
  * words with 0xFFFFFFFF marking a removed particle, float32 u, s and w), for
  * a species of mass mass_me [m_e] and the kinetic-energy window [emin, emax)
  * MeV.  The result is written to the caller's device memory *out_dev.

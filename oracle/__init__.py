@@ -209,8 +209,9 @@ class OracleSim:
             self.f[k][...] = 0.0
 
     def field_update(self):
-        """a6 at the current step index (does not advance it)."""
+        """a6 at the current step index, which then advances by one."""
         lib().or_field_update(C.byref(self.grid), C.byref(self._fields()), self.step_index)
+        self.step_index += 1
 
     def step(self, nsteps=1):
         """Whole steps: zero J, push and deposit every mobile species, a6."""

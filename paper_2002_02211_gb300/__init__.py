@@ -47,7 +47,7 @@ class pic_config_t(C.Structure):
                 ("waist_lambda", C.c_double), ("fwhm_periods", C.c_double),
                 ("t_peak_periods", C.c_double), ("nspecies", C.c_int),
                 ("sp", pic_species_t * MAX_SPECIES), ("sort_every", C.c_int), ("tile_x", C.c_int),
-                ("tile_y", C.c_int)]
+                ("tile_y", C.c_int), ("precision", C.c_int)]
 
 
 _I32P = C.POINTER(C.c_int32)
@@ -58,6 +58,19 @@ class pic_particles_t(C.Structure):
     _fields_ = [("n", C.c_int64), ("ix", _I32P), ("iy", _I32P), ("ox", _F32P), ("oy", _F32P),
                 ("ux", _F32P), ("uy", _F32P), ("uz", _F32P), ("sx", _F32P), ("sy", _F32P),
                 ("sz", _F32P), ("w", _F32P), ("id", _I32P)]
+
+
+_F64P = C.POINTER(C.c_double)
+
+
+class pic_particles_f64_t(C.Structure):
+    _fields_ = [("n", C.c_int64), ("ix", _I32P), ("iy", _I32P)] + \
+        [(k, _F64P) for k in ("ox", "oy", "ux", "uy", "uz", "sx", "sy", "sz", "w")] + [("id", _I32P)]
+
+
+class pic_fields_f64_t(C.Structure):
+    _fields_ = [(k, _F64P) for k in ("ex", "ey", "ez", "bx", "by", "bz", "jx", "jy", "jz",
+                                     "by_left", "bz_left")]
 
 
 class pic_fields_t(C.Structure):
@@ -79,6 +92,8 @@ _SIGS = {
     "pic_set_particles": [C.c_void_p, C.c_int, C.POINTER(pic_particles_t), C.c_void_p],
     "pic_get_count": [C.c_void_p, C.c_int, C.POINTER(C.c_int64)],
     "pic_get_particles": [C.c_void_p, C.c_int, C.POINTER(pic_particles_t), C.c_void_p],
+    "pic_get_particles_f64": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
+    "pic_get_fields_f64": [C.c_void_p, C.c_void_p, C.c_void_p],
     "pic_set_fields": [C.c_void_p, C.POINTER(pic_fields_t), C.c_void_p],
     "pic_get_fields": [C.c_void_p, C.POINTER(pic_fields_t), C.c_void_p],
     "pic_set_step": [C.c_void_p, C.c_int64],
@@ -143,7 +158,8 @@ def moments_noalloc(n, cell, ux, uy, uz, sx, sy, sz, w, mass_me, emin, emax, out
                                       C.c_void_p(int(out_dev)), _stream(stream)))
 
 
-def config_from_workload(wl, capacity_factor: float = 1.0, sort_every: int = 0, tile=(0, 0)):
+def config_from_workload(wl, capacity_factor: float = 1.0, sort_every: int = 0, tile=(0, 0),
+                         precision: int = 32):
     """pic_config_t for a workload description (nx, ny, dx_lambda, ..., species)."""
     cfg = pic_config_t()
     cfg.nx, cfg.ny = wl.nx, wl.ny
@@ -163,6 +179,7 @@ def config_from_workload(wl, capacity_factor: float = 1.0, sort_every: int = 0, 
         cfg.sp[s].capacity = int(math.ceil(sp.ppc * ncx * wl.ny * capacity_factor))
     cfg.sort_every = sort_every
     cfg.tile_x, cfg.tile_y = tile
+    cfg.precision = precision
     return cfg
 
 
@@ -243,6 +260,23 @@ class Simulation:
         p = pic_particles_t(n=n, **{k: _ptr(v, _I32P if v.dtype == np.int32 else _F32P)
                                     for k, v in out.items()})
         self._c(load().pic_get_particles(self.h, s, C.byref(p), self._s))
+        return out
+
+    def get_particles_f64(self, s):
+        n = self.count(s)
+        out = {k: np.empty(n, np.int32 if k in ("ix", "iy", "id") else np.float64)
+               for k in ("ix", "iy", "ox", "oy", "ux", "uy", "uz", "sx", "sy", "sz", "w", "id")}
+        p = pic_particles_f64_t(n=n, **{k: _ptr(v, _I32P if v.dtype == np.int32 else _F64P)
+                                        for k, v in out.items()})
+        self._c(load().pic_get_particles_f64(self.h, s, C.byref(p), self._s))
+        return out
+
+    def get_fields_f64(self):
+        out = {k: np.empty((self.ny, self.nx), np.float64) for k in self.FIELD_KEYS}
+        out["by_left"] = np.empty(self.ny, np.float64)
+        out["bz_left"] = np.empty(self.ny, np.float64)
+        pf = pic_fields_f64_t(**{k: _ptr(v, _F64P) for k, v in out.items()})
+        self._c(load().pic_get_fields_f64(self.h, C.byref(pf), self._s))
         return out
 
     def set_fields(self, f):

@@ -9,15 +9,16 @@ namespace {
 
 // B <- B - h curl E.  Bx on every column; By, Bz on the columns whose x+1
 // neighbour exists (all of them when x is periodic).
-__global__ void __launch_bounds__(256) k_b_half(const MeshParams m, float hdx, float hdy) {
+template <typename R>
+__global__ void __launch_bounds__(256) k_b_half(const MeshParams<R> m, R hdx, R hdy) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
     if (i >= m.nx) return;
     const int jp = j + 1 == m.ny ? 0 : j + 1;
     const size_t P = m.plane;
-    float *EB = m.EB;
+    R *EB = m.EB;
     const size_t c = (size_t)j * m.ld + i, cjp = (size_t)jp * m.ld + i;
-    const float ez = EB[2 * P + c];
+    const R ez = EB[2 * P + c];
     EB[3 * P + c] -= hdy * (EB[2 * P + cjp] - ez);
     const bool periodic = m.bc_x == 1;
     if (i < m.nx - 1 || periodic) {
@@ -35,15 +36,16 @@ __global__ void __launch_bounds__(256) k_b_half(const MeshParams m, float hdx, f
 //   Bz(-1/2) = (4 g - 2 Ey(0) - (1-r) Bz(1/2)) / (1+r)
 //   By(nx-1/2) = (-2 Ez(nx-1) - (1-r) By(nx-3/2) + q dBx(nx-1)) / (1+r)
 //   Bz(nx-1/2) = (2 Ey(nx-1) - (1-r) Bz(nx-3/2)) / (1+r)
-__global__ void k_boundary(const MeshParams m, float *bnd, const double *prof, double fz, double fy,
-                           double r, double q) {
+template <typename R>
+__global__ void k_boundary(const MeshParams<R> m, R *bnd, const double *prof, double fz, double fy, double r,
+                           double q) {
     // incident Ez (f) and Ey (g) at t^{n+1/2}: the time factor fz, fy (envelope x
     // carrier, one number per step) times the transverse profile prof[j] at y_j
     // and prof[ny + j] at y_{j+1/2}
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= m.ny) return;
     const size_t P = m.plane;
-    float *EB = m.EB;
+    R *EB = m.EB;
     const size_t c0 = (size_t)j * m.ld, cl = c0 + m.nx - 1;
     const size_t cm = (size_t)(j == 0 ? m.ny - 1 : j - 1) * m.ld;
     const double f = fz * prof[j];
@@ -51,24 +53,24 @@ __global__ void k_boundary(const MeshParams m, float *bnd, const double *prof, d
     const double ir = 1.0 / (1.0 + r), mr = 1.0 - r;
     const double dbx0 = (double)EB[3 * P + c0] - (double)EB[3 * P + cm];
     const double dbxl = (double)EB[3 * P + cl] - (double)EB[3 * P + cm + m.nx - 1];
-    bnd[j] = (float)((2.0 * EB[2 * P + c0] - mr * EB[4 * P + c0] - q * dbx0 - 4.0 * f) * ir);
-    bnd[m.ny + j] = (float)((4.0 * g - 2.0 * EB[1 * P + c0] - mr * EB[5 * P + c0]) * ir);
-    EB[4 * P + cl] = (float)((-2.0 * EB[2 * P + cl] - mr * EB[4 * P + cl - 1] + q * dbxl) * ir);
-    EB[5 * P + cl] = (float)((2.0 * EB[1 * P + cl] - mr * EB[5 * P + cl - 1]) * ir);
+    bnd[j] = (R)((2.0 * EB[2 * P + c0] - mr * EB[4 * P + c0] - q * dbx0 - 4.0 * f) * ir);
+    bnd[m.ny + j] = (R)((4.0 * g - 2.0 * EB[1 * P + c0] - mr * EB[5 * P + c0]) * ir);
+    EB[4 * P + cl] = (R)((-2.0 * EB[2 * P + cl] - mr * EB[4 * P + cl - 1] + q * dbxl) * ir);
+    EB[5 * P + cl] = (R)((2.0 * EB[1 * P + cl] - mr * EB[5 * P + cl - 1]) * ir);
 }
 
 // E <- E + dt (curl B - J), then J <- 0
-__global__ void __launch_bounds__(256) k_e_full(const MeshParams m, const float *bnd, float dt,
-                                                float dtdx, float dtdy) {
+template <typename R>
+__global__ void __launch_bounds__(256) k_e_full(const MeshParams<R> m, const R *bnd, R dt, R dtdx, R dtdy) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
     if (i >= m.nx) return;
     const int jm = j == 0 ? m.ny - 1 : j - 1;
     const size_t P = m.plane;
-    float *EB = m.EB;
-    float *J = m.J;
+    R *EB = m.EB;
+    R *J = m.J;
     const size_t c = (size_t)j * m.ld + i, cjm = (size_t)jm * m.ld + i;
-    float by_im, bz_im;
+    R by_im, bz_im;
     if (i > 0) {
         by_im = EB[4 * P + c - 1];
         bz_im = EB[5 * P + c - 1];
@@ -79,13 +81,13 @@ __global__ void __launch_bounds__(256) k_e_full(const MeshParams m, const float 
         by_im = bnd[j];
         bz_im = bnd[m.ny + j];
     }
-    const float bx = EB[3 * P + c], by = EB[4 * P + c], bz = EB[5 * P + c];
+    const R bx = EB[3 * P + c], by = EB[4 * P + c], bz = EB[5 * P + c];
     EB[0 * P + c] += dtdy * (bz - EB[5 * P + cjm]) - dt * J[0 * P + c];
     EB[1 * P + c] += -dtdx * (bz - bz_im) - dt * J[1 * P + c];
     EB[2 * P + c] += dtdx * (by - by_im) - dtdy * (bx - EB[3 * P + cjm]) - dt * J[2 * P + c];
-    J[0 * P + c] = 0.f;
-    J[1 * P + c] = 0.f;
-    J[2 * P + c] = 0.f;
+    J[0 * P + c] = R(0);
+    J[1 * P + c] = R(0);
+    J[2 * P + c] = R(0);
 }
 
 }  // namespace
@@ -105,20 +107,28 @@ static void laser_time_factors(const LaserParams &L, double t, double *fz, doubl
     }
 }
 
-cudaError_t launch_field_update(const MeshParams &m, float *bnd, const double *prof, const LaserParams &L,
+template <typename R>
+cudaError_t launch_field_update(const MeshParams<R> &m, R *bnd, const double *prof, const LaserParams &L,
                                 double dt, double dx, double dy, long long step, cudaStream_t st) {
     const dim3 blk(256), grd((m.nx + 255) / 256, m.ny);
-    const float hdx = (float)(0.5 * dt / dx), hdy = (float)(0.5 * dt / dy);
-    k_b_half<<<grd, blk, 0, st>>>(m, hdx, hdy);
+    const R hdx = (R)(0.5 * dt / dx), hdy = (R)(0.5 * dt / dy);
+    k_b_half<R><<<grd, blk, 0, st>>>(m, hdx, hdy);
     if (m.bc_x == 0) {
         double fz, fy;
         laser_time_factors(L, ((double)step + 0.5) * dt, &fz, &fy);
-        k_boundary<<<(m.ny + 127) / 128, 128, 0, st>>>(m, bnd, prof, fz, fy, dt / dx, dt / dy);
+        k_boundary<R><<<(m.ny + 127) / 128, 128, 0, st>>>(m, bnd, prof, fz, fy, dt / dx, dt / dy);
     }
-    k_e_full<<<grd, blk, 0, st>>>(m, bnd, (float)dt, (float)(dt / dx), (float)(dt / dy));
-    k_b_half<<<grd, blk, 0, st>>>(m, hdx, hdy);
+    k_e_full<R><<<grd, blk, 0, st>>>(m, bnd, (R)dt, (R)(dt / dx), (R)(dt / dy));
+    k_b_half<R><<<grd, blk, 0, st>>>(m, hdx, hdy);
     return cudaGetLastError();
 }
+
+template cudaError_t launch_field_update<float>(const MeshParams<float> &, float *, const double *,
+                                                const LaserParams &, double, double, double, long long,
+                                                cudaStream_t);
+template cudaError_t launch_field_update<double>(const MeshParams<double> &, double *, const double *,
+                                                 const LaserParams &, double, double, double, long long,
+                                                 cudaStream_t);
 
 // transverse laser profile exp(-((y - yc)/w0)^2) at y_j (first ny) and y_{j+1/2}
 void laser_profile(const LaserParams &L, int ny, double *host) {

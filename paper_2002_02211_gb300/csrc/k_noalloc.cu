@@ -96,7 +96,7 @@ extern "C" pic_status_t pic_moments_noalloc(int64_t n, const uint32_t *cell, con
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     int32_t *count = reinterpret_cast<int32_t *>(scratch + kCount);
     k_store_count<<<1, 1, 0, st>>>(count, (int32_t)n);
-    DevSpecies d{};
+    DevSpecies<float> d{};
     d.cell = const_cast<uint32_t *>(cell);
     d.ux = const_cast<float *>(ux);
     d.uy = const_cast<float *>(uy);
@@ -108,7 +108,7 @@ extern "C" pic_status_t pic_moments_noalloc(int64_t n, const uint32_t *cell, con
     d.n = count;
     const float lo = std::isinf(emin_mev) && emin_mev < 0 ? -INFINITY : (float)emin_mev;
     const float hi = std::isinf(emax_mev) && emax_mev > 0 ? INFINITY : (float)emax_mev;
-    e = launch_moments(d, (float)(mass_me * 0.51099895), lo, hi, scratch, scratch + kResult, st);
+    e = launch_moments<float>(d, (float)(mass_me * 0.51099895), lo, hi, scratch, scratch + kResult, st);
     if (e == cudaSuccess) {
         k_moments_out<<<1, 1, 0, st>>>(scratch + kResult, out_dev);
         e = cudaGetLastError();

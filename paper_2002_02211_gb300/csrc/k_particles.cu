@@ -53,7 +53,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned phase)
 }
 
 // a4 and the boundary rule shared by both paths; returns false if removed
-__device__ __forceinline__ bool finish_move(const MeshParams &m, int &ix1, int &iy1) {
+template <typename R>
+__device__ __forceinline__ bool finish_move(const MeshParams<R> &m, int &ix1, int &iy1) {
     bool alive = true;
     if (m.bc_x == 0) {
         alive = ix1 >= 2 && ix1 <= m.nx - 3;
@@ -79,46 +80,76 @@ __device__ __forceinline__ bool finish_move(const MeshParams &m, int &ix1, int &
 // the next one in flight.  Each record runs a1-a5, gathering from and
 // depositing into shared memory when the particle's 4x4 stencil lies inside
 // the window and the mesh (no wrap), otherwise through global memory.  The
-// current window is finally added to J with 16-byte vector atomics.
+// current window is finally added to J with 16-byte vector atomics (float)
+// or scalar atomics (double).
 // ---------------------------------------------------------------------------
 constexpr int kFusedThreads = 256;
 #ifndef PIC_FUSED_MINB
 #define PIC_FUSED_MINB 3  // resident CTAs per SM the register budget is sized for
 #endif
-constexpr int kRec = 10;  // staged words per particle: cell ox oy ux uy uz sx sy sz w
+constexpr int kRec = 9;  // staged reals per particle: ox oy ux uy uz sx sy sz w (plus the cell word)
 
-template <int TX, int TY>
+template <int TX, int TY, typename R>
 struct TileConst {
-    static constexpr int WX = window_wx(TX), WY = window_wy(TY), WA = WX * WY;
-    static constexpr size_t smem_bytes = (size_t)(9 * WA + 2 * kRec * kFusedThreads) * sizeof(float);
+    static constexpr int WX = window_wx<R>(TX), WY = window_wy(TY), WA = WX * WY;
+    // field window, current window, and a two-stage ring of cell words and reals
+    static constexpr size_t smem_bytes =
+        (size_t)9 * WA * sizeof(R) + 2 * kFusedThreads * (sizeof(uint32_t) + kRec * sizeof(R));
 };
 
-template <int WX, int WA>
+template <typename R, int WX, int WA>
 struct SmemMeshT {
-    const float *F;
-    float *Jw;
-    __device__ __forceinline__ float f(int c, int x, int y) const { return F[c * WA + y * WX + x]; }
-    __device__ __forceinline__ void j(int c, int x, int y, float v) const { atomicAdd(&Jw[c * WA + y * WX + x], v); }
+    const R *F;
+    R *Jw;
+    __device__ __forceinline__ R f(int c, int x, int y) const { return F[c * WA + y * WX + x]; }
+    __device__ __forceinline__ void j(int c, int x, int y, R v) const { atomicAdd(&Jw[c * WA + y * WX + x], v); }
 };
 
 __device__ __forceinline__ void cp_async4(void *dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+template <typename R>
+__device__ __forceinline__ void cp_async_r(R *dst, const R *src) {
+    if (sizeof(R) == 4)
+        cp_async4(dst, src);
+    else
+        cp_async8(dst, src);
+}
+
+// J window -> global J
+template <typename R>
+__device__ __forceinline__ void flush_add(R *dst, const R *src);
+template <>
+__device__ __forceinline__ void flush_add<float>(float *dst, const float *src) {
+    const float4 v = *reinterpret_cast<const float4 *>(src);
+    if (v.x == 0.f && v.y == 0.f && v.z == 0.f && v.w == 0.f) return;
+    atomicAdd(reinterpret_cast<float4 *>(dst), v);
+}
+template <>
+__device__ __forceinline__ void flush_add<double>(double *dst, const double *src) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (src[k] != 0.0) atomicAdd(dst + k, src[k]);
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-template <int TX, int TY>
-__global__ void __launch_bounds__(kFusedThreads, PIC_FUSED_MINB)
-    k_step_fused(const StepParams P, const __grid_constant__ CUtensorMap tmapEB) {
-    using TC = TileConst<TX, TY>;
+template <int TX, int TY, typename R>
+__global__ void __launch_bounds__(kFusedThreads, sizeof(R) == 4 ? PIC_FUSED_MINB : 2)
+    k_step_fused(const StepParams<R> P, const __grid_constant__ CUtensorMap tmapEB) {
+    using TC = TileConst<TX, TY, R>;
     constexpr int WX = TC::WX, WY = TC::WY, WA = TC::WA;
     extern __shared__ __align__(1024) unsigned char dsm[];
     __shared__ __align__(8) uint64_t bar;
-    float *sF = reinterpret_cast<float *>(dsm);
-    float *sJ = sF + 6 * WA;
-    float *ring = sJ + 3 * WA;  // [2][kRec][kFusedThreads]
-    const MeshParams &m = P.m;
+    R *sF = reinterpret_cast<R *>(dsm);
+    R *sJ = sF + 6 * WA;
+    R *ring = sJ + 3 * WA;                                             // [2][kRec][kFusedThreads]
+    uint32_t *cring = reinterpret_cast<uint32_t *>(ring + 2 * kRec * kFusedThreads);  // [2][kFusedThreads]
+    const MeshParams<R> &m = P.m;
 
     const int tile = blockIdx.x;
     const int ty = tile / P.t.ntx, tx = tile - ty * P.t.ntx;
@@ -128,25 +159,25 @@ __global__ void __launch_bounds__(kFusedThreads, PIC_FUSED_MINB)
     if (tid == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
-        mbar_expect_tx(&bar, (unsigned)(6 * WA * sizeof(float)));
+        mbar_expect_tx(&bar, (unsigned)(6 * WA * sizeof(R)));
         tma_load_3d(sF, &tmapEB, &bar, wx0, wy0, 0);
     }
 
-    float *ring0 = ring + tid;
+    R *ring0 = ring + tid;
     // particle record `slot` of species S into ring stage `buf`
-    auto prefetch = [&](const DevSpecies &S, int slot, bool live, int buf) {
+    auto prefetch = [&](const DevSpecies<R> &S, int slot, bool live, int buf) {
         if (live) {
-            float *r = ring0 + buf * kRec * kFusedThreads;
-            cp_async4(r + 0 * kFusedThreads, S.cell + slot);
-            cp_async4(r + 1 * kFusedThreads, S.ox + slot);
-            cp_async4(r + 2 * kFusedThreads, S.oy + slot);
-            cp_async4(r + 3 * kFusedThreads, S.ux + slot);
-            cp_async4(r + 4 * kFusedThreads, S.uy + slot);
-            cp_async4(r + 5 * kFusedThreads, S.uz + slot);
-            cp_async4(r + 6 * kFusedThreads, S.sx + slot);
-            cp_async4(r + 7 * kFusedThreads, S.sy + slot);
-            cp_async4(r + 8 * kFusedThreads, S.sz + slot);
-            cp_async4(r + 9 * kFusedThreads, S.w + slot);
+            R *r = ring0 + buf * kRec * kFusedThreads;
+            cp_async4(cring + buf * kFusedThreads + tid, S.cell + slot);
+            cp_async_r(r + 0 * kFusedThreads, S.ox + slot);
+            cp_async_r(r + 1 * kFusedThreads, S.oy + slot);
+            cp_async_r(r + 2 * kFusedThreads, S.ux + slot);
+            cp_async_r(r + 3 * kFusedThreads, S.uy + slot);
+            cp_async_r(r + 4 * kFusedThreads, S.uz + slot);
+            cp_async_r(r + 5 * kFusedThreads, S.sx + slot);
+            cp_async_r(r + 6 * kFusedThreads, S.sy + slot);
+            cp_async_r(r + 7 * kFusedThreads, S.sz + slot);
+            cp_async_r(r + 8 * kFusedThreads, S.w + slot);
         }
         cp_async_commit();
     };
@@ -165,7 +196,7 @@ __global__ void __launch_bounds__(kFusedThreads, PIC_FUSED_MINB)
         const int beg = P.sp[first].tile_start[tile];
         prefetch(P.sp[first], beg + tid, tid < P.sp[first].tile_start[tile + 1] - beg, 0);
     }
-    for (int i = tid; i < 3 * WA; i += kFusedThreads) sJ[i] = 0.f;
+    for (int i = tid; i < 3 * WA; i += kFusedThreads) sJ[i] = R(0);
     __syncthreads();
     if (!mbar_wait_bounded(&bar, 0)) {
         if (tid == 0) atomicOr(P.err, PIC_EF_TIMEOUT);
@@ -173,8 +204,8 @@ __global__ void __launch_bounds__(kFusedThreads, PIC_FUSED_MINB)
         return;
     }
 
-    const SmemMeshT<WX, WA> sm{sF, sJ};
-    const GlobalMesh gm{m.EB, m.J, m.nx, m.ny, m.ld, m.bc_x == 1, m.plane, P.err};
+    const SmemMeshT<R, WX, WA> sm{sF, sJ};
+    const GlobalMesh<R> gm{m.EB, m.J, m.nx, m.ny, m.ld, m.bc_x == 1, m.plane, P.err};
     // window interior where a whole stencil [i-1, i+2] fits, intersected with the mesh
     const int xlo = max(wx0 + 1, 1), xhi = min(wx0 + WX - 3, m.nx - 3);
     const int ylo = max(wy0 + 1, 1), yhi = min(wy0 + WY - 3, m.ny - 3);
@@ -184,7 +215,7 @@ __global__ void __launch_bounds__(kFusedThreads, PIC_FUSED_MINB)
     // the next change of cell: with the layered tile order each thread meets
     // the same cell on every pass through the layers.
     int acc_key = -1;  // window offset of the accumulated cell
-    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    R acc[8] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
     auto acc_flush = [&]() {
         if (acc_key >= 0) {
             atomicAdd(&sJ[acc_key], acc[0]);
@@ -199,17 +230,17 @@ __global__ void __launch_bounds__(kFusedThreads, PIC_FUSED_MINB)
     };
 
     for (int sp = 0; sp < P.nsp; ++sp) {
-        const DevSpecies &S = P.sp[sp];
+        const DevSpecies<R> &S = P.sp[sp];
         if (!S.mobile) continue;
         const int beg = S.tile_start[tile], len = S.tile_start[tile + 1] - beg;
-        const float qm = S.qm, a = S.a, q = S.q;
-        float dacc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        float dlo = 0.f, dhi = 0.f, dm = 0.f, dshift = 0.f;
+        const R qm = S.qm, a = S.a, q = S.q;
+        R dacc[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+        R dlo = R(0), dhi = R(0), dm = R(0), dshift = R(0);
         if (diag) {
-            dlo = P.diag.lo[sp];
-            dhi = P.diag.hi[sp];
-            dm = P.diag.m_mev[sp];
-            dshift = (float)P.diag.shift[sp];
+            dlo = (R)P.diag.lo[sp];
+            dhi = (R)P.diag.hi[sp];
+            dm = (R)P.diag.m_mev[sp];
+            dshift = (R)P.diag.shift[sp];
         }
         int buf = 0;
         if (sp != first) prefetch(S, beg + tid, tid < len, 0);
@@ -219,37 +250,32 @@ __global__ void __launch_bounds__(kFusedThreads, PIC_FUSED_MINB)
             cp_async_wait1();
             if (k < len) {
                 const int slot = beg + k;
-                const float *r = ring0 + buf * kRec * kFusedThreads;
-                const uint32_t c = __float_as_uint(r[0]);
+                const R *r = ring0 + buf * kRec * kFusedThreads;
+                const uint32_t c = cring[buf * kFusedThreads + tid];
                 if (c != PIC_DEAD) {
                     const int ix = (int)(c & 0xFFFFu), iy = (int)(c >> 16);
-                    const float ox = r[1 * kFusedThreads], oy = r[2 * kFusedThreads];
-                    float u[3] = {r[3 * kFusedThreads], r[4 * kFusedThreads], r[5 * kFusedThreads]};
-                    float spn[3] = {r[6 * kFusedThreads], r[7 * kFusedThreads], r[8 * kFusedThreads]};
-                    const float w = r[9 * kFusedThreads];
+                    const R ox = r[0 * kFusedThreads], oy = r[1 * kFusedThreads];
+                    R u[3] = {r[2 * kFusedThreads], r[3 * kFusedThreads], r[4 * kFusedThreads]};
+                    R spn[3] = {r[5 * kFusedThreads], r[6 * kFusedThreads], r[7 * kFusedThreads]};
+                    const R w = r[8 * kFusedThreads];
                     const bool fast = ix >= xlo && ix <= xhi && iy >= ylo && iy <= yhi;
-                    float E[3], B[3];
+                    R E[3], B[3];
                     if (fast)
                         gather_eb(sm, ix - wx0, iy - wy0, ox, oy, E, B);
                     else
                         gather_eb(gm, ix, iy, ox, oy, E, B);
                     push_spin(qm, a, m.dt, E, B, u, spn);
-                    const float gi = rsqrtf(1.f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                    const R gi = Real<R>::rsqrt(R(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
                     int ix1 = ix, iy1 = iy;
-                    float ox1 = ox, oy1 = oy;
+                    R ox1 = ox, oy1 = oy;
                     advance_axis(ix1, ox1, u[0] * gi * m.dt_dx);
                     advance_axis(iy1, oy1, u[1] * gi * m.dt_dy);
-                    const float qw = q * w, vz = u[2] * gi;
+                    const R qw = q * w, vz = u[2] * gi;
                     if (fast && ix1 == ix && iy1 == iy) {
-                        // in-cell Esirkepov weights (see deposit_in_cell), summed per cell
+                        // in-cell Esirkepov weights, summed per cell
                         const int key = (iy - wy0) * WX + (ix - wx0);
-                        const float d = ox1 - ox, e = oy1 - oy;
-                        const float xm = ox + 0.5f * d, ym = oy + 0.5f * e;
-                        const float jx = qw * m.dx_dt * d, jy = qw * m.dy_dt * e, cz = qw * vz;
-                        const float de = d * e * (1.f / 12.f);
-                        const float v[8] = {jx * (1.f - ym), jx * ym, jy * (1.f - xm), jy * xm,
-                                            cz * ((1.f - xm) * (1.f - ym) + de), cz * (xm * (1.f - ym) - de),
-                                            cz * ((1.f - xm) * ym - de), cz * (xm * ym + de)};
+                        R v[8];
+                        in_cell_weights(ox, oy, ox1, oy1, qw, vz, m.dx_dt, m.dy_dt, v);
                         if (key != acc_key) {
                             acc_flush();
                             acc_key = key;
@@ -266,20 +292,20 @@ __global__ void __launch_bounds__(kFusedThreads, PIC_FUSED_MINB)
                         deposit_esirkepov(gm, ix, iy, ox, oy, ix1, iy1, ox1, oy1, qw, vz, m.dx_dt, m.dy_dt);
                     }
                     const bool alive = finish_move(m, ix1, iy1);
-                    const float chk = u[0] * u[0] + u[1] * u[1] + u[2] * u[2] + spn[0] * spn[0] +
-                                      spn[1] * spn[1] + spn[2] * spn[2];
+                    const R chk = u[0] * u[0] + u[1] * u[1] + u[2] * u[2] + spn[0] * spn[0] +
+                                  spn[1] * spn[1] + spn[2] * spn[2];
                     bad |= !isfinite(chk);
                     if (diag && alive) {
-                        const float e = ekin_mev(dm, u[0], u[1], u[2]);
+                        const R e = ekin_mev(dm, u[0], u[1], u[2]);
                         if (e >= dlo && e < dhi) {
-                            const float ep = e - dshift;
+                            const R ep = e - dshift;
                             dacc[0] += w;
                             dacc[1] += w * spn[0];
                             dacc[2] += w * spn[1];
                             dacc[3] += w * spn[2];
                             dacc[4] += w * ep;
                             dacc[5] += w * ep * ep;
-                            dacc[6] += 1.f;
+                            dacc[6] += R(1);
                         }
                     }
                     S.cell[slot] = alive ? pack_cell(ix1, iy1) : PIC_DEAD;
@@ -317,7 +343,7 @@ __global__ void __launch_bounds__(kFusedThreads, PIC_FUSED_MINB)
     if (bad) atomicOr(P.err, PIC_EF_NAN);
     __syncthreads();
 
-    // flush the current window: 16-byte quads, skipping all-zero ones and
+    // flush the current window: groups of 4 values, skipping all-zero ones and
     // rows / columns outside the mesh (nothing is deposited there)
     constexpr int WQ = WX / 4;
     for (int qd = tid; qd < 3 * WY * WQ; qd += kFusedThreads) {
@@ -326,9 +352,7 @@ __global__ void __launch_bounds__(kFusedThreads, PIC_FUSED_MINB)
         const int y = rr / WQ, xq = rr - y * WQ;
         const int gy = wy0 + y, gx = wx0 + 4 * xq;
         if (gy < 0 || gy >= m.ny || gx < 0 || gx >= m.ld) continue;
-        const float4 v = *reinterpret_cast<const float4 *>(&sJ[c * WA + y * WX + 4 * xq]);
-        if (v.x == 0.f && v.y == 0.f && v.z == 0.f && v.w == 0.f) continue;
-        atomicAdd(reinterpret_cast<float4 *>(&m.J[c * m.plane + (size_t)gy * m.ld + gx]), v);
+        flush_add<R>(&m.J[c * m.plane + (size_t)gy * m.ld + gx], &sJ[c * WA + y * WX + 4 * xq]);
     }
 }
 
@@ -336,10 +360,11 @@ __global__ void __launch_bounds__(kFusedThreads, PIC_FUSED_MINB)
 // Split path, a1-a4: one thread per slot, global-memory gather; keeps x^n and
 // v_z^{n+1/2} for the deposit.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_push_split(const StepParams P, int s) {
-    const DevSpecies &S = P.sp[s];
-    const MeshParams &m = P.m;
-    const GlobalMesh gm{m.EB, m.J, m.nx, m.ny, m.ld, m.bc_x == 1, m.plane, P.err};
+template <typename R>
+__global__ void __launch_bounds__(256) k_push_split(const StepParams<R> P, int s) {
+    const DevSpecies<R> &S = P.sp[s];
+    const MeshParams<R> &m = P.m;
+    const GlobalMesh<R> gm{m.EB, m.J, m.nx, m.ny, m.ld, m.bc_x == 1, m.plane, P.err};
     unsigned bad = 0;
     const int n = *S.n;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
@@ -347,15 +372,15 @@ __global__ void __launch_bounds__(256) k_push_split(const StepParams P, int s) {
         S.cell_old[p] = c;
         if (c == PIC_DEAD) continue;
         const int ix = (int)(c & 0xFFFFu), iy = (int)(c >> 16);
-        const float ox = S.ox[p], oy = S.oy[p];
-        float u[3] = {S.ux[p], S.uy[p], S.uz[p]};
-        float sp[3] = {S.sx[p], S.sy[p], S.sz[p]};
-        float E[3], B[3];
+        const R ox = S.ox[p], oy = S.oy[p];
+        R u[3] = {S.ux[p], S.uy[p], S.uz[p]};
+        R sp[3] = {S.sx[p], S.sy[p], S.sz[p]};
+        R E[3], B[3];
         gather_eb(gm, ix, iy, ox, oy, E, B);
         push_spin(S.qm, S.a, m.dt, E, B, u, sp);
-        const float gi = rsqrtf(1.f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        const R gi = Real<R>::rsqrt(R(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
         int ix1 = ix, iy1 = iy;
-        float ox1 = ox, oy1 = oy;
+        R ox1 = ox, oy1 = oy;
         advance_axis(ix1, ox1, u[0] * gi * m.dt_dx);
         advance_axis(iy1, oy1, u[1] * gi * m.dt_dy);
         if (!finite3(u) || !finite3(sp)) bad |= PIC_EF_NAN;
@@ -378,10 +403,11 @@ __global__ void __launch_bounds__(256) k_push_split(const StepParams P, int s) {
 
 // Split path, a5: current of the move recorded by k_push_split, then the
 // wrap / removal of the new position.
-__global__ void __launch_bounds__(256) k_deposit_split(const StepParams P, int s) {
-    const DevSpecies &S = P.sp[s];
-    const MeshParams &m = P.m;
-    const GlobalMesh gm{m.EB, m.J, m.nx, m.ny, m.ld, m.bc_x == 1, m.plane, P.err};
+template <typename R>
+__global__ void __launch_bounds__(256) k_deposit_split(const StepParams<R> P, int s) {
+    const DevSpecies<R> &S = P.sp[s];
+    const MeshParams<R> &m = P.m;
+    const GlobalMesh<R> gm{m.EB, m.J, m.nx, m.ny, m.ld, m.bc_x == 1, m.plane, P.err};
     const int n = *S.n;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
         const uint32_t c0 = S.cell_old[p];
@@ -389,9 +415,9 @@ __global__ void __launch_bounds__(256) k_deposit_split(const StepParams P, int s
         const int ix = (int)(c0 & 0xFFFFu), iy = (int)(c0 >> 16);
         const uint32_t c1 = S.cell[p];
         int ix1 = (int)(c1 & 0xFFFFu) - 1, iy1 = (int)(c1 >> 16) - 1;
-        const float ox1 = S.ox[p], oy1 = S.oy[p];
-        deposit_esirkepov(gm, ix, iy, S.ox_old[p], S.oy_old[p], ix1, iy1, ox1, oy1,
-                          S.q * S.w[p], S.vz[p], m.dx_dt, m.dy_dt);
+        const R ox1 = S.ox[p], oy1 = S.oy[p];
+        deposit_esirkepov(gm, ix, iy, S.ox_old[p], S.oy_old[p], ix1, iy1, ox1, oy1, S.q * S.w[p], S.vz[p],
+                          m.dx_dt, m.dy_dt);
         const bool alive = finish_move(m, ix1, iy1);
         S.cell[p] = alive ? pack_cell(ix1, iy1) : PIC_DEAD;
     }
@@ -400,18 +426,19 @@ __global__ void __launch_bounds__(256) k_deposit_split(const StepParams P, int s
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-template <int TX, int TY>
-static cudaError_t launch_fused_t(const StepParams &P, const CUtensorMap &tmapEB, cudaStream_t st) {
-    constexpr size_t smem = TileConst<TX, TY>::smem_bytes;
-    if (P.t.WX != TileConst<TX, TY>::WX || P.t.WY != TileConst<TX, TY>::WY) return cudaErrorInvalidValue;
+template <int TX, int TY, typename R>
+static cudaError_t launch_fused_t(const StepParams<R> &P, const CUtensorMap &tmapEB, cudaStream_t st) {
+    using TC = TileConst<TX, TY, R>;
+    constexpr size_t smem = TC::smem_bytes;
+    if (P.t.WX != TC::WX || P.t.WY != TC::WY) return cudaErrorInvalidValue;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_step_fused<TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_step_fused<TX, TY, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    k_step_fused<TX, TY><<<P.t.ntx * P.t.nty, kFusedThreads, smem, st>>>(P, tmapEB);
+    k_step_fused<TX, TY, R><<<P.t.ntx * P.t.nty, kFusedThreads, smem, st>>>(P, tmapEB);
     return cudaGetLastError();
 }
 
@@ -420,13 +447,14 @@ bool fused_tile_supported(int tx, int ty) {
            (tx == 32 && ty == 16) || (tx == 64 && ty == 16);
 }
 
-cudaError_t launch_step_fused(const StepParams &P, const CUtensorMap &tmapEB, cudaStream_t st) {
+template <typename R>
+cudaError_t launch_step_fused(const StepParams<R> &P, const CUtensorMap &tmapEB, cudaStream_t st) {
     const int tx = P.t.TX, ty = P.t.TY;
-    if (tx == 8 && ty == 4) return launch_fused_t<8, 4>(P, tmapEB, st);
-    if (tx == 16 && ty == 8) return launch_fused_t<16, 8>(P, tmapEB, st);
-    if (tx == 32 && ty == 8) return launch_fused_t<32, 8>(P, tmapEB, st);
-    if (tx == 32 && ty == 16) return launch_fused_t<32, 16>(P, tmapEB, st);
-    if (tx == 64 && ty == 16) return launch_fused_t<64, 16>(P, tmapEB, st);
+    if (tx == 8 && ty == 4) return launch_fused_t<8, 4, R>(P, tmapEB, st);
+    if (tx == 16 && ty == 8) return launch_fused_t<16, 8, R>(P, tmapEB, st);
+    if (tx == 32 && ty == 8) return launch_fused_t<32, 8, R>(P, tmapEB, st);
+    if (tx == 32 && ty == 16) return launch_fused_t<32, 16, R>(P, tmapEB, st);
+    if (tx == 64 && ty == 16) return launch_fused_t<64, 16, R>(P, tmapEB, st);
     return cudaErrorInvalidValue;
 }
 
@@ -435,14 +463,21 @@ static int blocks_for(int n) {
     return b < 1 ? 1 : (b > 152 * 32 ? 152 * 32 : b);
 }
 
-cudaError_t launch_push_split(const StepParams &P, int s, int n_upper, cudaStream_t st) {
-    const int blocks = blocks_for(n_upper);
-    k_push_split<<<blocks, 256, 0, st>>>(P, s);
+template <typename R>
+cudaError_t launch_push_split(const StepParams<R> &P, int s, int n_upper, cudaStream_t st) {
+    k_push_split<R><<<blocks_for(n_upper), 256, 0, st>>>(P, s);
     return cudaGetLastError();
 }
 
-cudaError_t launch_deposit_split(const StepParams &P, int s, int n_upper, cudaStream_t st) {
-    const int blocks = blocks_for(n_upper);
-    k_deposit_split<<<blocks, 256, 0, st>>>(P, s);
+template <typename R>
+cudaError_t launch_deposit_split(const StepParams<R> &P, int s, int n_upper, cudaStream_t st) {
+    k_deposit_split<R><<<blocks_for(n_upper), 256, 0, st>>>(P, s);
     return cudaGetLastError();
 }
+
+template cudaError_t launch_step_fused<float>(const StepParams<float> &, const CUtensorMap &, cudaStream_t);
+template cudaError_t launch_step_fused<double>(const StepParams<double> &, const CUtensorMap &, cudaStream_t);
+template cudaError_t launch_push_split<float>(const StepParams<float> &, int, int, cudaStream_t);
+template cudaError_t launch_push_split<double>(const StepParams<double> &, int, int, cudaStream_t);
+template cudaError_t launch_deposit_split<float>(const StepParams<float> &, int, int, cudaStream_t);
+template cudaError_t launch_deposit_split<double>(const StepParams<double> &, int, int, cudaStream_t);

@@ -32,33 +32,34 @@ __device__ void block_sum(double (&v)[NV], double *row) {
     }
 }
 
-__device__ __forceinline__ float ekin(float m_mev, float ux, float uy, float uz) {
+template <typename R>
+__device__ __forceinline__ R ekin(R m_mev, R ux, R uy, R uz) {
     return ekin_mev(m_mev, ux, uy, uz);
 }
 
 // pass 1: sum w, sum w s (3), sum w e, count.  Each thread folds float sums of
 // at most 16 particles into its double accumulators.
-__global__ void __launch_bounds__(RT) k_mom1(const DevSpecies S, float m_mev, float emin, float emax,
-                                             double *partials) {
+template <typename R>
+__global__ void __launch_bounds__(RT) k_mom1(const DevSpecies<R> S, R m_mev, R emin, R emax, double *partials) {
     double acc[6] = {0, 0, 0, 0, 0, 0};
-    float f[6] = {0, 0, 0, 0, 0, 0};
+    R f[6] = {0, 0, 0, 0, 0, 0};
     int k = 0;
     const int n = *S.n;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
         if (S.cell[p] == PIC_DEAD) continue;
-        const float e = ekin(m_mev, S.ux[p], S.uy[p], S.uz[p]);
+        const R e = ekin(m_mev, S.ux[p], S.uy[p], S.uz[p]);
         if (!(e >= emin && e < emax)) continue;
-        const float w = S.w[p];
+        const R w = S.w[p];
         f[0] += w;
         f[1] += w * S.sx[p];
         f[2] += w * S.sy[p];
         f[3] += w * S.sz[p];
         f[4] += w * e;
-        f[5] += 1.f;
+        f[5] += R(1);
         if (++k == 16) {
             for (int q = 0; q < 6; ++q) {
                 acc[q] += (double)f[q];
-                f[q] = 0.f;
+                f[q] = R(0);
             }
             k = 0;
         }
@@ -109,23 +110,24 @@ __global__ void __launch_bounds__(RT) k_final_maxsum(const double *partials, int
 }
 
 // pass 2: sum w (e - mean)^2, the mean read from pass 1's result
-__global__ void __launch_bounds__(RT) k_mom2(const DevSpecies S, float m_mev, float emin, float emax,
-                                             const double *r1, double *partials) {
+template <typename R>
+__global__ void __launch_bounds__(RT) k_mom2(const DevSpecies<R> S, R m_mev, R emin, R emax, const double *r1,
+                                             double *partials) {
     const double sw = r1[0];
-    const float mean = sw > 0.0 ? (float)(r1[4] / sw) : 0.f;
+    const R mean = sw > 0.0 ? (R)(r1[4] / sw) : R(0);
     double acc[1] = {0.0};
-    float f = 0.f;
+    R f = R(0);
     int k = 0;
     const int n = *S.n;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
         if (S.cell[p] == PIC_DEAD) continue;
-        const float e = ekin(m_mev, S.ux[p], S.uy[p], S.uz[p]);
+        const R e = ekin(m_mev, S.ux[p], S.uy[p], S.uz[p]);
         if (!(e >= emin && e < emax)) continue;
-        const float d = e - mean;
+        const R d = e - mean;
         f += S.w[p] * d * d;
         if (++k == 16) {
             acc[0] += (double)f;
-            f = 0.f;
+            f = R(0);
             k = 0;
         }
     }
@@ -134,24 +136,26 @@ __global__ void __launch_bounds__(RT) k_mom2(const DevSpecies S, float m_mev, fl
 }
 
 // CIC charge density of one species at the nodes
-__global__ void k_rho(const DevSpecies S, const MeshParams m, float *rho) {
+template <typename R>
+__global__ void k_rho(const DevSpecies<R> S, const MeshParams<R> m, R *rho) {
     const int n = *S.n;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
         const uint32_t c = S.cell[p];
         if (c == PIC_DEAD) continue;
         const int ix = (int)(c & 0xFFFFu), iy = (int)(c >> 16);
-        const float ox = S.ox[p], oy = S.oy[p], qw = S.q * S.w[p];
+        const R ox = S.ox[p], oy = S.oy[p], qw = S.q * S.w[p], one = R(1);
         const int ix1 = ix + 1 == m.nx ? 0 : ix + 1;
         const int iy1 = iy + 1 == m.ny ? 0 : iy + 1;
-        atomicAdd(&rho[(size_t)iy * m.ld + ix], qw * (1.f - ox) * (1.f - oy));
-        atomicAdd(&rho[(size_t)iy * m.ld + ix1], qw * ox * (1.f - oy));
-        atomicAdd(&rho[(size_t)iy1 * m.ld + ix], qw * (1.f - ox) * oy);
+        atomicAdd(&rho[(size_t)iy * m.ld + ix], qw * (one - ox) * (one - oy));
+        atomicAdd(&rho[(size_t)iy * m.ld + ix1], qw * ox * (one - oy));
+        atomicAdd(&rho[(size_t)iy1 * m.ld + ix], qw * (one - ox) * oy);
         atomicAdd(&rho[(size_t)iy1 * m.ld + ix1], qw * ox * oy);
     }
 }
 
 // div E - rho - rho_bg on nodes i in [i0, i1]: block max |r| and sum r^2
-__global__ void __launch_bounds__(RT) k_gauss(const MeshParams m, const float *rho, const float *rho_bg,
+template <typename R>
+__global__ void __launch_bounds__(RT) k_gauss(const MeshParams<R> m, const R *rho, const R *rho_bg,
                                               double idx, double idy, int i0, int i1, double *partials) {
     double vmax = 0.0, ssq = 0.0;
     const int w = i1 - i0 + 1;
@@ -184,7 +188,8 @@ __global__ void __launch_bounds__(RT) k_gauss(const MeshParams m, const float *r
     }
 }
 
-__global__ void k_negate(const float *src, float *dst, size_t n) {
+template <typename R>
+__global__ void k_negate(const R *src, R *dst, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         dst[i] = -src[i];
 }
@@ -235,31 +240,45 @@ cudaError_t launch_diag_final(const double *rows, int nrows, int nsp, double *sh
 
 
 // result[0..5] = sums of pass 1, result[6] = sum w (e - mean)^2
-cudaError_t launch_moments(const DevSpecies &S, float m_mev, float emin, float emax, double *partials,
-                           double *result, cudaStream_t st) {
-    k_mom1<<<RB, RT, 0, st>>>(S, m_mev, emin, emax, partials);
+template <typename R>
+cudaError_t launch_moments(const DevSpecies<R> &S, R m_mev, R emin, R emax, double *partials, double *result,
+                           cudaStream_t st) {
+    k_mom1<R><<<RB, RT, 0, st>>>(S, m_mev, emin, emax, partials);
     k_final<<<1, RT, 0, st>>>(partials, RB, 6, result);
-    k_mom2<<<RB, RT, 0, st>>>(S, m_mev, emin, emax, result, partials);
+    k_mom2<R><<<RB, RT, 0, st>>>(S, m_mev, emin, emax, result, partials);
     k_final<<<1, RT, 0, st>>>(partials, RB, 1, result + 6);
     return cudaGetLastError();
 }
 
-cudaError_t launch_rho(const DevSpecies &S, int n_upper, const MeshParams &m, float *rho, cudaStream_t st) {
+template <typename R>
+cudaError_t launch_rho(const DevSpecies<R> &S, int n_upper, const MeshParams<R> &m, R *rho, cudaStream_t st) {
     int b = (n_upper + 255) / 256;
     if (b > 152 * 16) b = 152 * 16;
     if (b < 1) b = 1;
-    k_rho<<<b, 256, 0, st>>>(S, m, rho);
+    k_rho<R><<<b, 256, 0, st>>>(S, m, rho);
     return cudaGetLastError();
 }
 
-cudaError_t launch_gauss(const MeshParams &m, const float *rho, const float *rho_bg, double dx, double dy,
-                         int i0, int i1, double *partials, double *result, cudaStream_t st) {
-    k_gauss<<<RB, RT, 0, st>>>(m, rho, rho_bg, 1.0 / dx, 1.0 / dy, i0, i1, partials);
+template <typename R>
+cudaError_t launch_gauss(const MeshParams<R> &m, const R *rho, const R *rho_bg, double dx, double dy, int i0,
+                         int i1, double *partials, double *result, cudaStream_t st) {
+    k_gauss<R><<<RB, RT, 0, st>>>(m, rho, rho_bg, 1.0 / dx, 1.0 / dy, i0, i1, partials);
     k_final_maxsum<<<1, RT, 0, st>>>(partials, RB, result);
     return cudaGetLastError();
 }
 
-cudaError_t launch_negate_copy(const float *src, float *dst, size_t n, cudaStream_t st) {
-    k_negate<<<152 * 4, 256, 0, st>>>(src, dst, n);
+template <typename R>
+cudaError_t launch_negate_copy(const R *src, R *dst, size_t n, cudaStream_t st) {
+    k_negate<R><<<152 * 4, 256, 0, st>>>(src, dst, n);
     return cudaGetLastError();
 }
+
+#define PIC_INST(R)                                                                                        \
+    template cudaError_t launch_moments<R>(const DevSpecies<R> &, R, R, R, double *, double *, cudaStream_t); \
+    template cudaError_t launch_rho<R>(const DevSpecies<R> &, int, const MeshParams<R> &, R *, cudaStream_t); \
+    template cudaError_t launch_gauss<R>(const MeshParams<R> &, const R *, const R *, double, double, int, int,  \
+                                         double *, double *, cudaStream_t);                                 \
+    template cudaError_t launch_negate_copy<R>(const R *, R *, size_t, cudaStream_t);
+PIC_INST(float)
+PIC_INST(double)
+#undef PIC_INST

@@ -14,11 +14,6 @@
 
 namespace {
 
-__device__ __forceinline__ int tile_of(uint32_t c, const TileGeom t) {
-    const int ix = (int)(c & 0xFFFFu), iy = (int)(c >> 16);
-    return (iy / t.TY) * t.ntx + ix / t.TX;
-}
-
 __global__ void k_pack(const int32_t *ix, const int32_t *iy, uint32_t *cell, int n, int xlo, int xhi,
                        int ny, unsigned *err) {
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
@@ -121,7 +116,8 @@ __global__ void __launch_bounds__(1024) k_scan(const int32_t *count, int nt, int
     }
 }
 
-__global__ void k_scatter(const DevSpecies src, const DevSpecies dst, const TileGeom t,
+template <typename R>
+__global__ void k_scatter(const DevSpecies<R> src, const DevSpecies<R> dst, const TileGeom t,
                           const int32_t *rank, const int32_t *tile_start, const int32_t *tile_R,
                           const int32_t *cell_off) {
     const int n = *src.n;
@@ -172,7 +168,8 @@ cudaError_t launch_unpack_cells(const uint32_t *cell, int32_t *ix, int32_t *iy, 
 // *src.n is read by the kernels and replaced by the sorted count at the end.
 // Scratch: cell_count and cell_off [ntiles * C], tile_R and tile_total
 // [ntiles], rank [n_upper].
-cudaError_t launch_tile_sort(const DevSpecies &src, const DevSpecies &dst, const TileGeom &t,
+template <typename R>
+cudaError_t launch_tile_sort(const DevSpecies<R> &src, const DevSpecies<R> &dst, const TileGeom &t,
                              const SortScratch &w, int32_t *tile_start, int32_t *n_tmp, int n_upper,
                              cudaStream_t st) {
     const int nt = t.ntx * t.nty, C = t.TX * t.TY;
@@ -182,8 +179,33 @@ cudaError_t launch_tile_sort(const DevSpecies &src, const DevSpecies &dst, const
     k_rank<<<g, 256, 0, st>>>(src.cell, src.n, t, w.cell_count, w.rank);
     k_layout<<<nt, C, 0, st>>>(w.cell_count, C, w.cell_off, w.tile_R, w.tile_total);
     k_scan<<<1, 1024, 0, st>>>(w.tile_total, nt, tile_start, w.cursor, n_tmp);
-    k_scatter<<<g, 256, 0, st>>>(src, dst, t, w.rank, tile_start, w.tile_R, w.cell_off);
+    k_scatter<R><<<g, 256, 0, st>>>(src, dst, t, w.rank, tile_start, w.tile_R, w.cell_off);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return cudaMemcpyAsync(const_cast<int32_t *>(src.n), n_tmp, sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
 }
+
+template cudaError_t launch_tile_sort<float>(const DevSpecies<float> &, const DevSpecies<float> &,
+                                             const TileGeom &, const SortScratch &, int32_t *, int32_t *, int,
+                                             cudaStream_t);
+template cudaError_t launch_tile_sort<double>(const DevSpecies<double> &, const DevSpecies<double> &,
+                                              const TileGeom &, const SortScratch &, int32_t *, int32_t *, int,
+                                              cudaStream_t);
+
+// element-wise precision conversion (host transfers of the FP64 instantiation)
+namespace {
+template <typename A, typename B>
+__global__ void k_convert(const A *src, B *dst, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = (B)src[i];
+}
+}  // namespace
+
+template <typename A, typename B>
+cudaError_t launch_convert(const A *src, B *dst, size_t n, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    k_convert<A, B><<<152 * 8, 256, 0, st>>>(src, dst, n);
+    return cudaGetLastError();
+}
+template cudaError_t launch_convert<float, double>(const float *, double *, size_t, cudaStream_t);
+template cudaError_t launch_convert<double, float>(const double *, float *, size_t, cudaStream_t);

@@ -4,6 +4,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -21,7 +22,7 @@ constexpr double kMec2Mev = 0.51099895;
 
 struct SpeciesBuf {
     uint32_t *cell = nullptr;
-    float *f[9] = {};  // ox oy ux uy uz sx sy sz w
+    void *f[9] = {};  // ox oy ux uy uz sx sy sz w (float or double)
     int32_t *id = nullptr;
 };
 
@@ -33,13 +34,16 @@ struct Ctx {
     size_t plane = 0;
     TileGeom tg{};
     int ntiles = 0;
-    float *EB = nullptr, *J = nullptr, *bnd = nullptr, *rho = nullptr, *rho_bg = nullptr;
+    int rb = 4;  // bytes per real: 4 for the FP32 path, 8 for the FP64 instantiation
+    void *EB = nullptr, *J = nullptr, *bnd = nullptr, *rho = nullptr, *rho_bg = nullptr;
+    void *stage = nullptr;  // max(plane, capacity) doubles: precision conversions of transfers
+    size_t stage_elems = 0;
     SpeciesBuf buf[PIC_MAX_SPECIES][2];
     int cur[PIC_MAX_SPECIES] = {};
     int n_upper[PIC_MAX_SPECIES] = {};  // host bound on the device slot counts (sizes grids)
     int32_t *tile_start[PIC_MAX_SPECIES] = {};
     uint32_t *cell_old[PIC_MAX_SPECIES] = {};
-    float *old_f[PIC_MAX_SPECIES][3] = {};  // ox_old, oy_old, vz
+    void *old_f[PIC_MAX_SPECIES][3] = {};  // ox_old, oy_old, vz
     int32_t *tile_count = nullptr, *tile_cursor = nullptr;
     int32_t *cell_count = nullptr, *cell_off = nullptr, *tile_R = nullptr;
     int32_t *n_dev = nullptr;  // [PIC_MAX_SPECIES + 1] slot counts; the last entry is sort scratch
@@ -49,7 +53,7 @@ struct Ctx {
     double *laser_prof = nullptr;  // [2][ny] transverse profile at y_j, y_{j+1/2}
     // in-step Eq. (4) diagnostics
     int diag_every = 0;
-    float diag_lo[PIC_MAX_SPECIES] = {}, diag_hi[PIC_MAX_SPECIES] = {};
+    double diag_lo[PIC_MAX_SPECIES] = {}, diag_hi[PIC_MAX_SPECIES] = {};
     double *diag_rows = nullptr, *diag_shift = nullptr;
     pic_moments_dev *diag_out = nullptr;
     long long diag_step = -1;
@@ -71,70 +75,79 @@ pic_status_t fail(Ctx *c, pic_status_t s, const std::string &msg) {
     return s;
 }
 
-#define CK(call)                                                                         \
-    do {                                                                                 \
-        cudaError_t e_ = (call);                                                         \
-        if (e_ != cudaSuccess)                                                           \
-            return fail(c, PIC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+#define CK(...)                                                                                 \
+    do {                                                                                        \
+        cudaError_t e_ = (__VA_ARGS__);                                                         \
+        if (e_ != cudaSuccess)                                                                  \
+            return fail(c, PIC_ERR_CUDA, std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
 cudaStream_t S(void *stream) { return reinterpret_cast<cudaStream_t>(stream); }
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
-DevSpecies dev_species(Ctx *c, int s, int which) {
-    DevSpecies d{};
+template <typename R>
+DevSpecies<R> dev_species(Ctx *c, int s, int which) {
+    DevSpecies<R> d{};
     const SpeciesBuf &b = c->buf[s][which];
     d.cell = b.cell;
-    d.ox = b.f[0];
-    d.oy = b.f[1];
-    d.ux = b.f[2];
-    d.uy = b.f[3];
-    d.uz = b.f[4];
-    d.sx = b.f[5];
-    d.sy = b.f[6];
-    d.sz = b.f[7];
-    d.w = b.f[8];
+    d.ox = static_cast<R *>(b.f[0]);
+    d.oy = static_cast<R *>(b.f[1]);
+    d.ux = static_cast<R *>(b.f[2]);
+    d.uy = static_cast<R *>(b.f[3]);
+    d.uz = static_cast<R *>(b.f[4]);
+    d.sx = static_cast<R *>(b.f[5]);
+    d.sy = static_cast<R *>(b.f[6]);
+    d.sz = static_cast<R *>(b.f[7]);
+    d.w = static_cast<R *>(b.f[8]);
     d.id = b.id;
     d.tile_start = c->tile_start[s];
     d.cell_old = c->cell_old[s];
-    d.ox_old = c->old_f[s][0];
-    d.oy_old = c->old_f[s][1];
-    d.vz = c->old_f[s][2];
+    d.ox_old = static_cast<R *>(c->old_f[s][0]);
+    d.oy_old = static_cast<R *>(c->old_f[s][1]);
+    d.vz = static_cast<R *>(c->old_f[s][2]);
     const pic_species_t &sp = c->cfg.sp[s];
-    d.qm = (float)(sp.q / sp.m);
-    d.q = (float)sp.q;
-    d.a = (float)sp.a;
+    d.qm = (R)(sp.q / sp.m);
+    d.q = (R)sp.q;
+    d.a = (R)sp.a;
     d.mobile = sp.mobile;
     d.n = c->n_dev + s;
     return d;
 }
 
-MeshParams mesh(Ctx *c) {
-    MeshParams m{};
+template <typename R>
+MeshParams<R> mesh(Ctx *c) {
+    MeshParams<R> m{};
     m.nx = c->cfg.nx;
     m.ny = c->cfg.ny;
     m.ld = c->ld;
     m.bc_x = c->cfg.bc_x;
-    m.dt = (float)c->dt;
-    m.dt_dx = (float)(c->dt / c->dx);
-    m.dt_dy = (float)(c->dt / c->dy);
-    m.dx_dt = (float)(c->dx / c->dt);
-    m.dy_dt = (float)(c->dy / c->dt);
-    m.EB = c->EB;
-    m.J = c->J;
+    m.dt = (R)c->dt;
+    m.dt_dx = (R)(c->dt / c->dx);
+    m.dt_dy = (R)(c->dt / c->dy);
+    m.dx_dt = (R)(c->dx / c->dt);
+    m.dy_dt = (R)(c->dy / c->dt);
+    m.EB = static_cast<R *>(c->EB);
+    m.J = static_cast<R *>(c->J);
     m.plane = c->plane;
     return m;
 }
 
-StepParams step_params(Ctx *c) {
-    StepParams P{};
-    P.m = mesh(c);
+template <typename R>
+StepParams<R> step_params(Ctx *c) {
+    StepParams<R> P{};
+    P.m = mesh<R>(c);
     P.t = c->tg;
     P.nsp = c->cfg.nspecies;
-    for (int s = 0; s < P.nsp; ++s) P.sp[s] = dev_species(c, s, c->cur[s]);
+    for (int s = 0; s < P.nsp; ++s) P.sp[s] = dev_species<R>(c, s, c->cur[s]);
     P.err = c->err;
     return P;
+}
+
+// runs f(R{}) with R the context's real type
+template <class F>
+auto with_real(Ctx *c, F &&f) {
+    return c->rb == 8 ? f(double{}) : f(float{});
 }
 
 LaserParams laser(Ctx *c) {
@@ -159,7 +172,7 @@ void choose_tiles(Ctx *c) {
     // tile shapes the fused kernel is compiled for (pic_validate_config checks)
     c->tg.TX = tx;
     c->tg.TY = ty;
-    c->tg.WX = window_wx(tx);
+    c->tg.WX = c->rb == 8 ? window_wx<double>(tx) : window_wx<float>(tx);
     c->tg.WY = window_wy(ty);
     c->tg.ntx = (c->cfg.nx + tx - 1) / tx;
     c->tg.nty = (c->cfg.ny + ty - 1) / ty;
@@ -174,10 +187,11 @@ pic_status_t make_tensor_map(Ctx *c) {
         return fail(c, PIC_ERR_CUDA, "cuTensorMapEncodeTiled not available");
     auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     cuuint64_t dims[3] = {(cuuint64_t)c->cfg.nx, (cuuint64_t)c->cfg.ny, 6};
-    cuuint64_t strides[2] = {(cuuint64_t)c->ld * sizeof(float), (cuuint64_t)c->plane * sizeof(float)};
+    cuuint64_t strides[2] = {(cuuint64_t)c->ld * c->rb, (cuuint64_t)c->plane * c->rb};
     cuuint32_t box[3] = {(cuuint32_t)c->tg.WX, (cuuint32_t)c->tg.WY, 6};
     cuuint32_t es[3] = {1, 1, 1};
-    CUresult r = enc(&c->tmapEB, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->EB, dims, strides, box, es,
+    const CUtensorMapDataType dtype = c->rb == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    CUresult r = enc(&c->tmapEB, dtype, 3, c->EB, dims, strides, box, es,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(c, PIC_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
@@ -202,9 +216,12 @@ pic_status_t check_flags(Ctx *c, cudaStream_t st) {
 // ever shrinks, so n_upper still bounds it)
 pic_status_t sort_species(Ctx *c, int s, cudaStream_t st) {
     const int from = c->cur[s], to = 1 - from;
-    DevSpecies src = dev_species(c, s, from), dst = dev_species(c, s, to);
     SortScratch w{c->cell_count, c->cell_off, c->tile_R, c->tile_count, c->tile_cursor, c->scratch_i32};
-    CK(launch_tile_sort(src, dst, c->tg, w, c->tile_start[s], c->n_dev + PIC_MAX_SPECIES, c->n_upper[s], st));
+    CK(with_real(c, [&](auto z) {
+        using T = decltype(z);
+        return launch_tile_sort<T>(dev_species<T>(c, s, from), dev_species<T>(c, s, to), c->tg, w, c->tile_start[s],
+                                   c->n_dev + PIC_MAX_SPECIES, c->n_upper[s], st);
+    }));
     c->launches += 4;
     c->cur[s] = to;
     return PIC_OK;
@@ -220,7 +237,7 @@ pic_status_t alloc_old(Ctx *c, int s) {
     if (c->cell_old[s]) return PIC_OK;
     const size_t cap = (size_t)c->cfg.sp[s].capacity;
     CK(cudaMalloc(&c->cell_old[s], cap * sizeof(uint32_t) + 16));
-    for (int k = 0; k < 3; ++k) CK(cudaMalloc(&c->old_f[s][k], cap * sizeof(float) + 16));
+    for (int k = 0; k < 3; ++k) CK(cudaMalloc(&c->old_f[s][k], cap * c->rb + 16));
     return PIC_OK;
 }
 
@@ -252,6 +269,8 @@ pic_status_t pic_validate_config(const pic_config_t *cfg) {
     if ((cfg->tile_x != 0 || cfg->tile_y != 0) && !fused_tile_supported(cfg->tile_x, cfg->tile_y))
         return fail(c, PIC_ERR_ARG, "tile must be one of 8x4, 16x8, 32x8, 32x16, 64x16 cells");
     if (cfg->sort_every < 0) return fail(c, PIC_ERR_ARG, "sort_every must be >= 0");
+    if (cfg->precision != 0 && cfg->precision != 32 && cfg->precision != 64)
+        return fail(c, PIC_ERR_ARG, "precision must be 32 or 64 (0: 32)");
     return PIC_OK;
 }
 
@@ -265,6 +284,8 @@ pic_status_t pic_create(const pic_config_t *cfg, void *stream, void **ctx_out) {
     if (!c) return fail(nullptr, PIC_ERR_CUDA, "host allocation failed");
     c->cfg = *cfg;
     if (c->cfg.sort_every == 0) c->cfg.sort_every = 32;
+    if (c->cfg.precision == 0) c->cfg.precision = 32;
+    c->rb = c->cfg.precision == 64 ? 8 : 4;
     cudaStream_t st = S(stream);
     auto bail = [&](pic_status_t s) {
         g_create_error = c->last_error;
@@ -286,22 +307,23 @@ pic_status_t pic_create(const pic_config_t *cfg, void *stream, void **ctx_out) {
     c->ld = round_up(cfg->nx, 32);
     c->plane = (size_t)c->ld * cfg->ny;
     choose_tiles(c);
-    CKC(cudaMalloc(&c->EB, 6 * c->plane * sizeof(float)));
-    CKC(cudaMalloc(&c->J, 3 * c->plane * sizeof(float)));
-    CKC(cudaMalloc(&c->bnd, 2 * (size_t)cfg->ny * sizeof(float)));
-    CKC(cudaMalloc(&c->rho, c->plane * sizeof(float)));
-    CKC(cudaMalloc(&c->rho_bg, c->plane * sizeof(float)));
-    CKC(cudaMemsetAsync(c->EB, 0, 6 * c->plane * sizeof(float), st));
-    CKC(cudaMemsetAsync(c->J, 0, 3 * c->plane * sizeof(float), st));
-    CKC(cudaMemsetAsync(c->bnd, 0, 2 * (size_t)cfg->ny * sizeof(float), st));
-    CKC(cudaMemsetAsync(c->rho_bg, 0, c->plane * sizeof(float), st));
+    const size_t rb = c->rb;
+    CKC(cudaMalloc(&c->EB, 6 * c->plane * rb));
+    CKC(cudaMalloc(&c->J, 3 * c->plane * rb));
+    CKC(cudaMalloc(&c->bnd, 2 * (size_t)cfg->ny * rb));
+    CKC(cudaMalloc(&c->rho, c->plane * rb));
+    CKC(cudaMalloc(&c->rho_bg, c->plane * rb));
+    CKC(cudaMemsetAsync(c->EB, 0, 6 * c->plane * rb, st));
+    CKC(cudaMemsetAsync(c->J, 0, 3 * c->plane * rb, st));
+    CKC(cudaMemsetAsync(c->bnd, 0, 2 * (size_t)cfg->ny * rb, st));
+    CKC(cudaMemsetAsync(c->rho_bg, 0, c->plane * rb, st));
     int64_t capmax = 0;
     for (int s = 0; s < cfg->nspecies; ++s) {
         const size_t cap = (size_t)cfg->sp[s].capacity;
         capmax = capmax > (int64_t)cap ? capmax : (int64_t)cap;
         for (int b = 0; b < 2; ++b) {
             CKC(cudaMalloc(&c->buf[s][b].cell, cap * sizeof(uint32_t) + 16));
-            for (int k = 0; k < 9; ++k) CKC(cudaMalloc(&c->buf[s][b].f[k], cap * sizeof(float) + 16));
+            for (int k = 0; k < 9; ++k) CKC(cudaMalloc(&c->buf[s][b].f[k], cap * rb + 16));
             CKC(cudaMalloc(&c->buf[s][b].id, cap * sizeof(int32_t) + 16));
         }
         CKC(cudaMalloc(&c->tile_start[s], (c->ntiles + 1) * sizeof(int32_t)));
@@ -315,6 +337,8 @@ pic_status_t pic_create(const pic_config_t *cfg, void *stream, void **ctx_out) {
     CKC(cudaMalloc(&c->n_dev, (PIC_MAX_SPECIES + 1) * sizeof(int32_t)));
     CKC(cudaMemsetAsync(c->n_dev, 0, (PIC_MAX_SPECIES + 1) * sizeof(int32_t), st));
     CKC(cudaMalloc(&c->scratch_i32, 2 * (size_t)capmax * sizeof(int32_t) + 16));
+    c->stage_elems = std::max((size_t)capmax, c->plane);
+    CKC(cudaMalloc(&c->stage, c->stage_elems * sizeof(double) + 16));
     CKC(cudaMalloc(&c->err, sizeof(unsigned)));
     CKC(cudaMemsetAsync(c->err, 0, sizeof(unsigned), st));
     CKC(cudaMalloc(&c->partials, (size_t)reduce_blocks() * 8 * sizeof(double)));
@@ -346,6 +370,7 @@ void pic_destroy(void *ctx) {
     cudaFree(c->bnd);
     cudaFree(c->rho);
     cudaFree(c->rho_bg);
+    cudaFree(c->stage);
     for (int s = 0; s < PIC_MAX_SPECIES; ++s) {
         for (int b = 0; b < 2; ++b) {
             cudaFree(c->buf[s][b].cell);
@@ -402,8 +427,15 @@ pic_status_t pic_set_particles(void *ctx, int s, const pic_particles_t *p, void 
     if (n) {
         CK(cudaMemcpyAsync(dix, p->ix, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(diy, p->iy, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        for (int k = 0; k < 9; ++k)
-            CK(cudaMemcpyAsync(B.f[k], src[k], n * sizeof(float), cudaMemcpyHostToDevice, st));
+        for (int k = 0; k < 9; ++k) {
+            if (c->rb == 4) {
+                CK(cudaMemcpyAsync(B.f[k], src[k], n * sizeof(float), cudaMemcpyHostToDevice, st));
+            } else {  // FP64 instantiation: widen on the device
+                CK(cudaMemcpyAsync(c->stage, src[k], n * sizeof(float), cudaMemcpyHostToDevice, st));
+                CK(launch_convert<float, double>(static_cast<float *>(c->stage), static_cast<double *>(B.f[k]), n, st));
+                c->launches += 1;
+            }
+        }
         CK(cudaMemcpyAsync(B.id, p->id, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     }
     const int xlo = c->cfg.bc_x == PIC_BC_OPEN ? 2 : 0;
@@ -439,12 +471,14 @@ pic_status_t pic_get_count(void *ctx, int s, int64_t *n) {
     return r;
 }
 
-pic_status_t pic_get_particles(void *ctx, int s, pic_particles_t *out, void *stream) {
-    Ctx *c = static_cast<Ctx *>(ctx);
-    if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
+}  // extern "C"
+
+// particle slots of one species -> host arrays of float (OutT = float) or
+// double (OutT = double), whatever the context's precision
+template <typename OutT, typename PT>
+static pic_status_t get_particles_t(Ctx *c, int s, PT *out, cudaStream_t st) {
     if (s < 0 || s >= c->cfg.nspecies || !out) return fail(c, PIC_ERR_ARG, "bad species or output");
     if (c->pending_deposit) return fail(c, PIC_ERR_STATE, "a move is waiting for pic_deposit");
-    cudaStream_t st = S(stream);
     int32_t nv = 0;
     pic_status_t rc = read_count(c, s, st, &nv);
     if (rc != PIC_OK) return rc;
@@ -452,7 +486,7 @@ pic_status_t pic_get_particles(void *ctx, int s, pic_particles_t *out, void *str
     if ((int64_t)n > out->n) return fail(c, PIC_ERR_ARG, "output arrays too small");
     out->n = (int64_t)n;
     if (!n) return PIC_OK;
-    float *dst[9] = {out->ox, out->oy, out->ux, out->uy, out->uz, out->sx, out->sy, out->sz, out->w};
+    OutT *dst[9] = {out->ox, out->oy, out->ux, out->uy, out->uz, out->sx, out->sy, out->sz, out->w};
     if (!out->ix || !out->iy || !out->id) return fail(c, PIC_ERR_ARG, "null output array");
     for (int k = 0; k < 9; ++k)
         if (!dst[k]) return fail(c, PIC_ERR_ARG, "null output array");
@@ -462,51 +496,117 @@ pic_status_t pic_get_particles(void *ctx, int s, pic_particles_t *out, void *str
     c->launches += 1;
     CK(cudaMemcpyAsync(out->ix, dix, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(out->iy, diy, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    for (int k = 0; k < 9; ++k)
-        CK(cudaMemcpyAsync(dst[k], B.f[k], n * sizeof(float), cudaMemcpyDeviceToHost, st));
+    for (int k = 0; k < 9; ++k) {
+        if ((size_t)c->rb == sizeof(OutT)) {
+            CK(cudaMemcpyAsync(dst[k], B.f[k], n * sizeof(OutT), cudaMemcpyDeviceToHost, st));
+        } else {
+            if (c->rb == 8)
+                CK(launch_convert<double, float>(static_cast<const double *>(B.f[k]), static_cast<float *>(c->stage), n, st));
+            else
+                CK(launch_convert<float, double>(static_cast<const float *>(B.f[k]), static_cast<double *>(c->stage), n, st));
+            c->launches += 1;
+            CK(cudaMemcpyAsync(dst[k], c->stage, n * sizeof(OutT), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));  // stage is reused by the next array
+        }
+    }
     CK(cudaMemcpyAsync(out->id, B.id, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     return PIC_OK;
 }
 
-static pic_status_t copy_fields(Ctx *c, pic_fields_t *f, bool to_dev, cudaStream_t st) {
-    float *host[9] = {f->ex, f->ey, f->ez, f->bx, f->by, f->bz, f->jx, f->jy, f->jz};
+extern "C" {
+
+pic_status_t pic_get_particles(void *ctx, int s, pic_particles_t *out, void *stream) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
+    return get_particles_t<float>(c, s, out, S(stream));
+}
+
+pic_status_t pic_get_particles_f64(void *ctx, int s, pic_particles_f64_t *out, void *stream) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
+    return get_particles_t<double>(c, s, out, S(stream));
+}
+
+}  // extern "C"
+
+// one pitched device array of `rows` x `cols` reals <-> a dense host array of
+// HostT, converting through the staging buffer when the types differ
+template <typename HostT>
+static pic_status_t xfer_plane(Ctx *c, HostT *host, void *dev, size_t rows, size_t cols, size_t pitch_elems,
+                               bool to_dev, cudaStream_t st) {
+    const size_t hp = cols * sizeof(HostT);
+    if ((size_t)c->rb == sizeof(HostT)) {
+        if (to_dev)
+            CK(cudaMemcpy2DAsync(dev, pitch_elems * c->rb, host, hp, hp, rows, cudaMemcpyHostToDevice, st));
+        else
+            CK(cudaMemcpy2DAsync(host, hp, dev, pitch_elems * c->rb, hp, rows, cudaMemcpyDeviceToHost, st));
+        return PIC_OK;
+    }
+    const size_t total = rows * pitch_elems;
+    if (total > c->stage_elems) return fail(c, PIC_ERR_CUDA, "staging buffer too small");
+    if (to_dev) {
+        CK(cudaMemcpy2DAsync(c->stage, pitch_elems * sizeof(HostT), host, hp, hp, rows, cudaMemcpyHostToDevice, st));
+        if (c->rb == 8)
+            CK(launch_convert<float, double>(static_cast<const float *>(c->stage), static_cast<double *>(dev), total, st));
+        else
+            CK(launch_convert<double, float>(static_cast<const double *>(c->stage), static_cast<float *>(dev), total, st));
+    } else {
+        if (c->rb == 8)
+            CK(launch_convert<double, float>(static_cast<const double *>(dev), static_cast<float *>(c->stage), total, st));
+        else
+            CK(launch_convert<float, double>(static_cast<const float *>(dev), static_cast<double *>(c->stage), total, st));
+        CK(cudaMemcpy2DAsync(host, hp, c->stage, pitch_elems * sizeof(HostT), hp, rows, cudaMemcpyDeviceToHost, st));
+    }
+    c->launches += 1;
+    CK(cudaStreamSynchronize(st));  // the stage is reused by the next plane
+    return PIC_OK;
+}
+
+template <typename HostT, typename FT>
+static pic_status_t copy_fields(Ctx *c, FT *f, bool to_dev, cudaStream_t st) {
+    HostT *host[9] = {f->ex, f->ey, f->ez, f->bx, f->by, f->bz, f->jx, f->jy, f->jz};
     const size_t nx = c->cfg.nx, ny = c->cfg.ny;
     for (int k = 0; k < 9; ++k) {
         if (!host[k]) continue;
-        float *d = k < 6 ? c->EB + k * c->plane : c->J + (k - 6) * c->plane;
-        if (to_dev)
-            CK(cudaMemcpy2DAsync(d, c->ld * sizeof(float), host[k], nx * sizeof(float), nx * sizeof(float), ny,
-                                 cudaMemcpyHostToDevice, st));
-        else
-            CK(cudaMemcpy2DAsync(host[k], nx * sizeof(float), d, c->ld * sizeof(float), nx * sizeof(float), ny,
-                                 cudaMemcpyDeviceToHost, st));
+        char *base = static_cast<char *>(k < 6 ? c->EB : c->J);
+        void *d = base + (size_t)(k < 6 ? k : k - 6) * c->plane * c->rb;
+        pic_status_t r = xfer_plane<HostT>(c, host[k], d, ny, nx, c->ld, to_dev, st);
+        if (r != PIC_OK) return r;
     }
-    float *lb[2] = {f->by_left, f->bz_left};
+    HostT *lb[2] = {f->by_left, f->bz_left};
     for (int k = 0; k < 2; ++k) {
         if (!lb[k]) continue;
-        if (to_dev)
-            CK(cudaMemcpyAsync(c->bnd + k * ny, lb[k], ny * sizeof(float), cudaMemcpyHostToDevice, st));
-        else
-            CK(cudaMemcpyAsync(lb[k], c->bnd + k * ny, ny * sizeof(float), cudaMemcpyDeviceToHost, st));
+        void *d = static_cast<char *>(c->bnd) + (size_t)k * ny * c->rb;
+        pic_status_t r = xfer_plane<HostT>(c, lb[k], d, 1, ny, ny, to_dev, st);
+        if (r != PIC_OK) return r;
     }
     CK(cudaStreamSynchronize(st));
     return PIC_OK;
 }
+
+extern "C" {
 
 pic_status_t pic_set_fields(void *ctx, const pic_fields_t *f, void *stream) {
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
     if (!f) return fail(c, PIC_ERR_ARG, "null fields");
     pic_fields_t tmp = *f;
-    return copy_fields(c, &tmp, true, S(stream));
+    return copy_fields<float>(c, &tmp, true, S(stream));
 }
 
 pic_status_t pic_get_fields(void *ctx, pic_fields_t *f, void *stream) {
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
     if (!f) return fail(c, PIC_ERR_ARG, "null fields");
-    return copy_fields(c, f, false, S(stream));
+    return copy_fields<float>(c, f, false, S(stream));
+}
+
+pic_status_t pic_get_fields_f64(void *ctx, pic_fields_f64_t *f, void *stream) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
+    if (!f) return fail(c, PIC_ERR_ARG, "null fields");
+    return copy_fields<double>(c, f, false, S(stream));
 }
 
 pic_status_t pic_set_step(void *ctx, int64_t step) {
@@ -533,10 +633,12 @@ pic_status_t pic_gather_push_spin(void *ctx, void *stream) {
         pic_status_t r = alloc_old(c, s);
         if (r != PIC_OK) return r;
     }
-    StepParams P = step_params(c);
     for (int s = 0; s < c->cfg.nspecies; ++s)
         if (c->cfg.sp[s].mobile) {
-            CK(launch_push_split(P, s, c->n_upper[s], st));
+            CK(with_real(c, [&](auto z) {
+                using T = decltype(z);
+                return launch_push_split<T>(step_params<T>(c), s, c->n_upper[s], st);
+            }));
             c->launches += 1;
         }
     c->pending_deposit = true;
@@ -548,10 +650,12 @@ pic_status_t pic_deposit(void *ctx, void *stream) {
     if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
     if (!c->pending_deposit) return fail(c, PIC_ERR_STATE, "no pending move: call pic_gather_push_spin first");
     cudaStream_t st = S(stream);
-    StepParams P = step_params(c);
     for (int s = 0; s < c->cfg.nspecies; ++s)
         if (c->cfg.sp[s].mobile) {
-            CK(launch_deposit_split(P, s, c->n_upper[s], st));
+            CK(with_real(c, [&](auto z) {
+                using T = decltype(z);
+                return launch_deposit_split<T>(step_params<T>(c), s, c->n_upper[s], st);
+            }));
             c->launches += 1;
         }
     c->pending_deposit = false;
@@ -562,7 +666,11 @@ pic_status_t pic_field_update(void *ctx, void *stream) {
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
     if (c->pending_deposit) return fail(c, PIC_ERR_STATE, "a move is waiting for pic_deposit");
-    CK(launch_field_update(mesh(c), c->bnd, c->laser_prof, laser(c), c->dt, c->dx, c->dy, c->step, S(stream)));
+    CK(with_real(c, [&](auto z) {
+        using T = decltype(z);
+        return launch_field_update<T>(mesh<T>(c), static_cast<T *>(c->bnd), c->laser_prof, laser(c), c->dt, c->dx,
+                                      c->dy, c->step, S(stream));
+    }));
     c->launches += c->cfg.bc_x == PIC_BC_OPEN ? 4 : 3;
     c->step += 1;
     return PIC_OK;
@@ -572,19 +680,24 @@ pic_status_t pic_push_deposit(void *ctx, void *stream) {
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
     if (c->pending_deposit) return fail(c, PIC_ERR_STATE, "a move is waiting for pic_deposit");
-    StepParams P = step_params(c);
     const bool diag = c->diag_every > 0 && (c->step + 1) % c->diag_every == 0;
+    DiagParams D{};
     if (diag) {
-        P.diag.on = 1;
+        D.on = 1;
         for (int s = 0; s < c->cfg.nspecies; ++s) {
-            P.diag.lo[s] = c->diag_lo[s];
-            P.diag.hi[s] = c->diag_hi[s];
-            P.diag.m_mev[s] = (float)(c->cfg.sp[s].m * kMec2Mev);
+            D.lo[s] = c->diag_lo[s];
+            D.hi[s] = c->diag_hi[s];
+            D.m_mev[s] = c->cfg.sp[s].m * kMec2Mev;
         }
-        P.diag.shift = c->diag_shift;
-        P.diag.rows = c->diag_rows;
+        D.shift = c->diag_shift;
+        D.rows = c->diag_rows;
     }
-    CK(launch_step_fused(P, c->tmapEB, S(stream)));
+    CK(with_real(c, [&](auto z) {
+        using T = decltype(z);
+        StepParams<T> P = step_params<T>(c);
+        P.diag = D;
+        return launch_step_fused<T>(P, c->tmapEB, S(stream));
+    }));
     c->launches += 1;
     if (diag) {
         CK(launch_diag_final(c->diag_rows, c->ntiles, c->cfg.nspecies, c->diag_shift, c->diag_out, c->result,
@@ -602,8 +715,8 @@ pic_status_t pic_set_diagnostics(void *ctx, int every, const double *emin_mev, c
     for (int s = 0; s < c->cfg.nspecies; ++s) {
         const double lo = emin_mev ? emin_mev[s] : -INFINITY, hi = emax_mev ? emax_mev[s] : INFINITY;
         if (!(lo < hi)) return fail(c, PIC_ERR_ARG, "energy window must have emin < emax");
-        c->diag_lo[s] = std::isinf(lo) && lo < 0 ? -INFINITY : (float)lo;
-        c->diag_hi[s] = std::isinf(hi) && hi > 0 ? INFINITY : (float)hi;
+        c->diag_lo[s] = lo;
+        c->diag_hi[s] = hi;
     }
     c->diag_every = every;
     return PIC_OK;
@@ -662,10 +775,13 @@ pic_status_t pic_polarization(void *ctx, int s, double emin, double emax, pic_mo
     if (s < 0 || s >= c->cfg.nspecies || !out) return fail(c, PIC_ERR_ARG, "bad species or output");
     if (c->pending_deposit) return fail(c, PIC_ERR_STATE, "a move is waiting for pic_deposit");
     cudaStream_t st = S(stream);
-    DevSpecies d = dev_species(c, s, c->cur[s]);
-    const float lo = std::isinf(emin) && emin < 0 ? -INFINITY : (float)emin;
-    const float hi = std::isinf(emax) && emax > 0 ? INFINITY : (float)emax;
-    CK(launch_moments(d, (float)(c->cfg.sp[s].m * kMec2Mev), lo, hi, c->partials, c->result, st));
+    CK(with_real(c, [&](auto z) {
+        using T = decltype(z);
+        const T lo = std::isinf(emin) && emin < 0 ? -(T)INFINITY : (T)emin;
+        const T hi = std::isinf(emax) && emax > 0 ? (T)INFINITY : (T)emax;
+        return launch_moments<T>(dev_species<T>(c, s, c->cur[s]), (T)(c->cfg.sp[s].m * kMec2Mev), lo, hi,
+                                 c->partials, c->result, st);
+    }));
     c->launches += 4;
     double r[7];
     CK(cudaMemcpyAsync(r, c->result, 7 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -683,11 +799,16 @@ pic_status_t pic_capture_background(void *ctx, void *stream) {
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
     cudaStream_t st = S(stream);
-    MeshParams m = mesh(c);
-    CK(cudaMemsetAsync(c->rho, 0, c->plane * sizeof(float), st));
-    for (int s = 0; s < c->cfg.nspecies; ++s)
-        CK(launch_rho(dev_species(c, s, c->cur[s]), c->n_upper[s], m, c->rho, st));
-    CK(launch_negate_copy(c->rho, c->rho_bg, c->plane, st));
+    CK(cudaMemsetAsync(c->rho, 0, c->plane * c->rb, st));
+    CK(with_real(c, [&](auto z) {
+        using T = decltype(z);
+        for (int s = 0; s < c->cfg.nspecies; ++s) {
+            cudaError_t e = launch_rho<T>(dev_species<T>(c, s, c->cur[s]), c->n_upper[s], mesh<T>(c),
+                                          static_cast<T *>(c->rho), st);
+            if (e != cudaSuccess) return e;
+        }
+        return launch_negate_copy<T>(static_cast<const T *>(c->rho), static_cast<T *>(c->rho_bg), c->plane, st);
+    }));
     c->launches += c->cfg.nspecies + 1;
     return PIC_OK;
 }
@@ -698,14 +819,20 @@ pic_status_t pic_gauss_residual(void *ctx, double out[2], void *stream) {
     if (!out) return fail(c, PIC_ERR_ARG, "null output");
     if (c->pending_deposit) return fail(c, PIC_ERR_STATE, "a move is waiting for pic_deposit");
     cudaStream_t st = S(stream);
-    MeshParams m = mesh(c);
-    CK(cudaMemsetAsync(c->rho, 0, c->plane * sizeof(float), st));
-    for (int s = 0; s < c->cfg.nspecies; ++s)
-        CK(launch_rho(dev_species(c, s, c->cur[s]), c->n_upper[s], m, c->rho, st));
+    CK(cudaMemsetAsync(c->rho, 0, c->plane * c->rb, st));
     c->launches += c->cfg.nspecies + 2;
     const bool open = c->cfg.bc_x == PIC_BC_OPEN;
     const int i0 = open ? 3 : 0, i1 = open ? c->cfg.nx - 4 : c->cfg.nx - 1;
-    CK(launch_gauss(m, c->rho, c->rho_bg, c->dx, c->dy, i0, i1, c->partials, c->result, st));
+    CK(with_real(c, [&](auto z) {
+        using T = decltype(z);
+        for (int s = 0; s < c->cfg.nspecies; ++s) {
+            cudaError_t e = launch_rho<T>(dev_species<T>(c, s, c->cur[s]), c->n_upper[s], mesh<T>(c),
+                                          static_cast<T *>(c->rho), st);
+            if (e != cudaSuccess) return e;
+        }
+        return launch_gauss<T>(mesh<T>(c), static_cast<const T *>(c->rho), static_cast<const T *>(c->rho_bg),
+                               c->dx, c->dy, i0, i1, c->partials, c->result, st);
+    }));
     double r[2];
     CK(cudaMemcpyAsync(r, c->result, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));

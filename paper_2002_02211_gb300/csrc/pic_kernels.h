@@ -20,39 +20,49 @@ struct LaserParams {
 
 // k_particles.cu
 bool fused_tile_supported(int tx, int ty);
-cudaError_t launch_step_fused(const StepParams &P, const CUtensorMap &tmapEB, cudaStream_t st);
-cudaError_t launch_push_split(const StepParams &P, int s, int n_upper, cudaStream_t st);
-cudaError_t launch_deposit_split(const StepParams &P, int s, int n_upper, cudaStream_t st);
+template <typename R>
+cudaError_t launch_step_fused(const StepParams<R> &P, const CUtensorMap &tmapEB, cudaStream_t st);
+template <typename R>
+cudaError_t launch_push_split(const StepParams<R> &P, int s, int n_upper, cudaStream_t st);
+template <typename R>
+cudaError_t launch_deposit_split(const StepParams<R> &P, int s, int n_upper, cudaStream_t st);
 
 // k_fields.cu
-cudaError_t launch_field_update(const MeshParams &m, float *bnd, const double *prof, const LaserParams &L,
+template <typename R>
+cudaError_t launch_field_update(const MeshParams<R> &m, R *bnd, const double *prof, const LaserParams &L,
                                 double dt, double dx, double dy, long long step, cudaStream_t st);
 void laser_profile(const LaserParams &L, int ny, double *host);
 
 // k_sort.cu
-cudaError_t launch_pack_cells(const int32_t *ix, const int32_t *iy, uint32_t *cell, int n,
-                              int xlo, int xhi, int ny, unsigned *err, cudaStream_t st);
-cudaError_t launch_unpack_cells(const uint32_t *cell, int32_t *ix, int32_t *iy, int n,
-                                cudaStream_t st);
 struct SortScratch {
     int32_t *cell_count, *cell_off;  // [ntiles * TX * TY]
     int32_t *tile_R, *tile_total;    // [ntiles]
     int32_t *cursor;                 // [ntiles]
     int32_t *rank;                   // [n]
 };
-cudaError_t launch_tile_sort(const DevSpecies &src, const DevSpecies &dst, const TileGeom &t,
+cudaError_t launch_pack_cells(const int32_t *ix, const int32_t *iy, uint32_t *cell, int n,
+                              int xlo, int xhi, int ny, unsigned *err, cudaStream_t st);
+cudaError_t launch_unpack_cells(const uint32_t *cell, int32_t *ix, int32_t *iy, int n,
+                                cudaStream_t st);
+template <typename R>
+cudaError_t launch_tile_sort(const DevSpecies<R> &src, const DevSpecies<R> &dst, const TileGeom &t,
                              const SortScratch &w, int32_t *tile_start, int32_t *n_tmp, int n_upper,
                              cudaStream_t st);
+template <typename A, typename B>
+cudaError_t launch_convert(const A *src, B *dst, size_t n, cudaStream_t st);
 
 // k_reduce.cu
 int reduce_blocks();
-cudaError_t launch_moments(const DevSpecies &S, float m_mev, float emin, float emax,
-                           double *partials, double *result, cudaStream_t st);
-cudaError_t launch_rho(const DevSpecies &S, int n_upper, const MeshParams &m, float *rho, cudaStream_t st);
-cudaError_t launch_gauss(const MeshParams &m, const float *rho, const float *rho_bg, double dx,
-                         double dy, int i0, int i1, double *partials, double *result,
-                         cudaStream_t st);
-cudaError_t launch_negate_copy(const float *src, float *dst, size_t n, cudaStream_t st);
+template <typename R>
+cudaError_t launch_moments(const DevSpecies<R> &S, R m_mev, R emin, R emax, double *partials, double *result,
+                           cudaStream_t st);
+template <typename R>
+cudaError_t launch_rho(const DevSpecies<R> &S, int n_upper, const MeshParams<R> &m, R *rho, cudaStream_t st);
+template <typename R>
+cudaError_t launch_gauss(const MeshParams<R> &m, const R *rho, const R *rho_bg, double dx, double dy, int i0,
+                         int i1, double *partials, double *result, cudaStream_t st);
+template <typename R>
+cudaError_t launch_negate_copy(const R *src, R *dst, size_t n, cudaStream_t st);
 cudaError_t launch_diag_final(const double *rows, int nrows, int nsp, double *shift, pic_moments_dev *out,
                               double *tot, cudaStream_t st);
 

@@ -7,9 +7,11 @@ import paper_2002_02211_gb300 as pic
 import workloads as W
 
 
-def make_pair(wl, fields=None, step=0, capacity_factor=1.0, sort_every=0, tile=(0, 0), parts=None):
+def make_pair(wl, fields=None, step=0, capacity_factor=1.0, sort_every=0, tile=(0, 0), parts=None,
+              precision=32):
     parts = W.generate_particles(wl) if parts is None else parts
-    cfg = pic.config_from_workload(wl, capacity_factor=capacity_factor, sort_every=sort_every, tile=tile)
+    cfg = pic.config_from_workload(wl, capacity_factor=capacity_factor, sort_every=sort_every, tile=tile,
+                                   precision=precision)
     sim = pic.Simulation(cfg)
     for s, d in enumerate(parts):
         sim.set_particles(s, d)
@@ -22,9 +24,9 @@ def make_pair(wl, fields=None, step=0, capacity_factor=1.0, sort_every=0, tile=(
     return sim, orc, parts
 
 
-def gpu_by_id(sim, s, n_total):
+def gpu_by_id(sim, s, n_total, f64=False):
     """GPU particles of species s reordered by id; removed ones flagged."""
-    g = sim.get_particles(s)
+    g = sim.get_particles_f64(s) if f64 else sim.get_particles(s)
     out = {k: np.full(n_total, np.nan) for k in ("x", "y", "ux", "uy", "uz", "sx", "sy", "sz")}
     alive = np.zeros(n_total, bool)
     ids = g["id"]
@@ -43,11 +45,11 @@ def periodic_diff(a, b, n):
     return d - n * np.round(d / n)
 
 
-def compare_particles(sim, orc, s, u_tol=1e-5, s_tol=1e-5, x_tol=1e-5, u_floor=1e-3):
+def compare_particles(sim, orc, s, u_tol=1e-5, s_tol=1e-5, x_tol=1e-5, u_floor=1e-3, f64=False):
     """Per-particle comparison: u relative (floor u_floor), s absolute, x in cells."""
     p = orc.p[s]
     n = len(p["x"])
-    g, alive = gpu_by_id(sim, s, n)
+    g, alive = gpu_by_id(sim, s, n, f64=f64)
     oal = p["alive"].astype(bool)
     assert np.array_equal(alive, oal), f"alive sets differ: {np.sum(alive != oal)} particles"
     if not alive.any():
@@ -70,8 +72,8 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a))
 
 
-def compare_fields(sim, orc, keys, tol, region=None):
-    f = sim.get_fields()
+def compare_fields(sim, orc, keys, tol, region=None, f64=False):
+    f = sim.get_fields_f64() if f64 else sim.get_fields()
     errs = {}
     for k in keys:
         a, b = f[k].astype(np.float64), orc.f[k]
