@@ -60,6 +60,7 @@ def parse(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=10, help="timed steps of the FP64 line (0: skip)")
     return ap.parse_args(argv)
 
 
@@ -213,7 +214,40 @@ def cpu_baseline(wl):
     sim, n, desc = cpu_sample(wl)
     dt = run_oracle_steps(sim, CPU_SAMPLE_STEPS)
     return {"value": n * CPU_SAMPLE_STEPS / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{CPU_SAMPLE_STEPS} steps of {desc}", "seconds": round(dt, 2)}
+            "sample": f"{CPU_SAMPLE_STEPS} steps of {desc}", "seconds": round(dt, 2)}, sim
+
+
+def precision_study(pic, wl, oracle_sim):
+    """The CPU-baseline sample run on the GPU in FP32 and FP64: largest error
+    of every particle against the FP64 oracle after the same steps, and the
+    error of the Eq. (4) polarization of each species."""
+    sample = W.scaled(wl, ny=CPU_SAMPLE_NY)
+    parts = W.generate_particles(sample)
+    out = {}
+    for prec in (32, 64):
+        with pic.Simulation(pic.config_from_workload(sample, precision=prec)) as sim:
+            for s, d in enumerate(parts):
+                sim.set_particles(s, d)
+            sim.step(CPU_SAMPLE_STEPS)
+            du = ds = dx = dp = 0.0
+            for s in range(len(parts)):
+                g = sim.get_particles_f64(s)
+                o = oracle_sim.p[s]
+                live = g["ix"] >= 0
+                ids = g["id"][live]
+                ok = o["alive"][ids] > 0
+                ids = ids[ok]
+                sel = np.flatnonzero(live)[ok]
+                un = np.maximum(np.sqrt(sum(o[k][ids] ** 2 for k in ("ux", "uy", "uz"))), 1e-3)
+                du = max(du, float((np.sqrt(sum((g[k][sel] - o[k][ids]) ** 2 for k in ("ux", "uy", "uz"))) / un).max()))
+                ds = max(ds, float(np.sqrt(sum((g[k][sel] - o[k][ids]) ** 2 for k in ("sx", "sy", "sz"))).max()))
+                dx = max(dx, float(np.abs(g["ix"][sel] + g["ox"][sel] - o["x"][ids]).max()))
+                gm = sim.polarization(s)
+                om = oracle_sim.moments(s)
+                dp = max(dp, float(np.abs(gm["P"] - om[:3]).max()))
+            out[f"fp{prec}"] = {"u_rel_max": du, "s_abs_max": ds, "x_cells_max": dx, "P_abs_max": dp}
+    out["sample"] = f"{CPU_SAMPLE_STEPS} steps of {sample.name} ny={CPU_SAMPLE_NY}, every particle"
+    return out
 
 
 def main_reference(args):
@@ -354,11 +388,38 @@ def main_ours(args):
                        "(H2D + tile sort), pic_push_deposit, pic_field_update, pic_polarization "
                        "of every species (D2H)"}
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(wl)
-
     sim.close()
+
+    # FP64 instantiation of the same step on the same workload
+    fp64 = None
+    if args.precision == 32 and args.fp64_steps > 0:
+        cfg64 = pic.config_from_workload(wl, sort_every=args.sort_every, tile=tuple(args.tile), precision=64)
+        with pic.Simulation(cfg64, stream=stream) as s64:
+            for s, d in enumerate(parts):
+                s64.set_particles(s, d)
+            s64.set_diagnostics(args.diag_every)
+            for _ in range(2):
+                s64.step(1)
+            s64.sync()
+            barrier(world)
+            torch.cuda.synchronize(dev)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s64.step(args.fp64_steps)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            t64, u64 = combine(a.elapsed_time(b) * 1e-3, n_particles * args.fp64_steps, world, dev)
+            s64.sync()
+        fp64 = {"value": u64 / t64, "unit": UNIT, "ms_per_step": t64 * 1e3 / args.fp64_steps,
+                "steps": args.fp64_steps, "dtype": "f64",
+                "bound": "alu (FP64 arithmetic; GB300 FP64 is about 1/64 of its FP32 rate)"}
+
+    cpu = None
+    study = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu, orc_sample = cpu_baseline(wl)
+        study = precision_study(pic, wl, orc_sample)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": tmax * 1e3 / args.steps,
@@ -371,7 +432,7 @@ def main_ours(args):
                            "l2": "inputs larger than L2 (particle state 2.95 GB)",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "gpu_launches": launches,
+                "gpu_launches": launches, "fp64": fp64, "precision_study": study,
                 "diagnostics": {"step": diag_step,
                                 "P": {sp.name: [round(v, 6) for v in d["P"]] for sp, d in zip(wl.species, diag)},
                                 "ekin_mean_mev": {sp.name: d["ekin_mean"] for sp, d in zip(wl.species, diag)}}}

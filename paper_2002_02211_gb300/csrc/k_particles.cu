@@ -72,9 +72,9 @@ __device__ __forceinline__ bool finish_move(const MeshParams<R> &m, int &ix1, in
 // ---------------------------------------------------------------------------
 // Fused step kernel.  CTA = one tile of TX x TY cells (compile-time, so every
 // shared-memory offset below is an immediate).  Thread 0 stages the
-// 6-component field window (4 cells of margin before the tile in x and y,
-// at least 4 after, rows padded to a multiple of 32 floats) with one 3D TMA
-// load (zero fill outside the mesh).  Particle records of the tile (both
+// 6-component field window (rows padded to 128 bytes with the padding split
+// between the two sides of the tile, at least 4 cells each; 6 cells of
+// margin along y) with one 3D TMA load (zero fill outside the mesh).  Particle records of the tile (both
 // species, one slot range after the other) stream through a two-deep
 // cp.async ring in shared memory: while a thread computes one record it has
 // the next one in flight.  Each record runs a1-a5, gathering from and
@@ -92,6 +92,7 @@ constexpr int kRec = 9;  // staged reals per particle: ox oy ux uy uz sx sy sz w
 template <int TX, int TY, typename R>
 struct TileConst {
     static constexpr int WX = window_wx<R>(TX), WY = window_wy(TY), WA = WX * WY;
+    static constexpr int HX = window_hx<R>(TX), HY = window_hy();
     // field window, current window, and a two-stage ring of cell words and reals
     static constexpr size_t smem_bytes =
         (size_t)9 * WA * sizeof(R) + 2 * kFusedThreads * (sizeof(uint32_t) + kRec * sizeof(R));
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(kFusedThreads, sizeof(R) == 4 ? PIC_FUSED_MINB
 
     const int tile = blockIdx.x;
     const int ty = tile / P.t.ntx, tx = tile - ty * P.t.ntx;
-    const int wx0 = tx * TX - PIC_HALO, wy0 = ty * TY - PIC_HALO;
+    const int wx0 = tx * TX - TC::HX, wy0 = ty * TY - TC::HY;
     const int tid = threadIdx.x;
 
     if (tid == 0) {
@@ -430,7 +431,7 @@ template <int TX, int TY, typename R>
 static cudaError_t launch_fused_t(const StepParams<R> &P, const CUtensorMap &tmapEB, cudaStream_t st) {
     using TC = TileConst<TX, TY, R>;
     constexpr size_t smem = TC::smem_bytes;
-    if (P.t.WX != TC::WX || P.t.WY != TC::WY) return cudaErrorInvalidValue;
+    if (P.t.WX != TC::WX || P.t.WY != TC::WY || P.t.HX != TC::HX || P.t.HY != TC::HY) return cudaErrorInvalidValue;
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(k_step_fused<TX, TY, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -174,6 +174,8 @@ void choose_tiles(Ctx *c) {
     c->tg.TY = ty;
     c->tg.WX = c->rb == 8 ? window_wx<double>(tx) : window_wx<float>(tx);
     c->tg.WY = window_wy(ty);
+    c->tg.HX = c->rb == 8 ? window_hx<double>(tx) : window_hx<float>(tx);
+    c->tg.HY = window_hy();
     c->tg.ntx = (c->cfg.nx + tx - 1) / tx;
     c->tg.nty = (c->cfg.ny + ty - 1) / ty;
     c->ntiles = c->tg.ntx * c->tg.nty;

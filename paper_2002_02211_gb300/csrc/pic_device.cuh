@@ -24,7 +24,8 @@
 #define PIC_EF_RANGE 8u
 
 #define PIC_MAXSP 4
-#define PIC_HALO 4   // window margin around a tile, in cells, on every side
+#define PIC_HALO 4     // least window margin around a tile along x, in cells
+#define PIC_HALO_Y 4   // window margin along y, in cells
 
 // precision-specific intrinsics
 template <typename R>
@@ -78,6 +79,8 @@ struct TileGeom {
     int TX, TY;                    // tile size in cells
     int WX, WY;                    // window: x row stride (tile + 2 * PIC_HALO rounded up to
                                    // 128 bytes, so a row shift never changes a bank), y rows
+    int HX, HY;                    // window margins before the tile (the window starts at
+                                   // tile origin - (HX, HY)); HX is a multiple of 4 (TMA)
     int ntx, nty;                  // tiles along x and y
 };
 
@@ -85,7 +88,11 @@ template <typename R>
 __host__ __device__ constexpr int window_wx(int tx) {
     return (tx + 2 * PIC_HALO + (int)(128 / sizeof(R)) - 1) / (int)(128 / sizeof(R)) * (int)(128 / sizeof(R));
 }
-__host__ __device__ constexpr int window_wy(int ty) { return ty + 2 * PIC_HALO; }
+// the row padding is split evenly between the two sides of the tile
+template <typename R>
+__host__ __device__ constexpr int window_hx(int tx) { return (window_wx<R>(tx) - tx) / 2 / 4 * 4; }
+__host__ __device__ constexpr int window_wy(int ty) { return ty + 2 * PIC_HALO_Y; }
+__host__ __device__ constexpr int window_hy() { return PIC_HALO_Y; }
 
 // Eq. (4) moments accumulated inside the fused kernel on diagnostic steps:
 // per species and CTA the sums w, w s (3), w e', w e'^2, count over live
