@@ -227,6 +227,17 @@ pic_status_t pic_get_diagnostics(void *ctx, pic_moments_t *out, int64_t *step, v
 pic_status_t pic_polarization(void *ctx, int species, double emin_mev, double emax_mev,
                               pic_moments_t *out, void *stream);
 
+/* Energy spectra of one species (the dN/dE and dP/dE panels of Figs. 1-3):
+ * live particles with kinetic energy in [emin, emax) MeV go to one of nbins
+ * bins (1 <= nbins <= PIC_MAX_HIST_BINS), equal in energy (log_bins = 0) or
+ * in log energy (log_bins != 0, emin > 0).  out[5 b + 0..4] (host) = count,
+ * sum w, sum w sx, sum w sy, sum w sz of bin b; dN/dE = sum w / bin width and
+ * dP/dE = (sum w s) / (sum w) per bin (Eq. 4 over the bin).  Per-block float
+ * sums, FP64 across blocks.  Synchronous. */
+#define PIC_MAX_HIST_BINS 1024
+pic_status_t pic_energy_histogram(void *ctx, int species, double emin_mev, double emax_mev, int nbins,
+                                  int log_bins, double *out, void *stream);
+
 /* Sets the immobile background charge to minus the CIC charge density of
  * the current particles (a neutral start).  Asynchronous. */
 pic_status_t pic_capture_background(void *ctx, void *stream);

@@ -92,6 +92,7 @@ def lib():
             "or_div_e": (None, [G, F, _DP]),
             "or_div_b": (None, [G, F, _DP]),
             "or_moments": (None, [S, P, C.c_double, C.c_double, _DP]),
+            "or_histogram": (None, [S, P, C.c_double, C.c_double, C.c_int, C.c_int, _DP]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -255,6 +256,14 @@ class OracleSim:
         pp = self._parts(s)
         lib().or_moments(C.byref(self.spec[s]), C.byref(pp), float(emin), float(emax), out)
         return np.array(out[:])
+
+    def histogram(self, s, emin, emax, nbins, log_bins=False):
+        """[nbins][5]: count, sum w, sum w s (3) per kinetic-energy bin."""
+        out = np.zeros(5 * nbins)
+        pp = self._parts(s)
+        lib().or_histogram(C.byref(self.spec[s]), C.byref(pp), float(emin), float(emax), int(nbins),
+                           1 if log_bins else 0, _dp(out))
+        return out.reshape(nbins, 5)
 
     def laser(self, t, y, comp):
         v = C.c_double()

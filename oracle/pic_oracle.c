@@ -488,3 +488,33 @@ void or_moments(const or_species_t *sp, const or_particles_t *p,
     out[5] = mean;
     out[6] = sw > 0 ? var / sw : 0.0;
 }
+
+/* Energy spectra behind Figs. 1-3 (c), (d): per kinetic-energy bin the
+ * particle count, the weight and the weighted spin; dP/dE of a bin is its
+ * sum w s / sum w (Eq. 4 restricted to the bin). */
+void or_histogram(const or_species_t *sp, const or_particles_t *p, double emin_mev,
+                  double emax_mev, int nbins, int log_bins, double *out)
+{
+    for (int b = 0; b < 5 * nbins; ++b)
+        out[b] = 0.0;
+    for (long i = 0; i < p->n; ++i) {
+        if (!p->alive[i])
+            continue;
+        double u[3] = {p->ux[i], p->uy[i], p->uz[i]};
+        double ek = (sqrt(1.0 + dot3(u, u)) - 1.0) * sp->m * MEC2_MEV;
+        if (ek < emin_mev || ek >= emax_mev)
+            continue;
+        double f = log_bins ? log(ek / emin_mev) / log(emax_mev / emin_mev)
+                            : (ek - emin_mev) / (emax_mev - emin_mev);
+        int b = (int)floor(f * nbins);
+        if (b < 0)
+            b = 0;
+        if (b >= nbins)
+            b = nbins - 1;
+        out[5 * b + 0] += 1.0;
+        out[5 * b + 1] += p->w[i];
+        out[5 * b + 2] += p->w[i] * p->sx[i];
+        out[5 * b + 3] += p->w[i] * p->sy[i];
+        out[5 * b + 4] += p->w[i] * p->sz[i];
+    }
+}

@@ -103,6 +103,13 @@ void or_div_b(const or_grid_t *g, const or_fields_t *f, double *div);
 void or_moments(const or_species_t *sp, const or_particles_t *p,
                 double emin_mev, double emax_mev, double out[7]);
 
+/* Energy spectra (the dN/dE and dP/dE panels of Figs. 1-3): live particles
+ * with kinetic energy in [emin, emax) go to one of nbins bins, equal in
+ * energy (log_bins = 0) or in log energy (log_bins = 1, emin > 0);
+ * out[5 b + 0..4] = count, sum w, sum w sx, sum w sy, sum w sz of bin b. */
+void or_histogram(const or_species_t *sp, const or_particles_t *p, double emin_mev,
+                  double emax_mev, int nbins, int log_bins, double *out);
+
 #ifdef __cplusplus
 }
 #endif

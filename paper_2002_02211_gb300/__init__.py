@@ -108,6 +108,8 @@ _SIGS = {
     "pic_polarization": [C.c_void_p, C.c_int, C.c_double, C.c_double, C.POINTER(pic_moments_t),
                          C.c_void_p],
     "pic_capture_background": [C.c_void_p, C.c_void_p],
+    "pic_energy_histogram": [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
+                             C.POINTER(C.c_double), C.c_void_p],
     "pic_gauss_residual": [C.c_void_p, C.POINTER(C.c_double), C.c_void_p],
     "pic_sync": [C.c_void_p, C.c_void_p],
     "pic_set_diagnostics": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
@@ -347,6 +349,13 @@ class Simulation:
         self._c(load().pic_get_diagnostics(self.h, out, C.byref(st), self._s))
         return st.value, [dict(P=np.array(m.P[:]), sum_w=m.sum_w, count=m.count, ekin_mean=m.ekin_mean,
                                ekin_var=m.ekin_var) for m in out]
+
+    def energy_histogram(self, s, emin, emax, nbins, log_bins=False):
+        """[nbins][5]: count, sum w, sum w s (3) per kinetic-energy bin."""
+        out = np.zeros(5 * nbins)
+        self._c(load().pic_energy_histogram(self.h, s, float(emin), float(emax), int(nbins),
+                                            1 if log_bins else 0, _ptr(out, C.POINTER(C.c_double)), self._s))
+        return out.reshape(nbins, 5)
 
     def capture_background(self):
         self._c(load().pic_capture_background(self.h, self._s))

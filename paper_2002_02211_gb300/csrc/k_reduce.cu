@@ -227,9 +227,52 @@ __global__ void k_diag_moments(const double *tot, int nsp, double *shift, pic_mo
     if (sw > 0) shift[sp] = sh + d;
 }
 
+// Energy spectra: each block bins its particles in shared memory (float, a
+// few thousand particles per block), then adds its bins to the FP64
+// histogram out[nbins][5] (count, sum w, sum w s) with global atomics.
+template <typename R>
+__global__ void __launch_bounds__(RT) k_hist(const DevSpecies<R> S, R m_mev, R emin, R emax, int nbins,
+                                             int log_bins, double *out) {
+    extern __shared__ float sh[];  // [nbins][5]
+    for (int i = threadIdx.x; i < 5 * nbins; i += blockDim.x) sh[i] = 0.f;
+    __syncthreads();
+    const int n = *S.n;
+    const R scale = log_bins ? R(1) / log(emax / emin) : R(1) / (emax - emin);
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        if (S.cell[p] == PIC_DEAD) continue;
+        const R e = ekin(m_mev, S.ux[p], S.uy[p], S.uz[p]);
+        if (!(e >= emin && e < emax)) continue;
+        const R f = log_bins ? log(e / emin) * scale : (e - emin) * scale;
+        int b = (int)floor(f * (R)nbins);
+        b = b < 0 ? 0 : (b >= nbins ? nbins - 1 : b);
+        const float w = (float)S.w[p];
+        atomicAdd(&sh[5 * b + 0], 1.f);
+        atomicAdd(&sh[5 * b + 1], w);
+        atomicAdd(&sh[5 * b + 2], w * (float)S.sx[p]);
+        atomicAdd(&sh[5 * b + 3], w * (float)S.sy[p]);
+        atomicAdd(&sh[5 * b + 4], w * (float)S.sz[p]);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 5 * nbins; i += blockDim.x)
+        if (sh[i] != 0.f) atomicAdd(&out[i], (double)sh[i]);
+}
+
 }  // namespace
 
 int reduce_blocks() { return RB; }
+
+template <typename R>
+cudaError_t launch_histogram(const DevSpecies<R> &S, R m_mev, R emin, R emax, int nbins, int log_bins,
+                             double *out, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double) * 5 * nbins, st);
+    if (e != cudaSuccess) return e;
+    k_hist<R><<<152 * 32, RT, sizeof(float) * 5 * nbins, st>>>(S, m_mev, emin, emax, nbins, log_bins, out);
+    return cudaGetLastError();
+}
+template cudaError_t launch_histogram<float>(const DevSpecies<float> &, float, float, float, int, int, double *,
+                                             cudaStream_t);
+template cudaError_t launch_histogram<double>(const DevSpecies<double> &, double, double, double, int, int,
+                                              double *, cudaStream_t);
 
 cudaError_t launch_diag_final(const double *rows, int nrows, int nsp, double *shift, pic_moments_dev *out,
                               double *tot, cudaStream_t st) {

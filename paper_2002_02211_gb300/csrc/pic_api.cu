@@ -51,6 +51,7 @@ struct Ctx {
     unsigned *err = nullptr;
     double *partials = nullptr, *result = nullptr;
     double *laser_prof = nullptr;  // [2][ny] transverse profile at y_j, y_{j+1/2}
+    double *hist = nullptr;        // [PIC_MAX_HIST_BINS][5] energy spectrum
     // in-step Eq. (4) diagnostics
     int diag_every = 0;
     double diag_lo[PIC_MAX_SPECIES] = {}, diag_hi[PIC_MAX_SPECIES] = {};
@@ -345,6 +346,7 @@ pic_status_t pic_create(const pic_config_t *cfg, void *stream, void **ctx_out) {
     CKC(cudaMemsetAsync(c->err, 0, sizeof(unsigned), st));
     CKC(cudaMalloc(&c->partials, (size_t)reduce_blocks() * 8 * sizeof(double)));
     CKC(cudaMalloc(&c->result, 64 * sizeof(double)));  // moments results and diagnostic column sums
+    CKC(cudaMalloc(&c->hist, (size_t)PIC_MAX_HIST_BINS * 5 * sizeof(double)));
     CKC(cudaMalloc(&c->diag_rows, (size_t)c->ntiles * PIC_MAX_SPECIES * 8 * sizeof(double)));
     CKC(cudaMalloc(&c->diag_shift, PIC_MAX_SPECIES * sizeof(double)));
     CKC(cudaMemsetAsync(c->diag_shift, 0, PIC_MAX_SPECIES * sizeof(double), st));
@@ -397,6 +399,7 @@ void pic_destroy(void *ctx) {
     cudaFree(c->diag_shift);
     cudaFree(c->diag_out);
     cudaFree(c->laser_prof);
+    cudaFree(c->hist);
     delete c;
 }
 
@@ -795,6 +798,26 @@ pic_status_t pic_polarization(void *ctx, int s, double emin, double emax, pic_mo
     out->ekin_mean = sw > 0 ? r[4] / sw : 0.0;
     out->ekin_var = sw > 0 ? r[6] / sw : 0.0;
     return fl;
+}
+
+pic_status_t pic_energy_histogram(void *ctx, int s, double emin, double emax, int nbins, int log_bins,
+                                  double *out, void *stream) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
+    if (s < 0 || s >= c->cfg.nspecies || !out) return fail(c, PIC_ERR_ARG, "bad species or output");
+    if (nbins < 1 || nbins > PIC_MAX_HIST_BINS) return fail(c, PIC_ERR_ARG, "nbins must be in [1, 1024]");
+    if (!(emin < emax) || !std::isfinite(emin) || !std::isfinite(emax) || (log_bins && !(emin > 0)))
+        return fail(c, PIC_ERR_ARG, "need finite emin < emax (and emin > 0 for log bins)");
+    if (c->pending_deposit) return fail(c, PIC_ERR_STATE, "a move is waiting for pic_deposit");
+    cudaStream_t st = S(stream);
+    CK(with_real(c, [&](auto z) {
+        using T = decltype(z);
+        return launch_histogram<T>(dev_species<T>(c, s, c->cur[s]), (T)(c->cfg.sp[s].m * kMec2Mev), (T)emin,
+                                   (T)emax, nbins, log_bins ? 1 : 0, c->hist, st);
+    }));
+    c->launches += 1;
+    CK(cudaMemcpyAsync(out, c->hist, sizeof(double) * 5 * nbins, cudaMemcpyDeviceToHost, st));
+    return check_flags(c, st);
 }
 
 pic_status_t pic_capture_background(void *ctx, void *stream) {

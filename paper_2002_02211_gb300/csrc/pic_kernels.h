@@ -63,6 +63,9 @@ cudaError_t launch_gauss(const MeshParams<R> &m, const R *rho, const R *rho_bg, 
                          int i1, double *partials, double *result, cudaStream_t st);
 template <typename R>
 cudaError_t launch_negate_copy(const R *src, R *dst, size_t n, cudaStream_t st);
+template <typename R>
+cudaError_t launch_histogram(const DevSpecies<R> &S, R m_mev, R emin, R emax, int nbins, int log_bins,
+                             double *out, cudaStream_t st);
 cudaError_t launch_diag_final(const double *rows, int nrows, int nsp, double *shift, pic_moments_dev *out,
                               double *tot, cudaStream_t st);
 

@@ -56,6 +56,8 @@ MUTATIONS = [
     ("boundary transverse sign at x_max",
      "f->by[cl] = (-2.0 * f->ez[cl] - (1.0 - r) * f->by[cl - 1] + q * dbxl) / (1.0 + r);",
      "f->by[cl] = (-2.0 * f->ez[cl] - (1.0 - r) * f->by[cl - 1] - q * dbxl) / (1.0 + r);"),
+    ("histogram bin rounding", "int b = (int)floor(f * nbins);", "int b = (int)floor(f * nbins + 0.5);"),
+    ("histogram spin unweighted", "out[5 * b + 3] += p->w[i] * p->sy[i];", "out[5 * b + 3] += p->sy[i];"),
     ("moments unweighted mean", "swy += p->w[i] * p->sy[i];", "swy += p->sy[i];"),
     ("energy uses total energy", "double ek = (sqrt(1.0 + dot3(u, u)) - 1.0) * sp->m * MEC2_MEV;\n        if (ek < emin_mev",
      "double ek = (sqrt(1.0 + dot3(u, u))) * sp->m * MEC2_MEV;\n        if (ek < emin_mev"),

@@ -579,3 +579,45 @@ def test_open_boundary_is_stable_for_2d_fields(oracle_mod, dy_lambda, cfl):
         es.append(energy())
     assert max(es) < 1.5 * e0, es
     assert es[-1] < e0, es
+
+
+def test_histogram_hand_built_spectrum(oracle_mod):
+    P, _ = _read_golden()
+    want = []
+    with open(os.path.join(GOLDEN, "histogram_dpde.txt")) as fh:
+        for line in fh:
+            t = line.split()
+            if t and t[0] == "bin":
+                want.append([float(v) for v in t[2:]])
+    sp = W.Species("e", q=-1.0, m=1.0, a=0.0, n0=0.01, ppc=1, u_th=0.0, s0=(1, 0, 0))
+    wl = W.Workload(name="h", nx=8, ny=8, dx_lambda=1 / 16, dy_lambda=1 / 16, cfl=0.95,
+                    steps=1, species=(sp,), pol="none", bc_x="periodic")
+    n, f32 = len(P), np.float32
+    d = dict(ix=np.full(n, 3, np.int32), iy=np.full(n, 3, np.int32), ox=np.full(n, 0.5, f32),
+             oy=np.full(n, 0.5, f32), ux=P[:, 0].astype(f32), uy=P[:, 1].astype(f32),
+             uz=P[:, 2].astype(f32), sx=P[:, 3].astype(f32), sy=P[:, 4].astype(f32),
+             sz=P[:, 5].astype(f32), w=np.array([1, 1, 2, 4], f32), id=np.arange(n, dtype=np.int32))
+    sim = oracle_mod.OracleSim(wl, [d])
+    np.testing.assert_allclose(sim.histogram(0, 0.0, 3.0, 3), np.array(want), atol=1e-15)
+
+
+@pytest.mark.parametrize("log_bins", [False, True])
+def test_histogram_sums_to_the_eq4_moments(oracle_mod, log_bins):
+    # summing the bins gives back the count, weight and weighted spin of the
+    # whole window (Eq. 4 over the window); dP/dE of one bin is Eq. (4) over it
+    wl = W.small_case(nx=24, ny=16, ppc=4, u_th=0.8, bc_x="periodic")
+    sim = oracle_mod.OracleSim(wl, W.generate_particles(wl))
+    sim.p[0]["sx"][:] = np.cos(np.arange(len(sim.p[0]["sx"])))
+    sim.p[0]["sy"][:] = np.sin(np.arange(len(sim.p[0]["sx"])))
+    emin, emax = (0.01, 0.5) if log_bins else (0.0, 0.5)
+    h = sim.histogram(0, emin, emax, 17, log_bins)
+    m = sim.moments(0, emin, emax)
+    assert h[:, 0].sum() == m[4]
+    assert h[:, 1].sum() == pytest.approx(m[3], rel=1e-13)
+    np.testing.assert_allclose(h[:, 2:5].sum(axis=0) / h[:, 1].sum(), m[:3], atol=1e-13)
+    b = int(np.argmax(h[:, 0]))
+    edges = (emin * (emax / emin) ** (np.arange(18) / 17) if log_bins
+             else emin + (emax - emin) * np.arange(18) / 17)
+    mb = sim.moments(0, edges[b], edges[b + 1])
+    assert h[b, 0] == mb[4]
+    np.testing.assert_allclose(h[b, 2:5] / h[b, 1], mb[:3], atol=1e-12)

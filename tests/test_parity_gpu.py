@@ -139,6 +139,39 @@ def test_in_step_diagnostics_match_polarization():
     sim.set_diagnostics(0)
 
 
+@pytest.mark.parametrize("precision", [32, 64])
+@pytest.mark.parametrize("log_bins", [False, True])
+def test_energy_histogram(precision, log_bins):
+    # on the generated state (identical inputs) and after steps: counts are
+    # exact except for particles within a relative 1e-5 of a bin edge (the
+    # bin is decided in the kernel's precision), sums within float rounding
+    wl = W.small_case(nx=48, ny=32, ppc=4, u_th=0.7, two_species=True)
+    f = W.random_fields(wl, seed=3, e_amp=0.2, b_amp=0.5)
+    sim, orc, _ = make_pair(wl, fields=f, precision=precision)
+    nb = 32
+    for stage in range(2):
+        for s in range(2):
+            m = wl.species[s].m
+            emin, emax = (1e-3 * m, 0.3 * m) if log_bins else (0.0, 0.3 * m)
+            g = sim.energy_histogram(s, emin, emax, nb, log_bins)
+            o = orc.histogram(s, emin, emax, nb, log_bins)
+            p = orc.p[s]
+            u2 = p["ux"] ** 2 + p["uy"] ** 2 + p["uz"] ** 2
+            e = u2 / (1 + np.sqrt(1 + u2)) * m * 0.51099895
+            edges = (emin * (emax / emin) ** (np.arange(nb + 1) / nb) if log_bins
+                     else emin + (emax - emin) * np.arange(nb + 1) / nb)
+            near = np.zeros(nb + 2)
+            for k, ed in enumerate(edges):
+                near[k] = np.sum((np.abs(e - ed) <= 1e-5 * max(abs(ed), 1e-12)) & (p["alive"] > 0))
+            slack = near[:-2] + near[1:-1] + 1e-9
+            assert np.all(np.abs(g[:, 0] - o[:, 0]) <= slack), (g[:, 0], o[:, 0])
+            assert g[:, 0].sum() >= o[:, 0].sum() - near.sum()
+            ok = np.abs(g[:, 0] - o[:, 0]) == 0
+            np.testing.assert_allclose(g[ok, 1:], o[ok, 1:], rtol=1e-4, atol=1e-7 * o[:, 1].max())
+        sim.step(3)
+        orc.step(3)
+
+
 def test_polarization_unchanged_without_fields():
     wl = W.small_case(nx=32, ny=16, ppc=2, pol="none", a0=0.0, u_th=0.0, bc_x="periodic")
     sim, orc, _ = make_pair(wl)
