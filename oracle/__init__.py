@@ -1,13 +1,13 @@
-"""FP64 CPU oracle of the 2D3V PIC + Thomas-BMT step (test infrastructure).
+"""FP64 CPU oracle of the 2D3V and 3D3V PIC + Thomas-BMT step (test infrastructure).
 
 TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the benchmark's
 CPU-baseline leg are the only users.  It does not import, link or share code
 with the CUDA library.
 
-The arithmetic is plain C (``pic_oracle.c``); this module builds it with gcc,
-derives the oracle's own units from a workload (length c/omega0, time
-1/omega0, dt = cfl / sqrt(1/dx^2 + 1/dy^2)) and holds the state in float64
-numpy arrays.
+The arithmetic is plain C (``pic_oracle.c`` for 2D3V, ``pic_oracle3.c`` for
+3D3V); this module builds it with gcc, derives the oracle's own units from a
+workload (length c/omega0, time 1/omega0, dt = cfl / sqrt(sum 1/dx_i^2)) and
+holds the state in float64 numpy arrays.
 """
 from __future__ import annotations
 
@@ -30,16 +30,18 @@ BC = {"open": 0, "periodic": 1}
 POL = {"none": 0, "lp-y": 1, "cp": 2}
 
 
+SOURCES = ("pic_oracle.c", "pic_oracle3.c")
+
+
 def build(force: bool = False) -> str:
-    """Compile pic_oracle.c into liboracle.so next to it (gcc, FP64, no FMA contraction)."""
-    src = os.path.join(_HERE, "pic_oracle.c")
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(src),
-                                                   os.path.getmtime(os.path.join(_HERE, "pic_oracle.h")))):
+    """Compile the oracle sources into liboracle.so next to them (gcc, FP64, no FMA contraction)."""
+    srcs = [os.path.join(_HERE, f) for f in SOURCES]
+    newest = max(os.path.getmtime(f) for f in srcs + [os.path.join(_HERE, "pic_oracle.h")])
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
         return _LIB_PATH
     tmp = _LIB_PATH + f".{os.getpid()}.tmp"
     subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-                           src, "-o", tmp, "-lm"])
+                           *srcs, "-o", tmp, "-lm"])
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -67,6 +69,22 @@ class Parts(C.Structure):
                                     ("x", "y", "ux", "uy", "uz", "sx", "sy", "sz", "w")] + [("alive", _IP)]
 
 
+class Grid3(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("dx", C.c_double),
+                ("dy", C.c_double), ("dz", C.c_double), ("dt", C.c_double), ("bc_x", C.c_int),
+                ("pol", C.c_int), ("a0", C.c_double), ("w0", C.c_double), ("tau", C.c_double),
+                ("t_peak", C.c_double)]
+
+
+class Fields3(C.Structure):
+    _fields_ = [(k, _DP) for k in ("ex", "ey", "ez", "bx", "by", "bz", "jx", "jy", "jz", "byL", "bzL")]
+
+
+class Parts3(C.Structure):
+    _fields_ = [("n", C.c_long)] + [(k, _DP) for k in
+                                    ("x", "y", "z", "ux", "uy", "uz", "sx", "sy", "sz", "w")] + [("alive", _IP)]
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -76,7 +94,19 @@ def lib():
             build()
             L = C.CDLL(_LIB_PATH)
         G, S, F, P = C.POINTER(Grid), C.POINTER(Spec), C.POINTER(Fields), C.POINTER(Parts)
+        G3, F3, P3 = C.POINTER(Grid3), C.POINTER(Fields3), C.POINTER(Parts3)
+        d = C.c_double
         sig = {
+            "or3_gather": (None, [G3, F3, d, d, d, _DP, _DP]),
+            "or3_deposit_one": (None, [G3, F3, d, d, d, d, d, d, d]),
+            "or3_push": (None, [G3, S, P3, F3, _DP, _DP, _DP]),
+            "or3_deposit": (None, [G3, S, P3, _DP, _DP, _DP, F3]),
+            "or3_laser": (None, [G3, d, d, d, C.c_int, _DP]),
+            "or3_field_update": (None, [G3, F3, C.c_long]),
+            "or3_step": (None, [G3, S, P3, _IP, C.c_int, F3, C.c_long]),
+            "or3_rho": (None, [G3, S, P3, _DP]),
+            "or3_div_e": (None, [G3, F3, _DP]),
+            "or3_div_b": (None, [G3, F3, _DP]),
             "or_gather": (None, [G, F, C.c_double, C.c_double, _DP, _DP]),
             "or_boris": (None, [C.c_double, C.c_double, _DP, _DP, _DP]),
             "or_omega": (None, [C.c_double, C.c_double, _DP, _DP, _DP, _DP]),
@@ -132,8 +162,10 @@ def spin_rotate(Om, dt, s):
     return np.array(ss[:])
 
 
-def derive_grid(wl) -> Grid:
+def derive_grid(wl):
     """The oracle's own units: lengths in c/omega0 (lambda = 2 pi), time in 1/omega0."""
+    if wl.dim == 3:
+        return derive_grid3(wl)
     two_pi = 2.0 * math.pi
     dx, dy = wl.dx_lambda * two_pi, wl.dy_lambda * two_pi
     dt = wl.cfl / math.sqrt(1.0 / dx ** 2 + 1.0 / dy ** 2)
@@ -141,6 +173,17 @@ def derive_grid(wl) -> Grid:
     return Grid(nx=wl.nx, ny=wl.ny, dx=dx, dy=dy, dt=dt, bc_x=BC[wl.bc_x],
                 pol=POL[wl.pol] if wl.bc_x == "open" else 0, a0=wl.a0,
                 w0=wl.waist_lambda * two_pi, tau=tau, t_peak=wl.t_peak_periods * two_pi)
+
+
+def derive_grid3(wl) -> Grid3:
+    """derive_grid for a 3D3V workload: dt = cfl / sqrt(1/dx^2 + 1/dy^2 + 1/dz^2)."""
+    two_pi = 2.0 * math.pi
+    dx, dy, dz = wl.dx_lambda * two_pi, wl.dy_lambda * two_pi, wl.dz_lambda * two_pi
+    dt = wl.cfl / math.sqrt(1.0 / dx ** 2 + 1.0 / dy ** 2 + 1.0 / dz ** 2)
+    tau = wl.fwhm_periods * two_pi / math.sqrt(2.0 * math.log(2.0))
+    return Grid3(nx=wl.nx, ny=wl.ny, nz=wl.nz, dx=dx, dy=dy, dz=dz, dt=dt, bc_x=BC[wl.bc_x],
+                 pol=POL[wl.pol] if wl.bc_x == "open" else 0, a0=wl.a0,
+                 w0=wl.waist_lambda * two_pi, tau=tau, t_peak=wl.t_peak_periods * two_pi)
 
 
 class OracleSim:
@@ -152,6 +195,11 @@ class OracleSim:
     """
 
     FIELD_KEYS = ("ex", "ey", "ez", "bx", "by", "bz", "jx", "jy", "jz")
+
+    def __new__(cls, wl, *args, **kw):
+        if cls is OracleSim and wl.dim == 3:
+            return super().__new__(OracleSim3)
+        return super().__new__(cls)
 
     def __init__(self, wl, particles, fields=None, step=0):
         self.wl = wl
@@ -268,4 +316,124 @@ class OracleSim:
     def laser(self, t, y, comp):
         v = C.c_double()
         lib().or_laser(C.byref(self.grid), t, y, comp, C.byref(v))
+        return v.value
+
+
+class OracleSim3(OracleSim):
+    """OracleSim of a 3D3V workload: mesh arrays [nz][ny][nx], left boundary
+    arrays [nz][ny], particle positions x = ix + ox, y = iy + oy, z = iz + oz.
+    ``OracleSim(wl, ...)`` returns one of these when ``wl.dim == 3``."""
+
+    def __init__(self, wl, particles, fields=None, step=0):
+        self.wl = wl
+        self.grid = derive_grid3(wl)
+        shape = (wl.nz, wl.ny, wl.nx)
+        self.f = {k: np.zeros(shape) for k in self.FIELD_KEYS}
+        self.f["byL"] = np.zeros((wl.nz, wl.ny))
+        self.f["bzL"] = np.zeros((wl.nz, wl.ny))
+        if fields is not None:
+            for k, v in fields.items():
+                self.f[k][...] = np.asarray(v, dtype=np.float64)
+        self.spec = [Spec(q=s.q, m=s.m, a=s.a) for s in wl.species]
+        self.mobile = np.array([1 if s.mobile else 0 for s in wl.species], dtype=np.int32)
+        self.p = []
+        for d in particles:
+            self.p.append(dict(
+                x=d["ix"].astype(np.float64) + d["ox"].astype(np.float64),
+                y=d["iy"].astype(np.float64) + d["oy"].astype(np.float64),
+                z=d["iz"].astype(np.float64) + d["oz"].astype(np.float64),
+                ux=d["ux"].astype(np.float64), uy=d["uy"].astype(np.float64),
+                uz=d["uz"].astype(np.float64), sx=d["sx"].astype(np.float64),
+                sy=d["sy"].astype(np.float64), sz=d["sz"].astype(np.float64),
+                w=d["w"].astype(np.float64), alive=np.ones(len(d["ix"]), np.int32),
+                id=d["id"].copy()))
+        self.step_index = step
+        self.rho_bg = np.zeros(shape)
+        if wl.neutralizing_background:
+            self.rho_bg = -self.rho()
+
+    def _fields(self):
+        return Fields3(**{k: _dp(self.f[k]) for k in self.f})
+
+    def _parts(self, s):
+        d = self.p[s]
+        kw = {k: _dp(d[k]) for k in ("x", "y", "z", "ux", "uy", "uz", "sx", "sy", "sz", "w")}
+        return Parts3(n=len(d["x"]), alive=d["alive"].ctypes.data_as(_IP), **kw)
+
+    def push(self, s):
+        """a1-a4 for species s; returns the old positions (x, y, z) for the deposit."""
+        n = len(self.p[s]["x"])
+        xo, yo, zo = np.zeros(n), np.zeros(n), np.zeros(n)
+        pp = self._parts(s)
+        lib().or3_push(C.byref(self.grid), C.byref(self.spec[s]), C.byref(pp),
+                       C.byref(self._fields()), _dp(xo), _dp(yo), _dp(zo))
+        return xo, yo, zo
+
+    def deposit(self, s, xo, yo, zo):
+        pp = self._parts(s)
+        lib().or3_deposit(C.byref(self.grid), C.byref(self.spec[s]), C.byref(pp),
+                          _dp(xo), _dp(yo), _dp(zo), C.byref(self._fields()))
+
+    def field_update(self):
+        lib().or3_field_update(C.byref(self.grid), C.byref(self._fields()), self.step_index)
+        self.step_index += 1
+
+    def step(self, nsteps=1):
+        nsp = len(self.p)
+        for _ in range(nsteps):
+            parts = (Parts3 * nsp)(*[self._parts(s) for s in range(nsp)])
+            specs = (Spec * nsp)(*self.spec)
+            lib().or3_step(C.byref(self.grid), specs, parts,
+                           self.mobile.ctypes.data_as(_IP), nsp, C.byref(self._fields()),
+                           self.step_index)
+            self.step_index += 1
+
+    def _mesh(self):
+        return np.zeros((self.wl.nz, self.wl.ny, self.wl.nx))
+
+    def rho(self):
+        r = self._mesh()
+        for s in range(len(self.p)):
+            pp = self._parts(s)
+            lib().or3_rho(C.byref(self.grid), C.byref(self.spec[s]), C.byref(pp), _dp(r))
+        return r
+
+    def div_e(self):
+        d = self._mesh()
+        lib().or3_div_e(C.byref(self.grid), C.byref(self._fields()), _dp(d))
+        return d
+
+    def div_b(self):
+        d = self._mesh()
+        lib().or3_div_b(C.byref(self.grid), C.byref(self._fields()), _dp(d))
+        return d
+
+    def gauss_residual(self):
+        r = self.div_e() - self.rho() - self.rho_bg
+        if self.wl.bc_x == "open":
+            r = r[:, :, 3:self.wl.nx - 3]
+        return r
+
+    def _moment_parts(self, s):
+        # the moments and spectra read only u, s, w and alive: the 2D view serves
+        d = self.p[s]
+        kw = {k: _dp(d[k]) for k in ("x", "y", "ux", "uy", "uz", "sx", "sy", "sz", "w")}
+        return Parts(n=len(d["x"]), alive=d["alive"].ctypes.data_as(_IP), **kw)
+
+    def moments(self, s, emin=-np.inf, emax=np.inf):
+        out = (C.c_double * 7)()
+        pp = self._moment_parts(s)
+        lib().or_moments(C.byref(self.spec[s]), C.byref(pp), float(emin), float(emax), out)
+        return np.array(out[:])
+
+    def histogram(self, s, emin, emax, nbins, log_bins=False):
+        out = np.zeros(5 * nbins)
+        pp = self._moment_parts(s)
+        lib().or_histogram(C.byref(self.spec[s]), C.byref(pp), float(emin), float(emax), int(nbins),
+                           1 if log_bins else 0, _dp(out))
+        return out.reshape(nbins, 5)
+
+    def laser(self, t, y, z, comp):
+        v = C.c_double()
+        lib().or3_laser(C.byref(self.grid), t, y, z, comp, C.byref(v))
         return v.value

@@ -110,6 +110,52 @@ void or_moments(const or_species_t *sp, const or_particles_t *p,
 void or_histogram(const or_species_t *sp, const or_particles_t *p, double emin_mev,
                   double emax_mev, int nbins, int log_bins, double *out);
 
+/* ---- 3D3V (pic_oracle3.c) ------------------------------------------------
+ * Positions in cell units; mesh arrays [nz][ny][nx]; staggering of [k][j][i]:
+ *   Ex (i+1/2, j, k)   Ey (i, j+1/2, k)   Ez (i, j, k+1/2)
+ *   Bx (i, j+1/2, k+1/2)   By (i+1/2, j, k+1/2)   Bz (i+1/2, j+1/2, k)
+ * y and z are periodic; x is open (Silver-Mueller, laser at x_min) or periodic.
+ * With open x, By and Bz at i = nx-1 hold the right-hand boundary values and
+ * byL, bzL ([nz][ny]) the left-hand ones at x = -1/2.  The laser profile is
+ * Gaussian in the radius about the box axis (y, z) = (ny dy/2, nz dz/2). */
+typedef struct {
+    int nx, ny, nz;
+    double dx, dy, dz, dt;
+    int bc_x, pol;
+    double a0, w0, tau, t_peak;
+} or_grid3_t;
+
+typedef struct {
+    double *ex, *ey, *ez, *bx, *by, *bz;   /* [nz*ny*nx] */
+    double *jx, *jy, *jz;
+    double *byL, *bzL;                     /* [nz*ny] */
+} or_fields3_t;
+
+typedef struct {
+    long n;
+    double *x, *y, *z;
+    double *ux, *uy, *uz;
+    double *sx, *sy, *sz;
+    double *w;
+    int *alive;
+} or_particles3_t;
+
+void or3_gather(const or_grid3_t *g, const or_fields3_t *f, double X, double Y, double Z,
+                double E[3], double B[3]);
+void or3_deposit_one(const or_grid3_t *g, or_fields3_t *f, double qw, double X0, double Y0,
+                     double Z0, double X1, double Y1, double Z1);
+void or3_push(const or_grid3_t *g, const or_species_t *sp, or_particles3_t *p,
+              const or_fields3_t *f, double *x_old, double *y_old, double *z_old);
+void or3_deposit(const or_grid3_t *g, const or_species_t *sp, or_particles3_t *p,
+                 const double *x_old, const double *y_old, const double *z_old, or_fields3_t *f);
+void or3_laser(const or_grid3_t *g, double t, double y, double z, int comp, double *val);
+void or3_field_update(const or_grid3_t *g, or_fields3_t *f, long step);
+void or3_step(const or_grid3_t *g, const or_species_t *sp, or_particles3_t *p, const int *mobile,
+              int nsp, or_fields3_t *f, long step);
+void or3_rho(const or_grid3_t *g, const or_species_t *sp, const or_particles3_t *p, double *rho);
+void or3_div_e(const or_grid3_t *g, const or_fields3_t *f, double *div);
+void or3_div_b(const or_grid3_t *g, const or_fields3_t *f, double *div);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,5 +1,6 @@
 """Plant plausible mistakes in copies of the oracle (on the CPU) and check that
-the pins in test_oracle_pins.py catch every one of them."""
+the pins catch every one of them: test_oracle_pins.py for the 2D3V source,
+test_oracle3_pins.py for the 3D3V source."""
 import os
 import subprocess
 import sys
@@ -8,8 +9,6 @@ import tempfile
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-SRC = os.path.join(ROOT, "oracle", "pic_oracle.c")
-
 # (name, exact text in pic_oracle.c, replacement)
 MUTATIONS = [
     ("boris drops second half kick", "u[k] = um[k] + c[k] + 0.5 * qm * dt * E[k];", "u[k] = um[k] + c[k];"),
@@ -64,22 +63,60 @@ MUTATIONS = [
 ]
 
 
-@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
-def test_pins_catch_planted_mistake(name, old, new):
-    src = open(SRC).read()
-    assert src.count(old) >= 1, f"mutation anchor not found: {name}"
-    mutated = src.replace(old, new, 1)
+# the same for the 3D3V source, pic_oracle3.c
+MUTATIONS3 = [
+    ("3d Bx z-curl sign", "f->bx[c] -= h * ((f->ez[cjp] - f->ez[c]) / g->dy - (f->ey[ckp] - f->ey[c]) / g->dz);",
+     "f->bx[c] -= h * ((f->ez[cjp] - f->ez[c]) / g->dy + (f->ey[ckp] - f->ey[c]) / g->dz);"),
+    ("3d By uses dy for z", "f->by[c] -= h * ((f->ex[ckp] - f->ex[c]) / g->dz",
+     "f->by[c] -= h * ((f->ex[ckp] - f->ex[c]) / g->dy"),
+    ("3d Ex z-difference reversed", "- (f->by[c] - f->by[ckm]) / g->dz - f->jx[c]);",
+     "- (f->by[ckm] - f->by[c]) / g->dz - f->jx[c]);"),
+    ("3d Ez ignores Jz", "(f->bx[c] - f->bx[cjm]) / g->dy - f->jz[c]);", "(f->bx[c] - f->bx[cjm]) / g->dy);"),
+    ("3d left Bz transverse sign", "- (1.0 - r) * f->bz[c0] - qz * dzb0) / (1.0 + r);",
+     "- (1.0 - r) * f->bz[c0] + qz * dzb0) / (1.0 + r);"),
+    ("3d right Bz without transverse term", "- (1.0 - r) * f->bz[cl - 1] + qz * dzbl) / (1.0 + r);",
+     "- (1.0 - r) * f->bz[cl - 1]) / (1.0 + r);"),
+    ("3d Jz scale uses dy", "cz = -qw * g->dz / g->dt;", "cz = -qw * g->dy / g->dt;"),
+    ("3d Wz third-order term", "dSx[i] * dSy[j] / 3.0;", "dSx[i] * dSy[j] / 2.0;"),
+    ("3d Wx mixed term", "0.5 * S0y[j] * dSz[k] +", "0.5 * S0y[j] * S0z[k] +"),
+    ("3d gather stagger of Ez", "E[2] = interp3(g, f->ez, X, Y, Z, 0.0, 0.0, 0.5);",
+     "E[2] = interp3(g, f->ez, X, Y, Z, 0.0, 0.0, 0.0);"),
+    ("3d gather stagger of Bx", "B[0] = interp3(g, f->bx, X, Y, Z, 0.0, 0.5, 0.5);",
+     "B[0] = interp3(g, f->bx, X, Y, Z, 0.0, 0.5, 0.0);"),
+    ("3d z weight of the gather", "shape1_3(zs - (double)k);", "shape1_3(zs - (double)k0);"),
+    ("3d z advance uses dy", "double Z1 = p->z[i] + g->dt * u[2] / gam / g->dz;",
+     "double Z1 = p->z[i] + g->dt * u[2] / gam / g->dy;"),
+    ("3d laser axis off centre in z", "zc = 0.5 * g->nz * g->dz;", "zc = 0.0;"),
+    ("3d laser Ey source at the Ez height", "or3_laser(g, t, ((double)j + 0.5) * g->dy, (double)k * g->dz, 0, &gin);",
+     "or3_laser(g, t, ((double)j + 0.5) * g->dy, ((double)k + 0.5) * g->dz, 0, &gin);"),
+    ("3d div E uses dy for z", "(f->ez[c] - f->ez[at3(g, i, j, k - 1)]) / g->dz;",
+     "(f->ez[c] - f->ez[at3(g, i, j, k - 1)]) / g->dy;"),
+    ("3d rho z weight", "shape1_3(p->z[n] - (double)(k0 + c));", "shape1_3(p->z[n] - (double)(k0));"),
+]
+
+CASES = ([("pic_oracle.c", "test_oracle_pins.py") + m for m in MUTATIONS] +
+         [("pic_oracle3.c", "test_oracle3_pins.py") + m for m in MUTATIONS3])
+
+
+@pytest.mark.parametrize("src_name,pins,name,old,new", CASES, ids=[c[2] for c in CASES])
+def test_pins_catch_planted_mistake(src_name, pins, name, old, new):
+    import shutil
     with tempfile.TemporaryDirectory() as td:
-        c = os.path.join(td, "pic_oracle.c")
-        with open(c, "w") as fh:
-            fh.write(mutated)
-        import shutil
+        srcs = []
+        for f in ("pic_oracle.c", "pic_oracle3.c"):
+            text = open(os.path.join(ROOT, "oracle", f)).read()
+            if f == src_name:
+                assert text.count(old) >= 1, f"mutation anchor not found: {name}"
+                text = text.replace(old, new, 1)
+            srcs.append(os.path.join(td, f))
+            with open(srcs[-1], "w") as fh:
+                fh.write(text)
         shutil.copy(os.path.join(ROOT, "oracle", "pic_oracle.h"), td)
         so = os.path.join(td, "liboracle_mut.so")
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-                               c, "-o", so, "-lm"])
+                               *srcs, "-o", so, "-lm"])
         env = dict(os.environ, PIC_ORACLE_LIB=so)
         r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                            os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                            os.path.join(ROOT, "tests", pins)],
                            cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
         assert r.returncode != 0, f"pins did not catch: {name}\n{r.stdout[-2000:]}"

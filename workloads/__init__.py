@@ -1,7 +1,7 @@
 """Seeded synthetic workloads shared by the CUDA path and the oracle.
 
 This module holds data only: the workload parameters (the paper's setup of
-Sec. 2 scaled to the 2D3V cases built here) and seeded random draws of the
+Sec. 2 scaled to the 2D3V and 3D3V cases built here) and seeded random draws of the
 initial particle state and, for single-step tests, of random mesh fields.  It
 contains none of the method's arithmetic; both the oracle and the CUDA
 library derive their own time step, units and boundary handling from these
@@ -10,6 +10,7 @@ parameters.
 Particle state of one species (all arrays of length n):
   ix, iy   int32   cell indices (node i sits at x = i dx)
   ox, oy   float32 offsets inside the cell, in [0, 1)
+  iz, oz   the same along z (3D3V workloads only)
   ux,uy,uz float32 momentum u = p / (m c)
   sx,sy,sz float32 unit spin
   w        float32 density carried by the macro-particle [n_c]
@@ -25,8 +26,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-__all__ = ["Species", "Workload", "CONFIG1", "CONFIG3", "generate_particles",
-           "random_fields", "small_case", "scaled"]
+__all__ = ["Species", "Workload", "CONFIG1", "CONFIG2", "CONFIG3", "generate_particles",
+           "random_fields", "small_case", "small_case3", "scaled"]
 
 
 @dataclass(frozen=True)
@@ -50,7 +51,7 @@ class Workload:
     ny: int
     dx_lambda: float          # cell size in laser wavelengths
     dy_lambda: float
-    cfl: float                # dt = cfl / sqrt(1/dx^2 + 1/dy^2)
+    cfl: float                # dt = cfl / sqrt(1/dx^2 + 1/dy^2 [+ 1/dz^2])
     steps: int
     species: tuple
     a0: float = 0.0
@@ -62,6 +63,9 @@ class Workload:
     neutralizing_background: bool = False  # immobile ions = -rho_e at t = 0
     seed: int = 1
     lambda_um: float = 0.8
+    dim: int = 2                 # 2: 2D3V mesh [ny][nx]; 3: 3D3V mesh [nz][ny][nx]
+    nz: int = 1
+    dz_lambda: float = 1.0
 
 
 ELECTRON = dict(q=-1.0, m=1.0, a=0.00116)
@@ -88,6 +92,18 @@ CONFIG3 = Workload(
     bc_x="open", neutralizing_background=False, seed=3)
 
 
+# 3D3V laser-wakefield precision study: 512x256x256 cells, dx = lambda/20,
+# dy = dz = lambda/8, 2 ppc electrons at 0.003 n_c over immobile ions (66,584,576
+# electrons: every cell but the two-cell vacuum margins along x), spins +y, LP
+# Gaussian laser a0 = 3 (waist 8 lambda: the setup leaves it open).
+CONFIG2 = Workload(
+    name="3d3v-512x256x256-ppc2-lp-a0_3",
+    nx=512, ny=256, dx_lambda=1 / 20, dy_lambda=1 / 8, cfl=0.95, steps=2000,
+    species=(Species("electron", n0=0.003, ppc=2, u_th=1e-3, s0=(0.0, 1.0, 0.0), **ELECTRON),),
+    a0=3.0, waist_lambda=8.0, fwhm_periods=10.0, t_peak_periods=15.0, pol="lp-y",
+    bc_x="open", neutralizing_background=True, seed=2, dim=3, nz=256, dz_lambda=1 / 8)
+
+
 def scaled(wl: Workload, **kw) -> Workload:
     """A copy of a workload with some fields replaced."""
     return dataclasses.replace(wl, **kw)
@@ -104,6 +120,16 @@ def small_case(nx=40, ny=24, ppc=2, bc_x="open", seed=11, pol="lp-y", a0=4.0,
                     cfl=0.95, steps=10, species=tuple(sp), a0=a0, waist_lambda=1.0,
                     fwhm_periods=2.0, t_peak_periods=1.0, pol=pol, bc_x=bc_x,
                     neutralizing_background=not two_species, seed=seed)
+
+
+def small_case3(nx=24, ny=16, nz=12, ppc=2, bc_x="open", seed=12, pol="lp-y", a0=4.0,
+                two_species=False, u_th=0.05, dx_lambda=1 / 16, dy_lambda=1 / 12,
+                dz_lambda=1 / 10) -> Workload:
+    """Few-tile 3D3V test workload; sizes need not be tile multiples."""
+    base = small_case(nx=nx, ny=ny, ppc=ppc, bc_x=bc_x, seed=seed, pol=pol, a0=a0,
+                      two_species=two_species, u_th=u_th)
+    return dataclasses.replace(base, name=f"small3-{nx}x{ny}x{nz}", dim=3, nz=nz,
+                               dx_lambda=dx_lambda, dy_lambda=dy_lambda, dz_lambda=dz_lambda)
 
 
 def _region_x(wl: Workload):
@@ -125,21 +151,28 @@ def generate_particles(wl: Workload, seed: int | None = None):
     rng = np.random.default_rng(wl.seed if seed is None else seed)
     x0, x1 = _region_x(wl)
     ncx = x1 - x0
-    gy, gx = np.meshgrid(np.arange(wl.ny, dtype=np.int32),
-                         np.arange(x0, x1, dtype=np.int32), indexing="ij")
+    three = wl.dim == 3
+    nzc = wl.nz if three else 1
+    gz, gy, gx = np.meshgrid(np.arange(nzc, dtype=np.int32), np.arange(wl.ny, dtype=np.int32),
+                             np.arange(x0, x1, dtype=np.int32), indexing="ij")
     out = []
     for s, sp in enumerate(wl.species):
-        n = sp.ppc * ncx * wl.ny
+        n = sp.ppc * ncx * wl.ny * nzc
+        extra = {}
         if sp.colocate_with >= 0:
             ref = out[sp.colocate_with]
             if len(ref["ix"]) != n:
                 raise ValueError("co-located species need the same particle count")
             ix, iy, ox, oy = ref["ix"], ref["iy"], ref["ox"], ref["oy"]
+            if three:
+                extra = dict(iz=ref["iz"], oz=ref["oz"])
         else:
             ix = np.tile(gx.ravel(), sp.ppc)
             iy = np.tile(gy.ravel(), sp.ppc)
             ox = rng.random(n, dtype=np.float32)
             oy = rng.random(n, dtype=np.float32)
+            if three:
+                extra = dict(iz=np.tile(gz.ravel(), sp.ppc), oz=rng.random(n, dtype=np.float32))
         uth = np.float32(sp.u_th)
         ux = rng.standard_normal(n, dtype=np.float32) * uth
         uy = rng.standard_normal(n, dtype=np.float32) * uth
@@ -150,14 +183,14 @@ def generate_particles(wl: Workload, seed: int | None = None):
             sx=np.full(n, s0[0], np.float32), sy=np.full(n, s0[1], np.float32),
             sz=np.full(n, s0[2], np.float32),
             w=np.full(n, np.float32(sp.n0 / sp.ppc), np.float32),
-            id=np.arange(n, dtype=np.int32)))
+            id=np.arange(n, dtype=np.int32), **extra))
     return out
 
 
 def random_fields(wl: Workload, seed: int, e_amp: float = 0.5, b_amp: float = 0.5):
-    """Random mesh fields (float32, [ny][nx]) for single-step tests."""
+    """Random mesh fields (float32, [ny][nx] or [nz][ny][nx]) for single-step tests."""
     rng = np.random.default_rng(seed)
-    shape = (wl.ny, wl.nx)
+    shape = (wl.nz, wl.ny, wl.nx) if wl.dim == 3 else (wl.ny, wl.nx)
     f = {}
     for k, amp in (("ex", e_amp), ("ey", e_amp), ("ez", e_amp),
                    ("bx", b_amp), ("by", b_amp), ("bz", b_amp)):
