@@ -1,15 +1,21 @@
 #!/usr/bin/env python
-"""Throughput of the 2D3V PIC + Thomas-BMT step on GB300.
+"""Throughput of the PIC + Thomas-BMT step on GB300.
 
 One step = the fused gather / Boris / spin / advance / Esirkepov kernel
 (pic_push_deposit), the Yee update (pic_field_update), the tile sort every
 --sort-every steps and, every --diag-every steps, the FP64 Eq. (4) moments of
-every species (accumulated inside the fused kernel), on the high-density
-pre-polarised hydrogen workload:
-4096 x 1024 cells (dx = lambda/32), 8 ppc electrons + 8 ppc protons, CP laser
-a0 = 60.  Prints one JSON line (rank 0).
+every species (accumulated inside the fused kernel).  Workloads:
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  config2 (default)  3D3V laser-wakefield precision study: 512 x 256 x 256
+                     cells (dx = lambda/20, dy = dz = lambda/8), 2 ppc
+                     electrons at 0.003 n_c, LP laser a0 = 3
+  config3            2D3V pre-polarised hydrogen: 4096 x 1024 cells
+                     (dx = lambda/32), 8 + 8 ppc electrons and protons, CP a0 = 60
+  config1            2D3V 256 x 128, 4 ppc, LP a0 = 4 (small; L2 resident)
+
+Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload ...]
 
 Several GPUs run independent replicas (one per rank, launched by torchrun):
 the step has no exchange between runs, so there is no collective on the
@@ -36,13 +42,22 @@ import workloads as W  # noqa: E402
 
 METRIC = "particle-steps/s (push+spin+deposit) and % HBM roofline, FP32 vs FP64 at stated error"
 UNIT = "particle-steps/s"
-# algorithmic bytes of the fused kernel: per particle read cell, ox, oy, u(3),
-# s(3), w = 40 B and write cell, ox, oy, u, s = 36 B; per cell the E, B
-# window (24 B) and the current added to J (12 B)
-BYTES_PER_PARTICLE = 76
+# algorithmic bytes of the fused kernel: per particle read cell, offsets, u(3),
+# s(3), w and write cell, offsets, u, s -- 2D3V 40 + 36 = 76 B, 3D3V (one more
+# offset) 44 + 40 = 84 B; per cell the E, B window (24 B) and the current added
+# to J (12 B)
+BYTES_PER_PARTICLE = {2: 76, 3: 84}
 BYTES_PER_CELL = 36
-CPU_SAMPLE_NY = 32
+# CPU samples of the workload (the oracle is slow): the CPU-baseline leg and
+# the precision study run CPU_SAMPLE_STEPS steps of CPU_SAMPLE (10-30 s of
+# oracle work); the reference arm runs every one of its --steps on REF_SAMPLE
+# (a fraction of a second of oracle work per step)
+CPU_SAMPLE = {2: {"ny": 32}, 3: {"nz": 4}}
+REF_SAMPLE = {2: {"ny": 32}, 3: {"ny": 32, "nz": 4}}
 CPU_SAMPLE_STEPS = 6
+DEFAULT_SORT_EVERY = {2: 32, 3: 2}
+KERNEL = {2: ("k_step_fused", ("k_particles.cu", "pic_device.cuh", "pic_ptx.cuh")),
+          3: ("k_step_fused3", ("k_particles3.cu", "pic_device3.cuh", "pic_device.cuh", "pic_ptx.cuh"))}
 
 
 def parse(argv=None):
@@ -51,11 +66,12 @@ def parse(argv=None):
     ap.add_argument("--steps", type=int, default=600)
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["config3", "config1"], default="config3")
-    ap.add_argument("--sort-every", type=int, default=32)
+    ap.add_argument("--workload", choices=["config2", "config3", "config1"], default="config2")
+    ap.add_argument("--sort-every", type=int, default=0, help="0: 32 in 2D3V, 2 in 3D3V")
     ap.add_argument("--diag-every", type=int, default=10)
-    ap.add_argument("--tile", type=int, nargs=2, default=(0, 0))
+    ap.add_argument("--tile", type=int, nargs="+", default=None)
     ap.add_argument("--ny", type=int, default=0, help="smaller ny for profiling captures")
+    ap.add_argument("--nz", type=int, default=0, help="smaller nz (3D3V) for profiling captures")
     ap.add_argument("--precision", type=int, choices=[32, 64], default=32)
     ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--no-e2e", action="store_true")
@@ -64,9 +80,17 @@ def parse(argv=None):
     return ap.parse_args(argv)
 
 
-def workload(name, ny=0):
-    wl = W.CONFIG3 if name == "config3" else W.CONFIG1
-    return W.scaled(wl, ny=ny) if ny else wl
+def workload(name, ny=0, nz=0):
+    wl = {"config1": W.CONFIG1, "config2": W.CONFIG2, "config3": W.CONFIG3}[name]
+    if ny:
+        wl = W.scaled(wl, ny=ny)
+    if nz and wl.dim == 3:
+        wl = W.scaled(wl, nz=nz)
+    return wl
+
+
+def n_cells(wl):
+    return wl.nx * wl.ny * (wl.nz if wl.dim == 3 else 1)
 
 
 # ---------------------------------------------------------------------------
@@ -171,21 +195,25 @@ def measured_hbm_peak():
         return 6800.0, "fallback"
 
 
-def traffic_record():
+def kernel_source_hash(dim):
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL[dim][1]:
+        with open(os.path.join(ROOT, "paper_2002_02211_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def traffic_record(dim, wl):
     """dram bytes per launch of the fused kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
-    p = os.path.join(ROOT, "profiles", "k_step_fused.traffic.json")
+    summary, if it was taken on the current kernel source for this workload."""
+    p = os.path.join(ROOT, "profiles", KERNEL[dim][0] + ".traffic.json")
     try:
         with open(p) as fh:
             rec = json.load(fh)
     except (OSError, ValueError):
         return None
-    import hashlib
-    h = hashlib.sha256()
-    for f in ("k_particles.cu", "pic_device.cuh"):
-        with open(os.path.join(ROOT, "paper_2002_02211_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    if rec.get("source_sha256") != h.hexdigest():
+    if rec.get("source_sha256") != kernel_source_hash(dim) or rec.get("workload", wl.name) != wl.name:
         return None
     return rec
 
@@ -193,14 +221,19 @@ def traffic_record():
 # ---------------------------------------------------------------------------
 # the oracle leg (CPU baseline and --impl reference)
 # ---------------------------------------------------------------------------
-def cpu_sample(wl):
+def sample_workload(wl, table=None):
+    cut = (table or CPU_SAMPLE)[wl.dim]
+    return W.scaled(wl, **cut), ", ".join(f"{k}={v}" for k, v in cut.items())
+
+
+def cpu_sample(wl, table=None):
     import oracle
-    sample = W.scaled(wl, ny=CPU_SAMPLE_NY)
+    sample, cut = sample_workload(wl, table)
     parts = W.generate_particles(sample)
     sim = oracle.OracleSim(sample, parts)
     n = sum(len(p["x"]) for p in sim.p)
-    desc = (f"{wl.name} with ny={CPU_SAMPLE_NY} ({sample.nx}x{sample.ny} cells, {n} particles), "
-            f"FP64 C oracle, single thread")
+    shape = "x".join(str(v) for v in ((sample.nx, sample.ny, sample.nz) if wl.dim == 3 else (sample.nx, sample.ny)))
+    desc = f"{wl.name} with {cut} ({shape} cells, {n} particles), FP64 C oracle, single thread"
     return sim, n, desc
 
 
@@ -221,13 +254,16 @@ def precision_study(pic, wl, oracle_sim):
     """The CPU-baseline sample run on the GPU in FP32 and FP64: largest error
     of every particle against the FP64 oracle after the same steps, and the
     error of the Eq. (4) polarization of each species."""
-    sample = W.scaled(wl, ny=CPU_SAMPLE_NY)
+    sample, cut = sample_workload(wl)
     parts = W.generate_particles(sample)
+    pos = ("x", "y", "z") if wl.dim == 3 else ("x", "y")
     out = {}
     for prec in (32, 64):
         with pic.Simulation(pic.config_from_workload(sample, precision=prec)) as sim:
             for s, d in enumerate(parts):
                 sim.set_particles(s, d)
+            if sample.neutralizing_background:
+                sim.capture_background()
             sim.step(CPU_SAMPLE_STEPS)
             du = ds = dx = dp = 0.0
             for s in range(len(parts)):
@@ -241,21 +277,22 @@ def precision_study(pic, wl, oracle_sim):
                 un = np.maximum(np.sqrt(sum(o[k][ids] ** 2 for k in ("ux", "uy", "uz"))), 1e-3)
                 du = max(du, float((np.sqrt(sum((g[k][sel] - o[k][ids]) ** 2 for k in ("ux", "uy", "uz"))) / un).max()))
                 ds = max(ds, float(np.sqrt(sum((g[k][sel] - o[k][ids]) ** 2 for k in ("sx", "sy", "sz"))).max()))
-                dx = max(dx, float(np.abs(g["ix"][sel] + g["ox"][sel] - o["x"][ids]).max()))
+                for a in pos:
+                    dx = max(dx, float(np.abs(g["i" + a][sel] + g["o" + a][sel] - o[a][ids]).max()))
                 gm = sim.polarization(s)
                 om = oracle_sim.moments(s)
                 dp = max(dp, float(np.abs(gm["P"] - om[:3]).max()))
             out[f"fp{prec}"] = {"u_rel_max": du, "s_abs_max": ds, "x_cells_max": dx, "P_abs_max": dp}
-    out["sample"] = f"{CPU_SAMPLE_STEPS} steps of {sample.name} ny={CPU_SAMPLE_NY}, every particle"
+    out["sample"] = f"{CPU_SAMPLE_STEPS} steps of {wl.name} with {cut}, every particle"
     return out
 
 
 def main_reference(args):
     rank, world, _ = dist_env()
-    wl = workload(args.workload, args.ny)
+    wl = workload(args.workload, args.ny, args.nz)
     if rank != 0:
         return
-    sim, n, desc = cpu_sample(wl)
+    sim, n, desc = cpu_sample(wl, REF_SAMPLE)
     run_oracle_steps(sim, args.warmup)
     dt = run_oracle_steps(sim, args.steps)
     v = n * args.steps / dt
@@ -282,13 +319,16 @@ def main_ours(args):
     torch.cuda.set_device(local)
     init_dist(world, "nccl")
     dev = torch.device("cuda", local)
-    wl = workload(args.workload, args.ny)
+    wl = workload(args.workload, args.ny, args.nz)
+    dim = wl.dim
+    if args.sort_every <= 0:
+        args.sort_every = DEFAULT_SORT_EVERY[dim]
     parts = W.generate_particles(wl)
     n_particles = sum(len(p["ix"]) for p in parts)
-    n_cells = wl.nx * wl.ny
+    cells = n_cells(wl)
 
     stream = torch.cuda.Stream(device=dev)
-    cfg = pic.config_from_workload(wl, sort_every=args.sort_every, tile=tuple(args.tile),
+    cfg = pic.config_from_workload(wl, sort_every=args.sort_every, tile=args.tile,
                                    precision=args.precision)
     sim = pic.Simulation(cfg, stream=stream)
     for s, d in enumerate(parts):
@@ -340,18 +380,21 @@ def main_ours(args):
     diag_step, diag = sim.get_diagnostics()
 
     elapsed = start.elapsed_time(end) * 1e-3
-    t_fused = float(np.mean([a.elapsed_time(b) for a, b in ev_pairs])) * 1e-3
+    fused_ms = np.array([a.elapsed_time(b) for a, b in ev_pairs])
+    t_fused = float(fused_ms.mean()) * 1e-3
+    # the fused kernel over the run, in tenths (the laser enters and heats the plasma)
+    fused_trend = [round(float(c.mean()), 3) for c in np.array_split(fused_ms, min(10, len(fused_ms)))]
     tmax, units = combine(elapsed, n_particles * args.steps, world, dev)
     value = units / tmax
 
     peak, peak_kind = measured_hbm_peak()
     wb = args.precision // 32  # algorithmic bytes scale with the real width (the cell word stays 4 B)
-    bytes_fused = (4 + (BYTES_PER_PARTICLE - 4) * wb) * n_particles + BYTES_PER_CELL * wb * n_cells
+    bytes_fused = (4 + (BYTES_PER_PARTICLE[dim] - 4) * wb) * n_particles + BYTES_PER_CELL * wb * cells
     achieved = bytes_fused / t_fused / 1e9
-    tr = traffic_record()
+    tr = traffic_record(dim, wl) if args.precision == 32 else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": tr["dram_bytes_per_launch"] if tr else None,
-                "kernel": "k_step_fused", "kernel_ms": t_fused * 1e3,
+                "kernel": KERNEL[dim][0], "kernel_ms": t_fused * 1e3, "kernel_ms_by_tenth": fused_trend,
                 "algorithmic_bytes": bytes_fused, "peak_source": f"{peak_kind} hbm_gbs"}
 
     # end to end through the C ABI with host buffers: upload the particle state
@@ -362,12 +405,14 @@ def main_ours(args):
         ptrs = []
         for d in parts:
             pp = {}
-            for k in ("ix", "iy", "ox", "oy", "ux", "uy", "uz", "sx", "sy", "sz", "w", "id"):
+            keys = ("ix", "iy", "ox", "oy", "ux", "uy", "uz", "sx", "sy", "sz", "w", "id")
+            keys += ("iz", "oz") if dim == 3 else ()
+            for k in keys:
                 t = torch.from_numpy(np.ascontiguousarray(d[k])).pin_memory()
                 pinned.append(t)
                 pp[k] = t.data_ptr()
             ptrs.append((len(d["ix"]), pp))
-        h2d = sum(len(d["ix"]) * 4 * 12 for d in parts)
+        h2d = sum(len(d["ix"]) * 4 * (14 if dim == 3 else 12) for d in parts)
         d2h = len(parts) * 7 * 8
         barrier(world)
         torch.cuda.synchronize(dev)
@@ -393,10 +438,12 @@ def main_ours(args):
     # FP64 instantiation of the same step on the same workload
     fp64 = None
     if args.precision == 32 and args.fp64_steps > 0:
-        cfg64 = pic.config_from_workload(wl, sort_every=args.sort_every, tile=tuple(args.tile), precision=64)
+        cfg64 = pic.config_from_workload(wl, sort_every=args.sort_every, tile=args.tile, precision=64)
         with pic.Simulation(cfg64, stream=stream) as s64:
             for s, d in enumerate(parts):
                 s64.set_particles(s, d)
+            if wl.neutralizing_background:
+                s64.capture_background()
             s64.set_diagnostics(args.diag_every)
             for _ in range(2):
                 s64.step(1)
@@ -426,10 +473,13 @@ def main_ours(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if args.precision == 32 else "f64",
                 "data": "synthetic",
-                "config": {"workload": wl.name, "cells": [wl.nx, wl.ny], "particles": n_particles,
+                "config": {"workload": wl.name,
+                           "cells": [wl.nx, wl.ny] + ([wl.nz] if dim == 3 else []),
+                           "particles": n_particles,
                            "species": [s.name for s in wl.species], "sort_every": args.sort_every,
-                           "diag_every": args.diag_every, "tile": list(args.tile),
-                           "l2": "inputs larger than L2 (particle state 2.95 GB)",
+                           "diag_every": args.diag_every, "tile": args.tile or "default",
+                           "l2": "inputs larger than L2 (particle state %.2f GB)"
+                                 % (n_particles * (8 + (dim + 7) * 4 * wb) / 1e9),
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": launches, "fp64": fp64, "precision_study": study,

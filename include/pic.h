@@ -1,6 +1,6 @@
 /*
- * pic.h -- C ABI of the GB300 (sm_103a) 2D3V electromagnetic particle-in-cell
- * step with Thomas-BMT spin tracking.
+ * pic.h -- C ABI of the GB300 (sm_103a) 2D3V and 3D3V electromagnetic
+ * particle-in-cell step with Thomas-BMT spin tracking.
  *
  * The method (Sec. 2 of Huetzen et al., "Simulation of Polarized Beams from
  * Laser-Plasma Accelerators"): particles are pushed in the plasma and laser
@@ -36,6 +36,14 @@
  * left boundary values By(-1/2), Bz(-1/2) are the arrays by_left, bz_left [ny].
  * Particles live in [2, nx-2) along x with open boundaries (a particle that
  * leaves is removed after its current is deposited) and wrap when periodic.
+ *
+ * 3D3V (pic_config_t.dim = 3): host mesh arrays are [nz][ny][nx]; element
+ * [k][j][i] of
+ *   Ex sits at (i+1/2, j, k)     Ey at (i, j+1/2, k)     Ez at (i, j, k+1/2)
+ *   Bx at (i, j+1/2, k+1/2)      By at (i+1/2, j, k+1/2) Bz at (i+1/2, j+1/2, k)
+ * y and z are periodic; by_left, bz_left are [nz][ny] (at x = -1/2, the y and
+ * z positions of By and Bz); particles carry iz, oz as well.  The laser
+ * profile is Gaussian in the radius about the box axis (ny dy / 2, nz dz / 2).
  */
 #ifndef PIC_H
 #define PIC_H
@@ -91,6 +99,12 @@ typedef struct {
                                     production path) or 64 (the FP64 instantiation
                                     of the same kernels); 0 means 32.  Reductions
                                     are FP64 in both.                              */
+    int dim;                     /* 2 (or 0): 2D3V; 3: 3D3V                        */
+    int nz;                      /* 3D3V: cells along z, 4 <= nz <= 1020; nx, ny <= 2044 */
+    double dz_lambda;            /* 3D3V: cell size along z [lambda]; then
+                                    dt = cfl / sqrt(1/dx^2 + 1/dy^2 + 1/dz^2)      */
+    int tile_z;                  /* 3D3V tiles (tile_x, tile_y, tile_z): 8x8x4,
+                                    16x4x4 or 8x4x4 (0, 0, 0: 16x4x4)              */
 } pic_config_t;
 
 /* Host-side particle arrays of one species (n entries each).  ix, iy are cell
@@ -103,6 +117,8 @@ typedef struct {
     float *sx, *sy, *sz;  /* spin          */
     float *w;             /* density carried by the macro-particle [n_c] */
     int32_t *id;          /* caller's particle identity, carried through sorts */
+    int32_t *iz;          /* 3D3V only (ignored in 2D3V): cell index and offset along z */
+    float *oz;
 } pic_particles_t;
 
 /* The same with float64 arrays (read-back of either precision at full width). */
@@ -114,9 +130,12 @@ typedef struct {
     double *sx, *sy, *sz;
     double *w;
     int32_t *id;
+    int32_t *iz;
+    double *oz;
 } pic_particles_f64_t;
 
-/* Host-side mesh arrays, [ny][nx] float32 each (by_left, bz_left: [ny]).
+/* Host-side mesh arrays, [ny][nx] float32 each (by_left, bz_left: [ny]); in
+ * 3D3V [nz][ny][nx] (by_left, bz_left: [nz][ny]).
  * A NULL member is skipped by pic_set_fields / pic_get_fields. */
 typedef struct {
     float *ex, *ey, *ez, *bx, *by, *bz, *jx, *jy, *jz;
@@ -148,8 +167,9 @@ pic_status_t pic_create(const pic_config_t *cfg, void *stream, void **ctx_out);
 /* Releases everything the context owns.  NULL is accepted. */
 void pic_destroy(void *ctx);
 
-/* Time step dt [1/omega0] and cell sizes dx, dy [c/omega0] the context derived. */
-pic_status_t pic_get_grid(void *ctx, double *dt, double *dx, double *dy);
+/* Time step dt [1/omega0] and cell sizes dx, dy, dz [c/omega0] the context
+ * derived (dz = 0 in 2D3V).  NULL outputs are skipped. */
+pic_status_t pic_get_grid(void *ctx, double *dt, double *dx, double *dy, double *dz);
 
 /* Loads the particles of one species from host float32 arrays (widened
  * exactly with precision 64; replacing what was there) and sorts them by tile.  n <= capacity (else PIC_ERR_OVERFLOW).

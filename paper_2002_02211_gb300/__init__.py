@@ -1,4 +1,4 @@
-"""Python binding of libpic.so, the GB300 (sm_103a) 2D3V PIC + Thomas-BMT step.
+"""Python binding of libpic.so, the GB300 (sm_103a) 2D3V / 3D3V PIC + Thomas-BMT step.
 
 Argument marshalling only: every function below calls the C entry point of
 the same name declared in include/pic.h, and all arithmetic runs in the CUDA
@@ -47,7 +47,8 @@ class pic_config_t(C.Structure):
                 ("waist_lambda", C.c_double), ("fwhm_periods", C.c_double),
                 ("t_peak_periods", C.c_double), ("nspecies", C.c_int),
                 ("sp", pic_species_t * MAX_SPECIES), ("sort_every", C.c_int), ("tile_x", C.c_int),
-                ("tile_y", C.c_int), ("precision", C.c_int)]
+                ("tile_y", C.c_int), ("precision", C.c_int), ("dim", C.c_int), ("nz", C.c_int),
+                ("dz_lambda", C.c_double), ("tile_z", C.c_int)]
 
 
 _I32P = C.POINTER(C.c_int32)
@@ -57,7 +58,7 @@ _F32P = C.POINTER(C.c_float)
 class pic_particles_t(C.Structure):
     _fields_ = [("n", C.c_int64), ("ix", _I32P), ("iy", _I32P), ("ox", _F32P), ("oy", _F32P),
                 ("ux", _F32P), ("uy", _F32P), ("uz", _F32P), ("sx", _F32P), ("sy", _F32P),
-                ("sz", _F32P), ("w", _F32P), ("id", _I32P)]
+                ("sz", _F32P), ("w", _F32P), ("id", _I32P), ("iz", _I32P), ("oz", _F32P)]
 
 
 _F64P = C.POINTER(C.c_double)
@@ -65,7 +66,8 @@ _F64P = C.POINTER(C.c_double)
 
 class pic_particles_f64_t(C.Structure):
     _fields_ = [("n", C.c_int64), ("ix", _I32P), ("iy", _I32P)] + \
-        [(k, _F64P) for k in ("ox", "oy", "ux", "uy", "uz", "sx", "sy", "sz", "w")] + [("id", _I32P)]
+        [(k, _F64P) for k in ("ox", "oy", "ux", "uy", "uz", "sx", "sy", "sz", "w")] + \
+        [("id", _I32P), ("iz", _I32P), ("oz", _F64P)]
 
 
 class pic_fields_f64_t(C.Structure):
@@ -88,7 +90,7 @@ _lib = None
 _SIGS = {
     "pic_validate_config": [C.POINTER(pic_config_t)],
     "pic_create": [C.POINTER(pic_config_t), C.c_void_p, C.POINTER(C.c_void_p)],
-    "pic_get_grid": [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)],
+    "pic_get_grid": [C.c_void_p] + [C.POINTER(C.c_double)] * 4,
     "pic_set_particles": [C.c_void_p, C.c_int, C.POINTER(pic_particles_t), C.c_void_p],
     "pic_get_count": [C.c_void_p, C.c_int, C.POINTER(C.c_int64)],
     "pic_get_particles": [C.c_void_p, C.c_int, C.POINTER(pic_particles_t), C.c_void_p],
@@ -160,9 +162,12 @@ def moments_noalloc(n, cell, ux, uy, uz, sx, sy, sz, w, mass_me, emin, emax, out
                                       C.c_void_p(int(out_dev)), _stream(stream)))
 
 
-def config_from_workload(wl, capacity_factor: float = 1.0, sort_every: int = 0, tile=(0, 0),
+def config_from_workload(wl, capacity_factor: float = 1.0, sort_every: int = 0, tile=None,
                          precision: int = 32):
-    """pic_config_t for a workload description (nx, ny, dx_lambda, ..., species)."""
+    """pic_config_t for a workload description (nx, ny, dx_lambda, ..., species;
+    dim, nz, dz_lambda for 3D3V).  tile: (tx, ty) in 2D3V, (tx, ty, tz) in
+    3D3V, None for the library's choice."""
+    three = getattr(wl, "dim", 2) == 3
     cfg = pic_config_t()
     cfg.nx, cfg.ny = wl.nx, wl.ny
     cfg.dx_lambda, cfg.dy_lambda = wl.dx_lambda, wl.dy_lambda
@@ -178,15 +183,22 @@ def config_from_workload(wl, capacity_factor: float = 1.0, sort_every: int = 0, 
     for s, sp in enumerate(wl.species):
         cfg.sp[s].q, cfg.sp[s].m, cfg.sp[s].a = sp.q, sp.m, sp.a
         cfg.sp[s].mobile = 1 if sp.mobile else 0
-        cfg.sp[s].capacity = int(math.ceil(sp.ppc * ncx * wl.ny * capacity_factor))
+        cfg.sp[s].capacity = int(math.ceil(sp.ppc * ncx * wl.ny * (wl.nz if three else 1) * capacity_factor))
     cfg.sort_every = sort_every
-    cfg.tile_x, cfg.tile_y = tile
+    tile = tuple(tile) if tile else (0, 0, 0)
+    cfg.tile_x, cfg.tile_y = tile[0], tile[1]
     cfg.precision = precision
+    if three:
+        cfg.dim, cfg.nz, cfg.dz_lambda = 3, wl.nz, wl.dz_lambda
+        cfg.tile_z = tile[2] if len(tile) > 2 else 0
     return cfg
 
 
 def _ptr(a, t):
     return a.ctypes.data_as(t)
+
+
+_INT_KEYS = ("ix", "iy", "iz", "id")
 
 
 class Simulation:
@@ -198,6 +210,8 @@ class Simulation:
         L = load()
         self.cfg = cfg
         self.nx, self.ny = cfg.nx, cfg.ny
+        self.dim = 3 if cfg.dim == 3 else 2
+        self.nz = cfg.nz if self.dim == 3 else 1
         self.nspecies = cfg.nspecies
         h = C.c_void_p()
         _check(L.pic_create(C.byref(cfg), _stream(stream), C.byref(h)))
@@ -229,15 +243,29 @@ class Simulation:
         return _stream(self.stream)
 
     def grid(self):
-        dt, dx, dy = C.c_double(), C.c_double(), C.c_double()
-        self._c(load().pic_get_grid(self.h, C.byref(dt), C.byref(dx), C.byref(dy)))
-        return dt.value, dx.value, dy.value
+        """(dt, dx, dy) in 2D3V, (dt, dx, dy, dz) in 3D3V."""
+        v = [C.c_double() for _ in range(4)]
+        self._c(load().pic_get_grid(self.h, *[C.byref(x) for x in v]))
+        return tuple(x.value for x in v[:4 if self.dim == 3 else 3])
+
+    @property
+    def _pkeys(self):
+        base = ("ix", "iy", "ox", "oy", "ux", "uy", "uz", "sx", "sy", "sz", "w", "id")
+        return base + (("iz", "oz") if self.dim == 3 else ())
+
+    @property
+    def _mesh_shape(self):
+        return (self.nz, self.ny, self.nx) if self.dim == 3 else (self.ny, self.nx)
+
+    @property
+    def _bnd_shape(self):
+        return (self.nz, self.ny) if self.dim == 3 else (self.ny,)
 
     # state ----------------------------------------------------------------
     def set_particles(self, s, d):
         n = len(d["ix"])
-        arr = {k: np.ascontiguousarray(d[k], dtype=np.int32 if k in ("ix", "iy", "id") else np.float32)
-               for k in ("ix", "iy", "ox", "oy", "ux", "uy", "uz", "sx", "sy", "sz", "w", "id")}
+        arr = {k: np.ascontiguousarray(d[k], dtype=np.int32 if k in _INT_KEYS else np.float32)
+               for k in self._pkeys}
         p = pic_particles_t(n=n, **{k: _ptr(v, _I32P if v.dtype == np.int32 else _F32P)
                                     for k, v in arr.items()})
         self._c(load().pic_set_particles(self.h, s, C.byref(p), self._s))
@@ -245,7 +273,7 @@ class Simulation:
     def set_particles_raw(self, s, n, ptrs):
         """Like set_particles, from raw host addresses (e.g. pinned buffers):
         ptrs maps every pic_particles_t array name to an integer address."""
-        kw = {k: C.cast(C.c_void_p(int(v)), _I32P if k in ("ix", "iy", "id") else _F32P)
+        kw = {k: C.cast(C.c_void_p(int(v)), _I32P if k in _INT_KEYS else _F32P)
               for k, v in ptrs.items()}
         p = pic_particles_t(n=int(n), **kw)
         self._c(load().pic_set_particles(self.h, s, C.byref(p), self._s))
@@ -257,8 +285,7 @@ class Simulation:
 
     def get_particles(self, s):
         n = self.count(s)
-        out = {k: np.empty(n, np.int32 if k in ("ix", "iy", "id") else np.float32)
-               for k in ("ix", "iy", "ox", "oy", "ux", "uy", "uz", "sx", "sy", "sz", "w", "id")}
+        out = {k: np.empty(n, np.int32 if k in _INT_KEYS else np.float32) for k in self._pkeys}
         p = pic_particles_t(n=n, **{k: _ptr(v, _I32P if v.dtype == np.int32 else _F32P)
                                     for k, v in out.items()})
         self._c(load().pic_get_particles(self.h, s, C.byref(p), self._s))
@@ -266,17 +293,16 @@ class Simulation:
 
     def get_particles_f64(self, s):
         n = self.count(s)
-        out = {k: np.empty(n, np.int32 if k in ("ix", "iy", "id") else np.float64)
-               for k in ("ix", "iy", "ox", "oy", "ux", "uy", "uz", "sx", "sy", "sz", "w", "id")}
+        out = {k: np.empty(n, np.int32 if k in _INT_KEYS else np.float64) for k in self._pkeys}
         p = pic_particles_f64_t(n=n, **{k: _ptr(v, _I32P if v.dtype == np.int32 else _F64P)
                                         for k, v in out.items()})
         self._c(load().pic_get_particles_f64(self.h, s, C.byref(p), self._s))
         return out
 
     def get_fields_f64(self):
-        out = {k: np.empty((self.ny, self.nx), np.float64) for k in self.FIELD_KEYS}
-        out["by_left"] = np.empty(self.ny, np.float64)
-        out["bz_left"] = np.empty(self.ny, np.float64)
+        out = {k: np.empty(self._mesh_shape, np.float64) for k in self.FIELD_KEYS}
+        out["by_left"] = np.empty(self._bnd_shape, np.float64)
+        out["bz_left"] = np.empty(self._bnd_shape, np.float64)
         pf = pic_fields_f64_t(**{k: _ptr(v, _F64P) for k, v in out.items()})
         self._c(load().pic_get_fields_f64(self.h, C.byref(pf), self._s))
         return out
@@ -286,15 +312,18 @@ class Simulation:
         kw = {}
         for k, v in f.items():
             a = np.ascontiguousarray(v, dtype=np.float32)
+            want = self._bnd_shape if k in ("by_left", "bz_left") else self._mesh_shape
+            if a.shape != want:
+                raise ValueError(f"{k}: shape {a.shape}, expected {want}")
             keep[k] = a
             kw[k] = _ptr(a, _F32P)
         pf = pic_fields_t(**kw)
         self._c(load().pic_set_fields(self.h, C.byref(pf), self._s))
 
     def get_fields(self):
-        out = {k: np.empty((self.ny, self.nx), np.float32) for k in self.FIELD_KEYS}
-        out["by_left"] = np.empty(self.ny, np.float32)
-        out["bz_left"] = np.empty(self.ny, np.float32)
+        out = {k: np.empty(self._mesh_shape, np.float32) for k in self.FIELD_KEYS}
+        out["by_left"] = np.empty(self._bnd_shape, np.float32)
+        out["bz_left"] = np.empty(self._bnd_shape, np.float32)
         pf = pic_fields_t(**{k: _ptr(v, _F32P) for k, v in out.items()})
         self._c(load().pic_get_fields(self.h, C.byref(pf), self._s))
         return out

@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(256) k_e_full(const MeshParams<R> m, const R *
 
 // laser time factors at t: the incident Ez (comp 1) and Ey (comp 0) on the
 // axis, i.e. without the transverse profile
-static void laser_time_factors(const LaserParams &L, double t, double *fz, double *fy) {
+void laser_time_factors(const LaserParams &L, double t, double *fz, double *fy) {
     const double e = (t - L.t_peak) / L.tau;
     const double env = std::exp(-e * e);
     const double ph = t - L.t_peak;

@@ -1,0 +1,153 @@
+// k_fields3.cu -- a6 in 3D: Yee FDTD update (Yee 1966) in three stages, B
+// half step, E full step with -J (which is then cleared), B half step, with a
+// first-order Silver-Mueller boundary at x_min (laser source) and x_max.
+// One thread per cell, x fastest (coalesced rows), y and z periodic.
+#include <cmath>
+
+#include "pic_device3.cuh"
+#include "pic_kernels.h"
+
+namespace {
+
+template <typename R>
+struct Idx3 {
+    size_t c, cjp, ckp, cjm, ckm;
+    int i, j, k;
+};
+
+template <typename R>
+__device__ __forceinline__ bool cell_of_thread(const MeshParams3<R> &m, Idx3<R> &q) {
+    q.i = blockIdx.x * blockDim.x + threadIdx.x;
+    q.j = blockIdx.y;
+    q.k = blockIdx.z;
+    if (q.i >= m.nx) return false;
+    const int jp = q.j + 1 == m.ny ? 0 : q.j + 1, jm = q.j == 0 ? m.ny - 1 : q.j - 1;
+    const int kp = q.k + 1 == m.nz ? 0 : q.k + 1, km = q.k == 0 ? m.nz - 1 : q.k - 1;
+    const size_t row = (size_t)m.ld;
+    const size_t slab = (size_t)m.ny * m.ld;
+    q.c = q.k * slab + q.j * row + q.i;
+    q.cjp = q.k * slab + jp * row + q.i;
+    q.cjm = q.k * slab + jm * row + q.i;
+    q.ckp = kp * slab + q.j * row + q.i;
+    q.ckm = km * slab + q.j * row + q.i;
+    return true;
+}
+
+// B <- B - h curl E.  Bx on every column; By, Bz where the x+1 neighbour exists
+template <typename R>
+__global__ void __launch_bounds__(256) k_b_half3(const MeshParams3<R> m, R hdx, R hdy, R hdz) {
+    Idx3<R> q;
+    if (!cell_of_thread(m, q)) return;
+    const size_t P = m.plane;
+    R *EB = m.EB;
+    const R ex = EB[0 * P + q.c], ey = EB[1 * P + q.c], ez = EB[2 * P + q.c];
+    EB[3 * P + q.c] -= hdy * (EB[2 * P + q.cjp] - ez) - hdz * (EB[1 * P + q.ckp] - ey);
+    if (q.i < m.nx - 1 || m.bc_x == 1) {
+        const size_t cip = q.c - q.i + (q.i + 1 == m.nx ? 0 : q.i + 1);
+        EB[4 * P + q.c] -= hdz * (EB[0 * P + q.ckp] - ex) - hdx * (EB[2 * P + cip] - ez);
+        EB[5 * P + q.c] -= hdx * (EB[1 * P + cip] - ey) - hdy * (EB[0 * P + q.cjp] - ex);
+    }
+}
+
+// boundary B at t^{n+1/2}; one thread per (j, k).  With r = dt/dx, qy = dt/dy,
+// qz = dt/dz and the incident Ez (f) and Ey (g):
+//   By(-1/2) = (2 Ez(0) - (1-r) By(1/2) - qy dyBx - 4 f) / (1+r)
+//   Bz(-1/2) = (4 g - 2 Ey(0) - (1-r) Bz(1/2) - qz dzBx) / (1+r)
+//   By(nx-1/2) = (-2 Ez - (1-r) By(nx-3/2) + qy dyBx) / (1+r)
+//   Bz(nx-1/2) = ( 2 Ey - (1-r) Bz(nx-3/2) + qz dzBx) / (1+r)
+// dyBx = Bx(j+1/2) - Bx(j-1/2) and dzBx = Bx(k+1/2) - Bx(k-1/2), taken in the
+// boundary column.  bnd holds By(-1/2) [nz][ny] then Bz(-1/2) [nz][ny].
+template <typename R>
+__global__ void k_boundary3(const MeshParams3<R> m, R *bnd, const double *prof, double fz, double fy, double r,
+                            double qy, double qz) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.y;
+    if (j >= m.ny) return;
+    const size_t P = m.plane, slab = (size_t)m.ny * m.ld;
+    R *EB = m.EB;
+    const int jm = j == 0 ? m.ny - 1 : j - 1, km = k == 0 ? m.nz - 1 : k - 1;
+    const size_t c0 = k * slab + (size_t)j * m.ld, cl = c0 + m.nx - 1;
+    const size_t cy0 = k * slab + (size_t)jm * m.ld, cz0 = km * slab + (size_t)j * m.ld;
+    const size_t b = (size_t)k * m.ny + j, nb = (size_t)m.ny * m.nz;
+    const double f = fz * prof[b];        // Ez source at (y_j, z_{k+1/2})
+    const double g = fy * prof[nb + b];   // Ey source at (y_{j+1/2}, z_k)
+    const double ir = 1.0 / (1.0 + r), mr = 1.0 - r;
+    const double bx0 = EB[3 * P + c0], bxl = EB[3 * P + cl];
+    const double dyb0 = bx0 - (double)EB[3 * P + cy0], dzb0 = bx0 - (double)EB[3 * P + cz0];
+    const double dybl = bxl - (double)EB[3 * P + cy0 + m.nx - 1], dzbl = bxl - (double)EB[3 * P + cz0 + m.nx - 1];
+    bnd[b] = (R)((2.0 * EB[2 * P + c0] - mr * EB[4 * P + c0] - qy * dyb0 - 4.0 * f) * ir);
+    bnd[nb + b] = (R)((4.0 * g - 2.0 * EB[1 * P + c0] - mr * EB[5 * P + c0] - qz * dzb0) * ir);
+    EB[4 * P + cl] = (R)((-2.0 * EB[2 * P + cl] - mr * EB[4 * P + cl - 1] + qy * dybl) * ir);
+    EB[5 * P + cl] = (R)((2.0 * EB[1 * P + cl] - mr * EB[5 * P + cl - 1] + qz * dzbl) * ir);
+}
+
+// E <- E + dt (curl B - J), then J <- 0
+template <typename R>
+__global__ void __launch_bounds__(256) k_e_full3(const MeshParams3<R> m, const R *bnd, R dt, R dtdx, R dtdy,
+                                                 R dtdz) {
+    Idx3<R> q;
+    if (!cell_of_thread(m, q)) return;
+    const size_t P = m.plane;
+    R *EB = m.EB;
+    R *J = m.J;
+    R by_im, bz_im;
+    if (q.i > 0) {
+        by_im = EB[4 * P + q.c - 1];
+        bz_im = EB[5 * P + q.c - 1];
+    } else if (m.bc_x == 1) {
+        by_im = EB[4 * P + q.c + m.nx - 1];
+        bz_im = EB[5 * P + q.c + m.nx - 1];
+    } else {
+        const size_t b = (size_t)q.k * m.ny + q.j;
+        by_im = bnd[b];
+        bz_im = bnd[(size_t)m.ny * m.nz + b];
+    }
+    const R bx = EB[3 * P + q.c], by = EB[4 * P + q.c], bz = EB[5 * P + q.c];
+    EB[0 * P + q.c] += dtdy * (bz - EB[5 * P + q.cjm]) - dtdz * (by - EB[4 * P + q.ckm]) - dt * J[0 * P + q.c];
+    EB[1 * P + q.c] += dtdz * (bx - EB[3 * P + q.ckm]) - dtdx * (bz - bz_im) - dt * J[1 * P + q.c];
+    EB[2 * P + q.c] += dtdx * (by - by_im) - dtdy * (bx - EB[3 * P + q.cjm]) - dt * J[2 * P + q.c];
+    J[0 * P + q.c] = R(0);
+    J[1 * P + q.c] = R(0);
+    J[2 * P + q.c] = R(0);
+}
+
+}  // namespace
+
+template <typename R>
+cudaError_t launch_field_update3(const MeshParams3<R> &m, R *bnd, const double *prof, const LaserParams &L,
+                                 double dt, double dx, double dy, double dz, long long step, cudaStream_t st) {
+    const dim3 blk(128), grd((m.nx + 127) / 128, m.ny, m.nz);
+    const R hdx = (R)(0.5 * dt / dx), hdy = (R)(0.5 * dt / dy), hdz = (R)(0.5 * dt / dz);
+    k_b_half3<R><<<grd, blk, 0, st>>>(m, hdx, hdy, hdz);
+    if (m.bc_x == 0) {
+        double fz, fy;
+        laser_time_factors(L, ((double)step + 0.5) * dt, &fz, &fy);
+        k_boundary3<R><<<dim3((m.ny + 127) / 128, m.nz), 128, 0, st>>>(m, bnd, prof, fz, fy, dt / dx, dt / dy,
+                                                                       dt / dz);
+    }
+    k_e_full3<R><<<grd, blk, 0, st>>>(m, bnd, (R)dt, (R)(dt / dx), (R)(dt / dy), (R)(dt / dz));
+    k_b_half3<R><<<grd, blk, 0, st>>>(m, hdx, hdy, hdz);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_field_update3<float>(const MeshParams3<float> &, float *, const double *,
+                                                 const LaserParams &, double, double, double, double, long long,
+                                                 cudaStream_t);
+template cudaError_t launch_field_update3<double>(const MeshParams3<double> &, double *, const double *,
+                                                  const LaserParams &, double, double, double, double, long long,
+                                                  cudaStream_t);
+
+// transverse laser profile exp(-((y - yc)^2 + (z - zc)^2) / w0^2): [nz][ny] at
+// (y_j, z_{k+1/2}) (the Ez source), then [nz][ny] at (y_{j+1/2}, z_k) (Ey)
+void laser_profile3(const LaserParams &L, int ny, int nz, double dz, double *host) {
+    const double zc = 0.5 * nz * dz;
+    const size_t nb = (size_t)ny * nz;
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j) {
+            const double ya = (double)j * L.dy - L.yc, za = ((double)k + 0.5) * dz - zc;
+            const double yb = ((double)j + 0.5) * L.dy - L.yc, zb = (double)k * dz - zc;
+            const size_t b = (size_t)k * ny + j;
+            host[b] = std::exp(-(ya * ya + za * za) / (L.w0 * L.w0));
+            host[nb + b] = std::exp(-(yb * yb + zb * zb) / (L.w0 * L.w0));
+        }
+}

@@ -5,52 +5,11 @@
 
 #include "pic_device.cuh"
 #include "pic_kernels.h"
+#include "pic_ptx.cuh"
+
+using namespace pic_ptx;
 
 namespace {
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void fence_mbar_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar,
-                                            int x, int y, int z) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase) {
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}" : "=r"(ok) : "r"(smem_u32(bar)), "r"(phase) : "memory");
-    return ok != 0;
-}
-
-// bounded wait: about a second at most, then report and give up
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned phase) {
-    for (unsigned it = 0; it < (1u << 22); ++it) {
-        if (mbar_try_wait(bar, phase)) return true;
-        __nanosleep(64);
-    }
-    return false;
-}
 
 // a4 and the boundary rule shared by both paths; returns false if removed
 template <typename R>
@@ -106,20 +65,6 @@ struct SmemMeshT {
     __device__ __forceinline__ void j(int c, int x, int y, R v) const { atomicAdd(&Jw[c * WA + y * WX + x], v); }
 };
 
-__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-template <typename R>
-__device__ __forceinline__ void cp_async_r(R *dst, const R *src) {
-    if (sizeof(R) == 4)
-        cp_async4(dst, src);
-    else
-        cp_async8(dst, src);
-}
-
 // J window -> global J
 template <typename R>
 __device__ __forceinline__ void flush_add(R *dst, const R *src);
@@ -135,10 +80,6 @@ __device__ __forceinline__ void flush_add<double>(double *dst, const double *src
     for (int k = 0; k < 4; ++k)
         if (src[k] != 0.0) atomicAdd(dst + k, src[k]);
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
 template <int TX, int TY, typename R>
 __global__ void __launch_bounds__(kFusedThreads, sizeof(R) == 4 ? PIC_FUSED_MINB : 2)
     k_step_fused(const StepParams<R> P, const __grid_constant__ CUtensorMap tmapEB) {

@@ -1,0 +1,462 @@
+// k_particles3.cu -- 3D3V particle kernels: the fused a1-a5 step kernel (one
+// CTA per tile of TX x TY x TZ cells, 4D TMA-staged field window, shared-memory
+// current window) and the split a1-a4 / a5 kernels.
+#include <cuda.h>
+
+#include "pic_device3.cuh"
+#include "pic_kernels.h"
+#include "pic_ptx.cuh"
+
+using namespace pic_ptx;
+
+namespace {
+
+// a4 boundary rule: removal at the open x ends, periodic wraps
+template <typename R>
+__device__ __forceinline__ bool finish_move3(const MeshParams3<R> &m, int &ix1, int &iy1, int &iz1) {
+    bool alive = true;
+    if (m.bc_x == 0) {
+        alive = ix1 >= 2 && ix1 <= m.nx - 3;
+    } else {
+        if (ix1 < 0) ix1 += m.nx;
+        else if (ix1 >= m.nx) ix1 -= m.nx;
+    }
+    if (iy1 < 0) iy1 += m.ny;
+    else if (iy1 >= m.ny) iy1 -= m.ny;
+    if (iz1 < 0) iz1 += m.nz;
+    else if (iz1 >= m.nz) iz1 -= m.nz;
+    return alive;
+}
+
+constexpr int kThreads3 = 256;
+#ifndef PIC3_MINB
+#define PIC3_MINB 3  // resident CTAs per SM the register budget of the FP32 kernel is sized for
+#endif
+#ifndef PIC3_ACC
+#define PIC3_ACC 0   // 1: sum the in-cell currents of a cell's consecutive particles in registers
+#endif
+constexpr int kRec3 = 10;  // staged reals per particle: ox oy oz ux uy uz sx sy sz w (plus the cell word)
+
+template <int TX, int TY, int TZ, typename R>
+struct TileConst3 {
+    static constexpr int WX = window3_wx<R>(TX), WY = window3_w(TY), WZ = window3_w(TZ);
+    static constexpr int WA = WX * WY * WZ;     // current window [3][WZ][WY][WX]
+    static constexpr int FX = window3_fx<R>(TX);
+    static constexpr int FA = FX * WY * WZ;     // field window [6][WZ][WY][FX]
+    static constexpr int HX = window3_hx(), HY = window3_h(), HZ = window3_h();
+    // field window, current window, one record stage per thread
+    static constexpr size_t smem_bytes =
+        (size_t)(6 * FA + 3 * WA) * sizeof(R) + kThreads3 * (sizeof(uint32_t) + kRec3 * sizeof(R));
+};
+
+template <typename R, int WX, int WY, int WA, int FX, int FA>
+struct SmemMesh3T {
+    const R *F;
+    R *Jw;
+    __device__ __forceinline__ R f(int c, int x, int y, int z) const { return F[c * FA + (z * WY + y) * FX + x]; }
+    __device__ __forceinline__ void j(int c, int x, int y, int z, R v) const {
+        atomicAdd(&Jw[c * WA + (z * WY + y) * WX + x], v);
+    }
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Fused 3D step kernel.  Thread 0 stages the 6-component field window (x
+// margin 4 cells before the tile, row rounded up to 16 bytes; along y and z
+// the tile plus 1 + PIC3_MARGIN cells before and 2 + PIC3_MARGIN after) with
+// one 4D TMA load, zero-filled outside the mesh.  Each thread owns one record
+// slot in shared memory: it copies the record it is about to process into
+// registers and at once requests its next record into the same slot
+// (cp.async), so one record is always in flight while it computes.  A record
+// runs a1-a5 against shared memory when its stencil [cell-1, cell+2]^3 lies in
+// the window and in the mesh (no wrap), else against global memory through a
+// NodeBlock3 (wrapped offsets formed once, loads without branches).  In-cell
+// currents of consecutive particles of one cell (the layered tile order gives
+// a thread the same cell on every layer) are summed in registers.  The current
+// window is added to J at the end (16-byte vector atomics in float).
+// ---------------------------------------------------------------------------
+template <int TX, int TY, int TZ, typename R>
+__global__ void __launch_bounds__(kThreads3, sizeof(R) == 4 ? PIC3_MINB : 1)
+    k_step_fused3(const StepParams3<R> P, const __grid_constant__ CUtensorMap tmapEB) {
+    using TC = TileConst3<TX, TY, TZ, R>;
+    constexpr int WX = TC::WX, WY = TC::WY, WZ = TC::WZ, WA = TC::WA, FX = TC::FX, FA = TC::FA;
+    extern __shared__ __align__(1024) unsigned char dsm[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ double sdiag[kThreads3 / 32][8];
+    R *sF = reinterpret_cast<R *>(dsm);
+    R *sJ = sF + 6 * FA;
+    R *ring = sJ + 3 * WA;                                                // [kRec3][kThreads3]
+    uint32_t *cring = reinterpret_cast<uint32_t *>(ring + kRec3 * kThreads3);  // [kThreads3]
+    const MeshParams3<R> &m = P.m;
+
+    const int tile = blockIdx.x;
+    const int tz = tile / (P.t.ntx * P.t.nty);
+    const int rem = tile - tz * P.t.ntx * P.t.nty;
+    const int ty = rem / P.t.ntx, tx = rem - ty * P.t.ntx;
+    const int wx0 = tx * TX - TC::HX, wy0 = ty * TY - TC::HY, wz0 = tz * TZ - TC::HZ;
+    const int tid = threadIdx.x;
+
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        mbar_expect_tx(&bar, (unsigned)(6 * FA * sizeof(R)));
+        tma_load_4d(sF, &tmapEB, &bar, wx0, wy0, wz0, 0);
+    }
+
+    R *ring0 = ring + tid;
+    auto prefetch = [&](const DevSpecies3<R> &S, int slot, bool live) {
+        if (live) {
+            R *r = ring0;
+            cp_async4(cring + tid, S.cell + slot);
+            cp_async_r(r + 0 * kThreads3, S.ox + slot);
+            cp_async_r(r + 1 * kThreads3, S.oy + slot);
+            cp_async_r(r + 2 * kThreads3, S.oz + slot);
+            cp_async_r(r + 3 * kThreads3, S.ux + slot);
+            cp_async_r(r + 4 * kThreads3, S.uy + slot);
+            cp_async_r(r + 5 * kThreads3, S.uz + slot);
+            cp_async_r(r + 6 * kThreads3, S.sx + slot);
+            cp_async_r(r + 7 * kThreads3, S.sy + slot);
+            cp_async_r(r + 8 * kThreads3, S.sz + slot);
+            cp_async_r(r + 9 * kThreads3, S.w + slot);
+        }
+        cp_async_commit();
+    };
+
+    const bool diag = P.diag.on != 0;
+    int first = -1;
+    for (int sp = 0; sp < P.nsp && first < 0; ++sp)
+        if (P.sp[sp].mobile) first = sp;
+    if (first >= 0) {
+        const int beg = P.sp[first].tile_start[tile];
+        prefetch(P.sp[first], beg + tid, tid < P.sp[first].tile_start[tile + 1] - beg);
+    }
+    for (int i = tid; i < 3 * WA; i += kThreads3) sJ[i] = R(0);
+    __syncthreads();
+    if (!mbar_wait_bounded(&bar, 0)) {
+        if (tid == 0) atomicOr(P.err, PIC_EF_TIMEOUT);
+        cp_async_wait0();
+        return;
+    }
+
+    const SmemMesh3T<R, WX, WY, WA, FX, FA> sm{sF, sJ};
+    const int xlo = max(wx0 + 1, 1), xhi = min(wx0 + WX - 3, m.nx - 3);
+    const int ylo = max(wy0 + 1, 1), yhi = min(wy0 + WY - 3, m.ny - 3);
+    const int zlo = max(wz0 + 1, 1), zhi = min(wz0 + WZ - 3, m.nz - 3);
+    bool bad = false;
+    // in-cell currents summed per cell: window offset of the cell, 12 values
+    // (Jx at the 4 (y, z) edges, Jy at the 4 (x, z) edges, Jz at the 4 (x, y) edges)
+    constexpr int SY = WX, SZ = WX * WY;
+    int acc_key = -1;
+    R acc[12];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) acc[q] = R(0);
+    auto acc_flush = [&]() {
+        if (acc_key >= 0) {
+            const int k = acc_key;
+            atomicAdd(&sJ[k], acc[0]);
+            atomicAdd(&sJ[k + SY], acc[1]);
+            atomicAdd(&sJ[k + SZ], acc[2]);
+            atomicAdd(&sJ[k + SY + SZ], acc[3]);
+            atomicAdd(&sJ[WA + k], acc[4]);
+            atomicAdd(&sJ[WA + k + 1], acc[5]);
+            atomicAdd(&sJ[WA + k + SZ], acc[6]);
+            atomicAdd(&sJ[WA + k + 1 + SZ], acc[7]);
+            atomicAdd(&sJ[2 * WA + k], acc[8]);
+            atomicAdd(&sJ[2 * WA + k + 1], acc[9]);
+            atomicAdd(&sJ[2 * WA + k + SY], acc[10]);
+            atomicAdd(&sJ[2 * WA + k + 1 + SY], acc[11]);
+        }
+    };
+
+    for (int sp = 0; sp < P.nsp; ++sp) {
+        const DevSpecies3<R> &S = P.sp[sp];
+        if (!S.mobile) continue;
+        const int beg = S.tile_start[tile], len = S.tile_start[tile + 1] - beg;
+        const R qm = S.qm, a = S.a, q = S.q;
+        R dacc[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+        R dlo = R(0), dhi = R(0), dm = R(0), dshift = R(0);
+        if (diag) {
+            dlo = (R)P.diag.lo[sp];
+            dhi = (R)P.diag.hi[sp];
+            dm = (R)P.diag.m_mev[sp];
+            dshift = (R)P.diag.shift[sp];
+        }
+        if (sp != first) prefetch(S, beg + tid, tid < len);
+        for (int k0 = 0; k0 < len; k0 += kThreads3) {
+            const int k = k0 + tid;
+            cp_async_wait0();
+            if (k < len) {
+                const int slot = beg + k;
+                const R *r = ring0;
+                const uint32_t c = cring[tid];
+                const R ox = r[0 * kThreads3], oy = r[1 * kThreads3], oz = r[2 * kThreads3];
+                R u[3] = {r[3 * kThreads3], r[4 * kThreads3], r[5 * kThreads3]};
+                R spn[3] = {r[6 * kThreads3], r[7 * kThreads3], r[8 * kThreads3]};
+                const R w = r[9 * kThreads3];
+                // the slot is free again: request the next record
+                prefetch(S, beg + k + kThreads3, k + kThreads3 < len);
+                if (c != PIC_DEAD) {
+                    int ix, iy, iz;
+                    unpack_cell3(c, ix, iy, iz);
+                    const bool fast = ix >= xlo && ix <= xhi && iy >= ylo && iy <= yhi && iz >= zlo && iz <= zhi;
+                    R E[3], B[3];
+                    if (fast) {
+                        gather_eb3(sm, ix - wx0, iy - wy0, iz - wz0, ox, oy, oz, E, B);
+                    } else {
+                        const NodeBlock3<R> nb(m, ix, iy, iz, P.err);
+                        gather_eb3(nb, 1, 1, 1, ox, oy, oz, E, B);
+                    }
+                    push_spin(qm, a, m.dt, E, B, u, spn);
+                    const R gi = Real<R>::rsqrt(R(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                    int ix1 = ix, iy1 = iy, iz1 = iz;
+                    R ox1 = ox, oy1 = oy, oz1 = oz;
+                    advance_axis(ix1, ox1, u[0] * gi * m.dt_dx);
+                    advance_axis(iy1, oy1, u[1] * gi * m.dt_dy);
+                    advance_axis(iz1, oz1, u[2] * gi * m.dt_dz);
+                    const R qw = q * w;
+                    const bool in_cell = ix1 == ix && iy1 == iy && iz1 == iz;
+                    if (fast && in_cell && !PIC3_ACC) {
+                        R v[12];
+                        in_cell_weights3(ox, oy, oz, ox1, oy1, oz1, qw, m.dx_dt, m.dy_dt, m.dz_dt, v);
+                        deposit_in_cell3(sm, ix - wx0, iy - wy0, iz - wz0, v);
+                    } else if (fast && in_cell) {
+                        R v[12];
+                        in_cell_weights3(ox, oy, oz, ox1, oy1, oz1, qw, m.dx_dt, m.dy_dt, m.dz_dt, v);
+                        const int key = ((iz - wz0) * WY + (iy - wy0)) * WX + (ix - wx0);
+                        if (key != acc_key) {
+                            acc_flush();
+                            acc_key = key;
+#pragma unroll
+                            for (int q12 = 0; q12 < 12; ++q12) acc[q12] = v[q12];
+                        } else {
+#pragma unroll
+                            for (int q12 = 0; q12 < 12; ++q12) acc[q12] += v[q12];
+                        }
+                    } else if (fast) {
+                        deposit_esirkepov3(sm, ix - wx0, iy - wy0, iz - wz0, ox, oy, oz, ix1 - wx0, iy1 - wy0,
+                                           iz1 - wz0, ox1, oy1, oz1, qw, m.dx_dt, m.dy_dt, m.dz_dt);
+                    } else {
+                        const NodeBlock3<R> nb(m, ix, iy, iz, P.err);
+                        if (in_cell) {
+                            R v[12];
+                            in_cell_weights3(ox, oy, oz, ox1, oy1, oz1, qw, m.dx_dt, m.dy_dt, m.dz_dt, v);
+                            deposit_in_cell3(nb, 1, 1, 1, v);
+                        } else {
+                            deposit_esirkepov3(nb, 1, 1, 1, ox, oy, oz, ix1 - ix + 1, iy1 - iy + 1, iz1 - iz + 1,
+                                               ox1, oy1, oz1, qw, m.dx_dt, m.dy_dt, m.dz_dt);
+                        }
+                    }
+                    const bool alive = finish_move3(m, ix1, iy1, iz1);
+                    const R chk = u[0] * u[0] + u[1] * u[1] + u[2] * u[2] + spn[0] * spn[0] +
+                                  spn[1] * spn[1] + spn[2] * spn[2];
+                    bad |= !isfinite(chk);
+                    if (diag && alive) {
+                        const R e = ekin_mev(dm, u[0], u[1], u[2]);
+                        if (e >= dlo && e < dhi) {
+                            const R ep = e - dshift;
+                            dacc[0] += w;
+                            dacc[1] += w * spn[0];
+                            dacc[2] += w * spn[1];
+                            dacc[3] += w * spn[2];
+                            dacc[4] += w * ep;
+                            dacc[5] += w * ep * ep;
+                            dacc[6] += R(1);
+                        }
+                    }
+                    S.cell[slot] = alive ? pack_cell3(ix1, iy1, iz1) : PIC_DEAD;
+                    S.ox[slot] = ox1;
+                    S.oy[slot] = oy1;
+                    S.oz[slot] = oz1;
+                    S.ux[slot] = u[0];
+                    S.uy[slot] = u[1];
+                    S.uz[slot] = u[2];
+                    S.sx[slot] = spn[0];
+                    S.sy[slot] = spn[1];
+                    S.sz[slot] = spn[2];
+                }
+            }
+        }
+        cp_async_wait0();
+        if (diag) {
+            const int lane = tid & 31, wid = tid >> 5;
+            for (int qd = 0; qd < 7; ++qd) {
+                double v = (double)dacc[qd];
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+                if (lane == 0) sdiag[wid][qd] = v;
+            }
+            __syncthreads();
+            if (tid < 7) {
+                double t = 0.0;
+                for (int w8 = 0; w8 < kThreads3 / 32; ++w8) t += sdiag[w8][tid];
+                P.diag.rows[((size_t)sp * 8 + tid) * gridDim.x + blockIdx.x] = t;
+            }
+            __syncthreads();
+        }
+    }
+    acc_flush();
+    if (bad) atomicOr(P.err, PIC_EF_NAN);
+    __syncthreads();
+
+    // current window -> J: rows outside the mesh and all-zero groups skipped
+    if constexpr (sizeof(R) == 4) {
+        constexpr int WQ = WX / 4;
+        for (int qd = tid; qd < 3 * WZ * WY * WQ; qd += kThreads3) {
+            const int row = qd / WQ, xq = qd - row * WQ;
+            const int c = row / (WZ * WY), zy = row - c * WZ * WY;
+            const int z = zy / WY, y = zy - z * WY;
+            const int gz = wz0 + z, gy = wy0 + y, gx = wx0 + 4 * xq;
+            if (gz < 0 || gz >= m.nz || gy < 0 || gy >= m.ny || gx < 0 || gx >= m.ld) continue;
+            const float4 v = *reinterpret_cast<const float4 *>(&sJ[c * WA + zy * WX + 4 * xq]);
+            if (v.x == 0.f && v.y == 0.f && v.z == 0.f && v.w == 0.f) continue;
+            atomicAdd(reinterpret_cast<float4 *>(&m.J[c * m.plane + ((size_t)gz * m.ny + gy) * m.ld + gx]), v);
+        }
+    } else {
+        for (int e = tid; e < 3 * WA; e += kThreads3) {
+            const int row = e / WX, x = e - row * WX;
+            const int c = row / (WZ * WY), zy = row - c * WZ * WY;
+            const int z = zy / WY, y = zy - z * WY;
+            const int gz = wz0 + z, gy = wy0 + y, gx = wx0 + x;
+            if (gz < 0 || gz >= m.nz || gy < 0 || gy >= m.ny || gx < 0 || gx >= m.nx) continue;
+            const R v = sJ[e];
+            if (v != R(0)) atomicAdd(&m.J[c * m.plane + ((size_t)gz * m.ny + gy) * m.ld + gx], v);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Split path, a1-a4 (one thread per slot, global-memory gather); keeps x^n for
+// the deposit and stores the unwrapped new cell shifted by +1 per axis.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(256) k_push_split3(const StepParams3<R> P, int s) {
+    const DevSpecies3<R> &S = P.sp[s];
+    const MeshParams3<R> &m = P.m;
+    unsigned bad = 0;
+    const int n = *S.n;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const uint32_t c = S.cell[p];
+        S.cell_old[p] = c;
+        if (c == PIC_DEAD) continue;
+        int ix, iy, iz;
+        unpack_cell3(c, ix, iy, iz);
+        const R ox = S.ox[p], oy = S.oy[p], oz = S.oz[p];
+        R u[3] = {S.ux[p], S.uy[p], S.uz[p]};
+        R sp[3] = {S.sx[p], S.sy[p], S.sz[p]};
+        R E[3], B[3];
+        const NodeBlock3<R> nb(m, ix, iy, iz, P.err);
+        gather_eb3(nb, 1, 1, 1, ox, oy, oz, E, B);
+        push_spin(S.qm, S.a, m.dt, E, B, u, sp);
+        const R gi = Real<R>::rsqrt(R(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        int ix1 = ix, iy1 = iy, iz1 = iz;
+        R ox1 = ox, oy1 = oy, oz1 = oz;
+        advance_axis(ix1, ox1, u[0] * gi * m.dt_dx);
+        advance_axis(iy1, oy1, u[1] * gi * m.dt_dy);
+        advance_axis(iz1, oz1, u[2] * gi * m.dt_dz);
+        if (!finite3(u) || !finite3(sp)) bad |= PIC_EF_NAN;
+        S.ox_old[p] = ox;
+        S.oy_old[p] = oy;
+        S.oz_old[p] = oz;
+        S.cell[p] = pack_cell3(ix1 + 1, iy1 + 1, iz1 + 1);
+        S.ox[p] = ox1;
+        S.oy[p] = oy1;
+        S.oz[p] = oz1;
+        S.ux[p] = u[0];
+        S.uy[p] = u[1];
+        S.uz[p] = u[2];
+        S.sx[p] = sp[0];
+        S.sy[p] = sp[1];
+        S.sz[p] = sp[2];
+    }
+    if (bad) atomicOr(P.err, bad);
+}
+
+// Split path, a5: current of the recorded move, then the wrap / removal.
+template <typename R>
+__global__ void __launch_bounds__(256) k_deposit_split3(const StepParams3<R> P, int s) {
+    const DevSpecies3<R> &S = P.sp[s];
+    const MeshParams3<R> &m = P.m;
+    const int n = *S.n;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const uint32_t c0 = S.cell_old[p];
+        if (c0 == PIC_DEAD) continue;
+        int ix, iy, iz, ix1, iy1, iz1;
+        unpack_cell3(c0, ix, iy, iz);
+        unpack_cell3(S.cell[p], ix1, iy1, iz1);
+        ix1 -= 1;
+        iy1 -= 1;
+        iz1 -= 1;
+        const R ox = S.ox_old[p], oy = S.oy_old[p], oz = S.oz_old[p];
+        const R ox1 = S.ox[p], oy1 = S.oy[p], oz1 = S.oz[p];
+        const R qw = S.q * S.w[p];
+        const NodeBlock3<R> nb(m, ix, iy, iz, P.err);
+        if (ix1 == ix && iy1 == iy && iz1 == iz) {
+            R v[12];
+            in_cell_weights3(ox, oy, oz, ox1, oy1, oz1, qw, m.dx_dt, m.dy_dt, m.dz_dt, v);
+            deposit_in_cell3(nb, 1, 1, 1, v);
+        } else {
+            deposit_esirkepov3(nb, 1, 1, 1, ox, oy, oz, ix1 - ix + 1, iy1 - iy + 1, iz1 - iz + 1, ox1, oy1, oz1, qw,
+                               m.dx_dt, m.dy_dt, m.dz_dt);
+        }
+        const bool alive = finish_move3(m, ix1, iy1, iz1);
+        S.cell[p] = alive ? pack_cell3(ix1, iy1, iz1) : PIC_DEAD;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <int TX, int TY, int TZ, typename R>
+static cudaError_t launch_fused3_t(const StepParams3<R> &P, const CUtensorMap &tmapEB, cudaStream_t st) {
+    using TC = TileConst3<TX, TY, TZ, R>;
+    constexpr size_t smem = TC::smem_bytes;
+    if (P.t.WX != TC::WX || P.t.WY != TC::WY || P.t.WZ != TC::WZ || P.t.FX != TC::FX || P.t.HX != TC::HX ||
+        P.t.HY != TC::HY || P.t.HZ != TC::HZ)
+        return cudaErrorInvalidValue;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_step_fused3<TX, TY, TZ, R>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    k_step_fused3<TX, TY, TZ, R><<<P.t.ntx * P.t.nty * P.t.ntz, kThreads3, smem, st>>>(P, tmapEB);
+    return cudaGetLastError();
+}
+
+bool fused3_tile_supported(int tx, int ty, int tz) {
+    return (tx == 8 && ty == 8 && tz == 4) || (tx == 16 && ty == 4 && tz == 4) || (tx == 8 && ty == 4 && tz == 4);
+}
+
+template <typename R>
+cudaError_t launch_step_fused3(const StepParams3<R> &P, const CUtensorMap &tmapEB, cudaStream_t st) {
+    const int tx = P.t.TX, ty = P.t.TY, tz = P.t.TZ;
+    if (tx == 8 && ty == 8 && tz == 4) return launch_fused3_t<8, 8, 4, R>(P, tmapEB, st);
+    if (tx == 16 && ty == 4 && tz == 4) return launch_fused3_t<16, 4, 4, R>(P, tmapEB, st);
+    if (tx == 8 && ty == 4 && tz == 4) return launch_fused3_t<8, 4, 4, R>(P, tmapEB, st);
+    return cudaErrorInvalidValue;
+}
+
+static int blocks3_for(int n) {
+    int b = (n + 255) / 256;
+    return b < 1 ? 1 : (b > 152 * 32 ? 152 * 32 : b);
+}
+
+template <typename R>
+cudaError_t launch_push_split3(const StepParams3<R> &P, int s, int n_upper, cudaStream_t st) {
+    k_push_split3<R><<<blocks3_for(n_upper), 256, 0, st>>>(P, s);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_deposit_split3(const StepParams3<R> &P, int s, int n_upper, cudaStream_t st) {
+    k_deposit_split3<R><<<blocks3_for(n_upper), 256, 0, st>>>(P, s);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_step_fused3<float>(const StepParams3<float> &, const CUtensorMap &, cudaStream_t);
+template cudaError_t launch_step_fused3<double>(const StepParams3<double> &, const CUtensorMap &, cudaStream_t);
+template cudaError_t launch_push_split3<float>(const StepParams3<float> &, int, int, cudaStream_t);
+template cudaError_t launch_push_split3<double>(const StepParams3<double> &, int, int, cudaStream_t);
+template cudaError_t launch_deposit_split3<float>(const StepParams3<float> &, int, int, cudaStream_t);
+template cudaError_t launch_deposit_split3<double>(const StepParams3<double> &, int, int, cudaStream_t);

@@ -188,6 +188,71 @@ __global__ void __launch_bounds__(RT) k_gauss(const MeshParams<R> m, const R *rh
     }
 }
 
+// 3D3V: CIC charge density at the nodes (periodic y, z; x wraps when periodic)
+template <typename R>
+__global__ void k_rho3(const DevSpecies3<R> S, const MeshParams3<R> m, R *rho) {
+    const int n = *S.n;
+    const size_t slab = (size_t)m.ny * m.ld;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const uint32_t c = S.cell[p];
+        if (c == PIC_DEAD) continue;
+        int ix, iy, iz;
+        unpack_cell3(c, ix, iy, iz);
+        const R one = R(1), qw = S.q * S.w[p];
+        const R wx[2] = {one - S.ox[p], S.ox[p]}, wy[2] = {one - S.oy[p], S.oy[p]}, wz[2] = {one - S.oz[p], S.oz[p]};
+        const int xs[2] = {ix, ix + 1 == m.nx ? 0 : ix + 1};
+        const int ys[2] = {iy, iy + 1 == m.ny ? 0 : iy + 1};
+        const int zs[2] = {iz, iz + 1 == m.nz ? 0 : iz + 1};
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int d = 0; d < 2; ++d)
+                    atomicAdd(&rho[zs[d] * slab + (size_t)ys[b] * m.ld + xs[a]], qw * wx[a] * wy[b] * wz[d]);
+    }
+}
+
+// 3D3V div E - rho - rho_bg on nodes with i in [i0, i1]: block max |r| and sum r^2
+template <typename R>
+__global__ void __launch_bounds__(RT) k_gauss3(const MeshParams3<R> m, const R *rho, const R *rho_bg, double idx,
+                                               double idy, double idz, int i0, int i1, double *partials) {
+    double vmax = 0.0, ssq = 0.0;
+    const int w = i1 - i0 + 1;
+    const long long total = (long long)w * m.ny * m.nz;
+    const size_t slab = (size_t)m.ny * m.ld;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long jk = q / w;
+        const int i = i0 + (int)(q - jk * w);
+        const int k = (int)(jk / m.ny), j = (int)(jk - (long long)k * m.ny);
+        const int im = i == 0 ? m.nx - 1 : i - 1, jm = j == 0 ? m.ny - 1 : j - 1, km = k == 0 ? m.nz - 1 : k - 1;
+        const size_t c = k * slab + (size_t)j * m.ld + i;
+        const double div = ((double)m.EB[c] - (double)m.EB[k * slab + (size_t)j * m.ld + im]) * idx +
+                           ((double)m.EB[m.plane + c] - (double)m.EB[m.plane + k * slab + (size_t)jm * m.ld + i]) * idy +
+                           ((double)m.EB[2 * m.plane + c] -
+                            (double)m.EB[2 * m.plane + km * slab + (size_t)j * m.ld + i]) * idz;
+        const double r = div - (double)rho[c] - (double)rho_bg[c];
+        vmax = fmax(vmax, fabs(r));
+        ssq += r * r;
+    }
+    __shared__ double smax[RT], ssum[RT];
+    smax[threadIdx.x] = vmax;
+    ssum[threadIdx.x] = ssq;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + o]);
+            ssum[threadIdx.x] += ssum[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = smax[0];
+        partials[2 * blockIdx.x + 1] = ssum[0];
+    }
+}
+
 template <typename R>
 __global__ void k_negate(const R *src, R *dst, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
@@ -311,6 +376,23 @@ cudaError_t launch_gauss(const MeshParams<R> &m, const R *rho, const R *rho_bg, 
 }
 
 template <typename R>
+cudaError_t launch_rho3(const DevSpecies3<R> &S, int n_upper, const MeshParams3<R> &m, R *rho, cudaStream_t st) {
+    int b = (n_upper + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    if (b < 1) b = 1;
+    k_rho3<R><<<b, 256, 0, st>>>(S, m, rho);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_gauss3(const MeshParams3<R> &m, const R *rho, const R *rho_bg, double dx, double dy, double dz,
+                          int i0, int i1, double *partials, double *result, cudaStream_t st) {
+    k_gauss3<R><<<RB, RT, 0, st>>>(m, rho, rho_bg, 1.0 / dx, 1.0 / dy, 1.0 / dz, i0, i1, partials);
+    k_final_maxsum<<<1, RT, 0, st>>>(partials, RB, result);
+    return cudaGetLastError();
+}
+
+template <typename R>
 cudaError_t launch_negate_copy(const R *src, R *dst, size_t n, cudaStream_t st) {
     k_negate<R><<<152 * 4, 256, 0, st>>>(src, dst, n);
     return cudaGetLastError();
@@ -321,7 +403,10 @@ cudaError_t launch_negate_copy(const R *src, R *dst, size_t n, cudaStream_t st) 
     template cudaError_t launch_rho<R>(const DevSpecies<R> &, int, const MeshParams<R> &, R *, cudaStream_t); \
     template cudaError_t launch_gauss<R>(const MeshParams<R> &, const R *, const R *, double, double, int, int,  \
                                          double *, double *, cudaStream_t);                                 \
-    template cudaError_t launch_negate_copy<R>(const R *, R *, size_t, cudaStream_t);
+    template cudaError_t launch_negate_copy<R>(const R *, R *, size_t, cudaStream_t);                    \
+    template cudaError_t launch_rho3<R>(const DevSpecies3<R> &, int, const MeshParams3<R> &, R *, cudaStream_t); \
+    template cudaError_t launch_gauss3<R>(const MeshParams3<R> &, const R *, const R *, double, double, double, \
+                                          int, int, double *, double *, cudaStream_t);
 PIC_INST(float)
 PIC_INST(double)
 #undef PIC_INST

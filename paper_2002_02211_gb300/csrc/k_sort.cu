@@ -9,7 +9,9 @@
 // cell on every pass through the layers, which the fused kernel uses to sum
 // the in-cell currents in registers.  Steps: rank of each particle in its
 // cell (atomics), per-tile layout (block min and scan over the cells),
-// exclusive scan of the tile totals, scatter.
+// exclusive scan of the tile totals, scatter.  The 2D3V and 3D3V layouts
+// differ only in the cell packing and the tile key.
+#include "pic_device3.cuh"
 #include "pic_kernels.h"
 
 namespace {
@@ -35,15 +37,59 @@ __global__ void k_unpack(const uint32_t *cell, int32_t *ix, int32_t *iy, int n) 
     }
 }
 
-__device__ __forceinline__ int cell_key(uint32_t c, const TileGeom t, int &tile) {
-    const int ix = (int)(c & 0xFFFFu), iy = (int)(c >> 16);
-    const int tx = ix / t.TX, ty = iy / t.TY;
-    tile = ty * t.ntx + tx;
-    return tile * (t.TX * t.TY) + (iy - ty * t.TY) * t.TX + (ix - tx * t.TX);
+__global__ void k_pack3(const int32_t *ix, const int32_t *iy, const int32_t *iz, uint32_t *cell, int n, int xlo,
+                        int xhi, int ny, int nz, unsigned *err) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const int x = ix[p], y = iy[p], z = iz[p];
+        if (x < xlo || x > xhi || y < 0 || y >= ny || z < 0 || z >= nz) {
+            atomicOr(err, PIC_EF_RANGE);
+            cell[p] = PIC_DEAD;
+        } else {
+            cell[p] = pack_cell3(x, y, z);
+        }
+    }
 }
 
+__global__ void k_unpack3(const uint32_t *cell, int32_t *ix, int32_t *iy, int32_t *iz, int n) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const uint32_t c = cell[p];
+        int x = -1, y = -1, z = -1;
+        if (c != PIC_DEAD) unpack_cell3(c, x, y, z);
+        ix[p] = x;
+        iy[p] = y;
+        iz[p] = z;
+    }
+}
+
+// sort key of a packed cell: global index of (tile, cell inside the tile)
+struct Key2 {
+    TileGeom t;
+    __device__ __forceinline__ int operator()(uint32_t c, int &tile) const {
+        const int ix = (int)(c & 0xFFFFu), iy = (int)(c >> 16);
+        const int tx = ix / t.TX, ty = iy / t.TY;
+        tile = ty * t.ntx + tx;
+        return tile * (t.TX * t.TY) + (iy - ty * t.TY) * t.TX + (ix - tx * t.TX);
+    }
+    int cells() const { return t.TX * t.TY; }
+    int tiles() const { return t.ntx * t.nty; }
+};
+
+struct Key3 {
+    TileGeom3 t;
+    __device__ __forceinline__ int operator()(uint32_t c, int &tile) const {
+        int ix, iy, iz;
+        unpack_cell3(c, ix, iy, iz);
+        const int tx = ix / t.TX, ty = iy / t.TY, tz = iz / t.TZ;
+        tile = (tz * t.nty + ty) * t.ntx + tx;
+        return tile * (t.TX * t.TY * t.TZ) + ((iz - tz * t.TZ) * t.TY + (iy - ty * t.TY)) * t.TX + (ix - tx * t.TX);
+    }
+    int cells() const { return t.TX * t.TY * t.TZ; }
+    int tiles() const { return t.ntx * t.nty * t.ntz; }
+};
+
 // per-cell counts and each particle's rank inside its cell (-1: removed)
-__global__ void k_rank(const uint32_t *cell, const int32_t *n_src, const TileGeom t, int32_t *cell_count,
+template <class K>
+__global__ void k_rank(const uint32_t *cell, const int32_t *n_src, const K key, int32_t *cell_count,
                        int32_t *rank) {
     const int n = *n_src;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
@@ -51,7 +97,7 @@ __global__ void k_rank(const uint32_t *cell, const int32_t *n_src, const TileGeo
         int r = -1;
         if (c != PIC_DEAD) {
             int tile;
-            r = atomicAdd(&cell_count[cell_key(c, t, tile)], 1);
+            r = atomicAdd(&cell_count[key(c, tile)], 1);
         }
         rank[p] = r;
     }
@@ -116,30 +162,30 @@ __global__ void __launch_bounds__(1024) k_scan(const int32_t *count, int nt, int
     }
 }
 
+// the arrays a sort moves: the cell word, nf reals and the id
 template <typename R>
-__global__ void k_scatter(const DevSpecies<R> src, const DevSpecies<R> dst, const TileGeom t,
-                          const int32_t *rank, const int32_t *tile_start, const int32_t *tile_R,
-                          const int32_t *cell_off) {
+struct SortArrays {
+    uint32_t *cell;
+    R *f[10];
+    int32_t *id;
+    const int32_t *n;
+};
+
+template <typename R, int NF, class K>
+__global__ void k_scatter(const SortArrays<R> src, const SortArrays<R> dst, const K kf, const int32_t *rank,
+                          const int32_t *tile_start, const int32_t *tile_R, const int32_t *cell_off, int C) {
     const int n = *src.n;
-    const int C = t.TX * t.TY;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
         const int r = rank[p];
         if (r < 0) continue;
         const uint32_t c = src.cell[p];
         int tile;
-        const int key = cell_key(c, t, tile);
-        const int lc = key - tile * C, R = tile_R[tile];
-        const int pos = tile_start[tile] + (r < R ? r * C + lc : R * C + cell_off[key] + (r - R));
+        const int key = kf(c, tile);
+        const int lc = key - tile * C, Rl = tile_R[tile];
+        const int pos = tile_start[tile] + (r < Rl ? r * C + lc : Rl * C + cell_off[key] + (r - Rl));
         dst.cell[pos] = c;
-        dst.ox[pos] = src.ox[p];
-        dst.oy[pos] = src.oy[p];
-        dst.ux[pos] = src.ux[p];
-        dst.uy[pos] = src.uy[p];
-        dst.uz[pos] = src.uz[p];
-        dst.sx[pos] = src.sx[p];
-        dst.sy[pos] = src.sy[p];
-        dst.sz[pos] = src.sz[p];
-        dst.w[pos] = src.w[p];
+#pragma unroll
+        for (int k = 0; k < NF; ++k) dst.f[k][pos] = src.f[k][p];
         dst.id[pos] = src.id[p];
     }
 }
@@ -164,6 +210,48 @@ cudaError_t launch_unpack_cells(const uint32_t *cell, int32_t *ix, int32_t *iy, 
     return cudaGetLastError();
 }
 
+cudaError_t launch_pack_cells3(const int32_t *ix, const int32_t *iy, const int32_t *iz, uint32_t *cell, int n,
+                               int xlo, int xhi, int ny, int nz, unsigned *err, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    k_pack3<<<grid_for(n), 256, 0, st>>>(ix, iy, iz, cell, n, xlo, xhi, ny, nz, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_cells3(const uint32_t *cell, int32_t *ix, int32_t *iy, int32_t *iz, int n,
+                                 cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    k_unpack3<<<grid_for(n), 256, 0, st>>>(cell, ix, iy, iz, n);
+    return cudaGetLastError();
+}
+
+namespace {
+template <typename R, int NF, class K>
+cudaError_t tile_sort(const SortArrays<R> &src, const SortArrays<R> &dst, const K &key, const SortScratch &w,
+                      int32_t *tile_start, int32_t *n_tmp, int n_upper, cudaStream_t st) {
+    const int nt = key.tiles(), C = key.cells();
+    cudaError_t e = cudaMemsetAsync(w.cell_count, 0, sizeof(int32_t) * (size_t)nt * C, st);
+    if (e != cudaSuccess) return e;
+    const int g = grid_for(n_upper);
+    k_rank<K><<<g, 256, 0, st>>>(src.cell, src.n, key, w.cell_count, w.rank);
+    k_layout<<<nt, C, 0, st>>>(w.cell_count, C, w.cell_off, w.tile_R, w.tile_total);
+    k_scan<<<1, 1024, 0, st>>>(w.tile_total, nt, tile_start, w.cursor, n_tmp);
+    k_scatter<R, NF, K><<<g, 256, 0, st>>>(src, dst, key, w.rank, tile_start, w.tile_R, w.cell_off, C);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(const_cast<int32_t *>(src.n), n_tmp, sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+}
+
+template <typename R>
+SortArrays<R> arrays2(const DevSpecies<R> &S) {
+    return SortArrays<R>{S.cell, {S.ox, S.oy, S.ux, S.uy, S.uz, S.sx, S.sy, S.sz, S.w, nullptr}, S.id, S.n};
+}
+
+template <typename R>
+SortArrays<R> arrays3(const DevSpecies3<R> &S) {
+    return SortArrays<R>{S.cell, {S.ox, S.oy, S.oz, S.ux, S.uy, S.uz, S.sx, S.sy, S.sz, S.w}, S.id, S.n};
+}
+}  // namespace
+
 // n_upper bounds the source count (sizes the grids); the device counter
 // *src.n is read by the kernels and replaced by the sorted count at the end.
 // Scratch: cell_count and cell_off [ntiles * C], tile_R and tile_total
@@ -172,18 +260,22 @@ template <typename R>
 cudaError_t launch_tile_sort(const DevSpecies<R> &src, const DevSpecies<R> &dst, const TileGeom &t,
                              const SortScratch &w, int32_t *tile_start, int32_t *n_tmp, int n_upper,
                              cudaStream_t st) {
-    const int nt = t.ntx * t.nty, C = t.TX * t.TY;
-    cudaError_t e = cudaMemsetAsync(w.cell_count, 0, sizeof(int32_t) * (size_t)nt * C, st);
-    if (e != cudaSuccess) return e;
-    const int g = grid_for(n_upper);
-    k_rank<<<g, 256, 0, st>>>(src.cell, src.n, t, w.cell_count, w.rank);
-    k_layout<<<nt, C, 0, st>>>(w.cell_count, C, w.cell_off, w.tile_R, w.tile_total);
-    k_scan<<<1, 1024, 0, st>>>(w.tile_total, nt, tile_start, w.cursor, n_tmp);
-    k_scatter<R><<<g, 256, 0, st>>>(src, dst, t, w.rank, tile_start, w.tile_R, w.cell_off);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    return cudaMemcpyAsync(const_cast<int32_t *>(src.n), n_tmp, sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+    return tile_sort<R, 9>(arrays2(src), arrays2(dst), Key2{t}, w, tile_start, n_tmp, n_upper, st);
 }
+
+template <typename R>
+cudaError_t launch_tile_sort3(const DevSpecies3<R> &src, const DevSpecies3<R> &dst, const TileGeom3 &t,
+                              const SortScratch &w, int32_t *tile_start, int32_t *n_tmp, int n_upper,
+                              cudaStream_t st) {
+    return tile_sort<R, 10>(arrays3(src), arrays3(dst), Key3{t}, w, tile_start, n_tmp, n_upper, st);
+}
+
+template cudaError_t launch_tile_sort3<float>(const DevSpecies3<float> &, const DevSpecies3<float> &,
+                                              const TileGeom3 &, const SortScratch &, int32_t *, int32_t *, int,
+                                              cudaStream_t);
+template cudaError_t launch_tile_sort3<double>(const DevSpecies3<double> &, const DevSpecies3<double> &,
+                                               const TileGeom3 &, const SortScratch &, int32_t *, int32_t *, int,
+                                               cudaStream_t);
 
 template cudaError_t launch_tile_sort<float>(const DevSpecies<float> &, const DevSpecies<float> &,
                                              const TileGeom &, const SortScratch &, int32_t *, int32_t *, int,

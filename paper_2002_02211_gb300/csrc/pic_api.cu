@@ -23,16 +23,20 @@ constexpr double kMec2Mev = 0.51099895;
 struct SpeciesBuf {
     uint32_t *cell = nullptr;
     void *f[9] = {};  // ox oy ux uy uz sx sy sz w (float or double)
+    void *oz = nullptr;  // 3D3V only
     int32_t *id = nullptr;
 };
 
 struct Ctx {
     pic_config_t cfg{};
     int device = 0;
-    double dt = 0, dx = 0, dy = 0;
+    int dim = 2;
+    double dt = 0, dx = 0, dy = 0, dz = 0;
     int ld = 0;
-    size_t plane = 0;
+    size_t plane = 0;  // elements of one mesh component: ny * ld (2D3V), nz * ny * ld (3D3V)
+    size_t bnd_n = 0;  // left boundary values per component: ny (2D3V), nz * ny (3D3V)
     TileGeom tg{};
+    TileGeom3 tg3{};
     int ntiles = 0;
     int rb = 4;  // bytes per real: 4 for the FP32 path, 8 for the FP64 instantiation
     void *EB = nullptr, *J = nullptr, *bnd = nullptr, *rho = nullptr, *rho_bg = nullptr;
@@ -43,14 +47,14 @@ struct Ctx {
     int n_upper[PIC_MAX_SPECIES] = {};  // host bound on the device slot counts (sizes grids)
     int32_t *tile_start[PIC_MAX_SPECIES] = {};
     uint32_t *cell_old[PIC_MAX_SPECIES] = {};
-    void *old_f[PIC_MAX_SPECIES][3] = {};  // ox_old, oy_old, vz
+    void *old_f[PIC_MAX_SPECIES][3] = {};  // ox_old, oy_old, then vz (2D3V) or oz_old (3D3V)
     int32_t *tile_count = nullptr, *tile_cursor = nullptr;
     int32_t *cell_count = nullptr, *cell_off = nullptr, *tile_R = nullptr;
     int32_t *n_dev = nullptr;  // [PIC_MAX_SPECIES + 1] slot counts; the last entry is sort scratch
-    int32_t *scratch_i32 = nullptr;  // 2 * max capacity, for ix / iy transfers
+    int32_t *scratch_i32 = nullptr;  // 3 * max capacity, for ix / iy / iz transfers
     unsigned *err = nullptr;
     double *partials = nullptr, *result = nullptr;
-    double *laser_prof = nullptr;  // [2][ny] transverse profile at y_j, y_{j+1/2}
+    double *laser_prof = nullptr;  // [2][bnd_n] transverse profile at the Ez and Ey source points
     double *hist = nullptr;        // [PIC_MAX_HIST_BINS][5] energy spectrum
     // in-step Eq. (4) diagnostics
     int diag_every = 0;
@@ -145,6 +149,67 @@ StepParams<R> step_params(Ctx *c) {
     return P;
 }
 
+template <typename R>
+DevSpecies3<R> dev_species3(Ctx *c, int s, int which) {
+    const DevSpecies<R> d = dev_species<R>(c, s, which);
+    DevSpecies3<R> e{};
+    e.cell = d.cell;
+    e.ox = d.ox;
+    e.oy = d.oy;
+    e.oz = static_cast<R *>(c->buf[s][which].oz);
+    e.ux = d.ux;
+    e.uy = d.uy;
+    e.uz = d.uz;
+    e.sx = d.sx;
+    e.sy = d.sy;
+    e.sz = d.sz;
+    e.w = d.w;
+    e.id = d.id;
+    e.tile_start = d.tile_start;
+    e.cell_old = d.cell_old;
+    e.ox_old = d.ox_old;
+    e.oy_old = d.oy_old;
+    e.oz_old = static_cast<R *>(c->old_f[s][2]);
+    e.qm = d.qm;
+    e.q = d.q;
+    e.a = d.a;
+    e.mobile = d.mobile;
+    e.n = d.n;
+    return e;
+}
+
+template <typename R>
+MeshParams3<R> mesh3(Ctx *c) {
+    MeshParams3<R> m{};
+    m.nx = c->cfg.nx;
+    m.ny = c->cfg.ny;
+    m.nz = c->cfg.nz;
+    m.ld = c->ld;
+    m.bc_x = c->cfg.bc_x;
+    m.dt = (R)c->dt;
+    m.dt_dx = (R)(c->dt / c->dx);
+    m.dt_dy = (R)(c->dt / c->dy);
+    m.dt_dz = (R)(c->dt / c->dz);
+    m.dx_dt = (R)(c->dx / c->dt);
+    m.dy_dt = (R)(c->dy / c->dt);
+    m.dz_dt = (R)(c->dz / c->dt);
+    m.EB = static_cast<R *>(c->EB);
+    m.J = static_cast<R *>(c->J);
+    m.plane = c->plane;
+    return m;
+}
+
+template <typename R>
+StepParams3<R> step_params3(Ctx *c) {
+    StepParams3<R> P{};
+    P.m = mesh3<R>(c);
+    P.t = c->tg3;
+    P.nsp = c->cfg.nspecies;
+    for (int s = 0; s < P.nsp; ++s) P.sp[s] = dev_species3<R>(c, s, c->cur[s]);
+    P.err = c->err;
+    return P;
+}
+
 // runs f(R{}) with R the context's real type
 template <class F>
 auto with_real(Ctx *c, F &&f) {
@@ -163,7 +228,37 @@ LaserParams laser(Ctx *c) {
     return L;
 }
 
+void choose_tiles3(Ctx *c) {
+    int tx = c->cfg.tile_x, ty = c->cfg.tile_y, tz = c->cfg.tile_z;
+    if (tx <= 0 || ty <= 0 || tz <= 0) {
+        tx = 16;
+        ty = 4;
+        tz = 4;
+    }
+    TileGeom3 &t = c->tg3;
+    t.TX = tx;
+    t.TY = ty;
+    t.TZ = tz;
+    t.WX = c->rb == 8 ? window3_wx<double>(tx) : window3_wx<float>(tx);
+    t.FX = c->rb == 8 ? window3_fx<double>(tx) : window3_fx<float>(tx);
+    t.WY = window3_w(ty);
+    t.WZ = window3_w(tz);
+    t.HX = window3_hx();
+    t.HY = window3_h();
+    t.HZ = window3_h();
+    t.ntx = (c->cfg.nx + tx - 1) / tx;
+    t.nty = (c->cfg.ny + ty - 1) / ty;
+    t.ntz = (c->cfg.nz + tz - 1) / tz;
+    c->ntiles = t.ntx * t.nty * t.ntz;
+}
+
+int tile_cells(const Ctx *c) { return c->dim == 3 ? c->tg3.TX * c->tg3.TY * c->tg3.TZ : c->tg.TX * c->tg.TY; }
+
 void choose_tiles(Ctx *c) {
+    if (c->dim == 3) {
+        choose_tiles3(c);
+        return;
+    }
     int tx = c->cfg.tile_x, ty = c->cfg.tile_y;
     if (tx <= 0 || ty <= 0) {
         const long long cells = (long long)c->cfg.nx * c->cfg.ny;
@@ -189,14 +284,24 @@ pic_status_t make_tensor_map(Ctx *c) {
     if (!fn || q != cudaDriverEntryPointSuccess)
         return fail(c, PIC_ERR_CUDA, "cuTensorMapEncodeTiled not available");
     auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    cuuint64_t dims[3] = {(cuuint64_t)c->cfg.nx, (cuuint64_t)c->cfg.ny, 6};
-    cuuint64_t strides[2] = {(cuuint64_t)c->ld * c->rb, (cuuint64_t)c->plane * c->rb};
-    cuuint32_t box[3] = {(cuuint32_t)c->tg.WX, (cuuint32_t)c->tg.WY, 6};
-    cuuint32_t es[3] = {1, 1, 1};
     const CUtensorMapDataType dtype = c->rb == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-    CUresult r = enc(&c->tmapEB, dtype, 3, c->EB, dims, strides, box, es,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r;
+    if (c->dim == 3) {
+        // [6][nz][ny][ld] as a 4D tensor (x, y, z, component); box = the tile window
+        const cuuint64_t dims[4] = {(cuuint64_t)c->cfg.nx, (cuuint64_t)c->cfg.ny, (cuuint64_t)c->cfg.nz, 6};
+        const cuuint64_t strides[3] = {(cuuint64_t)c->ld * c->rb, (cuuint64_t)c->ld * c->cfg.ny * c->rb,
+                                       (cuuint64_t)c->plane * c->rb};
+        const cuuint32_t box[4] = {(cuuint32_t)c->tg3.FX, (cuuint32_t)c->tg3.WY, (cuuint32_t)c->tg3.WZ, 6};
+        r = enc(&c->tmapEB, dtype, 4, c->EB, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+        const cuuint64_t dims[3] = {(cuuint64_t)c->cfg.nx, (cuuint64_t)c->cfg.ny, 6};
+        const cuuint64_t strides[2] = {(cuuint64_t)c->ld * c->rb, (cuuint64_t)c->plane * c->rb};
+        const cuuint32_t box[3] = {(cuuint32_t)c->tg.WX, (cuuint32_t)c->tg.WY, 6};
+        r = enc(&c->tmapEB, dtype, 3, c->EB, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
     if (r != CUDA_SUCCESS) return fail(c, PIC_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
     return PIC_OK;
 }
@@ -222,6 +327,9 @@ pic_status_t sort_species(Ctx *c, int s, cudaStream_t st) {
     SortScratch w{c->cell_count, c->cell_off, c->tile_R, c->tile_count, c->tile_cursor, c->scratch_i32};
     CK(with_real(c, [&](auto z) {
         using T = decltype(z);
+        if (c->dim == 3)
+            return launch_tile_sort3<T>(dev_species3<T>(c, s, from), dev_species3<T>(c, s, to), c->tg3, w,
+                                        c->tile_start[s], c->n_dev + PIC_MAX_SPECIES, c->n_upper[s], st);
         return launch_tile_sort<T>(dev_species<T>(c, s, from), dev_species<T>(c, s, to), c->tg, w, c->tile_start[s],
                                    c->n_dev + PIC_MAX_SPECIES, c->n_upper[s], st);
     }));
@@ -253,8 +361,14 @@ extern "C" {
 pic_status_t pic_validate_config(const pic_config_t *cfg) {
     Ctx *c = nullptr;
     if (!cfg) return fail(c, PIC_ERR_ARG, "null config");
-    if (cfg->nx < 8 || cfg->ny < 4 || cfg->nx > 32767 || cfg->ny > 32767)
+    if (cfg->dim != 0 && cfg->dim != 2 && cfg->dim != 3) return fail(c, PIC_ERR_ARG, "dim must be 2 or 3 (0: 2)");
+    const bool d3 = cfg->dim == 3;
+    if (!d3 && (cfg->nx < 8 || cfg->ny < 4 || cfg->nx > 32767 || cfg->ny > 32767))
         return fail(c, PIC_ERR_ARG, "nx must be in [8, 32767] and ny in [4, 32767]");
+    if (d3 && (cfg->nx < 8 || cfg->ny < 4 || cfg->nz < 4 || cfg->nx > PIC3_MAX_NX || cfg->ny > PIC3_MAX_NY ||
+               cfg->nz > PIC3_MAX_NZ))
+        return fail(c, PIC_ERR_ARG, "3D3V needs 8 <= nx <= 2044, 4 <= ny <= 2044, 4 <= nz <= 1020");
+    if (d3 && !(cfg->dz_lambda > 0)) return fail(c, PIC_ERR_ARG, "dz_lambda must be > 0");
     if (!(cfg->dx_lambda > 0) || !(cfg->dy_lambda > 0)) return fail(c, PIC_ERR_ARG, "cell sizes must be > 0");
     if (!(cfg->cfl > 0 && cfg->cfl < 1)) return fail(c, PIC_ERR_ARG, "cfl must be in (0, 1)");
     if (cfg->bc_x != PIC_BC_OPEN && cfg->bc_x != PIC_BC_PERIODIC) return fail(c, PIC_ERR_ARG, "bad bc_x");
@@ -269,8 +383,11 @@ pic_status_t pic_validate_config(const pic_config_t *cfg) {
         if (sp.capacity < 0 || sp.capacity > 0x7FFFFFF0LL)
             return fail(c, PIC_ERR_ARG, "species capacity must be in [0, 2^31 - 16]");
     }
-    if ((cfg->tile_x != 0 || cfg->tile_y != 0) && !fused_tile_supported(cfg->tile_x, cfg->tile_y))
+    if (!d3 && (cfg->tile_x != 0 || cfg->tile_y != 0) && !fused_tile_supported(cfg->tile_x, cfg->tile_y))
         return fail(c, PIC_ERR_ARG, "tile must be one of 8x4, 16x8, 32x8, 32x16, 64x16 cells");
+    if (d3 && (cfg->tile_x != 0 || cfg->tile_y != 0 || cfg->tile_z != 0) &&
+        !fused3_tile_supported(cfg->tile_x, cfg->tile_y, cfg->tile_z))
+        return fail(c, PIC_ERR_ARG, "3D3V tile must be one of 8x8x4, 16x4x4, 8x4x4 cells");
     if (cfg->sort_every < 0) return fail(c, PIC_ERR_ARG, "sort_every must be >= 0");
     if (cfg->precision != 0 && cfg->precision != 32 && cfg->precision != 64)
         return fail(c, PIC_ERR_ARG, "precision must be 32 or 64 (0: 32)");
@@ -289,6 +406,7 @@ pic_status_t pic_create(const pic_config_t *cfg, void *stream, void **ctx_out) {
     if (c->cfg.sort_every == 0) c->cfg.sort_every = 32;
     if (c->cfg.precision == 0) c->cfg.precision = 32;
     c->rb = c->cfg.precision == 64 ? 8 : 4;
+    c->dim = c->cfg.dim == 3 ? 3 : 2;
     cudaStream_t st = S(stream);
     auto bail = [&](pic_status_t s) {
         g_create_error = c->last_error;
@@ -306,19 +424,25 @@ pic_status_t pic_create(const pic_config_t *cfg, void *stream, void **ctx_out) {
     CKC(cudaGetDevice(&c->device));
     c->dx = cfg->dx_lambda * kTwoPi;
     c->dy = cfg->dy_lambda * kTwoPi;
-    c->dt = cfg->cfl / std::sqrt(1.0 / (c->dx * c->dx) + 1.0 / (c->dy * c->dy));
+    c->dz = c->dim == 3 ? cfg->dz_lambda * kTwoPi : 0.0;
+    {
+        double s2 = 1.0 / (c->dx * c->dx) + 1.0 / (c->dy * c->dy);
+        if (c->dim == 3) s2 += 1.0 / (c->dz * c->dz);
+        c->dt = cfg->cfl / std::sqrt(s2);
+    }
     c->ld = round_up(cfg->nx, 32);
-    c->plane = (size_t)c->ld * cfg->ny;
+    c->bnd_n = (size_t)cfg->ny * (c->dim == 3 ? cfg->nz : 1);
+    c->plane = (size_t)c->ld * c->bnd_n;
     choose_tiles(c);
     const size_t rb = c->rb;
     CKC(cudaMalloc(&c->EB, 6 * c->plane * rb));
     CKC(cudaMalloc(&c->J, 3 * c->plane * rb));
-    CKC(cudaMalloc(&c->bnd, 2 * (size_t)cfg->ny * rb));
+    CKC(cudaMalloc(&c->bnd, 2 * c->bnd_n * rb));
     CKC(cudaMalloc(&c->rho, c->plane * rb));
     CKC(cudaMalloc(&c->rho_bg, c->plane * rb));
     CKC(cudaMemsetAsync(c->EB, 0, 6 * c->plane * rb, st));
     CKC(cudaMemsetAsync(c->J, 0, 3 * c->plane * rb, st));
-    CKC(cudaMemsetAsync(c->bnd, 0, 2 * (size_t)cfg->ny * rb, st));
+    CKC(cudaMemsetAsync(c->bnd, 0, 2 * c->bnd_n * rb, st));
     CKC(cudaMemsetAsync(c->rho_bg, 0, c->plane * rb, st));
     int64_t capmax = 0;
     for (int s = 0; s < cfg->nspecies; ++s) {
@@ -327,19 +451,20 @@ pic_status_t pic_create(const pic_config_t *cfg, void *stream, void **ctx_out) {
         for (int b = 0; b < 2; ++b) {
             CKC(cudaMalloc(&c->buf[s][b].cell, cap * sizeof(uint32_t) + 16));
             for (int k = 0; k < 9; ++k) CKC(cudaMalloc(&c->buf[s][b].f[k], cap * rb + 16));
+            if (c->dim == 3) CKC(cudaMalloc(&c->buf[s][b].oz, cap * rb + 16));
             CKC(cudaMalloc(&c->buf[s][b].id, cap * sizeof(int32_t) + 16));
         }
         CKC(cudaMalloc(&c->tile_start[s], (c->ntiles + 1) * sizeof(int32_t)));
         CKC(cudaMemsetAsync(c->tile_start[s], 0, (c->ntiles + 1) * sizeof(int32_t), st));
     }
     CKC(cudaMalloc(&c->tile_count, c->ntiles * sizeof(int32_t)));
-    CKC(cudaMalloc(&c->cell_count, (size_t)c->ntiles * c->tg.TX * c->tg.TY * sizeof(int32_t)));
-    CKC(cudaMalloc(&c->cell_off, (size_t)c->ntiles * c->tg.TX * c->tg.TY * sizeof(int32_t)));
+    CKC(cudaMalloc(&c->cell_count, (size_t)c->ntiles * tile_cells(c) * sizeof(int32_t)));
+    CKC(cudaMalloc(&c->cell_off, (size_t)c->ntiles * tile_cells(c) * sizeof(int32_t)));
     CKC(cudaMalloc(&c->tile_R, c->ntiles * sizeof(int32_t)));
     CKC(cudaMalloc(&c->tile_cursor, c->ntiles * sizeof(int32_t)));
     CKC(cudaMalloc(&c->n_dev, (PIC_MAX_SPECIES + 1) * sizeof(int32_t)));
     CKC(cudaMemsetAsync(c->n_dev, 0, (PIC_MAX_SPECIES + 1) * sizeof(int32_t), st));
-    CKC(cudaMalloc(&c->scratch_i32, 2 * (size_t)capmax * sizeof(int32_t) + 16));
+    CKC(cudaMalloc(&c->scratch_i32, 3 * (size_t)capmax * sizeof(int32_t) + 16));
     c->stage_elems = std::max((size_t)capmax, c->plane);
     CKC(cudaMalloc(&c->stage, c->stage_elems * sizeof(double) + 16));
     CKC(cudaMalloc(&c->err, sizeof(unsigned)));
@@ -353,8 +478,11 @@ pic_status_t pic_create(const pic_config_t *cfg, void *stream, void **ctx_out) {
     CKC(cudaMalloc(&c->diag_out, PIC_MAX_SPECIES * sizeof(pic_moments_dev)));
     CKC(cudaMemsetAsync(c->diag_out, 0, PIC_MAX_SPECIES * sizeof(pic_moments_dev), st));
     {
-        std::vector<double> prof(2 * (size_t)cfg->ny);
-        laser_profile(laser(c), cfg->ny, prof.data());
+        std::vector<double> prof(2 * c->bnd_n);
+        if (c->dim == 3)
+            laser_profile3(laser(c), cfg->ny, cfg->nz, c->dz, prof.data());
+        else
+            laser_profile(laser(c), cfg->ny, prof.data());
         CKC(cudaMalloc(&c->laser_prof, prof.size() * sizeof(double)));
         CKC(cudaMemcpyAsync(c->laser_prof, prof.data(), prof.size() * sizeof(double), cudaMemcpyHostToDevice, st));
         CKC(cudaStreamSynchronize(st));
@@ -379,6 +507,7 @@ void pic_destroy(void *ctx) {
         for (int b = 0; b < 2; ++b) {
             cudaFree(c->buf[s][b].cell);
             for (int k = 0; k < 9; ++k) cudaFree(c->buf[s][b].f[k]);
+            cudaFree(c->buf[s][b].oz);
             cudaFree(c->buf[s][b].id);
         }
         cudaFree(c->tile_start[s]);
@@ -403,12 +532,13 @@ void pic_destroy(void *ctx) {
     delete c;
 }
 
-pic_status_t pic_get_grid(void *ctx, double *dt, double *dx, double *dy) {
+pic_status_t pic_get_grid(void *ctx, double *dt, double *dx, double *dy, double *dz) {
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
     if (dt) *dt = c->dt;
     if (dx) *dx = c->dx;
     if (dy) *dy = c->dy;
+    if (dz) *dz = c->dz;
     return PIC_OK;
 }
 
@@ -419,8 +549,9 @@ pic_status_t pic_set_particles(void *ctx, int s, const pic_particles_t *p, void 
     if (p->n < 0) return fail(c, PIC_ERR_ARG, "negative particle count");
     if (p->n > c->cfg.sp[s].capacity) return fail(c, PIC_ERR_OVERFLOW, "more particles than capacity");
     const float *src[9] = {p->ox, p->oy, p->ux, p->uy, p->uz, p->sx, p->sy, p->sz, p->w};
+    const bool d3 = c->dim == 3;
     if (p->n > 0) {
-        if (!p->ix || !p->iy || !p->id) return fail(c, PIC_ERR_ARG, "null particle array");
+        if (!p->ix || !p->iy || !p->id || (d3 && (!p->iz || !p->oz))) return fail(c, PIC_ERR_ARG, "null particle array");
         for (int k = 0; k < 9; ++k)
             if (!src[k]) return fail(c, PIC_ERR_ARG, "null particle array");
     }
@@ -428,16 +559,20 @@ pic_status_t pic_set_particles(void *ctx, int s, const pic_particles_t *p, void 
     const size_t n = (size_t)p->n;
     const int b = c->cur[s];
     SpeciesBuf &B = c->buf[s][b];
-    int32_t *dix = c->scratch_i32, *diy = c->scratch_i32 + c->cfg.sp[s].capacity;
+    const size_t cap = (size_t)c->cfg.sp[s].capacity;
+    int32_t *dix = c->scratch_i32, *diy = c->scratch_i32 + cap, *diz = c->scratch_i32 + 2 * cap;
     if (n) {
         CK(cudaMemcpyAsync(dix, p->ix, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(diy, p->iy, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        for (int k = 0; k < 9; ++k) {
+        if (d3) CK(cudaMemcpyAsync(diz, p->iz, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        for (int k = 0; k < (d3 ? 10 : 9); ++k) {
+            const float *from = k < 9 ? src[k] : p->oz;
+            void *to = k < 9 ? B.f[k] : B.oz;
             if (c->rb == 4) {
-                CK(cudaMemcpyAsync(B.f[k], src[k], n * sizeof(float), cudaMemcpyHostToDevice, st));
+                CK(cudaMemcpyAsync(to, from, n * sizeof(float), cudaMemcpyHostToDevice, st));
             } else {  // FP64 instantiation: widen on the device
-                CK(cudaMemcpyAsync(c->stage, src[k], n * sizeof(float), cudaMemcpyHostToDevice, st));
-                CK(launch_convert<float, double>(static_cast<float *>(c->stage), static_cast<double *>(B.f[k]), n, st));
+                CK(cudaMemcpyAsync(c->stage, from, n * sizeof(float), cudaMemcpyHostToDevice, st));
+                CK(launch_convert<float, double>(static_cast<float *>(c->stage), static_cast<double *>(to), n, st));
                 c->launches += 1;
             }
         }
@@ -445,7 +580,10 @@ pic_status_t pic_set_particles(void *ctx, int s, const pic_particles_t *p, void 
     }
     const int xlo = c->cfg.bc_x == PIC_BC_OPEN ? 2 : 0;
     const int xhi = c->cfg.bc_x == PIC_BC_OPEN ? c->cfg.nx - 3 : c->cfg.nx - 1;
-    CK(launch_pack_cells(dix, diy, B.cell, (int)n, xlo, xhi, c->cfg.ny, c->err, st));
+    if (d3)
+        CK(launch_pack_cells3(dix, diy, diz, B.cell, (int)n, xlo, xhi, c->cfg.ny, c->cfg.nz, c->err, st));
+    else
+        CK(launch_pack_cells(dix, diy, B.cell, (int)n, xlo, xhi, c->cfg.ny, c->err, st));
     c->launches += n ? 1 : 0;
     const int32_t nn = (int32_t)n;
     CK(cudaMemcpyAsync(c->n_dev + s, &nn, sizeof(int32_t), cudaMemcpyHostToDevice, st));
@@ -491,24 +629,32 @@ static pic_status_t get_particles_t(Ctx *c, int s, PT *out, cudaStream_t st) {
     if ((int64_t)n > out->n) return fail(c, PIC_ERR_ARG, "output arrays too small");
     out->n = (int64_t)n;
     if (!n) return PIC_OK;
-    OutT *dst[9] = {out->ox, out->oy, out->ux, out->uy, out->uz, out->sx, out->sy, out->sz, out->w};
-    if (!out->ix || !out->iy || !out->id) return fail(c, PIC_ERR_ARG, "null output array");
+    const bool d3 = c->dim == 3;
+    OutT *dst[10] = {out->ox, out->oy, out->ux, out->uy, out->uz, out->sx, out->sy, out->sz, out->w, out->oz};
+    if (!out->ix || !out->iy || !out->id || (d3 && (!out->iz || !out->oz)))
+        return fail(c, PIC_ERR_ARG, "null output array");
     for (int k = 0; k < 9; ++k)
         if (!dst[k]) return fail(c, PIC_ERR_ARG, "null output array");
     const SpeciesBuf &B = c->buf[s][c->cur[s]];
-    int32_t *dix = c->scratch_i32, *diy = c->scratch_i32 + c->cfg.sp[s].capacity;
-    CK(launch_unpack_cells(B.cell, dix, diy, (int)n, st));
+    const size_t cap = (size_t)c->cfg.sp[s].capacity;
+    int32_t *dix = c->scratch_i32, *diy = c->scratch_i32 + cap, *diz = c->scratch_i32 + 2 * cap;
+    if (d3)
+        CK(launch_unpack_cells3(B.cell, dix, diy, diz, (int)n, st));
+    else
+        CK(launch_unpack_cells(B.cell, dix, diy, (int)n, st));
     c->launches += 1;
     CK(cudaMemcpyAsync(out->ix, dix, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(out->iy, diy, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    for (int k = 0; k < 9; ++k) {
+    if (d3) CK(cudaMemcpyAsync(out->iz, diz, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    for (int k = 0; k < (d3 ? 10 : 9); ++k) {
+        const void *from = k < 9 ? B.f[k] : B.oz;
         if ((size_t)c->rb == sizeof(OutT)) {
-            CK(cudaMemcpyAsync(dst[k], B.f[k], n * sizeof(OutT), cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(dst[k], from, n * sizeof(OutT), cudaMemcpyDeviceToHost, st));
         } else {
             if (c->rb == 8)
-                CK(launch_convert<double, float>(static_cast<const double *>(B.f[k]), static_cast<float *>(c->stage), n, st));
+                CK(launch_convert<double, float>(static_cast<const double *>(from), static_cast<float *>(c->stage), n, st));
             else
-                CK(launch_convert<float, double>(static_cast<const float *>(B.f[k]), static_cast<double *>(c->stage), n, st));
+                CK(launch_convert<float, double>(static_cast<const float *>(from), static_cast<double *>(c->stage), n, st));
             c->launches += 1;
             CK(cudaMemcpyAsync(dst[k], c->stage, n * sizeof(OutT), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));  // stage is reused by the next array
@@ -571,7 +717,7 @@ static pic_status_t xfer_plane(Ctx *c, HostT *host, void *dev, size_t rows, size
 template <typename HostT, typename FT>
 static pic_status_t copy_fields(Ctx *c, FT *f, bool to_dev, cudaStream_t st) {
     HostT *host[9] = {f->ex, f->ey, f->ez, f->bx, f->by, f->bz, f->jx, f->jy, f->jz};
-    const size_t nx = c->cfg.nx, ny = c->cfg.ny;
+    const size_t nx = c->cfg.nx, ny = c->bnd_n;  // rows: ny (2D3V) or nz * ny (3D3V)
     for (int k = 0; k < 9; ++k) {
         if (!host[k]) continue;
         char *base = static_cast<char *>(k < 6 ? c->EB : c->J);
@@ -642,6 +788,7 @@ pic_status_t pic_gather_push_spin(void *ctx, void *stream) {
         if (c->cfg.sp[s].mobile) {
             CK(with_real(c, [&](auto z) {
                 using T = decltype(z);
+                if (c->dim == 3) return launch_push_split3<T>(step_params3<T>(c), s, c->n_upper[s], st);
                 return launch_push_split<T>(step_params<T>(c), s, c->n_upper[s], st);
             }));
             c->launches += 1;
@@ -659,6 +806,7 @@ pic_status_t pic_deposit(void *ctx, void *stream) {
         if (c->cfg.sp[s].mobile) {
             CK(with_real(c, [&](auto z) {
                 using T = decltype(z);
+                if (c->dim == 3) return launch_deposit_split3<T>(step_params3<T>(c), s, c->n_upper[s], st);
                 return launch_deposit_split<T>(step_params<T>(c), s, c->n_upper[s], st);
             }));
             c->launches += 1;
@@ -673,6 +821,9 @@ pic_status_t pic_field_update(void *ctx, void *stream) {
     if (c->pending_deposit) return fail(c, PIC_ERR_STATE, "a move is waiting for pic_deposit");
     CK(with_real(c, [&](auto z) {
         using T = decltype(z);
+        if (c->dim == 3)
+            return launch_field_update3<T>(mesh3<T>(c), static_cast<T *>(c->bnd), c->laser_prof, laser(c), c->dt,
+                                           c->dx, c->dy, c->dz, c->step, S(stream));
         return launch_field_update<T>(mesh<T>(c), static_cast<T *>(c->bnd), c->laser_prof, laser(c), c->dt, c->dx,
                                       c->dy, c->step, S(stream));
     }));
@@ -699,6 +850,11 @@ pic_status_t pic_push_deposit(void *ctx, void *stream) {
     }
     CK(with_real(c, [&](auto z) {
         using T = decltype(z);
+        if (c->dim == 3) {
+            StepParams3<T> P = step_params3<T>(c);
+            P.diag = D;
+            return launch_step_fused3<T>(P, c->tmapEB, S(stream));
+        }
         StepParams<T> P = step_params<T>(c);
         P.diag = D;
         return launch_step_fused<T>(P, c->tmapEB, S(stream));
@@ -828,8 +984,10 @@ pic_status_t pic_capture_background(void *ctx, void *stream) {
     CK(with_real(c, [&](auto z) {
         using T = decltype(z);
         for (int s = 0; s < c->cfg.nspecies; ++s) {
-            cudaError_t e = launch_rho<T>(dev_species<T>(c, s, c->cur[s]), c->n_upper[s], mesh<T>(c),
-                                          static_cast<T *>(c->rho), st);
+            cudaError_t e = c->dim == 3 ? launch_rho3<T>(dev_species3<T>(c, s, c->cur[s]), c->n_upper[s], mesh3<T>(c),
+                                                          static_cast<T *>(c->rho), st)
+                                        : launch_rho<T>(dev_species<T>(c, s, c->cur[s]), c->n_upper[s], mesh<T>(c),
+                                                        static_cast<T *>(c->rho), st);
             if (e != cudaSuccess) return e;
         }
         return launch_negate_copy<T>(static_cast<const T *>(c->rho), static_cast<T *>(c->rho_bg), c->plane, st);
@@ -851,17 +1009,22 @@ pic_status_t pic_gauss_residual(void *ctx, double out[2], void *stream) {
     CK(with_real(c, [&](auto z) {
         using T = decltype(z);
         for (int s = 0; s < c->cfg.nspecies; ++s) {
-            cudaError_t e = launch_rho<T>(dev_species<T>(c, s, c->cur[s]), c->n_upper[s], mesh<T>(c),
-                                          static_cast<T *>(c->rho), st);
+            cudaError_t e = c->dim == 3 ? launch_rho3<T>(dev_species3<T>(c, s, c->cur[s]), c->n_upper[s], mesh3<T>(c),
+                                                          static_cast<T *>(c->rho), st)
+                                        : launch_rho<T>(dev_species<T>(c, s, c->cur[s]), c->n_upper[s], mesh<T>(c),
+                                                        static_cast<T *>(c->rho), st);
             if (e != cudaSuccess) return e;
         }
+        if (c->dim == 3)
+            return launch_gauss3<T>(mesh3<T>(c), static_cast<const T *>(c->rho), static_cast<const T *>(c->rho_bg),
+                                    c->dx, c->dy, c->dz, i0, i1, c->partials, c->result, st);
         return launch_gauss<T>(mesh<T>(c), static_cast<const T *>(c->rho), static_cast<const T *>(c->rho_bg),
                                c->dx, c->dy, i0, i1, c->partials, c->result, st);
     }));
     double r[2];
     CK(cudaMemcpyAsync(r, c->result, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    const double cnt = (double)(i1 - i0 + 1) * c->cfg.ny;
+    const double cnt = (double)(i1 - i0 + 1) * c->bnd_n;
     out[0] = r[0];
     out[1] = std::sqrt(r[1] / cnt);
     return PIC_OK;

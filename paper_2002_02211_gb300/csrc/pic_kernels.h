@@ -6,6 +6,7 @@
 #include <string>
 
 #include "pic_device.cuh"
+#include "pic_device3.cuh"
 
 // device-side copy of pic_moments_t (same layout: seven doubles)
 struct pic_moments_dev {
@@ -32,6 +33,20 @@ template <typename R>
 cudaError_t launch_field_update(const MeshParams<R> &m, R *bnd, const double *prof, const LaserParams &L,
                                 double dt, double dx, double dy, long long step, cudaStream_t st);
 void laser_profile(const LaserParams &L, int ny, double *host);
+void laser_time_factors(const LaserParams &L, double t, double *fz, double *fy);
+
+// k_particles3.cu, k_fields3.cu (3D3V)
+bool fused3_tile_supported(int tx, int ty, int tz);
+template <typename R>
+cudaError_t launch_step_fused3(const StepParams3<R> &P, const CUtensorMap &tmapEB, cudaStream_t st);
+template <typename R>
+cudaError_t launch_push_split3(const StepParams3<R> &P, int s, int n_upper, cudaStream_t st);
+template <typename R>
+cudaError_t launch_deposit_split3(const StepParams3<R> &P, int s, int n_upper, cudaStream_t st);
+template <typename R>
+cudaError_t launch_field_update3(const MeshParams3<R> &m, R *bnd, const double *prof, const LaserParams &L,
+                                 double dt, double dx, double dy, double dz, long long step, cudaStream_t st);
+void laser_profile3(const LaserParams &L, int ny, int nz, double dz, double *host);
 
 // k_sort.cu
 struct SortScratch {
@@ -48,6 +63,14 @@ template <typename R>
 cudaError_t launch_tile_sort(const DevSpecies<R> &src, const DevSpecies<R> &dst, const TileGeom &t,
                              const SortScratch &w, int32_t *tile_start, int32_t *n_tmp, int n_upper,
                              cudaStream_t st);
+cudaError_t launch_pack_cells3(const int32_t *ix, const int32_t *iy, const int32_t *iz, uint32_t *cell, int n,
+                               int xlo, int xhi, int ny, int nz, unsigned *err, cudaStream_t st);
+cudaError_t launch_unpack_cells3(const uint32_t *cell, int32_t *ix, int32_t *iy, int32_t *iz, int n,
+                                 cudaStream_t st);
+template <typename R>
+cudaError_t launch_tile_sort3(const DevSpecies3<R> &src, const DevSpecies3<R> &dst, const TileGeom3 &t,
+                              const SortScratch &w, int32_t *tile_start, int32_t *n_tmp, int n_upper,
+                              cudaStream_t st);
 template <typename A, typename B>
 cudaError_t launch_convert(const A *src, B *dst, size_t n, cudaStream_t st);
 
@@ -66,6 +89,11 @@ cudaError_t launch_negate_copy(const R *src, R *dst, size_t n, cudaStream_t st);
 template <typename R>
 cudaError_t launch_histogram(const DevSpecies<R> &S, R m_mev, R emin, R emax, int nbins, int log_bins,
                              double *out, cudaStream_t st);
+template <typename R>
+cudaError_t launch_rho3(const DevSpecies3<R> &S, int n_upper, const MeshParams3<R> &m, R *rho, cudaStream_t st);
+template <typename R>
+cudaError_t launch_gauss3(const MeshParams3<R> &m, const R *rho, const R *rho_bg, double dx, double dy, double dz,
+                          int i0, int i1, double *partials, double *result, cudaStream_t st);
 cudaError_t launch_diag_final(const double *rows, int nrows, int nsp, double *shift, pic_moments_dev *out,
                               double *tot, cudaStream_t st);
 

@@ -7,7 +7,7 @@ import paper_2002_02211_gb300 as pic
 import workloads as W
 
 
-def make_pair(wl, fields=None, step=0, capacity_factor=1.0, sort_every=0, tile=(0, 0), parts=None,
+def make_pair(wl, fields=None, step=0, capacity_factor=1.0, sort_every=0, tile=None, parts=None,
               precision=32):
     parts = W.generate_particles(wl) if parts is None else parts
     cfg = pic.config_from_workload(wl, capacity_factor=capacity_factor, sort_every=sort_every, tile=tile,
@@ -27,13 +27,14 @@ def make_pair(wl, fields=None, step=0, capacity_factor=1.0, sort_every=0, tile=(
 def gpu_by_id(sim, s, n_total, f64=False):
     """GPU particles of species s reordered by id; removed ones flagged."""
     g = sim.get_particles_f64(s) if f64 else sim.get_particles(s)
-    out = {k: np.full(n_total, np.nan) for k in ("x", "y", "ux", "uy", "uz", "sx", "sy", "sz")}
+    pos = ("x", "y", "z") if "iz" in g else ("x", "y")
+    out = {k: np.full(n_total, np.nan) for k in pos + ("ux", "uy", "uz", "sx", "sy", "sz")}
     alive = np.zeros(n_total, bool)
     ids = g["id"]
     live = g["ix"] >= 0
     assert len(np.unique(ids)) == len(ids), "duplicate particle ids"
-    out["x"][ids[live]] = g["ix"][live] + g["ox"][live].astype(np.float64)
-    out["y"][ids[live]] = g["iy"][live] + g["oy"][live].astype(np.float64)
+    for a in pos:
+        out[a][ids[live]] = g["i" + a][live] + g["o" + a][live].astype(np.float64)
     for k in ("ux", "uy", "uz", "sx", "sy", "sz"):
         out[k][ids[live]] = g[k][live]
     alive[ids[live]] = True
@@ -58,9 +59,11 @@ def compare_particles(sim, orc, s, u_tol=1e-5, s_tol=1e-5, x_tol=1e-5, u_floor=1
     du = np.sqrt(sum((g[k][m] - p[k][m]) ** 2 for k in ("ux", "uy", "uz")))
     un = np.maximum(np.sqrt(sum(p[k][m] ** 2 for k in ("ux", "uy", "uz"))), u_floor)
     ds = np.sqrt(sum((g[k][m] - p[k][m]) ** 2 for k in ("sx", "sy", "sz")))
-    dx = np.abs(periodic_diff(g["x"][m], p["x"][m], orc.wl.nx))
-    dy = np.abs(periodic_diff(g["y"][m], p["y"][m], orc.wl.ny))
-    err = dict(u=float((du / un).max()), s=float(ds.max()), x=float(max(dx.max(), dy.max())))
+    dpos = [np.abs(periodic_diff(g["x"][m], p["x"][m], orc.wl.nx)).max(),
+            np.abs(periodic_diff(g["y"][m], p["y"][m], orc.wl.ny)).max()]
+    if "z" in p:
+        dpos.append(np.abs(periodic_diff(g["z"][m], p["z"][m], orc.wl.nz)).max())
+    err = dict(u=float((du / un).max()), s=float(ds.max()), x=float(max(dpos)))
     assert err["u"] <= u_tol, err
     assert err["s"] <= s_tol, err
     assert err["x"] <= x_tol, err
