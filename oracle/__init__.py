@@ -318,11 +318,61 @@ class OracleSim:
         lib().or_laser(C.byref(self.grid), t, y, comp, C.byref(v))
         return v.value
 
+    # moving window -----------------------------------------------------------
+    POS = ("x", "y")
+
+    def shift_window(self, ncells, inject=None):
+        """Co-moving window (Sec. 2: the simulation box follows the laser): the
+        box moves ncells cells in +x between two steps.  In box coordinates
+        every mesh array and the neutralizing background slide ncells columns
+        toward x_min (columns that leave are dropped, the uncovered columns at
+        x_max start at zero), the left boundary values By(-1/2), Bz(-1/2) are
+        those of the column now at x = -1/2, particles move by -ncells cells
+        and the ones whose cell falls below the plasma region (x < 2) are
+        removed.  ``inject`` (one dict per species, workloads layout) is the
+        plasma of the uncovered columns; with a neutralizing background its
+        immobile ions (minus its charge density) join the background."""
+        n = int(ncells)
+        assert 1 <= n <= self.wl.nx - 8 and self.wl.bc_x == "open"
+        self.f["byL"][...] = self.f["by"][..., n - 1]
+        self.f["bzL"][...] = self.f["bz"][..., n - 1]
+        for k in self.FIELD_KEYS:
+            a = self.f[k]
+            a[..., :-n] = a[..., n:].copy()
+            a[..., -n:] = 0.0
+        self.rho_bg[..., :-n] = self.rho_bg[..., n:].copy()
+        self.rho_bg[..., -n:] = 0.0
+        for d in self.p:
+            d["x"] -= n
+            d["alive"][d["x"] < 2.0] = 0
+        if inject is not None:
+            new = [self._particles_from(d) for d in inject]
+            if self.wl.neutralizing_background:
+                keep = self.p
+                self.p = new
+                self.rho_bg -= self.rho()
+                self.p = keep
+            for s, d in enumerate(new):
+                for k in d:
+                    self.p[s][k] = np.concatenate([self.p[s][k], d[k]])
+
+    def _particles_from(self, d):
+        out = dict(ux=d["ux"].astype(np.float64), uy=d["uy"].astype(np.float64),
+                   uz=d["uz"].astype(np.float64), sx=d["sx"].astype(np.float64),
+                   sy=d["sy"].astype(np.float64), sz=d["sz"].astype(np.float64),
+                   w=d["w"].astype(np.float64), alive=np.ones(len(d["ix"]), np.int32),
+                   id=d["id"].copy())
+        for a in self.POS:
+            out[a] = d["i" + a].astype(np.float64) + d["o" + a].astype(np.float64)
+        return out
+
 
 class OracleSim3(OracleSim):
     """OracleSim of a 3D3V workload: mesh arrays [nz][ny][nx], left boundary
     arrays [nz][ny], particle positions x = ix + ox, y = iy + oy, z = iz + oz.
     ``OracleSim(wl, ...)`` returns one of these when ``wl.dim == 3``."""
+
+    POS = ("x", "y", "z")
 
     def __init__(self, wl, particles, fields=None, step=0):
         self.wl = wl

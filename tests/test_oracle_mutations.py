@@ -120,3 +120,50 @@ def test_pins_catch_planted_mistake(src_name, pins, name, old, new):
                             os.path.join(ROOT, "tests", pins)],
                            cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
         assert r.returncode != 0, f"pins did not catch: {name}\n{r.stdout[-2000:]}"
+
+
+# planted mistakes in the oracle's Python layer (the co-moving window), caught
+# by test_oracle_window_pins.py
+MUTATIONS_PY = [
+    ("window shifts fields the wrong way", "a[..., :-n] = a[..., n:].copy()", "a[..., n:] = a[..., :-n].copy()"),
+    ("window moves particles forward", 'd["x"] -= n', 'd["x"] += n'),
+    ("window removal threshold", 'd["alive"][d["x"] < 2.0] = 0', 'd["alive"][d["x"] < 1.0] = 0'),
+    ("window background not shifted", "self.rho_bg[..., :-n] = self.rho_bg[..., n:].copy()", "pass"),
+    ("window injects no ions", "self.rho_bg -= self.rho()", "pass"),
+    ("window keeps the old columns", "a[..., -n:] = 0.0", "pass"),
+]
+
+
+def _run_window_pins(old=None, new=None):
+    """Run the window pins against a copy of the oracle package (sources
+    included), optionally with one planted mistake; returns the pytest run."""
+    with tempfile.TemporaryDirectory() as td:
+        pkg = os.path.join(td, "oracle")
+        os.makedirs(pkg)
+        for f in ("pic_oracle.c", "pic_oracle3.c", "pic_oracle.h"):
+            with open(os.path.join(ROOT, "oracle", f)) as src, open(os.path.join(pkg, f), "w") as dst:
+                dst.write(src.read())
+        text = open(os.path.join(ROOT, "oracle", "__init__.py")).read()
+        if old is not None:
+            assert text.count(old) >= 1, f"mutation anchor not found: {old}"
+            text = text.replace(old, new, 1)
+        with open(os.path.join(pkg, "__init__.py"), "w") as fh:
+            fh.write(text)
+        env = dict(os.environ, PYTHONPATH=td + os.pathsep + ROOT)
+        env.pop("PIC_ORACLE_LIB", None)
+        return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                               os.path.join(ROOT, "tests", "test_oracle_window_pins.py")],
+                              cwd=td, env=env, capture_output=True, text=True, timeout=600)
+
+
+def test_window_pins_pass_on_an_unmodified_copy():
+    r = _run_window_pins()
+    assert r.returncode == 0, r.stdout[-2000:]
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS_PY, ids=[m[0] for m in MUTATIONS_PY])
+def test_window_pins_catch_planted_mistake(name, old, new):
+    r = _run_window_pins(old, new)
+    # caught = a pin failed (not an error while collecting or building)
+    assert r.returncode == 1 and "failed" in r.stdout.splitlines()[-1], \
+        f"pins did not catch: {name}\n{r.stdout[-2000:]}"

@@ -27,7 +27,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 __all__ = ["Species", "Workload", "CONFIG1", "CONFIG2", "CONFIG3", "generate_particles",
-           "random_fields", "small_case", "small_case3", "scaled"]
+           "injection_particles", "random_fields", "small_case", "small_case3", "scaled"]
 
 
 @dataclass(frozen=True)
@@ -185,6 +185,21 @@ def generate_particles(wl: Workload, seed: int | None = None):
             w=np.full(n, np.float32(sp.n0 / sp.ppc), np.float32),
             id=np.arange(n, dtype=np.int32), **extra))
     return out
+
+
+def injection_particles(wl: Workload, ncells: int, seed: int, id_base: int = 0):
+    """Plasma for the ncells columns that a moving-window shift by ncells
+    uncovers at the right end: cells [nx-2-ncells, nx-2) along x (the last two
+    columns stay vacuum), drawn with the workload's recipe (uniform in the cell,
+    Gaussian thermal momenta, the species' spin and weight).  Ids start at
+    id_base.  One dict per species, as generate_particles returns."""
+    sub = dataclasses.replace(wl, nx=ncells, bc_x="periodic")
+    parts = generate_particles(sub, seed=seed)
+    x0 = wl.nx - 2 - ncells
+    for d in parts:
+        d["ix"] = (d["ix"] + x0).astype(np.int32)
+        d["id"] = (d["id"] + id_base).astype(np.int32)
+    return parts
 
 
 def random_fields(wl: Workload, seed: int, e_amp: float = 0.5, b_amp: float = 0.5):
