@@ -267,6 +267,25 @@ pic_status_t pic_capture_background(void *ctx, void *stream);
  * out[1] = sqrt(sum r^2 / count), FP64.  Synchronous. */
 pic_status_t pic_gauss_residual(void *ctx, double out[2], void *stream);
 
+/* Co-moving window (Sec. 2: the box follows the laser through the plasma):
+ * moves the box ncells cells along +x between two steps.  In box coordinates
+ * every mesh array slides ncells columns toward x = 0 (the columns that leave
+ * are dropped; the uncovered ones at x_max start at zero), the left boundary
+ * values By(-1/2), Bz(-1/2) become those of the old column ncells - 1, every
+ * particle moves by -ncells cells and those whose cell falls below x = 2 are
+ * removed.  inject is NULL or an array of nspecies host particle sets (same
+ * layout as pic_set_particles) holding the plasma of the uncovered columns,
+ * normally cells [nx - 2 - ncells, nx - 2) in the moved box; they are appended
+ * (PIC_ERR_OVERFLOW if a species' capacity would be exceeded, nothing changed
+ * then) and, after pic_capture_background, their immobile ions join the
+ * background.  Every species is then sorted.  Needs PIC_BC_OPEN and
+ * 1 <= ncells <= nx - 8; the laser source keeps its time profile at the new
+ * x = 0.  Synchronous.  The step index is unchanged. */
+pic_status_t pic_shift_window(void *ctx, int ncells, const pic_particles_t *inject, void *stream);
+
+/* Cells the window has moved since pic_create. */
+pic_status_t pic_get_window(void *ctx, int64_t *offset_cells);
+
 /* Waits for the stream and reports device-side error flags. */
 pic_status_t pic_sync(void *ctx, void *stream);
 

@@ -114,6 +114,8 @@ _SIGS = {
                              C.POINTER(C.c_double), C.c_void_p],
     "pic_gauss_residual": [C.c_void_p, C.POINTER(C.c_double), C.c_void_p],
     "pic_sync": [C.c_void_p, C.c_void_p],
+    "pic_shift_window": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
+    "pic_get_window": [C.c_void_p, C.POINTER(C.c_int64)],
     "pic_set_diagnostics": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
     "pic_get_diagnostics": [C.c_void_p, C.c_void_p, C.POINTER(C.c_int64), C.c_void_p],
     "pic_moments_noalloc": [C.c_int64] + [C.c_void_p] * 8 + [C.c_double, C.c_double, C.c_double,
@@ -396,3 +398,23 @@ class Simulation:
 
     def sync(self):
         self._c(load().pic_sync(self.h, self._s))
+
+    def shift_window(self, ncells, inject=None):
+        """pic_shift_window: inject is None or one particle dict per species."""
+        if inject is None:
+            self._c(load().pic_shift_window(self.h, int(ncells), None, self._s))
+            return
+        keep = []
+        arr = (pic_particles_t * self.nspecies)()
+        for s, d in enumerate(inject):
+            a = {k: np.ascontiguousarray(d[k], dtype=np.int32 if k in _INT_KEYS else np.float32)
+                 for k in self._pkeys}
+            keep.append(a)
+            arr[s] = pic_particles_t(n=len(a["ix"]), **{k: _ptr(v, _I32P if v.dtype == np.int32 else _F32P)
+                                                         for k, v in a.items()})
+        self._c(load().pic_shift_window(self.h, int(ncells), arr, self._s))
+
+    def window(self):
+        v = C.c_int64()
+        self._c(load().pic_get_window(self.h, C.byref(v)))
+        return v.value

@@ -254,6 +254,12 @@ __global__ void __launch_bounds__(RT) k_gauss3(const MeshParams3<R> m, const R *
 }
 
 template <typename R>
+__global__ void k_subtract(R *dst, const R *src, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] -= src[i];
+}
+
+template <typename R>
 __global__ void k_negate(const R *src, R *dst, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         dst[i] = -src[i];
@@ -393,6 +399,12 @@ cudaError_t launch_gauss3(const MeshParams3<R> &m, const R *rho, const R *rho_bg
 }
 
 template <typename R>
+cudaError_t launch_subtract(R *dst, const R *src, size_t n, cudaStream_t st) {
+    k_subtract<R><<<152 * 4, 256, 0, st>>>(dst, src, n);
+    return cudaGetLastError();
+}
+
+template <typename R>
 cudaError_t launch_negate_copy(const R *src, R *dst, size_t n, cudaStream_t st) {
     k_negate<R><<<152 * 4, 256, 0, st>>>(src, dst, n);
     return cudaGetLastError();
@@ -404,6 +416,7 @@ cudaError_t launch_negate_copy(const R *src, R *dst, size_t n, cudaStream_t st) 
     template cudaError_t launch_gauss<R>(const MeshParams<R> &, const R *, const R *, double, double, int, int,  \
                                          double *, double *, cudaStream_t);                                 \
     template cudaError_t launch_negate_copy<R>(const R *, R *, size_t, cudaStream_t);                    \
+    template cudaError_t launch_subtract<R>(R *, const R *, size_t, cudaStream_t);                       \
     template cudaError_t launch_rho3<R>(const DevSpecies3<R> &, int, const MeshParams3<R> &, R *, cudaStream_t); \
     template cudaError_t launch_gauss3<R>(const MeshParams3<R> &, const R *, const R *, double, double, double, \
                                           int, int, double *, double *, cudaStream_t);

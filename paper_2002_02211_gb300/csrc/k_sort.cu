@@ -301,3 +301,77 @@ cudaError_t launch_convert(const A *src, B *dst, size_t n, cudaStream_t st) {
 }
 template cudaError_t launch_convert<float, double>(const float *, double *, size_t, cudaStream_t);
 template cudaError_t launch_convert<double, float>(const double *, float *, size_t, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// co-moving window: mesh rows and particle cells slide ncells toward x_min
+// ---------------------------------------------------------------------------
+namespace {
+
+// dst row r = src row r moved n columns toward x_min, zero in the uncovered
+// columns (rows of ld reals, nx of them used)
+template <typename R>
+__global__ void k_shift_rows(const R *src, R *dst, size_t rows, int nx, int ld, int n) {
+    const size_t total = rows * (size_t)ld;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(q % ld);
+        dst[q] = i + n < nx ? src[q + n] : R(0);
+    }
+}
+
+// left boundary values By(-1/2), Bz(-1/2) of the moved box: the old column n-1
+template <typename R>
+__global__ void k_ghost_from_column(const R *by, const R *bz, R *bnd, size_t rows, int ld, int n) {
+    for (size_t r = blockIdx.x * (size_t)blockDim.x + threadIdx.x; r < rows; r += (size_t)gridDim.x * blockDim.x) {
+        bnd[r] = by[r * ld + n - 1];
+        bnd[rows + r] = bz[r * ld + n - 1];
+    }
+}
+
+// particle cells move n cells toward x_min; cells below x = 2 are removed
+template <bool D3>
+__global__ void k_shift_cells(uint32_t *cell, const int32_t *n_src, int n) {
+    const int np = *n_src;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
+        const uint32_t c = cell[p];
+        if (c == PIC_DEAD) continue;
+        if (D3) {
+            int ix, iy, iz;
+            unpack_cell3(c, ix, iy, iz);
+            cell[p] = ix - n < 2 ? PIC_DEAD : pack_cell3(ix - n, iy, iz);
+        } else {
+            const int ix = (int)(c & 0xFFFFu) - n;
+            cell[p] = ix < 2 ? PIC_DEAD : ((c & 0xFFFF0000u) | (uint32_t)ix);
+        }
+    }
+}
+
+}  // namespace
+
+template <typename R>
+cudaError_t launch_shift_rows(const R *src, R *dst, size_t rows, int nx, int ld, int n, cudaStream_t st) {
+    k_shift_rows<R><<<152 * 8, 256, 0, st>>>(src, dst, rows, nx, ld, n);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_ghost_from_column(const R *by, const R *bz, R *bnd, size_t rows, int ld, int n, cudaStream_t st) {
+    k_ghost_from_column<R><<<(int)((rows + 255) / 256), 256, 0, st>>>(by, bz, bnd, rows, ld, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shift_cells(uint32_t *cell, const int32_t *n_src, int n_upper, int ncells, bool d3,
+                               cudaStream_t st) {
+    if (n_upper == 0) return cudaSuccess;
+    if (d3)
+        k_shift_cells<true><<<grid_for(n_upper), 256, 0, st>>>(cell, n_src, ncells);
+    else
+        k_shift_cells<false><<<grid_for(n_upper), 256, 0, st>>>(cell, n_src, ncells);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_shift_rows<float>(const float *, float *, size_t, int, int, int, cudaStream_t);
+template cudaError_t launch_shift_rows<double>(const double *, double *, size_t, int, int, int, cudaStream_t);
+template cudaError_t launch_ghost_from_column<float>(const float *, const float *, float *, size_t, int, int,
+                                                     cudaStream_t);
+template cudaError_t launch_ghost_from_column<double>(const double *, const double *, double *, size_t, int, int,
+                                                      cudaStream_t);

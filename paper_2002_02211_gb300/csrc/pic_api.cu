@@ -65,6 +65,8 @@ struct Ctx {
     CUtensorMap tmapEB;
     bool pending_deposit = false;
     long long step = 0;
+    long long window = 0;         // cells the co-moving window has moved
+    bool has_background = false;  // pic_capture_background was called
     int since_sort = 0;
     long long launches = 0;  // kernels launched by this context
     std::string last_error;
@@ -344,6 +346,60 @@ pic_status_t read_count(Ctx *c, int s, cudaStream_t st, int32_t *n) {
     return PIC_OK;
 }
 
+// Host particles p of species s into slots [base, base + p->n) of the current
+// buffer (widened on the device with precision 64), cells packed and range
+// checked; the slot count becomes base + p->n.  Synchronous.
+pic_status_t upload_particles(Ctx *c, int s, const pic_particles_t *p, int64_t base, cudaStream_t st) {
+    const float *src[9] = {p->ox, p->oy, p->ux, p->uy, p->uz, p->sx, p->sy, p->sz, p->w};
+    const bool d3 = c->dim == 3;
+    if (p->n > 0) {
+        if (!p->ix || !p->iy || !p->id || (d3 && (!p->iz || !p->oz))) return fail(c, PIC_ERR_ARG, "null particle array");
+        for (int k = 0; k < 9; ++k)
+            if (!src[k]) return fail(c, PIC_ERR_ARG, "null particle array");
+    }
+    const size_t n = (size_t)p->n;
+    SpeciesBuf &B = c->buf[s][c->cur[s]];
+    const size_t cap = (size_t)c->cfg.sp[s].capacity;
+    int32_t *dix = c->scratch_i32, *diy = c->scratch_i32 + cap, *diz = c->scratch_i32 + 2 * cap;
+    const size_t rb = c->rb;
+    if (n) {
+        CK(cudaMemcpyAsync(dix, p->ix, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(diy, p->iy, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        if (d3) CK(cudaMemcpyAsync(diz, p->iz, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        for (int k = 0; k < (d3 ? 10 : 9); ++k) {
+            const float *from = k < 9 ? src[k] : p->oz;
+            char *to = static_cast<char *>(k < 9 ? B.f[k] : B.oz) + base * rb;
+            if (rb == 4) {
+                CK(cudaMemcpyAsync(to, from, n * sizeof(float), cudaMemcpyHostToDevice, st));
+            } else {  // FP64 instantiation: widen on the device
+                CK(cudaMemcpyAsync(c->stage, from, n * sizeof(float), cudaMemcpyHostToDevice, st));
+                CK(launch_convert<float, double>(static_cast<float *>(c->stage), reinterpret_cast<double *>(to), n, st));
+                c->launches += 1;
+            }
+        }
+        CK(cudaMemcpyAsync(B.id + base, p->id, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    }
+    const int xlo = c->cfg.bc_x == PIC_BC_OPEN ? 2 : 0;
+    const int xhi = c->cfg.bc_x == PIC_BC_OPEN ? c->cfg.nx - 3 : c->cfg.nx - 1;
+    if (d3)
+        CK(launch_pack_cells3(dix, diy, diz, B.cell + base, (int)n, xlo, xhi, c->cfg.ny, c->cfg.nz, c->err, st));
+    else
+        CK(launch_pack_cells(dix, diy, B.cell + base, (int)n, xlo, xhi, c->cfg.ny, c->err, st));
+    c->launches += n ? 1 : 0;
+    const int32_t nn = (int32_t)(base + (int64_t)n);
+    CK(cudaMemcpyAsync(c->n_dev + s, &nn, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    c->n_upper[s] = (int)nn;
+    pic_status_t r = check_flags(c, st);
+    if (r != PIC_OK) {
+        const int32_t keep = (int32_t)base;
+        cudaMemcpyAsync(c->n_dev + s, &keep, sizeof(int32_t), cudaMemcpyHostToDevice, st);
+        cudaStreamSynchronize(st);
+        c->n_upper[s] = (int)base;
+        return r;
+    }
+    return PIC_OK;
+}
+
 pic_status_t alloc_old(Ctx *c, int s) {
     if (c->cell_old[s]) return PIC_OK;
     const size_t cap = (size_t)c->cfg.sp[s].capacity;
@@ -548,55 +604,10 @@ pic_status_t pic_set_particles(void *ctx, int s, const pic_particles_t *p, void 
     if (s < 0 || s >= c->cfg.nspecies || !p) return fail(c, PIC_ERR_ARG, "bad species or particles");
     if (p->n < 0) return fail(c, PIC_ERR_ARG, "negative particle count");
     if (p->n > c->cfg.sp[s].capacity) return fail(c, PIC_ERR_OVERFLOW, "more particles than capacity");
-    const float *src[9] = {p->ox, p->oy, p->ux, p->uy, p->uz, p->sx, p->sy, p->sz, p->w};
-    const bool d3 = c->dim == 3;
-    if (p->n > 0) {
-        if (!p->ix || !p->iy || !p->id || (d3 && (!p->iz || !p->oz))) return fail(c, PIC_ERR_ARG, "null particle array");
-        for (int k = 0; k < 9; ++k)
-            if (!src[k]) return fail(c, PIC_ERR_ARG, "null particle array");
-    }
     cudaStream_t st = S(stream);
-    const size_t n = (size_t)p->n;
-    const int b = c->cur[s];
-    SpeciesBuf &B = c->buf[s][b];
-    const size_t cap = (size_t)c->cfg.sp[s].capacity;
-    int32_t *dix = c->scratch_i32, *diy = c->scratch_i32 + cap, *diz = c->scratch_i32 + 2 * cap;
-    if (n) {
-        CK(cudaMemcpyAsync(dix, p->ix, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(diy, p->iy, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        if (d3) CK(cudaMemcpyAsync(diz, p->iz, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        for (int k = 0; k < (d3 ? 10 : 9); ++k) {
-            const float *from = k < 9 ? src[k] : p->oz;
-            void *to = k < 9 ? B.f[k] : B.oz;
-            if (c->rb == 4) {
-                CK(cudaMemcpyAsync(to, from, n * sizeof(float), cudaMemcpyHostToDevice, st));
-            } else {  // FP64 instantiation: widen on the device
-                CK(cudaMemcpyAsync(c->stage, from, n * sizeof(float), cudaMemcpyHostToDevice, st));
-                CK(launch_convert<float, double>(static_cast<float *>(c->stage), static_cast<double *>(to), n, st));
-                c->launches += 1;
-            }
-        }
-        CK(cudaMemcpyAsync(B.id, p->id, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    }
-    const int xlo = c->cfg.bc_x == PIC_BC_OPEN ? 2 : 0;
-    const int xhi = c->cfg.bc_x == PIC_BC_OPEN ? c->cfg.nx - 3 : c->cfg.nx - 1;
-    if (d3)
-        CK(launch_pack_cells3(dix, diy, diz, B.cell, (int)n, xlo, xhi, c->cfg.ny, c->cfg.nz, c->err, st));
-    else
-        CK(launch_pack_cells(dix, diy, B.cell, (int)n, xlo, xhi, c->cfg.ny, c->err, st));
-    c->launches += n ? 1 : 0;
-    const int32_t nn = (int32_t)n;
-    CK(cudaMemcpyAsync(c->n_dev + s, &nn, sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    c->n_upper[s] = (int)n;
+    pic_status_t r = upload_particles(c, s, p, 0, st);
+    if (r != PIC_OK) return r;
     c->pending_deposit = false;
-    pic_status_t r = check_flags(c, st);
-    if (r != PIC_OK) {
-        const int32_t zero = 0;
-        cudaMemcpyAsync(c->n_dev + s, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, st);
-        cudaStreamSynchronize(st);
-        c->n_upper[s] = 0;
-        return r;
-    }
     r = sort_species(c, s, st);
     if (r != PIC_OK) return r;
     c->since_sort = 0;
@@ -979,6 +990,7 @@ pic_status_t pic_energy_histogram(void *ctx, int s, double emin, double emax, in
 pic_status_t pic_capture_background(void *ctx, void *stream) {
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
+    c->has_background = true;
     cudaStream_t st = S(stream);
     CK(cudaMemsetAsync(c->rho, 0, c->plane * c->rb, st));
     CK(with_real(c, [&](auto z) {
@@ -1027,6 +1039,94 @@ pic_status_t pic_gauss_residual(void *ctx, double out[2], void *stream) {
     const double cnt = (double)(i1 - i0 + 1) * c->bnd_n;
     out[0] = r[0];
     out[1] = std::sqrt(r[1] / cnt);
+    return PIC_OK;
+}
+
+pic_status_t pic_shift_window(void *ctx, int ncells, const pic_particles_t *inject, void *stream) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
+    if (c->cfg.bc_x != PIC_BC_OPEN) return fail(c, PIC_ERR_ARG, "the moving window needs open x boundaries");
+    if (ncells < 1 || ncells > c->cfg.nx - 8) return fail(c, PIC_ERR_ARG, "ncells must be in [1, nx - 8]");
+    if (c->pending_deposit) return fail(c, PIC_ERR_STATE, "a move is waiting for pic_deposit");
+    cudaStream_t st = S(stream);
+    const size_t rows = c->bnd_n;  // mesh rows of one component
+    // inject counts fit?
+    int32_t cur[PIC_MAX_SPECIES] = {};
+    for (int s = 0; s < c->cfg.nspecies; ++s) {
+        pic_status_t r = read_count(c, s, st, &cur[s]);
+        if (r != PIC_OK) return r;
+        const int64_t m = inject ? inject[s].n : 0;
+        if (m < 0) return fail(c, PIC_ERR_ARG, "negative injection count");
+        if (cur[s] + m > c->cfg.sp[s].capacity) return fail(c, PIC_ERR_OVERFLOW, "injection exceeds the capacity");
+    }
+    CK(with_real(c, [&](auto z) -> cudaError_t {
+        using T = decltype(z);
+        T *EB = static_cast<T *>(c->EB), *J = static_cast<T *>(c->J);
+        cudaError_t e = launch_ghost_from_column<T>(EB + 4 * c->plane, EB + 5 * c->plane, static_cast<T *>(c->bnd),
+                                                    rows, c->ld, ncells, st);
+        if (e != cudaSuccess) return e;
+        T *planes[10];
+        for (int k = 0; k < 6; ++k) planes[k] = EB + k * c->plane;
+        for (int k = 0; k < 3; ++k) planes[6 + k] = J + k * c->plane;
+        planes[9] = static_cast<T *>(c->rho_bg);
+        T *tmp = static_cast<T *>(c->stage);  // at least plane reals
+        for (int k = 0; k < 10; ++k) {
+            e = cudaMemcpyAsync(tmp, planes[k], c->plane * sizeof(T), cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) return e;
+            e = launch_shift_rows<T>(tmp, planes[k], rows, c->cfg.nx, c->ld, ncells, st);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }));
+    c->launches += 11;
+    for (int s = 0; s < c->cfg.nspecies; ++s) {
+        CK(launch_shift_cells(c->buf[s][c->cur[s]].cell, c->n_dev + s, c->n_upper[s], ncells, c->dim == 3, st));
+        c->launches += 1;
+    }
+    for (int s = 0; s < c->cfg.nspecies; ++s) {
+        if (!inject || inject[s].n == 0) continue;
+        const int64_t base = cur[s];  // the slot count (removed particles stay until the sort)
+        pic_status_t r = upload_particles(c, s, &inject[s], base, st);
+        if (r != PIC_OK) return r;
+        if (c->has_background) {
+            // the injected plasma brings its immobile ions: rho_bg -= rho(injected)
+            const int32_t m = (int32_t)inject[s].n;
+            CK(cudaMemcpyAsync(c->n_dev + PIC_MAX_SPECIES, &m, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+            CK(cudaMemsetAsync(c->rho, 0, c->plane * c->rb, st));
+            CK(with_real(c, [&](auto z) -> cudaError_t {
+                using T = decltype(z);
+                cudaError_t e;
+                if (c->dim == 3) {
+                    DevSpecies3<T> v = dev_species3<T>(c, s, c->cur[s]);
+                    v.cell += base; v.ox += base; v.oy += base; v.oz += base; v.w += base;
+                    v.n = c->n_dev + PIC_MAX_SPECIES;
+                    e = launch_rho3<T>(v, m, mesh3<T>(c), static_cast<T *>(c->rho), st);
+                } else {
+                    DevSpecies<T> v = dev_species<T>(c, s, c->cur[s]);
+                    v.cell += base; v.ox += base; v.oy += base; v.w += base;
+                    v.n = c->n_dev + PIC_MAX_SPECIES;
+                    e = launch_rho<T>(v, m, mesh<T>(c), static_cast<T *>(c->rho), st);
+                }
+                if (e != cudaSuccess) return e;
+                return launch_subtract<T>(static_cast<T *>(c->rho_bg), static_cast<const T *>(c->rho), c->plane, st);
+            }));
+            c->launches += 2;
+            CK(cudaStreamSynchronize(st));  // the scratch count is reused by the sort
+        }
+    }
+    for (int s = 0; s < c->cfg.nspecies; ++s) {
+        pic_status_t r = sort_species(c, s, st);
+        if (r != PIC_OK) return r;
+    }
+    c->since_sort = 0;
+    c->window += ncells;
+    return check_flags(c, st);
+}
+
+pic_status_t pic_get_window(void *ctx, int64_t *offset) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c || !offset) return fail(c, PIC_ERR_ARG, "null argument");
+    *offset = c->window;
     return PIC_OK;
 }
 

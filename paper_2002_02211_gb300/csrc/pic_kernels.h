@@ -71,6 +71,12 @@ template <typename R>
 cudaError_t launch_tile_sort3(const DevSpecies3<R> &src, const DevSpecies3<R> &dst, const TileGeom3 &t,
                               const SortScratch &w, int32_t *tile_start, int32_t *n_tmp, int n_upper,
                               cudaStream_t st);
+template <typename R>
+cudaError_t launch_shift_rows(const R *src, R *dst, size_t rows, int nx, int ld, int n, cudaStream_t st);
+template <typename R>
+cudaError_t launch_ghost_from_column(const R *by, const R *bz, R *bnd, size_t rows, int ld, int n, cudaStream_t st);
+cudaError_t launch_shift_cells(uint32_t *cell, const int32_t *n_src, int n_upper, int ncells, bool d3,
+                               cudaStream_t st);
 template <typename A, typename B>
 cudaError_t launch_convert(const A *src, B *dst, size_t n, cudaStream_t st);
 
@@ -86,6 +92,8 @@ cudaError_t launch_gauss(const MeshParams<R> &m, const R *rho, const R *rho_bg, 
                          int i1, double *partials, double *result, cudaStream_t st);
 template <typename R>
 cudaError_t launch_negate_copy(const R *src, R *dst, size_t n, cudaStream_t st);
+template <typename R>
+cudaError_t launch_subtract(R *dst, const R *src, size_t n, cudaStream_t st);
 template <typename R>
 cudaError_t launch_histogram(const DevSpecies<R> &S, R m_mev, R emin, R emax, int nbins, int log_bins,
                              double *out, cudaStream_t st);
