@@ -325,6 +325,39 @@ pic_status_t pic_moments_noalloc(int64_t n, const uint32_t *cell, const float *u
 /* Reason for the last failure on this context (or of pic_create when ctx is NULL). */
 const char *pic_last_error(void *ctx);
 
+/* ---- batches of independent 2D3V runs --------------------------------------
+ * A parameter scan (density, a0, mesh size, particles per cell, run length)
+ * advanced together: each batch step is one launch of a persistent fused
+ * kernel that takes (run, tile) items of every active run from one queue, the
+ * batched Yee update over every (run, row), and a step-counter advance; the
+ * stretches between tile sorts are captured once as CUDA graphs and replayed.
+ * Runs share the tile shape and the sort cadence (taken from cfgs[0], or
+ * chosen by pic_batch_tune) and must be 2D3V in precision 32. */
+
+/* Creates nruns contexts (cfgs[r], as pic_create) and the batch around them;
+ * run r takes nsteps[r] batch steps, then stays idle.  Synchronous. */
+pic_status_t pic_batch_create(const pic_config_t *cfgs, int nruns, const int64_t *nsteps, void *stream,
+                              void **batch);
+/* Releases the batch and its runs' contexts.  NULL is accepted. */
+void pic_batch_destroy(void *batch);
+/* The context of run r (owned by the batch): load particles and fields, read
+ * results with the single-run calls (pic_set_particles, pic_polarization,
+ * pic_get_fields, ...).  Do not call pic_destroy on it. */
+pic_status_t pic_batch_run(void *batch, int r, void **ctx);
+/* Advances every run that has steps left by up to nsteps steps.  Synchronous
+ * at the end (checks every run's error flags). */
+pic_status_t pic_batch_step(void *batch, int64_t nsteps, void *stream);
+/* done[r] = batch steps run r has taken ([nruns]). */
+pic_status_t pic_batch_steps_done(void *batch, int64_t *done);
+/* Autotuner: for every candidate tile shape (tiles[2k], tiles[2k+1]) and sort
+ * cadence sorts[q] it re-tiles the runs, takes one sort cycle of steps and
+ * times probe_steps steps (the steps count toward the runs), then keeps the
+ * fastest pair: chosen = {tile_x, tile_y, sort_every}.  Synchronous. */
+pic_status_t pic_batch_tune(void *batch, int probe_steps, const int *tiles, int ntiles, const int *sorts,
+                            int nsorts, int *chosen, void *stream);
+/* One-line reason for the last failure of a batch call (NULL: of pic_batch_create). */
+const char *pic_batch_last_error(void *batch);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,7 +19,7 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["PicError", "pic_config_t", "pic_species_t", "config_from_workload", "Simulation",
+__all__ = ["PicError", "pic_config_t", "pic_species_t", "config_from_workload", "Simulation", "Batch",
            "load", "LIB_PATH"]
 
 LIB_PATH = _build.LIB
@@ -115,6 +115,11 @@ _SIGS = {
     "pic_gauss_residual": [C.c_void_p, C.POINTER(C.c_double), C.c_void_p],
     "pic_sync": [C.c_void_p, C.c_void_p],
     "pic_shift_window": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
+    "pic_batch_create": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)],
+    "pic_batch_run": [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)],
+    "pic_batch_step": [C.c_void_p, C.c_int64, C.c_void_p],
+    "pic_batch_steps_done": [C.c_void_p, C.c_void_p],
+    "pic_batch_tune": [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
     "pic_get_window": [C.c_void_p, C.POINTER(C.c_int64)],
     "pic_set_diagnostics": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
     "pic_get_diagnostics": [C.c_void_p, C.c_void_p, C.POINTER(C.c_int64), C.c_void_p],
@@ -140,6 +145,10 @@ def load(build: bool = True):
         L.pic_destroy.restype = None
         L.pic_last_error.argtypes = [C.c_void_p]
         L.pic_last_error.restype = C.c_char_p
+        L.pic_batch_destroy.argtypes = [C.c_void_p]
+        L.pic_batch_destroy.restype = None
+        L.pic_batch_last_error.argtypes = [C.c_void_p]
+        L.pic_batch_last_error.restype = C.c_char_p
         _lib = L
     return _lib
 
@@ -208,21 +217,28 @@ class Simulation:
 
     FIELD_KEYS = ("ex", "ey", "ez", "bx", "by", "bz", "jx", "jy", "jz")
 
-    def __init__(self, cfg: pic_config_t, stream=None):
+    def __init__(self, cfg: pic_config_t, stream=None, handle=None):
+        """A new context (pic_create), or with ``handle`` a view of a context
+        owned elsewhere (a batch run), which close() leaves alone."""
         L = load()
         self.cfg = cfg
         self.nx, self.ny = cfg.nx, cfg.ny
         self.dim = 3 if cfg.dim == 3 else 2
         self.nz = cfg.nz if self.dim == 3 else 1
         self.nspecies = cfg.nspecies
-        h = C.c_void_p()
-        _check(L.pic_create(C.byref(cfg), _stream(stream), C.byref(h)))
+        self.owner = handle is None
+        if handle is None:
+            h = C.c_void_p()
+            _check(L.pic_create(C.byref(cfg), _stream(stream), C.byref(h)))
+        else:
+            h = handle
         self.h = h
         self.stream = stream
 
     def close(self):
         if getattr(self, "h", None):
-            load().pic_destroy(self.h)
+            if self.owner:
+                load().pic_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -418,3 +434,68 @@ class Simulation:
         v = C.c_int64()
         self._c(load().pic_get_window(self.h, C.byref(v)))
         return v.value
+
+
+class Batch:
+    """A batch of independent 2D3V runs (pic_batch_*): one persistent fused
+    launch and one batched field update per step for every run, sort-free
+    stretches replayed as CUDA graphs."""
+
+    def __init__(self, cfgs, nsteps, stream=None):
+        L = load()
+        n = len(cfgs)
+        arr = (pic_config_t * n)(*cfgs)
+        steps = (C.c_int64 * n)(*[int(v) for v in nsteps])
+        h = C.c_void_p()
+        st = L.pic_batch_create(arr, n, steps, _stream(stream), C.byref(h))
+        if st != 0:
+            msg = L.pic_batch_last_error(None)
+            raise PicError(st, msg.decode() if msg else "")
+        self.h = h
+        self.n = n
+        self.cfgs = list(cfgs)
+        self.stream = stream
+
+    def _c(self, status):
+        if status != 0:
+            msg = load().pic_batch_last_error(self.h)
+            raise PicError(status, msg.decode() if msg else "")
+
+    def run(self, r):
+        """Simulation view of run r (owned by the batch)."""
+        h = C.c_void_p()
+        self._c(load().pic_batch_run(self.h, int(r), C.byref(h)))
+        return Simulation(self.cfgs[r], stream=self.stream, handle=h)
+
+    def step(self, nsteps):
+        self._c(load().pic_batch_step(self.h, int(nsteps), _stream(self.stream)))
+
+    def steps_done(self):
+        out = (C.c_int64 * self.n)()
+        self._c(load().pic_batch_steps_done(self.h, out))
+        return list(out)
+
+    def tune(self, probe_steps, tiles=((16, 8), (32, 8)), sorts=(16, 32, 64)):
+        t = (C.c_int * (2 * len(tiles)))(*[v for tt in tiles for v in tt])
+        q = (C.c_int * len(sorts))(*sorts)
+        out = (C.c_int * 3)()
+        self._c(load().pic_batch_tune(self.h, int(probe_steps), t, len(tiles), q, len(sorts), out,
+                                      _stream(self.stream)))
+        return tuple(out)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().pic_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

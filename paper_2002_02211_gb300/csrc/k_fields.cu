@@ -7,13 +7,10 @@
 
 namespace {
 
-// B <- B - h curl E.  Bx on every column; By, Bz on the columns whose x+1
-// neighbour exists (all of them when x is periodic).
+// B <- B - h curl E at (i, j).  Bx on every column; By, Bz on the columns
+// whose x+1 neighbour exists (all of them when x is periodic).
 template <typename R>
-__global__ void __launch_bounds__(256) k_b_half(const MeshParams<R> m, R hdx, R hdy) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y;
-    if (i >= m.nx) return;
+__device__ __forceinline__ void b_half_cell(const MeshParams<R> &m, int i, int j, R hdx, R hdy) {
     const int jp = j + 1 == m.ny ? 0 : j + 1;
     const size_t P = m.plane;
     R *EB = m.EB;
@@ -28,6 +25,12 @@ __global__ void __launch_bounds__(256) k_b_half(const MeshParams<R> m, R hdx, R 
     }
 }
 
+template <typename R>
+__global__ void __launch_bounds__(256) k_b_half(const MeshParams<R> m, R hdx, R hdy) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m.nx) b_half_cell(m, i, blockIdx.y, hdx, hdy);
+}
+
 // boundary B at t^{n+1/2}: the incoming characteristic is the laser at x_min
 // and zero at x_max, imposed on time-centred values with E^{n+1} from its own
 // update including the transverse term dBx = Bx(j+1/2) - Bx(j-1/2) (r = dt/dx,
@@ -37,13 +40,11 @@ __global__ void __launch_bounds__(256) k_b_half(const MeshParams<R> m, R hdx, R 
 //   By(nx-1/2) = (-2 Ez(nx-1) - (1-r) By(nx-3/2) + q dBx(nx-1)) / (1+r)
 //   Bz(nx-1/2) = (2 Ey(nx-1) - (1-r) Bz(nx-3/2)) / (1+r)
 template <typename R>
-__global__ void k_boundary(const MeshParams<R> m, R *bnd, const double *prof, double fz, double fy, double r,
-                           double q) {
+__device__ __forceinline__ void boundary_row(const MeshParams<R> &m, R *bnd, const double *prof, double fz,
+                                             double fy, double r, double q, int j) {
     // incident Ez (f) and Ey (g) at t^{n+1/2}: the time factor fz, fy (envelope x
     // carrier, one number per step) times the transverse profile prof[j] at y_j
     // and prof[ny + j] at y_{j+1/2}
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= m.ny) return;
     const size_t P = m.plane;
     R *EB = m.EB;
     const size_t c0 = (size_t)j * m.ld, cl = c0 + m.nx - 1;
@@ -59,12 +60,17 @@ __global__ void k_boundary(const MeshParams<R> m, R *bnd, const double *prof, do
     EB[5 * P + cl] = (R)((2.0 * EB[1 * P + cl] - mr * EB[5 * P + cl - 1]) * ir);
 }
 
-// E <- E + dt (curl B - J), then J <- 0
 template <typename R>
-__global__ void __launch_bounds__(256) k_e_full(const MeshParams<R> m, const R *bnd, R dt, R dtdx, R dtdy) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y;
-    if (i >= m.nx) return;
+__global__ void k_boundary(const MeshParams<R> m, R *bnd, const double *prof, double fz, double fy, double r,
+                           double q) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < m.ny) boundary_row(m, bnd, prof, fz, fy, r, q, j);
+}
+
+// E <- E + dt (curl B - J) at (i, j), then J <- 0
+template <typename R>
+__device__ __forceinline__ void e_full_cell(const MeshParams<R> &m, const R *bnd, R dt, R dtdx, R dtdy, int i,
+                                            int j) {
     const int jm = j == 0 ? m.ny - 1 : j - 1;
     const size_t P = m.plane;
     R *EB = m.EB;
@@ -90,7 +96,77 @@ __global__ void __launch_bounds__(256) k_e_full(const MeshParams<R> m, const R *
     J[2 * P + c] = R(0);
 }
 
+template <typename R>
+__global__ void __launch_bounds__(256) k_e_full(const MeshParams<R> m, const R *bnd, R dt, R dtdx, R dtdy) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m.nx) e_full_cell(m, bnd, dt, dtdx, dtdy, i, blockIdx.y);
+}
+
+// ---------------------------------------------------------------------------
+// batched field update: one block per (run, row) item, runs past their last
+// step skipped; the same cell updates as the single-run kernels, with the
+// per-step scalars taken from the run's mesh parameters and laser table
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(256) k_b_half_batch(const BatchField<R> *runs, const int2 *rows, int nrows,
+                                                      const long long *step, const long long *nsteps) {
+    for (int b = blockIdx.x; b < nrows; b += gridDim.x) {
+        const int2 rj = rows[b];
+        if (step[rj.x] >= nsteps[rj.x]) continue;
+        const MeshParams<R> &m = runs[rj.x].m;
+        const R hdx = R(0.5) * m.dt_dx, hdy = R(0.5) * m.dt_dy;
+        for (int i = threadIdx.x; i < m.nx; i += blockDim.x) b_half_cell(m, i, rj.y, hdx, hdy);
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_e_full_batch(const BatchField<R> *runs, const int2 *rows, int nrows,
+                                                      const long long *step, const long long *nsteps) {
+    for (int b = blockIdx.x; b < nrows; b += gridDim.x) {
+        const int2 rj = rows[b];
+        if (step[rj.x] >= nsteps[rj.x]) continue;
+        const BatchField<R> &F = runs[rj.x];
+        for (int i = threadIdx.x; i < F.m.nx; i += blockDim.x)
+            e_full_cell(F.m, F.bnd, F.m.dt, F.m.dt_dx, F.m.dt_dy, i, rj.y);
+    }
+}
+
+template <typename R>
+__global__ void k_boundary_batch(const BatchField<R> *runs, const int2 *rows, int nrows, const long long *step,
+                                 const long long *nsteps) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nrows; b += gridDim.x * blockDim.x) {
+        const int2 rj = rows[b];
+        const long long k = step[rj.x];
+        if (k >= nsteps[rj.x]) continue;
+        const BatchField<R> &F = runs[rj.x];
+        if (F.m.bc_x != 0) continue;
+        const double *lf = F.laser + 2 * (k - F.step0);
+        boundary_row(F.m, F.bnd, F.prof, lf[0], lf[1], F.r, F.q, rj.y);
+    }
+}
+
+// step counters of the active runs advance; the fused kernel's queue rewinds
+__global__ void k_batch_advance(long long *step, const long long *nsteps, int nruns, int *counter) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nruns; r += gridDim.x * blockDim.x)
+        if (step[r] < nsteps[r]) step[r] += 1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0;
+}
+
 }  // namespace
+
+template <typename R>
+cudaError_t launch_field_update_batch(const BatchField<R> *runs, const int2 *rows, int nrows, long long *step,
+                                      const long long *nsteps, int nruns, int *counter, cudaStream_t st) {
+    const int g = nrows < 152 * 16 ? nrows : 152 * 16;
+    k_b_half_batch<R><<<g, 256, 0, st>>>(runs, rows, nrows, step, nsteps);
+    k_boundary_batch<R><<<(nrows + 255) / 256, 256, 0, st>>>(runs, rows, nrows, step, nsteps);
+    k_e_full_batch<R><<<g, 256, 0, st>>>(runs, rows, nrows, step, nsteps);
+    k_b_half_batch<R><<<g, 256, 0, st>>>(runs, rows, nrows, step, nsteps);
+    k_batch_advance<<<(nruns + 255) / 256, 256, 0, st>>>(step, nsteps, nruns, counter);
+    return cudaGetLastError();
+}
+template cudaError_t launch_field_update_batch<float>(const BatchField<float> *, const int2 *, int, long long *,
+                                                      const long long *, int, int *, cudaStream_t);
 
 // laser time factors at t: the incident Ez (comp 1) and Ey (comp 0) on the
 // axis, i.e. without the transverse profile

@@ -80,29 +80,30 @@ __device__ __forceinline__ void flush_add<double>(double *dst, const double *src
     for (int k = 0; k < 4; ++k)
         if (src[k] != 0.0) atomicAdd(dst + k, src[k]);
 }
+// One tile of the fused step: the body of k_step_fused (one CTA per tile) and
+// of k_step_fused_batch (persistent CTAs taking tiles of many runs).  `bar`
+// is an initialised mbarrier whose current phase has parity `phase`; `ntiles`
+// is the run's tile count (the stride of the diagnostic rows).  Returns false
+// if the window wait gave up.
 template <int TX, int TY, typename R>
-__global__ void __launch_bounds__(kFusedThreads, sizeof(R) == 4 ? PIC_FUSED_MINB : 2)
-    k_step_fused(const StepParams<R> P, const __grid_constant__ CUtensorMap tmapEB) {
+__device__ __forceinline__ bool fused_tile(const StepParams<R> &P, const CUtensorMap *tmap, const int tile,
+                                           const int ntiles, uint64_t &bar, const unsigned phase,
+                                           unsigned char *dsm, double (*sdiag)[8]) {
     using TC = TileConst<TX, TY, R>;
     constexpr int WX = TC::WX, WY = TC::WY, WA = TC::WA;
-    extern __shared__ __align__(1024) unsigned char dsm[];
-    __shared__ __align__(8) uint64_t bar;
     R *sF = reinterpret_cast<R *>(dsm);
     R *sJ = sF + 6 * WA;
     R *ring = sJ + 3 * WA;                                             // [2][kRec][kFusedThreads]
     uint32_t *cring = reinterpret_cast<uint32_t *>(ring + 2 * kRec * kFusedThreads);  // [2][kFusedThreads]
     const MeshParams<R> &m = P.m;
 
-    const int tile = blockIdx.x;
     const int ty = tile / P.t.ntx, tx = tile - ty * P.t.ntx;
     const int wx0 = tx * TX - TC::HX, wy0 = ty * TY - TC::HY;
     const int tid = threadIdx.x;
 
     if (tid == 0) {
-        mbar_init(&bar, 1);
-        fence_mbar_init();
         mbar_expect_tx(&bar, (unsigned)(6 * WA * sizeof(R)));
-        tma_load_3d(sF, &tmapEB, &bar, wx0, wy0, 0);
+        tma_load_3d(sF, tmap, &bar, wx0, wy0, 0);
     }
 
     R *ring0 = ring + tid;
@@ -125,8 +126,7 @@ __global__ void __launch_bounds__(kFusedThreads, sizeof(R) == 4 ? PIC_FUSED_MINB
     };
 
     // Eq. (4) diagnostic sums of one species: float per thread (at most
-    // total/256 particles each), then double across the CTA
-    __shared__ double sdiag[kFusedThreads / 32][8];
+    // total/256 particles each), then double across the CTA (sdiag)
     const bool diag = P.diag.on != 0;
 
     // the first record of the first mobile species is requested before the
@@ -140,10 +140,10 @@ __global__ void __launch_bounds__(kFusedThreads, sizeof(R) == 4 ? PIC_FUSED_MINB
     }
     for (int i = tid; i < 3 * WA; i += kFusedThreads) sJ[i] = R(0);
     __syncthreads();
-    if (!mbar_wait_bounded(&bar, 0)) {
+    if (!mbar_wait_bounded(&bar, phase)) {
         if (tid == 0) atomicOr(P.err, PIC_EF_TIMEOUT);
         cp_async_wait0();
-        return;
+        return false;
     }
 
     const SmemMeshT<R, WX, WA> sm{sF, sJ};
@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(kFusedThreads, sizeof(R) == 4 ? PIC_FUSED_MINB
             if (tid < 7) {
                 double t = 0.0;
                 for (int w8 = 0; w8 < kFusedThreads / 32; ++w8) t += sdiag[w8][tid];
-                P.diag.rows[((size_t)sp * 8 + tid) * gridDim.x + blockIdx.x] = t;
+                P.diag.rows[((size_t)sp * 8 + tid) * ntiles + tile] = t;
             }
             __syncthreads();
         }
@@ -295,6 +295,57 @@ __global__ void __launch_bounds__(kFusedThreads, sizeof(R) == 4 ? PIC_FUSED_MINB
         const int gy = wy0 + y, gx = wx0 + 4 * xq;
         if (gy < 0 || gy >= m.ny || gx < 0 || gx >= m.ld) continue;
         flush_add<R>(&m.J[c * m.plane + (size_t)gy * m.ld + gx], &sJ[c * WA + y * WX + 4 * xq]);
+    }
+    return true;
+}
+
+template <int TX, int TY, typename R>
+__global__ void __launch_bounds__(kFusedThreads, sizeof(R) == 4 ? PIC_FUSED_MINB : 2)
+    k_step_fused(const __grid_constant__ StepParams<R> P, const __grid_constant__ CUtensorMap tmapEB) {
+    extern __shared__ __align__(1024) unsigned char dsm[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ double sdiag[kFusedThreads / 32][8];
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    // (fused_tile's barrier after clearing the current window orders the
+    // initialisation before every other thread's first wait)
+    fused_tile<TX, TY, R>(P, &tmapEB, blockIdx.x, gridDim.x, bar, 0u, dsm, sdiag);
+}
+
+// ---------------------------------------------------------------------------
+// Batched step: persistent CTAs (a few per SM) take (run, tile) work items
+// from a queue shared by all runs of a batch and run fused_tile on each, with
+// the run's parameters and tensor map read from global memory.  Items of runs
+// that have finished their steps are skipped.
+// ---------------------------------------------------------------------------
+template <int TX, int TY, typename R>
+__global__ void __launch_bounds__(kFusedThreads, sizeof(R) == 4 ? PIC_FUSED_MINB : 2)
+    k_step_fused_batch(const BatchFused<R> W) {
+    extern __shared__ __align__(1024) unsigned char dsm[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ double sdiag[kFusedThreads / 32][8];
+    __shared__ int s_item;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    unsigned phase = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(W.counter, 1);
+        __syncthreads();
+        const int w = s_item;
+        __syncthreads();
+        if (w >= W.nwork) break;
+        const int2 rt = W.work[w];
+        if (W.step[rt.x] >= W.nsteps[rt.x]) continue;
+        const CUtensorMap *tm = W.tmaps + rt.x;
+        if (threadIdx.x == 0) fence_tensormap_acquire(tm);
+        if (!fused_tile<TX, TY, R>(W.params[rt.x], tm, rt.y, W.params[rt.x].t.ntx * W.params[rt.x].t.nty, bar,
+                                   phase, dsm, sdiag))
+            break;
+        phase ^= 1u;
     }
 }
 
@@ -383,6 +434,51 @@ static cudaError_t launch_fused_t(const StepParams<R> &P, const CUtensorMap &tma
     k_step_fused<TX, TY, R><<<P.t.ntx * P.t.nty, kFusedThreads, smem, st>>>(P, tmapEB);
     return cudaGetLastError();
 }
+
+template <int TX, int TY, typename R>
+static cudaError_t launch_fused_batch_t(const BatchFused<R> &W, int ctas, cudaStream_t st) {
+    using TC = TileConst<TX, TY, R>;
+    constexpr size_t smem = TC::smem_bytes;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_step_fused_batch<TX, TY, R>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    k_step_fused_batch<TX, TY, R><<<ctas, kFusedThreads, smem, st>>>(W);
+    return cudaGetLastError();
+}
+
+template <int TX, int TY>
+static int batch_occupancy_t() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_fused_batch<TX, TY, float>, kFusedThreads,
+                                                      TileConst<TX, TY, float>::smem_bytes) != cudaSuccess)
+        return 1;
+    return n > 0 ? n : 1;
+}
+
+// resident CTAs per SM of the batched kernel for a tile shape
+int fused_batch_occupancy(int tx, int ty) {
+    if (tx == 8 && ty == 4) return batch_occupancy_t<8, 4>();
+    if (tx == 16 && ty == 8) return batch_occupancy_t<16, 8>();
+    if (tx == 32 && ty == 8) return batch_occupancy_t<32, 8>();
+    if (tx == 32 && ty == 16) return batch_occupancy_t<32, 16>();
+    if (tx == 64 && ty == 16) return batch_occupancy_t<64, 16>();
+    return 1;
+}
+
+template <typename R>
+cudaError_t launch_step_fused_batch(const BatchFused<R> &W, int tx, int ty, int ctas, cudaStream_t st) {
+    if (tx == 8 && ty == 4) return launch_fused_batch_t<8, 4, R>(W, ctas, st);
+    if (tx == 16 && ty == 8) return launch_fused_batch_t<16, 8, R>(W, ctas, st);
+    if (tx == 32 && ty == 8) return launch_fused_batch_t<32, 8, R>(W, ctas, st);
+    if (tx == 32 && ty == 16) return launch_fused_batch_t<32, 16, R>(W, ctas, st);
+    if (tx == 64 && ty == 16) return launch_fused_batch_t<64, 16, R>(W, ctas, st);
+    return cudaErrorInvalidValue;
+}
+template cudaError_t launch_step_fused_batch<float>(const BatchFused<float> &, int, int, int, cudaStream_t);
 
 bool fused_tile_supported(int tx, int ty) {
     return (tx == 8 && ty == 4) || (tx == 16 && ty == 8) || (tx == 32 && ty == 8) ||

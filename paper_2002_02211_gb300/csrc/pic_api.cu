@@ -400,6 +400,46 @@ pic_status_t upload_particles(Ctx *c, int s, const pic_particles_t *p, int64_t b
     return PIC_OK;
 }
 
+// new 2D3V tile shape: the tile-dependent arrays, the window tensor map, and
+// every species re-sorted into the new tiles
+pic_status_t retile(Ctx *c, int tx, int ty, cudaStream_t st) {
+    if (c->dim != 2 || !fused_tile_supported(tx, ty)) return fail(c, PIC_ERR_ARG, "unsupported tile shape");
+    CK(cudaStreamSynchronize(st));
+    for (int s = 0; s < PIC_MAX_SPECIES; ++s) {
+        cudaFree(c->tile_start[s]);
+        c->tile_start[s] = nullptr;
+    }
+    cudaFree(c->tile_count);
+    cudaFree(c->cell_count);
+    cudaFree(c->cell_off);
+    cudaFree(c->tile_R);
+    cudaFree(c->tile_cursor);
+    cudaFree(c->diag_rows);
+    c->cfg.tile_x = tx;
+    c->cfg.tile_y = ty;
+    choose_tiles(c);
+    for (int s = 0; s < c->cfg.nspecies; ++s) {
+        CK(cudaMalloc(&c->tile_start[s], (c->ntiles + 1) * sizeof(int32_t)));
+        CK(cudaMemsetAsync(c->tile_start[s], 0, (c->ntiles + 1) * sizeof(int32_t), st));
+    }
+    const size_t cells = (size_t)c->ntiles * tile_cells(c);
+    CK(cudaMalloc(&c->tile_count, c->ntiles * sizeof(int32_t)));
+    CK(cudaMalloc(&c->cell_count, cells * sizeof(int32_t)));
+    CK(cudaMalloc(&c->cell_off, cells * sizeof(int32_t)));
+    CK(cudaMalloc(&c->tile_R, c->ntiles * sizeof(int32_t)));
+    CK(cudaMalloc(&c->tile_cursor, c->ntiles * sizeof(int32_t)));
+    CK(cudaMalloc(&c->diag_rows, (size_t)c->ntiles * PIC_MAX_SPECIES * 8 * sizeof(double)));
+    pic_status_t r = make_tensor_map(c);
+    if (r != PIC_OK) return r;
+    for (int s = 0; s < c->cfg.nspecies; ++s) {
+        r = sort_species(c, s, st);
+        if (r != PIC_OK) return r;
+    }
+    c->since_sort = 0;
+    CK(cudaStreamSynchronize(st));
+    return PIC_OK;
+}
+
 pic_status_t alloc_old(Ctx *c, int s) {
     if (c->cell_old[s]) return PIC_OK;
     const size_t cap = (size_t)c->cfg.sp[s].capacity;
@@ -1146,6 +1186,402 @@ pic_status_t pic_launch_count(void *ctx, int64_t *count) {
 const char *pic_last_error(void *ctx) {
     Ctx *c = static_cast<Ctx *>(ctx);
     return c ? c->last_error.c_str() : g_create_error.c_str();
+}
+
+}  // extern "C"
+
+
+// ===========================================================================
+// Batches of independent 2D3V runs (parameter scans: density, a0, mesh size,
+// particles per cell, run length).  Each run keeps its own context (state,
+// buffers, tile arrays); a batch step is one launch of the persistent fused
+// kernel over the (run, tile) items of every active run, the batched field
+// update over every (run, row), and a step-counter advance.  Sort-free
+// stretches of steps are captured once in a CUDA graph (one per buffer
+// parity) and replayed; the tile sorts run per run between replays.
+// ===========================================================================
+namespace {
+
+struct Batch {
+    std::vector<Ctx *> runs;
+    std::vector<long long> todo;   // steps each run still has to take
+    std::vector<long long> done;   // steps taken in this batch
+    int tx = 16, ty = 8, sort_every = 32, since_sort = 0, parity = -1;
+    bool prepared = false;
+    StepParams<float> *params[2] = {};
+    CUtensorMap *tmaps = nullptr;
+    BatchField<float> *fields = nullptr;
+    double *laser = nullptr;
+    int2 *work = nullptr, *rows = nullptr;
+    int nwork = 0, nrows = 0, ctas = 0;
+    long long *step = nullptr, *nsteps = nullptr;
+    int *counter = nullptr;
+    std::vector<std::pair<int, cudaGraphExec_t>> graphs[2];  // (steps, graph) per parity
+    std::string last_error;
+};
+
+pic_status_t bfail(Batch *b, pic_status_t s, const std::string &msg) {
+    if (b) b->last_error = msg;
+    else g_create_error = msg;
+    return s;
+}
+
+#define BCK(...)                                                                                \
+    do {                                                                                        \
+        cudaError_t e_ = (__VA_ARGS__);                                                         \
+        if (e_ != cudaSuccess)                                                                  \
+            return bfail(b, PIC_ERR_CUDA, std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+void drop_graphs(Batch *b) {
+    for (auto &v : b->graphs)
+        for (auto &g : v) cudaGraphExecDestroy(g.second);
+    b->graphs[0].clear();
+    b->graphs[1].clear();
+}
+
+void free_tables(Batch *b) {
+    drop_graphs(b);
+    cudaFree(b->params[0]);
+    cudaFree(b->params[1]);
+    cudaFree(b->tmaps);
+    cudaFree(b->fields);
+    cudaFree(b->laser);
+    cudaFree(b->work);
+    cudaFree(b->rows);
+    cudaFree(b->step);
+    cudaFree(b->nsteps);
+    cudaFree(b->counter);
+    b->params[0] = b->params[1] = nullptr;
+    b->tmaps = nullptr;
+    b->fields = nullptr;
+    b->laser = nullptr;
+    b->work = b->rows = nullptr;
+    b->step = b->nsteps = nullptr;
+    b->counter = nullptr;
+    b->prepared = false;
+}
+
+// every species of every run in buffer `parity`
+pic_status_t align_parity(Batch *b, cudaStream_t st) {
+    if (b->parity < 0) b->parity = b->runs[0]->cur[0];
+    for (Ctx *c : b->runs)
+        for (int s = 0; s < c->cfg.nspecies; ++s)
+            if (c->cur[s] != b->parity) {
+                pic_status_t r = sort_species(c, s, st);
+                if (r != PIC_OK) return bfail(b, r, c->last_error);
+            }
+    return PIC_OK;
+}
+
+// device tables of the batch: per-run parameters for both parities, tensor
+// maps, field data with laser tables, work items (largest runs first), rows
+pic_status_t prepare(Batch *b, cudaStream_t st) {
+    free_tables(b);
+    const int n = (int)b->runs.size();
+    std::vector<StepParams<float>> P[2];
+    std::vector<CUtensorMap> tm(n);
+    std::vector<BatchField<float>> F(n);
+    std::vector<long long> step0(n), end(n);
+    std::vector<size_t> laser_off(n);
+    size_t laser_total = 0;
+    std::vector<long long> left(n);
+    for (int r = 0; r < n; ++r) {
+        left[r] = b->todo[r] - b->done[r];
+        laser_off[r] = laser_total;
+        laser_total += 2 * (size_t)std::max<long long>(left[r], 1);
+    }
+    std::vector<double> lt(laser_total, 0.0);
+    std::vector<std::pair<long long, int>> order;
+    for (int r = 0; r < n; ++r) {
+        Ctx *c = b->runs[r];
+        for (int p = 0; p < 2; ++p) {
+            StepParams<float> q = step_params<float>(c);
+            for (int s = 0; s < q.nsp; ++s) q.sp[s] = dev_species<float>(c, s, p);
+            q.diag = DiagParams{};
+            P[p].push_back(q);
+        }
+        tm[r] = c->tmapEB;
+        F[r].m = mesh<float>(c);
+        F[r].bnd = static_cast<float *>(c->bnd);
+        F[r].prof = c->laser_prof;
+        F[r].step0 = c->step;
+        F[r].r = c->dt / c->dx;
+        F[r].q = c->dt / c->dy;
+        step0[r] = c->step;
+        end[r] = c->step + left[r];
+        const LaserParams L = laser(c);
+        for (long long k = 0; k < left[r]; ++k)
+            laser_time_factors(L, ((double)(c->step + k) + 0.5) * c->dt, &lt[laser_off[r] + 2 * k],
+                               &lt[laser_off[r] + 2 * k + 1]);
+        order.push_back({-(long long)c->ntiles * left[r], r});
+    }
+    std::sort(order.begin(), order.end());
+    std::vector<int2> work, rows;
+    for (auto &o : order) {
+        Ctx *c = b->runs[o.second];
+        for (int t = 0; t < c->ntiles; ++t) work.push_back(make_int2(o.second, t));
+        for (int j = 0; j < c->cfg.ny; ++j) rows.push_back(make_int2(o.second, j));
+    }
+    b->nwork = (int)work.size();
+    b->nrows = (int)rows.size();
+    BCK(cudaMalloc(&b->laser, lt.size() * sizeof(double)));
+    BCK(cudaMemcpyAsync(b->laser, lt.data(), lt.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    for (int r = 0; r < n; ++r) F[r].laser = b->laser + laser_off[r];
+    for (int p = 0; p < 2; ++p) {
+        BCK(cudaMalloc(&b->params[p], n * sizeof(StepParams<float>)));
+        BCK(cudaMemcpyAsync(b->params[p], P[p].data(), n * sizeof(StepParams<float>), cudaMemcpyHostToDevice, st));
+    }
+    BCK(cudaMalloc(&b->tmaps, n * sizeof(CUtensorMap)));
+    BCK(cudaMemcpyAsync(b->tmaps, tm.data(), n * sizeof(CUtensorMap), cudaMemcpyHostToDevice, st));
+    BCK(cudaMalloc(&b->fields, n * sizeof(BatchField<float>)));
+    BCK(cudaMemcpyAsync(b->fields, F.data(), n * sizeof(BatchField<float>), cudaMemcpyHostToDevice, st));
+    BCK(cudaMalloc(&b->work, work.size() * sizeof(int2)));
+    BCK(cudaMemcpyAsync(b->work, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+    BCK(cudaMalloc(&b->rows, rows.size() * sizeof(int2)));
+    BCK(cudaMemcpyAsync(b->rows, rows.data(), rows.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+    BCK(cudaMalloc(&b->step, n * sizeof(long long)));
+    BCK(cudaMemcpyAsync(b->step, step0.data(), n * sizeof(long long), cudaMemcpyHostToDevice, st));
+    BCK(cudaMalloc(&b->nsteps, n * sizeof(long long)));
+    BCK(cudaMemcpyAsync(b->nsteps, end.data(), n * sizeof(long long), cudaMemcpyHostToDevice, st));
+    BCK(cudaMalloc(&b->counter, sizeof(int)));
+    BCK(cudaMemsetAsync(b->counter, 0, sizeof(int), st));
+    BCK(cudaStreamSynchronize(st));
+    int dev = 0, sms = 0;
+    BCK(cudaGetDevice(&dev));
+    BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    b->ctas = sms * fused_batch_occupancy(b->tx, b->ty);
+    b->prepared = true;
+    return PIC_OK;
+}
+
+// one batch step on the stream (launches only; capturable)
+cudaError_t enqueue_step(Batch *b, int parity, cudaStream_t st) {
+    BatchFused<float> W{b->params[parity], b->tmaps, b->work, b->nwork, b->counter, b->step, b->nsteps};
+    cudaError_t e = launch_step_fused_batch<float>(W, b->tx, b->ty, b->ctas, st);
+    if (e != cudaSuccess) return e;
+    return launch_field_update_batch<float>(b->fields, b->rows, b->nrows, b->step, b->nsteps, (int)b->runs.size(),
+                                            b->counter, st);
+}
+
+pic_status_t run_graph(Batch *b, int steps, cudaStream_t st) {
+    auto &cache = b->graphs[b->parity];
+    cudaGraphExec_t exec = nullptr;
+    for (auto &g : cache)
+        if (g.first == steps) exec = g.second;
+    if (!exec) {
+        cudaStream_t cs;
+        BCK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        for (int k = 0; k < steps && e == cudaSuccess; ++k) e = enqueue_step(b, b->parity, cs);
+        cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+        cudaStreamDestroy(cs);
+        BCK(e);
+        BCK(e2);
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        BCK(e);
+        cache.push_back({steps, exec});
+    }
+    BCK(cudaGraphLaunch(exec, st));
+    for (Ctx *c : b->runs) c->launches += 6LL * steps;
+    return PIC_OK;
+}
+
+// up to nsteps batch steps: sort-free stretches as graph replays, tile sorts
+// between them (runs still active only)
+pic_status_t batch_advance(Batch *b, long long nsteps, cudaStream_t st) {
+    const int n = (int)b->runs.size();
+    pic_status_t r = align_parity(b, st);
+    if (r != PIC_OK) return r;
+    if (!b->prepared) {
+        r = prepare(b, st);
+        if (r != PIC_OK) return r;
+    }
+    while (nsteps > 0) {
+        long long active = 0;
+        for (int k = 0; k < n; ++k) active += b->done[k] < b->todo[k];
+        if (!active) break;
+        const int chunk = (int)std::min<long long>(nsteps, b->sort_every - b->since_sort);
+        r = run_graph(b, chunk, st);
+        if (r != PIC_OK) return r;
+        for (int k = 0; k < n; ++k) {
+            const long long take = std::min<long long>(chunk, b->todo[k] - b->done[k]);
+            if (take > 0) {
+                b->done[k] += take;
+                b->runs[k]->step += take;
+            }
+        }
+        nsteps -= chunk;
+        b->since_sort += chunk;
+        if (b->since_sort >= b->sort_every) {
+            const int next = 1 - b->parity;
+            for (int k = 0; k < n; ++k) {
+                Ctx *c = b->runs[k];
+                for (int s = 0; s < c->cfg.nspecies; ++s) {
+                    r = sort_species(c, s, st);
+                    if (r != PIC_OK) return bfail(b, r, c->last_error);
+                }
+            }
+            b->parity = next;
+            b->since_sort = 0;
+        }
+    }
+    return PIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pic_status_t pic_batch_create(const pic_config_t *cfgs, int nruns, const int64_t *nsteps, void *stream,
+                              void **batch_out) {
+    Batch *b = nullptr;
+    if (!batch_out || !cfgs || !nsteps || nruns < 1) return bfail(b, PIC_ERR_ARG, "need configs, steps and nruns >= 1");
+    *batch_out = nullptr;
+    b = new (std::nothrow) Batch();
+    if (!b) return bfail(nullptr, PIC_ERR_CUDA, "host allocation failed");
+    b->tx = cfgs[0].tile_x > 0 ? cfgs[0].tile_x : 16;
+    b->ty = cfgs[0].tile_y > 0 ? cfgs[0].tile_y : 8;
+    b->sort_every = cfgs[0].sort_every > 0 ? cfgs[0].sort_every : 32;
+    for (int r = 0; r < nruns; ++r) {
+        pic_config_t cfg = cfgs[r];
+        if ((cfg.dim != 0 && cfg.dim != 2) || (cfg.precision != 0 && cfg.precision != 32) || nsteps[r] < 0) {
+            pic_batch_destroy(b);
+            return bfail(nullptr, PIC_ERR_ARG, "batch runs must be 2D3V, precision 32, steps >= 0");
+        }
+        cfg.tile_x = b->tx;
+        cfg.tile_y = b->ty;
+        void *h = nullptr;
+        pic_status_t st = pic_create(&cfg, stream, &h);
+        if (st != PIC_OK) {
+            const std::string why = "run " + std::to_string(r) + ": " + g_create_error;
+            pic_batch_destroy(b);
+            return bfail(nullptr, st, why);
+        }
+        b->runs.push_back(static_cast<Ctx *>(h));
+        b->todo.push_back(nsteps[r]);
+        b->done.push_back(0);
+    }
+    *batch_out = b;
+    return PIC_OK;
+}
+
+void pic_batch_destroy(void *batch) {
+    Batch *b = static_cast<Batch *>(batch);
+    if (!b) return;
+    free_tables(b);
+    for (Ctx *c : b->runs) pic_destroy(c);
+    delete b;
+}
+
+pic_status_t pic_batch_run(void *batch, int r, void **ctx) {
+    Batch *b = static_cast<Batch *>(batch);
+    if (!b || !ctx || r < 0 || r >= (int)b->runs.size()) return bfail(b, PIC_ERR_ARG, "bad batch or run index");
+    b->prepared = false;  // the caller may change the run's state (particles, fields, step)
+    *ctx = b->runs[r];
+    return PIC_OK;
+}
+
+pic_status_t pic_batch_step(void *batch, int64_t nsteps, void *stream) {
+    Batch *b = static_cast<Batch *>(batch);
+    if (!b) return bfail(nullptr, PIC_ERR_ARG, "null batch");
+    if (nsteps < 0) return bfail(b, PIC_ERR_ARG, "negative step count");
+    cudaStream_t st = S(stream);
+    for (Ctx *c : b->runs)
+        if (c->pending_deposit) return bfail(b, PIC_ERR_STATE, "a run has a move waiting for pic_deposit");
+    pic_status_t r = batch_advance(b, nsteps, st);
+    if (r != PIC_OK) return r;
+    for (size_t k = 0; k < b->runs.size(); ++k) {
+        r = check_flags(b->runs[k], st);
+        if (r != PIC_OK) return bfail(b, r, "run " + std::to_string(k) + ": " + b->runs[k]->last_error);
+    }
+    return PIC_OK;
+}
+
+pic_status_t pic_batch_steps_done(void *batch, int64_t *done) {
+    Batch *b = static_cast<Batch *>(batch);
+    if (!b || !done) return bfail(b, PIC_ERR_ARG, "null argument");
+    for (size_t k = 0; k < b->runs.size(); ++k) done[k] = b->done[k];
+    return PIC_OK;
+}
+
+pic_status_t pic_batch_tune(void *batch, int probe_steps, const int *tiles, int ntiles, const int *sorts, int nsorts,
+                            int *chosen, void *stream) {
+    Batch *b = static_cast<Batch *>(batch);
+    if (!b) return bfail(nullptr, PIC_ERR_ARG, "null batch");
+    if (probe_steps < 1 || !tiles || ntiles < 1 || !sorts || nsorts < 1 || !chosen)
+        return bfail(b, PIC_ERR_ARG, "need probe_steps >= 1 and candidate tiles and sort cadences");
+    for (int k = 0; k < ntiles; ++k)
+        if (!fused_tile_supported(tiles[2 * k], tiles[2 * k + 1])) return bfail(b, PIC_ERR_ARG, "unsupported tile");
+    for (int k = 0; k < nsorts; ++k)
+        if (sorts[k] < 1) return bfail(b, PIC_ERR_ARG, "sort cadence must be >= 1");
+    cudaStream_t st = S(stream);
+    cudaEvent_t e0, e1;
+    BCK(cudaEventCreate(&e0));
+    BCK(cudaEventCreate(&e1));
+    double best = -1.0;
+    int bt = 0, bs = 0;
+    pic_status_t r = PIC_OK;
+    for (int t = 0; t < ntiles && r == PIC_OK; ++t) {
+        if (tiles[2 * t] != b->tx || tiles[2 * t + 1] != b->ty) {
+            for (Ctx *c : b->runs)
+                if ((r = retile(c, tiles[2 * t], tiles[2 * t + 1], st)) != PIC_OK) break;
+            if (r != PIC_OK) break;
+            b->tx = tiles[2 * t];
+            b->ty = tiles[2 * t + 1];
+            b->parity = -1;
+            b->since_sort = 0;
+            free_tables(b);
+        }
+        for (int q = 0; q < nsorts && r == PIC_OK; ++q) {
+            b->sort_every = sorts[q];
+            b->since_sort = 0;
+            // one sort cycle as warm-up (graph capture), then the probe
+            if ((r = batch_advance(b, sorts[q], st)) != PIC_OK) break;
+            std::vector<long long> before = b->done;
+            long long parts = 0;
+            for (Ctx *c : b->runs)
+                for (int s = 0; s < c->cfg.nspecies; ++s) parts += c->cfg.sp[s].mobile ? c->n_upper[s] : 0;
+            cudaEventRecord(e0, st);
+            if ((r = batch_advance(b, probe_steps, st)) != PIC_OK) break;
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            long long taken = 0;
+            for (size_t k = 0; k < b->runs.size(); ++k) taken += b->done[k] - before[k];
+            const double rate = taken > 0 && ms > 0 ? (double)parts * probe_steps / ms : 0.0;
+            if (rate > best) {
+                best = rate;
+                bt = t;
+                bs = q;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (r != PIC_OK) return r;
+    if (tiles[2 * bt] != b->tx || tiles[2 * bt + 1] != b->ty) {
+        for (Ctx *c : b->runs)
+            if ((r = retile(c, tiles[2 * bt], tiles[2 * bt + 1], st)) != PIC_OK) return bfail(b, r, c->last_error);
+        b->tx = tiles[2 * bt];
+        b->ty = tiles[2 * bt + 1];
+        b->parity = -1;
+        free_tables(b);
+    }
+    b->sort_every = sorts[bs];
+    b->since_sort = 0;
+    chosen[0] = b->tx;
+    chosen[1] = b->ty;
+    chosen[2] = b->sort_every;
+    return PIC_OK;
+}
+
+const char *pic_batch_last_error(void *batch) {
+    Batch *b = static_cast<Batch *>(batch);
+    return b ? b->last_error.c_str() : g_create_error.c_str();
 }
 
 }  // extern "C"

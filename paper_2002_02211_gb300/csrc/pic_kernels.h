@@ -19,8 +19,38 @@ struct LaserParams {
     double a0, w0, tau, t_peak, yc, dy;
 };
 
+// batched step of many 2D3V runs (pic_batch.cu): the work queue of the
+// persistent fused kernel
+template <typename R>
+struct BatchFused {
+    const StepParams<R> *params;   // [nruns]
+    const CUtensorMap *tmaps;      // [nruns], 64-byte aligned
+    const int2 *work;              // [nwork] (run, tile)
+    int nwork;
+    int *counter;                  // queue head, zero before the launch
+    const long long *step, *nsteps;  // [nruns]: items of runs with step >= nsteps are skipped
+};
+
+// per-run field data of a batch: mesh, left boundary values, laser profile,
+// laser time factors (fz, fy) of steps step0, step0 + 1, ..., r = dt/dx, q = dt/dy
+template <typename R>
+struct BatchField {
+    MeshParams<R> m;
+    R *bnd;
+    const double *prof;
+    const double *laser;
+    long long step0;
+    double r, q;
+};
+template <typename R>
+cudaError_t launch_field_update_batch(const BatchField<R> *runs, const int2 *rows, int nrows, long long *step,
+                                      const long long *nsteps, int nruns, int *counter, cudaStream_t st);
+
 // k_particles.cu
 bool fused_tile_supported(int tx, int ty);
+template <typename R>
+cudaError_t launch_step_fused_batch(const BatchFused<R> &W, int tx, int ty, int ctas, cudaStream_t st);
+int fused_batch_occupancy(int tx, int ty);
 template <typename R>
 cudaError_t launch_step_fused(const StepParams<R> &P, const CUtensorMap &tmapEB, cudaStream_t st);
 template <typename R>

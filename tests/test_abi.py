@@ -37,7 +37,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_binding_names_match_header():
     for n in _declared():
-        if n in ("pic_destroy", "pic_last_error"):
+        if n in ("pic_destroy", "pic_last_error", "pic_batch_destroy", "pic_batch_last_error"):
             continue
         assert n in pic._SIGS, n
 
@@ -47,7 +47,8 @@ def _status(cfg):
 
 
 def test_validate_config_accepts_the_workloads():
-    for wl in (W.CONFIG1, W.CONFIG3, W.small_case(), W.small_case(bc_x="periodic", two_species=True)):
+    for wl in (W.CONFIG1, W.CONFIG2, W.CONFIG3, W.small_case(), W.small_case(bc_x="periodic", two_species=True),
+               W.small_case3()):
         assert _status(pic.config_from_workload(wl)) == 0
 
 

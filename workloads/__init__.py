@@ -26,7 +26,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-__all__ = ["Species", "Workload", "CONFIG1", "CONFIG2", "CONFIG3", "generate_particles",
+__all__ = ["Species", "Workload", "CONFIG1", "CONFIG2", "CONFIG3", "batch_scan", "generate_particles",
            "injection_particles", "random_fields", "small_case", "small_case3", "scaled"]
 
 
@@ -102,6 +102,33 @@ CONFIG2 = Workload(
     species=(Species("electron", n0=0.003, ppc=2, u_th=1e-3, s0=(0.0, 1.0, 0.0), **ELECTRON),),
     a0=3.0, waist_lambda=8.0, fwhm_periods=10.0, t_peak_periods=15.0, pol="lp-y",
     bc_x="open", neutralizing_background=True, seed=2, dim=3, nz=256, dz_lambda=1 / 8)
+
+
+def batch_scan(nruns: int = 256, seed: int = 4, size_scale: float = 1.0, step_scale: float = 1.0):
+    """Parameter scan of independent 2D3V runs of uneven sizes: per run Nx in
+    {128, 256, 512, 1024} (equal odds: uniform in log Nx), Ny = Nx/2,
+    dx = dy = lambda/16, electron density n0 ~ U(0.001, 0.05) n_c over immobile
+    ions, ppc ~ U{2..8}, LP laser a0 ~ U(2, 20) (waist a quarter of the box
+    height, FWHM 10 periods, peak at 15 periods), spins +y, steps ~
+    U{300..1500}; seed-drawn.  size_scale / step_scale shrink the meshes and
+    run lengths for tests.  Returns [(Workload, steps)]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for r in range(nruns):
+        nx = int(rng.choice([128, 256, 512, 1024]))
+        nx = max(16, int(round(nx * size_scale / 8)) * 8)
+        ny = max(8, nx // 2)
+        n0 = float(rng.uniform(0.001, 0.05))
+        a0 = float(rng.uniform(2.0, 20.0))
+        ppc = int(rng.integers(2, 9))
+        steps = max(1, int(round(int(rng.integers(300, 1501)) * step_scale)))
+        sp = Species("electron", n0=n0, ppc=ppc, u_th=1e-3, s0=(0.0, 1.0, 0.0), **ELECTRON)
+        wl = Workload(name=f"scan{r}-{nx}x{ny}-ppc{ppc}", nx=nx, ny=ny, dx_lambda=1 / 16, dy_lambda=1 / 16,
+                      cfl=0.95, steps=steps, species=(sp,), a0=a0, waist_lambda=ny / 16 / 4,
+                      fwhm_periods=10.0, t_peak_periods=15.0, pol="lp-y", bc_x="open",
+                      neutralizing_background=True, seed=seed * 1000 + r)
+        out.append((wl, steps))
+    return out
 
 
 def scaled(wl: Workload, **kw) -> Workload:
