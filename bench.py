@@ -12,6 +12,11 @@ every species (accumulated inside the fused kernel).  Workloads:
   config3            2D3V pre-polarised hydrogen: 4096 x 1024 cells
                      (dx = lambda/32), 8 + 8 ppc electrons and protons, CP a0 = 60
   config1            2D3V 256 x 128, 4 ppc, LP a0 = 4 (small; L2 resident)
+  config4            parameter scan: 256 independent 2D3V runs of uneven
+                     sizes (128x64 .. 1024x512), densities, a0, ppc and
+                     lengths (300-1500 steps), run to completion as one batch
+                     (pic_batch_*, autotuned tiles and sort cadence) and, for
+                     comparison, one after another through the single-run calls
 
 Prints one JSON line (rank 0).
 
@@ -66,7 +71,8 @@ def parse(argv=None):
     ap.add_argument("--steps", type=int, default=600)
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["config2", "config3", "config1"], default="config2")
+    ap.add_argument("--workload", choices=["config2", "config3", "config1", "config4"], default="config2")
+    ap.add_argument("--scan-runs", type=int, default=256, help="config4: runs of the scan")
     ap.add_argument("--sort-every", type=int, default=0, help="0: 32 in 2D3V, 2 in 3D3V")
     ap.add_argument("--diag-every", type=int, default=10)
     ap.add_argument("--tile", type=int, nargs="+", default=None)
@@ -81,6 +87,8 @@ def parse(argv=None):
 
 
 def workload(name, ny=0, nz=0):
+    if name == "config4":  # one run of the scan stands for it where a single workload is needed
+        return W.batch_scan(1)[0][0]
     wl = {"config1": W.CONFIG1, "config2": W.CONFIG2, "config3": W.CONFIG3}[name]
     if ny:
         wl = W.scaled(wl, ny=ny)
@@ -492,10 +500,105 @@ def main_ours(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# config4: the batched parameter scan against looped single runs
+# ---------------------------------------------------------------------------
+def main_scan(args):
+    import torch
+
+    import paper_2002_02211_gb300 as pic
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    init_dist(world, "nccl")
+    dev = torch.device("cuda", local)
+    # replicas: every rank runs its share of the scan (runs dealt round-robin)
+    runs = W.batch_scan(args.scan_runs)[rank::world]
+    parts = [W.generate_particles(wl) for wl, _ in runs]
+    stream = torch.cuda.Stream(device=dev)
+    cfgs = [pic.config_from_workload(wl) for wl, _ in runs]
+    work = sum(len(p[0]["ix"]) * n for p, (_, n) in zip(parts, runs))
+
+    def load(sim, r):
+        for s, d in enumerate(parts[r]):
+            sim.set_particles(s, d)
+        sim.capture_background()
+
+    # batched: upload, autotune (its probe steps are real steps of the runs),
+    # then every run to completion
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    with pic.Batch(cfgs, [n for _, n in runs], stream=stream) as b:
+        for r in range(len(runs)):
+            load(b.run(r), r)
+        stream.synchronize()
+        t_up = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        chosen = b.tune(4, tiles=((16, 8), (32, 8)), sorts=(16, 32, 64))
+        done0 = b.steps_done()
+        launches0 = b.launch_count()
+        stream.synchronize()
+        t_tune = time.perf_counter() - t0
+        clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.step(10 ** 9)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        clk = clocks.stop()
+        t_run = e0.elapsed_time(e1) * 1e-3
+        launches = b.launch_count() - launches0
+        t1 = time.perf_counter()
+        pol = [b.run(r).polarization(0)["P"].tolist() for r in range(len(runs))]
+        t_read = time.perf_counter() - t1
+        tuned_work = sum(len(p[0]["ix"]) * d for p, d in zip(parts, done0))
+    timed_work = work - tuned_work
+    t_run, timed_work_all = combine(t_run, timed_work, world, dev)
+    e2e_time, work_all = combine(t_up + t_tune + t_run + t_read, work, world, dev)
+
+    # looped: the same runs one after another, each through pic_step
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for r, (wl, n) in enumerate(runs):
+        cfg = pic.config_from_workload(wl, sort_every=chosen[2], tile=chosen[:2])
+        with pic.Simulation(cfg, stream=stream) as sim:
+            load(sim, r)
+            sim.step(n)
+            sim.sync()
+    t_loop = time.perf_counter() - t0
+    t_loop, _ = combine(t_loop, 0, world, dev)
+
+    if rank == 0:
+        value = timed_work_all / t_run
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": max(n for _, n in runs),
+                "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"batched scan of {args.scan_runs} 2D3V runs (seed 4)",
+                           "runs_per_rank": len(runs), "particle_steps": work_all,
+                           "tuned": {"tile": list(chosen[:2]), "sort_every": chosen[2]},
+                           "l2": "inputs larger than L2", "parallelism": f"replicas x{world} (runs dealt)"},
+                "batched_s": t_run, "looped_single_runs": {"value": work_all / t_loop, "seconds": t_loop,
+                                                           "what": "each run alone: pic_create, upload, pic_step"},
+                "speedup_vs_looped": (work_all / t_loop) and value / (work_all / t_loop),
+                "e2e": {"value": work_all / e2e_time, "unit": UNIT,
+                        "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+                        "what": "upload of every run's particles, autotune, all steps, Eq. (4) read-back"},
+                "clocks": clk, "gpu_launches": launches,
+                "P_first_runs": pol[:4]}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def main(argv=None):
     args = parse(argv)
     if args.impl == "reference":
         main_reference(args)
+    elif args.workload == "config4":
+        main_scan(args)
     else:
         main_ours(args)
 

@@ -355,6 +355,8 @@ pic_status_t pic_batch_steps_done(void *batch, int64_t *done);
  * fastest pair: chosen = {tile_x, tile_y, sort_every}.  Synchronous. */
 pic_status_t pic_batch_tune(void *batch, int probe_steps, const int *tiles, int ntiles, const int *sorts,
                             int nsorts, int *chosen, void *stream);
+/* Kernels launched for the batch and its runs so far. */
+pic_status_t pic_batch_launch_count(void *batch, int64_t *count);
 /* One-line reason for the last failure of a batch call (NULL: of pic_batch_create). */
 const char *pic_batch_last_error(void *batch);
 

@@ -119,6 +119,7 @@ _SIGS = {
     "pic_batch_run": [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)],
     "pic_batch_step": [C.c_void_p, C.c_int64, C.c_void_p],
     "pic_batch_steps_done": [C.c_void_p, C.c_void_p],
+    "pic_batch_launch_count": [C.c_void_p, C.POINTER(C.c_int64)],
     "pic_batch_tune": [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
     "pic_get_window": [C.c_void_p, C.POINTER(C.c_int64)],
     "pic_set_diagnostics": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
@@ -474,6 +475,11 @@ class Batch:
         out = (C.c_int64 * self.n)()
         self._c(load().pic_batch_steps_done(self.h, out))
         return list(out)
+
+    def launch_count(self):
+        v = C.c_int64()
+        self._c(load().pic_batch_launch_count(self.h, C.byref(v)))
+        return v.value
 
     def tune(self, probe_steps, tiles=((16, 8), (32, 8)), sorts=(16, 32, 64)):
         t = (C.c_int * (2 * len(tiles)))(*[v for tt in tiles for v in tt])

@@ -1216,6 +1216,7 @@ struct Batch {
     int nwork = 0, nrows = 0, ctas = 0;
     long long *step = nullptr, *nsteps = nullptr;
     int *counter = nullptr;
+    long long launches = 0;  // kernels the batch launched (graph nodes included, run contexts' own not)
     std::vector<std::pair<int, cudaGraphExec_t>> graphs[2];  // (steps, graph) per parity
     std::string last_error;
 };
@@ -1385,7 +1386,7 @@ pic_status_t run_graph(Batch *b, int steps, cudaStream_t st) {
         cache.push_back({steps, exec});
     }
     BCK(cudaGraphLaunch(exec, st));
-    for (Ctx *c : b->runs) c->launches += 6LL * steps;
+    b->launches += 6LL * steps;  // fused, 2 x B half step, boundary, E step, advance
     return PIC_OK;
 }
 
@@ -1576,6 +1577,15 @@ pic_status_t pic_batch_tune(void *batch, int probe_steps, const int *tiles, int 
     chosen[0] = b->tx;
     chosen[1] = b->ty;
     chosen[2] = b->sort_every;
+    return PIC_OK;
+}
+
+pic_status_t pic_batch_launch_count(void *batch, int64_t *count) {
+    Batch *b = static_cast<Batch *>(batch);
+    if (!b || !count) return bfail(b, PIC_ERR_ARG, "null argument");
+    long long n = b->launches;
+    for (Ctx *c : b->runs) n += c->launches;  // the runs' own: uploads, sorts, reductions
+    *count = n;
     return PIC_OK;
 }
 
