@@ -176,6 +176,10 @@ pic_status_t pic_get_grid(void *ctx, double *dt, double *dx, double *dy, double 
  * Cells must lie in the particle region (else PIC_ERR_ARG).  Synchronous. */
 pic_status_t pic_set_particles(void *ctx, int species, const pic_particles_t *p, void *stream);
 
+/* The same from float64 host arrays (exact with precision 64; rounded to
+ * float with precision 32). */
+pic_status_t pic_set_particles_f64(void *ctx, int s, const pic_particles_f64_t *p, void *stream);
+
 /* Number of particle slots of one species (live and removed since the last
  * sort).  Synchronises the legacy default stream. */
 pic_status_t pic_get_count(void *ctx, int species, int64_t *n);
@@ -324,6 +328,42 @@ pic_status_t pic_moments_noalloc(int64_t n, const uint32_t *cell, const float *u
 
 /* Reason for the last failure on this context (or of pic_create when ctx is NULL). */
 const char *pic_last_error(void *ctx);
+
+/* ---- adjoint (2D3V) ----------------------------------------------------------
+ * Loss on the final state: over the live particles of one species,
+ *   L = sum_i a_i s_i / sum_i a_i,   a_i = w_i e_i sig((e_i - e_cut) / e_width),
+ * e_i the kinetic energy [MeV], s_i the spin component `axis`, sig the
+ * logistic function: the polarization (Eq. 4) of the energetic part of the
+ * beam, weighted by energy. */
+typedef struct {
+    int species;
+    int axis;             /* 0: x, 1: y, 2: z */
+    double e_cut_mev;
+    double e_width_mev;   /* > 0 */
+} pic_loss_t;
+
+/* L of the current state.  Synchronous. */
+pic_status_t pic_loss(void *ctx, const pic_loss_t *loss, double *value, void *stream);
+
+/* Runs nsteps steps forward from the current state (split path, no tile
+ * sorts: every slot keeps its particle) keeping a checkpoint every
+ * checkpoint_every steps, evaluates L at the end, and back-propagates: each
+ * stretch is recomputed from its checkpoint with every state stored, and the
+ * adjoint of every step (the transposes of the Yee stages and the
+ * vector-Jacobian products of gather, push, spin, advance and deposit) runs
+ * back through it.  Out: L, dL/da0 (laser amplitude); the gradients with
+ * respect to each particle's initial state and weight are kept for
+ * pic_adjoint_particle_grads.  The context ends in the final forward state.
+ * Device memory: (ceil(nsteps / checkpoint_every) + checkpoint_every + 1)
+ * copies of the particle state and E, B.  Synchronous.  2D3V only. */
+pic_status_t pic_adjoint(void *ctx, int nsteps, int checkpoint_every, const pic_loss_t *loss, double *loss_value,
+                         double *dloss_da0, void *stream);
+
+/* Gradients of the last pic_adjoint with respect to the initial state of the
+ * slots of species s: ox, oy <- dL/d(offset) (per cell), ux, uy, uz <- dL/du,
+ * sx, sy, sz <- dL/ds, w <- dL/dw; ix, iy, id <- the slot's initial cell and
+ * identity.  out->n >= the slot count (set to it).  Synchronous. */
+pic_status_t pic_adjoint_particle_grads(void *ctx, int s, pic_particles_f64_t *out, void *stream);
 
 /* ---- batches of independent 2D3V runs --------------------------------------
  * A parameter scan (density, a0, mesh size, particles per cell, run length)

@@ -318,6 +318,19 @@ class OracleSim:
         lib().or_laser(C.byref(self.grid), t, y, comp, C.byref(v))
         return v.value
 
+    def loss(self, s, axis=1, e_cut_mev=50.0, e_width_mev=5.0):
+        """L = sum a_i s_i / sum a_i over the live particles of species s, with
+        a_i = w_i e_i sig((e_i - e_cut) / e_width), e_i = (gamma - 1) m c^2 [MeV]
+        and s_i the spin component `axis`: the energy-weighted polarization
+        (Eq. 4) of the energetic part of the beam."""
+        d = self.p[s]
+        live = d["alive"] > 0
+        u2 = d["ux"][live] ** 2 + d["uy"][live] ** 2 + d["uz"][live] ** 2
+        e = (np.sqrt(1.0 + u2) - 1.0) * self.spec[s].m * MEC2_MEV
+        a = d["w"][live] * e / (1.0 + np.exp(-(e - e_cut_mev) / e_width_mev))
+        spin = d[("sx", "sy", "sz")[axis]][live]
+        return float((a * spin).sum() / a.sum()) if a.sum() > 0 else 0.0
+
     # moving window -----------------------------------------------------------
     POS = ("x", "y")
 

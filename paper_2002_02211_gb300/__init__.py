@@ -80,6 +80,10 @@ class pic_fields_t(C.Structure):
                                      "by_left", "bz_left")]
 
 
+class pic_loss_t(C.Structure):
+    _fields_ = [("species", C.c_int), ("axis", C.c_int), ("e_cut_mev", C.c_double), ("e_width_mev", C.c_double)]
+
+
 class pic_moments_t(C.Structure):
     _fields_ = [("P", C.c_double * 3), ("sum_w", C.c_double), ("count", C.c_double),
                 ("ekin_mean", C.c_double), ("ekin_var", C.c_double)]
@@ -93,6 +97,7 @@ _SIGS = {
     "pic_get_grid": [C.c_void_p] + [C.POINTER(C.c_double)] * 4,
     "pic_set_particles": [C.c_void_p, C.c_int, C.POINTER(pic_particles_t), C.c_void_p],
     "pic_get_count": [C.c_void_p, C.c_int, C.POINTER(C.c_int64)],
+    "pic_set_particles_f64": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
     "pic_get_particles": [C.c_void_p, C.c_int, C.POINTER(pic_particles_t), C.c_void_p],
     "pic_get_particles_f64": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
     "pic_get_fields_f64": [C.c_void_p, C.c_void_p, C.c_void_p],
@@ -115,6 +120,10 @@ _SIGS = {
     "pic_gauss_residual": [C.c_void_p, C.POINTER(C.c_double), C.c_void_p],
     "pic_sync": [C.c_void_p, C.c_void_p],
     "pic_shift_window": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
+    "pic_loss": [C.c_void_p, C.POINTER(pic_loss_t), C.POINTER(C.c_double), C.c_void_p],
+    "pic_adjoint": [C.c_void_p, C.c_int, C.c_int, C.POINTER(pic_loss_t), C.POINTER(C.c_double),
+                    C.POINTER(C.c_double), C.c_void_p],
+    "pic_adjoint_particle_grads": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
     "pic_batch_create": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)],
     "pic_batch_run": [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)],
     "pic_batch_step": [C.c_void_p, C.c_int64, C.c_void_p],
@@ -289,6 +298,15 @@ class Simulation:
                                     for k, v in arr.items()})
         self._c(load().pic_set_particles(self.h, s, C.byref(p), self._s))
 
+    def set_particles_f64(self, s, d):
+        """set_particles from float64 arrays (exact in a precision-64 context)."""
+        n = len(d["ix"])
+        arr = {k: np.ascontiguousarray(d[k], dtype=np.int32 if k in _INT_KEYS else np.float64)
+               for k in self._pkeys}
+        p = pic_particles_f64_t(n=n, **{k: _ptr(v, _I32P if v.dtype == np.int32 else _F64P)
+                                        for k, v in arr.items()})
+        self._c(load().pic_set_particles_f64(self.h, s, C.byref(p), self._s))
+
     def set_particles_raw(self, s, n, ptrs):
         """Like set_particles, from raw host addresses (e.g. pinned buffers):
         ptrs maps every pic_particles_t array name to an integer address."""
@@ -415,6 +433,35 @@ class Simulation:
 
     def sync(self):
         self._c(load().pic_sync(self.h, self._s))
+
+    # adjoint (2D3V) ----------------------------------------------------------
+    @staticmethod
+    def _loss(species=0, axis=1, e_cut_mev=50.0, e_width_mev=5.0):
+        return pic_loss_t(species=species, axis=axis, e_cut_mev=e_cut_mev, e_width_mev=e_width_mev)
+
+    def loss(self, **kw):
+        """pic_loss of the current state (keywords: species, axis, e_cut_mev, e_width_mev)."""
+        v = C.c_double()
+        self._c(load().pic_loss(self.h, C.byref(self._loss(**kw)), C.byref(v), self._s))
+        return v.value
+
+    def adjoint(self, nsteps, checkpoint_every, **kw):
+        """pic_adjoint: (L, dL/da0); per-particle gradients via adjoint_particle_grads."""
+        v, g = C.c_double(), C.c_double()
+        self._c(load().pic_adjoint(self.h, int(nsteps), int(checkpoint_every), C.byref(self._loss(**kw)),
+                                   C.byref(v), C.byref(g), self._s))
+        return v.value, g.value
+
+    def adjoint_particle_grads(self, s):
+        """dL/d(initial state) of the slots of species s: keys ox oy ux uy uz sx sy sz w
+        (float64) and the slots' initial ix, iy and id."""
+        n = self.count(s)
+        keys = ("ix", "iy", "ox", "oy", "ux", "uy", "uz", "sx", "sy", "sz", "w", "id")
+        out = {k: np.empty(max(n, 1), np.int32 if k in _INT_KEYS else np.float64) for k in keys}
+        p = pic_particles_f64_t(n=len(out["ix"]), **{k: _ptr(v, _I32P if v.dtype == np.int32 else _F64P)
+                                                     for k, v in out.items()})
+        self._c(load().pic_adjoint_particle_grads(self.h, s, C.byref(p), self._s))
+        return {k: v[:p.n] for k, v in out.items()}
 
     def shift_window(self, ncells, inject=None):
         """pic_shift_window: inject is None or one particle dict per species."""

@@ -1,0 +1,385 @@
+// k_adjoint.cu -- discrete adjoint of the 2D3V step (gather, Boris push,
+// Thomas-BMT rotation, position advance, Esirkepov current, three-stage Yee
+// update with the Silver-Mueller boundary and laser source), for the gradient
+// of a loss on the final particle state with respect to the initial particle
+// state, the particle weights and the laser amplitude a0.
+//
+// The step is linear in the mesh fields except through the particles, so the
+// mesh part of the adjoint is the transpose of each field stage; the particle
+// part is, per particle, the vector-Jacobian product of the forward arithmetic,
+// taken by running the forward device functions (gather_eb, push_spin,
+// deposit_esirkepov) on forward-mode dual numbers.  Adjoint kernels run in the
+// reverse order of the forward stages:
+//   b_half^T, e_full^T (-> lambda_J), boundary^T (-> dL/da0), b_half^T, particles^T.
+#include <algorithm>
+
+#include "pic_dual.cuh"
+#include "pic_kernels.h"
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// mesh transposes (the same validity rules as the forward stages)
+// ---------------------------------------------------------------------------
+// forward: Bx(j,i) -= hdy (Ez(j+1,i) - Ez(j,i));  By(j,i) += hdx (Ez(j,i+1) - Ez(j,i));
+//          Bz(j,i) -= hdx (Ey(j,i+1) - Ey(j,i)) - hdy (Ex(j+1,i) - Ex(j,i)),
+// By, Bz only where column i+1 exists.  Transpose: lambda_E += C^T lambda_B.
+template <typename R>
+__global__ void __launch_bounds__(256) k_adj_b_half(const AdjMesh<R> A, R hdx, R hdy) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    const int nx = A.nx, ny = A.ny, ld = A.ld;
+    if (i >= nx) return;
+    const bool per = A.bc_x == 1;
+    const size_t P = A.plane;
+    R *L = A.LEB;
+    const int jm = j == 0 ? ny - 1 : j - 1;
+    const int im = i == 0 ? (per ? nx - 1 : -1) : i - 1;
+    auto valid = [&](int k) { return k >= 0 && (per || k < nx - 1); };
+    const size_t c = (size_t)j * ld + i, cjm = (size_t)jm * ld + i;
+    R lez = hdy * (L[3 * P + c] - L[3 * P + cjm]) - (valid(i) ? hdx * L[4 * P + c] : R(0));
+    R ley = valid(i) ? hdx * L[5 * P + c] : R(0);
+    R lex = valid(i) ? hdy * (L[5 * P + cjm] - L[5 * P + c]) : R(0);
+    if (valid(im)) {
+        const size_t cim = (size_t)j * ld + im;
+        lez += hdx * L[4 * P + cim];
+        ley -= hdx * L[5 * P + cim];
+    }
+    L[0 * P + c] += lex;
+    L[1 * P + c] += ley;
+    L[2 * P + c] += lez;
+}
+
+// forward: Ex(j,i) += dtdy (Bz(j,i) - Bz(j-1,i)) - dt Jx;  Ey(j,i) -= dtdx (Bz(j,i) - Bz(j,i-1)) + dt Jy;
+//          Ez(j,i) += dtdx (By(j,i) - By(j,i-1)) - dtdy (Bx(j,i) - Bx(j-1,i)) - dt Jz,
+// with the left boundary values byL, bzL in place of column -1 when x is open.
+// Transpose: lambda_B += C^T lambda_E, lambda_ghost, lambda_J = -dt lambda_E.
+template <typename R>
+__global__ void __launch_bounds__(256) k_adj_e_full(const AdjMesh<R> A, R dt, R dtdx, R dtdy) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    const int nx = A.nx, ny = A.ny, ld = A.ld;
+    if (i >= nx) return;
+    const bool per = A.bc_x == 1;
+    const size_t P = A.plane;
+    R *L = A.LEB;
+    const int jp = j + 1 == ny ? 0 : j + 1;
+    const int ip = i + 1 == nx ? (per ? 0 : -1) : i + 1;
+    const size_t c = (size_t)j * ld + i, cjp = (size_t)jp * ld + i;
+    const R lex = L[c], ley = L[P + c], lez = L[2 * P + c];
+    R lbz = dtdy * (lex - L[cjp]) - dtdx * ley;
+    R lby = dtdx * lez;
+    const R lbx = dtdy * (L[2 * P + cjp] - lez);
+    if (ip >= 0) {
+        const size_t cip = (size_t)j * ld + ip;
+        lbz += dtdx * L[P + cip];
+        lby -= dtdx * L[2 * P + cip];
+    }
+    L[3 * P + c] += lbx;
+    L[4 * P + c] += lby;
+    L[5 * P + c] += lbz;
+    A.LJ[c] = -dt * lex;
+    A.LJ[P + c] = -dt * ley;
+    A.LJ[2 * P + c] = -dt * lez;
+    if (i == 0 && !per) {
+        A.Lbnd[j] = -dtdx * lez;       // By(-1/2)
+        A.Lbnd[ny + j] = dtdx * ley;   // Bz(-1/2)
+    }
+}
+
+// forward (open x): byL = (2 Ez(0) - (1-r) By(0) - q (Bx(j,0) - Bx(j-1,0)) - 4 a0 phz prof_j) / (1+r)
+//                   bzL = (4 a0 phy prof'_j - 2 Ey(0) - (1-r) Bz(0)) / (1+r)
+//                   By(nx-1) = (-2 Ez(nx-1) - (1-r) By(nx-2) + q (Bx(j,nx-1) - Bx(j-1,nx-1))) / (1+r)
+//                   Bz(nx-1) = (2 Ey(nx-1) - (1-r) Bz(nx-2)) / (1+r)
+// (assignments: the adjoints of the overwritten values are consumed).
+template <typename R>
+__global__ void k_adj_boundary(const AdjMesh<R> A, const double *prof, double phz, double phy, double r, double q,
+                               double *dl_da0) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ny = A.ny, nx = A.nx, ld = A.ld;
+    double acc = 0.0;
+    if (j < ny) {
+        const size_t P = A.plane;
+        R *L = A.LEB;
+        const int jm = j == 0 ? ny - 1 : j - 1;
+        const double ir = 1.0 / (1.0 + r), mr = 1.0 - r;
+        const size_t c0 = (size_t)j * ld, cm0 = (size_t)jm * ld;
+        const double lyl = A.Lbnd[j], lzl = A.Lbnd[ny + j];
+        L[2 * P + c0] += (R)(2.0 * ir * lyl);
+        L[4 * P + c0] += (R)(-mr * ir * lyl);
+        atomicAdd(&L[3 * P + c0], (R)(-q * ir * lyl));
+        atomicAdd(&L[3 * P + cm0], (R)(q * ir * lyl));
+        L[1 * P + c0] += (R)(-2.0 * ir * lzl);
+        L[5 * P + c0] += (R)(-mr * ir * lzl);
+        acc = (-4.0 * phz * prof[j] * lyl + 4.0 * phy * prof[ny + j] * lzl) * ir;
+        A.Lbnd[j] = R(0);
+        A.Lbnd[ny + j] = R(0);
+        const size_t cl = c0 + nx - 1, cml = cm0 + nx - 1;
+        const double lyr = L[4 * P + cl], lzr = L[5 * P + cl];
+        L[4 * P + cl] = R(0);
+        L[5 * P + cl] = R(0);
+        L[2 * P + cl] += (R)(-2.0 * ir * lyr);
+        atomicAdd(&L[4 * P + cl - 1], (R)(-mr * ir * lyr));
+        atomicAdd(&L[3 * P + cl], (R)(q * ir * lyr));
+        atomicAdd(&L[3 * P + cml], (R)(-q * ir * lyr));
+        L[1 * P + cl] += (R)(2.0 * ir * lzr);
+        atomicAdd(&L[5 * P + cl - 1], (R)(-mr * ir * lzr));
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(dl_da0, acc);
+}
+
+// ---------------------------------------------------------------------------
+// particles
+// ---------------------------------------------------------------------------
+// wrapped global node index (periodic y, and x when periodic); -1 outside
+template <typename R>
+__device__ __forceinline__ long long node(const AdjMesh<R> &A, int x, int y) {
+    if (A.bc_x == 1) x = x < 0 ? x + A.nx : (x >= A.nx ? x - A.nx : x);
+    y = y < 0 ? y + A.ny : (y >= A.ny ? y - A.ny : y);
+    if (x < 0 || x >= A.nx || y < 0 || y >= A.ny) return -1;
+    return (long long)y * A.ld + x;
+}
+
+// field values of the stored state for the forward gather
+template <typename R>
+struct StoredMesh {
+    const AdjMesh<R> *A;
+    const R *EB;
+    __device__ __forceinline__ R f(int c, int x, int y) const {
+        const long long k = node(*A, x, y);
+        return k < 0 ? R(0) : EB[c * A->plane + k];
+    }
+};
+
+// <lambda_J, J> of one deposit, as a dual number
+template <typename R, typename D>
+struct JDot {
+    const AdjMesh<R> *A;
+    D *acc;
+    __device__ __forceinline__ void j(int c, int x, int y, const D &v) const {
+        const long long k = node(*A, x, y);
+        if (k >= 0) *acc += v * A->LJ[c * A->plane + k];
+    }
+};
+
+// transpose of gather_eb: lambda of each staggered node += weight x lambda of
+// the gathered value (the weights and nodes of gather_eb, written out)
+template <typename R>
+__device__ __forceinline__ void gather_transpose(const AdjMesh<R> &A, int ix, int iy, R ox, R oy, const R lE[3],
+                                                 const R lB[3]) {
+    const R half = R(0.5), one = R(1);
+    const R xn0 = one - ox, xn1 = ox, yn0 = one - oy, yn1 = oy;
+    const bool rx = ox >= half, ry = oy >= half;
+    const int hx = rx ? ix : ix - 1, hy = ry ? iy : iy - 1;
+    const R ohx = rx ? ox - half : ox + half, ohy = ry ? oy - half : oy + half;
+    const R xh0 = one - ohx, xh1 = ohx, yh0 = one - ohy, yh1 = ohy;
+    auto bil = [&](int c, int x, int y, R a0, R a1, R b0, R b1, R lam) {
+        if (lam == R(0)) return;
+        const R w[4] = {b0 * a0, b0 * a1, b1 * a0, b1 * a1};
+        const int dx[4] = {0, 1, 0, 1}, dy[4] = {0, 0, 1, 1};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const long long n = node(A, x + dx[k], y + dy[k]);
+            if (n >= 0) atomicAdd(&A.LEB[c * A.plane + n], w[k] * lam);
+        }
+    };
+    bil(0, hx, iy, xh0, xh1, yn0, yn1, lE[0]);
+    bil(1, ix, hy, xn0, xn1, yh0, yh1, lE[1]);
+    bil(2, ix, iy, xn0, xn1, yn0, yn1, lE[2]);
+    bil(3, ix, hy, xn0, xn1, yh0, yh1, lB[0]);
+    bil(4, hx, iy, xh0, xh1, yn0, yn1, lB[1]);
+    bil(5, hx, hy, xh0, xh1, yh0, yh1, lB[2]);
+}
+
+// One adjoint particle step.  In: the particle state at step n (stored), the
+// fields E^n, B^n (stored), lambda_J of the step, and the particle lambdas of
+// step n+1; out: the particle lambdas of step n, lambda_w accumulated, the
+// gather's transpose added to the mesh lambdas.
+template <typename R>
+__global__ void __launch_bounds__(128) k_adj_particles(const AdjMesh<R> A, const AdjParticles<R> S) {
+    using D5 = Dual<R, 5>;
+    using D3 = Dual<R, 3>;
+    using D2 = Dual<R, 2>;
+    const StoredMesh<R> sm{&A, S.EB};
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < S.n; p += (long long)gridDim.x * blockDim.x) {
+        const uint32_t c = S.cell[p];
+        if (c == PIC_DEAD) continue;
+        const int ix = (int)(c & 0xFFFFu), iy = (int)(c >> 16);
+        const R ox = S.ox[p], oy = S.oy[p], w = S.w[p];
+        const R u0[3] = {S.ux[p], S.uy[p], S.uz[p]};
+        const R s0[3] = {S.sx[p], S.sy[p], S.sz[p]};
+        // forward of this step, as the split path computes it
+        R E[3], B[3];
+        gather_eb(sm, ix, iy, ox, oy, E, B);
+        R un[3] = {u0[0], u0[1], u0[2]}, sn[3] = {s0[0], s0[1], s0[2]};
+        push_spin(S.qm, S.a, A.dt, E, B, un, sn);
+        const R gi = Real<R>::rsqrt(R(1) + un[0] * un[0] + un[1] * un[1] + un[2] * un[2]);
+        int ix1 = ix, iy1 = iy;
+        R ox1 = ox, oy1 = oy;
+        advance_axis(ix1, ox1, un[0] * gi * A.dt_dx);
+        advance_axis(iy1, oy1, un[1] * gi * A.dt_dy);
+        const R vz = un[2] * gi;
+        // lambdas of step n+1 (zero for a particle removed in this step)
+        R lx1 = S.lx[p], ly1 = S.ly[p];
+        R lu[3] = {S.lux[p], S.luy[p], S.luz[p]}, ls[3] = {S.lsx[p], S.lsy[p], S.lsz[p]};
+        // a5: <lambda_J, J> as a function of (ox, oy, ox1, oy1, vz)
+        D5 acc(R(0));
+        const JDot<R, D5> jd{&A, &acc};
+        deposit_esirkepov(jd, ix, iy, D5::var(ox, 0), D5::var(oy, 1), ix1, iy1, D5::var(ox1, 2), D5::var(oy1, 3),
+                          D5(S.q * w), D5::var(vz, 4), D5(A.dx_dt), D5(A.dy_dt));
+        if (w != R(0)) S.lw[p] += acc.v / w;
+        lx1 += acc.d[2];
+        ly1 += acc.d[3];
+        // a4: ox1 = ox + dt/dx ux gi, oy1 = oy + dt/dy uy gi, vz = uz gi
+        const R cv[3] = {lx1 * A.dt_dx, ly1 * A.dt_dy, acc.d[4]};
+        const R cu = cv[0] * un[0] + cv[1] * un[1] + cv[2] * un[2];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) lu[k] += gi * cv[k] - un[k] * cu * gi * gi * gi;
+        R lox = lx1 + acc.d[0], loy = ly1 + acc.d[1];
+        // a2 + a3: vector-Jacobian product of push_spin over (u, s, E, B), three inputs a pass
+        R lin[12];
+#pragma unroll
+        for (int pass = 0; pass < 4; ++pass) {
+            D3 Ed[3], Bd[3], ud[3], sd[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                ud[k] = pass == 0 ? D3::var(u0[k], k) : D3(u0[k]);
+                sd[k] = pass == 1 ? D3::var(s0[k], k) : D3(s0[k]);
+                Ed[k] = pass == 2 ? D3::var(E[k], k) : D3(E[k]);
+                Bd[k] = pass == 3 ? D3::var(B[k], k) : D3(B[k]);
+            }
+            push_spin(D3(S.qm), D3(S.a), D3(A.dt), Ed, Bd, ud, sd);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                R v = R(0);
+#pragma unroll
+                for (int o = 0; o < 3; ++o) v += lu[o] * ud[o].d[k] + ls[o] * sd[o].d[k];
+                lin[pass * 3 + k] = v;
+            }
+        }
+        // a1: the gathered values depend on the mesh (transpose into lambda_EB)
+        // and on the offsets (dual gather)
+        gather_transpose(A, ix, iy, ox, oy, lin + 6, lin + 9);
+        {
+            D2 Eg[3], Bg[3];
+            gather_eb(sm, ix, iy, D2::var(ox, 0), D2::var(oy, 1), Eg, Bg);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                lox += lin[6 + k] * Eg[k].d[0] + lin[9 + k] * Bg[k].d[0];
+                loy += lin[6 + k] * Eg[k].d[1] + lin[9 + k] * Bg[k].d[1];
+            }
+        }
+        S.lx[p] = lox;
+        S.ly[p] = loy;
+        S.lux[p] = lin[0];
+        S.luy[p] = lin[1];
+        S.luz[p] = lin[2];
+        S.lsx[p] = lin[3];
+        S.lsy[p] = lin[4];
+        S.lsz[p] = lin[5];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// loss: L = sum a_i s_i / sum a_i over the live particles of a species, with
+// a_i = w_i e_i sig((e_i - ec)/de), e_i the kinetic energy [MeV] and s_i the
+// chosen spin component (the energy-weighted polarization above ec)
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(256) k_loss_sums(const AdjParticles<R> S, LossParams L, double *sums) {
+    double a = 0.0, as = 0.0;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < S.n; p += (long long)gridDim.x * blockDim.x) {
+        if (S.cell[p] == PIC_DEAD) continue;
+        const double ux = S.ux[p], uy = S.uy[p], uz = S.uz[p];
+        const double u2 = ux * ux + uy * uy + uz * uz;
+        const double e = L.m_mev * u2 / (1.0 + sqrt(1.0 + u2));
+        const double sg = 1.0 / (1.0 + exp(-(e - L.ec) / L.de));
+        const double ai = (double)S.w[p] * e * sg;
+        const double sp = L.axis == 0 ? S.sx[p] : (L.axis == 1 ? S.sy[p] : S.sz[p]);
+        a += ai;
+        as += ai * sp;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xFFFFFFFFu, a, o);
+        as += __shfl_down_sync(0xFFFFFFFFu, as, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(sums, a);
+        atomicAdd(sums + 1, as);
+    }
+}
+
+// lambdas of the final state: dL/du, dL/ds, dL/dw (positions: zero)
+template <typename R>
+__global__ void __launch_bounds__(256) k_loss_grad(const AdjParticles<R> S, LossParams L, const double *sums) {
+    const double A = sums[0], Lv = A > 0 ? sums[1] / A : 0.0;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < S.n; p += (long long)gridDim.x * blockDim.x) {
+        S.lx[p] = R(0);
+        S.ly[p] = R(0);
+        S.lux[p] = S.luy[p] = S.luz[p] = R(0);
+        S.lsx[p] = S.lsy[p] = S.lsz[p] = R(0);
+        S.lw[p] = R(0);
+        if (S.cell[p] == PIC_DEAD || !(A > 0)) continue;
+        const double ux = S.ux[p], uy = S.uy[p], uz = S.uz[p];
+        const double u2 = ux * ux + uy * uy + uz * uz;
+        const double g = sqrt(1.0 + u2);
+        const double e = L.m_mev * u2 / (1.0 + g);
+        const double sg = 1.0 / (1.0 + exp(-(e - L.ec) / L.de));
+        const double w = S.w[p];
+        const double sp = L.axis == 0 ? S.sx[p] : (L.axis == 1 ? S.sy[p] : S.sz[p]);
+        const double dla = (sp - Lv) / A;                    // dL/da_i
+        const double dade = w * (sg + e * sg * (1.0 - sg) / L.de);
+        const double k = dla * dade * L.m_mev / g;          // dL/du = k u  (de/du = m u / g)
+        S.lux[p] = (R)(k * ux);
+        S.luy[p] = (R)(k * uy);
+        S.luz[p] = (R)(k * uz);
+        const double ai = w * e * sg;
+        (L.axis == 0 ? S.lsx : (L.axis == 1 ? S.lsy : S.lsz))[p] = (R)(ai / A);
+        S.lw[p] = (R)(dla * e * sg);
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <typename R>
+cudaError_t launch_adjoint_fields(const AdjMesh<R> &A, const double *prof, double phz, double phy, double *dl_da0,
+                                  cudaStream_t st) {
+    const dim3 blk(256), grd((A.nx + 255) / 256, A.ny);
+    const R hdx = R(0.5) * A.dt_dx, hdy = R(0.5) * A.dt_dy;
+    k_adj_b_half<R><<<grd, blk, 0, st>>>(A, hdx, hdy);
+    k_adj_e_full<R><<<grd, blk, 0, st>>>(A, A.dt, A.dt_dx, A.dt_dy);
+    if (A.bc_x == 0)
+        k_adj_boundary<R><<<(A.ny + 127) / 128, 128, 0, st>>>(A, prof, phz, phy, A.r, A.q, dl_da0);
+    k_adj_b_half<R><<<grd, blk, 0, st>>>(A, hdx, hdy);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_adjoint_particles(const AdjMesh<R> &A, const AdjParticles<R> &S, cudaStream_t st) {
+    if (S.n == 0) return cudaSuccess;
+    long long b = (S.n + 127) / 128;
+    if (b > 152 * 32) b = 152 * 32;
+    k_adj_particles<R><<<(int)b, 128, 0, st>>>(A, S);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_loss(const AdjParticles<R> &S, const LossParams &L, double *sums, bool grad, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(sums, 0, 2 * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    const int b = S.n > 0 ? (int)std::min<long long>((S.n + 255) / 256, 152 * 8) : 1;
+    k_loss_sums<R><<<b, 256, 0, st>>>(S, L, sums);
+    if (grad) k_loss_grad<R><<<b, 256, 0, st>>>(S, L, sums);
+    return cudaGetLastError();
+}
+
+#define PIC_ADJ_INST(R)                                                                                     \
+    template cudaError_t launch_adjoint_fields<R>(const AdjMesh<R> &, const double *, double, double, double *, \
+                                                  cudaStream_t);                                          \
+    template cudaError_t launch_adjoint_particles<R>(const AdjMesh<R> &, const AdjParticles<R> &, cudaStream_t); \
+    template cudaError_t launch_loss<R>(const AdjParticles<R> &, const LossParams &, double *, bool, cudaStream_t);
+PIC_ADJ_INST(float)
+PIC_ADJ_INST(double)
+#undef PIC_ADJ_INST

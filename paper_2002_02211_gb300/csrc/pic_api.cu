@@ -66,6 +66,11 @@ struct Ctx {
     bool pending_deposit = false;
     long long step = 0;
     long long window = 0;         // cells the co-moving window has moved
+    // adjoint results: per species the lambdas of the initial state
+    // (lx ly lux luy luz lsx lsy lsz lw), the initial cells, and the slot counts
+    void *adj_lam[PIC_MAX_SPECIES][9] = {};
+    uint32_t *adj_cell0[PIC_MAX_SPECIES] = {};
+    long long adj_n[PIC_MAX_SPECIES] = {};
     bool has_background = false;  // pic_capture_background was called
     int since_sort = 0;
     long long launches = 0;  // kernels launched by this context
@@ -347,10 +352,12 @@ pic_status_t read_count(Ctx *c, int s, cudaStream_t st, int32_t *n) {
 }
 
 // Host particles p of species s into slots [base, base + p->n) of the current
-// buffer (widened on the device with precision 64), cells packed and range
-// checked; the slot count becomes base + p->n.  Synchronous.
-pic_status_t upload_particles(Ctx *c, int s, const pic_particles_t *p, int64_t base, cudaStream_t st) {
-    const float *src[9] = {p->ox, p->oy, p->ux, p->uy, p->uz, p->sx, p->sy, p->sz, p->w};
+// buffer (float or double host arrays; converted on the device when the
+// context's precision differs), cells packed and range checked; the slot
+// count becomes base + p->n.  Synchronous.
+template <typename HostT, typename PT>
+pic_status_t upload_particles(Ctx *c, int s, const PT *p, int64_t base, cudaStream_t st) {
+    const HostT *src[9] = {p->ox, p->oy, p->ux, p->uy, p->uz, p->sx, p->sy, p->sz, p->w};
     const bool d3 = c->dim == 3;
     if (p->n > 0) {
         if (!p->ix || !p->iy || !p->id || (d3 && (!p->iz || !p->oz))) return fail(c, PIC_ERR_ARG, "null particle array");
@@ -367,13 +374,16 @@ pic_status_t upload_particles(Ctx *c, int s, const pic_particles_t *p, int64_t b
         CK(cudaMemcpyAsync(diy, p->iy, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         if (d3) CK(cudaMemcpyAsync(diz, p->iz, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         for (int k = 0; k < (d3 ? 10 : 9); ++k) {
-            const float *from = k < 9 ? src[k] : p->oz;
+            const HostT *from = k < 9 ? src[k] : p->oz;
             char *to = static_cast<char *>(k < 9 ? B.f[k] : B.oz) + base * rb;
-            if (rb == 4) {
-                CK(cudaMemcpyAsync(to, from, n * sizeof(float), cudaMemcpyHostToDevice, st));
-            } else {  // FP64 instantiation: widen on the device
-                CK(cudaMemcpyAsync(c->stage, from, n * sizeof(float), cudaMemcpyHostToDevice, st));
-                CK(launch_convert<float, double>(static_cast<float *>(c->stage), reinterpret_cast<double *>(to), n, st));
+            if (rb == sizeof(HostT)) {
+                CK(cudaMemcpyAsync(to, from, n * sizeof(HostT), cudaMemcpyHostToDevice, st));
+            } else {  // convert on the device through the staging buffer
+                CK(cudaMemcpyAsync(c->stage, from, n * sizeof(HostT), cudaMemcpyHostToDevice, st));
+                if (rb == 8)
+                    CK(launch_convert<float, double>(static_cast<float *>(c->stage), reinterpret_cast<double *>(to), n, st));
+                else
+                    CK(launch_convert<double, float>(static_cast<double *>(c->stage), reinterpret_cast<float *>(to), n, st));
                 c->launches += 1;
             }
         }
@@ -609,6 +619,8 @@ void pic_destroy(void *ctx) {
         cudaFree(c->tile_start[s]);
         cudaFree(c->cell_old[s]);
         for (int k = 0; k < 3; ++k) cudaFree(c->old_f[s][k]);
+        for (int k = 0; k < 9; ++k) cudaFree(c->adj_lam[s][k]);
+        cudaFree(c->adj_cell0[s]);
     }
     cudaFree(c->tile_count);
     cudaFree(c->cell_count);
@@ -645,7 +657,25 @@ pic_status_t pic_set_particles(void *ctx, int s, const pic_particles_t *p, void 
     if (p->n < 0) return fail(c, PIC_ERR_ARG, "negative particle count");
     if (p->n > c->cfg.sp[s].capacity) return fail(c, PIC_ERR_OVERFLOW, "more particles than capacity");
     cudaStream_t st = S(stream);
-    pic_status_t r = upload_particles(c, s, p, 0, st);
+    pic_status_t r = upload_particles<float>(c, s, p, 0, st);
+    if (r != PIC_OK) return r;
+    c->pending_deposit = false;
+    r = sort_species(c, s, st);
+    if (r != PIC_OK) return r;
+    c->since_sort = 0;
+    CK(cudaStreamSynchronize(st));
+    return PIC_OK;
+}
+
+pic_status_t pic_set_particles_f64(void *ctx, int s, const pic_particles_f64_t *p, void *stream) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
+    if (s < 0 || s >= c->cfg.nspecies || !p) return fail(c, PIC_ERR_ARG, "bad species or particles");
+    if (p->n < 0) return fail(c, PIC_ERR_ARG, "negative particle count");
+    if (p->n > c->cfg.sp[s].capacity) return fail(c, PIC_ERR_OVERFLOW, "more particles than capacity");
+    if (p->n > 0 && (int64_t)c->stage_elems < p->n) return fail(c, PIC_ERR_ARG, "too many particles");
+    cudaStream_t st = S(stream);
+    pic_status_t r = upload_particles<double>(c, s, p, 0, st);
     if (r != PIC_OK) return r;
     c->pending_deposit = false;
     r = sort_species(c, s, st);
@@ -1126,7 +1156,7 @@ pic_status_t pic_shift_window(void *ctx, int ncells, const pic_particles_t *inje
     for (int s = 0; s < c->cfg.nspecies; ++s) {
         if (!inject || inject[s].n == 0) continue;
         const int64_t base = cur[s];  // the slot count (removed particles stay until the sort)
-        pic_status_t r = upload_particles(c, s, &inject[s], base, st);
+        pic_status_t r = upload_particles<float>(c, s, &inject[s], base, st);
         if (r != PIC_OK) return r;
         if (c->has_background) {
             // the injected plasma brings its immobile ions: rho_bg -= rho(injected)
@@ -1592,6 +1622,325 @@ pic_status_t pic_batch_launch_count(void *batch, int64_t *count) {
 const char *pic_batch_last_error(void *batch) {
     Batch *b = static_cast<Batch *>(batch);
     return b ? b->last_error.c_str() : g_create_error.c_str();
+}
+
+}  // extern "C"
+
+
+// ===========================================================================
+// Adjoint of the 2D3V step: the gradient of a loss on the final particle
+// state (the energy-weighted polarization above a cut, the beam quality the
+// paper's runs look at) with respect to the initial particle state, the
+// particle weights and the laser amplitude.  The forward pass runs the split
+// kernels without tile sorts (slots keep their particles) and keeps a
+// checkpoint every K steps; the backward pass recomputes each stretch of K
+// steps from its checkpoint, storing every step's state, and runs the adjoint
+// kernels back through it.
+// ===========================================================================
+namespace {
+
+// one stored state: every species' cell words and 8 reals per slot
+// (ox oy ux uy uz sx sy sz), then E, B
+struct Snap {
+    size_t bytes = 0;
+    size_t off_cell[PIC_MAX_SPECIES] = {}, off_real[PIC_MAX_SPECIES] = {}, off_eb = 0;
+};
+
+Snap snap_layout(Ctx *c, const long long *n) {
+    Snap L;
+    size_t o = 0;
+    auto al = [](size_t v) { return (v + 255) / 256 * 256; };
+    for (int s = 0; s < c->cfg.nspecies; ++s) {
+        L.off_cell[s] = o;
+        o = al(o + (size_t)n[s] * sizeof(uint32_t));
+        L.off_real[s] = o;
+        o = al(o + (size_t)n[s] * 8 * c->rb);
+    }
+    L.off_eb = o;
+    o = al(o + 6 * c->plane * c->rb);
+    L.bytes = o;
+    return L;
+}
+
+static const int kSnapField[8] = {0, 1, 2, 3, 4, 5, 6, 7};  // SpeciesBuf::f index of each stored real
+
+pic_status_t snap_copy(Ctx *c, const Snap &L, const long long *n, char *snap, bool save, cudaStream_t st) {
+    for (int s = 0; s < c->cfg.nspecies; ++s) {
+        SpeciesBuf &B = c->buf[s][c->cur[s]];
+        char *cs = snap + L.off_cell[s];
+        if (n[s] == 0) continue;
+        if (save) CK(cudaMemcpyAsync(cs, B.cell, n[s] * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+        else CK(cudaMemcpyAsync(B.cell, cs, n[s] * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+        for (int k = 0; k < 8; ++k) {
+            char *r = snap + L.off_real[s] + (size_t)k * n[s] * c->rb;
+            if (save) CK(cudaMemcpyAsync(r, B.f[kSnapField[k]], n[s] * c->rb, cudaMemcpyDeviceToDevice, st));
+            else CK(cudaMemcpyAsync(B.f[kSnapField[k]], r, n[s] * c->rb, cudaMemcpyDeviceToDevice, st));
+        }
+    }
+    char *eb = snap + L.off_eb;
+    if (save) CK(cudaMemcpyAsync(eb, c->EB, 6 * c->plane * c->rb, cudaMemcpyDeviceToDevice, st));
+    else CK(cudaMemcpyAsync(c->EB, eb, 6 * c->plane * c->rb, cudaMemcpyDeviceToDevice, st));
+    return PIC_OK;
+}
+
+template <typename R>
+AdjParticles<R> adj_particles(Ctx *c, int s, const Snap &L, const long long *n, const char *snap) {
+    AdjParticles<R> P{};
+    P.n = n[s];
+    P.cell = reinterpret_cast<const uint32_t *>(snap + L.off_cell[s]);
+    const R *r = reinterpret_cast<const R *>(snap + L.off_real[s]);
+    P.ox = r;
+    P.oy = r + n[s];
+    P.ux = r + 2 * n[s];
+    P.uy = r + 3 * n[s];
+    P.uz = r + 4 * n[s];
+    P.sx = r + 5 * n[s];
+    P.sy = r + 6 * n[s];
+    P.sz = r + 7 * n[s];
+    P.w = static_cast<const R *>(c->buf[s][c->cur[s]].f[8]);
+    P.EB = reinterpret_cast<const R *>(snap + L.off_eb);
+    const pic_species_t &sp = c->cfg.sp[s];
+    P.qm = (R)(sp.q / sp.m);
+    P.q = (R)sp.q;
+    P.a = (R)sp.a;
+    R **lam[9] = {&P.lx, &P.ly, &P.lux, &P.luy, &P.luz, &P.lsx, &P.lsy, &P.lsz, &P.lw};
+    for (int k = 0; k < 9; ++k) *lam[k] = static_cast<R *>(c->adj_lam[s][k]);
+    return P;
+}
+
+template <typename R>
+AdjMesh<R> adj_mesh(Ctx *c, void *LEB, void *LJ, void *Lbnd) {
+    const MeshParams<R> m = mesh<R>(c);
+    AdjMesh<R> A{};
+    A.nx = m.nx;
+    A.ny = m.ny;
+    A.ld = m.ld;
+    A.bc_x = m.bc_x;
+    A.plane = m.plane;
+    A.dt = m.dt;
+    A.dt_dx = m.dt_dx;
+    A.dt_dy = m.dt_dy;
+    A.dx_dt = m.dx_dt;
+    A.dy_dt = m.dy_dt;
+    A.r = c->dt / c->dx;
+    A.q = c->dt / c->dy;
+    A.LEB = static_cast<R *>(LEB);
+    A.LJ = static_cast<R *>(LJ);
+    A.Lbnd = static_cast<R *>(Lbnd);
+    return A;
+}
+
+pic_status_t forward_split_step(Ctx *c, cudaStream_t st) {
+    pic_status_t r = pic_gather_push_spin(c, st);
+    if (r == PIC_OK) r = pic_deposit(c, st);
+    if (r == PIC_OK) r = pic_field_update(c, st);
+    return r;
+}
+
+pic_status_t check_loss(Ctx *c, const pic_loss_t *loss) {
+    if (!loss) return fail(c, PIC_ERR_ARG, "null loss");
+    if (loss->species < 0 || loss->species >= c->cfg.nspecies) return fail(c, PIC_ERR_ARG, "bad loss species");
+    if (loss->axis < 0 || loss->axis > 2) return fail(c, PIC_ERR_ARG, "loss axis must be 0, 1 or 2");
+    if (!(loss->e_width_mev > 0)) return fail(c, PIC_ERR_ARG, "loss width must be > 0");
+    return PIC_OK;
+}
+
+LossParams loss_params(Ctx *c, const pic_loss_t *loss) {
+    return LossParams{c->cfg.sp[loss->species].m * kMec2Mev, loss->e_cut_mev, loss->e_width_mev, loss->axis};
+}
+
+}  // namespace
+
+extern "C" {
+
+pic_status_t pic_loss(void *ctx, const pic_loss_t *loss, double *value, void *stream) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
+    if (!value) return fail(c, PIC_ERR_ARG, "null output");
+    pic_status_t r = check_loss(c, loss);
+    if (r != PIC_OK) return r;
+    if (c->pending_deposit) return fail(c, PIC_ERR_STATE, "a move is waiting for pic_deposit");
+    cudaStream_t st = S(stream);
+    const int s = loss->species;
+    int32_t n = 0;
+    if ((r = read_count(c, s, st, &n)) != PIC_OK) return r;
+    CK(with_real(c, [&](auto z) {
+        using T = decltype(z);
+        AdjParticles<T> P{};
+        const DevSpecies<T> d = dev_species<T>(c, s, c->cur[s]);
+        P.n = n;
+        P.cell = d.cell;
+        P.ox = d.ox; P.oy = d.oy; P.ux = d.ux; P.uy = d.uy; P.uz = d.uz; P.sx = d.sx; P.sy = d.sy; P.sz = d.sz;
+        P.w = d.w;
+        return launch_loss<T>(P, loss_params(c, loss), c->result, false, st);
+    }));
+    double h[2];
+    CK(cudaMemcpyAsync(h, c->result, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *value = h[0] > 0 ? h[1] / h[0] : 0.0;
+    return check_flags(c, st);
+}
+
+pic_status_t pic_adjoint(void *ctx, int nsteps, int checkpoint_every, const pic_loss_t *loss, double *loss_value,
+                         double *dloss_da0, void *stream) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
+    if (c->dim != 2) return fail(c, PIC_ERR_ARG, "the adjoint is built for 2D3V");
+    if (nsteps < 1 || checkpoint_every < 1) return fail(c, PIC_ERR_ARG, "need nsteps >= 1 and checkpoint_every >= 1");
+    pic_status_t r = check_loss(c, loss);
+    if (r != PIC_OK) return r;
+    if (c->pending_deposit) return fail(c, PIC_ERR_STATE, "a move is waiting for pic_deposit");
+    cudaStream_t st = S(stream);
+    const int nsp = c->cfg.nspecies, K = checkpoint_every;
+    long long n[PIC_MAX_SPECIES] = {};
+    for (int s = 0; s < nsp; ++s) {
+        int32_t v = 0;
+        if ((r = read_count(c, s, st, &v)) != PIC_OK) return r;
+        n[s] = v;
+    }
+    const Snap L = snap_layout(c, n);
+    const int nck = (nsteps + K - 1) / K;
+    const size_t nsnap = (size_t)nck + (size_t)K + 1;  // checkpoints, one stretch, the final state
+    char *store = nullptr;
+    void *LEB = nullptr, *LJ = nullptr, *Lbnd = nullptr;
+    double *sums = nullptr, *dla0 = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(store);
+        cudaFree(LEB);
+        cudaFree(LJ);
+        cudaFree(Lbnd);
+        cudaFree(sums);
+        cudaFree(dla0);
+    };
+#define ACK(...)                                                                                       \
+    do {                                                                                               \
+        cudaError_t e_ = (__VA_ARGS__);                                                                \
+        if (e_ != cudaSuccess) {                                                                       \
+            cleanup();                                                                                 \
+            return fail(c, PIC_ERR_CUDA, std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_));   \
+        }                                                                                              \
+    } while (0)
+#define ARET(expr)                                                                                     \
+    do {                                                                                               \
+        pic_status_t r_ = (expr);                                                                      \
+        if (r_ != PIC_OK) {                                                                            \
+            cleanup();                                                                                 \
+            return r_;                                                                                 \
+        }                                                                                              \
+    } while (0)
+    ACK(cudaMalloc(&store, nsnap * L.bytes));
+    ACK(cudaMalloc(&LEB, 6 * c->plane * c->rb));
+    ACK(cudaMalloc(&LJ, 3 * c->plane * c->rb));
+    ACK(cudaMalloc(&Lbnd, 2 * (size_t)c->cfg.ny * c->rb));
+    ACK(cudaMalloc(&sums, 2 * sizeof(double)));
+    ACK(cudaMalloc(&dla0, sizeof(double)));
+    for (int s = 0; s < nsp; ++s) {
+        for (int k = 0; k < 9; ++k) {
+            cudaFree(c->adj_lam[s][k]);
+            c->adj_lam[s][k] = nullptr;
+            ACK(cudaMalloc(&c->adj_lam[s][k], (size_t)n[s] * c->rb + 16));
+            ACK(cudaMemsetAsync(c->adj_lam[s][k], 0, (size_t)n[s] * c->rb + 16, st));
+        }
+        cudaFree(c->adj_cell0[s]);
+        c->adj_cell0[s] = nullptr;
+        ACK(cudaMalloc(&c->adj_cell0[s], (size_t)n[s] * sizeof(uint32_t) + 16));
+        if (n[s]) ACK(cudaMemcpyAsync(c->adj_cell0[s], c->buf[s][c->cur[s]].cell, n[s] * sizeof(uint32_t),
+                                      cudaMemcpyDeviceToDevice, st));
+        c->adj_n[s] = n[s];
+    }
+    auto snap = [&](size_t k) { return store + k * L.bytes; };
+    char *final_state = snap(nck + K);
+    const long long step0 = c->step;
+    // forward with checkpoints
+    for (int k = 0; k < nsteps; ++k) {
+        if (k % K == 0) ARET(snap_copy(c, L, n, snap(k / K), true, st));
+        ARET(forward_split_step(c, st));
+    }
+    ARET(snap_copy(c, L, n, final_state, true, st));
+    // loss and the lambdas of the final state
+    const int ls = loss->species;
+    ACK(with_real(c, [&](auto z) {
+        using T = decltype(z);
+        return launch_loss<T>(adj_particles<T>(c, ls, L, n, final_state), loss_params(c, loss), sums, true, st);
+    }));
+    double h[2];
+    ACK(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, st));
+    ACK(cudaMemsetAsync(LEB, 0, 6 * c->plane * c->rb, st));
+    ACK(cudaMemsetAsync(LJ, 0, 3 * c->plane * c->rb, st));
+    ACK(cudaMemsetAsync(Lbnd, 0, 2 * (size_t)c->cfg.ny * c->rb, st));
+    ACK(cudaMemsetAsync(dla0, 0, sizeof(double), st));
+    LaserParams unit = laser(c);
+    unit.a0 = 1.0;  // time factors per unit a0: the source is linear in a0
+    // backward, one stretch at a time
+    for (int i = nck - 1; i >= 0; --i) {
+        const int k0 = i * K, k1 = std::min(nsteps, k0 + K);
+        // restore the checkpoint and store every state of the stretch
+        ARET(snap_copy(c, L, n, snap(i), false, st));
+        c->step = step0 + k0;
+        for (int k = k0; k < k1; ++k) {
+            ARET(snap_copy(c, L, n, snap(nck + (k - k0)), true, st));
+            if (k + 1 < k1) ARET(forward_split_step(c, st));
+        }
+        for (int k = k1 - 1; k >= k0; --k) {
+            const char *state = snap(nck + (k - k0));
+            double phz = 0.0, phy = 0.0;
+            laser_time_factors(unit, ((double)(step0 + k) + 0.5) * c->dt, &phz, &phy);
+            ACK(with_real(c, [&](auto z) -> cudaError_t {
+                using T = decltype(z);
+                const AdjMesh<T> A = adj_mesh<T>(c, LEB, LJ, Lbnd);
+                cudaError_t e = launch_adjoint_fields<T>(A, c->laser_prof, phz, phy, dla0, st);
+                for (int s = 0; s < nsp && e == cudaSuccess; ++s)
+                    if (c->cfg.sp[s].mobile) e = launch_adjoint_particles<T>(A, adj_particles<T>(c, s, L, n, state), st);
+                return e;
+            }));
+            c->launches += 4 + nsp;
+        }
+    }
+    // the context ends in the final forward state
+    ARET(snap_copy(c, L, n, final_state, false, st));
+    c->step = step0 + nsteps;
+    double g = 0.0;
+    ACK(cudaMemcpyAsync(&g, dla0, sizeof(double), cudaMemcpyDeviceToHost, st));
+    ACK(cudaStreamSynchronize(st));
+    cleanup();
+#undef ACK
+#undef ARET
+    if (loss_value) *loss_value = h[0] > 0 ? h[1] / h[0] : 0.0;
+    if (dloss_da0) *dloss_da0 = g;
+    return check_flags(c, st);
+}
+
+pic_status_t pic_adjoint_particle_grads(void *ctx, int s, pic_particles_f64_t *out, void *stream) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
+    if (s < 0 || s >= c->cfg.nspecies || !out) return fail(c, PIC_ERR_ARG, "bad species or output");
+    if (!c->adj_lam[s][0]) return fail(c, PIC_ERR_STATE, "no adjoint has run");
+    const long long n = c->adj_n[s];
+    if (out->n < n) return fail(c, PIC_ERR_ARG, "output arrays too small");
+    out->n = n;
+    if (!n) return PIC_OK;
+    double *dst[9] = {out->ox, out->oy, out->ux, out->uy, out->uz, out->sx, out->sy, out->sz, out->w};
+    for (int k = 0; k < 9; ++k)
+        if (!dst[k]) return fail(c, PIC_ERR_ARG, "null output array");
+    if (!out->ix || !out->iy || !out->id) return fail(c, PIC_ERR_ARG, "null output array");
+    cudaStream_t st = S(stream);
+    for (int k = 0; k < 9; ++k) {
+        if (c->rb == 8) {
+            CK(cudaMemcpyAsync(dst[k], c->adj_lam[s][k], n * sizeof(double), cudaMemcpyDeviceToHost, st));
+        } else {
+            CK(launch_convert<float, double>(static_cast<const float *>(c->adj_lam[s][k]),
+                                             static_cast<double *>(c->stage), n, st));
+            CK(cudaMemcpyAsync(dst[k], c->stage, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+        }
+    }
+    int32_t *dix = c->scratch_i32, *diy = c->scratch_i32 + c->cfg.sp[s].capacity;
+    CK(launch_unpack_cells(c->adj_cell0[s], dix, diy, (int)n, st));
+    CK(cudaMemcpyAsync(out->ix, dix, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(out->iy, diy, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(out->id, c->buf[s][c->cur[s]].id, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return PIC_OK;
 }
 
 }  // extern "C"

@@ -135,5 +135,37 @@ cudaError_t launch_gauss3(const MeshParams3<R> &m, const R *rho, const R *rho_bg
 cudaError_t launch_diag_final(const double *rows, int nrows, int nsp, double *shift, pic_moments_dev *out,
                               double *tot, cudaStream_t st);
 
+// k_adjoint.cu: discrete adjoint of the 2D3V step
+template <typename R>
+struct AdjMesh {
+    int nx, ny, ld, bc_x;
+    size_t plane;
+    R dt, dt_dx, dt_dy, dx_dt, dy_dt;
+    double r, q;              // dt/dx, dt/dy of the boundary
+    R *LEB;                   // [6][ny][ld] lambda of E, B
+    R *LJ;                    // [3][ny][ld] lambda of J (written by the E-step transpose)
+    R *Lbnd;                  // [2][ny] lambda of By(-1/2), Bz(-1/2)
+};
+template <typename R>
+struct AdjParticles {
+    long long n;              // slots
+    const uint32_t *cell;     // stored state at the step (2D3V packing)
+    const R *ox, *oy, *ux, *uy, *uz, *sx, *sy, *sz, *w;
+    const R *EB;              // stored E, B at the step
+    R qm, q, a;
+    R *lx, *ly, *lux, *luy, *luz, *lsx, *lsy, *lsz, *lw;  // lambdas, in: step n+1, out: step n
+};
+struct LossParams {
+    double m_mev, ec, de;     // species rest energy, sigmoid centre and width [MeV]
+    int axis;                 // spin component of the loss
+};
+template <typename R>
+cudaError_t launch_adjoint_fields(const AdjMesh<R> &A, const double *prof, double phz, double phy, double *dl_da0,
+                                  cudaStream_t st);
+template <typename R>
+cudaError_t launch_adjoint_particles(const AdjMesh<R> &A, const AdjParticles<R> &S, cudaStream_t st);
+template <typename R>
+cudaError_t launch_loss(const AdjParticles<R> &S, const LossParams &L, double *sums, bool grad, cudaStream_t st);
+
 // pic_api.cu: the message pic_last_error(NULL) returns
 void set_global_error(const std::string &msg);
