@@ -12,6 +12,10 @@ every species (accumulated inside the fused kernel).  Workloads:
   config3            2D3V pre-polarised hydrogen: 4096 x 1024 cells
                      (dx = lambda/32), 8 + 8 ppc electrons and protons, CP a0 = 60
   config1            2D3V 256 x 128, 4 ppc, LP a0 = 4 (small; L2 resident)
+  config5            gradient of the beam loss (energy-weighted polarization
+                     above 50 MeV) by the adjoint: 1024 x 512, 8 ppc, 64-knot
+                     density ramp, a0 = 5, --adj-steps steps with a checkpoint
+                     every --checkpoint steps; adjoint time against a forward run
   config4            parameter scan: 256 independent 2D3V runs of uneven
                      sizes (128x64 .. 1024x512), densities, a0, ppc and
                      lengths (300-1500 steps), run to completion as one batch
@@ -71,7 +75,9 @@ def parse(argv=None):
     ap.add_argument("--steps", type=int, default=600)
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["config2", "config3", "config1", "config4"], default="config2")
+    ap.add_argument("--workload", choices=["config2", "config3", "config1", "config4", "config5"], default="config2")
+    ap.add_argument("--adj-steps", type=int, default=1000, help="config5: run length of the adjoint")
+    ap.add_argument("--checkpoint", type=int, default=50, help="config5: checkpoint interval")
     ap.add_argument("--scan-runs", type=int, default=256, help="config4: runs of the scan")
     ap.add_argument("--sort-every", type=int, default=0, help="0: 32 in 2D3V, 2 in 3D3V")
     ap.add_argument("--diag-every", type=int, default=10)
@@ -89,6 +95,8 @@ def parse(argv=None):
 def workload(name, ny=0, nz=0):
     if name == "config4":  # one run of the scan stands for it where a single workload is needed
         return W.batch_scan(1)[0][0]
+    if name == "config5":
+        return W.CONFIG5
     wl = {"config1": W.CONFIG1, "config2": W.CONFIG2, "config3": W.CONFIG3}[name]
     if ny:
         wl = W.scaled(wl, ny=ny)
@@ -593,12 +601,109 @@ def main_scan(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# config5: the adjoint against forward runs
+# ---------------------------------------------------------------------------
+def main_adjoint(args):
+    import torch
+
+    import paper_2002_02211_gb300 as pic
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    init_dist(world, "nccl")
+    dev = torch.device("cuda", local)
+    wl = W.CONFIG5
+    parts = W.generate_particles(wl)
+    parts[0]["w"] = W.ramp_weights(wl, parts, W.ramp_knots()).astype(np.float32)
+    n = len(parts[0]["ix"])
+    loss = dict(species=0, axis=1, e_cut_mev=50.0, e_width_mev=5.0)
+    stream = torch.cuda.Stream(device=dev)
+    out = {}
+    clocks = ClockSampler(local)
+    clocks.start()
+    for prec in (32, 64):
+        def fresh():
+            sim = pic.Simulation(pic.config_from_workload(wl, precision=prec), stream=stream)
+            sim.set_particles(0, parts[0])
+            sim.capture_background()
+            sim.sync()
+            return sim
+
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        with fresh() as sim:            # production forward: fused kernel, tile sorts
+            ev[0].record(stream)
+            sim.step(args.adj_steps)
+            ev[1].record(stream)
+            torch.cuda.synchronize(dev)
+            t_fwd = ev[0].elapsed_time(ev[1]) * 1e-3
+        with fresh() as sim:            # the adjoint's own forward path: split kernels, no sorts
+            ev[0].record(stream)
+            for _ in range(args.adj_steps):
+                sim.gather_push_spin()
+                sim.deposit()
+                sim.field_update()
+            ev[1].record(stream)
+            torch.cuda.synchronize(dev)
+            t_split = ev[0].elapsed_time(ev[1]) * 1e-3
+        with fresh() as sim:
+            barrier(world)
+            t0 = time.perf_counter()
+            value, dla0 = sim.adjoint(args.adj_steps, args.checkpoint, **loss)
+            t_adj = time.perf_counter() - t0
+            g = sim.adjoint_particle_grads(0)
+        out[f"fp{prec}"] = {"forward_s": t_fwd, "forward_split_s": t_split, "adjoint_s": t_adj,
+                            "adjoint_over_forward": t_adj / t_fwd, "adjoint_over_split_forward": t_adj / t_split,
+                            "loss": value, "dloss_da0": dla0,
+                            "dloss_dw_abs_sum": float(np.abs(g["w"]).sum())}
+        if prec == 64:
+            # accuracy: the FP64 adjoint's dL/da0 against central differences
+            # of the same forward path, on a 150-step horizon (the run's
+            # sensitivity grows with the horizon: at 1000 steps the exact
+            # derivative of the discrete run and any finite difference part)
+            def loss_at(a0, steps):
+                cfg = pic.config_from_workload(W.scaled(wl, a0=a0), precision=64)
+                with pic.Simulation(cfg, stream=stream) as sim:
+                    sim.set_particles(0, parts[0])
+                    sim.capture_background()
+                    for _ in range(steps):
+                        sim.gather_push_spin()
+                        sim.deposit()
+                        sim.field_update()
+                    return sim.loss(**loss)
+
+            acc = {"steps": 150}
+            with fresh() as sim:
+                acc["adjoint"] = sim.adjoint(150, args.checkpoint, **loss)[1]
+            for h in (1e-4, 1e-8):
+                acc[f"fd_h{h:g}"] = (loss_at(wl.a0 + h, 150) - loss_at(wl.a0 - h, 150)) / (2 * h)
+            acc["rel_err_vs_fd_h1e-8"] = abs(acc["adjoint"] - acc["fd_h1e-08"]) / abs(acc["fd_h1e-08"])
+            acc["long_horizon_fd_h1e-4"] = (loss_at(wl.a0 + 1e-4, args.adj_steps) -
+                                            loss_at(wl.a0 - 1e-4, args.adj_steps)) / 2e-4
+            out["fp64"]["accuracy"] = acc
+    clk = clocks.stop()
+    if rank == 0:
+        r32 = out["fp32"]
+        line = {"metric": METRIC, "value": n * args.adj_steps / r32["adjoint_s"], "unit": UNIT + " (adjoint)",
+                "n_gpus": world, "steps": args.adj_steps, "warmup": 0, "ms_per_step": 1e3 * r32["adjoint_s"] / args.adj_steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": wl.name, "particles": n, "checkpoint_every": args.checkpoint,
+                           "loss": loss, "parallelism": f"replicas x{world}"},
+                "adjoint": out, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def main(argv=None):
     args = parse(argv)
     if args.impl == "reference":
         main_reference(args)
     elif args.workload == "config4":
         main_scan(args)
+    elif args.workload == "config5":
+        main_adjoint(args)
     else:
         main_ours(args)
 

@@ -26,7 +26,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-__all__ = ["Species", "Workload", "CONFIG1", "CONFIG2", "CONFIG3", "batch_scan", "generate_particles",
+__all__ = ["Species", "Workload", "CONFIG1", "CONFIG2", "CONFIG3", "CONFIG5", "batch_scan", "ramp_weights",
+           "generate_particles",
            "injection_particles", "random_fields", "small_case", "small_case3", "scaled"]
 
 
@@ -129,6 +130,36 @@ def batch_scan(nruns: int = 256, seed: int = 4, size_scale: float = 1.0, step_sc
                       neutralizing_background=True, seed=seed * 1000 + r)
         out.append((wl, steps))
     return out
+
+
+# 2D3V gradient study: 1024x512 cells (dx = dy = lambda/16), 8 ppc electrons
+# whose density follows a 64-knot piecewise-linear ramp (ramp_weights), LP
+# laser a0 = 5, spins +y; 1000 steps, checkpoint every 50 (the run length and
+# interval belong to the adjoint call).
+CONFIG5 = Workload(
+    name="2d3v-1024x512-ppc8-ramp64-lp-a0_5",
+    nx=1024, ny=512, dx_lambda=1 / 16, dy_lambda=1 / 16, cfl=0.95, steps=1000,
+    species=(Species("electron", n0=0.01, ppc=8, u_th=1e-3, s0=(0.0, 1.0, 0.0), **ELECTRON),),
+    a0=5.0, waist_lambda=8.0, fwhm_periods=10.0, t_peak_periods=15.0, pol="lp-y",
+    bc_x="open", neutralizing_background=True, seed=5)
+
+
+def ramp_knots(nknots: int = 64, n0: float = 0.01, ramp_fraction: float = 0.25):
+    """Knot values of a smooth up-ramp to n0 over the first ramp_fraction of
+    the plasma, flat after (a smoothstep sampled at the knots)."""
+    t = np.clip(np.linspace(0.0, 1.0, nknots) / ramp_fraction, 0.0, 1.0)
+    return n0 * t * t * (3.0 - 2.0 * t)
+
+
+def ramp_weights(wl: Workload, particles, knots):
+    """Weights n(x)/ppc of the first species for a piecewise-linear density
+    with the given knot values, knots spread evenly over the plasma [2, nx-2)."""
+    d = particles[0]
+    x = d["ix"].astype(np.float64) + d["ox"].astype(np.float64)
+    xk = np.linspace(2.0, wl.nx - 2.0, len(knots))
+    i = np.clip(np.searchsorted(xk, x) - 1, 0, len(xk) - 2)
+    t = (x - xk[i]) / (xk[i + 1] - xk[i])
+    return (np.asarray(knots)[i] * (1.0 - t) + np.asarray(knots)[i + 1] * t) / wl.species[0].ppc
 
 
 def scaled(wl: Workload, **kw) -> Workload:
