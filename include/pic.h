@@ -103,8 +103,8 @@ typedef struct {
     int nz;                      /* 3D3V: cells along z, 4 <= nz <= 1020; nx, ny <= 2044 */
     double dz_lambda;            /* 3D3V: cell size along z [lambda]; then
                                     dt = cfl / sqrt(1/dx^2 + 1/dy^2 + 1/dz^2)      */
-    int tile_z;                  /* 3D3V tiles (tile_x, tile_y, tile_z): 8x8x4,
-                                    16x4x4 or 8x4x4 (0, 0, 0: 16x4x4)              */
+    int tile_z;                  /* 3D3V tiles (tile_x, tile_y, tile_z): 16x4x4,
+                                    8x8x4, 8x4x4, 16x8x4 or 32x4x4 (0, 0, 0: 16x4x4) */
 } pic_config_t;
 
 /* Host-side particle arrays of one species (n entries each).  ix, iy are cell

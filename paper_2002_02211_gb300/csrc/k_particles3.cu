@@ -47,6 +47,9 @@ struct TileConst3 {
     // field window, current window, one record stage per thread
     static constexpr size_t smem_bytes =
         (size_t)(6 * FA + 3 * WA) * sizeof(R) + kThreads3 * (sizeof(uint32_t) + kRec3 * sizeof(R));
+    // resident CTAs per SM the register budget is sized for: three while three
+    // fit in shared memory (float), else two; the FP64 instantiation takes one
+    static constexpr int minb = sizeof(R) == 8 ? 1 : (smem_bytes <= 74 * 1024 ? PIC3_MINB : 2);
 };
 
 template <typename R, int WX, int WY, int WA, int FX, int FA>
@@ -77,7 +80,7 @@ struct SmemMesh3T {
 // window is added to J at the end (16-byte vector atomics in float).
 // ---------------------------------------------------------------------------
 template <int TX, int TY, int TZ, typename R>
-__global__ void __launch_bounds__(kThreads3, sizeof(R) == 4 ? PIC3_MINB : 1)
+__global__ void __launch_bounds__(kThreads3, (TileConst3<TX, TY, TZ, R>::minb))
     k_step_fused3(const StepParams3<R> P, const __grid_constant__ CUtensorMap tmapEB) {
     using TC = TileConst3<TX, TY, TZ, R>;
     constexpr int WX = TC::WX, WY = TC::WY, WZ = TC::WZ, WA = TC::WA, FX = TC::FX, FA = TC::FA;
@@ -425,7 +428,8 @@ static cudaError_t launch_fused3_t(const StepParams3<R> &P, const CUtensorMap &t
 }
 
 bool fused3_tile_supported(int tx, int ty, int tz) {
-    return (tx == 8 && ty == 8 && tz == 4) || (tx == 16 && ty == 4 && tz == 4) || (tx == 8 && ty == 4 && tz == 4);
+    return (tx == 8 && ty == 8 && tz == 4) || (tx == 16 && ty == 4 && tz == 4) || (tx == 8 && ty == 4 && tz == 4) ||
+           (tx == 16 && ty == 8 && tz == 4) || (tx == 32 && ty == 4 && tz == 4);
 }
 
 template <typename R>
@@ -434,6 +438,8 @@ cudaError_t launch_step_fused3(const StepParams3<R> &P, const CUtensorMap &tmapE
     if (tx == 8 && ty == 8 && tz == 4) return launch_fused3_t<8, 8, 4, R>(P, tmapEB, st);
     if (tx == 16 && ty == 4 && tz == 4) return launch_fused3_t<16, 4, 4, R>(P, tmapEB, st);
     if (tx == 8 && ty == 4 && tz == 4) return launch_fused3_t<8, 4, 4, R>(P, tmapEB, st);
+    if (tx == 16 && ty == 8 && tz == 4) return launch_fused3_t<16, 8, 4, R>(P, tmapEB, st);
+    if (tx == 32 && ty == 4 && tz == 4) return launch_fused3_t<32, 4, 4, R>(P, tmapEB, st);
     return cudaErrorInvalidValue;
 }
 

@@ -61,30 +61,35 @@ __global__ void k_unpack3(const uint32_t *cell, int32_t *ix, int32_t *iy, int32_
     }
 }
 
-// sort key of a packed cell: global index of (tile, cell inside the tile)
+// sort key of a packed cell: global index of (tile, cell inside the tile).
+// Tile sizes are powers of two, so the key is shifts and masks.
+__host__ __device__ constexpr int log2i(int v) { return v <= 1 ? 0 : 1 + log2i(v >> 1); }
+
 struct Key2 {
-    TileGeom t;
+    int sx, sy, ntx, nt;  // log2 of the tile sizes, tiles along x, tiles
+    explicit Key2(const TileGeom &t) : sx(log2i(t.TX)), sy(log2i(t.TY)), ntx(t.ntx), nt(t.ntx * t.nty) {}
     __device__ __forceinline__ int operator()(uint32_t c, int &tile) const {
         const int ix = (int)(c & 0xFFFFu), iy = (int)(c >> 16);
-        const int tx = ix / t.TX, ty = iy / t.TY;
-        tile = ty * t.ntx + tx;
-        return tile * (t.TX * t.TY) + (iy - ty * t.TY) * t.TX + (ix - tx * t.TX);
+        tile = (iy >> sy) * ntx + (ix >> sx);
+        return (tile << (sx + sy)) | ((iy & ((1 << sy) - 1)) << sx) | (ix & ((1 << sx) - 1));
     }
-    int cells() const { return t.TX * t.TY; }
-    int tiles() const { return t.ntx * t.nty; }
+    int cells() const { return 1 << (sx + sy); }
+    int tiles() const { return nt; }
 };
 
 struct Key3 {
-    TileGeom3 t;
+    int sx, sy, sz, ntx, nty, nt;
+    explicit Key3(const TileGeom3 &t)
+        : sx(log2i(t.TX)), sy(log2i(t.TY)), sz(log2i(t.TZ)), ntx(t.ntx), nty(t.nty), nt(t.ntx * t.nty * t.ntz) {}
     __device__ __forceinline__ int operator()(uint32_t c, int &tile) const {
         int ix, iy, iz;
         unpack_cell3(c, ix, iy, iz);
-        const int tx = ix / t.TX, ty = iy / t.TY, tz = iz / t.TZ;
-        tile = (tz * t.nty + ty) * t.ntx + tx;
-        return tile * (t.TX * t.TY * t.TZ) + ((iz - tz * t.TZ) * t.TY + (iy - ty * t.TY)) * t.TX + (ix - tx * t.TX);
+        tile = ((iz >> sz) * nty + (iy >> sy)) * ntx + (ix >> sx);
+        const int local = ((((iz & ((1 << sz) - 1)) << sy) | (iy & ((1 << sy) - 1))) << sx) | (ix & ((1 << sx) - 1));
+        return (tile << (sx + sy + sz)) | local;
     }
-    int cells() const { return t.TX * t.TY * t.TZ; }
-    int tiles() const { return t.ntx * t.nty * t.ntz; }
+    int cells() const { return 1 << (sx + sy + sz); }
+    int tiles() const { return nt; }
 };
 
 // per-cell counts and each particle's rank inside its cell (-1: removed)
@@ -134,32 +139,93 @@ __global__ void __launch_bounds__(1024) k_layout(const int32_t *cell_count, int 
     }
 }
 
-// exclusive scan of count[0..nt) into start[0..nt], cursor = start; one CTA
-__global__ void __launch_bounds__(1024) k_scan(const int32_t *count, int nt, int32_t *start,
-                                               int32_t *cursor, int32_t *n_out) {
-    __shared__ int32_t part[1024];
-    const int per = (nt + blockDim.x - 1) / blockDim.x;
-    const int b = threadIdx.x * per, e = min(b + per, nt);
-    int32_t s = 0;
-    for (int i = b; i < e; ++i) s += count[i];
-    part[threadIdx.x] = s;
+// exclusive scan of count[0..nt) into start[0..nt] (start[nt] and *n_out =
+// the total) in three passes: each block scans a chunk of kScanChunk counts and
+// keeps its total, one block scans the totals, each block adds its offset
+constexpr int kScanThreads = 1024, kScanPer = 4, kScanChunk = kScanThreads * kScanPer;
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int *warp_tot, int &block_total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_tot[wid] = incl;
     __syncthreads();
-    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
-        const int32_t v = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
+    if (wid == 0) {
+        int w = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xFFFFFFFFu, w, o);
+            if (lane >= o) w += t;
+        }
+        warp_tot[lane] = w;  // inclusive over warps
     }
-    int32_t run = part[threadIdx.x] - s;
-    for (int i = b; i < e; ++i) {
-        start[i] = run;
-        cursor[i] = run;
-        run += count[i];
+    __syncthreads();
+    block_total = warp_tot[(blockDim.x >> 5) - 1];
+    const int base = wid ? warp_tot[wid - 1] : 0;
+    __syncthreads();
+    return base + incl - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_chunks(const int32_t *count, int nt, int32_t *start,
+                                                             int32_t *chunk_tot) {
+    __shared__ int warp_tot[32];
+    const int b0 = blockIdx.x * kScanChunk + threadIdx.x * kScanPer;
+    int v[kScanPer], s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+        v[k] = b0 + k < nt ? count[b0 + k] : 0;
+        s += v[k];
     }
-    if (threadIdx.x == blockDim.x - 1) {
-        start[nt] = part[threadIdx.x];
-        *n_out = part[threadIdx.x];
+    int tot;
+    int run = block_exclusive_scan(s, warp_tot, tot);
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+        if (b0 + k < nt) start[b0 + k] = run;
+        run += v[k];
     }
+    if (threadIdx.x == 0) chunk_tot[blockIdx.x] = tot;
+}
+
+// exclusive scan of the chunk totals (at most kScanChunk of them), one block
+__global__ void __launch_bounds__(kScanThreads) k_scan_totals(int32_t *chunk_tot, int nchunks, int32_t *start, int nt,
+                                                             int32_t *n_out) {
+    __shared__ int warp_tot[32];
+    const int b0 = threadIdx.x * kScanPer;
+    int v[kScanPer], s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+        v[k] = b0 + k < nchunks ? chunk_tot[b0 + k] : 0;
+        s += v[k];
+    }
+    int tot;
+    int run = block_exclusive_scan(s, warp_tot, tot);
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+        if (b0 + k < nchunks) chunk_tot[b0 + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == 0) {
+        start[nt] = tot;
+        *n_out = tot;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_add(int32_t *start, int nt, const int32_t *chunk_off) {
+    const int off = chunk_off[blockIdx.x];
+    const int b0 = blockIdx.x * kScanChunk;
+    for (int i = threadIdx.x; i < kScanChunk && b0 + i < nt; i += blockDim.x) start[b0 + i] += off;
+}
+
+cudaError_t scan_tiles(const int32_t *count, int nt, int32_t *start, int32_t *scratch, int32_t *n_out,
+                       cudaStream_t st) {
+    const int nchunks = (nt + kScanChunk - 1) / kScanChunk;
+    if (nchunks > kScanChunk) return cudaErrorInvalidValue;  // more than 16.7M tiles
+    k_scan_chunks<<<nchunks, kScanThreads, 0, st>>>(count, nt, start, scratch);
+    k_scan_totals<<<1, kScanThreads, 0, st>>>(scratch, nchunks, start, nt, n_out);
+    k_scan_add<<<nchunks, kScanThreads, 0, st>>>(start, nt, scratch);
+    return cudaGetLastError();
 }
 
 // the arrays a sort moves: the cell word, nf reals and the id
@@ -234,7 +300,8 @@ cudaError_t tile_sort(const SortArrays<R> &src, const SortArrays<R> &dst, const 
     const int g = grid_for(n_upper);
     k_rank<K><<<g, 256, 0, st>>>(src.cell, src.n, key, w.cell_count, w.rank);
     k_layout<<<nt, C, 0, st>>>(w.cell_count, C, w.cell_off, w.tile_R, w.tile_total);
-    k_scan<<<1, 1024, 0, st>>>(w.tile_total, nt, tile_start, w.cursor, n_tmp);
+    e = scan_tiles(w.tile_total, nt, tile_start, w.cursor, n_tmp, st);
+    if (e != cudaSuccess) return e;
     k_scatter<R, NF, K><<<g, 256, 0, st>>>(src, dst, key, w.rank, tile_start, w.tile_R, w.cell_off, C);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -260,14 +327,14 @@ template <typename R>
 cudaError_t launch_tile_sort(const DevSpecies<R> &src, const DevSpecies<R> &dst, const TileGeom &t,
                              const SortScratch &w, int32_t *tile_start, int32_t *n_tmp, int n_upper,
                              cudaStream_t st) {
-    return tile_sort<R, 9>(arrays2(src), arrays2(dst), Key2{t}, w, tile_start, n_tmp, n_upper, st);
+    return tile_sort<R, 9>(arrays2(src), arrays2(dst), Key2(t), w, tile_start, n_tmp, n_upper, st);
 }
 
 template <typename R>
 cudaError_t launch_tile_sort3(const DevSpecies3<R> &src, const DevSpecies3<R> &dst, const TileGeom3 &t,
                               const SortScratch &w, int32_t *tile_start, int32_t *n_tmp, int n_upper,
                               cudaStream_t st) {
-    return tile_sort<R, 10>(arrays3(src), arrays3(dst), Key3{t}, w, tile_start, n_tmp, n_upper, st);
+    return tile_sort<R, 10>(arrays3(src), arrays3(dst), Key3(t), w, tile_start, n_tmp, n_upper, st);
 }
 
 template cudaError_t launch_tile_sort3<float>(const DevSpecies3<float> &, const DevSpecies3<float> &,

@@ -340,7 +340,7 @@ pic_status_t sort_species(Ctx *c, int s, cudaStream_t st) {
         return launch_tile_sort<T>(dev_species<T>(c, s, from), dev_species<T>(c, s, to), c->tg, w, c->tile_start[s],
                                    c->n_dev + PIC_MAX_SPECIES, c->n_upper[s], st);
     }));
-    c->launches += 4;
+    c->launches += 6;  // rank, layout, three scan passes, scatter
     c->cur[s] = to;
     return PIC_OK;
 }
@@ -493,7 +493,7 @@ pic_status_t pic_validate_config(const pic_config_t *cfg) {
         return fail(c, PIC_ERR_ARG, "tile must be one of 8x4, 16x8, 32x8, 32x16, 64x16 cells");
     if (d3 && (cfg->tile_x != 0 || cfg->tile_y != 0 || cfg->tile_z != 0) &&
         !fused3_tile_supported(cfg->tile_x, cfg->tile_y, cfg->tile_z))
-        return fail(c, PIC_ERR_ARG, "3D3V tile must be one of 8x8x4, 16x4x4, 8x4x4 cells");
+        return fail(c, PIC_ERR_ARG, "3D3V tile must be one of 16x4x4, 8x8x4, 8x4x4, 16x8x4, 32x4x4 cells");
     if (cfg->sort_every < 0) return fail(c, PIC_ERR_ARG, "sort_every must be >= 0");
     if (cfg->precision != 0 && cfg->precision != 32 && cfg->precision != 64)
         return fail(c, PIC_ERR_ARG, "precision must be 32 or 64 (0: 32)");

@@ -82,7 +82,7 @@ void laser_profile3(const LaserParams &L, int ny, int nz, double dz, double *hos
 struct SortScratch {
     int32_t *cell_count, *cell_off;  // [ntiles * TX * TY]
     int32_t *tile_R, *tile_total;    // [ntiles]
-    int32_t *cursor;                 // [ntiles]
+    int32_t *cursor;                 // [ntiles] scan scratch
     int32_t *rank;                   // [n]
 };
 cudaError_t launch_pack_cells(const int32_t *ix, const int32_t *iy, uint32_t *cell, int n,
