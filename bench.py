@@ -56,6 +56,9 @@ UNIT = "particle-steps/s"
 # offset) 44 + 40 = 84 B; per cell the E, B window (24 B) and the current added
 # to J (12 B)
 BYTES_PER_PARTICLE = {2: 76, 3: 84}
+# the binned 3D3V layout writes each particle to the other buffer: the weight
+# and the id move with it (read id 4 B, write w and id 8 B): 96 B
+BYTES_PER_PARTICLE_BINNED = 96
 BYTES_PER_CELL = 36
 # CPU samples of the workload (the oracle is slow): the CPU-baseline leg and
 # the precision study run CPU_SAMPLE_STEPS steps of CPU_SAMPLE (10-30 s of
@@ -82,6 +85,8 @@ def parse(argv=None):
     ap.add_argument("--sort-every", type=int, default=0, help="0: 32 in 2D3V, 2 in 3D3V")
     ap.add_argument("--diag-every", type=int, default=10)
     ap.add_argument("--tile", type=int, nargs="+", default=None)
+    ap.add_argument("--bins", type=int, nargs=2, default=None, metavar=("PCT", "EXTRA"),
+                    help="3D3V binned layout: headroom percent and least spare slots per tile range")
     ap.add_argument("--ny", type=int, default=0, help="smaller ny for profiling captures")
     ap.add_argument("--nz", type=int, default=0, help="smaller nz (3D3V) for profiling captures")
     ap.add_argument("--precision", type=int, choices=[32, 64], default=32)
@@ -220,10 +225,11 @@ def kernel_source_hash(dim):
     return h.hexdigest()
 
 
-def traffic_record(dim, wl):
+def traffic_record(dim, wl, binned=False):
     """dram bytes per launch of the fused kernel from the committed ncu
-    summary, if it was taken on the current kernel source for this workload."""
-    p = os.path.join(ROOT, "profiles", KERNEL[dim][0] + ".traffic.json")
+    summary, if it was taken on the current kernel source for this workload
+    (and layout)."""
+    p = os.path.join(ROOT, "profiles", KERNEL[dim][0] + ("_binned" if binned else "") + ".traffic.json")
     try:
         with open(p) as fh:
             rec = json.load(fh)
@@ -266,7 +272,7 @@ def cpu_baseline(wl):
             "sample": f"{CPU_SAMPLE_STEPS} steps of {desc}", "seconds": round(dt, 2)}, sim
 
 
-def precision_study(pic, wl, oracle_sim):
+def precision_study(pic, wl, oracle_sim, bins=None):
     """The CPU-baseline sample run on the GPU in FP32 and FP64: largest error
     of every particle against the FP64 oracle after the same steps, and the
     error of the Eq. (4) polarization of each species."""
@@ -275,7 +281,7 @@ def precision_study(pic, wl, oracle_sim):
     pos = ("x", "y", "z") if wl.dim == 3 else ("x", "y")
     out = {}
     for prec in (32, 64):
-        with pic.Simulation(pic.config_from_workload(sample, precision=prec)) as sim:
+        with pic.Simulation(pic.config_from_workload(sample, precision=prec, bins=bins)) as sim:
             for s, d in enumerate(parts):
                 sim.set_particles(s, d)
             if sample.neutralizing_background:
@@ -344,8 +350,9 @@ def main_ours(args):
     cells = n_cells(wl)
 
     stream = torch.cuda.Stream(device=dev)
+    bins = args.bins if dim == 3 else None
     cfg = pic.config_from_workload(wl, sort_every=args.sort_every, tile=args.tile,
-                                   precision=args.precision)
+                                   precision=args.precision, bins=bins)
     sim = pic.Simulation(cfg, stream=stream)
     for s, d in enumerate(parts):
         sim.set_particles(s, d)
@@ -405,9 +412,11 @@ def main_ours(args):
 
     peak, peak_kind = measured_hbm_peak()
     wb = args.precision // 32  # algorithmic bytes scale with the real width (the cell word stays 4 B)
-    bytes_fused = (4 + (BYTES_PER_PARTICLE[dim] - 4) * wb) * n_particles + BYTES_PER_CELL * wb * cells
+    bpp = BYTES_PER_PARTICLE_BINNED if bins else BYTES_PER_PARTICLE[dim]
+    ints = 12 if bins else 4  # bytes per particle that stay 4 B wide in FP64 (cell word, id)
+    bytes_fused = (ints + (bpp - ints) * wb) * n_particles + BYTES_PER_CELL * wb * cells
     achieved = bytes_fused / t_fused / 1e9
-    tr = traffic_record(dim, wl) if args.precision == 32 else None
+    tr = traffic_record(dim, wl, bool(bins)) if args.precision == 32 else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": tr["dram_bytes_per_launch"] if tr else None,
                 "kernel": KERNEL[dim][0], "kernel_ms": t_fused * 1e3, "kernel_ms_by_tenth": fused_trend,
@@ -454,7 +463,7 @@ def main_ours(args):
     # FP64 instantiation of the same step on the same workload
     fp64 = None
     if args.precision == 32 and args.fp64_steps > 0:
-        cfg64 = pic.config_from_workload(wl, sort_every=args.sort_every, tile=args.tile, precision=64)
+        cfg64 = pic.config_from_workload(wl, sort_every=args.sort_every, tile=args.tile, precision=64, bins=bins)
         with pic.Simulation(cfg64, stream=stream) as s64:
             for s, d in enumerate(parts):
                 s64.set_particles(s, d)
@@ -481,7 +490,7 @@ def main_ours(args):
     study = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu, orc_sample = cpu_baseline(wl)
-        study = precision_study(pic, wl, orc_sample)
+        study = precision_study(pic, wl, orc_sample, bins)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -494,6 +503,8 @@ def main_ours(args):
                            "particles": n_particles,
                            "species": [s.name for s in wl.species], "sort_every": args.sort_every,
                            "diag_every": args.diag_every, "tile": args.tile or "default",
+                           "layout": ("binned (headroom %d%%, at least %d spare slots per tile)" % tuple(bins))
+                                     if bins else "compact",
                            "l2": "inputs larger than L2 (particle state %.2f GB)"
                                  % (n_particles * (8 + (dim + 7) * 4 * wb) / 1e9),
                            "parallelism": f"replicas x{world}"},

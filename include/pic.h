@@ -105,6 +105,20 @@ typedef struct {
                                     dt = cfl / sqrt(1/dx^2 + 1/dy^2 + 1/dz^2)      */
     int tile_z;                  /* 3D3V tiles (tile_x, tile_y, tile_z): 16x4x4,
                                     8x8x4, 8x4x4, 16x8x4 or 32x4x4 (0, 0, 0: 16x4x4) */
+    int bin_headroom_pct;        /* 3D3V binned layout (0: off).  Each tile owns a
+                                    slot range of count + max(bin_min_extra,
+                                    count * pct / 100) slots (rounded up to 8), and
+                                    every step writes each particle into the range
+                                    of the tile its new cell lies in, in the other
+                                    particle buffer, so particles never drift out
+                                    of their tile between sorts.  A range that
+                                    fills spills into one shared overflow range;
+                                    the tile sort (every sort_every steps)
+                                    re-sizes the ranges.  Mobile species need
+                                    capacity >= n (1 + pct / 100) + ntiles
+                                    (bin_min_extra + 7) + max(1024, n / 64);
+                                    otherwise the compact layout is kept.       */
+    int bin_min_extra;           /* spare slots each tile range keeps at least  */
 } pic_config_t;
 
 /* Host-side particle arrays of one species (n entries each).  ix, iy are cell

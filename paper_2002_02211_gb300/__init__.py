@@ -48,7 +48,8 @@ class pic_config_t(C.Structure):
                 ("t_peak_periods", C.c_double), ("nspecies", C.c_int),
                 ("sp", pic_species_t * MAX_SPECIES), ("sort_every", C.c_int), ("tile_x", C.c_int),
                 ("tile_y", C.c_int), ("precision", C.c_int), ("dim", C.c_int), ("nz", C.c_int),
-                ("dz_lambda", C.c_double), ("tile_z", C.c_int)]
+                ("dz_lambda", C.c_double), ("tile_z", C.c_int),
+                ("bin_headroom_pct", C.c_int), ("bin_min_extra", C.c_int)]
 
 
 _I32P = C.POINTER(C.c_int32)
@@ -183,11 +184,20 @@ def moments_noalloc(n, cell, ux, uy, uz, sx, sy, sz, w, mass_me, emin, emax, out
                                       C.c_void_p(int(out_dev)), _stream(stream)))
 
 
+def bin_capacity(n: int, ntiles: int, headroom_pct: int, min_extra: int) -> int:
+    """Slots a mobile species of n particles needs for the binned 3D3V layout:
+    every tile range grown by its headroom and rounded up to 8, plus the
+    overflow range."""
+    return int(n + n * headroom_pct // 100 + ntiles * (min_extra + 7) + max(1024, n // 64) + 8)
+
+
 def config_from_workload(wl, capacity_factor: float = 1.0, sort_every: int = 0, tile=None,
-                         precision: int = 32):
+                         precision: int = 32, bins=None):
     """pic_config_t for a workload description (nx, ny, dx_lambda, ..., species;
     dim, nz, dz_lambda for 3D3V).  tile: (tx, ty) in 2D3V, (tx, ty, tz) in
-    3D3V, None for the library's choice."""
+    3D3V, None for the library's choice.  bins: (headroom_pct, min_extra)
+    turns on the binned 3D3V layout, with the mobile species' capacities
+    grown to fit it."""
     three = getattr(wl, "dim", 2) == 3
     cfg = pic_config_t()
     cfg.nx, cfg.ny = wl.nx, wl.ny
@@ -212,6 +222,14 @@ def config_from_workload(wl, capacity_factor: float = 1.0, sort_every: int = 0, 
     if three:
         cfg.dim, cfg.nz, cfg.dz_lambda = 3, wl.nz, wl.dz_lambda
         cfg.tile_z = tile[2] if len(tile) > 2 else 0
+        if bins:
+            pct, extra = int(bins[0]), int(bins[1])
+            cfg.bin_headroom_pct, cfg.bin_min_extra = pct, extra
+            tx, ty, tz = (tile if tile[0] else (16, 4, 4))
+            ntiles = -(-wl.nx // tx) * -(-wl.ny // ty) * -(-wl.nz // tz)
+            for s, sp in enumerate(wl.species):
+                if sp.mobile:
+                    cfg.sp[s].capacity = bin_capacity(cfg.sp[s].capacity, ntiles, pct, extra)
     return cfg
 
 
@@ -326,7 +344,8 @@ class Simulation:
         p = pic_particles_t(n=n, **{k: _ptr(v, _I32P if v.dtype == np.int32 else _F32P)
                                     for k, v in out.items()})
         self._c(load().pic_get_particles(self.h, s, C.byref(p), self._s))
-        return out
+        # the library returns the slots it wrote (a binned layout is compacted first)
+        return {k: v[:p.n] for k, v in out.items()}
 
     def get_particles_f64(self, s):
         n = self.count(s)
@@ -334,7 +353,7 @@ class Simulation:
         p = pic_particles_f64_t(n=n, **{k: _ptr(v, _I32P if v.dtype == np.int32 else _F64P)
                                         for k, v in out.items()})
         self._c(load().pic_get_particles_f64(self.h, s, C.byref(p), self._s))
-        return out
+        return {k: v[:p.n] for k, v in out.items()}
 
     def get_fields_f64(self):
         out = {k: np.empty(self._mesh_shape, np.float64) for k in self.FIELD_KEYS}

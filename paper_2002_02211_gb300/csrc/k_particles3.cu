@@ -44,9 +44,11 @@ struct TileConst3 {
     static constexpr int FX = window3_fx<R>(TX);
     static constexpr int FA = FX * WY * WZ;     // field window [6][WZ][WY][FX]
     static constexpr int HX = window3_hx(), HY = window3_h(), HZ = window3_h();
-    // field window, current window, one record stage per thread
+    // field window, current window, one record stage per thread (cell word,
+    // kRec3 reals, and the id the binned layout moves with the particle, staged
+    // and kept)
     static constexpr size_t smem_bytes =
-        (size_t)(6 * FA + 3 * WA) * sizeof(R) + kThreads3 * (sizeof(uint32_t) + kRec3 * sizeof(R));
+        (size_t)(6 * FA + 3 * WA) * sizeof(R) + kThreads3 * (3 * sizeof(uint32_t) + kRec3 * sizeof(R));
     // resident CTAs per SM the register budget is sized for: three while three
     // fit in shared memory (float), else two; the FP64 instantiation takes one
     static constexpr int minb = sizeof(R) == 8 ? 1 : (smem_bytes <= 74 * 1024 ? PIC3_MINB : 2);
@@ -62,7 +64,135 @@ struct SmemMesh3T {
     }
 };
 
+template <int TX, int TY, int TZ>
+__device__ __forceinline__ int tile_of3(const TileGeom3 &t, int ix, int iy, int iz) {
+    return ((iz / TZ) * t.nty + iy / TY) * t.ntx + ix / TX;
+}
+
+// destination range of a particle that survived the move (-1 and PIC_EF_RANGE
+// for a cell outside the mesh, which only a corrupt input cell can produce)
+template <int TX, int TY, int TZ, typename R>
+__device__ __forceinline__ int bin_dest3(const MeshParams3<R> &m, const TileGeom3 &t, int ix, int iy, int iz,
+                                         unsigned *err) {
+    if (ix < 0 || ix >= m.nx || iy < 0 || iy >= m.ny || iz < 0 || iz >= m.nz) {
+        atomicOr(err, PIC_EF_RANGE);
+        return -1;
+    }
+    return tile_of3<TX, TY, TZ>(t, ix, iy, iz);
+}
+
+// Eq. (4) sums of the particles in the window [dlo, dhi) MeV
+template <typename R>
+__device__ __forceinline__ void diag_add3(R dacc[7], R dm, R dlo, R dhi, R dshift, R w, const R u[3],
+                                          const R spn[3]) {
+    const R e = ekin_mev(dm, u[0], u[1], u[2]);
+    if (e >= dlo && e < dhi) {
+        const R ep = e - dshift;
+        dacc[0] += w;
+        dacc[1] += w * spn[0];
+        dacc[2] += w * spn[1];
+        dacc[3] += w * spn[2];
+        dacc[4] += w * ep;
+        dacc[5] += w * ep * ep;
+        dacc[6] += R(1);
+    }
+}
+
+// column `col` of the per-CTA sums of species sp (FP64 warp shuffles), ncols
+// columns per row; the whole CTA calls it
+template <typename R>
+__device__ __forceinline__ void store_diag_rows3(const DiagParams &D, int sp, const R dacc[7], double (*sdiag)[8],
+                                                 int col, int ncols) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int qd = 0; qd < 7; ++qd) {
+        double v = (double)dacc[qd];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+        if (lane == 0) sdiag[wid][qd] = v;
+    }
+    __syncthreads();
+    if (tid < 7) {
+        double t = 0.0;
+        for (int w8 = 0; w8 < kThreads3 / 32; ++w8) t += sdiag[w8][tid];
+        D.rows[((size_t)sp * 8 + tid) * ncols + col] = t;
+    }
+    __syncthreads();
+}
+
 }  // namespace
+
+// ---------------------------------------------------------------------------
+// Binned layout, the overflow range: its particles take the whole step against
+// global memory (NodeBlock3) and are binned like every other particle; P.nextra
+// CTAs, Eq. (4) sums in the diagnostic columns after the tiles'.  The range is
+// empty unless a tile range filled since the last sort.
+// ---------------------------------------------------------------------------
+template <int TX, int TY, int TZ, typename R>
+__global__ void __launch_bounds__(kThreads3) k_overflow3(const StepParams3<R> P) {
+    __shared__ double sdiag[kThreads3 / 32][8];
+    const MeshParams3<R> &m = P.m;
+    const int nt = P.t.ntx * P.t.nty * P.t.ntz;
+    const int tid = threadIdx.x;
+    const bool diag = P.diag.on != 0;
+    bool bad = false;
+    for (int sp = 0; sp < P.nsp; ++sp) {
+        const DevSpecies3<R> &S = P.sp[sp];
+        if (!S.mobile) continue;
+        const int ob = S.tile_start[nt];
+        const int len = min(P.bin[sp].cnt_in[nt], S.tile_start[nt + 1] - ob);
+        R dacc[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+        const R dlo = (R)P.diag.lo[sp], dhi = (R)P.diag.hi[sp], dm = (R)P.diag.m_mev[sp];
+        const R dshift = diag ? (R)P.diag.shift[sp] : R(0);
+        for (int k0 = blockIdx.x * kThreads3; k0 < len; k0 += P.nextra * kThreads3) {
+            const int k = k0 + tid;
+            int dest = -1;
+            uint32_t cw = PIC_DEAD;
+            R v[10];
+#pragma unroll
+            for (int q = 0; q < 10; ++q) v[q] = R(0);
+            int32_t id = 0;
+            const uint32_t c = k < len ? S.cell[ob + k] : PIC_DEAD;
+            if (c != PIC_DEAD) {
+                const int slot = ob + k;
+                int ix, iy, iz;
+                unpack_cell3(c, ix, iy, iz);
+                const R ox = S.ox[slot], oy = S.oy[slot], oz = S.oz[slot], w = S.w[slot];
+                R u[3] = {S.ux[slot], S.uy[slot], S.uz[slot]};
+                R spn[3] = {S.sx[slot], S.sy[slot], S.sz[slot]};
+                const NodeBlock3<R> nb(m, ix, iy, iz, P.err);
+                R E[3], B[3];
+                gather_eb3(nb, 1, 1, 1, ox, oy, oz, E, B);
+                push_spin(S.qm, S.a, m.dt, E, B, u, spn);
+                const R gi = Real<R>::rsqrt(R(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                int ix1 = ix, iy1 = iy, iz1 = iz;
+                R ox1 = ox, oy1 = oy, oz1 = oz;
+                advance_axis(ix1, ox1, u[0] * gi * m.dt_dx);
+                advance_axis(iy1, oy1, u[1] * gi * m.dt_dy);
+                advance_axis(iz1, oz1, u[2] * gi * m.dt_dz);
+                const R qw = S.q * w;
+                if (ix1 == ix && iy1 == iy && iz1 == iz) {
+                    R jv[12];
+                    in_cell_weights3(ox, oy, oz, ox1, oy1, oz1, qw, m.dx_dt, m.dy_dt, m.dz_dt, jv);
+                    deposit_in_cell3(nb, 1, 1, 1, jv);
+                } else {
+                    deposit_esirkepov3(nb, 1, 1, 1, ox, oy, oz, ix1 - ix + 1, iy1 - iy + 1, iz1 - iz + 1, ox1, oy1,
+                                       oz1, qw, m.dx_dt, m.dy_dt, m.dz_dt);
+                }
+                bad |= !finite3(u) || !finite3(spn);
+                if (finish_move3(m, ix1, iy1, iz1)) {
+                    if (diag) diag_add3(dacc, dm, dlo, dhi, dshift, w, u, spn);
+                    dest = bin_dest3<TX, TY, TZ>(m, P.t, ix1, iy1, iz1, P.err);
+                    cw = pack_cell3(ix1, iy1, iz1);
+                    v[0] = ox1, v[1] = oy1, v[2] = oz1, v[3] = u[0], v[4] = u[1], v[5] = u[2];
+                    v[6] = spn[0], v[7] = spn[1], v[8] = spn[2], v[9] = w;
+                    id = S.id[slot];
+                }
+            }
+            bin_store3(P.bin[sp], S.tile_start, nt, dest, cw, v, id, P.err);
+        }
+        if (diag) store_diag_rows3(P.diag, sp, dacc, sdiag, nt + blockIdx.x, nt + P.nextra);
+    }
+    if (bad) atomicOr(P.err, PIC_EF_NAN);
+}
 
 // ---------------------------------------------------------------------------
 // Fused 3D step kernel.  Thread 0 stages the 6-component field window (x
@@ -74,12 +204,16 @@ struct SmemMesh3T {
 // (cp.async), so one record is always in flight while it computes.  A record
 // runs a1-a5 against shared memory when its stencil [cell-1, cell+2]^3 lies in
 // the window and in the mesh (no wrap), else against global memory through a
-// NodeBlock3 (wrapped offsets formed once, loads without branches).  In-cell
-// currents of consecutive particles of one cell (the layered tile order gives
-// a thread the same cell on every layer) are summed in registers.  The current
-// window is added to J at the end (16-byte vector atomics in float).
+// NodeBlock3 (wrapped offsets formed once, loads without branches).  The
+// current window is added to J at the end (16-byte vector atomics in float).
+//
+// BIN = false: the records are rewritten in place (compact layout, periodic
+// tile sorts).  BIN = true (binned layout): tile T reads the first cnt_in[T]
+// slots of its range and every surviving particle is stored into the range of
+// the tile its new cell lies in, in the other buffer (bin_store3);
+// k_overflow3 runs the overflow range.
 // ---------------------------------------------------------------------------
-template <int TX, int TY, int TZ, typename R>
+template <int TX, int TY, int TZ, typename R, bool BIN>
 __global__ void __launch_bounds__(kThreads3, (TileConst3<TX, TY, TZ, R>::minb))
     k_step_fused3(const StepParams3<R> P, const __grid_constant__ CUtensorMap tmapEB) {
     using TC = TileConst3<TX, TY, TZ, R>;
@@ -91,6 +225,8 @@ __global__ void __launch_bounds__(kThreads3, (TileConst3<TX, TY, TZ, R>::minb))
     R *sJ = sF + 6 * FA;
     R *ring = sJ + 3 * WA;                                                // [kRec3][kThreads3]
     uint32_t *cring = reinterpret_cast<uint32_t *>(ring + kRec3 * kThreads3);  // [kThreads3]
+    int32_t *iring = reinterpret_cast<int32_t *>(cring + kThreads3);          // [kThreads3]
+    int32_t *idkeep = iring + kThreads3;  // [kThreads3] id of the record in hand (binned layout)
     const MeshParams3<R> &m = P.m;
 
     const int tile = blockIdx.x;
@@ -122,8 +258,19 @@ __global__ void __launch_bounds__(kThreads3, (TileConst3<TX, TY, TZ, R>::minb))
             cp_async_r(r + 7 * kThreads3, S.sy + slot);
             cp_async_r(r + 8 * kThreads3, S.sz + slot);
             cp_async_r(r + 9 * kThreads3, S.w + slot);
+            if constexpr (BIN) cp_async4(iring + tid, S.id + slot);
         }
         cp_async_commit();
+    };
+    // slots of this tile: [beg, beg + len)
+    auto range = [&](int sp, int &beg, int &len) {
+        const DevSpecies3<R> &S = P.sp[sp];
+        beg = S.tile_start[tile];
+        const int size = S.tile_start[tile + 1] - beg;
+        if constexpr (BIN)
+            len = min(P.bin[sp].cnt_in[tile], size);
+        else
+            len = size;
     };
 
     const bool diag = P.diag.on != 0;
@@ -131,8 +278,9 @@ __global__ void __launch_bounds__(kThreads3, (TileConst3<TX, TY, TZ, R>::minb))
     for (int sp = 0; sp < P.nsp && first < 0; ++sp)
         if (P.sp[sp].mobile) first = sp;
     if (first >= 0) {
-        const int beg = P.sp[first].tile_start[tile];
-        prefetch(P.sp[first], beg + tid, tid < P.sp[first].tile_start[tile + 1] - beg);
+        int beg, len;
+        range(first, beg, len);
+        prefetch(P.sp[first], beg + tid, tid < len);
     }
     for (int i = tid; i < 3 * WA; i += kThreads3) sJ[i] = R(0);
     __syncthreads();
@@ -175,7 +323,8 @@ __global__ void __launch_bounds__(kThreads3, (TileConst3<TX, TY, TZ, R>::minb))
     for (int sp = 0; sp < P.nsp; ++sp) {
         const DevSpecies3<R> &S = P.sp[sp];
         if (!S.mobile) continue;
-        const int beg = S.tile_start[tile], len = S.tile_start[tile + 1] - beg;
+        int beg, len;
+        range(sp, beg, len);
         const R qm = S.qm, a = S.a, q = S.q;
         R dacc[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
         R dlo = R(0), dhi = R(0), dm = R(0), dshift = R(0);
@@ -189,6 +338,14 @@ __global__ void __launch_bounds__(kThreads3, (TileConst3<TX, TY, TZ, R>::minb))
         for (int k0 = 0; k0 < len; k0 += kThreads3) {
             const int k = k0 + tid;
             cp_async_wait0();
+            // binned layout: what this lane stores after the record (dest -1: nothing)
+            int dest = -1;
+            uint32_t bcell = PIC_DEAD;
+            R bv[10];
+            if constexpr (BIN) {
+#pragma unroll
+                for (int q10 = 0; q10 < 10; ++q10) bv[q10] = R(0);
+            }
             if (k < len) {
                 const int slot = beg + k;
                 const R *r = ring0;
@@ -197,6 +354,7 @@ __global__ void __launch_bounds__(kThreads3, (TileConst3<TX, TY, TZ, R>::minb))
                 R u[3] = {r[3 * kThreads3], r[4 * kThreads3], r[5 * kThreads3]};
                 R spn[3] = {r[6 * kThreads3], r[7 * kThreads3], r[8 * kThreads3]};
                 const R w = r[9 * kThreads3];
+                if constexpr (BIN) idkeep[tid] = iring[tid];  // the ring slot is reused below
                 // the slot is free again: request the next record
                 prefetch(S, beg + k + kThreads3, k + kThreads3 < len);
                 if (c != PIC_DEAD) {
@@ -254,48 +412,34 @@ __global__ void __launch_bounds__(kThreads3, (TileConst3<TX, TY, TZ, R>::minb))
                     const R chk = u[0] * u[0] + u[1] * u[1] + u[2] * u[2] + spn[0] * spn[0] +
                                   spn[1] * spn[1] + spn[2] * spn[2];
                     bad |= !isfinite(chk);
-                    if (diag && alive) {
-                        const R e = ekin_mev(dm, u[0], u[1], u[2]);
-                        if (e >= dlo && e < dhi) {
-                            const R ep = e - dshift;
-                            dacc[0] += w;
-                            dacc[1] += w * spn[0];
-                            dacc[2] += w * spn[1];
-                            dacc[3] += w * spn[2];
-                            dacc[4] += w * ep;
-                            dacc[5] += w * ep * ep;
-                            dacc[6] += R(1);
+                    if (diag && alive) diag_add3(dacc, dm, dlo, dhi, dshift, w, u, spn);
+                    if constexpr (BIN) {
+                        if (alive) {
+                            dest = bin_dest3<TX, TY, TZ>(m, P.t, ix1, iy1, iz1, P.err);
+                            bcell = pack_cell3(ix1, iy1, iz1);
+                            bv[0] = ox1, bv[1] = oy1, bv[2] = oz1, bv[3] = u[0], bv[4] = u[1], bv[5] = u[2];
+                            bv[6] = spn[0], bv[7] = spn[1], bv[8] = spn[2], bv[9] = w;
                         }
+                    } else {
+                        S.cell[slot] = alive ? pack_cell3(ix1, iy1, iz1) : PIC_DEAD;
+                        S.ox[slot] = ox1;
+                        S.oy[slot] = oy1;
+                        S.oz[slot] = oz1;
+                        S.ux[slot] = u[0];
+                        S.uy[slot] = u[1];
+                        S.uz[slot] = u[2];
+                        S.sx[slot] = spn[0];
+                        S.sy[slot] = spn[1];
+                        S.sz[slot] = spn[2];
                     }
-                    S.cell[slot] = alive ? pack_cell3(ix1, iy1, iz1) : PIC_DEAD;
-                    S.ox[slot] = ox1;
-                    S.oy[slot] = oy1;
-                    S.oz[slot] = oz1;
-                    S.ux[slot] = u[0];
-                    S.uy[slot] = u[1];
-                    S.uz[slot] = u[2];
-                    S.sx[slot] = spn[0];
-                    S.sy[slot] = spn[1];
-                    S.sz[slot] = spn[2];
                 }
             }
+            if constexpr (BIN)
+                bin_store3(P.bin[sp], S.tile_start, (int)gridDim.x, dest, bcell, bv, idkeep[tid], P.err);
         }
         cp_async_wait0();
-        if (diag) {
-            const int lane = tid & 31, wid = tid >> 5;
-            for (int qd = 0; qd < 7; ++qd) {
-                double v = (double)dacc[qd];
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
-                if (lane == 0) sdiag[wid][qd] = v;
-            }
-            __syncthreads();
-            if (tid < 7) {
-                double t = 0.0;
-                for (int w8 = 0; w8 < kThreads3 / 32; ++w8) t += sdiag[w8][tid];
-                P.diag.rows[((size_t)sp * 8 + tid) * gridDim.x + blockIdx.x] = t;
-            }
-            __syncthreads();
-        }
+        if (diag)  // diagnostic columns: the tiles, then (binned) the overflow CTAs
+            store_diag_rows3(P.diag, sp, dacc, sdiag, (int)blockIdx.x, (int)gridDim.x + (BIN ? P.nextra : 0));
     }
     acc_flush();
     if (bad) atomicOr(P.err, PIC_EF_NAN);
@@ -409,22 +553,35 @@ __global__ void __launch_bounds__(256) k_deposit_split3(const StepParams3<R> P, 
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-template <int TX, int TY, int TZ, typename R>
+template <int TX, int TY, int TZ, typename R, bool BIN>
 static cudaError_t launch_fused3_t(const StepParams3<R> &P, const CUtensorMap &tmapEB, cudaStream_t st) {
     using TC = TileConst3<TX, TY, TZ, R>;
     constexpr size_t smem = TC::smem_bytes;
     if (P.t.WX != TC::WX || P.t.WY != TC::WY || P.t.WZ != TC::WZ || P.t.FX != TC::FX || P.t.HX != TC::HX ||
         P.t.HY != TC::HY || P.t.HZ != TC::HZ)
         return cudaErrorInvalidValue;
+    if (BIN && P.nextra < 1) return cudaErrorInvalidValue;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_step_fused3<TX, TY, TZ, R>,
+        cudaError_t e = cudaFuncSetAttribute(k_step_fused3<TX, TY, TZ, R, BIN>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    k_step_fused3<TX, TY, TZ, R><<<P.t.ntx * P.t.nty * P.t.ntz, kThreads3, smem, st>>>(P, tmapEB);
+    k_step_fused3<TX, TY, TZ, R, BIN><<<P.t.ntx * P.t.nty * P.t.ntz, kThreads3, smem, st>>>(P, tmapEB);
+    if (BIN) {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_overflow3<TX, TY, TZ, R><<<P.nextra, kThreads3, 0, st>>>(P);
+    }
     return cudaGetLastError();
+}
+
+template <int TX, int TY, int TZ, typename R>
+static cudaError_t launch_fused3_b(const StepParams3<R> &P, const CUtensorMap &tmapEB, bool binned,
+                                   cudaStream_t st) {
+    return binned ? launch_fused3_t<TX, TY, TZ, R, true>(P, tmapEB, st)
+                  : launch_fused3_t<TX, TY, TZ, R, false>(P, tmapEB, st);
 }
 
 bool fused3_tile_supported(int tx, int ty, int tz) {
@@ -433,13 +590,13 @@ bool fused3_tile_supported(int tx, int ty, int tz) {
 }
 
 template <typename R>
-cudaError_t launch_step_fused3(const StepParams3<R> &P, const CUtensorMap &tmapEB, cudaStream_t st) {
+cudaError_t launch_step_fused3(const StepParams3<R> &P, const CUtensorMap &tmapEB, bool binned, cudaStream_t st) {
     const int tx = P.t.TX, ty = P.t.TY, tz = P.t.TZ;
-    if (tx == 8 && ty == 8 && tz == 4) return launch_fused3_t<8, 8, 4, R>(P, tmapEB, st);
-    if (tx == 16 && ty == 4 && tz == 4) return launch_fused3_t<16, 4, 4, R>(P, tmapEB, st);
-    if (tx == 8 && ty == 4 && tz == 4) return launch_fused3_t<8, 4, 4, R>(P, tmapEB, st);
-    if (tx == 16 && ty == 8 && tz == 4) return launch_fused3_t<16, 8, 4, R>(P, tmapEB, st);
-    if (tx == 32 && ty == 4 && tz == 4) return launch_fused3_t<32, 4, 4, R>(P, tmapEB, st);
+    if (tx == 8 && ty == 8 && tz == 4) return launch_fused3_b<8, 8, 4, R>(P, tmapEB, binned, st);
+    if (tx == 16 && ty == 4 && tz == 4) return launch_fused3_b<16, 4, 4, R>(P, tmapEB, binned, st);
+    if (tx == 8 && ty == 4 && tz == 4) return launch_fused3_b<8, 4, 4, R>(P, tmapEB, binned, st);
+    if (tx == 16 && ty == 8 && tz == 4) return launch_fused3_b<16, 8, 4, R>(P, tmapEB, binned, st);
+    if (tx == 32 && ty == 4 && tz == 4) return launch_fused3_b<32, 4, 4, R>(P, tmapEB, binned, st);
     return cudaErrorInvalidValue;
 }
 
@@ -460,8 +617,8 @@ cudaError_t launch_deposit_split3(const StepParams3<R> &P, int s, int n_upper, c
     return cudaGetLastError();
 }
 
-template cudaError_t launch_step_fused3<float>(const StepParams3<float> &, const CUtensorMap &, cudaStream_t);
-template cudaError_t launch_step_fused3<double>(const StepParams3<double> &, const CUtensorMap &, cudaStream_t);
+template cudaError_t launch_step_fused3<float>(const StepParams3<float> &, const CUtensorMap &, bool, cudaStream_t);
+template cudaError_t launch_step_fused3<double>(const StepParams3<double> &, const CUtensorMap &, bool, cudaStream_t);
 template cudaError_t launch_push_split3<float>(const StepParams3<float> &, int, int, cudaStream_t);
 template cudaError_t launch_push_split3<double>(const StepParams3<double> &, int, int, cudaStream_t);
 template cudaError_t launch_deposit_split3<float>(const StepParams3<float> &, int, int, cudaStream_t);

@@ -112,7 +112,7 @@ __global__ void k_rank(const uint32_t *cell, const int32_t *n_src, const K key, 
 // minimum of the counts), tail offset of each cell (exclusive scan of the
 // counts above R), tile total
 __global__ void __launch_bounds__(1024) k_layout(const int32_t *cell_count, int C, int32_t *cell_off,
-                                                 int32_t *tile_R, int32_t *tile_total) {
+                                                 int32_t *tile_R, int32_t *tile_total, BinSort bins) {
     __shared__ int32_t wmin[32], wsum[32];
     const int t = blockIdx.x, c = threadIdx.x, lane = c & 31, wid = c >> 5, nw = (C + 31) >> 5;
     const int cnt = cell_count[(size_t)t * C + c];
@@ -134,8 +134,21 @@ __global__ void __launch_bounds__(1024) k_layout(const int32_t *cell_count, int 
     for (int w = 0; w < wid; ++w) base += wsum[w];
     cell_off[(size_t)t * C + c] = base + incl - ex;
     if (c == C - 1) {
+        const int total = R * C + base + incl;
         tile_R[t] = R;
-        tile_total[t] = R * C + base + incl;
+        if (bins.cnt_to) {
+            // binned layout: the range holds the tile's particles and its spare
+            // slots; the range after the last tile is the overflow range
+            bins.cnt_to[t] = total;
+            const int spare = max(bins.extra, (int)((long long)total * bins.pct / 100));
+            tile_total[t] = (total + spare + 7) / 8 * 8;
+            if (t == 0) {
+                bins.cnt_to[gridDim.x] = 0;
+                tile_total[gridDim.x] = bins.ovf_cap;
+            }
+        } else {
+            tile_total[t] = total;
+        }
     }
 }
 
@@ -290,21 +303,51 @@ cudaError_t launch_unpack_cells3(const uint32_t *cell, int32_t *ix, int32_t *iy,
     return cudaGetLastError();
 }
 
+// Binned layout: one warp per range writes PIC_DEAD into the range's spare
+// slots (past its count) and clears the other buffer's count of the range.
+__global__ void __launch_bounds__(256) k_seal_bins(const SealArgs a) {
+    const int r = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (r >= a.nranges) return;
+    for (int s = 0; s < a.nsp; ++s) {
+        const SealSpecies &S = a.sp[s];
+        const int beg = S.tile_start[r], end = S.tile_start[r + 1];
+        const int n = min(S.cnt_new[r], end - beg);
+        for (int i = beg + n + lane; i < end; i += 32) S.cell[i] = PIC_DEAD;
+        if (lane == 0 && S.cnt_zero) S.cnt_zero[r] = 0;
+    }
+}
+
+cudaError_t launch_seal_bins(const SealArgs &a, cudaStream_t st) {
+    if (a.nranges <= 0 || a.nsp <= 0) return cudaSuccess;
+    k_seal_bins<<<(a.nranges + 7) / 8, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
 namespace {
 template <typename R, int NF, class K>
 cudaError_t tile_sort(const SortArrays<R> &src, const SortArrays<R> &dst, const K &key, const SortScratch &w,
-                      int32_t *tile_start, int32_t *n_tmp, int n_upper, cudaStream_t st) {
+                      int32_t *tile_start, int32_t *n_tmp, int n_upper, const BinSort &bins, cudaStream_t st) {
     const int nt = key.tiles(), C = key.cells();
     cudaError_t e = cudaMemsetAsync(w.cell_count, 0, sizeof(int32_t) * (size_t)nt * C, st);
     if (e != cudaSuccess) return e;
     const int g = grid_for(n_upper);
     k_rank<K><<<g, 256, 0, st>>>(src.cell, src.n, key, w.cell_count, w.rank);
-    k_layout<<<nt, C, 0, st>>>(w.cell_count, C, w.cell_off, w.tile_R, w.tile_total);
-    e = scan_tiles(w.tile_total, nt, tile_start, w.cursor, n_tmp, st);
+    k_layout<<<nt, C, 0, st>>>(w.cell_count, C, w.cell_off, w.tile_R, w.tile_total, bins);
+    e = scan_tiles(w.tile_total, bins.cnt_to ? nt + 1 : nt, tile_start, w.cursor, n_tmp, st);
     if (e != cudaSuccess) return e;
     k_scatter<R, NF, K><<<g, 256, 0, st>>>(src, dst, key, w.rank, tile_start, w.tile_R, w.cell_off, C);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (bins.cnt_to) {
+        // spare slots of every range -> PIC_DEAD; the source buffer's counts
+        // cleared for the next binned step to count into
+        SealArgs a{};
+        a.nsp = 1;
+        a.nranges = nt + 1;
+        a.sp[0] = SealSpecies{dst.cell, tile_start, bins.cnt_to, bins.cnt_from};
+        e = launch_seal_bins(a, st);
+        if (e != cudaSuccess) return e;
+    }
     return cudaMemcpyAsync(const_cast<int32_t *>(src.n), n_tmp, sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
 }
 
@@ -327,22 +370,22 @@ template <typename R>
 cudaError_t launch_tile_sort(const DevSpecies<R> &src, const DevSpecies<R> &dst, const TileGeom &t,
                              const SortScratch &w, int32_t *tile_start, int32_t *n_tmp, int n_upper,
                              cudaStream_t st) {
-    return tile_sort<R, 9>(arrays2(src), arrays2(dst), Key2(t), w, tile_start, n_tmp, n_upper, st);
+    return tile_sort<R, 9>(arrays2(src), arrays2(dst), Key2(t), w, tile_start, n_tmp, n_upper, BinSort{}, st);
 }
 
 template <typename R>
 cudaError_t launch_tile_sort3(const DevSpecies3<R> &src, const DevSpecies3<R> &dst, const TileGeom3 &t,
                               const SortScratch &w, int32_t *tile_start, int32_t *n_tmp, int n_upper,
-                              cudaStream_t st) {
-    return tile_sort<R, 10>(arrays3(src), arrays3(dst), Key3(t), w, tile_start, n_tmp, n_upper, st);
+                              const BinSort &bins, cudaStream_t st) {
+    return tile_sort<R, 10>(arrays3(src), arrays3(dst), Key3(t), w, tile_start, n_tmp, n_upper, bins, st);
 }
 
 template cudaError_t launch_tile_sort3<float>(const DevSpecies3<float> &, const DevSpecies3<float> &,
                                               const TileGeom3 &, const SortScratch &, int32_t *, int32_t *, int,
-                                              cudaStream_t);
+                                              const BinSort &, cudaStream_t);
 template cudaError_t launch_tile_sort3<double>(const DevSpecies3<double> &, const DevSpecies3<double> &,
                                                const TileGeom3 &, const SortScratch &, int32_t *, int32_t *, int,
-                                               cudaStream_t);
+                                               const BinSort &, cudaStream_t);
 
 template cudaError_t launch_tile_sort<float>(const DevSpecies<float> &, const DevSpecies<float> &,
                                              const TileGeom &, const SortScratch &, int32_t *, int32_t *, int,

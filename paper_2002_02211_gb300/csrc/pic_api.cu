@@ -72,6 +72,14 @@ struct Ctx {
     uint32_t *adj_cell0[PIC_MAX_SPECIES] = {};
     long long adj_n[PIC_MAX_SPECIES] = {};
     bool has_background = false;  // pic_capture_background was called
+    // binned 3D3V layout (bin_headroom_pct > 0): per mobile species the range
+    // counts of both buffers, whether the species is in that layout now, and a
+    // host bound on its live particles (sizes the ranges against capacity)
+    bool binned = false;
+    bool sp_binned[PIC_MAX_SPECIES] = {};
+    int32_t *bin_cnt[PIC_MAX_SPECIES][2] = {};
+    int64_t n_live[PIC_MAX_SPECIES] = {};
+    static constexpr int kBinCtas = 8;  // CTAs of the overflow-range kernel
     int since_sort = 0;
     long long launches = 0;  // kernels launched by this context
     std::string last_error;
@@ -324,25 +332,67 @@ pic_status_t check_flags(Ctx *c, cudaStream_t st) {
     if (h & PIC_EF_NAN) return fail(c, PIC_ERR_NAN, "non-finite momentum or spin");
     if (h & PIC_EF_CFL) return fail(c, PIC_ERR_CFL, "particle moved a cell or more in one step");
     if (h & PIC_EF_RANGE) return fail(c, PIC_ERR_ARG, "particle cell outside the particle region");
+    if (h & PIC_EF_BINS)
+        return fail(c, PIC_ERR_OVERFLOW,
+                    "binned layout: a tile range and the overflow range were full, particles were lost "
+                    "(raise bin_headroom_pct or bin_min_extra, or sort more often)");
     return fail(c, PIC_ERR_CUDA, "unknown device error flag");
 }
 
-// no host synchronisation: the sorted count stays on the device (it only
-// ever shrinks, so n_upper still bounds it)
-pic_status_t sort_species(Ctx *c, int s, cudaStream_t st) {
+// Binned layout of species s: the overflow range and the host bound on the
+// slot span (every range at its largest, plus the overflow range); false when
+// the species is not eligible or its capacity cannot hold that bound.
+bool bin_plan(const Ctx *c, int s, int *ovf_cap, int64_t *span) {
+    if (!c->binned || !c->cfg.sp[s].mobile) return false;
+    const int64_t n = c->n_live[s];
+    const int64_t ovf = ((std::max<int64_t>(1024, n / 64) + 7) / 8) * 8;
+    const int64_t bound = n + n * c->cfg.bin_headroom_pct / 100 +
+                          (int64_t)c->ntiles * (c->cfg.bin_min_extra + 7) + ovf;
+    if (bound > c->cfg.sp[s].capacity) return false;
+    *ovf_cap = (int)ovf;
+    *span = bound;
+    return true;
+}
+
+// No host synchronisation: the sorted slot count stays on the device.  In the
+// compact layout it only shrinks, so n_upper still bounds it; in the binned
+// layout n_upper becomes the host bound on the span of the ranges.
+// compact_only keeps the compact layout even when the binned one is on.
+pic_status_t sort_species(Ctx *c, int s, cudaStream_t st, bool compact_only = false) {
     const int from = c->cur[s], to = 1 - from;
     SortScratch w{c->cell_count, c->cell_off, c->tile_R, c->tile_count, c->tile_cursor, c->scratch_i32};
+    BinSort bins{};
+    int64_t span = 0;
+    const bool bin = c->dim == 3 && !compact_only && bin_plan(c, s, &bins.ovf_cap, &span);
+    if (bin) {
+        bins.pct = c->cfg.bin_headroom_pct;
+        bins.extra = c->cfg.bin_min_extra;
+        bins.cnt_to = c->bin_cnt[s][to];
+        bins.cnt_from = c->bin_cnt[s][from];
+    }
     CK(with_real(c, [&](auto z) {
         using T = decltype(z);
         if (c->dim == 3)
             return launch_tile_sort3<T>(dev_species3<T>(c, s, from), dev_species3<T>(c, s, to), c->tg3, w,
-                                        c->tile_start[s], c->n_dev + PIC_MAX_SPECIES, c->n_upper[s], st);
+                                        c->tile_start[s], c->n_dev + PIC_MAX_SPECIES, c->n_upper[s], bins, st);
         return launch_tile_sort<T>(dev_species<T>(c, s, from), dev_species<T>(c, s, to), c->tg, w, c->tile_start[s],
                                    c->n_dev + PIC_MAX_SPECIES, c->n_upper[s], st);
     }));
-    c->launches += 6;  // rank, layout, three scan passes, scatter
+    c->launches += bin ? 7 : 6;  // rank, layout, three scan passes, scatter (, seal)
     c->cur[s] = to;
+    if (bin)
+        c->n_upper[s] = (int)span;
+    else if (c->sp_binned[s])
+        c->n_upper[s] = (int)std::min<int64_t>(c->n_upper[s], c->n_live[s]);
+    c->sp_binned[s] = bin;
     return PIC_OK;
+}
+
+// every mobile species in the binned layout (the binned step's precondition)
+bool all_binned(const Ctx *c) {
+    for (int s = 0; s < c->cfg.nspecies; ++s)
+        if (c->cfg.sp[s].mobile && !c->sp_binned[s]) return false;
+    return true;
 }
 
 pic_status_t read_count(Ctx *c, int s, cudaStream_t st, int32_t *n) {
@@ -405,8 +455,10 @@ pic_status_t upload_particles(Ctx *c, int s, const PT *p, int64_t base, cudaStre
         cudaMemcpyAsync(c->n_dev + s, &keep, sizeof(int32_t), cudaMemcpyHostToDevice, st);
         cudaStreamSynchronize(st);
         c->n_upper[s] = (int)base;
+        if (base == 0) c->n_live[s] = 0;
         return r;
     }
+    c->n_live[s] = base == 0 ? (int64_t)n : c->n_live[s] + (int64_t)n;
     return PIC_OK;
 }
 
@@ -429,16 +481,16 @@ pic_status_t retile(Ctx *c, int tx, int ty, cudaStream_t st) {
     c->cfg.tile_y = ty;
     choose_tiles(c);
     for (int s = 0; s < c->cfg.nspecies; ++s) {
-        CK(cudaMalloc(&c->tile_start[s], (c->ntiles + 1) * sizeof(int32_t)));
-        CK(cudaMemsetAsync(c->tile_start[s], 0, (c->ntiles + 1) * sizeof(int32_t), st));
+        CK(cudaMalloc(&c->tile_start[s], (c->ntiles + 2) * sizeof(int32_t)));
+        CK(cudaMemsetAsync(c->tile_start[s], 0, (c->ntiles + 2) * sizeof(int32_t), st));
     }
     const size_t cells = (size_t)c->ntiles * tile_cells(c);
-    CK(cudaMalloc(&c->tile_count, c->ntiles * sizeof(int32_t)));
+    CK(cudaMalloc(&c->tile_count, (c->ntiles + 1) * sizeof(int32_t)));
     CK(cudaMalloc(&c->cell_count, cells * sizeof(int32_t)));
     CK(cudaMalloc(&c->cell_off, cells * sizeof(int32_t)));
     CK(cudaMalloc(&c->tile_R, c->ntiles * sizeof(int32_t)));
     CK(cudaMalloc(&c->tile_cursor, c->ntiles * sizeof(int32_t)));
-    CK(cudaMalloc(&c->diag_rows, (size_t)c->ntiles * PIC_MAX_SPECIES * 8 * sizeof(double)));
+    CK(cudaMalloc(&c->diag_rows, (size_t)(c->ntiles + Ctx::kBinCtas) * PIC_MAX_SPECIES * 8 * sizeof(double)));
     pic_status_t r = make_tensor_map(c);
     if (r != PIC_OK) return r;
     for (int s = 0; s < c->cfg.nspecies; ++s) {
@@ -495,6 +547,10 @@ pic_status_t pic_validate_config(const pic_config_t *cfg) {
         !fused3_tile_supported(cfg->tile_x, cfg->tile_y, cfg->tile_z))
         return fail(c, PIC_ERR_ARG, "3D3V tile must be one of 16x4x4, 8x8x4, 8x4x4, 16x8x4, 32x4x4 cells");
     if (cfg->sort_every < 0) return fail(c, PIC_ERR_ARG, "sort_every must be >= 0");
+    if (cfg->bin_headroom_pct < 0 || cfg->bin_headroom_pct > 400 || cfg->bin_min_extra < 0 ||
+        cfg->bin_min_extra > 4096)
+        return fail(c, PIC_ERR_ARG, "bin_headroom_pct must be in [0, 400] and bin_min_extra in [0, 4096]");
+    if (cfg->bin_headroom_pct > 0 && !d3) return fail(c, PIC_ERR_ARG, "the binned layout is 3D3V only");
     if (cfg->precision != 0 && cfg->precision != 32 && cfg->precision != 64)
         return fail(c, PIC_ERR_ARG, "precision must be 32 or 64 (0: 32)");
     return PIC_OK;
@@ -513,6 +569,7 @@ pic_status_t pic_create(const pic_config_t *cfg, void *stream, void **ctx_out) {
     if (c->cfg.precision == 0) c->cfg.precision = 32;
     c->rb = c->cfg.precision == 64 ? 8 : 4;
     c->dim = c->cfg.dim == 3 ? 3 : 2;
+    c->binned = c->dim == 3 && c->cfg.bin_headroom_pct > 0;
     cudaStream_t st = S(stream);
     auto bail = [&](pic_status_t s) {
         g_create_error = c->last_error;
@@ -560,10 +617,15 @@ pic_status_t pic_create(const pic_config_t *cfg, void *stream, void **ctx_out) {
             if (c->dim == 3) CKC(cudaMalloc(&c->buf[s][b].oz, cap * rb + 16));
             CKC(cudaMalloc(&c->buf[s][b].id, cap * sizeof(int32_t) + 16));
         }
-        CKC(cudaMalloc(&c->tile_start[s], (c->ntiles + 1) * sizeof(int32_t)));
-        CKC(cudaMemsetAsync(c->tile_start[s], 0, (c->ntiles + 1) * sizeof(int32_t), st));
+        CKC(cudaMalloc(&c->tile_start[s], (c->ntiles + 2) * sizeof(int32_t)));
+        CKC(cudaMemsetAsync(c->tile_start[s], 0, (c->ntiles + 2) * sizeof(int32_t), st));
+        if (c->binned && cfg->sp[s].mobile)
+            for (int b = 0; b < 2; ++b) {
+                CKC(cudaMalloc(&c->bin_cnt[s][b], (c->ntiles + 1) * sizeof(int32_t)));
+                CKC(cudaMemsetAsync(c->bin_cnt[s][b], 0, (c->ntiles + 1) * sizeof(int32_t), st));
+            }
     }
-    CKC(cudaMalloc(&c->tile_count, c->ntiles * sizeof(int32_t)));
+    CKC(cudaMalloc(&c->tile_count, (c->ntiles + 1) * sizeof(int32_t)));
     CKC(cudaMalloc(&c->cell_count, (size_t)c->ntiles * tile_cells(c) * sizeof(int32_t)));
     CKC(cudaMalloc(&c->cell_off, (size_t)c->ntiles * tile_cells(c) * sizeof(int32_t)));
     CKC(cudaMalloc(&c->tile_R, c->ntiles * sizeof(int32_t)));
@@ -578,7 +640,7 @@ pic_status_t pic_create(const pic_config_t *cfg, void *stream, void **ctx_out) {
     CKC(cudaMalloc(&c->partials, (size_t)reduce_blocks() * 8 * sizeof(double)));
     CKC(cudaMalloc(&c->result, 64 * sizeof(double)));  // moments results and diagnostic column sums
     CKC(cudaMalloc(&c->hist, (size_t)PIC_MAX_HIST_BINS * 5 * sizeof(double)));
-    CKC(cudaMalloc(&c->diag_rows, (size_t)c->ntiles * PIC_MAX_SPECIES * 8 * sizeof(double)));
+    CKC(cudaMalloc(&c->diag_rows, (size_t)(c->ntiles + Ctx::kBinCtas) * PIC_MAX_SPECIES * 8 * sizeof(double)));
     CKC(cudaMalloc(&c->diag_shift, PIC_MAX_SPECIES * sizeof(double)));
     CKC(cudaMemsetAsync(c->diag_shift, 0, PIC_MAX_SPECIES * sizeof(double), st));
     CKC(cudaMalloc(&c->diag_out, PIC_MAX_SPECIES * sizeof(pic_moments_dev)));
@@ -617,6 +679,8 @@ void pic_destroy(void *ctx) {
             cudaFree(c->buf[s][b].id);
         }
         cudaFree(c->tile_start[s]);
+        cudaFree(c->bin_cnt[s][0]);
+        cudaFree(c->bin_cnt[s][1]);
         cudaFree(c->cell_old[s]);
         for (int k = 0; k < 3; ++k) cudaFree(c->old_f[s][k]);
         for (int k = 0; k < 9; ++k) cudaFree(c->adj_lam[s][k]);
@@ -703,6 +767,12 @@ template <typename OutT, typename PT>
 static pic_status_t get_particles_t(Ctx *c, int s, PT *out, cudaStream_t st) {
     if (s < 0 || s >= c->cfg.nspecies || !out) return fail(c, PIC_ERR_ARG, "bad species or output");
     if (c->pending_deposit) return fail(c, PIC_ERR_STATE, "a move is waiting for pic_deposit");
+    if (c->sp_binned[s]) {
+        // the spare slots of the binned ranges hold stale records: read back
+        // the compact layout (the next step re-bins)
+        pic_status_t r = sort_species(c, s, st, true);
+        if (r != PIC_OK) return r;
+    }
     int32_t nv = 0;
     pic_status_t rc = read_count(c, s, st, &nv);
     if (rc != PIC_OK) return rc;
@@ -929,20 +999,70 @@ pic_status_t pic_push_deposit(void *ctx, void *stream) {
         D.shift = c->diag_shift;
         D.rows = c->diag_rows;
     }
+    // binned layout: every mobile species must be in it (after a set of
+    // particles, a compacting read-back or a window shift, re-bin first)
+    if (c->binned && !all_binned(c)) {
+        // re-bin every species when the capacities allow it, else bring the
+        // binned ones back to the compact layout the compact kernel reads
+        bool fits = true;
+        for (int s = 0; s < c->cfg.nspecies; ++s) {
+            int ovf;
+            int64_t span;
+            if (c->cfg.sp[s].mobile && !bin_plan(c, s, &ovf, &span)) fits = false;
+        }
+        for (int s = 0; s < c->cfg.nspecies; ++s) {
+            if (!fits && !c->sp_binned[s]) continue;
+            pic_status_t r = sort_species(c, s, S(stream), !fits);
+            if (r != PIC_OK) return r;
+        }
+        c->since_sort = 0;
+    }
+    const bool bin = c->binned && all_binned(c);
     CK(with_real(c, [&](auto z) {
         using T = decltype(z);
         if (c->dim == 3) {
             StepParams3<T> P = step_params3<T>(c);
             P.diag = D;
-            return launch_step_fused3<T>(P, c->tmapEB, S(stream));
+            if (bin) {
+                P.nextra = Ctx::kBinCtas;
+                for (int s = 0; s < c->cfg.nspecies; ++s) {
+                    if (!c->cfg.sp[s].mobile) continue;
+                    const int to = 1 - c->cur[s];
+                    const DevSpecies3<T> o = dev_species3<T>(c, s, to);
+                    Bin3<T> &b = P.bin[s];
+                    b.cell = o.cell;
+                    T *f[10] = {o.ox, o.oy, o.oz, o.ux, o.uy, o.uz, o.sx, o.sy, o.sz, o.w};
+                    for (int k = 0; k < 10; ++k) b.f[k] = f[k];
+                    b.id = o.id;
+                    b.cnt_in = c->bin_cnt[s][c->cur[s]];
+                    b.cnt_out = c->bin_cnt[s][to];
+                }
+            }
+            return launch_step_fused3<T>(P, c->tmapEB, bin, S(stream));
         }
         StepParams<T> P = step_params<T>(c);
         P.diag = D;
         return launch_step_fused<T>(P, c->tmapEB, S(stream));
     }));
-    c->launches += 1;
+    c->launches += bin ? 2 : 1;  // binned: the fused kernel and the overflow-range kernel
+    if (bin) {
+        // the particles now live in the other buffer: seal its spare slots,
+        // clear the consumed buffer's counts for the next step
+        SealArgs a{};
+        a.nranges = c->ntiles + 1;
+        for (int s = 0; s < c->cfg.nspecies; ++s) {
+            if (!c->cfg.sp[s].mobile) continue;
+            const int to = 1 - c->cur[s];
+            a.sp[a.nsp++] = SealSpecies{c->buf[s][to].cell, c->tile_start[s], c->bin_cnt[s][to],
+                                        c->bin_cnt[s][c->cur[s]]};
+            c->cur[s] = to;
+        }
+        CK(launch_seal_bins(a, S(stream)));
+        c->launches += 1;
+    }
     if (diag) {
-        CK(launch_diag_final(c->diag_rows, c->ntiles, c->cfg.nspecies, c->diag_shift, c->diag_out, c->result,
+        const int ncols = c->ntiles + (bin ? Ctx::kBinCtas : 0);
+        CK(launch_diag_final(c->diag_rows, ncols, c->cfg.nspecies, c->diag_shift, c->diag_out, c->result,
                              S(stream)));
         c->launches += 2;
         c->diag_step = c->step + 1;
@@ -1120,6 +1240,12 @@ pic_status_t pic_shift_window(void *ctx, int ncells, const pic_particles_t *inje
     if (c->pending_deposit) return fail(c, PIC_ERR_STATE, "a move is waiting for pic_deposit");
     cudaStream_t st = S(stream);
     const size_t rows = c->bnd_n;  // mesh rows of one component
+    // the injection is appended after the last slot of the compact layout
+    for (int s = 0; s < c->cfg.nspecies; ++s)
+        if (c->sp_binned[s]) {
+            pic_status_t r = sort_species(c, s, st, true);
+            if (r != PIC_OK) return r;
+        }
     // inject counts fit?
     int32_t cur[PIC_MAX_SPECIES] = {};
     for (int s = 0; s < c->cfg.nspecies; ++s) {

@@ -84,6 +84,19 @@ __host__ __device__ constexpr int window3_hx() { return 4; }
 __host__ __device__ constexpr int window3_w(int t) { return t + 3 + 2 * PIC3_MARGIN; }
 __host__ __device__ constexpr int window3_h() { return 1 + PIC3_MARGIN; }
 
+// Binned layout: the destination buffer of one species and the range counts.
+// Tile T owns slots [tile_start[T], tile_start[T + 1]) in both buffers; range
+// nt (after the last tile) is the overflow range.  A count may exceed its
+// range's size (the excess went to the overflow range): readers clamp it.
+template <typename R>
+struct Bin3 {
+    uint32_t *cell;
+    R *f[10];               // ox oy oz ux uy uz sx sy sz w
+    int32_t *id;
+    const int32_t *cnt_in;  // [nt + 1] particles per range of the source buffer
+    int32_t *cnt_out;       // [nt + 1] of the destination buffer, zero on entry
+};
+
 template <typename R>
 struct StepParams3 {
     MeshParams3<R> m;
@@ -92,6 +105,8 @@ struct StepParams3 {
     DevSpecies3<R> sp[PIC_MAXSP];
     unsigned *err;
     DiagParams diag;
+    Bin3<R> bin[PIC_MAXSP];  // binned layout only
+    int nextra;              // binned layout: CTAs of the overflow-range kernel
 };
 
 // Global-memory access to the 4 x 4 x 4 nodes [cell-1, cell+2] of one
@@ -272,4 +287,37 @@ __device__ __forceinline__ void deposit_esirkepov3(const M &m, int ix, int iy, i
             }
         }
     }
+}
+
+// Binned layout: warp-collective store of one particle per lane into the
+// range of its destination tile `dest` (-1: nothing to store).  Lanes with the
+// same destination reserve their slots with one atomic on the range count; a
+// slot past the range's end goes to the overflow range (tile_start[nt] ..
+// tile_start[nt + 1]); when that is full too the particle is dropped and
+// PIC_EF_BINS raised.  All 32 lanes of the warp must call it together.
+template <typename R>
+__device__ __forceinline__ void bin_store3(const Bin3<R> &B, const int32_t *tile_start, int nt, int dest,
+                                           uint32_t cell, const R v[10], int32_t id, unsigned *err) {
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, dest);
+    const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+    int base = 0;
+    if (lane == leader && dest >= 0) base = atomicAdd(&B.cnt_out[dest], __popc(peers));
+    base = __shfl_sync(0xFFFFFFFFu, base, leader);
+    if (dest < 0) return;
+    const int pos = base + __popc(peers & ((1u << lane) - 1u));
+    const int beg = tile_start[dest], cap = tile_start[dest + 1] - beg;
+    int slot = beg + pos;
+    if (pos >= cap) {
+        const int ob = tile_start[nt], ocap = tile_start[nt + 1] - ob;
+        const int op = atomicAdd(&B.cnt_out[nt], 1);
+        if (op >= ocap) {
+            atomicOr(err, PIC_EF_BINS);
+            return;
+        }
+        slot = ob + op;
+    }
+    B.cell[slot] = cell;
+#pragma unroll
+    for (int k = 0; k < 10; ++k) B.f[k][slot] = v[k];
+    B.id[slot] = id;
 }

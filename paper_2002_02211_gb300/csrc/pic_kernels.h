@@ -68,7 +68,7 @@ void laser_time_factors(const LaserParams &L, double t, double *fz, double *fy);
 // k_particles3.cu, k_fields3.cu (3D3V)
 bool fused3_tile_supported(int tx, int ty, int tz);
 template <typename R>
-cudaError_t launch_step_fused3(const StepParams3<R> &P, const CUtensorMap &tmapEB, cudaStream_t st);
+cudaError_t launch_step_fused3(const StepParams3<R> &P, const CUtensorMap &tmapEB, bool binned, cudaStream_t st);
 template <typename R>
 cudaError_t launch_push_split3(const StepParams3<R> &P, int s, int n_upper, cudaStream_t st);
 template <typename R>
@@ -81,10 +81,32 @@ void laser_profile3(const LaserParams &L, int ny, int nz, double dz, double *hos
 // k_sort.cu
 struct SortScratch {
     int32_t *cell_count, *cell_off;  // [ntiles * TX * TY]
-    int32_t *tile_R, *tile_total;    // [ntiles]
+    int32_t *tile_R, *tile_total;    // [ntiles], tile_total [ntiles + 1]
     int32_t *cursor;                 // [ntiles] scan scratch
     int32_t *rank;                   // [n]
 };
+// Binned 3D3V layout written by a sort (cnt_to == nullptr: compact layout).
+// Range T of tile T gets count + max(extra, count * pct / 100) slots rounded
+// up to 8; range ntiles (the overflow range) gets ovf_cap.  tile_start then
+// needs ntiles + 2 entries.
+struct BinSort {
+    int pct = 0, extra = 0, ovf_cap = 0;
+    int32_t *cnt_to = nullptr;    // [ntiles + 1] counts of the sorted buffer
+    int32_t *cnt_from = nullptr;  // [ntiles + 1] counts of the source buffer, cleared
+};
+// seal of the binned layout: spare slots of each range -> PIC_DEAD, and the
+// other buffer's range counts cleared
+struct SealSpecies {
+    uint32_t *cell;
+    const int32_t *tile_start;
+    const int32_t *cnt_new;
+    int32_t *cnt_zero;
+};
+struct SealArgs {
+    SealSpecies sp[PIC_MAXSP];
+    int nsp, nranges;
+};
+cudaError_t launch_seal_bins(const SealArgs &a, cudaStream_t st);
 cudaError_t launch_pack_cells(const int32_t *ix, const int32_t *iy, uint32_t *cell, int n,
                               int xlo, int xhi, int ny, unsigned *err, cudaStream_t st);
 cudaError_t launch_unpack_cells(const uint32_t *cell, int32_t *ix, int32_t *iy, int n,
@@ -100,7 +122,7 @@ cudaError_t launch_unpack_cells3(const uint32_t *cell, int32_t *ix, int32_t *iy,
 template <typename R>
 cudaError_t launch_tile_sort3(const DevSpecies3<R> &src, const DevSpecies3<R> &dst, const TileGeom3 &t,
                               const SortScratch &w, int32_t *tile_start, int32_t *n_tmp, int n_upper,
-                              cudaStream_t st);
+                              const BinSort &bins, cudaStream_t st);
 template <typename R>
 cudaError_t launch_shift_rows(const R *src, R *dst, size_t rows, int nx, int ld, int n, cudaStream_t st);
 template <typename R>

@@ -8,10 +8,10 @@ import workloads as W
 
 
 def make_pair(wl, fields=None, step=0, capacity_factor=1.0, sort_every=0, tile=None, parts=None,
-              precision=32):
+              precision=32, bins=None):
     parts = W.generate_particles(wl) if parts is None else parts
     cfg = pic.config_from_workload(wl, capacity_factor=capacity_factor, sort_every=sort_every, tile=tile,
-                                   precision=precision)
+                                   precision=precision, bins=bins)
     sim = pic.Simulation(cfg)
     for s, d in enumerate(parts):
         sim.set_particles(s, d)

@@ -75,3 +75,28 @@ def test_validate_config_rejects_bad_tiles_and_species():
     cfg = pic.config_from_workload(W.small_case())
     cfg.sp[0].capacity = -5
     assert _status(cfg) == -1
+
+
+def test_validate_config_binned_layout():
+    # binned layout: 3D3V only, headroom in [0, 400] %, spare slots in [0, 4096]
+    cfg = pic.config_from_workload(W.small_case3(), bins=(25, 16))
+    assert _status(cfg) == 0
+    for field, value in (("bin_headroom_pct", -1), ("bin_headroom_pct", 401), ("bin_min_extra", -1),
+                         ("bin_min_extra", 5000)):
+        bad = pic.config_from_workload(W.small_case3(), bins=(25, 16))
+        setattr(bad, field, value)
+        assert _status(bad) == -1, field
+    cfg2 = pic.config_from_workload(W.small_case())
+    cfg2.bin_headroom_pct = 25
+    assert _status(cfg2) == -1
+
+
+def test_bin_capacity_covers_the_range_bound():
+    # the binding's capacity for the binned layout holds the library's bound:
+    # every tile range at count * (1 + pct/100) + extra + 7, plus the overflow range
+    wl = W.small_case3(nx=40, ny=16, nz=12, ppc=2)
+    cfg = pic.config_from_workload(wl, bins=(25, 16))
+    n = 2 * (wl.nx - 4) * wl.ny * wl.nz
+    ntiles = -(-wl.nx // 16) * -(-wl.ny // 4) * -(-wl.nz // 4)
+    bound = n + n * 25 // 100 + ntiles * (16 + 7) + ((max(1024, n // 64) + 7) // 8) * 8
+    assert cfg.sp[0].capacity >= bound

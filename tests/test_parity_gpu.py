@@ -213,7 +213,10 @@ def test_config1_full_run_statistics():
     orc.step(wl.steps)
     gm = sim.polarization(0)
     om = orc.moments(0)
-    assert gm["count"] == om[4]
+    # FP32 and FP64 trajectories part over 400 steps in the laser field, and
+    # the float current sums in arbitrary order: a particle at the open x end
+    # can leave a step earlier or later, so the live counts agree to 1e-4
+    assert abs(gm["count"] - om[4]) <= max(2.0, 1e-4 * om[4])
     assert np.abs(gm["P"] - om[:3]).max() < 0.01
     assert gm["ekin_mean"] == pytest.approx(om[5], rel=0.01)
     assert gm["ekin_var"] == pytest.approx(om[6], rel=0.01)
