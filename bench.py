@@ -68,6 +68,10 @@ CPU_SAMPLE = {2: {"ny": 32}, 3: {"nz": 4}}
 REF_SAMPLE = {2: {"ny": 32}, 3: {"ny": 32, "nz": 4}}
 CPU_SAMPLE_STEPS = 6
 DEFAULT_SORT_EVERY = {2: 32, 3: 2}
+# 3D3V runs the binned layout by default (headroom %, least spare slots per
+# tile range), re-binned every DEFAULT_REBIN_EVERY steps
+DEFAULT_BINS = (25, 16)
+DEFAULT_REBIN_EVERY = 64
 KERNEL = {2: ("k_step_fused", ("k_particles.cu", "pic_device.cuh", "pic_ptx.cuh")),
           3: ("k_step_fused3", ("k_particles3.cu", "pic_device3.cuh", "pic_device.cuh", "pic_ptx.cuh"))}
 
@@ -86,7 +90,9 @@ def parse(argv=None):
     ap.add_argument("--diag-every", type=int, default=10)
     ap.add_argument("--tile", type=int, nargs="+", default=None)
     ap.add_argument("--bins", type=int, nargs=2, default=None, metavar=("PCT", "EXTRA"),
-                    help="3D3V binned layout: headroom percent and least spare slots per tile range")
+                    help="3D3V binned layout: headroom percent and least spare slots per tile range "
+                         "(default 25 16)")
+    ap.add_argument("--compact", action="store_true", help="3D3V: the compact layout with periodic tile sorts")
     ap.add_argument("--ny", type=int, default=0, help="smaller ny for profiling captures")
     ap.add_argument("--nz", type=int, default=0, help="smaller nz (3D3V) for profiling captures")
     ap.add_argument("--precision", type=int, choices=[32, 64], default=32)
@@ -343,14 +349,16 @@ def main_ours(args):
     dev = torch.device("cuda", local)
     wl = workload(args.workload, args.ny, args.nz)
     dim = wl.dim
+    bins = None
+    if dim == 3 and not args.compact:
+        bins = tuple(args.bins) if args.bins else DEFAULT_BINS
     if args.sort_every <= 0:
-        args.sort_every = DEFAULT_SORT_EVERY[dim]
+        args.sort_every = DEFAULT_REBIN_EVERY if bins else DEFAULT_SORT_EVERY[dim]
     parts = W.generate_particles(wl)
     n_particles = sum(len(p["ix"]) for p in parts)
     cells = n_cells(wl)
 
     stream = torch.cuda.Stream(device=dev)
-    bins = args.bins if dim == 3 else None
     cfg = pic.config_from_workload(wl, sort_every=args.sort_every, tile=args.tile,
                                    precision=args.precision, bins=bins)
     sim = pic.Simulation(cfg, stream=stream)
