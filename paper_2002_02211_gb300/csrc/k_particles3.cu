@@ -30,7 +30,7 @@ __device__ __forceinline__ bool finish_move3(const MeshParams3<R> &m, int &ix1, 
 
 constexpr int kThreads3 = 256;
 #ifndef PIC3_MINB
-#define PIC3_MINB 3  // resident CTAs per SM the register budget of the FP32 kernel is sized for
+#define PIC3_MINB 4  // most resident CTAs per SM the register budget of the FP32 kernel is sized for
 #endif
 #ifndef PIC3_ACC
 #define PIC3_ACC 0   // 1: sum the in-cell currents of a cell's consecutive particles in registers
@@ -49,9 +49,14 @@ struct TileConst3 {
     // and kept)
     static constexpr size_t smem_bytes =
         (size_t)(6 * FA + 3 * WA) * sizeof(R) + kThreads3 * (3 * sizeof(uint32_t) + kRec3 * sizeof(R));
-    // resident CTAs per SM the register budget is sized for: three while three
-    // fit in shared memory (float), else two; the FP64 instantiation takes one
-    static constexpr int minb = sizeof(R) == 8 ? 1 : (smem_bytes <= 74 * 1024 ? PIC3_MINB : 2);
+    // resident CTAs per SM the register budget is sized for: as many as fit
+    // in the SM's 228 KB of shared memory (1 KB reserved per CTA, plus the
+    // static arrays), at most PIC3_MINB, at least two; the FP64 instantiation
+    // takes one.  At 2 particles per cell the kernel is latency bound, and a
+    // fourth CTA (64 registers, a few spilled) beats three (80 registers).
+    static constexpr int smem_ctas = (int)(228 * 1024 / (smem_bytes + 2048));
+    static constexpr int minb =
+        sizeof(R) == 8 ? 1 : (smem_ctas >= PIC3_MINB ? PIC3_MINB : (smem_ctas >= 3 ? 3 : 2));
 };
 
 template <typename R, int WX, int WY, int WA, int FX, int FA>
@@ -137,8 +142,8 @@ __global__ void __launch_bounds__(kThreads3) k_overflow3(const StepParams3<R> P)
     for (int sp = 0; sp < P.nsp; ++sp) {
         const DevSpecies3<R> &S = P.sp[sp];
         if (!S.mobile) continue;
-        const int ob = S.tile_start[nt];
-        const int len = min(P.bin[sp].cnt_in[nt], S.tile_start[nt + 1] - ob);
+        const BinRange rg = bin_range(S.tile_start, P.bin[sp].cnt_in, nt + 1, nt);
+        const int len = rg.len;
         R dacc[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
         const R dlo = (R)P.diag.lo[sp], dhi = (R)P.diag.hi[sp], dm = (R)P.diag.m_mev[sp];
         const R dshift = diag ? (R)P.diag.shift[sp] : R(0);
@@ -150,9 +155,9 @@ __global__ void __launch_bounds__(kThreads3) k_overflow3(const StepParams3<R> P)
 #pragma unroll
             for (int q = 0; q < 10; ++q) v[q] = R(0);
             int32_t id = 0;
-            const uint32_t c = k < len ? S.cell[ob + k] : PIC_DEAD;
+            const int slot = k < len ? bin_slot(rg, k) : 0;
+            const uint32_t c = k < len ? S.cell[slot] : PIC_DEAD;
             if (c != PIC_DEAD) {
-                const int slot = ob + k;
                 int ix, iy, iz;
                 unpack_cell3(c, ix, iy, iz);
                 const R ox = S.ox[slot], oy = S.oy[slot], oz = S.oz[slot], w = S.w[slot];
@@ -187,7 +192,7 @@ __global__ void __launch_bounds__(kThreads3) k_overflow3(const StepParams3<R> P)
                     id = S.id[slot];
                 }
             }
-            bin_store3(P.bin[sp], S.tile_start, nt, dest, cw, v, id, P.err);
+            bin_store3(P.bin[sp], S.tile_start, nt, -1, nullptr, dest, cw, v, id, P.err);
         }
         if (diag) store_diag_rows3(P.diag, sp, dacc, sdiag, nt + blockIdx.x, nt + P.nextra);
     }
@@ -221,6 +226,7 @@ __global__ void __launch_bounds__(kThreads3, (TileConst3<TX, TY, TZ, R>::minb))
     extern __shared__ __align__(1024) unsigned char dsm[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ double sdiag[kThreads3 / 32][8];
+    __shared__ int s_front[PIC_MAXSP];  // binned layout: stayers stored per species
     R *sF = reinterpret_cast<R *>(dsm);
     R *sJ = sF + 6 * FA;
     R *ring = sJ + 3 * WA;                                                // [kRec3][kThreads3]
@@ -262,15 +268,14 @@ __global__ void __launch_bounds__(kThreads3, (TileConst3<TX, TY, TZ, R>::minb))
         }
         cp_async_commit();
     };
-    // slots of this tile: [beg, beg + len)
-    auto range = [&](int sp, int &beg, int &len) {
+    // the particles of this tile: bin_slot(range, k), k < range.len
+    auto range = [&](int sp) {
         const DevSpecies3<R> &S = P.sp[sp];
-        beg = S.tile_start[tile];
-        const int size = S.tile_start[tile + 1] - beg;
-        if constexpr (BIN)
-            len = min(P.bin[sp].cnt_in[tile], size);
-        else
-            len = size;
+        if constexpr (BIN) return bin_range(S.tile_start, P.bin[sp].cnt_in, (int)gridDim.x + 1, tile);
+        BinRange b;
+        b.beg = S.tile_start[tile];
+        b.len = b.front = b.split = S.tile_start[tile + 1] - b.beg;
+        return b;
     };
 
     const bool diag = P.diag.on != 0;
@@ -278,11 +283,11 @@ __global__ void __launch_bounds__(kThreads3, (TileConst3<TX, TY, TZ, R>::minb))
     for (int sp = 0; sp < P.nsp && first < 0; ++sp)
         if (P.sp[sp].mobile) first = sp;
     if (first >= 0) {
-        int beg, len;
-        range(first, beg, len);
-        prefetch(P.sp[first], beg + tid, tid < len);
+        const BinRange rg = range(first);
+        prefetch(P.sp[first], tid < rg.len ? bin_slot(rg, tid) : 0, tid < rg.len);
     }
     for (int i = tid; i < 3 * WA; i += kThreads3) sJ[i] = R(0);
+    if (tid < PIC_MAXSP) s_front[tid] = 0;
     __syncthreads();
     if (!mbar_wait_bounded(&bar, 0)) {
         if (tid == 0) atomicOr(P.err, PIC_EF_TIMEOUT);
@@ -323,8 +328,8 @@ __global__ void __launch_bounds__(kThreads3, (TileConst3<TX, TY, TZ, R>::minb))
     for (int sp = 0; sp < P.nsp; ++sp) {
         const DevSpecies3<R> &S = P.sp[sp];
         if (!S.mobile) continue;
-        int beg, len;
-        range(sp, beg, len);
+        const BinRange rg = range(sp);
+        const int len = rg.len;
         const R qm = S.qm, a = S.a, q = S.q;
         R dacc[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
         R dlo = R(0), dhi = R(0), dm = R(0), dshift = R(0);
@@ -334,7 +339,7 @@ __global__ void __launch_bounds__(kThreads3, (TileConst3<TX, TY, TZ, R>::minb))
             dm = (R)P.diag.m_mev[sp];
             dshift = (R)P.diag.shift[sp];
         }
-        if (sp != first) prefetch(S, beg + tid, tid < len);
+        if (sp != first) prefetch(S, tid < len ? bin_slot(rg, tid) : 0, tid < len);
         for (int k0 = 0; k0 < len; k0 += kThreads3) {
             const int k = k0 + tid;
             cp_async_wait0();
@@ -347,7 +352,7 @@ __global__ void __launch_bounds__(kThreads3, (TileConst3<TX, TY, TZ, R>::minb))
                 for (int q10 = 0; q10 < 10; ++q10) bv[q10] = R(0);
             }
             if (k < len) {
-                const int slot = beg + k;
+                const int slot = rg.beg + k;  // compact layout (in-place rewrite)
                 const R *r = ring0;
                 const uint32_t c = cring[tid];
                 const R ox = r[0 * kThreads3], oy = r[1 * kThreads3], oz = r[2 * kThreads3];
@@ -356,7 +361,7 @@ __global__ void __launch_bounds__(kThreads3, (TileConst3<TX, TY, TZ, R>::minb))
                 const R w = r[9 * kThreads3];
                 if constexpr (BIN) idkeep[tid] = iring[tid];  // the ring slot is reused below
                 // the slot is free again: request the next record
-                prefetch(S, beg + k + kThreads3, k + kThreads3 < len);
+                prefetch(S, k + kThreads3 < len ? bin_slot(rg, k + kThreads3) : 0, k + kThreads3 < len);
                 if (c != PIC_DEAD) {
                     int ix, iy, iz;
                     unpack_cell3(c, ix, iy, iz);
@@ -435,7 +440,8 @@ __global__ void __launch_bounds__(kThreads3, (TileConst3<TX, TY, TZ, R>::minb))
                 }
             }
             if constexpr (BIN)
-                bin_store3(P.bin[sp], S.tile_start, (int)gridDim.x, dest, bcell, bv, idkeep[tid], P.err);
+                bin_store3(P.bin[sp], S.tile_start, (int)gridDim.x, tile, &s_front[sp], dest, bcell, bv, idkeep[tid],
+                           P.err);
         }
         cp_async_wait0();
         if (diag)  // diagnostic columns: the tiles, then (binned) the overflow CTAs
@@ -444,6 +450,14 @@ __global__ void __launch_bounds__(kThreads3, (TileConst3<TX, TY, TZ, R>::minb))
     acc_flush();
     if (bad) atomicOr(P.err, PIC_EF_NAN);
     __syncthreads();
+    if constexpr (BIN) {
+        // the destination range of this tile: its stayers, and where its arrivals start
+        if (tid < P.nsp && P.sp[tid].mobile) {
+            const int nr = (int)gridDim.x + 1;
+            P.bin[tid].cnt_out[tile] = s_front[tid];
+            P.bin[tid].cnt_out[nr + tile] = range(tid).len;
+        }
+    }
 
     // current window -> J: rows outside the mesh and all-zero groups skipped
     if constexpr (sizeof(R) == 4) {

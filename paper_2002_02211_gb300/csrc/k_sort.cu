@@ -137,13 +137,17 @@ __global__ void __launch_bounds__(1024) k_layout(const int32_t *cell_count, int 
         const int total = R * C + base + incl;
         tile_R[t] = R;
         if (bins.cnt_to) {
-            // binned layout: the range holds the tile's particles and its spare
-            // slots; the range after the last tile is the overflow range
+            // binned layout: the range holds the tile's particles (one front
+            // segment) and its spare slots; the range after the last tile is
+            // the overflow range
+            const int nr = gridDim.x + 1;
             bins.cnt_to[t] = total;
+            bins.cnt_to[nr + t] = total;
+            bins.cnt_to[2 * nr + t] = 0;
             const int spare = max(bins.extra, (int)((long long)total * bins.pct / 100));
             tile_total[t] = (total + spare + 7) / 8 * 8;
             if (t == 0) {
-                bins.cnt_to[gridDim.x] = 0;
+                bins.cnt_to[gridDim.x] = bins.cnt_to[nr + gridDim.x] = bins.cnt_to[2 * nr + gridDim.x] = 0;
                 tile_total[gridDim.x] = bins.ovf_cap;
             }
         } else {
@@ -303,17 +307,22 @@ cudaError_t launch_unpack_cells3(const uint32_t *cell, int32_t *ix, int32_t *iy,
     return cudaGetLastError();
 }
 
-// Binned layout: one warp per range writes PIC_DEAD into the range's spare
-// slots (past its count) and clears the other buffer's count of the range.
+// Binned layout: one warp per range writes PIC_DEAD into the slots of the
+// range outside its two segments, records the range's arrival base for the
+// next step, and clears the other buffer's front / split / back counters.
 __global__ void __launch_bounds__(256) k_seal_bins(const SealArgs a) {
-    const int r = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (r >= a.nranges) return;
+    const int r = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31, nr = a.nranges;
+    if (r >= nr) return;
     for (int s = 0; s < a.nsp; ++s) {
         const SealSpecies &S = a.sp[s];
-        const int beg = S.tile_start[r], end = S.tile_start[r + 1];
-        const int n = min(S.cnt_new[r], end - beg);
-        for (int i = beg + n + lane; i < end; i += 32) S.cell[i] = PIC_DEAD;
-        if (lane == 0 && S.cnt_zero) S.cnt_zero[r] = 0;
+        const BinRange b = bin_range(S.tile_start, S.cnt_new, nr, r);
+        const int end = S.tile_start[r + 1], back_end = b.beg + b.split + (b.len - b.front);
+        for (int i = b.beg + b.front + lane; i < b.beg + b.split; i += 32) S.cell[i] = PIC_DEAD;
+        for (int i = back_end + lane; i < end; i += 32) S.cell[i] = PIC_DEAD;
+        if (lane == 0) {
+            S.cnt_new[3 * nr + r] = b.beg + b.len;
+            if (S.cnt_zero) S.cnt_zero[r] = S.cnt_zero[nr + r] = S.cnt_zero[2 * nr + r] = 0;
+        }
     }
 }
 

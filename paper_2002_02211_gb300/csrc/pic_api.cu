@@ -73,8 +73,9 @@ struct Ctx {
     long long adj_n[PIC_MAX_SPECIES] = {};
     bool has_background = false;  // pic_capture_background was called
     // binned 3D3V layout (bin_headroom_pct > 0): per mobile species the range
-    // counts of both buffers, whether the species is in that layout now, and a
-    // host bound on its live particles (sizes the ranges against capacity)
+    // counters of both buffers (front, split, back, arrival base per range, Bin3), whether
+    // the species is in that layout now, and a host bound on its live
+    // particles (sizes the ranges against capacity)
     bool binned = false;
     bool sp_binned[PIC_MAX_SPECIES] = {};
     int32_t *bin_cnt[PIC_MAX_SPECIES][2] = {};
@@ -621,8 +622,8 @@ pic_status_t pic_create(const pic_config_t *cfg, void *stream, void **ctx_out) {
         CKC(cudaMemsetAsync(c->tile_start[s], 0, (c->ntiles + 2) * sizeof(int32_t), st));
         if (c->binned && cfg->sp[s].mobile)
             for (int b = 0; b < 2; ++b) {
-                CKC(cudaMalloc(&c->bin_cnt[s][b], (c->ntiles + 1) * sizeof(int32_t)));
-                CKC(cudaMemsetAsync(c->bin_cnt[s][b], 0, (c->ntiles + 1) * sizeof(int32_t), st));
+                CKC(cudaMalloc(&c->bin_cnt[s][b], 4 * (c->ntiles + 1) * sizeof(int32_t)));
+                CKC(cudaMemsetAsync(c->bin_cnt[s][b], 0, 4 * (c->ntiles + 1) * sizeof(int32_t), st));
             }
     }
     CKC(cudaMalloc(&c->tile_count, (c->ntiles + 1) * sizeof(int32_t)));

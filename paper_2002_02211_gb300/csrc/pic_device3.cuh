@@ -84,18 +84,43 @@ __host__ __device__ constexpr int window3_hx() { return 4; }
 __host__ __device__ constexpr int window3_w(int t) { return t + 3 + 2 * PIC3_MARGIN; }
 __host__ __device__ constexpr int window3_h() { return 1 + PIC3_MARGIN; }
 
-// Binned layout: the destination buffer of one species and the range counts.
-// Tile T owns slots [tile_start[T], tile_start[T + 1]) in both buffers; range
-// nt (after the last tile) is the overflow range.  A count may exceed its
-// range's size (the excess went to the overflow range): readers clamp it.
+// Binned layout.  Tile T owns slots [tile_start[T], tile_start[T + 1]) in
+// both particle buffers; range nt (after the last tile) is the overflow range.
+// In one buffer a range holds two segments: the particles that stayed in the
+// tile, [beg, beg + front), and the ones that arrived from other tiles,
+// [beg + split, beg + split + back), split being the range's particle count
+// in the buffer it was stepped from.  Counters per buffer, nr = nt + 1
+// ranges: cnt[r] front, cnt[nr + r] split, cnt[2 nr + r] back, and
+// cnt[3 nr + r] = beg + front + back, the first slot a step reading this
+// buffer gives to arrivals (written by the seal).  back may exceed the room
+// after split (the excess went to the overflow range): readers clamp it.
 template <typename R>
 struct Bin3 {
-    uint32_t *cell;
+    uint32_t *cell;         // destination buffer
     R *f[10];               // ox oy oz ux uy uz sx sy sz w
     int32_t *id;
-    const int32_t *cnt_in;  // [nt + 1] particles per range of the source buffer
-    int32_t *cnt_out;       // [nt + 1] of the destination buffer, zero on entry
+    const int32_t *cnt_in;  // [4 nr] counters of the source buffer
+    int32_t *cnt_out;       // [4 nr] of the destination buffer, front / split / back zero on entry
 };
+
+struct BinRange {
+    int beg, front, split, len;
+};
+
+__device__ __forceinline__ BinRange bin_range(const int32_t *tile_start, const int32_t *cnt, int nr, int r) {
+    BinRange b;
+    b.beg = tile_start[r];
+    const int cap = tile_start[r + 1] - b.beg;
+    b.front = cnt[r];
+    b.split = cnt[nr + r];
+    b.len = b.front + max(0, min(cnt[2 * nr + r], cap - b.split));
+    return b;
+}
+
+// slot of the k-th particle of a range (k < len)
+__device__ __forceinline__ int bin_slot(const BinRange &b, int k) {
+    return k < b.front ? b.beg + k : b.beg + b.split + (k - b.front);
+}
 
 template <typename R>
 struct StepParams3 {
@@ -290,32 +315,59 @@ __device__ __forceinline__ void deposit_esirkepov3(const M &m, int ix, int iy, i
 }
 
 // Binned layout: warp-collective store of one particle per lane into the
-// range of its destination tile `dest` (-1: nothing to store).  Lanes with the
-// same destination reserve their slots with one atomic on the range count; a
-// slot past the range's end goes to the overflow range (tile_start[nt] ..
-// tile_start[nt + 1]); when that is full too the particle is dropped and
-// PIC_EF_BINS raised.  All 32 lanes of the warp must call it together.
+// range of its destination tile `dest` (-1: nothing to store).  Stayers (dest
+// == tile, the storing CTA's own tile) take the next slots of the range's front
+// through the CTA's shared-memory counter *s_front; arrivals take slots from
+// the range's arrival base on, lanes with one destination reserving them with
+// one global atomic (all destinations of the warp in one round trip).  An
+// arrival past the range's end goes to the overflow range; when that is full
+// too the particle is dropped and PIC_EF_BINS raised.  tile = -1 (the
+// overflow-range kernel): every particle is an arrival.  All 32 lanes of the
+// warp must call it together.
 template <typename R>
-__device__ __forceinline__ void bin_store3(const Bin3<R> &B, const int32_t *tile_start, int nt, int dest,
-                                           uint32_t cell, const R v[10], int32_t id, unsigned *err) {
-    const unsigned peers = __match_any_sync(0xFFFFFFFFu, dest);
-    const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
-    int base = 0;
-    if (lane == leader && dest >= 0) base = atomicAdd(&B.cnt_out[dest], __popc(peers));
-    base = __shfl_sync(0xFFFFFFFFu, base, leader);
-    if (dest < 0) return;
-    const int pos = base + __popc(peers & ((1u << lane) - 1u));
-    const int beg = tile_start[dest], cap = tile_start[dest + 1] - beg;
-    int slot = beg + pos;
-    if (pos >= cap) {
-        const int ob = tile_start[nt], ocap = tile_start[nt + 1] - ob;
-        const int op = atomicAdd(&B.cnt_out[nt], 1);
-        if (op >= ocap) {
-            atomicOr(err, PIC_EF_BINS);
-            return;
-        }
-        slot = ob + op;
+__device__ __forceinline__ void bin_store3(const Bin3<R> &B, const int32_t *tile_start, int nt, int tile,
+                                           int *s_front, int dest, uint32_t cell, const R v[10], int32_t id,
+                                           unsigned *err) {
+    constexpr unsigned kAll = 0xFFFFFFFFu;
+    const int nr = nt + 1, lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    const bool stayer = dest >= 0 && dest == tile;
+    int slot = -1;
+    const unsigned stay = __ballot_sync(kAll, stayer);
+    if (stay) {
+        const int leader = __ffs(stay) - 1;
+        int b = 0;
+        if (lane == leader) b = atomicAdd(s_front, __popc(stay));
+        b = __shfl_sync(kAll, b, leader);
+        if (stayer) slot = tile_start[tile] + b + __popc(stay & below);
     }
+    const int arr = dest >= 0 && !stayer ? dest : -1;
+    if (__any_sync(kAll, arr >= 0)) {
+        const unsigned peers = __match_any_sync(kAll, arr);
+        const int leader = __ffs(peers) - 1;
+        int b = 0;
+        int base = 0, end = 0;
+        if (arr >= 0) {
+            base = B.cnt_in[3 * nr + arr];
+            end = tile_start[arr + 1];
+            if (lane == leader) b = atomicAdd(&B.cnt_out[2 * nr + arr], __popc(peers));
+        }
+        b = __shfl_sync(kAll, b, leader);
+        if (arr >= 0) {
+            const int s = base + b + __popc(peers & below);
+            if (s < end) {
+                slot = s;
+            } else {
+                const int ob = tile_start[nt], ocap = tile_start[nt + 1] - ob;
+                const int op = atomicAdd(&B.cnt_out[2 * nr + nt], 1);
+                if (op < ocap)
+                    slot = ob + op;
+                else
+                    atomicOr(err, PIC_EF_BINS);
+            }
+        }
+    }
+    if (slot < 0) return;
     B.cell[slot] = cell;
 #pragma unroll
     for (int k = 0; k < 10; ++k) B.f[k][slot] = v[k];

@@ -91,15 +91,15 @@ struct SortScratch {
 // needs ntiles + 2 entries.
 struct BinSort {
     int pct = 0, extra = 0, ovf_cap = 0;
-    int32_t *cnt_to = nullptr;    // [ntiles + 1] counts of the sorted buffer
-    int32_t *cnt_from = nullptr;  // [ntiles + 1] counts of the source buffer, cleared
+    int32_t *cnt_to = nullptr;    // [4 (ntiles + 1)] range counters (Bin3) of the sorted buffer
+    int32_t *cnt_from = nullptr;  // [4 (ntiles + 1)] of the source buffer, cleared
 };
-// seal of the binned layout: spare slots of each range -> PIC_DEAD, and the
-// other buffer's range counts cleared
+// seal of the binned layout: slots outside each range's two segments ->
+// PIC_DEAD, and the other buffer's range counters cleared
 struct SealSpecies {
     uint32_t *cell;
     const int32_t *tile_start;
-    const int32_t *cnt_new;
+    int32_t *cnt_new;
     int32_t *cnt_zero;
 };
 struct SealArgs {
