@@ -216,9 +216,10 @@ __global__ void __launch_bounds__(kThreads3) k_overflow3(const StepParams3<R> P)
 // tile sorts).  BIN = true (binned layout): tile T reads the first cnt_in[T]
 // slots of its range and every surviving particle is stored into the range of
 // the tile its new cell lies in, in the other buffer (bin_store3);
-// k_overflow3 runs the overflow range.
+// k_overflow3 runs the overflow range.  DIAG: the step accumulates the Eq. (4)
+// sums (the instantiation without them keeps their registers free).
 // ---------------------------------------------------------------------------
-template <int TX, int TY, int TZ, typename R, bool BIN>
+template <int TX, int TY, int TZ, typename R, bool BIN, bool DIAG>
 __global__ void __launch_bounds__(kThreads3, (TileConst3<TX, TY, TZ, R>::minb))
     k_step_fused3(const StepParams3<R> P, const __grid_constant__ CUtensorMap tmapEB) {
     using TC = TileConst3<TX, TY, TZ, R>;
@@ -278,7 +279,7 @@ __global__ void __launch_bounds__(kThreads3, (TileConst3<TX, TY, TZ, R>::minb))
         return b;
     };
 
-    const bool diag = P.diag.on != 0;
+    constexpr bool diag = DIAG;  // Eq. (4) sums on this step (a separate instantiation)
     int first = -1;
     for (int sp = 0; sp < P.nsp && first < 0; ++sp)
         if (P.sp[sp].mobile) first = sp;
@@ -567,7 +568,7 @@ __global__ void __launch_bounds__(256) k_deposit_split3(const StepParams3<R> P, 
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-template <int TX, int TY, int TZ, typename R, bool BIN>
+template <int TX, int TY, int TZ, typename R, bool BIN, bool DIAG>
 static cudaError_t launch_fused3_t(const StepParams3<R> &P, const CUtensorMap &tmapEB, cudaStream_t st) {
     using TC = TileConst3<TX, TY, TZ, R>;
     constexpr size_t smem = TC::smem_bytes;
@@ -577,12 +578,12 @@ static cudaError_t launch_fused3_t(const StepParams3<R> &P, const CUtensorMap &t
     if (BIN && P.nextra < 1) return cudaErrorInvalidValue;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_step_fused3<TX, TY, TZ, R, BIN>,
+        cudaError_t e = cudaFuncSetAttribute(k_step_fused3<TX, TY, TZ, R, BIN, DIAG>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    k_step_fused3<TX, TY, TZ, R, BIN><<<P.t.ntx * P.t.nty * P.t.ntz, kThreads3, smem, st>>>(P, tmapEB);
+    k_step_fused3<TX, TY, TZ, R, BIN, DIAG><<<P.t.ntx * P.t.nty * P.t.ntz, kThreads3, smem, st>>>(P, tmapEB);
     if (BIN) {
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -594,8 +595,12 @@ static cudaError_t launch_fused3_t(const StepParams3<R> &P, const CUtensorMap &t
 template <int TX, int TY, int TZ, typename R>
 static cudaError_t launch_fused3_b(const StepParams3<R> &P, const CUtensorMap &tmapEB, bool binned,
                                    cudaStream_t st) {
-    return binned ? launch_fused3_t<TX, TY, TZ, R, true>(P, tmapEB, st)
-                  : launch_fused3_t<TX, TY, TZ, R, false>(P, tmapEB, st);
+    const bool diag = P.diag.on != 0;
+    if (binned)
+        return diag ? launch_fused3_t<TX, TY, TZ, R, true, true>(P, tmapEB, st)
+                    : launch_fused3_t<TX, TY, TZ, R, true, false>(P, tmapEB, st);
+    return diag ? launch_fused3_t<TX, TY, TZ, R, false, true>(P, tmapEB, st)
+                : launch_fused3_t<TX, TY, TZ, R, false, false>(P, tmapEB, st);
 }
 
 bool fused3_tile_supported(int tx, int ty, int tz) {
