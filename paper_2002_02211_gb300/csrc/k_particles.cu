@@ -55,6 +55,11 @@ struct TileConst {
     // field window, current window, and a two-stage ring of cell words and reals
     static constexpr size_t smem_bytes =
         (size_t)9 * WA * sizeof(R) + 2 * kFusedThreads * (sizeof(uint32_t) + kRec * sizeof(R));
+    // resident CTAs per SM the register budget of the single-run kernel is
+    // sized for: without the in-step Eq. (4) sums a fourth CTA where four fit
+    // in shared memory (228 KB, 1 KB reserved per CTA), else PIC_FUSED_MINB
+    static constexpr int minb_nodiag =
+        sizeof(R) == 8 ? 2 : ((int)(228 * 1024 / (smem_bytes + 2048)) >= 4 ? 4 : PIC_FUSED_MINB);
 };
 
 template <typename R, int WX, int WA>
@@ -85,7 +90,7 @@ __device__ __forceinline__ void flush_add<double>(double *dst, const double *src
 // is an initialised mbarrier whose current phase has parity `phase`; `ntiles`
 // is the run's tile count (the stride of the diagnostic rows).  Returns false
 // if the window wait gave up.
-template <int TX, int TY, typename R>
+template <int TX, int TY, typename R, bool DIAG = true>
 __device__ __forceinline__ bool fused_tile(const StepParams<R> &P, const CUtensorMap *tmap, const int tile,
                                            const int ntiles, uint64_t &bar, const unsigned phase,
                                            unsigned char *dsm, double (*sdiag)[8]) {
@@ -127,7 +132,7 @@ __device__ __forceinline__ bool fused_tile(const StepParams<R> &P, const CUtenso
 
     // Eq. (4) diagnostic sums of one species: float per thread (at most
     // total/256 particles each), then double across the CTA (sdiag)
-    const bool diag = P.diag.on != 0;
+    const bool diag = DIAG && P.diag.on != 0;  // DIAG = false: the sums are compiled out
 
     // the first record of the first mobile species is requested before the
     // window wait, so both latencies overlap
@@ -299,8 +304,9 @@ __device__ __forceinline__ bool fused_tile(const StepParams<R> &P, const CUtenso
     return true;
 }
 
-template <int TX, int TY, typename R>
-__global__ void __launch_bounds__(kFusedThreads, sizeof(R) == 4 ? PIC_FUSED_MINB : 2)
+template <int TX, int TY, typename R, bool DIAG>
+__global__ void __launch_bounds__(kFusedThreads,
+                                  DIAG ? (sizeof(R) == 4 ? PIC_FUSED_MINB : 2) : TileConst<TX, TY, R>::minb_nodiag)
     k_step_fused(const __grid_constant__ StepParams<R> P, const __grid_constant__ CUtensorMap tmapEB) {
     extern __shared__ __align__(1024) unsigned char dsm[];
     __shared__ __align__(8) uint64_t bar;
@@ -311,7 +317,7 @@ __global__ void __launch_bounds__(kFusedThreads, sizeof(R) == 4 ? PIC_FUSED_MINB
     }
     // (fused_tile's barrier after clearing the current window orders the
     // initialisation before every other thread's first wait)
-    fused_tile<TX, TY, R>(P, &tmapEB, blockIdx.x, gridDim.x, bar, 0u, dsm, sdiag);
+    fused_tile<TX, TY, R, DIAG>(P, &tmapEB, blockIdx.x, gridDim.x, bar, 0u, dsm, sdiag);
 }
 
 // ---------------------------------------------------------------------------
@@ -419,20 +425,27 @@ __global__ void __launch_bounds__(256) k_deposit_split(const StepParams<R> P, in
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-template <int TX, int TY, typename R>
-static cudaError_t launch_fused_t(const StepParams<R> &P, const CUtensorMap &tmapEB, cudaStream_t st) {
+template <int TX, int TY, typename R, bool DIAG>
+static cudaError_t launch_fused_d(const StepParams<R> &P, const CUtensorMap &tmapEB, cudaStream_t st) {
     using TC = TileConst<TX, TY, R>;
     constexpr size_t smem = TC::smem_bytes;
-    if (P.t.WX != TC::WX || P.t.WY != TC::WY || P.t.HX != TC::HX || P.t.HY != TC::HY) return cudaErrorInvalidValue;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_step_fused<TX, TY, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_step_fused<TX, TY, R, DIAG>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    k_step_fused<TX, TY, R><<<P.t.ntx * P.t.nty, kFusedThreads, smem, st>>>(P, tmapEB);
+    k_step_fused<TX, TY, R, DIAG><<<P.t.ntx * P.t.nty, kFusedThreads, smem, st>>>(P, tmapEB);
     return cudaGetLastError();
+}
+
+// steps with in-step Eq. (4) sums run their own instantiation
+template <int TX, int TY, typename R>
+static cudaError_t launch_fused_t(const StepParams<R> &P, const CUtensorMap &tmapEB, cudaStream_t st) {
+    using TC = TileConst<TX, TY, R>;
+    if (P.t.WX != TC::WX || P.t.WY != TC::WY || P.t.HX != TC::HX || P.t.HY != TC::HY) return cudaErrorInvalidValue;
+    return P.diag.on ? launch_fused_d<TX, TY, R, true>(P, tmapEB, st) : launch_fused_d<TX, TY, R, false>(P, tmapEB, st);
 }
 
 template <int TX, int TY, typename R>
