@@ -103,12 +103,45 @@ __device__ __forceinline__ void diag_add3(R dacc[7], R dm, R dlo, R dhi, R dshif
     }
 }
 
+// Fused kernel, steps with the Eq. (4) sums: one record per lane, summed
+// over the warp at once (float shuffles) and added to the warp's FP64 row of
+// sdiag, so no accumulator stays live across the particle loop.  All 32 lanes
+// of the warp call it together.
+template <typename R>
+__device__ __forceinline__ void diag_warp3(const DiagParams &D, int sp, bool has, R w, const R u[3], const R spn[3],
+                                           double *row) {
+    R c[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+    if (has) diag_add3(c, (R)D.m_mev[sp], (R)D.lo[sp], (R)D.hi[sp], (R)D.shift[sp], w, u, spn);
+    if (!__any_sync(0xFFFFFFFFu, c[6] != R(0))) return;
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+        R v = c[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+        if ((threadIdx.x & 31) == 0) row[q] += (double)v;
+    }
+}
+
+// column `col` of the CTA's FP64 sums of species sp, kept per warp in sdiag
+// (ncols columns per row); the whole CTA calls it
+__device__ __forceinline__ void store_diag_sums3(const DiagParams &D, int sp, double (*sdiag)[8], int col, int ncols) {
+    __syncthreads();
+    const int tid = threadIdx.x;
+    if (tid < 7) {
+        double t = 0.0;
+        for (int w8 = 0; w8 < kThreads3 / 32; ++w8) t += sdiag[w8][tid];
+        D.rows[((size_t)sp * 8 + tid) * ncols + col] = t;
+    }
+    __syncthreads();
+}
+
 // column `col` of the per-CTA sums of species sp (FP64 warp shuffles), ncols
 // columns per row; the whole CTA calls it
 template <typename R>
 __device__ __forceinline__ void store_diag_rows3(const DiagParams &D, int sp, const R dacc[7], double (*sdiag)[8],
                                                  int col, int ncols) {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+#pragma unroll
     for (int qd = 0; qd < 7; ++qd) {
         double v = (double)dacc[qd];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
@@ -332,18 +365,16 @@ __global__ void __launch_bounds__(kThreads3, (TileConst3<TX, TY, TZ, R>::minb))
         const BinRange rg = range(sp);
         const int len = rg.len;
         const R qm = S.qm, a = S.a, q = S.q;
-        R dacc[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
-        R dlo = R(0), dhi = R(0), dm = R(0), dshift = R(0);
-        if (diag) {
-            dlo = (R)P.diag.lo[sp];
-            dhi = (R)P.diag.hi[sp];
-            dm = (R)P.diag.m_mev[sp];
-            dshift = (R)P.diag.shift[sp];
-        }
+        double *drow = sdiag[tid >> 5];  // this warp's Eq. (4) sums of the species (lane 0 only)
+        if (diag && (tid & 31) == 0)
+            for (int q = 0; q < 8; ++q) drow[q] = 0.0;
         if (sp != first) prefetch(S, tid < len ? bin_slot(rg, tid) : 0, tid < len);
         for (int k0 = 0; k0 < len; k0 += kThreads3) {
             const int k = k0 + tid;
             cp_async_wait0();
+            // Eq. (4) contribution of this lane's record, summed over the warp below
+            bool dhas = false;
+            R dw = R(0), du[3] = {R(0), R(0), R(0)}, ds[3] = {R(0), R(0), R(0)};
             // binned layout: what this lane stores after the record (dest -1: nothing)
             int dest = -1;
             uint32_t bcell = PIC_DEAD;
@@ -418,7 +449,12 @@ __global__ void __launch_bounds__(kThreads3, (TileConst3<TX, TY, TZ, R>::minb))
                     const R chk = u[0] * u[0] + u[1] * u[1] + u[2] * u[2] + spn[0] * spn[0] +
                                   spn[1] * spn[1] + spn[2] * spn[2];
                     bad |= !isfinite(chk);
-                    if (diag && alive) diag_add3(dacc, dm, dlo, dhi, dshift, w, u, spn);
+                    if (diag && alive) {
+                        dhas = true;
+                        dw = w;
+                        du[0] = u[0], du[1] = u[1], du[2] = u[2];
+                        ds[0] = spn[0], ds[1] = spn[1], ds[2] = spn[2];
+                    }
                     if constexpr (BIN) {
                         if (alive) {
                             dest = bin_dest3<TX, TY, TZ>(m, P.t, ix1, iy1, iz1, P.err);
@@ -440,13 +476,14 @@ __global__ void __launch_bounds__(kThreads3, (TileConst3<TX, TY, TZ, R>::minb))
                     }
                 }
             }
+            if constexpr (DIAG) diag_warp3(P.diag, sp, dhas, dw, du, ds, drow);
             if constexpr (BIN)
                 bin_store3(P.bin[sp], S.tile_start, (int)gridDim.x, tile, &s_front[sp], dest, bcell, bv, idkeep[tid],
                            P.err);
         }
         cp_async_wait0();
         if (diag)  // diagnostic columns: the tiles, then (binned) the overflow CTAs
-            store_diag_rows3(P.diag, sp, dacc, sdiag, (int)blockIdx.x, (int)gridDim.x + (BIN ? P.nextra : 0));
+            store_diag_sums3(P.diag, sp, sdiag, (int)blockIdx.x, (int)gridDim.x + (BIN ? P.nextra : 0));
     }
     acc_flush();
     if (bad) atomicOr(P.err, PIC_EF_NAN);
