@@ -190,6 +190,144 @@ __device__ __forceinline__ void gather_transpose(const AdjMesh<R> &A, int ix, in
     bil(5, hx, hy, xh0, xh1, yh0, yh1, lB[2]);
 }
 
+// Vector-Jacobian product of push_spin (a2 + a3), by hand: the forward
+// arithmetic is recomputed with its intermediates kept, then swept in reverse
+// with the derivatives of each formula of the branch the forward step takes
+// (Taylor series or sincos of the rotation angle).  In: the step's inputs and
+// the lambdas lun, lsn of the new u and s; out: the lambdas of u, s, E, B.
+// For a cross product c = p x q the sweep adds q x lc to lp and lc x p to lq.
+template <typename R>
+__device__ __forceinline__ void push_spin_vjp(R qm, R a, R dt, const R E[3], const R B[3], const R u[3],
+                                              const R s[3], const R lun[3], const R lsn[3], R lu[3], R ls[3],
+                                              R lE[3], R lB[3]) {
+    using M = Real<R>;
+    const R one = R(1), half = R(0.5), two = R(2);
+    auto cross = [](const R p[3], const R q[3], R c[3]) {
+        c[0] = p[1] * q[2] - p[2] * q[1];
+        c[1] = p[2] * q[0] - p[0] * q[2];
+        c[2] = p[0] * q[1] - p[1] * q[0];
+    };
+    auto dot = [](const R p[3], const R q[3]) { return p[0] * q[0] + p[1] * q[1] + p[2] * q[2]; };
+    // ---- forward, as push_spin computes it
+    const R h = half * qm * dt;
+    const R um[3] = {u[0] + h * E[0], u[1] + h * E[1], u[2] + h * E[2]};
+    const R gm = M::rsqrt(one + dot(um, um));
+    const R t[3] = {h * B[0] * gm, h * B[1] * gm, h * B[2] * gm};
+    const R T2 = one + dot(t, t);
+    const R f = M::div(two, T2);
+    R ut[3];
+    cross(um, t, ut);
+    const R up[3] = {um[0] + ut[0], um[1] + ut[1], um[2] + ut[2]};
+    const R sv[3] = {f * t[0], f * t[1], f * t[2]};
+    R us[3];
+    cross(up, sv, us);
+    const R un[3] = {um[0] + us[0] + h * E[0], um[1] + us[1] + h * E[1], um[2] + us[2] + h * E[2]};
+    const R b[3] = {half * (u[0] + un[0]), half * (u[1] + un[1]), half * (u[2] + un[2])};
+    const R g2 = one + dot(b, b);
+    const R gbi = M::rsqrt(g2);
+    const R gb = g2 * gbi;
+    const R v[3] = {b[0] * gbi, b[1] * gbi, b[2] * gbi};
+    const R ip1 = M::div(one, one + gb);
+    const R omB = a + gbi, omv = a * gb * ip1, omE = a + ip1;  // Eq. (3)
+    const R vB = dot(v, B);
+    R cE[3];
+    cross(v, E, cE);
+    const R k = -qm * dt;
+    const R w[3] = {k * (omB * B[0] - omv * vB * v[0] - omE * cE[0]),
+                    k * (omB * B[1] - omv * vB * v[1] - omE * cE[1]),
+                    k * (omB * B[2] - omv * vB * v[2] - omE * cE[2])};
+    const R th2 = dot(w, w);
+    R A, C, dA, dC;  // rotation factors and their derivatives in th2
+    if (th2 < M::kTaylor) {
+        A = one - th2 * (one / R(6));
+        C = half - th2 * (one / R(24));
+        dA = -(one / R(6));
+        dC = -(one / R(24));
+    } else {
+        const R rth = M::rsqrt(th2);  // 1 / theta
+        R sh, ch;
+        M::sincos_(half * th2 * rth, &sh, &ch);
+        const R sn = two * sh * ch, omc = two * sh * sh, cs = one - omc;  // sin, 1 - cos, cos of theta
+        A = sn * rth;
+        C = omc * rth * rth;
+        const R th = th2 * rth;
+        // dA/dth2 = (theta cos - sin) / (2 theta^3), dC/dth2 = (theta sin - 2 (1 - cos)) / (2 theta^4)
+        dA = half * (th * cs - sn) * rth * rth * rth;
+        dC = half * (th * sn - two * omc) * rth * rth * rth * rth;
+    }
+    R c[3], d[3];
+    cross(w, s, c);
+    cross(w, c, d);
+    // ---- reverse: s_new = s + A c + C d, c = w x s, d = w x c
+    const R lA = dot(lsn, c), lC = dot(lsn, d);
+    R ld[3] = {C * lsn[0], C * lsn[1], C * lsn[2]};
+    R lc[3], lw[3], tmp[3];
+    cross(ld, w, tmp);  // from d = w x c: lc += ld x w, lw += c x ld
+    lc[0] = A * lsn[0] + tmp[0], lc[1] = A * lsn[1] + tmp[1], lc[2] = A * lsn[2] + tmp[2];
+    cross(c, ld, lw);
+    cross(s, lc, tmp);  // from c = w x s: lw += s x lc, ls += lc x w
+    lw[0] += tmp[0], lw[1] += tmp[1], lw[2] += tmp[2];
+    cross(lc, w, tmp);
+    ls[0] = lsn[0] + tmp[0], ls[1] = lsn[1] + tmp[1], ls[2] = lsn[2] + tmp[2];
+    const R lth2 = lA * dA + lC * dC;
+    lw[0] += two * w[0] * lth2, lw[1] += two * w[1] * lth2, lw[2] += two * w[2] * lth2;
+    // w = k (omB B - omv vB v - omE cE)
+    const R lwv = dot(lw, v);
+    const R lomB = k * dot(lw, B), lomv = -k * vB * lwv, lvB = -k * omv * lwv, lomE = -k * dot(lw, cE);
+    R lv[3], lcE[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        lB[i] = k * omB * lw[i] + lvB * v[i];
+        lv[i] = -k * omv * vB * lw[i] + lvB * B[i];
+        lcE[i] = -k * omE * lw[i];
+    }
+    cross(E, lcE, tmp);  // cE = v x E: lv += E x lcE, lE += lcE x v
+    lv[0] += tmp[0], lv[1] += tmp[1], lv[2] += tmp[2];
+    cross(lcE, v, lE);
+    // omB = a + gbi, omv = a gb ip1, omE = a + ip1, ip1 = 1 / (1 + gb)
+    const R lip1 = a * gb * lomv + lomE;
+    const R lgb = a * ip1 * lomv - ip1 * ip1 * lip1;
+    // v = b gbi, gb = g2 gbi, gbi = g2^(-1/2), g2 = 1 + b.b
+    const R lgbi = lomB + dot(lv, b) + g2 * lgb;
+    const R lg2 = gbi * lgb - half * gbi * gbi * gbi * lgbi;
+    R lb[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) lb[i] = gbi * lv[i] + two * b[i] * lg2;
+    // b = (u + un) / 2
+    R lunt[3] = {lun[0] + half * lb[0], lun[1] + half * lb[1], lun[2] + half * lb[2]};
+    // un = um + up x sv + h E
+    R lum[3] = {lunt[0], lunt[1], lunt[2]};
+    R lup[3], lsv[3];
+    cross(sv, lunt, lup);   // lup = sv x lun
+    cross(lunt, up, lsv);   // lsv = lun x up
+    // sv = f t
+    const R lf = dot(lsv, t);
+    R lt[3] = {f * lsv[0], f * lsv[1], f * lsv[2]};
+    // up = um + um x t
+    lum[0] += lup[0], lum[1] += lup[1], lum[2] += lup[2];
+    cross(t, lup, tmp);  // lum += t x lup
+    lum[0] += tmp[0], lum[1] += tmp[1], lum[2] += tmp[2];
+    cross(lup, um, tmp);  // lt += lup x um
+    lt[0] += tmp[0], lt[1] += tmp[1], lt[2] += tmp[2];
+    // f = 2 / T2, T2 = 1 + t.t
+    const R lT2 = -half * f * f * lf;
+    lt[0] += two * t[0] * lT2, lt[1] += two * t[1] * lT2, lt[2] += two * t[2] * lT2;
+    // t = h B gm, gm = (1 + um.um)^(-1/2)
+    const R lgm = h * dot(lt, B);
+    const R gm3 = gm * gm * gm;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        lB[i] += h * gm * lt[i];
+        lum[i] -= gm3 * um[i] * lgm;
+    }
+    // um = u + h E; un's own h E term
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        lu[i] = half * lb[i] + lum[i];
+        lE[i] += h * (lum[i] + lunt[i]);
+    }
+}
+
 // One adjoint particle step.  In: the particle state at step n (stored), the
 // fields E^n, B^n (stored), lambda_J of the step, and the particle lambdas of
 // step n+1; out: the particle lambdas of step n, lambda_w accumulated, the
@@ -235,27 +373,9 @@ __global__ void __launch_bounds__(128) k_adj_particles(const AdjMesh<R> A, const
 #pragma unroll
         for (int k = 0; k < 3; ++k) lu[k] += gi * cv[k] - un[k] * cu * gi * gi * gi;
         R lox = lx1 + acc.d[0], loy = ly1 + acc.d[1];
-        // a2 + a3: vector-Jacobian product of push_spin over (u, s, E, B), three inputs a pass
+        // a2 + a3: vector-Jacobian product of push_spin over (u, s, E, B)
         R lin[12];
-#pragma unroll
-        for (int pass = 0; pass < 4; ++pass) {
-            D3 Ed[3], Bd[3], ud[3], sd[3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                ud[k] = pass == 0 ? D3::var(u0[k], k) : D3(u0[k]);
-                sd[k] = pass == 1 ? D3::var(s0[k], k) : D3(s0[k]);
-                Ed[k] = pass == 2 ? D3::var(E[k], k) : D3(E[k]);
-                Bd[k] = pass == 3 ? D3::var(B[k], k) : D3(B[k]);
-            }
-            push_spin(D3(S.qm), D3(S.a), D3(A.dt), Ed, Bd, ud, sd);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                R v = R(0);
-#pragma unroll
-                for (int o = 0; o < 3; ++o) v += lu[o] * ud[o].d[k] + ls[o] * sd[o].d[k];
-                lin[pass * 3 + k] = v;
-            }
-        }
+        push_spin_vjp(S.qm, S.a, A.dt, E, B, u0, s0, lu, ls, lin, lin + 3, lin + 6, lin + 9);
         // a1: the gathered values depend on the mesh (transpose into lambda_EB)
         // and on the offsets (dual gather)
         gather_transpose(A, ix, iy, ox, oy, lin + 6, lin + 9);
