@@ -627,6 +627,7 @@ def main_adjoint(args):
     import torch
 
     import paper_2002_02211_gb300 as pic
+    from paper_2002_02211_gb300.autograd import adjoint_forward_step
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -656,12 +657,10 @@ def main_adjoint(args):
             ev[1].record(stream)
             torch.cuda.synchronize(dev)
             t_fwd = ev[0].elapsed_time(ev[1]) * 1e-3
-        with fresh() as sim:            # the adjoint's own forward path: split kernels, no sorts
+        with fresh() as sim:            # the adjoint's own forward steps (no sorts)
             ev[0].record(stream)
             for _ in range(args.adj_steps):
-                sim.gather_push_spin()
-                sim.deposit()
-                sim.field_update()
+                adjoint_forward_step(sim)
             ev[1].record(stream)
             torch.cuda.synchronize(dev)
             t_split = ev[0].elapsed_time(ev[1]) * 1e-3
@@ -671,8 +670,9 @@ def main_adjoint(args):
             value, dla0 = sim.adjoint(args.adj_steps, args.checkpoint, **loss)
             t_adj = time.perf_counter() - t0
             g = sim.adjoint_particle_grads(0)
-        out[f"fp{prec}"] = {"forward_s": t_fwd, "forward_split_s": t_split, "adjoint_s": t_adj,
-                            "adjoint_over_forward": t_adj / t_fwd, "adjoint_over_split_forward": t_adj / t_split,
+        out[f"fp{prec}"] = {"forward_s": t_fwd, "forward_adjoint_path_s": t_split, "adjoint_s": t_adj,
+                            "adjoint_over_forward": t_adj / t_fwd,
+                            "adjoint_over_adjoint_path_forward": t_adj / t_split,
                             "loss": value, "dloss_da0": dla0,
                             "dloss_dw_abs_sum": float(np.abs(g["w"]).sum())}
         if prec == 64:
@@ -685,10 +685,8 @@ def main_adjoint(args):
                 with pic.Simulation(cfg, stream=stream) as sim:
                     sim.set_particles(0, parts[0])
                     sim.capture_background()
-                    for _ in range(steps):
-                        sim.gather_push_spin()
-                        sim.deposit()
-                        sim.field_update()
+                    for _ in range(steps):   # the adjoint's own forward steps
+                        adjoint_forward_step(sim)
                     return sim.loss(**loss)
 
             acc = {"steps": 150}

@@ -359,8 +359,9 @@ typedef struct {
 /* L of the current state.  Synchronous. */
 pic_status_t pic_loss(void *ctx, const pic_loss_t *loss, double *value, void *stream);
 
-/* Runs nsteps steps forward from the current state (split path, no tile
- * sorts: every slot keeps its particle) keeping a checkpoint every
+/* Runs nsteps steps forward from the current state (fused kernel in FP32,
+ * split kernels in FP64; no tile sorts: every slot keeps its particle, no
+ * in-step diagnostics) keeping a checkpoint every
  * checkpoint_every steps, evaluates L at the end, and back-propagates: each
  * stretch is recomputed from its checkpoint with every state stored, and the
  * adjoint of every step (the transposes of the Yee stages and the

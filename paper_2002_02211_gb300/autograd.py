@@ -52,13 +52,21 @@ class LossRun:
 
 def forward_loss(run: LossRun, a0, weights, spins):
     """The loss alone, through the same forward steps pic_adjoint takes
-    (split path, no tile sorts)."""
+    (no tile sorts; the fused kernel in FP32, the split kernels in FP64)."""
     with run.start(a0, weights, spins) as sim:
         for _ in range(run.nsteps):
-            sim.gather_push_spin()
-            sim.deposit()
-            sim.field_update()
+            adjoint_forward_step(sim)
         return sim.loss(species=run.species, **run.loss)
+
+
+def adjoint_forward_step(sim):
+    """One forward step the way pic_adjoint takes it."""
+    if sim.cfg.precision == 64:
+        sim.gather_push_spin()
+        sim.deposit()
+    else:
+        sim.push_deposit()
+    sim.field_update()
 
 
 def _slot_order(ids, slot_ids):

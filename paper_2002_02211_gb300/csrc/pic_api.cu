@@ -1758,8 +1758,9 @@ const char *pic_batch_last_error(void *batch) {
 // Adjoint of the 2D3V step: the gradient of a loss on the final particle
 // state (the energy-weighted polarization above a cut, the beam quality the
 // paper's runs look at) with respect to the initial particle state, the
-// particle weights and the laser amplitude.  The forward pass runs the split
-// kernels without tile sorts (slots keep their particles) and keeps a
+// particle weights and the laser amplitude.  The forward pass runs the fused
+// kernel (FP32; the split kernels in FP64) without tile sorts (slots keep
+// their particles) and keeps a
 // checkpoint every K steps; the backward pass recomputes each stretch of K
 // steps from its checkpoint, storing every step's state, and runs the adjoint
 // kernels back through it.
@@ -1857,9 +1858,21 @@ AdjMesh<R> adj_mesh(Ctx *c, void *LEB, void *LJ, void *Lbnd) {
     return A;
 }
 
-pic_status_t forward_split_step(Ctx *c, cudaStream_t st) {
-    pic_status_t r = pic_gather_push_spin(c, st);
-    if (r == PIC_OK) r = pic_deposit(c, st);
+// The adjoint's forward step, without tile sorts (every particle keeps its
+// slot) and without in-step diagnostics: the fused kernel in FP32; in FP64 the
+// split kernels, which run faster than the FP64 fused kernel once the
+// particles have drifted out of their tiles.
+pic_status_t forward_adjoint_step(Ctx *c, cudaStream_t st) {
+    pic_status_t r = PIC_OK;
+    if (c->rb == 8) {
+        r = pic_gather_push_spin(c, st);
+        if (r == PIC_OK) r = pic_deposit(c, st);
+    } else {
+        const int diag_every = c->diag_every;
+        c->diag_every = 0;
+        r = pic_push_deposit(c, st);
+        c->diag_every = diag_every;
+    }
     if (r == PIC_OK) r = pic_field_update(c, st);
     return r;
 }
@@ -1981,7 +1994,7 @@ pic_status_t pic_adjoint(void *ctx, int nsteps, int checkpoint_every, const pic_
     // forward with checkpoints
     for (int k = 0; k < nsteps; ++k) {
         if (k % K == 0) ARET(snap_copy(c, L, n, snap(k / K), true, st));
-        ARET(forward_split_step(c, st));
+        ARET(forward_adjoint_step(c, st));
     }
     ARET(snap_copy(c, L, n, final_state, true, st));
     // loss and the lambdas of the final state
@@ -2006,7 +2019,7 @@ pic_status_t pic_adjoint(void *ctx, int nsteps, int checkpoint_every, const pic_
         c->step = step0 + k0;
         for (int k = k0; k < k1; ++k) {
             ARET(snap_copy(c, L, n, snap(nck + (k - k0)), true, st));
-            if (k + 1 < k1) ARET(forward_split_step(c, st));
+            if (k + 1 < k1) ARET(forward_adjoint_step(c, st));
         }
         for (int k = k1 - 1; k >= k0; --k) {
             const char *state = snap(nck + (k - k0));
