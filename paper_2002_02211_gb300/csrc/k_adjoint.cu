@@ -161,11 +161,14 @@ struct JDot {
     }
 };
 
-// transpose of gather_eb: lambda of each staggered node += weight x lambda of
-// the gathered value (the weights and nodes of gather_eb, written out)
+// Reverse of the gather (a1), by hand, one pass over the 24 stencil nodes:
+// lambda of each staggered node += weight x lambda of the gathered value (the
+// transpose into lambda_EB), and the derivatives of <lE, E> + <lB, B> in the
+// offsets, whose bilinear weights move as (-1, +1) with ox (x weights) and
+// with oy (y weights), within the stencil branch the forward gather takes.
 template <typename R>
-__device__ __forceinline__ void gather_transpose(const AdjMesh<R> &A, int ix, int iy, R ox, R oy, const R lE[3],
-                                                 const R lB[3]) {
+__device__ __forceinline__ void gather_vjp(const AdjMesh<R> &A, const R *EB, int ix, int iy, R ox, R oy,
+                                           const R lE[3], const R lB[3], R &lox, R &loy) {
     const R half = R(0.5), one = R(1);
     const R xn0 = one - ox, xn1 = ox, yn0 = one - oy, yn1 = oy;
     const bool rx = ox >= half, ry = oy >= half;
@@ -174,13 +177,18 @@ __device__ __forceinline__ void gather_transpose(const AdjMesh<R> &A, int ix, in
     const R xh0 = one - ohx, xh1 = ohx, yh0 = one - ohy, yh1 = ohy;
     auto bil = [&](int c, int x, int y, R a0, R a1, R b0, R b1, R lam) {
         if (lam == R(0)) return;
-        const R w[4] = {b0 * a0, b0 * a1, b1 * a0, b1 * a1};
-        const int dx[4] = {0, 1, 0, 1}, dy[4] = {0, 0, 1, 1};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const long long n = node(A, x + dx[k], y + dy[k]);
-            if (n >= 0) atomicAdd(&A.LEB[c * A.plane + n], w[k] * lam);
-        }
+        const long long n00 = node(A, x, y), n10 = node(A, x + 1, y);
+        const long long n01 = node(A, x, y + 1), n11 = node(A, x + 1, y + 1);
+        const R *F = EB + c * A.plane;
+        const R f00 = n00 < 0 ? R(0) : F[n00], f10 = n10 < 0 ? R(0) : F[n10];
+        const R f01 = n01 < 0 ? R(0) : F[n01], f11 = n11 < 0 ? R(0) : F[n11];
+        lox += lam * (b0 * (f10 - f00) + b1 * (f11 - f01));
+        loy += lam * ((a0 * f01 + a1 * f11) - (a0 * f00 + a1 * f10));
+        R *L = A.LEB + c * A.plane;
+        if (n00 >= 0) atomicAdd(&L[n00], b0 * a0 * lam);
+        if (n10 >= 0) atomicAdd(&L[n10], b0 * a1 * lam);
+        if (n01 >= 0) atomicAdd(&L[n01], b1 * a0 * lam);
+        if (n11 >= 0) atomicAdd(&L[n11], b1 * a1 * lam);
     };
     bil(0, hx, iy, xh0, xh1, yn0, yn1, lE[0]);
     bil(1, ix, hy, xn0, xn1, yh0, yh1, lE[1]);
@@ -333,10 +341,8 @@ __device__ __forceinline__ void push_spin_vjp(R qm, R a, R dt, const R E[3], con
 // step n+1; out: the particle lambdas of step n, lambda_w accumulated, the
 // gather's transpose added to the mesh lambdas.
 template <typename R>
-__global__ void __launch_bounds__(128) k_adj_particles(const AdjMesh<R> A, const AdjParticles<R> S) {
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 1) k_adj_particles(const AdjMesh<R> A, const AdjParticles<R> S) {
     using D5 = Dual<R, 5>;
-    using D3 = Dual<R, 3>;
-    using D2 = Dual<R, 2>;
     const StoredMesh<R> sm{&A, S.EB};
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < S.n; p += (long long)gridDim.x * blockDim.x) {
         const uint32_t c = S.cell[p];
@@ -377,17 +383,8 @@ __global__ void __launch_bounds__(128) k_adj_particles(const AdjMesh<R> A, const
         R lin[12];
         push_spin_vjp(S.qm, S.a, A.dt, E, B, u0, s0, lu, ls, lin, lin + 3, lin + 6, lin + 9);
         // a1: the gathered values depend on the mesh (transpose into lambda_EB)
-        // and on the offsets (dual gather)
-        gather_transpose(A, ix, iy, ox, oy, lin + 6, lin + 9);
-        {
-            D2 Eg[3], Bg[3];
-            gather_eb(sm, ix, iy, D2::var(ox, 0), D2::var(oy, 1), Eg, Bg);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                lox += lin[6 + k] * Eg[k].d[0] + lin[9 + k] * Bg[k].d[0];
-                loy += lin[6 + k] * Eg[k].d[1] + lin[9 + k] * Bg[k].d[1];
-            }
-        }
+        // and on the offsets
+        gather_vjp(A, S.EB, ix, iy, ox, oy, lin + 6, lin + 9, lox, loy);
         S.lx[p] = lox;
         S.ly[p] = loy;
         S.lux[p] = lin[0];
