@@ -34,9 +34,10 @@ __device__ __forceinline__ bool finish_move(const MeshParams<R> &m, int &ix1, in
 // 6-component field window (rows padded to 128 bytes with the padding split
 // between the two sides of the tile, at least 4 cells each; 6 cells of
 // margin along y) with one 3D TMA load (zero fill outside the mesh).  Particle records of the tile (both
-// species, one slot range after the other) stream through a two-deep
-// cp.async ring in shared memory: while a thread computes one record it has
-// the next one in flight.  Each record runs a1-a5, gathering from and
+// species, one slot range after the other) stream through one shared-memory
+// slot per thread: a thread copies the record in hand to registers and at once
+// requests its next record into the slot (cp.async), so while it computes one
+// record it has the next one in flight.  Each record runs a1-a5, gathering from and
 // depositing into shared memory when the particle's 4x4 stencil lies inside
 // the window and the mesh (no wrap), otherwise through global memory.  The
 // current window is finally added to J with 16-byte vector atomics (float)
@@ -52,9 +53,10 @@ template <int TX, int TY, typename R>
 struct TileConst {
     static constexpr int WX = window_wx<R>(TX), WY = window_wy(TY), WA = WX * WY;
     static constexpr int HX = window_hx<R>(TX), HY = window_hy();
-    // field window, current window, and a two-stage ring of cell words and reals
+    // field window, current window, and one record slot per thread (cell word
+    // and reals)
     static constexpr size_t smem_bytes =
-        (size_t)9 * WA * sizeof(R) + 2 * kFusedThreads * (sizeof(uint32_t) + kRec * sizeof(R));
+        (size_t)9 * WA * sizeof(R) + kFusedThreads * (sizeof(uint32_t) + kRec * sizeof(R));
     // resident CTAs per SM the register budget of the single-run kernel is
     // sized for: without the in-step Eq. (4) sums a fourth CTA where four fit
     // in shared memory (228 KB, 1 KB reserved per CTA), else PIC_FUSED_MINB
@@ -98,8 +100,8 @@ __device__ __forceinline__ bool fused_tile(const StepParams<R> &P, const CUtenso
     constexpr int WX = TC::WX, WY = TC::WY, WA = TC::WA;
     R *sF = reinterpret_cast<R *>(dsm);
     R *sJ = sF + 6 * WA;
-    R *ring = sJ + 3 * WA;                                             // [2][kRec][kFusedThreads]
-    uint32_t *cring = reinterpret_cast<uint32_t *>(ring + 2 * kRec * kFusedThreads);  // [2][kFusedThreads]
+    R *ring = sJ + 3 * WA;                                             // [kRec][kFusedThreads]
+    uint32_t *cring = reinterpret_cast<uint32_t *>(ring + kRec * kFusedThreads);  // [kFusedThreads]
     const MeshParams<R> &m = P.m;
 
     const int ty = tile / P.t.ntx, tx = tile - ty * P.t.ntx;
@@ -112,11 +114,13 @@ __device__ __forceinline__ bool fused_tile(const StepParams<R> &P, const CUtenso
     }
 
     R *ring0 = ring + tid;
-    // particle record `slot` of species S into ring stage `buf`
-    auto prefetch = [&](const DevSpecies<R> &S, int slot, bool live, int buf) {
+    // particle record `slot` of species S into this thread's record slot (the
+    // thread copies the record in hand to registers first, so one record is
+    // in flight while it computes)
+    auto prefetch = [&](const DevSpecies<R> &S, int slot, bool live) {
         if (live) {
-            R *r = ring0 + buf * kRec * kFusedThreads;
-            cp_async4(cring + buf * kFusedThreads + tid, S.cell + slot);
+            R *r = ring0;
+            cp_async4(cring + tid, S.cell + slot);
             cp_async_r(r + 0 * kFusedThreads, S.ox + slot);
             cp_async_r(r + 1 * kFusedThreads, S.oy + slot);
             cp_async_r(r + 2 * kFusedThreads, S.ux + slot);
@@ -141,7 +145,7 @@ __device__ __forceinline__ bool fused_tile(const StepParams<R> &P, const CUtenso
         if (P.sp[sp].mobile) first = sp;
     if (first >= 0) {
         const int beg = P.sp[first].tile_start[tile];
-        prefetch(P.sp[first], beg + tid, tid < P.sp[first].tile_start[tile + 1] - beg, 0);
+        prefetch(P.sp[first], beg + tid, tid < P.sp[first].tile_start[tile + 1] - beg);
     }
     for (int i = tid; i < 3 * WA; i += kFusedThreads) sJ[i] = R(0);
     __syncthreads();
@@ -189,22 +193,22 @@ __device__ __forceinline__ bool fused_tile(const StepParams<R> &P, const CUtenso
             dm = (R)P.diag.m_mev[sp];
             dshift = (R)P.diag.shift[sp];
         }
-        int buf = 0;
-        if (sp != first) prefetch(S, beg + tid, tid < len, 0);
+        if (sp != first) prefetch(S, beg + tid, tid < len);
         for (int k0 = 0; k0 < len; k0 += kFusedThreads) {
             const int k = k0 + tid;
-            prefetch(S, beg + k + kFusedThreads, k + kFusedThreads < len, buf ^ 1);
-            cp_async_wait1();
+            cp_async_wait0();
             if (k < len) {
                 const int slot = beg + k;
-                const R *r = ring0 + buf * kRec * kFusedThreads;
-                const uint32_t c = cring[buf * kFusedThreads + tid];
+                const R *r = ring0;
+                const uint32_t c = cring[tid];
+                const R ox = r[0 * kFusedThreads], oy = r[1 * kFusedThreads];
+                R u[3] = {r[2 * kFusedThreads], r[3 * kFusedThreads], r[4 * kFusedThreads]};
+                R spn[3] = {r[5 * kFusedThreads], r[6 * kFusedThreads], r[7 * kFusedThreads]};
+                const R w = r[8 * kFusedThreads];
+                // the slot is free again: request the next record
+                prefetch(S, beg + k + kFusedThreads, k + kFusedThreads < len);
                 if (c != PIC_DEAD) {
                     const int ix = (int)(c & 0xFFFFu), iy = (int)(c >> 16);
-                    const R ox = r[0 * kFusedThreads], oy = r[1 * kFusedThreads];
-                    R u[3] = {r[2 * kFusedThreads], r[3 * kFusedThreads], r[4 * kFusedThreads]};
-                    R spn[3] = {r[5 * kFusedThreads], r[6 * kFusedThreads], r[7 * kFusedThreads]};
-                    const R w = r[8 * kFusedThreads];
                     const bool fast = ix >= xlo && ix <= xhi && iy >= ylo && iy <= yhi;
                     R E[3], B[3];
                     if (fast)
@@ -266,7 +270,6 @@ __device__ __forceinline__ bool fused_tile(const StepParams<R> &P, const CUtenso
                     S.sz[slot] = spn[2];
                 }
             }
-            buf ^= 1;
         }
         cp_async_wait0();
         if (diag) {
@@ -324,10 +327,11 @@ __global__ void __launch_bounds__(kFusedThreads,
 // Batched step: persistent CTAs (a few per SM) take (run, tile) work items
 // from a queue shared by all runs of a batch and run fused_tile on each, with
 // the run's parameters and tensor map read from global memory.  Items of runs
-// that have finished their steps are skipped.
+// that have finished their steps are skipped.  Batch steps take no in-step
+// Eq. (4) sums, so the tile body is the instantiation without them.
 // ---------------------------------------------------------------------------
 template <int TX, int TY, typename R>
-__global__ void __launch_bounds__(kFusedThreads, sizeof(R) == 4 ? PIC_FUSED_MINB : 2)
+__global__ void __launch_bounds__(kFusedThreads, TileConst<TX, TY, R>::minb_nodiag)
     k_step_fused_batch(const BatchFused<R> W) {
     extern __shared__ __align__(1024) unsigned char dsm[];
     __shared__ __align__(8) uint64_t bar;
@@ -348,8 +352,8 @@ __global__ void __launch_bounds__(kFusedThreads, sizeof(R) == 4 ? PIC_FUSED_MINB
         if (W.step[rt.x] >= W.nsteps[rt.x]) continue;
         const CUtensorMap *tm = W.tmaps + rt.x;
         if (threadIdx.x == 0) fence_tensormap_acquire(tm);
-        if (!fused_tile<TX, TY, R>(W.params[rt.x], tm, rt.y, W.params[rt.x].t.ntx * W.params[rt.x].t.nty, bar,
-                                   phase, dsm, sdiag))
+        if (!fused_tile<TX, TY, R, false>(W.params[rt.x], tm, rt.y, W.params[rt.x].t.ntx * W.params[rt.x].t.nty,
+                                          bar, phase, dsm, sdiag))
             break;
         phase ^= 1u;
     }
