@@ -6,14 +6,14 @@
 //
 // The step is linear in the mesh fields except through the particles, so the
 // mesh part of the adjoint is the transpose of each field stage; the particle
-// part is, per particle, the vector-Jacobian product of the forward arithmetic,
-// taken by running the forward device functions (gather_eb, push_spin,
-// deposit_esirkepov) on forward-mode dual numbers.  Adjoint kernels run in the
-// reverse order of the forward stages:
+// part is, per particle, the vector-Jacobian product of the forward arithmetic
+// (the gather, push_spin and the deposit swept in reverse by hand, each with
+// the derivatives of the branch the forward step takes).  Adjoint kernels run
+// in the reverse order of the forward stages:
 //   b_half^T, e_full^T (-> lambda_J), boundary^T (-> dL/da0), b_half^T, particles^T.
 #include <algorithm>
 
-#include "pic_dual.cuh"
+#include "pic_device.cuh"
 #include "pic_kernels.h"
 
 namespace {
@@ -150,16 +150,114 @@ struct StoredMesh {
     }
 };
 
-// <lambda_J, J> of one deposit, as a dual number
-template <typename R, typename D>
-struct JDot {
-    const AdjMesh<R> *A;
-    D *acc;
-    __device__ __forceinline__ void j(int c, int x, int y, const D &v) const {
-        const long long k = node(*A, x, y);
-        if (k >= 0) *acc += v * A->LJ[c * A->plane + k];
+// Reverse of the 2D3V Esirkepov deposit (a5), by hand: val = <lambda_J, J>
+// of one move, and its derivatives g in (ox, oy, ox1, oy1, vz), for the same
+// nodes and the same branch (in-cell closed form, or the general form over the
+// shape3 factors) as deposit_esirkepov; lambda_J outside the mesh counts zero.
+template <typename R>
+__device__ __forceinline__ void deposit_vjp(const AdjMesh<R> &A, int ix, int iy, R ox, R oy, int ix1, int iy1,
+                                            R ox1, R oy1, R qw, R vz, R dx_dt, R dy_dt, R &val, R g[5]) {
+    const R one = R(1), half = R(0.5), third = R(1) / R(3);
+    auto lam = [&](int c, int x, int y) {
+        const long long k = node(A, x, y);
+        return k < 0 ? R(0) : A.LJ[c * A.plane + k];
+    };
+    if (ix1 == ix && iy1 == iy) {
+        const R d = ox1 - ox, e = oy1 - oy;
+        const R xm = ox + half * d, ym = oy + half * e;
+        const R jx = qw * dx_dt * d, jy = qw * dy_dt * e, cz = qw * vz;
+        const R de = d * e * (one / R(12));
+        const R lx0 = lam(0, ix, iy), lx1 = lam(0, ix, iy + 1);
+        const R ly0 = lam(1, ix, iy), ly1 = lam(1, ix + 1, iy);
+        const R z00 = lam(2, ix, iy), z10 = lam(2, ix + 1, iy), z01 = lam(2, ix, iy + 1), z11 = lam(2, ix + 1, iy + 1);
+        const R Lx = lx0 * (one - ym) + lx1 * ym;
+        const R Ly = ly0 * (one - xm) + ly1 * xm;
+        const R K = z00 - z10 - z01 + z11;
+        const R Z = z00 * (one - xm) * (one - ym) + z10 * xm * (one - ym) + z01 * (one - xm) * ym + z11 * xm * ym + de * K;
+        val = jx * Lx + jy * Ly + cz * Z;
+        const R gd = qw * dx_dt * Lx + cz * e * (one / R(12)) * K;
+        const R ge = qw * dy_dt * Ly + cz * d * (one / R(12)) * K;
+        const R gxm = jy * (ly1 - ly0) + cz * ((z10 - z00) * (one - ym) + (z11 - z01) * ym);
+        const R gym = jx * (lx1 - lx0) + cz * ((z01 - z00) * (one - xm) + (z11 - z10) * xm);
+        // d = ox1 - ox, xm = ox + d / 2 (likewise e, ym)
+        g[0] = -gd + half * gxm;
+        g[2] = gd + half * gxm;
+        g[1] = -ge + half * gym;
+        g[3] = ge + half * gym;
+        g[4] = qw * Z;
+        return;
     }
-};
+    R S0x[3], dSx[3], S0y[3], dSy[3];
+    const int gx = shape3(ix, ox, ix1, ox1, S0x, dSx);
+    const int gy = shape3(iy, oy, iy1, oy1, S0y, dSy);
+    const bool crx = ix1 != ix, cry = iy1 != iy;
+    const int ni = crx ? 3 : 2, nj = cry ? 3 : 2;
+    const R cx = -qw * dx_dt, cy = -qw * dy_dt, cz = qw * vz;
+    R gS0x[3] = {R(0), R(0), R(0)}, gdSx[3] = {R(0), R(0), R(0)};
+    R gS0y[3] = {R(0), R(0), R(0)}, gdSy[3] = {R(0), R(0), R(0)};
+    R vx = R(0), vy = R(0), vzs = R(0);
+    // Jx(gx, gy+j) = cx dSx0 fy_j, Jx(gx+1, gy+j) = cx (dSx0 + dSx1) fy_j (crossing x)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        if (j >= nj) break;
+        const R fy = S0y[j] + half * dSy[j];
+        const R l1 = crx ? lam(0, gx + 1, gy + j) : R(0);
+        const R P = lam(0, gx, gy + j) + l1, Q = l1;
+        vx += fy * (dSx[0] * P + dSx[1] * Q);
+        gdSx[0] += cx * fy * P;
+        gdSx[1] += cx * fy * Q;
+        const R gf = cx * (dSx[0] * P + dSx[1] * Q);
+        gS0y[j] += gf;
+        gdSy[j] += half * gf;
+    }
+    // Jy(gx+i, gy) = cy dSy0 fx_i, Jy(gx+i, gy+1) = cy (dSy0 + dSy1) fx_i (crossing y)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        if (i >= ni) break;
+        const R fx = S0x[i] + half * dSx[i];
+        const R l1 = cry ? lam(1, gx + i, gy + 1) : R(0);
+        const R P = lam(1, gx + i, gy) + l1, Q = l1;
+        vy += fx * (dSy[0] * P + dSy[1] * Q);
+        gdSy[0] += cy * fx * P;
+        gdSy[1] += cy * fx * Q;
+        const R gf = cy * (dSy[0] * P + dSy[1] * Q);
+        gS0x[i] += gf;
+        gdSx[i] += half * gf;
+    }
+    // Jz(gx+i, gy+j) = cz wz(i, j)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        if (j >= nj) break;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            if (i >= ni) break;
+            const R l = lam(2, gx + i, gy + j);
+            vzs += l * (S0x[i] * S0y[j] + half * (dSx[i] * S0y[j] + S0x[i] * dSy[j]) + third * dSx[i] * dSy[j]);
+            const R cl = cz * l;
+            gS0x[i] += cl * (S0y[j] + half * dSy[j]);
+            gdSx[i] += cl * (half * S0y[j] + third * dSy[j]);
+            gS0y[j] += cl * (S0x[i] + half * dSx[i]);
+            gdSy[j] += cl * (half * S0x[i] + third * dSx[i]);
+        }
+    }
+    val = cx * vx + cy * vy + cz * vzs;
+    g[4] = qw * vzs;
+    // shape3 in reverse: S0, dS as functions of (o, o1) in each of its branches
+    auto shape_back = [&](int d, const R gS0[3], const R gdS[3], R &go, R &go1) {
+        if (d == 0) {
+            go = -gS0[0] + gS0[1] + gdS[0] - gdS[1];
+            go1 = -gdS[0] + gdS[1];
+        } else if (d > 0) {
+            go = -gS0[0] + gS0[1] + gdS[0] - gdS[1];
+            go1 = -gdS[1] + gdS[2];
+        } else {
+            go = -gS0[1] + gS0[2] + gdS[1] - gdS[2];
+            go1 = -gdS[0] + gdS[1];
+        }
+    };
+    shape_back(ix1 - ix, gS0x, gdSx, g[0], g[2]);
+    shape_back(iy1 - iy, gS0y, gdSy, g[1], g[3]);
+}
 
 // Reverse of the gather (a1), by hand, one pass over the 24 stencil nodes:
 // lambda of each staggered node += weight x lambda of the gathered value (the
@@ -342,7 +440,6 @@ __device__ __forceinline__ void push_spin_vjp(R qm, R a, R dt, const R E[3], con
 // gather's transpose added to the mesh lambdas.
 template <typename R>
 __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 1) k_adj_particles(const AdjMesh<R> A, const AdjParticles<R> S) {
-    using D5 = Dual<R, 5>;
     const StoredMesh<R> sm{&A, S.EB};
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < S.n; p += (long long)gridDim.x * blockDim.x) {
         const uint32_t c = S.cell[p];
@@ -365,20 +462,18 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 1) k_adj_particles(c
         // lambdas of step n+1 (zero for a particle removed in this step)
         R lx1 = S.lx[p], ly1 = S.ly[p];
         R lu[3] = {S.lux[p], S.luy[p], S.luz[p]}, ls[3] = {S.lsx[p], S.lsy[p], S.lsz[p]};
-        // a5: <lambda_J, J> as a function of (ox, oy, ox1, oy1, vz)
-        D5 acc(R(0));
-        const JDot<R, D5> jd{&A, &acc};
-        deposit_esirkepov(jd, ix, iy, D5::var(ox, 0), D5::var(oy, 1), ix1, iy1, D5::var(ox1, 2), D5::var(oy1, 3),
-                          D5(S.q * w), D5::var(vz, 4), D5(A.dx_dt), D5(A.dy_dt));
-        if (w != R(0)) S.lw[p] += acc.v / w;
-        lx1 += acc.d[2];
-        ly1 += acc.d[3];
+        // a5: <lambda_J, J> of the move and its derivatives in (ox, oy, ox1, oy1, vz)
+        R dval, dg[5];
+        deposit_vjp(A, ix, iy, ox, oy, ix1, iy1, ox1, oy1, S.q * w, vz, A.dx_dt, A.dy_dt, dval, dg);
+        if (w != R(0)) S.lw[p] += dval / w;
+        lx1 += dg[2];
+        ly1 += dg[3];
         // a4: ox1 = ox + dt/dx ux gi, oy1 = oy + dt/dy uy gi, vz = uz gi
-        const R cv[3] = {lx1 * A.dt_dx, ly1 * A.dt_dy, acc.d[4]};
+        const R cv[3] = {lx1 * A.dt_dx, ly1 * A.dt_dy, dg[4]};
         const R cu = cv[0] * un[0] + cv[1] * un[1] + cv[2] * un[2];
 #pragma unroll
         for (int k = 0; k < 3; ++k) lu[k] += gi * cv[k] - un[k] * cu * gi * gi * gi;
-        R lox = lx1 + acc.d[0], loy = ly1 + acc.d[1];
+        R lox = lx1 + dg[0], loy = ly1 + dg[1];
         // a2 + a3: vector-Jacobian product of push_spin over (u, s, E, B)
         R lin[12];
         push_spin_vjp(S.qm, S.a, A.dt, E, B, u0, s0, lu, ls, lin, lin + 3, lin + 6, lin + 9);
