@@ -307,9 +307,19 @@ cudaError_t launch_unpack_cells3(const uint32_t *cell, int32_t *ix, int32_t *iy,
     return cudaGetLastError();
 }
 
-// Binned layout: one warp per range writes PIC_DEAD into the slots of the
-// range outside its two segments, records the range's arrival base for the
-// next step, and clears the other buffer's front / split / back counters.
+// Binned layout, per range r of each species:
+//  - counters: record the range's arrival base for the next step and clear
+//    the other buffer's front / split / back counters;
+//  - fill: write PIC_DEAD into the slots of the range outside its two
+//    segments (slot-wise kernels then read the layout as a compact one with
+//    holes; the binned step itself reads only the segments).
+__device__ __forceinline__ void bin_counters(const SealSpecies &S, int nr, int r) {
+    const BinRange b = bin_range(S.tile_start, S.cnt_new, nr, r);
+    S.cnt_new[3 * nr + r] = b.beg + b.len;
+    if (S.cnt_zero) S.cnt_zero[r] = S.cnt_zero[nr + r] = S.cnt_zero[2 * nr + r] = 0;
+}
+
+// fill (and counters): one warp per range
 __global__ void __launch_bounds__(256) k_seal_bins(const SealArgs a) {
     const int r = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31, nr = a.nranges;
     if (r >= nr) return;
@@ -319,16 +329,23 @@ __global__ void __launch_bounds__(256) k_seal_bins(const SealArgs a) {
         const int end = S.tile_start[r + 1], back_end = b.beg + b.split + (b.len - b.front);
         for (int i = b.beg + b.front + lane; i < b.beg + b.split; i += 32) S.cell[i] = PIC_DEAD;
         for (int i = back_end + lane; i < end; i += 32) S.cell[i] = PIC_DEAD;
-        if (lane == 0) {
-            S.cnt_new[3 * nr + r] = b.beg + b.len;
-            if (S.cnt_zero) S.cnt_zero[r] = S.cnt_zero[nr + r] = S.cnt_zero[2 * nr + r] = 0;
-        }
+        if (lane == 0 && a.counters) bin_counters(S, nr, r);
     }
 }
 
+// counters alone: one thread per range
+__global__ void __launch_bounds__(256) k_bin_counters(const SealArgs a) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= a.nranges) return;
+    for (int s = 0; s < a.nsp; ++s) bin_counters(a.sp[s], a.nranges, r);
+}
+
 cudaError_t launch_seal_bins(const SealArgs &a, cudaStream_t st) {
-    if (a.nranges <= 0 || a.nsp <= 0) return cudaSuccess;
-    k_seal_bins<<<(a.nranges + 7) / 8, 256, 0, st>>>(a);
+    if (a.nranges <= 0 || a.nsp <= 0 || !(a.fill || a.counters)) return cudaSuccess;
+    if (a.fill)
+        k_seal_bins<<<(a.nranges + 7) / 8, 256, 0, st>>>(a);
+    else
+        k_bin_counters<<<(a.nranges + 255) / 256, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 

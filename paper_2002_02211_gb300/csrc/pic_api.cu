@@ -78,6 +78,10 @@ struct Ctx {
     // particles (sizes the ranges against capacity)
     bool binned = false;
     bool sp_binned[PIC_MAX_SPECIES] = {};
+    // the binned step leaves the slots outside the new segments unsealed
+    // (stale records); seal_pending writes PIC_DEAD there before any kernel
+    // that reads every slot
+    bool unsealed[PIC_MAX_SPECIES] = {};
     int32_t *bin_cnt[PIC_MAX_SPECIES][2] = {};
     int64_t n_live[PIC_MAX_SPECIES] = {};
     static constexpr int kBinCtas = 8;  // CTAs of the overflow-range kernel
@@ -355,11 +359,31 @@ bool bin_plan(const Ctx *c, int s, int *ovf_cap, int64_t *span) {
     return true;
 }
 
+// PIC_DEAD into the stale slots the binned steps left in every species'
+// current buffer (before a kernel that reads every slot)
+pic_status_t seal_pending(Ctx *c, cudaStream_t st) {
+    SealArgs a{};
+    a.nranges = c->ntiles + 1;
+    a.fill = true;
+    a.counters = false;
+    for (int s = 0; s < c->cfg.nspecies; ++s) {
+        if (!c->unsealed[s]) continue;
+        a.sp[a.nsp++] = SealSpecies{c->buf[s][c->cur[s]].cell, c->tile_start[s], c->bin_cnt[s][c->cur[s]], nullptr};
+        c->unsealed[s] = false;
+    }
+    if (a.nsp == 0) return PIC_OK;
+    CK(launch_seal_bins(a, st));
+    c->launches += 1;
+    return PIC_OK;
+}
+
 // No host synchronisation: the sorted slot count stays on the device.  In the
 // compact layout it only shrinks, so n_upper still bounds it; in the binned
 // layout n_upper becomes the host bound on the span of the ranges.
 // compact_only keeps the compact layout even when the binned one is on.
 pic_status_t sort_species(Ctx *c, int s, cudaStream_t st, bool compact_only = false) {
+    pic_status_t sr = seal_pending(c, st);
+    if (sr != PIC_OK) return sr;
     const int from = c->cur[s], to = 1 - from;
     SortScratch w{c->cell_count, c->cell_off, c->tile_R, c->tile_count, c->tile_cursor, c->scratch_i32};
     BinSort bins{};
@@ -416,6 +440,12 @@ pic_status_t upload_particles(Ctx *c, int s, const PT *p, int64_t base, cudaStre
             if (!src[k]) return fail(c, PIC_ERR_ARG, "null particle array");
     }
     const size_t n = (size_t)p->n;
+    if (base == 0) {
+        c->unsealed[s] = false;  // the upload replaces the layout
+    } else {
+        pic_status_t r = seal_pending(c, st);  // appended after sealed slots
+        if (r != PIC_OK) return r;
+    }
     SpeciesBuf &B = c->buf[s][c->cur[s]];
     const size_t cap = (size_t)c->cfg.sp[s].capacity;
     int32_t *dix = c->scratch_i32, *diy = c->scratch_i32 + cap, *diz = c->scratch_i32 + 2 * cap;
@@ -931,6 +961,8 @@ pic_status_t pic_gather_push_spin(void *ctx, void *stream) {
     if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
     if (c->pending_deposit) return fail(c, PIC_ERR_STATE, "a move is waiting for pic_deposit");
     cudaStream_t st = S(stream);
+    pic_status_t sr = seal_pending(c, st);  // the split kernels read every slot
+    if (sr != PIC_OK) return sr;
     for (int s = 0; s < c->cfg.nspecies; ++s) {
         if (!c->cfg.sp[s].mobile) continue;
         pic_status_t r = alloc_old(c, s);
@@ -1047,16 +1079,21 @@ pic_status_t pic_push_deposit(void *ctx, void *stream) {
     }));
     c->launches += bin ? 2 : 1;  // binned: the fused kernel and the overflow-range kernel
     if (bin) {
-        // the particles now live in the other buffer: seal its spare slots,
-        // clear the consumed buffer's counts for the next step
+        // the particles now live in the other buffer: its arrival bases for
+        // the next step, the consumed buffer's counters cleared; the slots
+        // outside the new segments are sealed only when a slot-wise kernel
+        // needs them (seal_pending)
         SealArgs a{};
         a.nranges = c->ntiles + 1;
+        a.fill = false;
+        a.counters = true;
         for (int s = 0; s < c->cfg.nspecies; ++s) {
             if (!c->cfg.sp[s].mobile) continue;
             const int to = 1 - c->cur[s];
             a.sp[a.nsp++] = SealSpecies{c->buf[s][to].cell, c->tile_start[s], c->bin_cnt[s][to],
                                         c->bin_cnt[s][c->cur[s]]};
             c->cur[s] = to;
+            c->unsealed[s] = true;
         }
         CK(launch_seal_bins(a, S(stream)));
         c->launches += 1;
@@ -1138,6 +1175,8 @@ pic_status_t pic_polarization(void *ctx, int s, double emin, double emax, pic_mo
     if (s < 0 || s >= c->cfg.nspecies || !out) return fail(c, PIC_ERR_ARG, "bad species or output");
     if (c->pending_deposit) return fail(c, PIC_ERR_STATE, "a move is waiting for pic_deposit");
     cudaStream_t st = S(stream);
+    pic_status_t sr = seal_pending(c, st);
+    if (sr != PIC_OK) return sr;
     CK(with_real(c, [&](auto z) {
         using T = decltype(z);
         const T lo = std::isinf(emin) && emin < 0 ? -(T)INFINITY : (T)emin;
@@ -1168,6 +1207,8 @@ pic_status_t pic_energy_histogram(void *ctx, int s, double emin, double emax, in
         return fail(c, PIC_ERR_ARG, "need finite emin < emax (and emin > 0 for log bins)");
     if (c->pending_deposit) return fail(c, PIC_ERR_STATE, "a move is waiting for pic_deposit");
     cudaStream_t st = S(stream);
+    pic_status_t sr = seal_pending(c, st);
+    if (sr != PIC_OK) return sr;
     CK(with_real(c, [&](auto z) {
         using T = decltype(z);
         return launch_histogram<T>(dev_species<T>(c, s, c->cur[s]), (T)(c->cfg.sp[s].m * kMec2Mev), (T)emin,
@@ -1183,6 +1224,8 @@ pic_status_t pic_capture_background(void *ctx, void *stream) {
     if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
     c->has_background = true;
     cudaStream_t st = S(stream);
+    pic_status_t sr = seal_pending(c, st);
+    if (sr != PIC_OK) return sr;
     CK(cudaMemsetAsync(c->rho, 0, c->plane * c->rb, st));
     CK(with_real(c, [&](auto z) {
         using T = decltype(z);
@@ -1205,6 +1248,8 @@ pic_status_t pic_gauss_residual(void *ctx, double out[2], void *stream) {
     if (!out) return fail(c, PIC_ERR_ARG, "null output");
     if (c->pending_deposit) return fail(c, PIC_ERR_STATE, "a move is waiting for pic_deposit");
     cudaStream_t st = S(stream);
+    pic_status_t sr = seal_pending(c, st);
+    if (sr != PIC_OK) return sr;
     CK(cudaMemsetAsync(c->rho, 0, c->plane * c->rb, st));
     c->launches += c->cfg.nspecies + 2;
     const bool open = c->cfg.bc_x == PIC_BC_OPEN;

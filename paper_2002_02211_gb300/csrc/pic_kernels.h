@@ -105,6 +105,8 @@ struct SealSpecies {
 struct SealArgs {
     SealSpecies sp[PIC_MAXSP];
     int nsp, nranges;
+    bool fill = true;      // write PIC_DEAD into the slots outside the segments
+    bool counters = true;  // arrival bases of cnt_new, cnt_zero cleared
 };
 cudaError_t launch_seal_bins(const SealArgs &a, cudaStream_t st);
 cudaError_t launch_pack_cells(const int32_t *ix, const int32_t *iy, uint32_t *cell, int n,
