@@ -843,8 +843,9 @@ static pic_status_t get_particles_t(Ctx *c, int s, PT *out, cudaStream_t st) {
         }
     }
     CK(cudaMemcpyAsync(out->id, B.id, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    return PIC_OK;
+    // device error flags of the steps before (a binned step that dropped
+    // particles, a non-finite value) are reported with the state they concern
+    return check_flags(c, st);
 }
 
 extern "C" {

@@ -185,3 +185,32 @@ def test_binned_layout_feeds_the_slot_wise_reductions():
     r_max, _ = sim.gauss_residual()
     r_orc = np.abs(orc.gauss_residual()).max()
     assert abs(r_max - r_orc) < 1e-4 + 1e-3 * r_orc, (r_max, r_orc)
+
+
+def test_binned_steps_then_split_path_and_fresh_upload():
+    # the split kernels read every slot: the stale slots the binned steps
+    # leave are sealed first; a fresh upload replaces the layout
+    wl = W.small_case3(nx=34, ny=16, nz=12, ppc=2, u_th=1.2, bc_x="periodic", pol="none", two_species=True)
+    sim, orc, parts = make_pair(wl, sort_every=4, bins=(25, 16))
+    sim.step(3)
+    orc.step(3)
+    sim.gather_push_spin()
+    sim.deposit()
+    sim.field_update()
+    orc.step(1)
+    sim.step(2)
+    orc.step(2)
+    for s in range(2):
+        compare_particles(sim, orc, s, 1e-4, 1e-4, 1e-4)
+    # upload the oracle's state over the binned layout and step on
+    sim.step(2)
+    for s, d in enumerate(parts):
+        sim.set_particles(s, d)
+    orc2 = oracle.OracleSim(wl, parts, fields=None)
+    sim.set_fields({k: orc2.f[k].astype(np.float32) for k in ("ex", "ey", "ez", "bx", "by", "bz")})
+    sim.set_step(0)
+    sim.step(2)
+    orc2.step(2)
+    for s in range(2):
+        compare_particles(sim, orc2, s, 1e-4, 1e-4, 1e-4)
+    sim.sync()  # no device error flag left (no particle dropped)
