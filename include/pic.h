@@ -113,10 +113,14 @@ typedef struct {
                                     particle buffer, so particles never drift out
                                     of their tile between sorts.  A range that
                                     fills spills into one shared overflow range;
-                                    the tile sort (every sort_every steps)
-                                    re-sizes the ranges.  Mobile species need
+                                    the tile sort (every sort_every steps, and
+                                    early once the overflow range is past half
+                                    full) re-sizes the ranges; particles that
+                                    find the overflow range full too are lost
+                                    and the next synchronising call returns
+                                    PIC_ERR_OVERFLOW.  Mobile species need
                                     capacity >= n (1 + pct / 100) + ntiles
-                                    (bin_min_extra + 7) + max(1024, n / 64);
+                                    (bin_min_extra + 7) + max(1024, n / 4);
                                     otherwise the compact layout is kept.       */
     int bin_min_extra;           /* spare slots each tile range keeps at least  */
 } pic_config_t;

@@ -188,7 +188,7 @@ def bin_capacity(n: int, ntiles: int, headroom_pct: int, min_extra: int) -> int:
     """Slots a mobile species of n particles needs for the binned 3D3V layout:
     every tile range grown by its headroom and rounded up to 8, plus the
     overflow range."""
-    return int(n + n * headroom_pct // 100 + ntiles * (min_extra + 7) + max(1024, n // 64) + 8)
+    return int(n + n * headroom_pct // 100 + ntiles * (min_extra + 7) + max(1024, n // 4) + 8)
 
 
 def config_from_workload(wl, capacity_factor: float = 1.0, sort_every: int = 0, tile=None,

@@ -313,10 +313,12 @@ cudaError_t launch_unpack_cells3(const uint32_t *cell, int32_t *ix, int32_t *iy,
 //  - fill: write PIC_DEAD into the slots of the range outside its two
 //    segments (slot-wise kernels then read the layout as a compact one with
 //    holes; the binned step itself reads only the segments).
-__device__ __forceinline__ void bin_counters(const SealSpecies &S, int nr, int r) {
+__device__ __forceinline__ void bin_counters(const SealSpecies &S, int nr, int r, volatile int *alert) {
     const BinRange b = bin_range(S.tile_start, S.cnt_new, nr, r);
     S.cnt_new[3 * nr + r] = b.beg + b.len;
     if (S.cnt_zero) S.cnt_zero[r] = S.cnt_zero[nr + r] = S.cnt_zero[2 * nr + r] = 0;
+    // the overflow range (the last one) past half full: ask for a re-bin
+    if (alert && r == nr - 1 && 2 * b.len > S.tile_start[r + 1] - b.beg) *alert = 1;
 }
 
 // fill (and counters): one warp per range
@@ -329,7 +331,7 @@ __global__ void __launch_bounds__(256) k_seal_bins(const SealArgs a) {
         const int end = S.tile_start[r + 1], back_end = b.beg + b.split + (b.len - b.front);
         for (int i = b.beg + b.front + lane; i < b.beg + b.split; i += 32) S.cell[i] = PIC_DEAD;
         for (int i = back_end + lane; i < end; i += 32) S.cell[i] = PIC_DEAD;
-        if (lane == 0 && a.counters) bin_counters(S, nr, r);
+        if (lane == 0 && a.counters) bin_counters(S, nr, r, a.ovf_alert);
     }
 }
 
@@ -337,7 +339,7 @@ __global__ void __launch_bounds__(256) k_seal_bins(const SealArgs a) {
 __global__ void __launch_bounds__(256) k_bin_counters(const SealArgs a) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= a.nranges) return;
-    for (int s = 0; s < a.nsp; ++s) bin_counters(a.sp[s], a.nranges, r);
+    for (int s = 0; s < a.nsp; ++s) bin_counters(a.sp[s], a.nranges, r, a.ovf_alert);
 }
 
 cudaError_t launch_seal_bins(const SealArgs &a, cudaStream_t st) {

@@ -82,9 +82,19 @@ struct Ctx {
     // (stale records); seal_pending writes PIC_DEAD there before any kernel
     // that reads every slot
     bool unsealed[PIC_MAX_SPECIES] = {};
+    // host-mapped flag the binned step raises when an overflow range is past
+    // half full; the next pic_push_deposit that sees it re-bins first.  It
+    // is read without synchronising, so it takes effect at the first step the
+    // host issues after the GPU raised it; a range that still fills before
+    // that drops particles and reports PIC_ERR_OVERFLOW.
+    volatile int *ovf_alert = nullptr;
+    int *ovf_alert_dev = nullptr;
     int32_t *bin_cnt[PIC_MAX_SPECIES][2] = {};
     int64_t n_live[PIC_MAX_SPECIES] = {};
-    static constexpr int kBinCtas = 8;  // CTAs of the overflow-range kernel
+    // CTAs of the overflow-range kernel: one per 256 slots of the largest
+    // overflow range, between kBinCtasMin and kBinCtasMax
+    static constexpr int kBinCtasMin = 8, kBinCtasMax = 152 * 4;
+    int bin_ctas = kBinCtasMin;
     int since_sort = 0;
     long long launches = 0;  // kernels launched by this context
     std::string last_error;
@@ -350,7 +360,7 @@ pic_status_t check_flags(Ctx *c, cudaStream_t st) {
 bool bin_plan(const Ctx *c, int s, int *ovf_cap, int64_t *span) {
     if (!c->binned || !c->cfg.sp[s].mobile) return false;
     const int64_t n = c->n_live[s];
-    const int64_t ovf = ((std::max<int64_t>(1024, n / 64) + 7) / 8) * 8;
+    const int64_t ovf = ((std::max<int64_t>(1024, n / 4) + 7) / 8) * 8;
     const int64_t bound = n + n * c->cfg.bin_headroom_pct / 100 +
                           (int64_t)c->ntiles * (c->cfg.bin_min_extra + 7) + ovf;
     if (bound > c->cfg.sp[s].capacity) return false;
@@ -405,8 +415,11 @@ pic_status_t sort_species(Ctx *c, int s, cudaStream_t st, bool compact_only = fa
     }));
     c->launches += bin ? 7 : 6;  // rank, layout, three scan passes, scatter (, seal)
     c->cur[s] = to;
-    if (bin)
+    if (bin) {
         c->n_upper[s] = (int)span;
+        const int want = (bins.ovf_cap + 255) / 256;
+        c->bin_ctas = std::min(Ctx::kBinCtasMax, std::max(c->bin_ctas, want));
+    }
     else if (c->sp_binned[s])
         c->n_upper[s] = (int)std::min<int64_t>(c->n_upper[s], c->n_live[s]);
     c->sp_binned[s] = bin;
@@ -521,7 +534,7 @@ pic_status_t retile(Ctx *c, int tx, int ty, cudaStream_t st) {
     CK(cudaMalloc(&c->cell_off, cells * sizeof(int32_t)));
     CK(cudaMalloc(&c->tile_R, c->ntiles * sizeof(int32_t)));
     CK(cudaMalloc(&c->tile_cursor, c->ntiles * sizeof(int32_t)));
-    CK(cudaMalloc(&c->diag_rows, (size_t)(c->ntiles + Ctx::kBinCtas) * PIC_MAX_SPECIES * 8 * sizeof(double)));
+    CK(cudaMalloc(&c->diag_rows, (size_t)(c->ntiles + Ctx::kBinCtasMax) * PIC_MAX_SPECIES * 8 * sizeof(double)));
     pic_status_t r = make_tensor_map(c);
     if (r != PIC_OK) return r;
     for (int s = 0; s < c->cfg.nspecies; ++s) {
@@ -650,6 +663,13 @@ pic_status_t pic_create(const pic_config_t *cfg, void *stream, void **ctx_out) {
         }
         CKC(cudaMalloc(&c->tile_start[s], (c->ntiles + 2) * sizeof(int32_t)));
         CKC(cudaMemsetAsync(c->tile_start[s], 0, (c->ntiles + 2) * sizeof(int32_t), st));
+        if (c->binned && cfg->sp[s].mobile && !c->ovf_alert) {
+            int *h = nullptr;
+            CKC(cudaHostAlloc(reinterpret_cast<void **>(&h), sizeof(int), cudaHostAllocMapped));
+            *h = 0;
+            c->ovf_alert = h;
+            CKC(cudaHostGetDevicePointer(reinterpret_cast<void **>(&c->ovf_alert_dev), h, 0));
+        }
         if (c->binned && cfg->sp[s].mobile)
             for (int b = 0; b < 2; ++b) {
                 CKC(cudaMalloc(&c->bin_cnt[s][b], 4 * (c->ntiles + 1) * sizeof(int32_t)));
@@ -671,7 +691,7 @@ pic_status_t pic_create(const pic_config_t *cfg, void *stream, void **ctx_out) {
     CKC(cudaMalloc(&c->partials, (size_t)reduce_blocks() * 8 * sizeof(double)));
     CKC(cudaMalloc(&c->result, 64 * sizeof(double)));  // moments results and diagnostic column sums
     CKC(cudaMalloc(&c->hist, (size_t)PIC_MAX_HIST_BINS * 5 * sizeof(double)));
-    CKC(cudaMalloc(&c->diag_rows, (size_t)(c->ntiles + Ctx::kBinCtas) * PIC_MAX_SPECIES * 8 * sizeof(double)));
+    CKC(cudaMalloc(&c->diag_rows, (size_t)(c->ntiles + Ctx::kBinCtasMax) * PIC_MAX_SPECIES * 8 * sizeof(double)));
     CKC(cudaMalloc(&c->diag_shift, PIC_MAX_SPECIES * sizeof(double)));
     CKC(cudaMemsetAsync(c->diag_shift, 0, PIC_MAX_SPECIES * sizeof(double), st));
     CKC(cudaMalloc(&c->diag_out, PIC_MAX_SPECIES * sizeof(pic_moments_dev)));
@@ -732,6 +752,7 @@ void pic_destroy(void *ctx) {
     cudaFree(c->diag_out);
     cudaFree(c->laser_prof);
     cudaFree(c->hist);
+    if (c->ovf_alert) cudaFreeHost(const_cast<int *>(c->ovf_alert));
     delete c;
 }
 
@@ -1034,8 +1055,14 @@ pic_status_t pic_push_deposit(void *ctx, void *stream) {
         D.rows = c->diag_rows;
     }
     // binned layout: every mobile species must be in it (after a set of
-    // particles, a compacting read-back or a window shift, re-bin first)
-    if (c->binned && !all_binned(c)) {
+    // particles, a compacting read-back or a window shift, re-bin first); an
+    // overflow range past half full also asks for a re-bin
+    bool rebin = false;
+    if (c->binned && c->ovf_alert && *c->ovf_alert) {
+        *c->ovf_alert = 0;
+        rebin = true;
+    }
+    if (c->binned && (rebin || !all_binned(c))) {
         // re-bin every species when the capacities allow it, else bring the
         // binned ones back to the compact layout the compact kernel reads
         bool fits = true;
@@ -1058,7 +1085,7 @@ pic_status_t pic_push_deposit(void *ctx, void *stream) {
             StepParams3<T> P = step_params3<T>(c);
             P.diag = D;
             if (bin) {
-                P.nextra = Ctx::kBinCtas;
+                P.nextra = c->bin_ctas;
                 for (int s = 0; s < c->cfg.nspecies; ++s) {
                     if (!c->cfg.sp[s].mobile) continue;
                     const int to = 1 - c->cur[s];
@@ -1088,6 +1115,7 @@ pic_status_t pic_push_deposit(void *ctx, void *stream) {
         a.nranges = c->ntiles + 1;
         a.fill = false;
         a.counters = true;
+        a.ovf_alert = c->ovf_alert_dev;
         for (int s = 0; s < c->cfg.nspecies; ++s) {
             if (!c->cfg.sp[s].mobile) continue;
             const int to = 1 - c->cur[s];
@@ -1100,7 +1128,7 @@ pic_status_t pic_push_deposit(void *ctx, void *stream) {
         c->launches += 1;
     }
     if (diag) {
-        const int ncols = c->ntiles + (bin ? Ctx::kBinCtas : 0);
+        const int ncols = c->ntiles + (bin ? c->bin_ctas : 0);
         CK(launch_diag_final(c->diag_rows, ncols, c->cfg.nspecies, c->diag_shift, c->diag_out, c->result,
                              S(stream)));
         c->launches += 2;

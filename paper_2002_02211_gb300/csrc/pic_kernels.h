@@ -107,6 +107,9 @@ struct SealArgs {
     int nsp, nranges;
     bool fill = true;      // write PIC_DEAD into the slots outside the segments
     bool counters = true;  // arrival bases of cnt_new, cnt_zero cleared
+    // with counters: set to 1 when an overflow range holds more than half its
+    // slots (host-mapped memory the next step reads to re-bin in time)
+    volatile int *ovf_alert = nullptr;
 };
 cudaError_t launch_seal_bins(const SealArgs &a, cudaStream_t st);
 cudaError_t launch_pack_cells(const int32_t *ix, const int32_t *iy, uint32_t *cell, int n,

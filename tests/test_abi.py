@@ -98,5 +98,5 @@ def test_bin_capacity_covers_the_range_bound():
     cfg = pic.config_from_workload(wl, bins=(25, 16))
     n = 2 * (wl.nx - 4) * wl.ny * wl.nz
     ntiles = -(-wl.nx // 16) * -(-wl.ny // 4) * -(-wl.nz // 4)
-    bound = n + n * 25 // 100 + ntiles * (16 + 7) + ((max(1024, n // 64) + 7) // 8) * 8
+    bound = n + n * 25 // 100 + ntiles * (16 + 7) + ((max(1024, n // 4) + 7) // 8) * 8
     assert cfg.sp[0].capacity >= bound
