@@ -199,12 +199,18 @@ pic_status_t pic_set_particles(void *ctx, int species, const pic_particles_t *p,
 pic_status_t pic_set_particles_f64(void *ctx, int s, const pic_particles_f64_t *p, void *stream);
 
 /* Number of particle slots of one species (live and removed since the last
- * sort).  Synchronises the legacy default stream. */
+ * sort; in the binned 3D3V layout the span of the tile ranges and the
+ * overflow range, whose spare slots hold no particle).  An upper bound for
+ * the room pic_get_particles needs.  Synchronises the legacy default stream. */
 pic_status_t pic_get_count(void *ctx, int species, int64_t *n);
 
 /* Copies every slot into caller arrays with room for out->n entries (set
  * out->n to that room; PIC_ERR_ARG if the slots do not fit); on return out->n
- * is the slot count.  A removed particle has ix = iy = -1.  Synchronous.
+ * is the slot count.  A removed particle has ix = iy = -1.  A species in the
+ * binned 3D3V layout is first sorted into the compact layout (the next step
+ * re-bins), so out->n may be below pic_get_count.  Returns the device error
+ * flags the steps before left (PIC_ERR_OVERFLOW if a binned step lost
+ * particles, PIC_ERR_NAN, ...).  Synchronous.
  * With precision 64 the values are rounded to float32; pic_get_particles_f64
  * returns them at full width (and widens float32 state exactly). */
 pic_status_t pic_get_particles(void *ctx, int species, pic_particles_t *out, void *stream);
