@@ -2,9 +2,12 @@
 """Throughput of the PIC + Thomas-BMT step on GB300.
 
 One step = the fused gather / Boris / spin / advance / Esirkepov kernel
-(pic_push_deposit), the Yee update (pic_field_update), the tile sort every
---sort-every steps and, every --diag-every steps, the FP64 Eq. (4) moments of
-every species (accumulated inside the fused kernel).  Workloads:
+(pic_push_deposit; in 3D3V by default in the binned layout, where it stores
+every particle into its new tile's slot range), the Yee update
+(pic_field_update), the tile sort every --sort-every steps (3D3V binned: a
+re-bin every 64 steps; --compact for the compact layout sorted every 2) and,
+every --diag-every steps, the FP64 Eq. (4) moments of every species
+(accumulated inside the fused kernel).  Workloads:
 
   config2 (default)  3D3V laser-wakefield precision study: 512 x 256 x 256
                      cells (dx = lambda/20, dy = dz = lambda/8), 2 ppc
