@@ -49,6 +49,58 @@ __global__ void __launch_bounds__(256) k_b_half3(const MeshParams3<R> m, R hdx, 
     }
 }
 
+// The same for float, four cells of a row per thread: 16-byte loads and
+// stores (rows are padded to a multiple of 32 cells, so a group of four starts
+// 16-byte aligned and stays inside its row's storage).  Cells past nx keep
+// their values; each cell's x + 1 neighbour is the next cell of the group, the
+// next group's first, or column 0 when x is periodic and the cell ends the row.
+__global__ void __launch_bounds__(128) k_b_half3_f4(const MeshParams3<float> m, float hdx, float hdy, float hdz) {
+    const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int j = blockIdx.y, k = blockIdx.z;
+    if (i0 >= m.nx) return;
+    const int jp = j + 1 == m.ny ? 0 : j + 1, kp = k + 1 == m.nz ? 0 : k + 1;
+    const size_t row = (size_t)m.ld, slab = (size_t)m.ny * m.ld, P = m.plane;
+    const size_t r0 = (size_t)k * slab + (size_t)j * row;  // start of the row
+    const size_t c = r0 + i0, cjp = (size_t)k * slab + (size_t)jp * row + i0, ckp = (size_t)kp * slab + (size_t)j * row + i0;
+    float *EB = m.EB;
+    auto ld4 = [&](size_t o) { return *reinterpret_cast<const float4 *>(EB + o); };
+    auto arr = [](const float4 v, float a[4]) { a[0] = v.x, a[1] = v.y, a[2] = v.z, a[3] = v.w; };
+    float ex[4], ey[4], ez[4], ezjp[4], eykp[4], exkp[4], exjp[4], bx[4], by[4], bz[4];
+    arr(ld4(c), ex);
+    arr(ld4(P + c), ey);
+    arr(ld4(2 * P + c), ez);
+    arr(ld4(2 * P + cjp), ezjp);
+    arr(ld4(P + ckp), eykp);
+    arr(ld4(ckp), exkp);
+    arr(ld4(cjp), exjp);
+    arr(ld4(3 * P + c), bx);
+    arr(ld4(4 * P + c), by);
+    arr(ld4(5 * P + c), bz);
+    const bool periodic = m.bc_x == 1;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int i = i0 + q;
+        if (i >= m.nx) break;
+        bx[q] -= hdy * (ezjp[q] - ez[q]) - hdz * (eykp[q] - ey[q]);
+        if (i < m.nx - 1 || periodic) {
+            float eyn, ezn;  // Ey, Ez at the x + 1 neighbour
+            if (i + 1 < m.nx && q < 3) {
+                eyn = ey[q + 1];
+                ezn = ez[q + 1];
+            } else {
+                const size_t cn = r0 + (i + 1 < m.nx ? i + 1 : 0);
+                eyn = EB[P + cn];
+                ezn = EB[2 * P + cn];
+            }
+            by[q] -= hdz * (exkp[q] - ex[q]) - hdx * (ezn - ez[q]);
+            bz[q] -= hdx * (eyn - ey[q]) - hdy * (exjp[q] - ex[q]);
+        }
+    }
+    *reinterpret_cast<float4 *>(EB + 3 * P + c) = make_float4(bx[0], bx[1], bx[2], bx[3]);
+    *reinterpret_cast<float4 *>(EB + 4 * P + c) = make_float4(by[0], by[1], by[2], by[3]);
+    *reinterpret_cast<float4 *>(EB + 5 * P + c) = make_float4(bz[0], bz[1], bz[2], bz[3]);
+}
+
 // boundary B at t^{n+1/2}; one thread per (j, k).  With r = dt/dx, qy = dt/dy,
 // qz = dt/dz and the incident Ez (f) and Ey (g):
 //   By(-1/2) = (2 Ez(0) - (1-r) By(1/2) - qy dyBx - 4 f) / (1+r)
@@ -117,8 +169,15 @@ template <typename R>
 cudaError_t launch_field_update3(const MeshParams3<R> &m, R *bnd, const double *prof, const LaserParams &L,
                                  double dt, double dx, double dy, double dz, long long step, cudaStream_t st) {
     const dim3 blk(128), grd((m.nx + 127) / 128, m.ny, m.nz);
+    const dim3 grd4((m.nx + 4 * 128 - 1) / (4 * 128), m.ny, m.nz);
     const R hdx = (R)(0.5 * dt / dx), hdy = (R)(0.5 * dt / dy), hdz = (R)(0.5 * dt / dz);
-    k_b_half3<R><<<grd, blk, 0, st>>>(m, hdx, hdy, hdz);
+    auto b_half = [&]() {
+        if constexpr (sizeof(R) == 4)
+            k_b_half3_f4<<<grd4, blk, 0, st>>>(m, hdx, hdy, hdz);
+        else
+            k_b_half3<R><<<grd, blk, 0, st>>>(m, hdx, hdy, hdz);
+    };
+    b_half();
     if (m.bc_x == 0) {
         double fz, fy;
         laser_time_factors(L, ((double)step + 0.5) * dt, &fz, &fy);
@@ -126,7 +185,7 @@ cudaError_t launch_field_update3(const MeshParams3<R> &m, R *bnd, const double *
                                                                        dt / dz);
     }
     k_e_full3<R><<<grd, blk, 0, st>>>(m, bnd, (R)dt, (R)(dt / dx), (R)(dt / dy), (R)(dt / dz));
-    k_b_half3<R><<<grd, blk, 0, st>>>(m, hdx, hdy, hdz);
+    b_half();
     return cudaGetLastError();
 }
 

@@ -321,17 +321,30 @@ __device__ __forceinline__ void bin_counters(const SealSpecies &S, int nr, int r
     if (alert && r == nr - 1 && 2 * b.len > S.tile_start[r + 1] - b.beg) *alert = 1;
 }
 
-// fill (and counters): one warp per range
+// fill (and counters): one warp per tile range; the overflow range (the last,
+// a quarter of the particles or more) shared by the warps of kSealOvfBlocks
+// blocks after those of the tile ranges, so that no single warp walks it
+constexpr int kSealOvfBlocks = 64;
+
 __global__ void __launch_bounds__(256) k_seal_bins(const SealArgs a) {
-    const int r = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31, nr = a.nranges;
-    if (r >= nr) return;
+    const int nr = a.nranges, lane = threadIdx.x & 31, wb = (nr - 1 + 7) / 8;
+    int r, g = 0, G = 1;  // range, this warp's share of it, warps sharing it
+    if ((int)blockIdx.x < wb) {
+        r = blockIdx.x * 8 + (threadIdx.x >> 5);
+        if (r >= nr - 1) return;
+    } else {
+        r = nr - 1;
+        g = (blockIdx.x - wb) * 8 + (threadIdx.x >> 5);
+        G = (gridDim.x - wb) * 8;
+    }
+    const int off = 32 * g + lane, stride = 32 * G;
     for (int s = 0; s < a.nsp; ++s) {
         const SealSpecies &S = a.sp[s];
         const BinRange b = bin_range(S.tile_start, S.cnt_new, nr, r);
         const int end = S.tile_start[r + 1], back_end = b.beg + b.split + (b.len - b.front);
-        for (int i = b.beg + b.front + lane; i < b.beg + b.split; i += 32) S.cell[i] = PIC_DEAD;
-        for (int i = back_end + lane; i < end; i += 32) S.cell[i] = PIC_DEAD;
-        if (lane == 0 && a.counters) bin_counters(S, nr, r, a.ovf_alert);
+        for (int i = b.beg + b.front + off; i < b.beg + b.split; i += stride) S.cell[i] = PIC_DEAD;
+        for (int i = back_end + off; i < end; i += stride) S.cell[i] = PIC_DEAD;
+        if (g == 0 && lane == 0 && a.counters) bin_counters(S, nr, r, a.ovf_alert);
     }
 }
 
@@ -345,7 +358,7 @@ __global__ void __launch_bounds__(256) k_bin_counters(const SealArgs a) {
 cudaError_t launch_seal_bins(const SealArgs &a, cudaStream_t st) {
     if (a.nranges <= 0 || a.nsp <= 0 || !(a.fill || a.counters)) return cudaSuccess;
     if (a.fill)
-        k_seal_bins<<<(a.nranges + 7) / 8, 256, 0, st>>>(a);
+        k_seal_bins<<<(a.nranges - 1 + 7) / 8 + kSealOvfBlocks, 256, 0, st>>>(a);
     else
         k_bin_counters<<<(a.nranges + 255) / 256, 256, 0, st>>>(a);
     return cudaGetLastError();
