@@ -341,7 +341,8 @@ pic_status_t pic_launch_count(void *ctx, int64_t *count);
  * threads) race on it and must be ordered by the caller.
  *
  * n must be in [0, PIC_NOALLOC_MAX_PARTICLES] (else PIC_ERR_ARG, with the
- * reason in pic_last_error(NULL)); the pointers must be device pointers of
+ * reason in pic_last_error(NULL); the reduction's loops index with 64 bits, so
+ * every n up to that limit is safe); the pointers must be device pointers of
  * the current device.  Asynchronous on `stream`.  No counterpart in the
  * paper: this is an interface variant, not part of the method. */
 #define PIC_NOALLOC_MAX_PARTICLES 2147483647LL

@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(256) k_push_split(const StepParams<R> P, int s
     const GlobalMesh<R> gm{m.EB, m.J, m.nx, m.ny, m.ld, m.bc_x == 1, m.plane, P.err};
     unsigned bad = 0;
     const int n = *S.n;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
         const uint32_t c = S.cell[p];
         S.cell_old[p] = c;
         if (c == PIC_DEAD) continue;
@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(256) k_deposit_split(const StepParams<R> P, in
     const MeshParams<R> &m = P.m;
     const GlobalMesh<R> gm{m.EB, m.J, m.nx, m.ny, m.ld, m.bc_x == 1, m.plane, P.err};
     const int n = *S.n;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
         const uint32_t c0 = S.cell_old[p];
         if (c0 == PIC_DEAD) continue;
         const int ix = (int)(c0 & 0xFFFFu), iy = (int)(c0 >> 16);

@@ -533,7 +533,7 @@ __global__ void __launch_bounds__(256) k_push_split3(const StepParams3<R> P, int
     const MeshParams3<R> &m = P.m;
     unsigned bad = 0;
     const int n = *S.n;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
         const uint32_t c = S.cell[p];
         S.cell_old[p] = c;
         if (c == PIC_DEAD) continue;
@@ -576,7 +576,7 @@ __global__ void __launch_bounds__(256) k_deposit_split3(const StepParams3<R> P, 
     const DevSpecies3<R> &S = P.sp[s];
     const MeshParams3<R> &m = P.m;
     const int n = *S.n;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
         const uint32_t c0 = S.cell_old[p];
         if (c0 == PIC_DEAD) continue;
         int ix, iy, iz, ix1, iy1, iz1;

@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(RT) k_mom1(const DevSpecies<R> S, R m_mev, R e
     R f[6] = {0, 0, 0, 0, 0, 0};
     int k = 0;
     const int n = *S.n;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
         if (S.cell[p] == PIC_DEAD) continue;
         const R e = ekin(m_mev, S.ux[p], S.uy[p], S.uz[p]);
         if (!(e >= emin && e < emax)) continue;
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(RT) k_mom2(const DevSpecies<R> S, R m_mev, R e
     R f = R(0);
     int k = 0;
     const int n = *S.n;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
         if (S.cell[p] == PIC_DEAD) continue;
         const R e = ekin(m_mev, S.ux[p], S.uy[p], S.uz[p]);
         if (!(e >= emin && e < emax)) continue;
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(RT) k_mom2(const DevSpecies<R> S, R m_mev, R e
 template <typename R>
 __global__ void k_rho(const DevSpecies<R> S, const MeshParams<R> m, R *rho) {
     const int n = *S.n;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
         const uint32_t c = S.cell[p];
         if (c == PIC_DEAD) continue;
         const int ix = (int)(c & 0xFFFFu), iy = (int)(c >> 16);
@@ -193,7 +193,7 @@ template <typename R>
 __global__ void k_rho3(const DevSpecies3<R> S, const MeshParams3<R> m, R *rho) {
     const int n = *S.n;
     const size_t slab = (size_t)m.ny * m.ld;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
         const uint32_t c = S.cell[p];
         if (c == PIC_DEAD) continue;
         int ix, iy, iz;
@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(RT) k_hist(const DevSpecies<R> S, R m_mev, R e
     __syncthreads();
     const int n = *S.n;
     const R scale = log_bins ? R(1) / log(emax / emin) : R(1) / (emax - emin);
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
         if (S.cell[p] == PIC_DEAD) continue;
         const R e = ekin(m_mev, S.ux[p], S.uy[p], S.uz[p]);
         if (!(e >= emin && e < emax)) continue;

@@ -18,7 +18,7 @@ namespace {
 
 __global__ void k_pack(const int32_t *ix, const int32_t *iy, uint32_t *cell, int n, int xlo, int xhi,
                        int ny, unsigned *err) {
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
         const int x = ix[p], y = iy[p];
         if (x < xlo || x > xhi || y < 0 || y >= ny) {
             atomicOr(err, PIC_EF_RANGE);
@@ -30,7 +30,7 @@ __global__ void k_pack(const int32_t *ix, const int32_t *iy, uint32_t *cell, int
 }
 
 __global__ void k_unpack(const uint32_t *cell, int32_t *ix, int32_t *iy, int n) {
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
         const uint32_t c = cell[p];
         ix[p] = c == PIC_DEAD ? -1 : (int)(c & 0xFFFFu);
         iy[p] = c == PIC_DEAD ? -1 : (int)(c >> 16);
@@ -39,7 +39,7 @@ __global__ void k_unpack(const uint32_t *cell, int32_t *ix, int32_t *iy, int n) 
 
 __global__ void k_pack3(const int32_t *ix, const int32_t *iy, const int32_t *iz, uint32_t *cell, int n, int xlo,
                         int xhi, int ny, int nz, unsigned *err) {
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
         const int x = ix[p], y = iy[p], z = iz[p];
         if (x < xlo || x > xhi || y < 0 || y >= ny || z < 0 || z >= nz) {
             atomicOr(err, PIC_EF_RANGE);
@@ -51,7 +51,7 @@ __global__ void k_pack3(const int32_t *ix, const int32_t *iy, const int32_t *iz,
 }
 
 __global__ void k_unpack3(const uint32_t *cell, int32_t *ix, int32_t *iy, int32_t *iz, int n) {
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
         const uint32_t c = cell[p];
         int x = -1, y = -1, z = -1;
         if (c != PIC_DEAD) unpack_cell3(c, x, y, z);
@@ -97,7 +97,7 @@ template <class K>
 __global__ void k_rank(const uint32_t *cell, const int32_t *n_src, const K key, int32_t *cell_count,
                        int32_t *rank) {
     const int n = *n_src;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
         const uint32_t c = cell[p];
         int r = -1;
         if (c != PIC_DEAD) {
@@ -258,7 +258,7 @@ template <typename R, int NF, class K>
 __global__ void k_scatter(const SortArrays<R> src, const SortArrays<R> dst, const K kf, const int32_t *rank,
                           const int32_t *tile_start, const int32_t *tile_R, const int32_t *cell_off, int C) {
     const int n = *src.n;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
         const int r = rank[p];
         if (r < 0) continue;
         const uint32_t c = src.cell[p];
@@ -482,7 +482,7 @@ __global__ void k_ghost_from_column(const R *by, const R *bz, R *bnd, size_t row
 template <bool D3>
 __global__ void k_shift_cells(uint32_t *cell, const int32_t *n_src, int n) {
     const int np = *n_src;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < np; p += (long long)gridDim.x * blockDim.x) {
         const uint32_t c = cell[p];
         if (c == PIC_DEAD) continue;
         if (D3) {

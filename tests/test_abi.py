@@ -100,3 +100,17 @@ def test_bin_capacity_covers_the_range_bound():
     ntiles = -(-wl.nx // 16) * -(-wl.ny // 4) * -(-wl.nz // 4)
     bound = n + n * 25 // 100 + ntiles * (16 + 7) + ((max(1024, n // 4) + 7) // 8) * 8
     assert cfg.sp[0].capacity >= bound
+
+
+def test_moments_noalloc_checks_its_arguments_on_the_host():
+    # the size limit is checked before any CUDA call: the largest accepted
+    # count is 2^31 - 1 (the device loops index with 64 bits), one more is
+    # refused, and so are a negative count and null pointers
+    L = pic.load()
+    args = [C.c_void_p(1)] * 8 + [C.c_double(1.0), C.c_double(0.0), C.c_double(1.0), C.c_void_p(1), None]
+    for n in (2 ** 31, -1):
+        assert L.pic_moments_noalloc(n, *args) == -1
+        assert b"2^31" in L.pic_last_error(None)
+    nulls = [None] * 8 + args[8:]
+    assert L.pic_moments_noalloc(10, *nulls) == -1
+    assert b"null" in L.pic_last_error(None)

@@ -68,3 +68,23 @@ def test_moments_noalloc_rejects_sizes_beyond_the_maximum():
     with pytest.raises(pic.PicError) as e:
         pic.moments_noalloc(2 ** 31, 1, 1, 1, 1, 1, 1, 1, 1, 1.0, 0.0, 1.0, 1)
     assert e.value.status == -1 and "2^31" in str(e.value)
+
+
+def test_moments_noalloc_count_slot_for_tiny_inputs():
+    # the particle count the entry point stores on the device before the
+    # reduction: an empty call must give zero moments, one live particle its own
+    torch = pytest.importorskip("torch")
+    assert torch.cuda.is_available()
+    out = torch.full((7,), float("nan"), dtype=torch.float64, device="cuda")
+    dev = {k: torch.zeros(4, dtype=torch.float32, device="cuda") for k in ("ux", "uy", "uz", "sx", "sy", "sz", "w")}
+    dev["cell"] = torch.zeros(4, dtype=torch.int32, device="cuda")
+    ptrs = [dev[k].data_ptr() for k in ("cell", "ux", "uy", "uz", "sx", "sy", "sz", "w")]
+    pic.moments_noalloc(0, *ptrs, 1.0, -math.inf, math.inf, out.data_ptr())
+    torch.cuda.synchronize()
+    assert out.cpu().numpy().tolist() == [0.0] * 7
+    dev["sy"][0] = 1.0
+    dev["w"][0] = 0.25
+    pic.moments_noalloc(1, *ptrs, 1.0, -math.inf, math.inf, out.data_ptr())
+    torch.cuda.synchronize()
+    m = out.cpu().numpy()
+    assert m[:3].tolist() == [0.0, 1.0, 0.0] and m[3] == 0.25 and m[4] == 1.0
