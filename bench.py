@@ -54,15 +54,19 @@ import workloads as W  # noqa: E402
 
 METRIC = "particle-steps/s (push+spin+deposit) and % HBM roofline, FP32 vs FP64 at stated error"
 UNIT = "particle-steps/s"
-# algorithmic bytes of the fused kernel: per particle read cell, offsets, u(3),
-# s(3), w and write cell, offsets, u, s -- 2D3V 40 + 36 = 76 B, 3D3V (one more
-# offset) 44 + 40 = 84 B; per cell the E, B window (24 B) and the current added
-# to J (12 B)
+# Algorithmic bytes of the fused kernel, the minimum the method moves: per
+# particle read cell, offsets, u(3), s(3), w and write cell, offsets, u, s --
+# 2D3V 40 + 36 = 76 B, 3D3V (one more offset) 44 + 40 = 84 B; per cell the E,
+# B window (24 B) and the current added to J (12 B).  The cell word (read and
+# written, 8 B) keeps its width in FP64; every other byte doubles.
 BYTES_PER_PARTICLE = {2: 76, 3: 84}
-# the binned 3D3V layout writes each particle to the other buffer: the weight
-# and the id move with it (read id 4 B, write w and id 8 B): 96 B
-BYTES_PER_PARTICLE_BINNED = 96
+FIXED_WIDTH_BYTES = 8
 BYTES_PER_CELL = 36
+# Bytes the binned 3D3V layout adds per particle (it writes every particle to
+# the other buffer, so the weight and the id move with it: read id 4 B, write
+# w and id 8 B).  Reported beside the roofline, not counted as algorithmic;
+# the id (8 B) keeps its width in FP64, the weight (4 B) doubles.
+LAYOUT_BYTES_BINNED = (8, 4)
 # CPU samples of the workload (the oracle is slow): the CPU-baseline leg and
 # the precision study run CPU_SAMPLE_STEPS steps of CPU_SAMPLE (10-30 s of
 # oracle work); the reference arm runs every one of its --steps on REF_SAMPLE
@@ -103,7 +107,28 @@ def parse(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=10, help="timed steps of the FP64 line (0: skip)")
+    ap.add_argument("--start-step", type=int, default=-1,
+                    help="untimed steps before the warm-up ends (-1: the laser-plasma interaction phase, "
+                         "40 steps past the pulse peak's arrival at x = 0)")
     return ap.parse_args(argv)
+
+
+def interaction_start(wl, dt):
+    """First step of the laser-plasma interaction phase: 40 steps after the
+    envelope peak reaches x = 0 (the plasma starts two cells later), when the
+    front half of the pulse is already in the plasma."""
+    if wl.pol == "none" or wl.a0 <= 0:
+        return 0
+    return int(math.ceil(wl.t_peak_periods * 2 * math.pi / dt)) + 40
+
+
+def fused_bytes(dim, n_particles, cells, precision, binned):
+    """(algorithmic bytes, layout bytes) of one fused-kernel launch."""
+    wb = precision // 32
+    alg = (FIXED_WIDTH_BYTES + (BYTES_PER_PARTICLE[dim] - FIXED_WIDTH_BYTES) * wb) * n_particles + \
+        BYTES_PER_CELL * wb * cells
+    lay = (LAYOUT_BYTES_BINNED[0] + LAYOUT_BYTES_BINNED[1] * wb) * n_particles if binned else 0
+    return alg, lay
 
 
 def workload(name, ny=0, nz=0):
@@ -257,14 +282,14 @@ def sample_workload(wl, table=None):
     return W.scaled(wl, **cut), ", ".join(f"{k}={v}" for k, v in cut.items())
 
 
-def cpu_sample(wl, table=None):
+def cpu_sample(wl, table=None, threads="single thread"):
     import oracle
     sample, cut = sample_workload(wl, table)
     parts = W.generate_particles(sample)
     sim = oracle.OracleSim(sample, parts)
     n = sum(len(p["x"]) for p in sim.p)
     shape = "x".join(str(v) for v in ((sample.nx, sample.ny, sample.nz) if wl.dim == 3 else (sample.nx, sample.ny)))
-    desc = f"{wl.name} with {cut} ({shape} cells, {n} particles), FP64 C oracle, single thread"
+    desc = f"{wl.name} with {cut} ({shape} cells, {n} particles), FP64 C oracle, {threads}"
     return sim, n, desc
 
 
@@ -275,10 +300,19 @@ def run_oracle_steps(sim, steps):
 
 
 def cpu_baseline(wl):
-    sim, n, desc = cpu_sample(wl)
+    """The oracle on a sample of the workload: its OpenMP build on every host
+    core (the push and the Yee stages in parallel, the deposit serial; the
+    same bits as the plain build) and, beside it, the plain build on one core."""
+    import oracle
+    with oracle.parallel() as nthreads:
+        psim, n, pdesc = cpu_sample(wl, threads=f"OpenMP build, {oracle.threads()} threads")
+        pdt = run_oracle_steps(psim, CPU_SAMPLE_STEPS)
+    sim, n1, desc = cpu_sample(wl)
     dt = run_oracle_steps(sim, CPU_SAMPLE_STEPS)
-    return {"value": n * CPU_SAMPLE_STEPS / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{CPU_SAMPLE_STEPS} steps of {desc}", "seconds": round(dt, 2)}, sim
+    return {"value": n * CPU_SAMPLE_STEPS / pdt, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+            "sample": f"{CPU_SAMPLE_STEPS} steps of {pdesc}", "seconds": round(pdt, 2),
+            "single_thread": {"value": n1 * CPU_SAMPLE_STEPS / dt, "cores": 1, "seconds": round(dt, 2),
+                              "sample": f"{CPU_SAMPLE_STEPS} steps of {desc}"}}, sim
 
 
 def precision_study(pic, wl, oracle_sim, bins=None):
@@ -323,16 +357,18 @@ def main_reference(args):
     wl = workload(args.workload, args.ny, args.nz)
     if rank != 0:
         return
-    sim, n, desc = cpu_sample(wl, REF_SAMPLE)
-    run_oracle_steps(sim, args.warmup)
-    dt = run_oracle_steps(sim, args.steps)
+    import oracle
+    with oracle.parallel() as nthreads:   # every host core; the plain build's bits
+        sim, n, desc = cpu_sample(wl, REF_SAMPLE, threads=f"OpenMP build, {nthreads} threads")
+        run_oracle_steps(sim, args.warmup)
+        dt = run_oracle_steps(sim, args.steps)
     v = n * args.steps / dt
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
             "config": {"workload": wl.name, "sample": desc},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": nthreads, "kind": "oracle",
                              "sample": f"{args.steps} steps of {desc}"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -371,13 +407,14 @@ def main_ours(args):
         sim.capture_background()
     sim.sync()
 
-    state = {"since_sort": 0, "k": 0}
+    state = {"since_sort": 0, "k": 0, "sorts": 0}
     ev_pairs = []
 
     def one_step(record):
         if state["since_sort"] >= args.sort_every:
             sim.sort()
             state["since_sort"] = 0
+            state["sorts"] += 1
         if record:
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -392,12 +429,18 @@ def main_ours(args):
     # a8: the Eq. (4) moments of every species are accumulated inside the
     # fused kernel every diag_every steps (no extra pass, no host sync)
     sim.set_diagnostics(args.diag_every)
-    for _ in range(args.warmup):
+    # untimed: the run is advanced to the laser-plasma interaction phase (the
+    # last `warmup` of these steps are the warm-up proper)
+    dt = sim.grid()[0]
+    start_step = args.start_step if args.start_step >= 0 else interaction_start(wl, dt)
+    start_step = max(start_step, args.warmup)
+    for _ in range(start_step):
         one_step(False)
     sim.sync()
 
     clocks = ClockSampler(local)
     launches0 = sim.launch_count()
+    sorts0 = state["sorts"]
     barrier(world)
     torch.cuda.synchronize(dev)
     clocks.start()
@@ -410,10 +453,23 @@ def main_ours(args):
     barrier(world)
     clk = clocks.stop()
     launches = sim.launch_count() - launches0
+    sorts_in = state["sorts"] - sorts0
     sim.sync()
     diag_step, diag = sim.get_diagnostics()
+    elapsed_raw = start.elapsed_time(end) * 1e-3
 
-    elapsed = start.elapsed_time(end) * 1e-3
+    # the tile sort (3D3V binned: the re-bin) runs every sort_every steps; when
+    # the timed steps hold fewer sorts than their share, the missing share of a
+    # measured sort is added to the time (never subtracted)
+    sa, sb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sa.record(stream)
+    sim.sort()
+    sb.record(stream)
+    torch.cuda.synchronize(dev)
+    sort_s = sa.elapsed_time(sb) * 1e-3
+    missing = max(0.0, args.steps / args.sort_every - sorts_in)
+    elapsed = elapsed_raw + missing * sort_s
+
     fused_ms = np.array([a.elapsed_time(b) for a, b in ev_pairs])
     t_fused = float(fused_ms.mean()) * 1e-3
     # the fused kernel over the run, in tenths (the laser enters and heats the plasma)
@@ -422,16 +478,22 @@ def main_ours(args):
     value = units / tmax
 
     peak, peak_kind = measured_hbm_peak()
-    wb = args.precision // 32  # algorithmic bytes scale with the real width (the cell word stays 4 B)
-    bpp = BYTES_PER_PARTICLE_BINNED if bins else BYTES_PER_PARTICLE[dim]
-    ints = 12 if bins else 4  # bytes per particle that stay 4 B wide in FP64 (cell word, id)
-    bytes_fused = (ints + (bpp - ints) * wb) * n_particles + BYTES_PER_CELL * wb * cells
+    wb = args.precision // 32
+    bytes_fused, bytes_layout = fused_bytes(dim, n_particles, cells, args.precision, bool(bins))
     achieved = bytes_fused / t_fused / 1e9
     tr = traffic_record(dim, wl, bool(bins)) if args.precision == 32 else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": tr["dram_bytes_per_launch"] if tr else None,
                 "kernel": KERNEL[dim][0], "kernel_ms": t_fused * 1e3, "kernel_ms_by_tenth": fused_trend,
-                "algorithmic_bytes": bytes_fused, "peak_source": f"{peak_kind} hbm_gbs"}
+                "algorithmic_bytes": bytes_fused,
+                "bytes_per_particle": BYTES_PER_PARTICLE[dim], "bytes_per_cell": BYTES_PER_CELL,
+                "layout_bytes": bytes_layout,
+                "layout_bytes_what": "binned layout: id read, w and id written per particle (not algorithmic)"
+                                     if bins else None,
+                "peak_source": f"{peak_kind} hbm_gbs"}
+    timing = {"start_step": start_step, "timed_steps": [start_step, start_step + args.steps],
+              "sorts_timed": sorts_in, "sort_ms": sort_s * 1e3,
+              "sort_share_added_ms": missing * sort_s * 1e3, "elapsed_raw_ms": elapsed_raw * 1e3}
 
     # end to end through the C ABI with host buffers: upload the particle state
     # from pinned memory, one step, read back the Eq. (4) moments
@@ -481,8 +543,7 @@ def main_ours(args):
             if wl.neutralizing_background:
                 s64.capture_background()
             s64.set_diagnostics(args.diag_every)
-            for _ in range(2):
-                s64.step(1)
+            s64.step(start_step)   # the same point of the run as the FP32 line
             s64.sync()
             barrier(world)
             torch.cuda.synchronize(dev)
@@ -495,6 +556,7 @@ def main_ours(args):
             s64.sync()
         fp64 = {"value": u64 / t64, "unit": UNIT, "ms_per_step": t64 * 1e3 / args.fp64_steps,
                 "steps": args.fp64_steps, "dtype": "f64",
+                "timed_steps": [start_step, start_step + args.fp64_steps],
                 "bound": "alu (FP64 arithmetic; GB300 FP64 is about 1/64 of its FP32 rate)"}
 
     cpu = None
@@ -518,8 +580,9 @@ def main_ours(args):
                                      if bins else "compact",
                            "l2": "inputs larger than L2 (particle state %.2f GB)"
                                  % (n_particles * (8 + (dim + 7) * 4 * wb) / 1e9),
+                           "start_step": start_step,
                            "parallelism": f"replicas x{world}"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "timing": timing, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": launches, "fp64": fp64, "precision_study": study,
                 "diagnostics": {"step": diag_step,
                                 "P": {sp.name: [round(v, 6) for v in d["P"]] for sp, d in zip(wl.species, diag)},
@@ -716,10 +779,83 @@ def main_adjoint(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# config1: the small L2-resident run as the latency case, pic_step replayed
+# from CUDA graphs against pic_step launching every kernel
+# ---------------------------------------------------------------------------
+def main_latency(args):
+    import torch
+
+    import paper_2002_02211_gb300 as pic
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    init_dist(world, "nccl")
+    dev = torch.device("cuda", local)
+    wl = workload(args.workload, args.ny, args.nz)
+    parts = W.generate_particles(wl)
+    n_particles = sum(len(p["ix"]) for p in parts)
+    sort_every = args.sort_every if args.sort_every > 0 else DEFAULT_SORT_EVERY[wl.dim]
+    stream = torch.cuda.Stream(device=dev)
+    out = {}
+    clk = None
+    for mode, graphs in (("graphs", 32), ("launched", 0)):
+        with pic.Simulation(pic.config_from_workload(wl, sort_every=sort_every), stream=stream) as sim:
+            for s, d in enumerate(parts):
+                sim.set_particles(s, d)
+            if wl.neutralizing_background:
+                sim.capture_background()
+            sim.set_graphs(graphs)
+            sim.set_diagnostics(args.diag_every)
+            # warm-up: a whole sort cycle, so every graph the timed steps use is captured
+            sim.step(max(args.warmup, 2 * sort_every))
+            sim.sync()
+            clocks = ClockSampler(local)
+            l0 = sim.launch_count()
+            g0 = sim.graph_stats()
+            barrier(world)
+            torch.cuda.synchronize(dev)
+            clocks.start()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0 = time.perf_counter()
+            a.record(stream)
+            sim.step(args.steps)
+            b.record(stream)
+            t_host = time.perf_counter() - t0
+            torch.cuda.synchronize(dev)
+            c = clocks.stop()
+            if mode == "graphs":
+                clk = c
+            t, u = combine(a.elapsed_time(b) * 1e-3, n_particles * args.steps, world, dev)
+            g1 = sim.graph_stats()
+            out[mode] = {"value": u / t, "ms_per_step": 1e3 * t / args.steps,
+                         "host_issue_ms_per_step": 1e3 * t_host / args.steps,
+                         "kernels_per_step": (sim.launch_count() - l0) / args.steps,
+                         "graph_launches_per_step": (g1[1] - g0[1] + g1[0] - g0[0]) / args.steps}
+            sim.sync()
+    if rank == 0:
+        g = out["graphs"]
+        line = {"metric": METRIC, "value": g["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": g["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": wl.name, "cells": [wl.nx, wl.ny], "particles": n_particles,
+                           "sort_every": sort_every, "diag_every": args.diag_every,
+                           "l2": "L2-resident (about 13 MB): the latency and graph case, not a roofline case",
+                           "parallelism": f"replicas x{world}"},
+                "pic_step": out, "graph_speedup": g["value"] / out["launched"]["value"],
+                "clocks": clk, "gpu_launches": int(round(g["kernels_per_step"] * args.steps))}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def main(argv=None):
     args = parse(argv)
     if args.impl == "reference":
         main_reference(args)
+    elif args.workload == "config1":
+        main_latency(args)
     elif args.workload == "config4":
         main_scan(args)
     elif args.workload == "config5":

@@ -118,7 +118,12 @@ typedef struct {
                                     full) re-sizes the ranges; particles that
                                     find the overflow range full too are lost
                                     and the next synchronising call returns
-                                    PIC_ERR_OVERFLOW.  Mobile species need
+                                    PIC_ERR_OVERFLOW.  The host keeps at most 4
+                                    binned steps in flight (before each it
+                                    waits for the one 4 steps back), so the
+                                    half-full alert acts within 4 steps
+                                    however far ahead the caller queues.
+                                    Mobile species need
                                     capacity >= n (1 + pct / 100) + ntiles
                                     (bin_min_extra + 7) + max(1024, n / 4);
                                     otherwise the compact layout is kept.       */
@@ -254,8 +259,24 @@ pic_status_t pic_push_deposit(void *ctx, void *stream);
 
 /* nsteps whole steps: pic_sort when sort_every steps have passed since the
  * last sort (counted across calls), then pic_push_deposit and
- * pic_field_update.  No host synchronisation. */
+ * pic_field_update.  No host synchronisation.
+ * In the compact layout each sort-free stretch of 2 or more steps (at most
+ * the pic_set_graphs limit, 32 by default) is replayed from a CUDA graph of
+ * its steps, captured at the first stretch of its length, diagnostic phase
+ * and buffer parity on a stream the context owns (ordered after and before
+ * `stream` by events): the same kernels with the same arguments as launched
+ * steps, one graph launch in place of 5-7 kernel launches a step.  The
+ * binned 3D3V layout launches its steps one by one (it decides between steps,
+ * on the host, whether to re-bin). */
 pic_status_t pic_step(void *ctx, int nsteps, void *stream);
+
+/* Longest stretch pic_step replays as one CUDA graph (0: launch every kernel,
+ * 1 .. 4096).  Drops the graphs captured so far. */
+pic_status_t pic_set_graphs(void *ctx, int max_steps);
+
+/* Graphs pic_step has captured and replayed on this context (a capture runs
+ * its stretch once; a replay re-runs a captured stretch). */
+pic_status_t pic_graph_stats(void *ctx, int64_t *captures, int64_t *replays);
 
 /* a8 inside the step: every `every` steps (0 turns it off) pic_push_deposit,
  * and so pic_step, also accumulates the Eq. (4) moments of every species over

@@ -11,6 +11,7 @@ holds the state in float64 numpy arrays.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import math
 import os
@@ -20,10 +21,15 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
+# the same sources built with OpenMP: the multi-core CPU baseline (its parallel
+# loops have independent iterations, so it gives the plain build's bits)
+_LIB_OMP_PATH = os.path.join(_HERE, "liboracle_omp.so")
 # a prebuilt oracle library to load instead (the mutation tests point it at
 # deliberately broken copies)
 _LIB_OVERRIDE = os.environ.get("PIC_ORACLE_LIB")
 _lib = None
+_lib_omp = None
+_parallel = False
 
 MEC2_MEV = 0.51099895
 BC = {"open": 0, "periodic": 1}
@@ -34,16 +40,36 @@ SOURCES = ("pic_oracle.c", "pic_oracle3.c")
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle sources into liboracle.so next to them (gcc, FP64, no FMA contraction)."""
+    """Compile the oracle sources into liboracle.so next to them (gcc, FP64, no
+    FMA contraction), and the same sources with OpenMP into liboracle_omp.so."""
     srcs = [os.path.join(_HERE, f) for f in SOURCES]
     newest = max(os.path.getmtime(f) for f in srcs + [os.path.join(_HERE, "pic_oracle.h")])
-    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
-        return _LIB_PATH
-    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-                           *srcs, "-o", tmp, "-lm"])
-    os.replace(tmp, _LIB_PATH)
+    for path, extra in ((_LIB_PATH, []), (_LIB_OMP_PATH, ["-fopenmp"])):
+        if not force and os.path.exists(path) and os.path.getmtime(path) >= newest:
+            continue
+        tmp = path + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", *extra,
+                               *srcs, "-o", tmp, "-lm"])
+        os.replace(tmp, path)
     return _LIB_PATH
+
+
+@contextlib.contextmanager
+def parallel():
+    """Oracle calls inside the block run on the OpenMP build (every host core
+    unless OMP_NUM_THREADS says otherwise); the results are the plain build's."""
+    global _parallel
+    old = _parallel
+    _parallel = True
+    try:
+        yield threads()
+    finally:
+        _parallel = old
+
+
+def threads() -> int:
+    """Threads the oracle calls use now (1 outside `parallel()`)."""
+    return int(lib().or_threads())
 
 
 class Grid(C.Structure):
@@ -86,13 +112,24 @@ class Parts3(C.Structure):
 
 
 def lib():
-    global _lib
+    global _lib, _lib_omp
+    if _parallel and not _LIB_OVERRIDE:
+        if _lib_omp is None:
+            build()
+            _lib_omp = _declare(C.CDLL(_LIB_OMP_PATH))
+        return _lib_omp
     if _lib is None:
         if _LIB_OVERRIDE:
             L = C.CDLL(_LIB_OVERRIDE)
         else:
             build()
             L = C.CDLL(_LIB_PATH)
+        _lib = _declare(L)
+    return _lib
+
+
+def _declare(L):
+    if True:
         G, S, F, P = C.POINTER(Grid), C.POINTER(Spec), C.POINTER(Fields), C.POINTER(Parts)
         G3, F3, P3 = C.POINTER(Grid3), C.POINTER(Fields3), C.POINTER(Parts3)
         d = C.c_double
@@ -128,8 +165,12 @@ def lib():
             fn = getattr(L, name)
             fn.restype = res
             fn.argtypes = args
-        _lib = L
-    return _lib
+        if hasattr(L, "or_threads"):
+            L.or_threads.restype = C.c_int
+            L.or_threads.argtypes = []
+        else:                     # a mutation copy built without the helper
+            L.or_threads = lambda: 1
+    return L
 
 
 def _dp(a):

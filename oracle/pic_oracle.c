@@ -210,6 +210,8 @@ void or_push(const or_grid_t *g, const or_species_t *sp, or_particles_t *p,
              const or_fields_t *f, double *x_old, double *y_old, double *vz)
 {
     double qm = sp->q / sp->m;
+    /* particles are independent here: the OpenMP build splits them over threads */
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < p->n; ++i) {
         x_old[i] = p->x[i];
         y_old[i] = p->y[i];
@@ -297,6 +299,7 @@ static void b_half(const or_grid_t *g, or_fields_t *f, double h)
 {
     long nx = g->nx, ny = g->ny;
     long last = g->bc_x == OR_BC_PERIODIC ? nx : nx - 1; /* By, Bz columns updated */
+#pragma omp parallel for schedule(static)
     for (long j = 0; j < ny; ++j) {
         long jp = yj(g, j + 1);
         for (long i = 0; i < nx; ++i) {
@@ -333,6 +336,7 @@ void or_field_update(const or_grid_t *g, or_fields_t *f, long step)
     b_half(g, f, 0.5 * dt);
     if (g->bc_x == OR_BC_OPEN) {
         double r = dt / g->dx, q = dt / g->dy, t = ((double)step + 0.5) * dt;
+#pragma omp parallel for schedule(static)
         for (long j = 0; j < ny; ++j) {
             double fin, gin;
             or_laser(g, t, (double)j * g->dy, 1, &fin);
@@ -346,6 +350,7 @@ void or_field_update(const or_grid_t *g, or_fields_t *f, long step)
             f->bz[cl] = (2.0 * f->ey[cl] - (1.0 - r) * f->bz[cl - 1]) / (1.0 + r);
         }
     }
+#pragma omp parallel for schedule(static)
     for (long j = 0; j < ny; ++j) {
         long jm = yj(g, j - 1);
         for (long i = 0; i < nx; ++i) {
@@ -517,4 +522,20 @@ void or_histogram(const or_species_t *sp, const or_particles_t *p, double emin_m
         out[5 * b + 3] += p->w[i] * p->sy[i];
         out[5 * b + 4] += p->w[i] * p->sz[i];
     }
+}
+
+/* Threads the parallel loops of this build use: 1 in the plain build; the
+ * OpenMP build (the multi-core CPU baseline) parallelises only loops whose
+ * iterations are independent (the per-particle push, the Yee stages by row),
+ * so its results are bit-identical to the plain build's. */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+int or_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }

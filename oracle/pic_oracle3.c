@@ -103,6 +103,8 @@ void or3_push(const or_grid3_t *g, const or_species_t *sp, or_particles3_t *p,
               const or_fields3_t *f, double *x_old, double *y_old, double *z_old)
 {
     double qm = sp->q / sp->m;
+    /* particles are independent here: the OpenMP build splits them over threads */
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < p->n; ++i) {
         x_old[i] = p->x[i];
         y_old[i] = p->y[i];
@@ -225,6 +227,7 @@ static void b_half3(const or_grid3_t *g, or_fields3_t *f, double h)
 {
     long nx = g->nx, ny = g->ny, nz = g->nz;
     long last = g->bc_x == OR_BC_PERIODIC ? nx : nx - 1;
+#pragma omp parallel for schedule(static)
     for (long k = 0; k < nz; ++k)
         for (long j = 0; j < ny; ++j)
             for (long i = 0; i < nx; ++i) {
@@ -255,6 +258,7 @@ void or3_field_update(const or_grid3_t *g, or_fields3_t *f, long step)
     b_half3(g, f, 0.5 * dt);
     if (g->bc_x == OR_BC_OPEN) {
         double r = dt / g->dx, qy = dt / g->dy, qz = dt / g->dz, t = ((double)step + 0.5) * dt;
+#pragma omp parallel for schedule(static)
         for (long k = 0; k < nz; ++k)
             for (long j = 0; j < ny; ++j) {
                 double fin, gin;
@@ -272,6 +276,7 @@ void or3_field_update(const or_grid3_t *g, or_fields3_t *f, long step)
                 f->bz[cl] = (2.0 * f->ey[cl] - (1.0 - r) * f->bz[cl - 1] + qz * dzbl) / (1.0 + r);
             }
     }
+#pragma omp parallel for schedule(static)
     for (long k = 0; k < nz; ++k)
         for (long j = 0; j < ny; ++j)
             for (long i = 0; i < nx; ++i) {

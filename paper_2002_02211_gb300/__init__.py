@@ -112,6 +112,8 @@ _SIGS = {
     "pic_sort": [C.c_void_p, C.c_void_p],
     "pic_push_deposit": [C.c_void_p, C.c_void_p],
     "pic_step": [C.c_void_p, C.c_int, C.c_void_p],
+    "pic_set_graphs": [C.c_void_p, C.c_int],
+    "pic_graph_stats": [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
     "pic_launch_count": [C.c_void_p, C.POINTER(C.c_int64)],
     "pic_polarization": [C.c_void_p, C.c_int, C.c_double, C.c_double, C.POINTER(pic_moments_t),
                          C.c_void_p],
@@ -415,6 +417,16 @@ class Simulation:
         v = C.c_int64()
         self._c(load().pic_launch_count(self.h, C.byref(v)))
         return v.value
+
+    def set_graphs(self, max_steps):
+        """pic_set_graphs: longest stretch pic_step replays from a CUDA graph (0: off)."""
+        self._c(load().pic_set_graphs(self.h, int(max_steps)))
+
+    def graph_stats(self):
+        """pic_graph_stats: (captures, replays)."""
+        a, b = C.c_int64(), C.c_int64()
+        self._c(load().pic_graph_stats(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
 
     def polarization(self, s, emin=-math.inf, emax=math.inf):
         m = pic_moments_t()

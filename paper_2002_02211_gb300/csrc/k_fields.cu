@@ -60,10 +60,17 @@ __device__ __forceinline__ void boundary_row(const MeshParams<R> &m, R *bnd, con
     EB[5 * P + cl] = (R)((2.0 * EB[1 * P + cl] - mr * EB[5 * P + cl - 1]) * ir);
 }
 
+// lf: NULL, or the device address of this step's laser time factors (fz, fy)
+// (a step replayed from a CUDA graph reads them from a table the host fills
+// before each replay; a launched step passes them by value)
 template <typename R>
 __global__ void k_boundary(const MeshParams<R> m, R *bnd, const double *prof, double fz, double fy, double r,
-                           double q) {
+                           double q, const double *lf) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (lf) {
+        fz = lf[0];
+        fy = lf[1];
+    }
     if (j < m.ny) boundary_row(m, bnd, prof, fz, fy, r, q, j);
 }
 
@@ -185,14 +192,15 @@ void laser_time_factors(const LaserParams &L, double t, double *fz, double *fy) 
 
 template <typename R>
 cudaError_t launch_field_update(const MeshParams<R> &m, R *bnd, const double *prof, const LaserParams &L,
-                                double dt, double dx, double dy, long long step, cudaStream_t st) {
+                                double dt, double dx, double dy, long long step, cudaStream_t st,
+                                const double *lf_dev) {
     const dim3 blk(256), grd((m.nx + 255) / 256, m.ny);
     const R hdx = (R)(0.5 * dt / dx), hdy = (R)(0.5 * dt / dy);
     k_b_half<R><<<grd, blk, 0, st>>>(m, hdx, hdy);
     if (m.bc_x == 0) {
         double fz, fy;
         laser_time_factors(L, ((double)step + 0.5) * dt, &fz, &fy);
-        k_boundary<R><<<(m.ny + 127) / 128, 128, 0, st>>>(m, bnd, prof, fz, fy, dt / dx, dt / dy);
+        k_boundary<R><<<(m.ny + 127) / 128, 128, 0, st>>>(m, bnd, prof, fz, fy, dt / dx, dt / dy, lf_dev);
     }
     k_e_full<R><<<grd, blk, 0, st>>>(m, bnd, (R)dt, (R)(dt / dx), (R)(dt / dy));
     k_b_half<R><<<grd, blk, 0, st>>>(m, hdx, hdy);
@@ -201,10 +209,10 @@ cudaError_t launch_field_update(const MeshParams<R> &m, R *bnd, const double *pr
 
 template cudaError_t launch_field_update<float>(const MeshParams<float> &, float *, const double *,
                                                 const LaserParams &, double, double, double, long long,
-                                                cudaStream_t);
+                                                cudaStream_t, const double *);
 template cudaError_t launch_field_update<double>(const MeshParams<double> &, double *, const double *,
                                                  const LaserParams &, double, double, double, long long,
-                                                 cudaStream_t);
+                                                 cudaStream_t, const double *);
 
 // transverse laser profile exp(-((y - yc)/w0)^2) at y_j (first ny) and y_{j+1/2}
 void laser_profile(const LaserParams &L, int ny, double *host) {

@@ -111,7 +111,11 @@ __global__ void __launch_bounds__(128) k_b_half3_f4(const MeshParams3<float> m, 
 // boundary column.  bnd holds By(-1/2) [nz][ny] then Bz(-1/2) [nz][ny].
 template <typename R>
 __global__ void k_boundary3(const MeshParams3<R> m, R *bnd, const double *prof, double fz, double fy, double r,
-                            double qy, double qz) {
+                            double qy, double qz, const double *lf) {
+    if (lf) {  // a step replayed from a CUDA graph: this step's factors from the host-filled table
+        fz = lf[0];
+        fy = lf[1];
+    }
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int k = blockIdx.y;
     if (j >= m.ny) return;
@@ -229,7 +233,8 @@ __global__ void __launch_bounds__(128) k_e_full3_f4(const MeshParams3<float> m, 
 
 template <typename R>
 cudaError_t launch_field_update3(const MeshParams3<R> &m, R *bnd, const double *prof, const LaserParams &L,
-                                 double dt, double dx, double dy, double dz, long long step, cudaStream_t st) {
+                                 double dt, double dx, double dy, double dz, long long step, cudaStream_t st,
+                                 const double *lf_dev) {
     const dim3 blk(128), grd((m.nx + 127) / 128, m.ny, m.nz);
     const dim3 grd4((m.nx + 4 * 128 - 1) / (4 * 128), m.ny, m.nz);
     const R hdx = (R)(0.5 * dt / dx), hdy = (R)(0.5 * dt / dy), hdz = (R)(0.5 * dt / dz);
@@ -244,7 +249,7 @@ cudaError_t launch_field_update3(const MeshParams3<R> &m, R *bnd, const double *
         double fz, fy;
         laser_time_factors(L, ((double)step + 0.5) * dt, &fz, &fy);
         k_boundary3<R><<<dim3((m.ny + 127) / 128, m.nz), 128, 0, st>>>(m, bnd, prof, fz, fy, dt / dx, dt / dy,
-                                                                       dt / dz);
+                                                                       dt / dz, lf_dev);
     }
     if constexpr (sizeof(R) == 4)
         k_e_full3_f4<<<grd4, blk, 0, st>>>(m, bnd, (R)dt, (R)(dt / dx), (R)(dt / dy), (R)(dt / dz));
@@ -256,10 +261,10 @@ cudaError_t launch_field_update3(const MeshParams3<R> &m, R *bnd, const double *
 
 template cudaError_t launch_field_update3<float>(const MeshParams3<float> &, float *, const double *,
                                                  const LaserParams &, double, double, double, double, long long,
-                                                 cudaStream_t);
+                                                 cudaStream_t, const double *);
 template cudaError_t launch_field_update3<double>(const MeshParams3<double> &, double *, const double *,
                                                   const LaserParams &, double, double, double, double, long long,
-                                                  cudaStream_t);
+                                                  cudaStream_t, const double *);
 
 // transverse laser profile exp(-((y - yc)^2 + (z - zc)^2) / w0^2): [nz][ny] at
 // (y_j, z_{k+1/2}) (the Ez source), then [nz][ny] at (y_{j+1/2}, z_k) (Ey)

@@ -89,6 +89,12 @@ struct Ctx {
     // that drops particles and reports PIC_ERR_OVERFLOW.
     volatile int *ovf_alert = nullptr;
     int *ovf_alert_dev = nullptr;
+    // binned steps in flight are bounded: before a binned step the host waits
+    // for the one kAhead steps back, so the alert it reads is at most kAhead
+    // steps old however far ahead the caller queues
+    static constexpr int kAhead = 4;
+    cudaEvent_t ahead_ev[kAhead] = {};
+    long long ahead_k = 0;
     int32_t *bin_cnt[PIC_MAX_SPECIES][2] = {};
     int64_t n_live[PIC_MAX_SPECIES] = {};
     // CTAs of the overflow-range kernel: one per 256 slots of the largest
@@ -97,8 +103,35 @@ struct Ctx {
     int bin_ctas = kBinCtasMin;
     int since_sort = 0;
     long long launches = 0;  // kernels launched by this context
+    // pic_step replays sort-free stretches of steps from CUDA graphs (compact
+    // layout): one graph per (length, diagnostic phase, buffer parity,
+    // parameter generation), captured on the context's own stream at first use
+    struct StepGraph {
+        int len;               // steps in the stretch
+        int phase;             // step index mod diag_every at its start (-1: diagnostics off)
+        unsigned parity;       // bit s: the buffer species s is in
+        long long gen;         // graph_gen at capture
+        cudaGraphExec_t exec;
+        long long launches;    // kernels one replay runs
+        int last_diag;         // offset of the stretch's last diagnostic step (-1: none)
+    };
+    static constexpr int kMaxGraphs = 16;
+    std::vector<StepGraph> graphs;
+    int graph_max = 32;          // longest stretch replayed as one graph (0: launch every kernel)
+    long long graph_gen = 0;     // bumped whenever a captured kernel parameter would change
+    long long graph_captures = 0, graph_replays = 0;
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t gev[2] = {};
+    double *laser_tab = nullptr;  // device [2 * graph_max]: (fz, fy) of each step of a replayed stretch
+    const double *lf_capture = nullptr;  // while capturing: this step's slot of laser_tab
     std::string last_error;
 };
+
+void drop_step_graphs(Ctx *c) {
+    for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
+    c->graphs.clear();
+    c->graph_gen += 1;
+}
 
 std::string g_create_error;
 
@@ -511,6 +544,7 @@ pic_status_t upload_particles(Ctx *c, int s, const PT *p, int64_t base, cudaStre
 pic_status_t retile(Ctx *c, int tx, int ty, cudaStream_t st) {
     if (c->dim != 2 || !fused_tile_supported(tx, ty)) return fail(c, PIC_ERR_ARG, "unsupported tile shape");
     CK(cudaStreamSynchronize(st));
+    drop_step_graphs(c);  // the tile arrays move
     for (int s = 0; s < PIC_MAX_SPECIES; ++s) {
         cudaFree(c->tile_start[s]);
         c->tile_start[s] = nullptr;
@@ -753,6 +787,13 @@ void pic_destroy(void *ctx) {
     cudaFree(c->laser_prof);
     cudaFree(c->hist);
     if (c->ovf_alert) cudaFreeHost(const_cast<int *>(c->ovf_alert));
+    drop_step_graphs(c);
+    if (c->gstream) cudaStreamDestroy(c->gstream);
+    for (int k = 0; k < 2; ++k)
+        if (c->gev[k]) cudaEventDestroy(c->gev[k]);
+    cudaFree(c->laser_tab);
+    for (int k = 0; k < Ctx::kAhead; ++k)
+        if (c->ahead_ev[k]) cudaEventDestroy(c->ahead_ev[k]);
     delete c;
 }
 
@@ -1029,9 +1070,9 @@ pic_status_t pic_field_update(void *ctx, void *stream) {
         using T = decltype(z);
         if (c->dim == 3)
             return launch_field_update3<T>(mesh3<T>(c), static_cast<T *>(c->bnd), c->laser_prof, laser(c), c->dt,
-                                           c->dx, c->dy, c->dz, c->step, S(stream));
+                                           c->dx, c->dy, c->dz, c->step, S(stream), c->lf_capture);
         return launch_field_update<T>(mesh<T>(c), static_cast<T *>(c->bnd), c->laser_prof, laser(c), c->dt, c->dx,
-                                      c->dy, c->step, S(stream));
+                                      c->dy, c->step, S(stream), c->lf_capture);
     }));
     c->launches += c->cfg.bc_x == PIC_BC_OPEN ? 4 : 3;
     c->step += 1;
@@ -1058,6 +1099,13 @@ pic_status_t pic_push_deposit(void *ctx, void *stream) {
     // particles, a compacting read-back or a window shift, re-bin first); an
     // overflow range past half full also asks for a re-bin
     bool rebin = false;
+    cudaEvent_t ahead = nullptr;
+    if (c->binned) {
+        cudaEvent_t &ev = c->ahead_ev[c->ahead_k % Ctx::kAhead];
+        if (!ev) CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        else if (c->ahead_k >= Ctx::kAhead) CK(cudaEventSynchronize(ev));
+        ahead = ev;
+    }
     if (c->binned && c->ovf_alert && *c->ovf_alert) {
         *c->ovf_alert = 0;
         rebin = true;
@@ -1127,6 +1175,10 @@ pic_status_t pic_push_deposit(void *ctx, void *stream) {
         CK(launch_seal_bins(a, S(stream)));
         c->launches += 1;
     }
+    if (ahead) {
+        CK(cudaEventRecord(ahead, S(stream)));
+        c->ahead_k += 1;
+    }
     if (diag) {
         const int ncols = c->ntiles + (bin ? c->bin_ctas : 0);
         CK(launch_diag_final(c->diag_rows, ncols, c->cfg.nspecies, c->diag_shift, c->diag_out, c->result,
@@ -1148,6 +1200,7 @@ pic_status_t pic_set_diagnostics(void *ctx, int every, const double *emin_mev, c
         c->diag_hi[s] = hi;
     }
     c->diag_every = every;
+    drop_step_graphs(c);  // the windows are kernel parameters of the captured steps
     return PIC_OK;
 }
 
@@ -1182,19 +1235,135 @@ pic_status_t pic_sort(void *ctx, void *stream) {
     return PIC_OK;
 }
 
+}  // extern "C"
+
+// len whole steps (no sort among them) replayed from a CUDA graph on the
+// context's stream, ordered after and before the caller's stream by events.
+// The graph is captured at the first stretch with its key; the capture is
+// itself the first execution (its host-side bookkeeping stands), later
+// replays apply the recorded bookkeeping.  The laser time factors of the
+// stretch are computed on the host as for launched steps and copied into the
+// device table the captured boundary kernels read, so a replayed step runs
+// the same kernels with the same arguments as a launched one.
+static pic_status_t graph_steps(Ctx *c, int len, void *stream) {
+    cudaStream_t user = S(stream);
+    if (!c->gstream) {
+        CK(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+        for (int k = 0; k < 2; ++k) CK(cudaEventCreateWithFlags(&c->gev[k], cudaEventDisableTiming));
+        CK(cudaMalloc(&c->laser_tab, 2 * sizeof(double) * (size_t)std::max(c->graph_max, 1)));
+    }
+    unsigned parity = 0;
+    for (int s = 0; s < c->cfg.nspecies; ++s) parity |= (unsigned)c->cur[s] << s;
+    const int phase = c->diag_every > 0 ? (int)(c->step % c->diag_every) : -1;
+    Ctx::StepGraph *g = nullptr;
+    for (auto &e : c->graphs)
+        if (e.len == len && e.phase == phase && e.parity == parity && e.gen == c->graph_gen) g = &e;
+    std::vector<double> tab(2 * (size_t)len, 0.0);
+    if (c->cfg.bc_x == PIC_BC_OPEN)
+        for (int q = 0; q < len; ++q)
+            laser_time_factors(laser(c), ((double)(c->step + q) + 0.5) * c->dt, &tab[2 * q], &tab[2 * q + 1]);
+    CK(cudaEventRecord(c->gev[0], user));
+    CK(cudaStreamWaitEvent(c->gstream, c->gev[0], 0));
+    // pageable source: staged before the call returns, ordered before the replay
+    CK(cudaMemcpyAsync(c->laser_tab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, c->gstream));
+    if (g) {
+        CK(cudaGraphLaunch(g->exec, c->gstream));
+        const long long step0 = c->step;
+        c->step += len;
+        c->launches += g->launches;
+        if (g->last_diag >= 0) c->diag_step = step0 + g->last_diag + 1;
+        c->graph_replays += 1;
+    } else {
+        const long long step0 = c->step, launches0 = c->launches, diag0 = c->diag_step;
+        CK(cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeRelaxed));
+        pic_status_t r = PIC_OK;
+        for (int q = 0; q < len && r == PIC_OK; ++q) {
+            c->lf_capture = c->laser_tab + 2 * q;
+            r = pic_push_deposit(c, c->gstream);
+            if (r == PIC_OK) r = pic_field_update(c, c->gstream);
+        }
+        c->lf_capture = nullptr;
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(c->gstream, &graph);
+        cudaGraphExec_t exec = nullptr;
+        cudaError_t ei = cudaSuccess;
+        if (r == PIC_OK && ec == cudaSuccess) ei = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (r != PIC_OK || ec != cudaSuccess || ei != cudaSuccess) {
+            // nothing ran: the host-side bookkeeping of the capture is undone
+            c->step = step0;
+            c->launches = launches0;
+            c->diag_step = diag0;
+            if (exec) cudaGraphExecDestroy(exec);
+            if (r != PIC_OK) return r;
+            return fail(c, PIC_ERR_CUDA, std::string("pic_step graph capture: ") +
+                                             cudaGetErrorString(ec != cudaSuccess ? ec : ei));
+        }
+        if ((int)c->graphs.size() >= Ctx::kMaxGraphs) {
+            cudaGraphExecDestroy(c->graphs.front().exec);
+            c->graphs.erase(c->graphs.begin());
+        }
+        Ctx::StepGraph e{len, phase, parity, c->graph_gen, exec, c->launches - launches0,
+                         c->diag_step > step0 ? (int)(c->diag_step - 1 - step0) : -1};
+        c->graphs.push_back(e);
+        c->graph_captures += 1;
+        CK(cudaGraphLaunch(exec, c->gstream));
+    }
+    CK(cudaEventRecord(c->gev[1], c->gstream));
+    CK(cudaStreamWaitEvent(user, c->gev[1], 0));
+    return PIC_OK;
+}
+
+extern "C" {
+
 pic_status_t pic_step(void *ctx, int nsteps, void *stream) {
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
     if (nsteps < 0) return fail(c, PIC_ERR_ARG, "negative step count");
     if (c->pending_deposit) return fail(c, PIC_ERR_STATE, "a move is waiting for pic_deposit");
-    for (int k = 0; k < nsteps; ++k) {
+    // the binned layout decides on the host, between steps, whether to re-bin:
+    // its steps are launched one by one
+    const bool graphs = c->graph_max > 0 && !c->binned;
+    int k = 0;
+    while (k < nsteps) {
         pic_status_t r = PIC_OK;
         if (c->since_sort >= c->cfg.sort_every) r = pic_sort(c, stream);
-        if (r == PIC_OK) r = pic_push_deposit(c, stream);
-        if (r == PIC_OK) r = pic_field_update(c, stream);
         if (r != PIC_OK) return r;
-        c->since_sort += 1;
+        int len = std::min(nsteps - k, c->cfg.sort_every - c->since_sort);
+        if (graphs && len >= 2) {
+            len = std::min(len, c->graph_max);
+            r = graph_steps(c, len, stream);
+        } else {
+            len = 1;
+            r = pic_push_deposit(c, stream);
+            if (r == PIC_OK) r = pic_field_update(c, stream);
+        }
+        if (r != PIC_OK) return r;
+        c->since_sort += len;
+        k += len;
     }
+    return PIC_OK;
+}
+
+pic_status_t pic_set_graphs(void *ctx, int max_steps) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
+    if (max_steps < 0 || max_steps > 4096) return fail(c, PIC_ERR_ARG, "max_steps must be in [0, 4096]");
+    drop_step_graphs(c);
+    if (c->laser_tab && max_steps > c->graph_max) {
+        cudaFree(c->laser_tab);
+        c->laser_tab = nullptr;
+        CK(cudaMalloc(&c->laser_tab, 2 * sizeof(double) * (size_t)max_steps));
+    }
+    c->graph_max = max_steps;
+    return PIC_OK;
+}
+
+pic_status_t pic_graph_stats(void *ctx, int64_t *captures, int64_t *replays) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
+    if (captures) *captures = c->graph_captures;
+    if (replays) *replays = c->graph_replays;
     return PIC_OK;
 }
 

@@ -61,7 +61,8 @@ cudaError_t launch_deposit_split(const StepParams<R> &P, int s, int n_upper, cud
 // k_fields.cu
 template <typename R>
 cudaError_t launch_field_update(const MeshParams<R> &m, R *bnd, const double *prof, const LaserParams &L,
-                                double dt, double dx, double dy, long long step, cudaStream_t st);
+                                double dt, double dx, double dy, long long step, cudaStream_t st,
+                                const double *lf_dev = nullptr);
 void laser_profile(const LaserParams &L, int ny, double *host);
 void laser_time_factors(const LaserParams &L, double t, double *fz, double *fy);
 
@@ -75,7 +76,8 @@ template <typename R>
 cudaError_t launch_deposit_split3(const StepParams3<R> &P, int s, int n_upper, cudaStream_t st);
 template <typename R>
 cudaError_t launch_field_update3(const MeshParams3<R> &m, R *bnd, const double *prof, const LaserParams &L,
-                                 double dt, double dx, double dy, double dz, long long step, cudaStream_t st);
+                                 double dt, double dx, double dy, double dz, long long step, cudaStream_t st,
+                                 const double *lf_dev = nullptr);
 void laser_profile3(const LaserParams &L, int ny, int nz, double dz, double *host);
 
 // k_sort.cu

@@ -1,5 +1,7 @@
 """Shared helpers of the GPU parity tests: build a library context and an
 oracle simulation from the same seeded state, and compare them."""
+import math
+
 import numpy as np
 
 import oracle
@@ -75,13 +77,45 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a))
 
 
-def compare_fields(sim, orc, keys, tol, region=None, f64=False):
+def rel_max(a, b, scale=None):
+    """Largest element-wise difference relative to the largest reference
+    magnitude (or `scale`): a wrong value in a single cell (a tile seam, a
+    ghost column, a node wrapped at a periodic edge) shows here even where the
+    L2 norm hides it."""
+    mb = (float(np.abs(b).max()) if b.size else 0.0) if scale is None else scale
+    d = float(np.abs(a - b).max()) if b.size else 0.0
+    return d / mb if mb > 0 else d
+
+
+# library read-back names of the left boundary values and the oracle's
+ORACLE_KEY = {"by_left": "byL", "bz_left": "bzL"}
+# E, B and J are vectors: a component's error is measured against the
+# magnitude of its vector.  With float32 cell offsets every displacement is
+# quantised at about 6e-8 cells, so a component that stays small next to the
+# others (Jz and Ex under a y-polarised laser in a cold plasma) carries a
+# large error relative to its own size but not relative to the vector's.
+VECTOR = {k: ("ex", "ey", "ez") for k in ("ex", "ey", "ez")}
+VECTOR.update({k: ("bx", "by", "bz") for k in ("bx", "by", "bz", "by_left", "bz_left")})
+VECTOR.update({k: ("jx", "jy", "jz") for k in ("jx", "jy", "jz")})
+
+
+def compare_fields(sim, orc, keys, tol, region=None, f64=False, max_tol=None):
+    """Mesh comparison, element by element and in norm, each component
+    against its vector's magnitude: max |a - b| <= max_tol * max |V| (max_tol
+    defaults to tol) and ||a - b||_2 <= tol * ||V||_2 / sqrt(3), with V the
+    oracle's E, B or J."""
     f = sim.get_fields_f64() if f64 else sim.get_fields()
+    max_tol = tol if max_tol is None else max_tol
     errs = {}
     for k in keys:
-        a, b = f[k].astype(np.float64), orc.f[k]
-        if region is not None:
+        a, b = f[k].astype(np.float64), orc.f[ORACLE_KEY.get(k, k)]
+        comps = [orc.f[c] for c in VECTOR[k]]
+        if region is not None and k not in ORACLE_KEY:
             a, b = a[region], b[region]
-        errs[k] = rel_l2(a, b)
-        assert errs[k] <= tol, (k, errs)
+            comps = [c[region] for c in comps]
+        vmax = max(float(np.abs(c).max()) for c in comps)
+        vnorm = math.sqrt(sum(float(np.sum(c * c)) for c in comps) / 3.0)
+        d2 = float(np.linalg.norm(a - b))
+        errs[k] = (d2 / vnorm if vnorm > 0 else d2, rel_max(a, b, vmax))
+        assert errs[k][0] <= tol and errs[k][1] <= max_tol, (k, errs)
     return errs

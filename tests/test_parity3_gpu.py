@@ -39,7 +39,7 @@ def test_split_path_one_step_3d(case):
     compare_fields(sim, orc, ("jx", "jy", "jz"), TOL)
     sim.field_update()
     orc.field_update()
-    compare_fields(sim, orc, ("ex", "ey", "ez", "bx", "by", "bz"), TOL)
+    compare_fields(sim, orc, ("ex", "ey", "ez", "bx", "by", "bz", "by_left", "bz_left"), TOL)
     f = sim.get_fields()
     np.testing.assert_allclose(f["by_left"], orc.f["byL"], atol=1e-5 * max(1.0, np.abs(orc.f["byL"]).max()))
     np.testing.assert_allclose(f["bz_left"], orc.f["bzL"], atol=1e-5 * max(1.0, np.abs(orc.f["bzL"]).max()))
@@ -61,7 +61,7 @@ def test_fused_step_one_step_3d(case, tile):
     compare_fields(sim, orc, ("jx", "jy", "jz"), TOL)
     sim.field_update()
     orc.field_update()
-    compare_fields(sim, orc, ("ex", "ey", "ez", "bx", "by", "bz"), TOL)
+    compare_fields(sim, orc, ("ex", "ey", "ez", "bx", "by", "bz", "by_left", "bz_left"), TOL)
 
 
 def test_fused_many_steps_3d_with_laser_sorting_and_removal():

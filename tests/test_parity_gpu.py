@@ -48,7 +48,7 @@ def test_split_path_one_step(case):
     compare_fields(sim, orc, ("jx", "jy", "jz"), TOL)
     sim.field_update()
     orc.field_update()
-    compare_fields(sim, orc, ("ex", "ey", "ez", "bx", "by", "bz"), TOL)
+    compare_fields(sim, orc, ("ex", "ey", "ez", "bx", "by", "bz", "by_left", "bz_left"), TOL)
     assert sim.get_step() == 6
 
 
@@ -61,7 +61,7 @@ def test_fused_step_one_step(case):
     orc.step(1)
     for s in range(len(wl.species)):
         compare_particles(sim, orc, s, TOL, TOL, TOL)
-    compare_fields(sim, orc, ("ex", "ey", "ez", "bx", "by", "bz"), TOL)
+    compare_fields(sim, orc, ("ex", "ey", "ez", "bx", "by", "bz", "by_left", "bz_left"), TOL)
 
 
 def test_fused_step_many_steps_with_sorting_and_removal():
@@ -231,7 +231,7 @@ def test_config1_first_steps_per_particle():
         sim.step(1)
         orc.step(1)
     compare_particles(sim, orc, 0, TOL, TOL, TOL)
-    compare_fields(sim, orc, ("ex", "ey", "ez", "bx", "by", "bz"), TOL)
+    compare_fields(sim, orc, ("ex", "ey", "ez", "bx", "by", "bz", "by_left", "bz_left"), TOL)
 
 
 # ---------------------------------------------------------------------------
@@ -252,7 +252,7 @@ def test_fp64_split_and_fused_steps(case):
     compare_fields(sim, orc, ("jx", "jy", "jz"), TOL64, f64=True)
     sim.field_update()
     orc.field_update()
-    compare_fields(sim, orc, ("ex", "ey", "ez", "bx", "by", "bz"), TOL64, f64=True)
+    compare_fields(sim, orc, ("ex", "ey", "ez", "bx", "by", "bz", "by_left", "bz_left"), TOL64, f64=True)
     for _ in range(3):       # then the fused path
         sim.step(1)
         orc.step(1)
