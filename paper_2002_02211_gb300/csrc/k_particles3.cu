@@ -4,6 +4,7 @@
 #include <cuda.h>
 
 #include "pic_device3.cuh"
+#include "pic_step3.cuh"
 #include "pic_kernels.h"
 #include "pic_ptx.cuh"
 
@@ -11,44 +12,20 @@ using namespace pic_ptx;
 
 namespace {
 
-// a4 boundary rule: removal at the open x ends, periodic wraps
-template <typename R>
-__device__ __forceinline__ bool finish_move3(const MeshParams3<R> &m, int &ix1, int &iy1, int &iz1) {
-    bool alive = true;
-    if (m.bc_x == 0) {
-        alive = ix1 >= 2 && ix1 <= m.nx - 3;
-    } else {
-        if (ix1 < 0) ix1 += m.nx;
-        else if (ix1 >= m.nx) ix1 -= m.nx;
-    }
-    if (iy1 < 0) iy1 += m.ny;
-    else if (iy1 >= m.ny) iy1 -= m.ny;
-    if (iz1 < 0) iz1 += m.nz;
-    else if (iz1 >= m.nz) iz1 -= m.nz;
-    return alive;
-}
-
 constexpr int kThreads3 = 256;
 #ifndef PIC3_MINB
 #define PIC3_MINB 4  // most resident CTAs per SM the register budget of the FP32 kernel is sized for
 #endif
-#ifndef PIC3_ACC
-#define PIC3_ACC 0   // 1: sum the in-cell currents of a cell's consecutive particles in registers
-#endif
 constexpr int kRec3 = 10;  // staged reals per particle: ox oy oz ux uy uz sx sy sz w (plus the cell word)
 
 template <int TX, int TY, int TZ, typename R>
-struct TileConst3 {
-    static constexpr int WX = window3_wx<R>(TX), WY = window3_w(TY), WZ = window3_w(TZ);
-    static constexpr int WA = WX * WY * WZ;     // current window [3][WZ][WY][WX]
-    static constexpr int FX = window3_fx<R>(TX);
-    static constexpr int FA = FX * WY * WZ;     // field window [6][WZ][WY][FX]
-    static constexpr int HX = window3_hx(), HY = window3_h(), HZ = window3_h();
+struct TileConst3 : WinConst3<TX, TY, TZ, R> {
+    using W = WinConst3<TX, TY, TZ, R>;
     // field window, current window, one record stage per thread (cell word,
     // kRec3 reals, and the id the binned layout moves with the particle, staged
     // and kept)
     static constexpr size_t smem_bytes =
-        (size_t)(6 * FA + 3 * WA) * sizeof(R) + kThreads3 * (3 * sizeof(uint32_t) + kRec3 * sizeof(R));
+        (size_t)(6 * W::FA + 3 * W::WA) * sizeof(R) + kThreads3 * (3 * sizeof(uint32_t) + kRec3 * sizeof(R));
     // resident CTAs per SM the register budget is sized for: as many as fit
     // in the SM's 228 KB of shared memory (1 KB reserved per CTA, plus the
     // static arrays), at most PIC3_MINB, at least two; the FP64 instantiation
@@ -58,69 +35,6 @@ struct TileConst3 {
     static constexpr int minb =
         sizeof(R) == 8 ? 1 : (smem_ctas >= PIC3_MINB ? PIC3_MINB : (smem_ctas >= 3 ? 3 : 2));
 };
-
-template <typename R, int WX, int WY, int WA, int FX, int FA>
-struct SmemMesh3T {
-    const R *F;
-    R *Jw;
-    __device__ __forceinline__ R f(int c, int x, int y, int z) const { return F[c * FA + (z * WY + y) * FX + x]; }
-    __device__ __forceinline__ void j(int c, int x, int y, int z, R v) const {
-        atomicAdd(&Jw[c * WA + (z * WY + y) * WX + x], v);
-    }
-};
-
-template <int TX, int TY, int TZ>
-__device__ __forceinline__ int tile_of3(const TileGeom3 &t, int ix, int iy, int iz) {
-    return ((iz / TZ) * t.nty + iy / TY) * t.ntx + ix / TX;
-}
-
-// destination range of a particle that survived the move (-1 and PIC_EF_RANGE
-// for a cell outside the mesh, which only a corrupt input cell can produce)
-template <int TX, int TY, int TZ, typename R>
-__device__ __forceinline__ int bin_dest3(const MeshParams3<R> &m, const TileGeom3 &t, int ix, int iy, int iz,
-                                         unsigned *err) {
-    if (ix < 0 || ix >= m.nx || iy < 0 || iy >= m.ny || iz < 0 || iz >= m.nz) {
-        atomicOr(err, PIC_EF_RANGE);
-        return -1;
-    }
-    return tile_of3<TX, TY, TZ>(t, ix, iy, iz);
-}
-
-// Eq. (4) sums of the particles in the window [dlo, dhi) MeV
-template <typename R>
-__device__ __forceinline__ void diag_add3(R dacc[7], R dm, R dlo, R dhi, R dshift, R w, const R u[3],
-                                          const R spn[3]) {
-    const R e = ekin_mev(dm, u[0], u[1], u[2]);
-    if (e >= dlo && e < dhi) {
-        const R ep = e - dshift;
-        dacc[0] += w;
-        dacc[1] += w * spn[0];
-        dacc[2] += w * spn[1];
-        dacc[3] += w * spn[2];
-        dacc[4] += w * ep;
-        dacc[5] += w * ep * ep;
-        dacc[6] += R(1);
-    }
-}
-
-// Fused kernel, steps with the Eq. (4) sums: one record per lane, summed
-// over the warp at once (float shuffles) and added to the warp's FP64 row of
-// sdiag, so no accumulator stays live across the particle loop.  All 32 lanes
-// of the warp call it together.
-template <typename R>
-__device__ __forceinline__ void diag_warp3(const DiagParams &D, int sp, bool has, R w, const R u[3], const R spn[3],
-                                           double *row) {
-    R c[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
-    if (has) diag_add3(c, (R)D.m_mev[sp], (R)D.lo[sp], (R)D.hi[sp], (R)D.shift[sp], w, u, spn);
-    if (!__any_sync(0xFFFFFFFFu, c[6] != R(0))) return;
-#pragma unroll
-    for (int q = 0; q < 7; ++q) {
-        R v = c[q];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-        if ((threadIdx.x & 31) == 0) row[q] += (double)v;
-    }
-}
 
 // column `col` of the CTA's FP64 sums of species sp, kept per warp in sdiag
 // (ncols columns per row); the whole CTA calls it
@@ -227,7 +141,7 @@ __global__ void __launch_bounds__(kThreads3) k_overflow3(const StepParams3<R> P)
             }
             bin_store3(P.bin[sp], S.tile_start, nt, -1, nullptr, dest, cw, v, id, P.err);
         }
-        if (diag) store_diag_rows3(P.diag, sp, dacc, sdiag, nt + blockIdx.x, nt + P.nextra);
+        if (diag) store_diag_rows3(P.diag, sp, dacc, sdiag, P.diag_cols0 + blockIdx.x, P.diag_cols0 + P.nextra);
     }
     if (bad) atomicOr(P.err, PIC_EF_NAN);
 }
@@ -236,22 +150,46 @@ __global__ void __launch_bounds__(kThreads3) k_overflow3(const StepParams3<R> P)
 // Fused 3D step kernel.  Thread 0 stages the 6-component field window (x
 // margin 4 cells before the tile, row rounded up to 16 bytes; along y and z
 // the tile plus 1 + PIC3_MARGIN cells before and 2 + PIC3_MARGIN after) with
-// one 4D TMA load, zero-filled outside the mesh.  Each thread owns one record
-// slot in shared memory: it copies the record it is about to process into
-// registers and at once requests its next record into the same slot
-// (cp.async), so one record is always in flight while it computes.  A record
-// runs a1-a5 against shared memory when its stencil [cell-1, cell+2]^3 lies in
-// the window and in the mesh (no wrap), else against global memory through a
-// NodeBlock3 (wrapped offsets formed once, loads without branches).  The
-// current window is added to J at the end (16-byte vector atomics in float).
+// one 4D TMA load, zero-filled outside the mesh, and alone waits for it (the
+// others wait at the block barrier).  Each thread owns one record slot in
+// shared memory: it copies the record it is about to process into registers
+// and at once requests its next record into the same slot (cp.async), so one
+// record is always in flight while it computes.  The current window is added
+// to J at the end (16-byte vector atomics in float), rows outside the mesh
+// wrapped onto the periodic rows.
 //
-// BIN = false: the records are rewritten in place (compact layout, periodic
-// tile sorts).  BIN = true (binned layout): tile T reads the first cnt_in[T]
-// slots of its range and every surviving particle is stored into the range of
-// the tile its new cell lies in, in the other buffer (bin_store3);
-// k_overflow3 runs the overflow range.  DIAG: the step accumulates the Eq. (4)
-// sums (the instantiation without them keeps their registers free).
+// BIN = false (compact layout, periodic tile sorts, records rewritten in
+// place): a particle may have drifted out of its tile since the last sort; it
+// runs a1-a5 against shared memory when its stencil [cell-1, cell+2]^3 lies
+// in the window and in the mesh (no wrap), else against global memory through
+// a NodeBlock3 (wrapped offsets formed once, loads without branches).
+//
+// BIN = true (binned layout): tile T reads its two segments and every
+// surviving particle is stored into the range of the tile its new cell lies
+// in, in the other buffer (bin_store3); k_overflow3 runs the overflow range.
+// The binned layout keeps every particle in its tile, so every stencil lies in
+// the window: the window of a tile at a periodic edge (y, z, and x when
+// periodic) is completed from the wrapped rows after the TMA load (which
+// fills rows outside the mesh with zeros), and there is no global-memory
+// path.  A warp whose lanes all stay in their cells deposits with the in-cell
+// closed form; once any lane crosses a cell face the whole warp takes the
+// general Esirkepov form, which gives the in-cell lanes the same values, so
+// the two forms never run one after the other in a warp.
+//
+// DIAG: the step accumulates the Eq. (4) sums (the instantiation without them
+// keeps their registers free).
 // ---------------------------------------------------------------------------
+// g mod n in [0, n): one compare each way for a window row next to the mesh,
+// the remainder only when a window spans more than a short mesh axis
+static __device__ __forceinline__ int wrap3(int g, int n) {
+    g = g < 0 ? g + n : (g >= n ? g - n : g);
+    if (g < 0 || g >= n) {
+        g %= n;
+        if (g < 0) g += n;
+    }
+    return g;
+}
+
 template <int TX, int TY, int TZ, typename R, bool BIN, bool DIAG>
 __global__ void __launch_bounds__(kThreads3, (TileConst3<TX, TY, TZ, R>::minb))
     k_step_fused3(const StepParams3<R> P, const __grid_constant__ CUtensorMap tmapEB) {
@@ -261,12 +199,12 @@ __global__ void __launch_bounds__(kThreads3, (TileConst3<TX, TY, TZ, R>::minb))
     __shared__ __align__(8) uint64_t bar;
     __shared__ double sdiag[kThreads3 / 32][8];
     __shared__ int s_front[PIC_MAXSP];  // binned layout: stayers stored per species
+    __shared__ int s_timeout;
     R *sF = reinterpret_cast<R *>(dsm);
     R *sJ = sF + 6 * FA;
     R *ring = sJ + 3 * WA;                                                // [kRec3][kThreads3]
     uint32_t *cring = reinterpret_cast<uint32_t *>(ring + kRec3 * kThreads3);  // [kThreads3]
     int32_t *iring = reinterpret_cast<int32_t *>(cring + kThreads3);          // [kThreads3]
-    int32_t *idkeep = iring + kThreads3;  // [kThreads3] id of the record in hand (binned layout)
     const MeshParams3<R> &m = P.m;
 
     const int tile = blockIdx.x;
@@ -320,44 +258,46 @@ __global__ void __launch_bounds__(kThreads3, (TileConst3<TX, TY, TZ, R>::minb))
         const BinRange rg = range(first);
         prefetch(P.sp[first], tid < rg.len ? bin_slot(rg, tid) : 0, tid < rg.len);
     }
-    for (int i = tid; i < 3 * WA; i += kThreads3) sJ[i] = R(0);
+    if constexpr (sizeof(R) == 4) {
+        float4 *j4 = reinterpret_cast<float4 *>(sJ);  // 3 WA is a multiple of 4, sJ 16-byte aligned
+        for (int i = tid; i < 3 * WA / 4; i += kThreads3) j4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+        for (int i = tid; i < 3 * WA; i += kThreads3) sJ[i] = R(0);
+    }
     if (tid < PIC_MAXSP) s_front[tid] = 0;
+    if (tid == 0) s_timeout = mbar_wait_bounded(&bar, 0) ? 0 : 1;  // one thread waits for the window
     __syncthreads();
-    if (!mbar_wait_bounded(&bar, 0)) {
+    if (s_timeout) {
         if (tid == 0) atomicOr(P.err, PIC_EF_TIMEOUT);
         cp_async_wait0();
         return;
+    }
+    if constexpr (BIN) {
+        // window rows outside the mesh: the wrapped rows' values
+        const bool wrap_x = m.bc_x == 1 && (wx0 < 0 || wx0 + FX > m.nx);
+        if (wy0 < 0 || wy0 + WY > m.ny || wz0 < 0 || wz0 + WZ > m.nz || wrap_x) {
+            for (int e = tid; e < 6 * WZ * WY * FX; e += kThreads3) {
+                const int row = e / FX, x = e - row * FX;
+                const int c = row / (WZ * WY), zy = row - c * (WZ * WY);
+                const int z = zy / WY, y = zy - z * WY;
+                const int gz = wz0 + z, gy = wy0 + y;
+                const bool row_out = gz < 0 || gz >= m.nz || gy < 0 || gy >= m.ny;
+                int gx = wx0 + x;
+                if (m.bc_x == 1) gx = wrap3(gx, m.nx);
+                if (!row_out && gx == wx0 + x) continue;  // in the mesh: the TMA loaded it
+                const size_t g = c * m.plane + ((size_t)wrap3(gz, m.nz) * m.ny + wrap3(gy, m.ny)) * m.ld;
+                sF[c * FA + zy * FX + x] = gx >= 0 && gx < m.ld ? m.EB[g + gx] : R(0);
+            }
+            __syncthreads();
+        }
     }
 
     const SmemMesh3T<R, WX, WY, WA, FX, FA> sm{sF, sJ};
     const int xlo = max(wx0 + 1, 1), xhi = min(wx0 + WX - 3, m.nx - 3);
     const int ylo = max(wy0 + 1, 1), yhi = min(wy0 + WY - 3, m.ny - 3);
     const int zlo = max(wz0 + 1, 1), zhi = min(wz0 + WZ - 3, m.nz - 3);
+    const int tx0 = wx0 + TC::HX, ty0 = wy0 + TC::HY, tz0 = wz0 + TC::HZ;
     bool bad = false;
-    // in-cell currents summed per cell: window offset of the cell, 12 values
-    // (Jx at the 4 (y, z) edges, Jy at the 4 (x, z) edges, Jz at the 4 (x, y) edges)
-    constexpr int SY = WX, SZ = WX * WY;
-    int acc_key = -1;
-    R acc[12];
-#pragma unroll
-    for (int q = 0; q < 12; ++q) acc[q] = R(0);
-    auto acc_flush = [&]() {
-        if (acc_key >= 0) {
-            const int k = acc_key;
-            atomicAdd(&sJ[k], acc[0]);
-            atomicAdd(&sJ[k + SY], acc[1]);
-            atomicAdd(&sJ[k + SZ], acc[2]);
-            atomicAdd(&sJ[k + SY + SZ], acc[3]);
-            atomicAdd(&sJ[WA + k], acc[4]);
-            atomicAdd(&sJ[WA + k + 1], acc[5]);
-            atomicAdd(&sJ[WA + k + SZ], acc[6]);
-            atomicAdd(&sJ[WA + k + 1 + SZ], acc[7]);
-            atomicAdd(&sJ[2 * WA + k], acc[8]);
-            atomicAdd(&sJ[2 * WA + k + 1], acc[9]);
-            atomicAdd(&sJ[2 * WA + k + SY], acc[10]);
-            atomicAdd(&sJ[2 * WA + k + 1 + SY], acc[11]);
-        }
-    };
 
     for (int sp = 0; sp < P.nsp; ++sp) {
         const DevSpecies3<R> &S = P.sp[sp];
@@ -372,97 +312,138 @@ __global__ void __launch_bounds__(kThreads3, (TileConst3<TX, TY, TZ, R>::minb))
         for (int k0 = 0; k0 < len; k0 += kThreads3) {
             const int k = k0 + tid;
             cp_async_wait0();
-            // Eq. (4) contribution of this lane's record, summed over the warp below
-            bool dhas = false;
-            R dw = R(0), du[3] = {R(0), R(0), R(0)}, ds[3] = {R(0), R(0), R(0)};
-            // binned layout: what this lane stores after the record (dest -1: nothing)
-            int dest = -1;
-            uint32_t bcell = PIC_DEAD;
-            R bv[10];
             if constexpr (BIN) {
+                // this lane's particle: a1-a4, then the deposit (form chosen per warp)
+                bool valid = false;
+                int ix = 0, iy = 0, iz = 0, ix1 = 0, iy1 = 0, iz1 = 0;
+                R ox = R(0), oy = R(0), oz = R(0), ox1 = R(0), oy1 = R(0), oz1 = R(0), w = R(0);
+                R u[3] = {R(0), R(0), R(0)}, spn[3] = {R(0), R(0), R(0)};
+                int32_t id = 0;
+                if (k < len) {
+                    const R *r = ring0;
+                    const uint32_t c = cring[tid];
+                    ox = r[0 * kThreads3], oy = r[1 * kThreads3], oz = r[2 * kThreads3];
+                    u[0] = r[3 * kThreads3], u[1] = r[4 * kThreads3], u[2] = r[5 * kThreads3];
+                    spn[0] = r[6 * kThreads3], spn[1] = r[7 * kThreads3], spn[2] = r[8 * kThreads3];
+                    w = r[9 * kThreads3];
+                    id = iring[tid];
+                    // the slot is free again: request the next record
+                    prefetch(S, k + kThreads3 < len ? bin_slot(rg, k + kThreads3) : 0, k + kThreads3 < len);
+                    if (c != PIC_DEAD) {
+                        unpack_cell3(c, ix, iy, iz);
+                        if (ix < tx0 || ix >= tx0 + TX || iy < ty0 || iy >= ty0 + TY || iz < tz0 ||
+                            iz >= tz0 + TZ) {
+                            atomicOr(P.err, PIC_EF_RANGE);  // not in its tile: only a corrupt layout
+                        } else {
+                            valid = true;
+                            R E[3], B[3];
+                            gather_eb3(sm, ix - wx0, iy - wy0, iz - wz0, ox, oy, oz, E, B);
+                            push_spin(qm, a, m.dt, E, B, u, spn);
+                            const R gi = Real<R>::rsqrt(R(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                            ix1 = ix, iy1 = iy, iz1 = iz;
+                            ox1 = ox, oy1 = oy, oz1 = oz;
+                            advance_axis(ix1, ox1, u[0] * gi * m.dt_dx);
+                            advance_axis(iy1, oy1, u[1] * gi * m.dt_dy);
+                            advance_axis(iz1, oz1, u[2] * gi * m.dt_dz);
+                        }
+                    }
+                }
+                const bool cross = valid && (ix1 != ix || iy1 != iy || iz1 != iz);
+                const bool general = __any_sync(0xFFFFFFFFu, cross);
+                int dest = -1;
+                uint32_t bcell = PIC_DEAD;
+                R bv[10];
 #pragma unroll
                 for (int q10 = 0; q10 < 10; ++q10) bv[q10] = R(0);
-            }
-            if (k < len) {
-                const int slot = rg.beg + k;  // compact layout (in-place rewrite)
-                const R *r = ring0;
-                const uint32_t c = cring[tid];
-                const R ox = r[0 * kThreads3], oy = r[1 * kThreads3], oz = r[2 * kThreads3];
-                R u[3] = {r[3 * kThreads3], r[4 * kThreads3], r[5 * kThreads3]};
-                R spn[3] = {r[6 * kThreads3], r[7 * kThreads3], r[8 * kThreads3]};
-                const R w = r[9 * kThreads3];
-                if constexpr (BIN) idkeep[tid] = iring[tid];  // the ring slot is reused below
-                // the slot is free again: request the next record
-                prefetch(S, k + kThreads3 < len ? bin_slot(rg, k + kThreads3) : 0, k + kThreads3 < len);
-                if (c != PIC_DEAD) {
-                    int ix, iy, iz;
-                    unpack_cell3(c, ix, iy, iz);
-                    const bool fast = ix >= xlo && ix <= xhi && iy >= ylo && iy <= yhi && iz >= zlo && iz <= zhi;
-                    R E[3], B[3];
-                    if (fast) {
-                        gather_eb3(sm, ix - wx0, iy - wy0, iz - wz0, ox, oy, oz, E, B);
-                    } else {
-                        const NodeBlock3<R> nb(m, ix, iy, iz, P.err);
-                        gather_eb3(nb, 1, 1, 1, ox, oy, oz, E, B);
-                    }
-                    push_spin(qm, a, m.dt, E, B, u, spn);
-                    const R gi = Real<R>::rsqrt(R(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-                    int ix1 = ix, iy1 = iy, iz1 = iz;
-                    R ox1 = ox, oy1 = oy, oz1 = oz;
-                    advance_axis(ix1, ox1, u[0] * gi * m.dt_dx);
-                    advance_axis(iy1, oy1, u[1] * gi * m.dt_dy);
-                    advance_axis(iz1, oz1, u[2] * gi * m.dt_dz);
+                bool dhas = false;
+                if (valid) {
                     const R qw = q * w;
-                    const bool in_cell = ix1 == ix && iy1 == iy && iz1 == iz;
-                    if (fast && in_cell && !PIC3_ACC) {
-                        R v[12];
-                        in_cell_weights3(ox, oy, oz, ox1, oy1, oz1, qw, m.dx_dt, m.dy_dt, m.dz_dt, v);
-                        deposit_in_cell3(sm, ix - wx0, iy - wy0, iz - wz0, v);
-                    } else if (fast && in_cell) {
-                        R v[12];
-                        in_cell_weights3(ox, oy, oz, ox1, oy1, oz1, qw, m.dx_dt, m.dy_dt, m.dz_dt, v);
-                        const int key = ((iz - wz0) * WY + (iy - wy0)) * WX + (ix - wx0);
-                        if (key != acc_key) {
-                            acc_flush();
-                            acc_key = key;
-#pragma unroll
-                            for (int q12 = 0; q12 < 12; ++q12) acc[q12] = v[q12];
-                        } else {
-#pragma unroll
-                            for (int q12 = 0; q12 < 12; ++q12) acc[q12] += v[q12];
-                        }
-                    } else if (fast) {
+                    if (general) {
                         deposit_esirkepov3(sm, ix - wx0, iy - wy0, iz - wz0, ox, oy, oz, ix1 - wx0, iy1 - wy0,
                                            iz1 - wz0, ox1, oy1, oz1, qw, m.dx_dt, m.dy_dt, m.dz_dt);
                     } else {
-                        const NodeBlock3<R> nb(m, ix, iy, iz, P.err);
-                        if (in_cell) {
-                            R v[12];
-                            in_cell_weights3(ox, oy, oz, ox1, oy1, oz1, qw, m.dx_dt, m.dy_dt, m.dz_dt, v);
-                            deposit_in_cell3(nb, 1, 1, 1, v);
-                        } else {
-                            deposit_esirkepov3(nb, 1, 1, 1, ox, oy, oz, ix1 - ix + 1, iy1 - iy + 1, iz1 - iz + 1,
-                                               ox1, oy1, oz1, qw, m.dx_dt, m.dy_dt, m.dz_dt);
-                        }
+                        R v[12];
+                        in_cell_weights3(ox, oy, oz, ox1, oy1, oz1, qw, m.dx_dt, m.dy_dt, m.dz_dt, v);
+                        deposit_in_cell3(sm, ix - wx0, iy - wy0, iz - wz0, v);
                     }
                     const bool alive = finish_move3(m, ix1, iy1, iz1);
-                    const R chk = u[0] * u[0] + u[1] * u[1] + u[2] * u[2] + spn[0] * spn[0] +
-                                  spn[1] * spn[1] + spn[2] * spn[2];
+                    const R chk = u[0] * u[0] + u[1] * u[1] + u[2] * u[2] + spn[0] * spn[0] + spn[1] * spn[1] +
+                                  spn[2] * spn[2];
                     bad |= !isfinite(chk);
-                    if (diag && alive) {
-                        dhas = true;
-                        dw = w;
-                        du[0] = u[0], du[1] = u[1], du[2] = u[2];
-                        ds[0] = spn[0], ds[1] = spn[1], ds[2] = spn[2];
+                    if (alive) {
+                        dhas = DIAG;
+                        dest = bin_dest3<TX, TY, TZ>(m, P.t, ix1, iy1, iz1, P.err);
+                        bcell = pack_cell3(ix1, iy1, iz1);
+                        bv[0] = ox1, bv[1] = oy1, bv[2] = oz1, bv[3] = u[0], bv[4] = u[1], bv[5] = u[2];
+                        bv[6] = spn[0], bv[7] = spn[1], bv[8] = spn[2], bv[9] = w;
                     }
-                    if constexpr (BIN) {
-                        if (alive) {
-                            dest = bin_dest3<TX, TY, TZ>(m, P.t, ix1, iy1, iz1, P.err);
-                            bcell = pack_cell3(ix1, iy1, iz1);
-                            bv[0] = ox1, bv[1] = oy1, bv[2] = oz1, bv[3] = u[0], bv[4] = u[1], bv[5] = u[2];
-                            bv[6] = spn[0], bv[7] = spn[1], bv[8] = spn[2], bv[9] = w;
+                }
+                if constexpr (DIAG) diag_warp3(P.diag, sp, dhas, w, u, spn, drow);
+                bin_store3(P.bin[sp], S.tile_start, (int)gridDim.x, tile, &s_front[sp], dest, bcell, bv, id, P.err,
+                           rg.beg);
+            } else {
+                // Eq. (4) contribution of this lane's record, summed over the warp below
+                bool dhas = false;
+                R dw = R(0), du[3] = {R(0), R(0), R(0)}, ds[3] = {R(0), R(0), R(0)};
+                if (k < len) {
+                    const int slot = rg.beg + k;  // compact layout (in-place rewrite)
+                    const R *r = ring0;
+                    const uint32_t c = cring[tid];
+                    const R ox = r[0 * kThreads3], oy = r[1 * kThreads3], oz = r[2 * kThreads3];
+                    R u[3] = {r[3 * kThreads3], r[4 * kThreads3], r[5 * kThreads3]};
+                    R spn[3] = {r[6 * kThreads3], r[7 * kThreads3], r[8 * kThreads3]};
+                    const R w = r[9 * kThreads3];
+                    // the slot is free again: request the next record
+                    prefetch(S, k + kThreads3 < len ? bin_slot(rg, k + kThreads3) : 0, k + kThreads3 < len);
+                    if (c != PIC_DEAD) {
+                        int ix, iy, iz;
+                        unpack_cell3(c, ix, iy, iz);
+                        const bool fast =
+                            ix >= xlo && ix <= xhi && iy >= ylo && iy <= yhi && iz >= zlo && iz <= zhi;
+                        R E[3], B[3];
+                        if (fast) {
+                            gather_eb3(sm, ix - wx0, iy - wy0, iz - wz0, ox, oy, oz, E, B);
+                        } else {
+                            const NodeBlock3<R> nb(m, ix, iy, iz, P.err);
+                            gather_eb3(nb, 1, 1, 1, ox, oy, oz, E, B);
                         }
-                    } else {
+                        push_spin(qm, a, m.dt, E, B, u, spn);
+                        const R gi = Real<R>::rsqrt(R(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                        int ix1 = ix, iy1 = iy, iz1 = iz;
+                        R ox1 = ox, oy1 = oy, oz1 = oz;
+                        advance_axis(ix1, ox1, u[0] * gi * m.dt_dx);
+                        advance_axis(iy1, oy1, u[1] * gi * m.dt_dy);
+                        advance_axis(iz1, oz1, u[2] * gi * m.dt_dz);
+                        const R qw = q * w;
+                        const bool in_cell = ix1 == ix && iy1 == iy && iz1 == iz;
+                        if (fast && in_cell) {
+                            R v[12];
+                            in_cell_weights3(ox, oy, oz, ox1, oy1, oz1, qw, m.dx_dt, m.dy_dt, m.dz_dt, v);
+                            deposit_in_cell3(sm, ix - wx0, iy - wy0, iz - wz0, v);
+                        } else if (fast) {
+                            deposit_esirkepov3(sm, ix - wx0, iy - wy0, iz - wz0, ox, oy, oz, ix1 - wx0, iy1 - wy0,
+                                               iz1 - wz0, ox1, oy1, oz1, qw, m.dx_dt, m.dy_dt, m.dz_dt);
+                        } else {
+                            const NodeBlock3<R> nb(m, ix, iy, iz, P.err);
+                            if (in_cell) {
+                                R v[12];
+                                in_cell_weights3(ox, oy, oz, ox1, oy1, oz1, qw, m.dx_dt, m.dy_dt, m.dz_dt, v);
+                                deposit_in_cell3(nb, 1, 1, 1, v);
+                            } else {
+                                deposit_esirkepov3(nb, 1, 1, 1, ox, oy, oz, ix1 - ix + 1, iy1 - iy + 1,
+                                                   iz1 - iz + 1, ox1, oy1, oz1, qw, m.dx_dt, m.dy_dt, m.dz_dt);
+                            }
+                        }
+                        const bool alive = finish_move3(m, ix1, iy1, iz1);
+                        const R chk = u[0] * u[0] + u[1] * u[1] + u[2] * u[2] + spn[0] * spn[0] +
+                                      spn[1] * spn[1] + spn[2] * spn[2];
+                        bad |= !isfinite(chk);
+                        if (diag && alive) {
+                            dhas = true;
+                            dw = w;
+                            du[0] = u[0], du[1] = u[1], du[2] = u[2];
+                            ds[0] = spn[0], ds[1] = spn[1], ds[2] = spn[2];
+                        }
                         S.cell[slot] = alive ? pack_cell3(ix1, iy1, iz1) : PIC_DEAD;
                         S.ox[slot] = ox1;
                         S.oy[slot] = oy1;
@@ -475,17 +456,13 @@ __global__ void __launch_bounds__(kThreads3, (TileConst3<TX, TY, TZ, R>::minb))
                         S.sz[slot] = spn[2];
                     }
                 }
+                if constexpr (DIAG) diag_warp3(P.diag, sp, dhas, dw, du, ds, drow);
             }
-            if constexpr (DIAG) diag_warp3(P.diag, sp, dhas, dw, du, ds, drow);
-            if constexpr (BIN)
-                bin_store3(P.bin[sp], S.tile_start, (int)gridDim.x, tile, &s_front[sp], dest, bcell, bv, idkeep[tid],
-                           P.err);
         }
         cp_async_wait0();
         if (diag)  // diagnostic columns: the tiles, then (binned) the overflow CTAs
             store_diag_sums3(P.diag, sp, sdiag, (int)blockIdx.x, (int)gridDim.x + (BIN ? P.nextra : 0));
     }
-    acc_flush();
     if (bad) atomicOr(P.err, PIC_EF_NAN);
     __syncthreads();
     if constexpr (BIN) {
@@ -497,28 +474,42 @@ __global__ void __launch_bounds__(kThreads3, (TileConst3<TX, TY, TZ, R>::minb))
         }
     }
 
-    // current window -> J: rows outside the mesh and all-zero groups skipped
+    // current window -> J: rows outside the mesh wrapped onto the periodic
+    // rows (only the binned layout deposits there), all-zero groups skipped
     if constexpr (sizeof(R) == 4) {
         constexpr int WQ = WX / 4;
         for (int qd = tid; qd < 3 * WZ * WY * WQ; qd += kThreads3) {
             const int row = qd / WQ, xq = qd - row * WQ;
             const int c = row / (WZ * WY), zy = row - c * WZ * WY;
             const int z = zy / WY, y = zy - z * WY;
-            const int gz = wz0 + z, gy = wy0 + y, gx = wx0 + 4 * xq;
-            if (gz < 0 || gz >= m.nz || gy < 0 || gy >= m.ny || gx < 0 || gx >= m.ld) continue;
             const float4 v = *reinterpret_cast<const float4 *>(&sJ[c * WA + zy * WX + 4 * xq]);
             if (v.x == 0.f && v.y == 0.f && v.z == 0.f && v.w == 0.f) continue;
-            atomicAdd(reinterpret_cast<float4 *>(&m.J[c * m.plane + ((size_t)gz * m.ny + gy) * m.ld + gx]), v);
+            const int gz = wrap3(wz0 + z, m.nz), gy = wrap3(wy0 + y, m.ny), gx = wx0 + 4 * xq;
+            R *row0 = m.J + c * m.plane + ((size_t)gz * m.ny + gy) * m.ld;
+            if (gx >= 0 && gx + 3 < m.nx) {
+                atomicAdd(reinterpret_cast<float4 *>(row0 + gx), v);
+            } else {
+                const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int q4 = 0; q4 < 4; ++q4) {
+                    int x = gx + q4;
+                    if (m.bc_x == 1) x = wrap3(x, m.nx);
+                    if (e[q4] != 0.f && x >= 0 && x < m.nx) atomicAdd(row0 + x, e[q4]);
+                }
+            }
         }
     } else {
         for (int e = tid; e < 3 * WA; e += kThreads3) {
+            const R v = sJ[e];
+            if (v == R(0)) continue;
             const int row = e / WX, x = e - row * WX;
             const int c = row / (WZ * WY), zy = row - c * WZ * WY;
             const int z = zy / WY, y = zy - z * WY;
-            const int gz = wz0 + z, gy = wy0 + y, gx = wx0 + x;
-            if (gz < 0 || gz >= m.nz || gy < 0 || gy >= m.ny || gx < 0 || gx >= m.nx) continue;
-            const R v = sJ[e];
-            if (v != R(0)) atomicAdd(&m.J[c * m.plane + ((size_t)gz * m.ny + gy) * m.ld + gx], v);
+            const int gz = wrap3(wz0 + z, m.nz), gy = wrap3(wy0 + y, m.ny);
+            int gx = wx0 + x;
+            if (m.bc_x == 1) gx = wrap3(gx, m.nx);
+            if (gx < 0 || gx >= m.nx) continue;
+            atomicAdd(&m.J[c * m.plane + ((size_t)gz * m.ny + gy) * m.ld + gx], v);
         }
     }
 }

@@ -270,6 +270,7 @@ StepParams3<R> step_params3(Ctx *c) {
     P.nsp = c->cfg.nspecies;
     for (int s = 0; s < P.nsp; ++s) P.sp[s] = dev_species3<R>(c, s, c->cur[s]);
     P.err = c->err;
+    P.diag_cols0 = c->ntiles;
     return P;
 }
 
@@ -1057,6 +1058,10 @@ pic_status_t pic_deposit(void *ctx, void *stream) {
                 return launch_deposit_split<T>(step_params<T>(c), s, c->n_upper[s], st);
             }));
             c->launches += 1;
+            // the split kernels move particles in their slots: a binned range
+            // may now hold particles of other tiles, so the next binned step
+            // re-bins first
+            c->sp_binned[s] = false;
         }
     c->pending_deposit = false;
     return PIC_OK;

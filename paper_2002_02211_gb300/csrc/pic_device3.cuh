@@ -132,6 +132,7 @@ struct StepParams3 {
     DiagParams diag;
     Bin3<R> bin[PIC_MAXSP];  // binned layout only
     int nextra;              // binned layout: CTAs of the overflow-range kernel
+    int diag_cols0;          // diagnostic columns of the fused kernel's CTAs (the overflow CTAs' follow)
 };
 
 // Global-memory access to the 4 x 4 x 4 nodes [cell-1, cell+2] of one
@@ -251,32 +252,46 @@ __device__ __forceinline__ void deposit_in_cell3(const M &m, int ix, int iy, int
 
 // general move (crosses at least one cell boundary): 3-node shapes per axis
 // from shape3 (org = min(old, new) cell); planes that only hold zeros when an
-// axis is not crossed are skipped
+// axis is not crossed are skipped.  The Esirkepov weight factors through the
+// midpoint shapes M = S0 + dS/2:
+//   S0y S0z + (dSy S0z + S0y dSz)/2 + dSy dSz/3 = My Mz + dSy dSz / 12,
+// and the prefix sums of dSx along x are formed once, so each current value
+// is one product of a prefix and a factor.
 template <typename R, class M>
 __device__ __forceinline__ void deposit_esirkepov3(const M &m, int ix, int iy, int iz, R ox, R oy, R oz, int ix1,
                                                    int iy1, int iz1, R ox1, R oy1, R oz1, R qw, R dx_dt, R dy_dt,
                                                    R dz_dt) {
-    const R half = R(0.5), third = R(1) / R(3);
+    const R half = R(0.5), k12 = R(1) / R(12);
     R S0x[3], dSx[3], S0y[3], dSy[3], S0z[3], dSz[3];
     const int gx = shape3(ix, ox, ix1, ox1, S0x, dSx);
     const int gy = shape3(iy, oy, iy1, oy1, S0y, dSy);
     const int gz = shape3(iz, oz, iz1, oz1, S0z, dSz);
     const int nx = ix1 != ix ? 3 : 2, ny = iy1 != iy ? 3 : 2, nz = iz1 != iz ? 3 : 2;
+    R Mx[3], My[3], Mz[3], Ex[3], Ey[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        Mx[a] = S0x[a] + half * dSx[a];
+        My[a] = S0y[a] + half * dSy[a];
+        Mz[a] = S0z[a] + half * dSz[a];
+        Ex[a] = k12 * dSx[a];
+        Ey[a] = k12 * dSy[a];
+    }
+    // prefixes -q w (dx/dt) sum_{i' <= i} dSx(i'); the last one is zero
     const R cx = -qw * dx_dt, cy = -qw * dy_dt, cz = -qw * dz_dt;
-    // Jx: prefix over i of dSx(i) F(j, k); the last prefix is zero
+    const R Px[2] = {cx * dSx[0], cx * (dSx[0] + dSx[1])};
+    const R Py[2] = {cy * dSy[0], cy * (dSy[0] + dSy[1])};
+    const R Pz[2] = {cz * dSz[0], cz * (dSz[0] + dSz[1])};
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         if (k >= nz) break;
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             if (j >= ny) break;
-            const R F = S0y[j] * S0z[k] + half * (dSy[j] * S0z[k] + S0y[j] * dSz[k]) + third * dSy[j] * dSz[k];
-            R acc = R(0);
+            const R F = My[j] * Mz[k] + Ey[j] * dSz[k];
 #pragma unroll
             for (int i = 0; i < 2; ++i) {
                 if (i >= nx - 1) break;
-                acc += dSx[i] * F;
-                m.j(0, gx + i, gy + j, gz + k, cx * acc);
+                m.j(0, gx + i, gy + j, gz + k, Px[i] * F);
             }
         }
     }
@@ -286,13 +301,11 @@ __device__ __forceinline__ void deposit_esirkepov3(const M &m, int ix, int iy, i
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             if (i >= nx) break;
-            const R F = S0x[i] * S0z[k] + half * (dSx[i] * S0z[k] + S0x[i] * dSz[k]) + third * dSx[i] * dSz[k];
-            R acc = R(0);
+            const R F = Mx[i] * Mz[k] + Ex[i] * dSz[k];
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
                 if (j >= ny - 1) break;
-                acc += dSy[j] * F;
-                m.j(1, gx + i, gy + j, gz + k, cy * acc);
+                m.j(1, gx + i, gy + j, gz + k, Py[j] * F);
             }
         }
     }
@@ -302,13 +315,11 @@ __device__ __forceinline__ void deposit_esirkepov3(const M &m, int ix, int iy, i
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             if (i >= nx) break;
-            const R F = S0x[i] * S0y[j] + half * (dSx[i] * S0y[j] + S0x[i] * dSy[j]) + third * dSx[i] * dSy[j];
-            R acc = R(0);
+            const R F = Mx[i] * My[j] + Ex[i] * dSy[j];
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
                 if (k >= nz - 1) break;
-                acc += dSz[k] * F;
-                m.j(2, gx + i, gy + j, gz + k, cz * acc);
+                m.j(2, gx + i, gy + j, gz + k, Pz[k] * F);
             }
         }
     }
@@ -322,12 +333,13 @@ __device__ __forceinline__ void deposit_esirkepov3(const M &m, int ix, int iy, i
 // one global atomic (all destinations of the warp in one round trip).  An
 // arrival past the range's end goes to the overflow range; when that is full
 // too the particle is dropped and PIC_EF_BINS raised.  tile = -1 (the
-// overflow-range kernel): every particle is an arrival.  All 32 lanes of the
-// warp must call it together.
+// overflow-range kernel): every particle is an arrival.  front_base: the first
+// slot of the tile's range when the caller holds it (else it is read from
+// tile_start).  All 32 lanes of the warp must call it together.
 template <typename R>
 __device__ __forceinline__ void bin_store3(const Bin3<R> &B, const int32_t *tile_start, int nt, int tile,
                                            int *s_front, int dest, uint32_t cell, const R v[10], int32_t id,
-                                           unsigned *err) {
+                                           unsigned *err, int front_base = -1) {
     constexpr unsigned kAll = 0xFFFFFFFFu;
     const int nr = nt + 1, lane = threadIdx.x & 31;
     const unsigned below = (1u << lane) - 1u;
@@ -339,7 +351,7 @@ __device__ __forceinline__ void bin_store3(const Bin3<R> &B, const int32_t *tile
         int b = 0;
         if (lane == leader) b = atomicAdd(s_front, __popc(stay));
         b = __shfl_sync(kAll, b, leader);
-        if (stayer) slot = tile_start[tile] + b + __popc(stay & below);
+        if (stayer) slot = (front_base >= 0 ? front_base : tile_start[tile]) + b + __popc(stay & below);
     }
     const int arr = dest >= 0 && !stayer ? dest : -1;
     if (__any_sync(kAll, arr >= 0)) {

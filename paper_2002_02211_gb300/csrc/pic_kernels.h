@@ -68,6 +68,7 @@ void laser_time_factors(const LaserParams &L, double t, double *fz, double *fy);
 
 // k_particles3.cu, k_fields3.cu (3D3V)
 bool fused3_tile_supported(int tx, int ty, int tz);
+
 template <typename R>
 cudaError_t launch_step_fused3(const StepParams3<R> &P, const CUtensorMap &tmapEB, bool binned, cudaStream_t st);
 template <typename R>
