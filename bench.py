@@ -89,7 +89,10 @@ def parse(argv=None):
     ap.add_argument("--steps", type=int, default=600)
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["config2", "config3", "config1", "config4", "config5"], default="config2")
+    ap.add_argument("--workload", choices=["config2", "config3", "config1", "config4", "config5", "precision"],
+                    default="config2")
+    ap.add_argument("--prec-steps", type=int, default=2000, help="precision: steps of the FP32 and FP64 runs")
+    ap.add_argument("--prec-cut-steps", type=int, default=200, help="precision: steps of the cut against the oracle")
     ap.add_argument("--adj-steps", type=int, default=1000, help="config5: run length of the adjoint")
     ap.add_argument("--checkpoint", type=int, default=50, help="config5: checkpoint interval")
     ap.add_argument("--scan-runs", type=int, default=256, help="config4: runs of the scan")
@@ -557,7 +560,8 @@ def main_ours(args):
         fp64 = {"value": u64 / t64, "unit": UNIT, "ms_per_step": t64 * 1e3 / args.fp64_steps,
                 "steps": args.fp64_steps, "dtype": "f64",
                 "timed_steps": [start_step, start_step + args.fp64_steps],
-                "bound": "alu (FP64 arithmetic; GB300 FP64 is about 1/64 of its FP32 rate)"}
+                "bound": "alu: the FP64 pipe, 75% of its peak busy at 4% of DRAM bandwidth "
+                         "(profiles/k_step_fused3-fp64_3d3v-512x256x32.md)"}
 
     cpu = None
     study = None
@@ -850,12 +854,147 @@ def main_latency(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# precision: the 3D3V laser-wakefield workload run in FP32 and in FP64 on the
+# GPU from the same seeded state (Eq. 4 polarization and kinetic-energy
+# moments compared every 10 steps), and a cut of it with the pulse in the
+# plasma run beside the FP64 oracle
+# ---------------------------------------------------------------------------
+def _moments_run(pic, wl, parts, precision, steps, every, stream, bins):
+    """Eq. (4) moments of species 0 every `every` steps of one run."""
+    import torch
+    cfg = pic.config_from_workload(wl, sort_every=DEFAULT_REBIN_EVERY, precision=precision, bins=bins)
+    rows = []
+    with pic.Simulation(cfg, stream=stream) as sim:
+        for s, d in enumerate(parts):
+            sim.set_particles(s, d)
+        if wl.neutralizing_background:
+            sim.capture_background()
+        sim.set_diagnostics(every)
+        t0 = time.perf_counter()
+        done = 0
+        while done < steps:
+            n = min(every, steps - done)
+            sim.step(n)
+            done += n
+            st, d = sim.get_diagnostics()
+            if st == done:
+                m = d[0]
+                rows.append((done, np.array(m["P"]), m["ekin_mean"], m["ekin_var"], m["count"]))
+        torch.cuda.synchronize()
+        seconds = time.perf_counter() - t0
+    return rows, seconds
+
+
+def _cut_against_oracle(pic, oracle, steps, stream):
+    """FP32 and FP64 GPU runs of a 512 x 32 x 8 cut of the workload (binned
+    layout, default tiles) beside the FP64 oracle, from the step where the
+    envelope peak is 30 steps from x = 0 (the laser at full amplitude from the
+    first step, the plasma driven within a few steps)."""
+    wl = W.scaled(W.CONFIG2, name="3d3v-512x32x8-cut-ppc2-lp-a0_3", ny=32, nz=8)
+    parts = W.generate_particles(wl)
+    sims = {}
+    for prec in (32, 64):
+        sim = pic.Simulation(pic.config_from_workload(wl, sort_every=DEFAULT_REBIN_EVERY, precision=prec,
+                                                      bins=DEFAULT_BINS), stream=stream)
+        for s, d in enumerate(parts):
+            sim.set_particles(s, d)
+        sims[prec] = sim
+    dt = sims[32].grid()[0]
+    start = int(round(wl.t_peak_periods * 2 * math.pi / dt)) - 30
+    with oracle.parallel() as nthreads:
+        orc = oracle.OracleSim(wl, parts, step=start)
+        for sim in sims.values():
+            sim.set_step(start)
+            sim.capture_background()
+        t0 = time.perf_counter()
+        for sim in sims.values():
+            sim.step(steps)
+        orc.step(steps)
+        t_orc = time.perf_counter() - t0
+    om = orc.moments(0)
+    p = orc.p[0]
+    alive = p["alive"].astype(bool)
+    un = np.maximum(np.sqrt(p["ux"] ** 2 + p["uy"] ** 2 + p["uz"] ** 2), 1e-3)
+    out = {"workload": wl.name, "steps": [start, start + steps], "particles": int(len(p["x"])),
+           "oracle_threads": nthreads, "oracle_seconds": round(t_orc, 1),
+           "hot_fraction_|u|>0.5": float(((un > 0.5) & alive).mean()),
+           "oracle_P": om[:3].tolist(), "oracle_ekin_mean_mev": om[5]}
+    for prec, sim in sims.items():
+        g = sim.polarization(0)
+        gp = sim.get_particles_f64(0)
+        live = gp["ix"] >= 0
+        ids = gp["id"][live]
+        both = alive[ids]
+        ids = ids[both]
+        sel = np.flatnonzero(live)[both]
+        du = np.sqrt(sum((gp[k][sel] - p[k][ids]) ** 2 for k in ("ux", "uy", "uz"))) / un[ids]
+        ds = np.sqrt(sum((gp[k][sel] - p[k][ids]) ** 2 for k in ("sx", "sy", "sz")))
+        dx = max(float(np.abs(gp["i" + a][sel] + gp["o" + a][sel] - p[a][ids]).max()) for a in ("x", "y", "z"))
+        out[f"fp{prec}"] = {
+            "P_abs_err": float(np.abs(np.array(g["P"]) - om[:3]).max()),
+            "ekin_mean_rel_err": abs(g["ekin_mean"] - om[5]) / abs(om[5]),
+            "ekin_var_rel_err": abs(g["ekin_var"] - om[6]) / abs(om[6]),
+            "count_diff": int(g["count"] - om[4]),
+            "u_rel_max": float(du.max()), "u_rel_median": float(np.median(du)),
+            "s_abs_max": float(ds.max()), "x_cells_max": dx,
+            "particles_over_1e-5_u": int((du > 1e-5).sum())}
+        sim.close()
+    return out
+
+
+def main_precision(args):
+    import torch
+
+    import oracle
+    import paper_2002_02211_gb300 as pic
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank != 0:
+        return
+    stream = torch.cuda.Stream(device=dev)
+    wl = W.CONFIG2
+    parts = W.generate_particles(wl)
+    every = 10
+    runs = {}
+    for prec in (32, 64):
+        runs[prec] = _moments_run(pic, wl, parts, prec, args.prec_steps, every, stream, DEFAULT_BINS)
+    r32, r64 = runs[32][0], runs[64][0]
+    by_step = {}
+    for (s32, p32, m32, v32, c32), (s64, p64, m64, v64, c64) in zip(r32, r64):
+        assert s32 == s64
+        by_step[s32] = {"dP": float(np.abs(p32 - p64).max()), "dmean": abs(m32 - m64) / abs(m64),
+                        "dvar": abs(v32 - v64) / abs(v64) if v64 else 0.0, "dcount": c32 - c64,
+                        "P64": p64.tolist(), "mean64": m64}
+    steps = sorted(by_step)
+    series = [[st, by_step[st]["dP"], by_step[st]["dmean"], by_step[st]["dvar"]] for st in steps[::10]]
+    end = by_step[steps[-1]]
+    cut = _cut_against_oracle(pic, oracle, args.prec_cut_steps, stream)
+    line = {"metric": "precision study: FP32 against FP64 on the GPU, and the GPU against the FP64 oracle",
+            "workload": wl.name, "steps": args.prec_steps, "diag_every": every,
+            "fp32_seconds": round(runs[32][1], 2), "fp64_seconds": round(runs[64][1], 2),
+            "fp32_vs_fp64": {"max_over_run": {"P_abs": max(by_step[s]["dP"] for s in steps),
+                                              "ekin_mean_rel": max(by_step[s]["dmean"] for s in steps),
+                                              "ekin_var_rel": max(by_step[s]["dvar"] for s in steps)},
+                             "end_of_run": {"step": steps[-1], "P_abs": end["dP"], "ekin_mean_rel": end["dmean"],
+                                            "ekin_var_rel": end["dvar"], "count_diff": end["dcount"],
+                                            "P_fp64": end["P64"], "ekin_mean_mev_fp64": end["mean64"]},
+                             "every_100_steps": {"columns": ["step", "P_abs", "ekin_mean_rel", "ekin_var_rel"],
+                                                 "rows": series}},
+            "cut_against_oracle": cut}
+    print(json.dumps(line), flush=True)
+
+
 def main(argv=None):
     args = parse(argv)
     if args.impl == "reference":
         main_reference(args)
     elif args.workload == "config1":
         main_latency(args)
+    elif args.workload == "precision":
+        main_precision(args)
     elif args.workload == "config4":
         main_scan(args)
     elif args.workload == "config5":

@@ -134,3 +134,41 @@ def test_per_particle_gradients_match_finite_differences():
                 vals.append(forward_loss(r2, 2.0, p2[0]["w"], np.stack([p2[0]["sx"], p2[0]["sy"], p2[0]["sz"]], 1)))
             fd = (vals[0] - vals[1]) / (2 * h)
             assert abs(g[key][slot] - fd) <= 1e-4 * abs(fd) + 1e-9, (pid, key, g[key][slot], fd)
+
+
+def test_fp32_adjoint_matches_fp64_adjoint_and_finite_differences():
+    # the FP32 adjoint (the one the benchmark times) differentiates the FP32
+    # forward run; it follows the FP64 adjoint, and the FP64 central
+    # differences, within the 1e-3 relative bar of the FP64 check (FP32
+    # rounding of the forward states moves the gradient by about 1e-6 here)
+    wl, parts, x, xk = _case()
+    n = len(x)
+    knots0 = np.array([0.03, 0.05, 0.06, 0.05, 0.04, 0.05])
+    w0 = _weights(knots0, x, xk, wl.species[0].ppc)
+    theta0, a00 = 1.3, 2.0
+    grads = {}
+    for prec in (32, 64):
+        run = LossRun(lambda a0, p=prec: pic.config_from_workload(W.scaled(wl, a0=a0), precision=p), parts, 0,
+                      NSTEPS, K, LOSS, neutralize=False)
+        with run.start(a00, w0, _spins(theta0, n)) as sim:
+            L, dla0 = sim.adjoint(NSTEPS, K, species=0, **LOSS)
+            g = sim.adjoint_particle_grads(0)
+        gw, gs = np.zeros(n), np.zeros((n, 3))
+        gw[g["id"]] = g["w"]
+        gs[g["id"], 0], gs[g["id"], 1] = g["sx"], g["sy"]
+        grads[prec] = {"L": L, "a0": dla0,
+                       "theta": float(np.sum(-math.sin(theta0) * gs[:, 0] + math.cos(theta0) * gs[:, 1])),
+                       "w_norm": float(np.linalg.norm(gw))}
+    run64 = _run(wl, parts)
+    fd = {}
+    for key in ("a0", "theta"):
+        vals = []
+        for sgn in (1, -1):
+            a, th = a00 + (sgn * H if key == "a0" else 0.0), theta0 + (sgn * H if key == "theta" else 0.0)
+            vals.append(forward_loss(run64, a, w0, _spins(th, n)))
+        fd[key] = (vals[0] - vals[1]) / (2 * H)
+    assert grads[32]["L"] == pytest.approx(grads[64]["L"], rel=1e-5)
+    for key in ("a0", "theta", "w_norm"):
+        assert grads[32][key] == pytest.approx(grads[64][key], rel=1e-3), (key, grads)
+    for key in ("a0", "theta"):
+        assert abs(grads[32][key] - fd[key]) <= 1e-3 * abs(fd[key]), (key, grads[32][key], fd[key])
