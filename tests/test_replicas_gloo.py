@@ -51,3 +51,19 @@ def test_single_rank_is_identity():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.combine(0.5, 123, 1) == (0.5, 123)
+
+
+def test_scan_split_balances_work():
+    # the 256-run scan split over 2, 4 and 8 ranks: every run exactly once,
+    # and the busiest rank within the greedy bound (mean + largest run)
+    sys.path.insert(0, ROOT)
+    import bench
+    import workloads as W
+    runs = W.batch_scan(256)
+    costs = [bench.run_cost(*r) for r in runs]
+    for world in (2, 4, 8):
+        share = bench.balance_runs(runs, world)
+        assert sorted(i for s in share for i in s) == list(range(len(runs)))
+        loads = [sum(costs[i] for i in s) for s in share]
+        assert max(loads) <= sum(costs) / world + max(costs)
+        assert max(loads) / min(loads) < 1.1
