@@ -80,7 +80,7 @@ DEFAULT_SORT_EVERY = {2: 32, 3: 2}
 DEFAULT_BINS = (25, 16)
 DEFAULT_REBIN_EVERY = 64
 KERNEL = {2: ("k_step_fused", ("k_particles.cu", "pic_device.cuh", "pic_ptx.cuh")),
-          3: ("k_step_fused3", ("k_particles3.cu", "pic_device3.cuh", "pic_device.cuh", "pic_ptx.cuh"))}
+          3: ("k_step_fused3", ("k_particles3.cu", "pic_device3.cuh", "pic_step3.cuh", "pic_device.cuh", "pic_ptx.cuh"))}
 
 
 def parse(argv=None):

@@ -85,7 +85,12 @@ struct Key3 {
         int ix, iy, iz;
         unpack_cell3(c, ix, iy, iz);
         tile = ((iz >> sz) * nty + (iy >> sy)) * ntx + (ix >> sx);
-        const int local = ((((iz & ((1 << sz) - 1)) << sy) | (iy & ((1 << sy) - 1))) << sx) | (ix & ((1 << sx) - 1));
+        int ly = iy & ((1 << sy) - 1);
+        // 16-wide tiles: rows in the order 0, 2, 1, 3 (of each group of four),
+        // so the two rows a warp's 32 cells span lie 2 rows (48 floats) apart
+        // in the field window, 16 banks, and their loads do not collide
+        if (sx == 4 && sy >= 2) ly = (ly & ~3) | ((ly & 1) << 1) | ((ly >> 1) & 1);
+        const int local = ((((iz & ((1 << sz) - 1)) << sy) | ly) << sx) | (ix & ((1 << sx) - 1));
         return (tile << (sx + sy + sz)) | local;
     }
     int cells() const { return 1 << (sx + sy + sz); }
