@@ -89,7 +89,8 @@ def parse(argv=None):
     ap.add_argument("--steps", type=int, default=600)
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["config2", "config3", "config1", "config4", "config5", "precision"],
+    ap.add_argument("--workload", choices=["config2", "config3", "config1", "config4", "config5", "precision",
+                                           "window"],
                     default="config2")
     ap.add_argument("--prec-steps", type=int, default=2000, help="precision: steps of the FP32 and FP64 runs")
     ap.add_argument("--prec-cut-steps", type=int, default=200, help="precision: steps of the cut against the oracle")
@@ -110,6 +111,10 @@ def parse(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=10, help="timed steps of the FP64 line (0: skip)")
+    ap.add_argument("--window-cells", type=int, default=16,
+                    help="window: cells a move of the co-moving window (a multiple of the tile width)")
+    ap.add_argument("--window-at", type=float, default=0.75,
+                    help="window: the box starts to move when the envelope peak reaches this fraction of nx")
     ap.add_argument("--start-step", type=int, default=-1,
                     help="untimed steps before the warm-up ends (-1: the laser-plasma interaction phase, "
                          "40 steps past the pulse peak's arrival at x = 0)")
@@ -123,6 +128,13 @@ def interaction_start(wl, dt):
     if wl.pol == "none" or wl.a0 <= 0:
         return 0
     return int(math.ceil(wl.t_peak_periods * 2 * math.pi / dt)) + 40
+
+
+def window_start(wl, dt, at):
+    """Step at which the laser envelope's peak reaches x = at * nx; a window
+    that starts there at the speed of light keeps the peak at that point."""
+    dx = wl.dx_lambda * 2 * math.pi
+    return int(math.ceil((wl.t_peak_periods * 2 * math.pi + at * wl.nx * dx) / dt))
 
 
 def fused_bytes(dim, n_particles, cells, precision, binned):
@@ -139,6 +151,8 @@ def workload(name, ny=0, nz=0):
         return W.batch_scan(1)[0][0]
     if name == "config5":
         return W.CONFIG5
+    if name == "window":
+        name = "config2"
     wl = {"config1": W.CONFIG1, "config2": W.CONFIG2, "config3": W.CONFIG3}[name]
     if ny:
         wl = W.scaled(wl, ny=ny)
@@ -1011,10 +1025,123 @@ def main_precision(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# window: config 2 with the co-moving window on the stepping path
+# ---------------------------------------------------------------------------
+def main_window(args):
+    """Config 2 run the way Sec. 2 runs it: once the envelope peak reaches
+    --window-at of the box, the box follows it at the speed of light, pic_step
+    moving it --window-cells cells at a time (in the binned layout by
+    relabelling whole tile columns) and taking in the plasma staged for each
+    move.  Timed from the step the window starts, every step a pic_step(1)
+    call bracketed by CUDA events, so the cost of a move is the difference
+    between the steps that make one and the steps that do not."""
+    import torch
+
+    import paper_2002_02211_gb300 as pic
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    init_dist(world, "nccl")
+    dev = torch.device("cuda", local)
+    wl = workload("config2", args.ny, args.nz)
+    bins = None if args.compact else (tuple(args.bins) if args.bins else DEFAULT_BINS)
+    sort_every = args.sort_every if args.sort_every > 0 else (DEFAULT_REBIN_EVERY if bins else DEFAULT_SORT_EVERY[3])
+    ncells = args.window_cells
+    parts = W.generate_particles(wl)
+    n_particles = sum(len(p["ix"]) for p in parts)
+    stream = torch.cuda.Stream(device=dev)
+    cfg = pic.config_from_workload(wl, sort_every=sort_every, tile=args.tile, bins=bins)
+    sim = pic.Simulation(cfg, stream=stream)
+    for s, d in enumerate(parts):
+        sim.set_particles(s, d)
+    sim.capture_background()
+    sim.set_diagnostics(args.diag_every)
+    dt, dx = sim.grid()[:2]
+    w0 = max(window_start(wl, dt, args.window_at), args.warmup)
+    sim.set_window(ncells, w0, 1.0)
+    # the plasma of every move: four distinct draws staged in turn, ids continuing
+    n_moves = int(math.ceil(args.steps * dt / dx / ncells)) + 2
+    draws = [W.injection_particles(wl, ncells, seed=900 + k) for k in range(min(4, n_moves))]
+    next_id = [len(p["ix"]) for p in parts]
+    for k in range(n_moves):
+        slab = []
+        for s, d in enumerate(draws[k % len(draws)]):
+            e = dict(d)
+            e["id"] = (d["id"] + next_id[s]).astype(np.int32)
+            next_id[s] += len(d["ix"])
+            slab.append(e)
+        sim.stage_injection(slab)
+    # untimed: the run up to the step the window starts (its last `warmup`
+    # steps are the warm-up)
+    sim.step(w0)
+    sim.sync()
+
+    clocks = ClockSampler(local)
+    launches0 = sim.launch_count()
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evs, moved = [], []
+    start.record(stream)
+    for _ in range(args.steps):
+        w = sim.window()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.step(1)
+        b.record(stream)
+        evs.append((a, b))
+        moved.append(sim.window() > w)
+    end.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clk = clocks.stop()
+    launches = sim.launch_count() - launches0
+    sim.sync()
+    diag_step, diag = sim.get_diagnostics()
+    elapsed = start.elapsed_time(end) * 1e-3
+    step_ms = np.array([a.elapsed_time(b) for a, b in evs])
+    moved = np.array(moved)
+    left = sim.staged_injections()
+    shift = sim.window()
+    sim.close()
+    tmax, units = combine(elapsed, n_particles * args.steps, world, dev)
+    if rank == 0:
+        plain = float(step_ms[~moved].mean()) if (~moved).any() else None
+        with_move = float(step_ms[moved].mean()) if moved.any() else None
+        line = {"metric": METRIC, "value": units / tmax, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": tmax * 1e3 / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": wl.name + "-comoving", "cells": [wl.nx, wl.ny, wl.nz],
+                           "particles": n_particles, "sort_every": sort_every,
+                           "layout": ("binned (headroom %d%%, at least %d spare slots per tile)" % tuple(bins))
+                                     if bins else "compact",
+                           "window": {"cells_per_move": ncells, "speed_c": 1.0, "start_step": w0,
+                                      "peak_at_cell": round(args.window_at * wl.nx)},
+                           "l2": "inputs larger than L2", "start_step": w0,
+                           "parallelism": f"replicas x{world}"},
+                "window": {"moves_timed": int(moved.sum()), "cells_moved_total": shift,
+                           "step_ms_without_move": plain, "step_ms_with_move": with_move,
+                           "move_ms": (with_move - plain) if plain is not None and with_move is not None else None,
+                           "plasma_staged": n_moves, "plasma_left": left,
+                           "particles_note": "value counts the particles at the start; moves remove and "
+                                             "inject equal plasma volumes"},
+                "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": clk, "gpu_launches": launches,
+                "diagnostics": {"step": diag_step,
+                                "P": {sp.name: [round(v, 6) for v in d["P"]] for sp, d in zip(wl.species, diag)}}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def main(argv=None):
     args = parse(argv)
     if args.impl == "reference":
         main_reference(args)
+    elif args.workload == "window":
+        main_window(args)
     elif args.workload == "config1":
         main_latency(args)
     elif args.workload == "precision":

@@ -324,13 +324,46 @@ pic_status_t pic_gauss_residual(void *ctx, double out[2], void *stream);
  * particle moves by -ncells cells and those whose cell falls below x = 2 are
  * removed.  inject is NULL or an array of nspecies host particle sets (same
  * layout as pic_set_particles) holding the plasma of the uncovered columns,
- * normally cells [nx - 2 - ncells, nx - 2) in the moved box; they are appended
- * (PIC_ERR_OVERFLOW if a species' capacity would be exceeded, nothing changed
- * then) and, after pic_capture_background, their immobile ions join the
- * background.  Every species is then sorted.  Needs PIC_BC_OPEN and
- * 1 <= ncells <= nx - 8; the laser source keeps its time profile at the new
- * x = 0.  Synchronous.  The step index is unchanged. */
+ * normally cells [nx - 2 - ncells, nx - 2) in the moved box; after
+ * pic_capture_background their immobile ions join the background.
+ * A species in the binned 3D3V layout, with ncells a multiple of the tile
+ * width along x, stays binned: its tile ranges are relabelled by whole tile
+ * columns (the ranges of the columns that left take the uncovered ones) and
+ * the plasma goes into its tiles' ranges; a range that is full passes the
+ * rest to the overflow range, and when that fills too particles are lost and
+ * PIC_ERR_OVERFLOW is returned.  Every other species takes the compact path:
+ * the plasma is appended after its slots (PIC_ERR_OVERFLOW, and nothing
+ * changed, if its capacity would be exceeded) and the species is sorted.
+ * Needs PIC_BC_OPEN and 1 <= ncells <= nx - 8; the laser source keeps its
+ * time profile at the new x = 0.  Synchronous.  The step index is unchanged. */
 pic_status_t pic_shift_window(void *ctx, int ncells, const pic_particles_t *inject, void *stream);
+
+/* The co-moving window on the stepping path.  With it on, pic_step makes the
+ * move pic_shift_window describes before the step from index n whenever
+ *     n >= start_step  and  moved + ncells <= floor((n - start_step) dt speed / dx),
+ * moved being the cells the window has moved since this call: the box
+ * follows a front that leaves at step start_step with speed `speed` (units of
+ * c), lagging it by less than ncells cells.  Each move takes the oldest
+ * plasma staged with pic_stage_injection (none staged: vacuum enters) and
+ * runs on the device without host synchronisation; a plasma that does not
+ * fit is reported by the next synchronising call (PIC_ERR_OVERFLOW).  In the
+ * binned 3D3V layout choose ncells a multiple of the tile width along x:
+ * other moves sort every species.  ncells = 0 switches the window off;
+ * otherwise 1 <= ncells <= nx - 8, speed > 0 and finite, PIC_BC_OPEN (else
+ * PIC_ERR_ARG).  pic_push_deposit and pic_field_update never move it. */
+pic_status_t pic_set_window(void *ctx, int ncells, int64_t start_step, double speed);
+
+/* Stages the plasma of one future move: inject = nspecies host particle sets
+ * (layout of pic_set_particles, cells of the moved box, normally
+ * [nx - 2 - ncells, nx - 2)), copied to device memory the context owns and
+ * queued behind the ones staged before; the moves of pic_step consume them
+ * in order.  Cells outside the particle region give PIC_ERR_ARG, a set larger
+ * than the species capacity PIC_ERR_OVERFLOW; nothing is queued then.
+ * Synchronous: the host arrays may be reused on return. */
+pic_status_t pic_stage_injection(void *ctx, const pic_particles_t *inject, void *stream);
+
+/* Staged plasmas not yet consumed by a move. */
+pic_status_t pic_staged_injections(void *ctx, int64_t *count);
 
 /* Cells the window has moved since pic_create. */
 pic_status_t pic_get_window(void *ctx, int64_t *offset_cells);

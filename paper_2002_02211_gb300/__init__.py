@@ -134,6 +134,9 @@ _SIGS = {
     "pic_batch_launch_count": [C.c_void_p, C.POINTER(C.c_int64)],
     "pic_batch_tune": [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
     "pic_get_window": [C.c_void_p, C.POINTER(C.c_int64)],
+    "pic_set_window": [C.c_void_p, C.c_int, C.c_int64, C.c_double],
+    "pic_stage_injection": [C.c_void_p, C.c_void_p, C.c_void_p],
+    "pic_staged_injections": [C.c_void_p, C.POINTER(C.c_int64)],
     "pic_set_diagnostics": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
     "pic_get_diagnostics": [C.c_void_p, C.c_void_p, C.POINTER(C.c_int64), C.c_void_p],
     "pic_moments_noalloc": [C.c_int64] + [C.c_void_p] * 8 + [C.c_double, C.c_double, C.c_double,
@@ -494,11 +497,7 @@ class Simulation:
         self._c(load().pic_adjoint_particle_grads(self.h, s, C.byref(p), self._s))
         return {k: v[:p.n] for k, v in out.items()}
 
-    def shift_window(self, ncells, inject=None):
-        """pic_shift_window: inject is None or one particle dict per species."""
-        if inject is None:
-            self._c(load().pic_shift_window(self.h, int(ncells), None, self._s))
-            return
+    def _inject_arr(self, inject):
         keep = []
         arr = (pic_particles_t * self.nspecies)()
         for s, d in enumerate(inject):
@@ -507,7 +506,34 @@ class Simulation:
             keep.append(a)
             arr[s] = pic_particles_t(n=len(a["ix"]), **{k: _ptr(v, _I32P if v.dtype == np.int32 else _F32P)
                                                          for k, v in a.items()})
+        return arr, keep
+
+    def shift_window(self, ncells, inject=None):
+        """pic_shift_window: inject is None or one particle dict per species."""
+        if inject is None:
+            self._c(load().pic_shift_window(self.h, int(ncells), None, self._s))
+            return
+        arr, keep = self._inject_arr(inject)
         self._c(load().pic_shift_window(self.h, int(ncells), arr, self._s))
+        del keep
+
+    def set_window(self, ncells, start_step=0, speed=1.0):
+        """pic_set_window: pic_step moves the box by ncells cells whenever it
+        lags a front leaving at start_step with `speed` (units of c) by
+        ncells; ncells = 0 switches it off."""
+        self._c(load().pic_set_window(self.h, int(ncells), int(start_step), float(speed)))
+
+    def stage_injection(self, inject):
+        """pic_stage_injection: one particle dict per species, the plasma of
+        one future move."""
+        arr, keep = self._inject_arr(inject)
+        self._c(load().pic_stage_injection(self.h, arr, self._s))
+        del keep
+
+    def staged_injections(self):
+        v = C.c_int64()
+        self._c(load().pic_staged_injections(self.h, C.byref(v)))
+        return v.value
 
     def window(self):
         v = C.c_int64()

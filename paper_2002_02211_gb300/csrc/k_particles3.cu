@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(kThreads3) k_overflow3(const StepParams3<R> P)
                 bad |= !finite3(u) || !finite3(spn);
                 if (finish_move3(m, ix1, iy1, iz1)) {
                     if (diag) diag_add3(dacc, dm, dlo, dhi, dshift, w, u, spn);
-                    dest = bin_dest3<TX, TY, TZ>(m, P.t, ix1, iy1, iz1, P.err);
+                    dest = bin_dest3<TX, TY, TZ>(m, P.t, ix1, iy1, iz1, P.err, P.bin[sp].txo);
                     cw = pack_cell3(ix1, iy1, iz1);
                     v[0] = ox1, v[1] = oy1, v[2] = oz1, v[3] = u[0], v[4] = u[1], v[5] = u[2];
                     v[6] = spn[0], v[7] = spn[1], v[8] = spn[2], v[9] = w;
@@ -240,10 +240,12 @@ __global__ void __launch_bounds__(kThreads3, (TileConst3<TX, TY, TZ, R>::minb))
         }
         cp_async_commit();
     };
+    // binned: the range this tile's particles of species sp live in
+    auto own = [&](int sp) { return tile - tx + bin_rot_x(tx, P.t.ntx, P.bin[sp].txo); };
     // the particles of this tile: bin_slot(range, k), k < range.len
     auto range = [&](int sp) {
         const DevSpecies3<R> &S = P.sp[sp];
-        if constexpr (BIN) return bin_range(S.tile_start, P.bin[sp].cnt_in, (int)gridDim.x + 1, tile);
+        if constexpr (BIN) return bin_range(S.tile_start, P.bin[sp].cnt_in, (int)gridDim.x + 1, own(sp));
         BinRange b;
         b.beg = S.tile_start[tile];
         b.len = b.front = b.split = S.tile_start[tile + 1] - b.beg;
@@ -372,14 +374,14 @@ __global__ void __launch_bounds__(kThreads3, (TileConst3<TX, TY, TZ, R>::minb))
                     bad |= !isfinite(chk);
                     if (alive) {
                         dhas = DIAG;
-                        dest = bin_dest3<TX, TY, TZ>(m, P.t, ix1, iy1, iz1, P.err);
+                        dest = bin_dest3<TX, TY, TZ>(m, P.t, ix1, iy1, iz1, P.err, P.bin[sp].txo);
                         bcell = pack_cell3(ix1, iy1, iz1);
                         bv[0] = ox1, bv[1] = oy1, bv[2] = oz1, bv[3] = u[0], bv[4] = u[1], bv[5] = u[2];
                         bv[6] = spn[0], bv[7] = spn[1], bv[8] = spn[2], bv[9] = w;
                     }
                 }
                 if constexpr (DIAG) diag_warp3(P.diag, sp, dhas, w, u, spn, drow);
-                bin_store3(P.bin[sp], S.tile_start, (int)gridDim.x, tile, &s_front[sp], dest, bcell, bv, id, P.err,
+                bin_store3(P.bin[sp], S.tile_start, (int)gridDim.x, own(sp), &s_front[sp], dest, bcell, bv, id, P.err,
                            rg.beg);
             } else {
                 // Eq. (4) contribution of this lane's record, summed over the warp below
@@ -469,8 +471,9 @@ __global__ void __launch_bounds__(kThreads3, (TileConst3<TX, TY, TZ, R>::minb))
         // the destination range of this tile: its stayers, and where its arrivals start
         if (tid < P.nsp && P.sp[tid].mobile) {
             const int nr = (int)gridDim.x + 1;
-            P.bin[tid].cnt_out[tile] = s_front[tid];
-            P.bin[tid].cnt_out[nr + tile] = range(tid).len;
+            const int r = own(tid);
+            P.bin[tid].cnt_out[r] = s_front[tid];
+            P.bin[tid].cnt_out[nr + r] = range(tid).len;
         }
     }
 

@@ -250,15 +250,6 @@ cudaError_t scan_tiles(const int32_t *count, int nt, int32_t *start, int32_t *sc
     return cudaGetLastError();
 }
 
-// the arrays a sort moves: the cell word, nf reals and the id
-template <typename R>
-struct SortArrays {
-    uint32_t *cell;
-    R *f[10];
-    int32_t *id;
-    const int32_t *n;
-};
-
 template <typename R, int NF, class K>
 __global__ void k_scatter(const SortArrays<R> src, const SortArrays<R> dst, const K kf, const int32_t *rank,
                           const int32_t *tile_start, const int32_t *tile_R, const int32_t *cell_off, int C) {
@@ -531,3 +522,192 @@ template cudaError_t launch_ghost_from_column<float>(const float *, const float 
                                                      cudaStream_t);
 template cudaError_t launch_ghost_from_column<double>(const double *, const double *, double *, size_t, int, int,
                                                       cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// co-moving window on the stepping path (no host synchronisation)
+// ---------------------------------------------------------------------------
+namespace {
+
+// Every mesh row moved n columns toward x_min in place, the uncovered columns
+// zero; one warp per row.  The warp reads a group of 256 columns into
+// registers before it writes them n columns lower, and the groups run in
+// increasing x, so every column is read before anything overwrites it.  The
+// left boundary values By(-1/2), Bz(-1/2) become the old column n - 1 of By
+// and Bz (read before the row moves).
+constexpr int kRowGroup = 8;  // columns a lane moves per group (256 a warp)
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_window_rows(const WindowRows<R> a) {
+    const int lane = threadIdx.x & 31;
+    const size_t warps = (size_t)gridDim.x * (blockDim.x >> 5);
+    const size_t total = a.rows * (size_t)a.nplanes;
+    for (size_t wq = blockIdx.x * (size_t)(blockDim.x >> 5) + (threadIdx.x >> 5); wq < total; wq += warps) {
+        const int pl = (int)(wq / a.rows);
+        const size_t r = wq - (size_t)pl * a.rows;
+        R *row = a.plane[pl] + r * a.ld;
+        if (lane == 0 && a.bnd && (pl == a.by || pl == a.bz)) a.bnd[(pl == a.by ? 0 : a.rows) + r] = row[a.n - 1];
+        __syncwarp();
+        for (int x0 = 0; x0 < a.nx; x0 += 32 * kRowGroup) {
+            R v[kRowGroup];
+#pragma unroll
+            for (int k = 0; k < kRowGroup; ++k) {
+                const int x = x0 + 32 * k + lane;
+                v[k] = x + a.n < a.nx ? row[x + a.n] : R(0);
+            }
+            __syncwarp();
+#pragma unroll
+            for (int k = 0; k < kRowGroup; ++k) {
+                const int x = x0 + 32 * k + lane;
+                if (x < a.nx) row[x] = v[k];
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// Binned layout: the ranges of the tile columns the move uncovered at x_max
+// (the last kt columns; the particles they held have all left the box) are
+// emptied: front, split and back zero in the current buffer's counters.
+// txo is the relabelling after the move (range of tile (tx, ty, tz) = that of
+// tile ((tx + txo) mod ntx, ty, tz)).
+__global__ void k_window_vacate(int32_t *cnt, int nr, int ntx, int nyz, int kt, int txo) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= kt * nyz) return;
+    const int yz = j / kt, tx = ntx - kt + (j - yz * kt);
+    const int r = yz * ntx + bin_rot_x(tx, ntx, txo);
+    cnt[r] = cnt[nr + r] = cnt[2 * nr + r] = 0;
+}
+
+// Binned layout: each staged particle is appended to the arrival segment of
+// its tile's range (slot beg + split + back, back counted up), or, when that
+// range is full, to the overflow range's; with both full it is dropped and
+// PIC_EF_BINS raised.  The arrival bases are recomputed afterwards.
+template <typename R>
+__global__ void k_window_inject3(const SortArrays<R> src, const SortArrays<R> dst, const int32_t *tile_start,
+                                 int32_t *cnt, const TileGeom3 t, int txo, unsigned *err) {
+    const int m = *src.n;
+    const int nt = t.ntx * t.nty * t.ntz, nr = nt + 1;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x) {
+        const uint32_t c = src.cell[i];
+        if (c == PIC_DEAD) continue;
+        int ix, iy, iz;
+        unpack_cell3(c, ix, iy, iz);
+        const int r = ((iz / t.TZ) * t.nty + iy / t.TY) * t.ntx + bin_rot_x(ix / t.TX, t.ntx, txo);
+        int slot = tile_start[r] + cnt[nr + r] + atomicAdd(&cnt[2 * nr + r], 1);
+        if (slot >= tile_start[r + 1]) {
+            slot = tile_start[nt] + cnt[nr + nt] + atomicAdd(&cnt[2 * nr + nt], 1);
+            if (slot >= tile_start[nt + 1]) {
+                atomicOr(err, PIC_EF_BINS);
+                continue;
+            }
+        }
+        dst.cell[slot] = c;
+#pragma unroll
+        for (int k = 0; k < 10; ++k) dst.f[k][slot] = src.f[k][i];
+        dst.id[slot] = src.id[i];
+    }
+}
+
+// Compact layout: the staged particles appended after the *n_dst slots in use
+// (nf reals a record), or, when they do not fit the capacity, nothing and
+// PIC_EF_CAP; k_window_count then adds the count.
+template <typename R, int NF>
+__global__ void k_window_append(const SortArrays<R> src, const SortArrays<R> dst, const int32_t *n_dst, int cap,
+                                unsigned *err) {
+    const int m = *src.n, n0 = *n_dst;
+    if ((long long)n0 + m > cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, PIC_EF_CAP);
+        return;
+    }
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x) {
+        const long long slot = n0 + i;
+        dst.cell[slot] = src.cell[i];
+#pragma unroll
+        for (int k = 0; k < NF; ++k) dst.f[k][slot] = src.f[k][i];
+        dst.id[slot] = src.id[i];
+    }
+}
+
+__global__ void k_window_count(int32_t *n_dst, const int32_t *m_src, int cap) {
+    const long long n = (long long)*n_dst + *m_src;
+    if (n <= cap) *n_dst = (int32_t)n;
+}
+
+// Live particles after a sort, into host-mapped memory: the sorted count of
+// the compact layout, or the sum of the tiles' counts (split counters) of the
+// binned one.  One block.
+__global__ void __launch_bounds__(1024) k_live_sample(const int32_t *n_dev, const int32_t *split, int nt,
+                                                      volatile long long *out) {
+    __shared__ long long part[32];
+    long long s = 0;
+    if (split)
+        for (int t = threadIdx.x; t < nt; t += blockDim.x) s += split[t];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long tot = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += part[w];
+        *out = split ? tot : (long long)*n_dev;
+        __threadfence_system();
+    }
+}
+
+}  // namespace
+
+template <typename R>
+cudaError_t launch_window_rows(const WindowRows<R> &a, cudaStream_t st) {
+    if (a.rows == 0 || a.nplanes <= 0) return cudaSuccess;
+    if (a.n < 1 || a.n > a.nx) return cudaErrorInvalidValue;
+    k_window_rows<R><<<152 * 16, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_window_vacate(int32_t *cnt, int nr, int ntx, int nyz, int kt, int txo, cudaStream_t st) {
+    const int n = kt * nyz;
+    if (n <= 0) return cudaSuccess;
+    k_window_vacate<<<(n + 255) / 256, 256, 0, st>>>(cnt, nr, ntx, nyz, kt, txo);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_window_inject3(const SortArrays<R> &src, int m_upper, const SortArrays<R> &dst,
+                                  const int32_t *tile_start, int32_t *cnt, const TileGeom3 &t, int txo,
+                                  unsigned *err, cudaStream_t st) {
+    if (m_upper <= 0) return cudaSuccess;
+    k_window_inject3<R><<<grid_for(m_upper), 256, 0, st>>>(src, dst, tile_start, cnt, t, txo, err);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_window_append(const SortArrays<R> &src, int m_upper, const SortArrays<R> &dst, int32_t *n_dst,
+                                 int cap, bool d3, unsigned *err, cudaStream_t st) {
+    if (m_upper <= 0) return cudaSuccess;
+    if (d3)
+        k_window_append<R, 10><<<grid_for(m_upper), 256, 0, st>>>(src, dst, n_dst, cap, err);
+    else
+        k_window_append<R, 9><<<grid_for(m_upper), 256, 0, st>>>(src, dst, n_dst, cap, err);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_window_count<<<1, 1, 0, st>>>(n_dst, src.n, cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_live_sample(const int32_t *n_dev, const int32_t *split, int nt, volatile long long *out,
+                               cudaStream_t st) {
+    k_live_sample<<<1, 1024, 0, st>>>(n_dev, split, nt, out);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_window_rows<float>(const WindowRows<float> &, cudaStream_t);
+template cudaError_t launch_window_rows<double>(const WindowRows<double> &, cudaStream_t);
+template cudaError_t launch_window_inject3<float>(const SortArrays<float> &, int, const SortArrays<float> &,
+                                                  const int32_t *, int32_t *, const TileGeom3 &, int, unsigned *,
+                                                  cudaStream_t);
+template cudaError_t launch_window_inject3<double>(const SortArrays<double> &, int, const SortArrays<double> &,
+                                                   const int32_t *, int32_t *, const TileGeom3 &, int, unsigned *,
+                                                   cudaStream_t);
+template cudaError_t launch_window_append<float>(const SortArrays<float> &, int, const SortArrays<float> &, int32_t *,
+                                                 int, bool, unsigned *, cudaStream_t);
+template cudaError_t launch_window_append<double>(const SortArrays<double> &, int, const SortArrays<double> &,
+                                                  int32_t *, int, bool, unsigned *, cudaStream_t);

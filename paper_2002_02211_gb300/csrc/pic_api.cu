@@ -5,9 +5,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <deque>
 #include <new>
 #include <string>
 #include <vector>
@@ -25,6 +27,18 @@ struct SpeciesBuf {
     void *f[9] = {};  // ox oy ux uy uz sx sy sz w (float or double)
     void *oz = nullptr;  // 3D3V only
     int32_t *id = nullptr;
+};
+
+// One window move's plasma on the device (pic_stage_injection): per species
+// the packed cells, the reals of a record (SortArrays order), the ids, and the
+// count, on the host and on the device (where the kernels read it).
+struct Slab {
+    void *mem = nullptr;
+    int64_t n[PIC_MAX_SPECIES] = {};
+    uint32_t *cell[PIC_MAX_SPECIES] = {};
+    void *f[PIC_MAX_SPECIES][10] = {};
+    int32_t *id[PIC_MAX_SPECIES] = {};
+    int32_t *n_dev[PIC_MAX_SPECIES] = {};
 };
 
 struct Ctx {
@@ -66,6 +80,29 @@ struct Ctx {
     bool pending_deposit = false;
     long long step = 0;
     long long window = 0;         // cells the co-moving window has moved
+    // co-moving window on the stepping path (pic_set_window): cells a move
+    // (0: off), the step index the light front starts from, its speed [c],
+    // and the cells moved when the window was set
+    int w_ncells = 0;
+    long long w_start = 0;
+    double w_speed = 1.0;
+    long long w_window0 = 0;
+    // staged plasma of the next moves, oldest first; memory of consumed
+    // slabs is freed at the next synchronous window call (kernels may still
+    // read it)
+    std::deque<Slab> inj_queue;
+    std::vector<void *> inj_spent;
+    // binned layout: tile-column relabelling of each species' ranges since
+    // its last sort (bin_rot_x)
+    int bin_txo[PIC_MAX_SPECIES] = {};
+    // live-particle counts the sorts leave in host-mapped memory: once a
+    // sort's event has completed, n_live becomes its count plus the particles
+    // injected since (a tighter bound than counting every injection)
+    volatile long long *live_host = nullptr;
+    long long *live_dev = nullptr;
+    cudaEvent_t live_ev[PIC_MAX_SPECIES] = {};
+    bool live_pending[PIC_MAX_SPECIES] = {};
+    int64_t live_added[PIC_MAX_SPECIES] = {};
     // adjoint results: per species the lambdas of the initial state
     // (lx ly lux luy luz lsx lsy lsz lw), the initial cells, and the slot counts
     void *adj_lam[PIC_MAX_SPECIES][9] = {};
@@ -421,6 +458,25 @@ pic_status_t seal_pending(Ctx *c, cudaStream_t st) {
     return PIC_OK;
 }
 
+// n_live of species s from the last sort's live count once that sort has
+// completed (non-blocking), plus the particles injected since
+void refresh_live(Ctx *c, int s) {
+    if (!c->live_pending[s]) return;
+    const cudaError_t q = cudaEventQuery(c->live_ev[s]);
+    if (q == cudaErrorNotReady) {
+        cudaGetLastError();  // not an error: clear it
+        return;
+    }
+    if (q != cudaSuccess) return;
+    c->n_live[s] = std::min<int64_t>(c->n_live[s], c->live_host[s] + c->live_added[s]);
+    c->live_pending[s] = false;
+}
+
+void add_live(Ctx *c, int s, int64_t m) {
+    c->n_live[s] += m;
+    c->live_added[s] += m;
+}
+
 // No host synchronisation: the sorted slot count stays on the device.  In the
 // compact layout it only shrinks, so n_upper still bounds it; in the binned
 // layout n_upper becomes the host bound on the span of the ranges.
@@ -428,6 +484,7 @@ pic_status_t seal_pending(Ctx *c, cudaStream_t st) {
 pic_status_t sort_species(Ctx *c, int s, cudaStream_t st, bool compact_only = false) {
     pic_status_t sr = seal_pending(c, st);
     if (sr != PIC_OK) return sr;
+    refresh_live(c, s);
     const int from = c->cur[s], to = 1 - from;
     SortScratch w{c->cell_count, c->cell_off, c->tile_R, c->tile_count, c->tile_cursor, c->scratch_i32};
     BinSort bins{};
@@ -449,6 +506,16 @@ pic_status_t sort_species(Ctx *c, int s, cudaStream_t st, bool compact_only = fa
     }));
     c->launches += bin ? 7 : 6;  // rank, layout, three scan passes, scatter (, seal)
     c->cur[s] = to;
+    c->bin_txo[s] = 0;
+    if (c->live_host) {
+        // the sorted live count: the compact count, or the binned tiles' counts
+        CK(launch_live_sample(c->n_dev + s, bin ? bins.cnt_to + c->ntiles + 1 : nullptr, c->ntiles,
+                              c->live_dev + s, st));
+        CK(cudaEventRecord(c->live_ev[s], st));
+        c->launches += 1;
+        c->live_pending[s] = true;
+        c->live_added[s] = 0;
+    }
     if (bin) {
         c->n_upper[s] = (int)span;
         const int want = (bins.ovf_cap + 255) / 256;
@@ -489,6 +556,7 @@ pic_status_t upload_particles(Ctx *c, int s, const PT *p, int64_t base, cudaStre
     const size_t n = (size_t)p->n;
     if (base == 0) {
         c->unsealed[s] = false;  // the upload replaces the layout
+        c->live_pending[s] = false;
     } else {
         pic_status_t r = seal_pending(c, st);  // appended after sealed slots
         if (r != PIC_OK) return r;
@@ -536,7 +604,10 @@ pic_status_t upload_particles(Ctx *c, int s, const PT *p, int64_t base, cudaStre
         if (base == 0) c->n_live[s] = 0;
         return r;
     }
-    c->n_live[s] = base == 0 ? (int64_t)n : c->n_live[s] + (int64_t)n;
+    if (base == 0)
+        c->n_live[s] = (int64_t)n;
+    else
+        add_live(c, s, (int64_t)n);
     return PIC_OK;
 }
 
@@ -586,6 +657,305 @@ pic_status_t alloc_old(Ctx *c, int s) {
     const size_t cap = (size_t)c->cfg.sp[s].capacity;
     CK(cudaMalloc(&c->cell_old[s], cap * sizeof(uint32_t) + 16));
     for (int k = 0; k < 3; ++k) CK(cudaMalloc(&c->old_f[s][k], cap * c->rb + 16));
+    return PIC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// co-moving window (Sec. 2): staged plasma and the device-side move
+// ---------------------------------------------------------------------------
+
+// the arrays of species s in buffer `which`, records in SortArrays order
+template <typename T>
+SortArrays<T> buf_arrays(Ctx *c, int s, int which) {
+    const SpeciesBuf &B = c->buf[s][which];
+    SortArrays<T> a{};
+    a.cell = B.cell;
+    a.id = B.id;
+    a.n = c->n_dev + s;
+    T *const *f = reinterpret_cast<T *const *>(B.f);
+    if (c->dim == 3) {
+        T *g[10] = {f[0], f[1], static_cast<T *>(B.oz), f[2], f[3], f[4], f[5], f[6], f[7], f[8]};
+        for (int k = 0; k < 10; ++k) a.f[k] = g[k];
+    } else {
+        for (int k = 0; k < 9; ++k) a.f[k] = f[k];
+    }
+    return a;
+}
+
+template <typename T>
+SortArrays<T> slab_arrays(const Slab &b, int s) {
+    SortArrays<T> a{};
+    a.cell = b.cell[s];
+    a.id = b.id[s];
+    a.n = b.n_dev[s];
+    for (int k = 0; k < 10; ++k) a.f[k] = static_cast<T *>(b.f[s][k]);
+    return a;
+}
+
+void ensure_live(Ctx *c) {
+    if (c->live_host) return;
+    long long *h = nullptr;
+    if (cudaHostAlloc(reinterpret_cast<void **>(&h), PIC_MAX_SPECIES * sizeof(long long), cudaHostAllocMapped) !=
+        cudaSuccess)
+        return;  // without samples n_live only counts up (still a bound)
+    for (int s = 0; s < PIC_MAX_SPECIES; ++s) h[s] = 0;
+    if (cudaHostGetDevicePointer(reinterpret_cast<void **>(&c->live_dev), h, 0) != cudaSuccess) {
+        cudaFreeHost(h);
+        return;
+    }
+    for (int s = 0; s < PIC_MAX_SPECIES; ++s)
+        if (cudaEventCreateWithFlags(&c->live_ev[s], cudaEventDisableTiming) != cudaSuccess) {
+            for (int q = 0; q < s; ++q) cudaEventDestroy(c->live_ev[q]);
+            cudaFreeHost(h);
+            c->live_dev = nullptr;
+            return;
+        }
+    c->live_host = h;
+}
+
+// frees the memory of consumed slabs (kernels that read it are done after
+// the stream synchronisation)
+pic_status_t free_spent(Ctx *c, cudaStream_t st) {
+    if (c->inj_spent.empty()) return PIC_OK;
+    CK(cudaStreamSynchronize(st));
+    for (void *m : c->inj_spent) cudaFree(m);
+    c->inj_spent.clear();
+    return PIC_OK;
+}
+
+// Host plasma of one move (one set per species, float arrays) into device
+// memory: cells packed and checked against the particle region, reals in the
+// context's precision.  Synchronous.
+pic_status_t stage_slab(Ctx *c, const pic_particles_t *inj, Slab *out, cudaStream_t st) {
+    const bool d3 = c->dim == 3;
+    const int nf = d3 ? 10 : 9;
+    const size_t rb = c->rb;
+    auto up16 = [](size_t b) { return (b + 15) / 16 * 16; };
+    size_t bytes = 0;
+    size_t off_cell[PIC_MAX_SPECIES], off_id[PIC_MAX_SPECIES], off_n[PIC_MAX_SPECIES],
+        off_f[PIC_MAX_SPECIES][10];
+    for (int s = 0; s < c->cfg.nspecies; ++s) {
+        const pic_particles_t &p = inj[s];
+        if (p.n < 0) return fail(c, PIC_ERR_ARG, "negative injection count");
+        if (p.n > c->cfg.sp[s].capacity) return fail(c, PIC_ERR_OVERFLOW, "injection exceeds the capacity");
+        if (p.n > 0) {
+            const float *src[9] = {p.ox, p.oy, p.ux, p.uy, p.uz, p.sx, p.sy, p.sz, p.w};
+            if (!p.ix || !p.iy || !p.id || (d3 && (!p.iz || !p.oz))) return fail(c, PIC_ERR_ARG, "null particle array");
+            for (int k = 0; k < 9; ++k)
+                if (!src[k]) return fail(c, PIC_ERR_ARG, "null particle array");
+        }
+        const size_t n = (size_t)p.n;
+        off_cell[s] = bytes, bytes += up16(n * 4);
+        off_id[s] = bytes, bytes += up16(n * 4);
+        off_n[s] = bytes, bytes += 16;
+        for (int k = 0; k < nf; ++k) off_f[s][k] = bytes, bytes += up16(n * rb);
+    }
+    Slab b;
+    CK(cudaMalloc(&b.mem, bytes));
+    char *base = static_cast<char *>(b.mem);
+    const int xlo = c->cfg.bc_x == PIC_BC_OPEN ? 2 : 0;
+    const int xhi = c->cfg.bc_x == PIC_BC_OPEN ? c->cfg.nx - 3 : c->cfg.nx - 1;
+    cudaError_t e = cudaSuccess;
+    for (int s = 0; s < c->cfg.nspecies && e == cudaSuccess; ++s) {
+        const pic_particles_t &p = inj[s];
+        const size_t n = (size_t)p.n;
+        b.n[s] = p.n;
+        b.cell[s] = reinterpret_cast<uint32_t *>(base + off_cell[s]);
+        b.id[s] = reinterpret_cast<int32_t *>(base + off_id[s]);
+        b.n_dev[s] = reinterpret_cast<int32_t *>(base + off_n[s]);
+        for (int k = 0; k < nf; ++k) b.f[s][k] = base + off_f[s][k];
+        const int32_t n32 = (int32_t)n;
+        e = cudaMemcpyAsync(b.n_dev[s], &n32, sizeof(int32_t), cudaMemcpyHostToDevice, st);
+        if (n == 0 || e != cudaSuccess) continue;
+        // cell indices through the scratch (3 x the capacity)
+        const size_t room = (size_t)c->cfg.sp[s].capacity;
+        int32_t *dix = c->scratch_i32, *diy = dix + room, *diz = diy + room;
+        e = cudaMemcpyAsync(dix, p.ix, n * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(diy, p.iy, n * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && d3) e = cudaMemcpyAsync(diz, p.iz, n * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = d3 ? launch_pack_cells3(dix, diy, diz, b.cell[s], (int)n, xlo, xhi, c->cfg.ny, c->cfg.nz, c->err, st)
+                   : launch_pack_cells(dix, diy, b.cell[s], (int)n, xlo, xhi, c->cfg.ny, c->err, st);
+        const float *src3[10] = {p.ox, p.oy, p.oz, p.ux, p.uy, p.uz, p.sx, p.sy, p.sz, p.w};
+        const float *src2[9] = {p.ox, p.oy, p.ux, p.uy, p.uz, p.sx, p.sy, p.sz, p.w};
+        for (int k = 0; k < nf && e == cudaSuccess; ++k) {
+            const float *from = d3 ? src3[k] : src2[k];
+            if (rb == 4) {
+                e = cudaMemcpyAsync(b.f[s][k], from, n * sizeof(float), cudaMemcpyHostToDevice, st);
+            } else {
+                e = cudaMemcpyAsync(c->stage, from, n * sizeof(float), cudaMemcpyHostToDevice, st);
+                if (e == cudaSuccess)
+                    e = launch_convert<float, double>(static_cast<float *>(c->stage), static_cast<double *>(b.f[s][k]),
+                                                      n, st);
+            }
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(b.id[s], p.id, n * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+        // the scratch and the staging buffer are reused by the next species
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaFree(b.mem);
+        return fail(c, PIC_ERR_CUDA, std::string("staging the window plasma: ") + cudaGetErrorString(e));
+    }
+    pic_status_t r = check_flags(c, st);
+    if (r != PIC_OK) {
+        cudaFree(b.mem);
+        return r;
+    }
+    *out = b;
+    return PIC_OK;
+}
+
+// One move of the co-moving window by ncells cells (the operation
+// pic_shift_window describes) without host synchronisation: the mesh rows
+// slide in place; each species either keeps the binned layout, its ranges
+// relabelled by whole tile columns (ncells a multiple of the tile width: the
+// ranges of the columns that left take the plasma of the uncovered ones, no
+// particle moves), or takes the compact path: cells shifted, the plasma
+// appended after the slots in use, a sort.  slab: the plasma, or nullptr.
+pic_status_t window_move(Ctx *c, int ncells, const Slab *slab, cudaStream_t st) {
+    const bool d3 = c->dim == 3;
+    CK(with_real(c, [&](auto z) -> cudaError_t {
+        using T = decltype(z);
+        WindowRows<T> a{};
+        T *EB = static_cast<T *>(c->EB), *J = static_cast<T *>(c->J);
+        for (int k = 0; k < 6; ++k) a.plane[k] = EB + k * c->plane;
+        for (int k = 0; k < 3; ++k) a.plane[6 + k] = J + k * c->plane;
+        a.plane[9] = static_cast<T *>(c->rho_bg);
+        a.nplanes = 10;
+        a.by = 4;
+        a.bz = 5;
+        a.bnd = static_cast<T *>(c->bnd);
+        a.rows = c->bnd_n;
+        a.nx = c->cfg.nx;
+        a.ld = c->ld;
+        a.n = ncells;
+        return launch_window_rows<T>(a, st);
+    }));
+    c->launches += 1;
+    bool sort[PIC_MAX_SPECIES] = {};
+    for (int s = 0; s < c->cfg.nspecies; ++s) {
+        const int64_t m = slab ? slab->n[s] : 0;
+        const bool rotate = d3 && c->sp_binned[s] && ncells % c->tg3.TX == 0;
+        if (!rotate && c->sp_binned[s]) {
+            pic_status_t r = sort_species(c, s, st, true);  // to the compact layout first
+            if (r != PIC_OK) return r;
+        }
+        const int cur = c->cur[s];
+        if (rotate) {
+            const int nt = c->ntiles, nr = nt + 1, ntx = c->tg3.ntx, kt = ncells / c->tg3.TX;
+            int32_t *cnt = c->bin_cnt[s][cur];
+            // every slot of the ranges (the span is tile_start[nt + 1])
+            CK(launch_shift_cells(c->buf[s][cur].cell, c->tile_start[s] + nt + 1, c->n_upper[s], ncells, true, st));
+            c->bin_txo[s] = (c->bin_txo[s] + kt) % ntx;
+            CK(launch_window_vacate(cnt, nr, ntx, c->tg3.nty * c->tg3.ntz, kt, c->bin_txo[s], st));
+            c->launches += 2;
+            if (m > 0) {
+                CK(with_real(c, [&](auto z) {
+                    using T = decltype(z);
+                    return launch_window_inject3<T>(slab_arrays<T>(*slab, s), (int)m, buf_arrays<T>(c, s, cur),
+                                                    c->tile_start[s], cnt, c->tg3, c->bin_txo[s], c->err, st);
+                }));
+                c->launches += 1;
+            }
+            // arrival bases (and the overflow alert) from the new counters
+            SealArgs a{};
+            a.nranges = nr;
+            a.fill = false;
+            a.counters = true;
+            a.ovf_alert = c->ovf_alert_dev;
+            a.nsp = 1;
+            a.sp[0] = SealSpecies{c->buf[s][cur].cell, c->tile_start[s], cnt, nullptr};
+            CK(launch_seal_bins(a, st));
+            c->launches += 1;
+        } else {
+            CK(launch_shift_cells(c->buf[s][cur].cell, c->n_dev + s, c->n_upper[s], ncells, d3, st));
+            c->launches += 1;
+            if (m > 0) {
+                CK(with_real(c, [&](auto z) {
+                    using T = decltype(z);
+                    return launch_window_append<T>(slab_arrays<T>(*slab, s), (int)m, buf_arrays<T>(c, s, cur),
+                                                   c->n_dev + s, (int)c->cfg.sp[s].capacity, d3, c->err, st);
+                }));
+                c->launches += 2;
+                c->n_upper[s] = (int)std::min<int64_t>((int64_t)c->n_upper[s] + m, c->cfg.sp[s].capacity);
+            }
+            sort[s] = true;
+        }
+        if (m > 0) {
+            add_live(c, s, m);
+            if (c->has_background) {
+                // the plasma brings its immobile ions: rho_bg -= rho(plasma),
+                // deposited with the charge negated
+                CK(with_real(c, [&](auto z) -> cudaError_t {
+                    using T = decltype(z);
+                    const SortArrays<T> b = slab_arrays<T>(*slab, s);
+                    if (d3) {
+                        DevSpecies3<T> v{};
+                        v.cell = b.cell;
+                        v.ox = b.f[0], v.oy = b.f[1], v.oz = b.f[2], v.w = b.f[9];
+                        v.q = (T)(-c->cfg.sp[s].q);
+                        v.n = b.n;
+                        return launch_rho3<T>(v, (int)m, mesh3<T>(c), static_cast<T *>(c->rho_bg), st);
+                    }
+                    DevSpecies<T> v{};
+                    v.cell = b.cell;
+                    v.ox = b.f[0], v.oy = b.f[1], v.w = b.f[8];
+                    v.q = (T)(-c->cfg.sp[s].q);
+                    v.n = b.n;
+                    return launch_rho<T>(v, (int)m, mesh<T>(c), static_cast<T *>(c->rho_bg), st);
+                }));
+                c->launches += 1;
+            }
+        }
+    }
+    bool all = true;
+    for (int s = 0; s < c->cfg.nspecies; ++s) {
+        if (!sort[s]) {
+            all = false;
+            continue;
+        }
+        pic_status_t r = sort_species(c, s, st);
+        if (r != PIC_OK) return r;
+    }
+    if (all) c->since_sort = 0;
+    c->window += ncells;
+    return PIC_OK;
+}
+
+// the window's next move is due before the step from index n: the box lags
+// the light front (speed w_speed, leaving at step w_start) by ncells cells
+bool window_due(const Ctx *c, long long n) {
+    if (c->w_ncells <= 0 || n < c->w_start) return false;
+    const double front = std::floor((double)(n - c->w_start) * c->dt * c->w_speed / c->dx);
+    return (double)(c->window - c->w_window0 + c->w_ncells) <= front;
+}
+
+// steps from the current index to the next due move (>= 1 when none is due
+// now; LLONG_MAX with the window off)
+long long window_next(const Ctx *c) {
+    if (c->w_ncells <= 0) return LLONG_MAX;
+    const double need = (double)(c->window - c->w_window0 + c->w_ncells) * c->dx / (c->dt * c->w_speed);
+    long long n = c->w_start + (long long)std::ceil(need) - 2;
+    n = std::max(n, c->step + 1);
+    for (int k = 0; k < 64 && !window_due(c, n); ++k) ++n;
+    return n - c->step;
+}
+
+// the moves due before the current step, each with the oldest staged plasma
+pic_status_t window_catch_up(Ctx *c, cudaStream_t st) {
+    while (window_due(c, c->step)) {
+        Slab b;
+        const bool have = !c->inj_queue.empty();
+        if (have) {
+            b = c->inj_queue.front();
+            c->inj_queue.pop_front();
+            c->inj_spent.push_back(b.mem);
+        }
+        pic_status_t r = window_move(c, c->w_ncells, have ? &b : nullptr, st);
+        if (r != PIC_OK) return r;
+    }
     return PIC_OK;
 }
 
@@ -788,6 +1158,13 @@ void pic_destroy(void *ctx) {
     cudaFree(c->laser_prof);
     cudaFree(c->hist);
     if (c->ovf_alert) cudaFreeHost(const_cast<int *>(c->ovf_alert));
+    for (auto &b : c->inj_queue) cudaFree(b.mem);
+    for (void *m : c->inj_spent) cudaFree(m);
+    if (c->live_host) {
+        cudaFreeHost(const_cast<long long *>(c->live_host));
+        for (int s = 0; s < PIC_MAX_SPECIES; ++s)
+            if (c->live_ev[s]) cudaEventDestroy(c->live_ev[s]);
+    }
     drop_step_graphs(c);
     if (c->gstream) cudaStreamDestroy(c->gstream);
     for (int k = 0; k < 2; ++k)
@@ -1122,6 +1499,7 @@ pic_status_t pic_push_deposit(void *ctx, void *stream) {
         for (int s = 0; s < c->cfg.nspecies; ++s) {
             int ovf;
             int64_t span;
+            refresh_live(c, s);
             if (c->cfg.sp[s].mobile && !bin_plan(c, s, &ovf, &span)) fits = false;
         }
         for (int s = 0; s < c->cfg.nspecies; ++s) {
@@ -1150,6 +1528,7 @@ pic_status_t pic_push_deposit(void *ctx, void *stream) {
                     b.id = o.id;
                     b.cnt_in = c->bin_cnt[s][c->cur[s]];
                     b.cnt_out = c->bin_cnt[s][to];
+                    b.txo = c->bin_txo[s];
                 }
             }
             return launch_step_fused3<T>(P, c->tmapEB, bin, S(stream));
@@ -1331,10 +1710,14 @@ pic_status_t pic_step(void *ctx, int nsteps, void *stream) {
     const bool graphs = c->graph_max > 0 && !c->binned;
     int k = 0;
     while (k < nsteps) {
-        pic_status_t r = PIC_OK;
+        // co-moving window: the moves due before this step, then stretches
+        // that end where the next one is due
+        pic_status_t r = window_catch_up(c, S(stream));
+        if (r != PIC_OK) return r;
         if (c->since_sort >= c->cfg.sort_every) r = pic_sort(c, stream);
         if (r != PIC_OK) return r;
         int len = std::min(nsteps - k, c->cfg.sort_every - c->since_sort);
+        len = (int)std::min<long long>(len, window_next(c));
         if (graphs && len >= 2) {
             len = std::min(len, c->graph_max);
             r = graph_steps(c, len, stream);
@@ -1488,84 +1871,79 @@ pic_status_t pic_shift_window(void *ctx, int ncells, const pic_particles_t *inje
     if (ncells < 1 || ncells > c->cfg.nx - 8) return fail(c, PIC_ERR_ARG, "ncells must be in [1, nx - 8]");
     if (c->pending_deposit) return fail(c, PIC_ERR_STATE, "a move is waiting for pic_deposit");
     cudaStream_t st = S(stream);
-    const size_t rows = c->bnd_n;  // mesh rows of one component
-    // the injection is appended after the last slot of the compact layout
-    for (int s = 0; s < c->cfg.nspecies; ++s)
-        if (c->sp_binned[s]) {
-            pic_status_t r = sort_species(c, s, st, true);
+    ensure_live(c);
+    pic_status_t r = free_spent(c, st);
+    if (r != PIC_OK) return r;
+    if (inject) {
+        // species that take the compact path append after their slots: the
+        // plasma must fit the capacity (checked before anything changes)
+        for (int s = 0; s < c->cfg.nspecies; ++s) {
+            if (inject[s].n < 0) return fail(c, PIC_ERR_ARG, "negative injection count");
+            const bool rotate = c->dim == 3 && c->sp_binned[s] && ncells % c->tg3.TX == 0;
+            if (rotate || inject[s].n == 0) continue;
+            if (c->sp_binned[s]) {
+                r = sort_species(c, s, st, true);
+                if (r != PIC_OK) return r;
+            }
+            int32_t cur = 0;
+            r = read_count(c, s, st, &cur);
             if (r != PIC_OK) return r;
-        }
-    // inject counts fit?
-    int32_t cur[PIC_MAX_SPECIES] = {};
-    for (int s = 0; s < c->cfg.nspecies; ++s) {
-        pic_status_t r = read_count(c, s, st, &cur[s]);
-        if (r != PIC_OK) return r;
-        const int64_t m = inject ? inject[s].n : 0;
-        if (m < 0) return fail(c, PIC_ERR_ARG, "negative injection count");
-        if (cur[s] + m > c->cfg.sp[s].capacity) return fail(c, PIC_ERR_OVERFLOW, "injection exceeds the capacity");
-    }
-    CK(with_real(c, [&](auto z) -> cudaError_t {
-        using T = decltype(z);
-        T *EB = static_cast<T *>(c->EB), *J = static_cast<T *>(c->J);
-        cudaError_t e = launch_ghost_from_column<T>(EB + 4 * c->plane, EB + 5 * c->plane, static_cast<T *>(c->bnd),
-                                                    rows, c->ld, ncells, st);
-        if (e != cudaSuccess) return e;
-        T *planes[10];
-        for (int k = 0; k < 6; ++k) planes[k] = EB + k * c->plane;
-        for (int k = 0; k < 3; ++k) planes[6 + k] = J + k * c->plane;
-        planes[9] = static_cast<T *>(c->rho_bg);
-        T *tmp = static_cast<T *>(c->stage);  // at least plane reals
-        for (int k = 0; k < 10; ++k) {
-            e = cudaMemcpyAsync(tmp, planes[k], c->plane * sizeof(T), cudaMemcpyDeviceToDevice, st);
-            if (e != cudaSuccess) return e;
-            e = launch_shift_rows<T>(tmp, planes[k], rows, c->cfg.nx, c->ld, ncells, st);
-            if (e != cudaSuccess) return e;
-        }
-        return cudaSuccess;
-    }));
-    c->launches += 11;
-    for (int s = 0; s < c->cfg.nspecies; ++s) {
-        CK(launch_shift_cells(c->buf[s][c->cur[s]].cell, c->n_dev + s, c->n_upper[s], ncells, c->dim == 3, st));
-        c->launches += 1;
-    }
-    for (int s = 0; s < c->cfg.nspecies; ++s) {
-        if (!inject || inject[s].n == 0) continue;
-        const int64_t base = cur[s];  // the slot count (removed particles stay until the sort)
-        pic_status_t r = upload_particles<float>(c, s, &inject[s], base, st);
-        if (r != PIC_OK) return r;
-        if (c->has_background) {
-            // the injected plasma brings its immobile ions: rho_bg -= rho(injected)
-            const int32_t m = (int32_t)inject[s].n;
-            CK(cudaMemcpyAsync(c->n_dev + PIC_MAX_SPECIES, &m, sizeof(int32_t), cudaMemcpyHostToDevice, st));
-            CK(cudaMemsetAsync(c->rho, 0, c->plane * c->rb, st));
-            CK(with_real(c, [&](auto z) -> cudaError_t {
-                using T = decltype(z);
-                cudaError_t e;
-                if (c->dim == 3) {
-                    DevSpecies3<T> v = dev_species3<T>(c, s, c->cur[s]);
-                    v.cell += base; v.ox += base; v.oy += base; v.oz += base; v.w += base;
-                    v.n = c->n_dev + PIC_MAX_SPECIES;
-                    e = launch_rho3<T>(v, m, mesh3<T>(c), static_cast<T *>(c->rho), st);
-                } else {
-                    DevSpecies<T> v = dev_species<T>(c, s, c->cur[s]);
-                    v.cell += base; v.ox += base; v.oy += base; v.w += base;
-                    v.n = c->n_dev + PIC_MAX_SPECIES;
-                    e = launch_rho<T>(v, m, mesh<T>(c), static_cast<T *>(c->rho), st);
-                }
-                if (e != cudaSuccess) return e;
-                return launch_subtract<T>(static_cast<T *>(c->rho_bg), static_cast<const T *>(c->rho), c->plane, st);
-            }));
-            c->launches += 2;
-            CK(cudaStreamSynchronize(st));  // the scratch count is reused by the sort
+            if (cur + inject[s].n > c->cfg.sp[s].capacity)
+                return fail(c, PIC_ERR_OVERFLOW, "injection exceeds the capacity");
         }
     }
-    for (int s = 0; s < c->cfg.nspecies; ++s) {
-        pic_status_t r = sort_species(c, s, st);
+    Slab b;
+    if (inject) {
+        r = stage_slab(c, inject, &b, st);
         if (r != PIC_OK) return r;
     }
-    c->since_sort = 0;
-    c->window += ncells;
+    r = window_move(c, ncells, inject ? &b : nullptr, st);
+    if (b.mem) {
+        cudaStreamSynchronize(st);
+        cudaFree(b.mem);
+    }
+    if (r != PIC_OK) return r;
     return check_flags(c, st);
+}
+
+pic_status_t pic_set_window(void *ctx, int ncells, int64_t start_step, double speed) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
+    if (ncells == 0) {
+        c->w_ncells = 0;
+        return PIC_OK;
+    }
+    if (c->cfg.bc_x != PIC_BC_OPEN) return fail(c, PIC_ERR_ARG, "the moving window needs open x boundaries");
+    if (ncells < 1 || ncells > c->cfg.nx - 8) return fail(c, PIC_ERR_ARG, "ncells must be 0 or in [1, nx - 8]");
+    if (!(speed > 0.0) || !std::isfinite(speed)) return fail(c, PIC_ERR_ARG, "speed must be positive and finite");
+    ensure_live(c);
+    c->w_ncells = ncells;
+    c->w_start = start_step;
+    c->w_speed = speed;
+    c->w_window0 = c->window;
+    return PIC_OK;
+}
+
+pic_status_t pic_stage_injection(void *ctx, const pic_particles_t *inject, void *stream) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, PIC_ERR_ARG, "null context");
+    if (!inject) return fail(c, PIC_ERR_ARG, "null injection");
+    if (c->cfg.bc_x != PIC_BC_OPEN) return fail(c, PIC_ERR_ARG, "the moving window needs open x boundaries");
+    cudaStream_t st = S(stream);
+    pic_status_t r = free_spent(c, st);
+    if (r != PIC_OK) return r;
+    Slab b;
+    r = stage_slab(c, inject, &b, st);
+    if (r != PIC_OK) return r;
+    c->inj_queue.push_back(b);
+    return PIC_OK;
+}
+
+pic_status_t pic_staged_injections(void *ctx, int64_t *count) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c || !count) return fail(c, PIC_ERR_ARG, "null argument");
+    *count = (int64_t)c->inj_queue.size();
+    return PIC_OK;
 }
 
 pic_status_t pic_get_window(void *ctx, int64_t *offset) {

@@ -23,6 +23,7 @@
 #define PIC_EF_TIMEOUT 4u
 #define PIC_EF_RANGE 8u
 #define PIC_EF_BINS 16u   // binned layout: a tile range and the overflow range were full
+#define PIC_EF_CAP 32u    // a window move's plasma did not fit the species capacity
 
 #define PIC_MAXSP 4
 #define PIC_HALO 4     // least window margin around a tile along x, in cells

@@ -101,7 +101,18 @@ struct Bin3 {
     int32_t *id;
     const int32_t *cnt_in;  // [4 nr] counters of the source buffer
     int32_t *cnt_out;       // [4 nr] of the destination buffer, front / split / back zero on entry
+    int txo;                // tile-column relabelling of the co-moving window (bin_rot_x)
 };
+
+// The co-moving window moves the box by whole tile columns without moving a
+// particle between ranges: after moves of kt columns in total since the last
+// sort, tile column tx uses the ranges of column (tx + txo) mod ntx, txo = kt
+// mod ntx (the columns that left the box lend their ranges to the uncovered
+// ones).  txo in [0, ntx).
+__host__ __device__ __forceinline__ int bin_rot_x(int tx, int ntx, int txo) {
+    const int r = tx + txo;
+    return r >= ntx ? r - ntx : r;
+}
 
 struct BinRange {
     int beg, front, split, len;

@@ -82,6 +82,16 @@ cudaError_t launch_field_update3(const MeshParams3<R> &m, R *bnd, const double *
 void laser_profile3(const LaserParams &L, int ny, int nz, double dz, double *host);
 
 // k_sort.cu
+// the arrays of one particle buffer a sort (or a window move) reads or
+// writes: the cell word, the reals of a record (2D3V: ox oy ux uy uz sx sy sz
+// w; 3D3V: ox oy oz ux uy uz sx sy sz w) and the id; n the device count
+template <typename R>
+struct SortArrays {
+    uint32_t *cell;
+    R *f[10];
+    int32_t *id;
+    const int32_t *n;
+};
 struct SortScratch {
     int32_t *cell_count, *cell_off;  // [ntiles * TX * TY]
     int32_t *tile_R, *tile_total;    // [ntiles], tile_total [ntiles + 1]
@@ -136,6 +146,38 @@ cudaError_t launch_shift_rows(const R *src, R *dst, size_t rows, int nx, int ld,
 template <typename R>
 cudaError_t launch_ghost_from_column(const R *by, const R *bz, R *bnd, size_t rows, int ld, int n, cudaStream_t st);
 cudaError_t launch_shift_cells(uint32_t *cell, const int32_t *n_src, int n_upper, int ncells, bool d3,
+                               cudaStream_t st);
+// co-moving window on the stepping path: every mesh component moved n
+// columns toward x_min in place (rows of ld reals, nx used), the left
+// boundary values taken from the old column n - 1 of plane[by], plane[bz]
+template <typename R>
+struct WindowRows {
+    R *plane[10];
+    int nplanes;
+    int by, bz;  // indices of By, Bz in plane[] (-1: none)
+    R *bnd;      // [2][rows] By(-1/2), Bz(-1/2)
+    size_t rows;
+    int nx, ld, n;
+};
+template <typename R>
+cudaError_t launch_window_rows(const WindowRows<R> &a, cudaStream_t st);
+// binned layout: the ranges of the last kt tile columns emptied (txo: the
+// column relabelling after the move)
+cudaError_t launch_window_vacate(int32_t *cnt, int nr, int ntx, int nyz, int kt, int txo, cudaStream_t st);
+// binned layout: staged particles (*src.n of them, at most m_upper) into their
+// tiles' ranges of the buffer dst, range counters cnt
+template <typename R>
+cudaError_t launch_window_inject3(const SortArrays<R> &src, int m_upper, const SortArrays<R> &dst,
+                                  const int32_t *tile_start, int32_t *cnt, const TileGeom3 &t, int txo,
+                                  unsigned *err, cudaStream_t st);
+// compact layout: staged particles appended after the *n_dst slots in use
+// (PIC_EF_CAP and nothing appended when they do not fit cap)
+template <typename R>
+cudaError_t launch_window_append(const SortArrays<R> &src, int m_upper, const SortArrays<R> &dst, int32_t *n_dst,
+                                 int cap, bool d3, unsigned *err, cudaStream_t st);
+// live particles after a sort into host-mapped memory (split: the binned
+// layout's tile counts, nullptr for the compact layout's *n_dev)
+cudaError_t launch_live_sample(const int32_t *n_dev, const int32_t *split, int nt, volatile long long *out,
                                cudaStream_t st);
 template <typename A, typename B>
 cudaError_t launch_convert(const A *src, B *dst, size_t n, cudaStream_t st);

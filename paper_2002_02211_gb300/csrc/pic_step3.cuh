@@ -44,21 +44,23 @@ struct SmemMesh3T {
     }
 };
 
+// range of the tile of cell (ix, iy, iz), tile columns relabelled by txo
+// (bin_rot_x; txo = 0: the tile's own index)
 template <int TX, int TY, int TZ>
-__device__ __forceinline__ int tile_of3(const TileGeom3 &t, int ix, int iy, int iz) {
-    return ((iz / TZ) * t.nty + iy / TY) * t.ntx + ix / TX;
+__device__ __forceinline__ int tile_of3(const TileGeom3 &t, int ix, int iy, int iz, int txo = 0) {
+    return ((iz / TZ) * t.nty + iy / TY) * t.ntx + bin_rot_x(ix / TX, t.ntx, txo);
 }
 
 // destination range of a particle that survived the move (-1 and PIC_EF_RANGE
 // for a cell outside the mesh, which only a corrupt input cell can produce)
 template <int TX, int TY, int TZ, typename R>
 __device__ __forceinline__ int bin_dest3(const MeshParams3<R> &m, const TileGeom3 &t, int ix, int iy, int iz,
-                                         unsigned *err) {
+                                         unsigned *err, int txo) {
     if (ix < 0 || ix >= m.nx || iy < 0 || iy >= m.ny || iz < 0 || iz >= m.nz) {
         atomicOr(err, PIC_EF_RANGE);
         return -1;
     }
-    return tile_of3<TX, TY, TZ>(t, ix, iy, iz);
+    return tile_of3<TX, TY, TZ>(t, ix, iy, iz, txo);
 }
 
 // Eq. (4) sums of the particles in the window [dlo, dhi) MeV
