@@ -94,6 +94,8 @@ def parse(argv=None):
                     default="config2")
     ap.add_argument("--prec-steps", type=int, default=2000, help="precision: steps of the FP32 and FP64 runs")
     ap.add_argument("--prec-cut-steps", type=int, default=200, help="precision: steps of the cut against the oracle")
+    ap.add_argument("--prec-static", action="store_true",
+                    help="precision: the box stays put (default: it co-moves with the pulse, as --workload window)")
     ap.add_argument("--adj-steps", type=int, default=1000, help="config5: run length of the adjoint")
     ap.add_argument("--checkpoint", type=int, default=50, help="config5: checkpoint interval")
     ap.add_argument("--scan-runs", type=int, default=256, help="config4: runs of the scan")
@@ -107,12 +109,14 @@ def parse(argv=None):
     ap.add_argument("--ny", type=int, default=0, help="smaller ny for profiling captures")
     ap.add_argument("--nz", type=int, default=0, help="smaller nz (3D3V) for profiling captures")
     ap.add_argument("--precision", type=int, choices=[32, 64], default=32)
-    ap.add_argument("--e2e-steps", type=int, default=4)
+    ap.add_argument("--e2e-steps", type=int, default=16)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=10, help="timed steps of the FP64 line (0: skip)")
     ap.add_argument("--window-cells", type=int, default=16,
                     help="window: cells a move of the co-moving window (a multiple of the tile width)")
+    ap.add_argument("--window-steps", type=int, default=200,
+                    help="config2: timed steps of the co-moving window leg (0: skip)")
     ap.add_argument("--window-at", type=float, default=0.75,
                     help="window: the box starts to move when the envelope peak reaches this fraction of nx")
     ap.add_argument("--start-step", type=int, default=-1,
@@ -553,22 +557,45 @@ def main_ours(args):
         d2h = len(parts) * 7 * 8
         barrier(world)
         torch.cuda.synchronize(dev)
+        phase = []  # per step: events before the upload, after it, after the step
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(stream)
             for s, (n, pp) in enumerate(ptrs):
                 sim.set_particles_raw(s, n, pp)
+            ev[1].record(stream)
             sim.push_deposit()
             sim.field_update()
+            ev[2].record(stream)
             for s in range(len(parts)):
                 sim.polarization(s)
+            phase.append(ev)
         torch.cuda.synchronize(dev)
         te = time.perf_counter() - t0
+        upload_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in phase]))
+        step_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in phase]))
+        # the tile sort inside the upload, timed alone on the uploaded state
+        # (pic_sort re-sorts the same particles), so the host link's share
+        # of the upload is the rest
+        sa, sb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sa.record(stream)
+        sim.sort()
+        sb.record(stream)
+        torch.cuda.synchronize(dev)
+        sort_alone = sa.elapsed_time(sb)
         te, eu = combine(te, n_particles * args.e2e_steps, world, dev)
         e2e = {"value": eu / te, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "steps": args.e2e_steps,
+               "steps": args.e2e_steps, "ms_per_step": te * 1e3 / args.e2e_steps,
+               "breakdown_ms": {"upload": upload_ms, "of_which_sort": sort_alone,
+                                "of_which_h2d_and_pack": upload_ms - sort_alone,
+                                "h2d_GBps": h2d / ((upload_ms - sort_alone) * 1e-3) / 1e9
+                                if upload_ms > sort_alone else None,
+                                "step": step_ms},
                "what": "per step: pic_set_particles of every species from pinned host memory "
                        "(H2D + tile sort), pic_push_deposit, pic_field_update, pic_polarization "
-                       "of every species (D2H)"}
+                       "of every species (D2H); breakdown from CUDA events around the upload and "
+                       "the step, the sort timed alone after the last upload"}
 
     sim.close()
 
@@ -599,6 +626,12 @@ def main_ours(args):
                 "bound": "alu: the FP64 pipe, 75% of its peak busy at 4% of DRAM bandwidth "
                          "(profiles/k_step_fused3-fp64_3d3v-512x256x32.md)"}
 
+    # config 2 with the co-moving window on (Sec. 2), timed from the step it starts
+    win = None
+    if dim == 3 and bins and args.window_steps > 0 and not (args.ny or args.nz):
+        win = window_leg(pic, wl, args, stream, dev, world, args.window_steps, bins, args.sort_every)
+        win.pop("particles", None)
+
     cpu = None
     study = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -623,7 +656,7 @@ def main_ours(args):
                            "start_step": start_step,
                            "parallelism": f"replicas x{world}"},
                 "timing": timing, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "gpu_launches": launches, "fp64": fp64, "precision_study": study,
+                "gpu_launches": launches, "fp64": fp64, "precision_study": study, "window": win,
                 "diagnostics": {"step": diag_step,
                                 "P": {sp.name: [round(v, 6) for v in d["P"]] for sp, d in zip(wl.species, diag)},
                                 "ekin_mean_mev": {sp.name: d["ekin_mean"] for sp, d in zip(wl.species, diag)}}}
@@ -898,10 +931,13 @@ def main_latency(args):
 # moments compared every 10 steps), and a cut of it with the pulse in the
 # plasma run beside the FP64 oracle
 # ---------------------------------------------------------------------------
-def _moments_run(pic, wl, parts, precision, steps, every, stream, bins):
-    """Eq. (4) moments of species 0 every `every` steps of one run."""
+def _moments_run(pic, wl, parts, precision, steps, every, stream, bins, window=None):
+    """Eq. (4) moments of species 0 every `every` steps of one run;
+    window = (cells a move, fraction of nx where the envelope peak starts it)
+    runs it co-moving."""
     import torch
-    cfg = pic.config_from_workload(wl, sort_every=DEFAULT_REBIN_EVERY, precision=precision, bins=bins)
+    cfg = pic.config_from_workload(wl, sort_every=DEFAULT_REBIN_EVERY, precision=precision, bins=bins,
+                                   window_cells=window[0] if window else 0)
     rows = []
     with pic.Simulation(cfg, stream=stream) as sim:
         for s, d in enumerate(parts):
@@ -909,6 +945,8 @@ def _moments_run(pic, wl, parts, precision, steps, every, stream, bins):
         if wl.neutralizing_background:
             sim.capture_background()
         sim.set_diagnostics(every)
+        if window:
+            stage_window(sim, wl, parts, window[0], window_start(wl, sim.grid()[0], window[1]), steps)
         t0 = time.perf_counter()
         done = 0
         while done < steps:
@@ -997,8 +1035,9 @@ def main_precision(args):
     parts = W.generate_particles(wl)
     every = 10
     runs = {}
+    window = None if args.prec_static else (args.window_cells, args.window_at)
     for prec in (32, 64):
-        runs[prec] = _moments_run(pic, wl, parts, prec, args.prec_steps, every, stream, DEFAULT_BINS)
+        runs[prec] = _moments_run(pic, wl, parts, prec, args.prec_steps, every, stream, DEFAULT_BINS, window)
     r32, r64 = runs[32][0], runs[64][0]
     by_step = {}
     for (s32, p32, m32, v32, c32), (s64, p64, m64, v64, c64) in zip(r32, r64):
@@ -1012,6 +1051,11 @@ def main_precision(args):
     cut = _cut_against_oracle(pic, oracle, args.prec_cut_steps, stream)
     line = {"metric": "precision study: FP32 against FP64 on the GPU, and the GPU against the FP64 oracle",
             "workload": wl.name, "steps": args.prec_steps, "diag_every": every,
+            "co_moving_window": None if window is None else
+            {"cells_per_move": window[0], "speed_c": 1.0,
+             "start_step": window_start(wl, wl.cfl / math.sqrt(sum((1 / (d * 2 * math.pi)) ** 2 for d in
+                                                                  (wl.dx_lambda, wl.dy_lambda, wl.dz_lambda))),
+                                        window[1])},
             "fp32_seconds": round(runs[32][1], 2), "fp64_seconds": round(runs[64][1], 2),
             "fp32_vs_fp64": {"max_over_run": {"P_abs": max(by_step[s]["dP"] for s in steps),
                                               "ekin_mean_rel": max(by_step[s]["dmean"] for s in steps),
@@ -1028,40 +1072,13 @@ def main_precision(args):
 # ---------------------------------------------------------------------------
 # window: config 2 with the co-moving window on the stepping path
 # ---------------------------------------------------------------------------
-def main_window(args):
-    """Config 2 run the way Sec. 2 runs it: once the envelope peak reaches
-    --window-at of the box, the box follows it at the speed of light, pic_step
-    moving it --window-cells cells at a time (in the binned layout by
-    relabelling whole tile columns) and taking in the plasma staged for each
-    move.  Timed from the step the window starts, every step a pic_step(1)
-    call bracketed by CUDA events, so the cost of a move is the difference
-    between the steps that make one and the steps that do not."""
-    import torch
-
-    import paper_2002_02211_gb300 as pic
-
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    init_dist(world, "nccl")
-    dev = torch.device("cuda", local)
-    wl = workload("config2", args.ny, args.nz)
-    bins = None if args.compact else (tuple(args.bins) if args.bins else DEFAULT_BINS)
-    sort_every = args.sort_every if args.sort_every > 0 else (DEFAULT_REBIN_EVERY if bins else DEFAULT_SORT_EVERY[3])
-    ncells = args.window_cells
-    parts = W.generate_particles(wl)
-    n_particles = sum(len(p["ix"]) for p in parts)
-    stream = torch.cuda.Stream(device=dev)
-    cfg = pic.config_from_workload(wl, sort_every=sort_every, tile=args.tile, bins=bins)
-    sim = pic.Simulation(cfg, stream=stream)
-    for s, d in enumerate(parts):
-        sim.set_particles(s, d)
-    sim.capture_background()
-    sim.set_diagnostics(args.diag_every)
+def stage_window(sim, wl, parts, ncells, w0, end_step):
+    """Turns the co-moving window on from step w0 (speed c, ncells cells a
+    move) and stages the plasma of every move before step end_step: four
+    seeded draws of the uncovered columns staged in turn, ids continuing
+    after the initial particles'.  Returns the plasmas staged."""
     dt, dx = sim.grid()[:2]
-    w0 = max(window_start(wl, dt, args.window_at), args.warmup)
-    sim.set_window(ncells, w0, 1.0)
-    # the plasma of every move: four distinct draws staged in turn, ids continuing
-    n_moves = int(math.ceil(args.steps * dt / dx / ncells)) + 2
+    n_moves = max(0, int(math.ceil((end_step - w0) * dt / dx / ncells))) + 2
     draws = [W.injection_particles(wl, ncells, seed=900 + k) for k in range(min(4, n_moves))]
     next_id = [len(p["ix"]) for p in parts]
     for k in range(n_moves):
@@ -1072,12 +1089,38 @@ def main_window(args):
             next_id[s] += len(d["ix"])
             slab.append(e)
         sim.stage_injection(slab)
+    sim.set_window(ncells, w0, 1.0)
+    return n_moves
+
+
+def window_leg(pic, wl, args, stream, dev, world, steps, bins, sort_every):
+    """Config 2 run the way Sec. 2 runs it: once the envelope peak reaches
+    --window-at of the box, the box follows it at the speed of light, pic_step
+    moving it --window-cells cells at a time (in the binned layout by
+    relabelling whole tile columns) and taking in the plasma staged for each
+    move.  Timed from the step the window starts, every step a pic_step(1)
+    call bracketed by CUDA events, so the cost of a move is the difference
+    between the steps that make one and the steps that do not."""
+    import torch
+
+    ncells = args.window_cells
+    parts = W.generate_particles(wl)
+    n_particles = sum(len(p["ix"]) for p in parts)
+    cfg = pic.config_from_workload(wl, sort_every=sort_every, tile=args.tile, bins=bins, window_cells=ncells)
+    sim = pic.Simulation(cfg, stream=stream)
+    for s, d in enumerate(parts):
+        sim.set_particles(s, d)
+    sim.capture_background()
+    sim.set_diagnostics(args.diag_every)
+    dt = sim.grid()[0]
+    w0 = max(window_start(wl, dt, args.window_at), args.warmup)
+    n_moves = stage_window(sim, wl, parts, ncells, w0, w0 + steps)
     # untimed: the run up to the step the window starts (its last `warmup`
     # steps are the warm-up)
     sim.step(w0)
     sim.sync()
 
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(int(dev.index or 0))
     launches0 = sim.launch_count()
     barrier(world)
     torch.cuda.synchronize(dev)
@@ -1085,7 +1128,7 @@ def main_window(args):
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     evs, moved = [], []
     start.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         w = sim.window()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
@@ -1103,33 +1146,53 @@ def main_window(args):
     elapsed = start.elapsed_time(end) * 1e-3
     step_ms = np.array([a.elapsed_time(b) for a, b in evs])
     moved = np.array(moved)
-    left = sim.staged_injections()
-    shift = sim.window()
+    out = {"left": sim.staged_injections(), "shift": sim.window(), "binned": sim.binned(0) if bins else False}
     sim.close()
-    tmax, units = combine(elapsed, n_particles * args.steps, world, dev)
+    tmax, units = combine(elapsed, n_particles * steps, world, dev)
+    plain = float(step_ms[~moved].mean()) if (~moved).any() else None
+    with_move = float(step_ms[moved].mean()) if moved.any() else None
+    return {"value": units / tmax, "unit": UNIT, "ms_per_step": tmax * 1e3 / steps, "steps": steps,
+            "timed_steps": [w0, w0 + steps], "particles": n_particles,
+            "window": {"cells_per_move": ncells, "speed_c": 1.0, "start_step": w0,
+                       "peak_at_cell": round(args.window_at * wl.nx), "moves_timed": int(moved.sum()),
+                       "cells_moved_total": out["shift"], "step_ms_without_move": plain,
+                       "step_ms_with_move": with_move,
+                       "move_ms": (with_move - plain) if plain is not None and with_move is not None else None,
+                       "plasma_staged": n_moves, "plasma_left": out["left"], "binned_at_end": out["binned"]},
+            "clocks": clk, "gpu_launches": launches,
+            "diagnostics": {"step": diag_step,
+                            "P": {sp.name: [round(v, 6) for v in d["P"]] for sp, d in zip(wl.species, diag)}},
+            "note": "value counts the particles at the start; a move removes and injects equal plasma volumes"}
+
+
+def main_window(args):
+    """Config 2 co-moving (window_leg) as its own JSON line."""
+    import torch
+
+    import paper_2002_02211_gb300 as pic
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    init_dist(world, "nccl")
+    dev = torch.device("cuda", local)
+    wl = workload("config2", args.ny, args.nz)
+    bins = None if args.compact else (tuple(args.bins) if args.bins else DEFAULT_BINS)
+    sort_every = args.sort_every if args.sort_every > 0 else (DEFAULT_REBIN_EVERY if bins else DEFAULT_SORT_EVERY[3])
+    stream = torch.cuda.Stream(device=dev)
+    leg = window_leg(pic, wl, args, stream, dev, world, args.steps, bins, sort_every)
     if rank == 0:
-        plain = float(step_ms[~moved].mean()) if (~moved).any() else None
-        with_move = float(step_ms[moved].mean()) if moved.any() else None
-        line = {"metric": METRIC, "value": units / tmax, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": tmax * 1e3 / args.steps, "higher_is_better": True,
+        line = {"metric": METRIC, "value": leg["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": leg["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": wl.name + "-comoving", "cells": [wl.nx, wl.ny, wl.nz],
-                           "particles": n_particles, "sort_every": sort_every,
+                           "particles": leg["particles"], "sort_every": sort_every,
                            "layout": ("binned (headroom %d%%, at least %d spare slots per tile)" % tuple(bins))
                                      if bins else "compact",
-                           "window": {"cells_per_move": ncells, "speed_c": 1.0, "start_step": w0,
-                                      "peak_at_cell": round(args.window_at * wl.nx)},
-                           "l2": "inputs larger than L2", "start_step": w0,
+                           "l2": "inputs larger than L2", "start_step": leg["window"]["start_step"],
                            "parallelism": f"replicas x{world}"},
-                "window": {"moves_timed": int(moved.sum()), "cells_moved_total": shift,
-                           "step_ms_without_move": plain, "step_ms_with_move": with_move,
-                           "move_ms": (with_move - plain) if plain is not None and with_move is not None else None,
-                           "plasma_staged": n_moves, "plasma_left": left,
-                           "particles_note": "value counts the particles at the start; moves remove and "
-                                             "inject equal plasma volumes"},
-                "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": clk, "gpu_launches": launches,
-                "diagnostics": {"step": diag_step,
-                                "P": {sp.name: [round(v, 6) for v in d["P"]] for sp, d in zip(wl.species, diag)}}}
+                "window": leg["window"], "timing": {"timed_steps": leg["timed_steps"]},
+                "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": leg["clocks"],
+                "gpu_launches": leg["gpu_launches"], "diagnostics": leg["diagnostics"], "note": leg["note"]}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

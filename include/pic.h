@@ -365,6 +365,12 @@ pic_status_t pic_stage_injection(void *ctx, const pic_particles_t *inject, void 
 /* Staged plasmas not yet consumed by a move. */
 pic_status_t pic_staged_injections(void *ctx, int64_t *count);
 
+/* *binned = 1 when species s is in the binned 3D3V layout now, else 0 (the
+ * compact layout: the binned layout is off, the species is immobile, or its
+ * capacity cannot hold the binned ranges of its live-particle bound, which
+ * counts every particle staged into it since the last completed count). */
+pic_status_t pic_get_layout(void *ctx, int species, int *binned);
+
 /* Cells the window has moved since pic_create. */
 pic_status_t pic_get_window(void *ctx, int64_t *offset_cells);
 

@@ -137,6 +137,7 @@ _SIGS = {
     "pic_set_window": [C.c_void_p, C.c_int, C.c_int64, C.c_double],
     "pic_stage_injection": [C.c_void_p, C.c_void_p, C.c_void_p],
     "pic_staged_injections": [C.c_void_p, C.POINTER(C.c_int64)],
+    "pic_get_layout": [C.c_void_p, C.c_int, C.POINTER(C.c_int)],
     "pic_set_diagnostics": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
     "pic_get_diagnostics": [C.c_void_p, C.c_void_p, C.POINTER(C.c_int64), C.c_void_p],
     "pic_moments_noalloc": [C.c_int64] + [C.c_void_p] * 8 + [C.c_double, C.c_double, C.c_double,
@@ -197,12 +198,15 @@ def bin_capacity(n: int, ntiles: int, headroom_pct: int, min_extra: int) -> int:
 
 
 def config_from_workload(wl, capacity_factor: float = 1.0, sort_every: int = 0, tile=None,
-                         precision: int = 32, bins=None):
+                         precision: int = 32, bins=None, window_cells: int = 0):
     """pic_config_t for a workload description (nx, ny, dx_lambda, ..., species;
     dim, nz, dz_lambda for 3D3V).  tile: (tx, ty) in 2D3V, (tx, ty, tz) in
     3D3V, None for the library's choice.  bins: (headroom_pct, min_extra)
     turns on the binned 3D3V layout, with the mobile species' capacities
-    grown to fit it."""
+    grown to fit it.  window_cells: cells a move of the co-moving window
+    takes in; the capacities then hold two moves' plasma more (the particle
+    count may exceed the initial one between moves, and the live-count bound
+    runs ahead of it until the device's count arrives)."""
     three = getattr(wl, "dim", 2) == 3
     cfg = pic_config_t()
     cfg.nx, cfg.ny = wl.nx, wl.ny
@@ -219,7 +223,8 @@ def config_from_workload(wl, capacity_factor: float = 1.0, sort_every: int = 0, 
     for s, sp in enumerate(wl.species):
         cfg.sp[s].q, cfg.sp[s].m, cfg.sp[s].a = sp.q, sp.m, sp.a
         cfg.sp[s].mobile = 1 if sp.mobile else 0
-        cfg.sp[s].capacity = int(math.ceil(sp.ppc * ncx * wl.ny * (wl.nz if three else 1) * capacity_factor))
+        cross = wl.ny * (wl.nz if three else 1)
+        cfg.sp[s].capacity = int(math.ceil(sp.ppc * (ncx * capacity_factor + 2 * window_cells) * cross))
     cfg.sort_every = sort_every
     tile = tuple(tile) if tile else (0, 0, 0)
     cfg.tile_x, cfg.tile_y = tile[0], tile[1]
@@ -529,6 +534,12 @@ class Simulation:
         arr, keep = self._inject_arr(inject)
         self._c(load().pic_stage_injection(self.h, arr, self._s))
         del keep
+
+    def binned(self, s):
+        """pic_get_layout: True when species s is in the binned 3D3V layout."""
+        v = C.c_int()
+        self._c(load().pic_get_layout(self.h, int(s), C.byref(v)))
+        return bool(v.value)
 
     def staged_injections(self):
         v = C.c_int64()

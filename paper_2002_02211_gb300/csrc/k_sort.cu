@@ -633,22 +633,23 @@ __global__ void k_window_count(int32_t *n_dst, const int32_t *m_src, int cap) {
     if (n <= cap) *n_dst = (int32_t)n;
 }
 
-// Live particles after a sort, into host-mapped memory: the sorted count of
-// the compact layout, or the sum of the tiles' counts (split counters) of the
-// binned one.  One block.
-__global__ void __launch_bounds__(1024) k_live_sample(const int32_t *n_dev, const int32_t *split, int nt,
-                                                      volatile long long *out) {
+// Live particles into host-mapped memory: the compact layout's count
+// (*n_dev), or the sum of the binned ranges' lengths (tile ranges and the
+// overflow range; removed particles still inside a segment count too, so it
+// is a bound).  One block.
+__global__ void __launch_bounds__(1024) k_live_sample(const int32_t *n_dev, const int32_t *tile_start,
+                                                      const int32_t *cnt, int nr, volatile long long *out) {
     __shared__ long long part[32];
     long long s = 0;
-    if (split)
-        for (int t = threadIdx.x; t < nt; t += blockDim.x) s += split[t];
+    if (tile_start)
+        for (int r = threadIdx.x; r < nr; r += blockDim.x) s += bin_range(tile_start, cnt, nr, r).len;
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
     if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
         long long tot = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += part[w];
-        *out = split ? tot : (long long)*n_dev;
+        *out = tile_start ? tot : (long long)*n_dev;
         __threadfence_system();
     }
 }
@@ -693,9 +694,9 @@ cudaError_t launch_window_append(const SortArrays<R> &src, int m_upper, const So
     return cudaGetLastError();
 }
 
-cudaError_t launch_live_sample(const int32_t *n_dev, const int32_t *split, int nt, volatile long long *out,
-                               cudaStream_t st) {
-    k_live_sample<<<1, 1024, 0, st>>>(n_dev, split, nt, out);
+cudaError_t launch_live_sample(const int32_t *n_dev, const int32_t *tile_start, const int32_t *cnt, int nr,
+                               volatile long long *out, cudaStream_t st) {
+    k_live_sample<<<1, 1024, 0, st>>>(n_dev, tile_start, cnt, nr, out);
     return cudaGetLastError();
 }
 

@@ -477,6 +477,20 @@ void add_live(Ctx *c, int s, int64_t m) {
     c->live_added[s] += m;
 }
 
+// the live count of species s into host-mapped memory (after a sort or a
+// window move; no-op until the window is used)
+pic_status_t live_sample(Ctx *c, int s, cudaStream_t st) {
+    if (!c->live_host) return PIC_OK;
+    const bool bin = c->sp_binned[s];
+    CK(launch_live_sample(c->n_dev + s, bin ? c->tile_start[s] : nullptr, c->bin_cnt[s][c->cur[s]],
+                          c->ntiles + 1, c->live_dev + s, st));
+    CK(cudaEventRecord(c->live_ev[s], st));
+    c->launches += 1;
+    c->live_pending[s] = true;
+    c->live_added[s] = 0;
+    return PIC_OK;
+}
+
 // No host synchronisation: the sorted slot count stays on the device.  In the
 // compact layout it only shrinks, so n_upper still bounds it; in the binned
 // layout n_upper becomes the host bound on the span of the ranges.
@@ -507,15 +521,6 @@ pic_status_t sort_species(Ctx *c, int s, cudaStream_t st, bool compact_only = fa
     c->launches += bin ? 7 : 6;  // rank, layout, three scan passes, scatter (, seal)
     c->cur[s] = to;
     c->bin_txo[s] = 0;
-    if (c->live_host) {
-        // the sorted live count: the compact count, or the binned tiles' counts
-        CK(launch_live_sample(c->n_dev + s, bin ? bins.cnt_to + c->ntiles + 1 : nullptr, c->ntiles,
-                              c->live_dev + s, st));
-        CK(cudaEventRecord(c->live_ev[s], st));
-        c->launches += 1;
-        c->live_pending[s] = true;
-        c->live_added[s] = 0;
-    }
     if (bin) {
         c->n_upper[s] = (int)span;
         const int want = (bins.ovf_cap + 255) / 256;
@@ -524,7 +529,7 @@ pic_status_t sort_species(Ctx *c, int s, cudaStream_t st, bool compact_only = fa
     else if (c->sp_binned[s])
         c->n_upper[s] = (int)std::min<int64_t>(c->n_upper[s], c->n_live[s]);
     c->sp_binned[s] = bin;
-    return PIC_OK;
+    return live_sample(c, s, st);
 }
 
 // every mobile species in the binned layout (the binned step's precondition)
@@ -883,8 +888,14 @@ pic_status_t window_move(Ctx *c, int ncells, const Slab *slab, cudaStream_t st) 
             }
             sort[s] = true;
         }
+        // n_live stays a bound at once; the sample of a binned species (after
+        // its plasma) tightens it when it completes
+        if (m > 0) add_live(c, s, m);
+        if (rotate) {
+            pic_status_t lr = live_sample(c, s, st);
+            if (lr != PIC_OK) return lr;
+        }
         if (m > 0) {
-            add_live(c, s, m);
             if (c->has_background) {
                 // the plasma brings its immobile ions: rho_bg -= rho(plasma),
                 // deposited with the charge negated
@@ -1936,6 +1947,14 @@ pic_status_t pic_stage_injection(void *ctx, const pic_particles_t *inject, void 
     r = stage_slab(c, inject, &b, st);
     if (r != PIC_OK) return r;
     c->inj_queue.push_back(b);
+    return PIC_OK;
+}
+
+pic_status_t pic_get_layout(void *ctx, int s, int *binned) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c || !binned) return fail(c, PIC_ERR_ARG, "null argument");
+    if (s < 0 || s >= c->cfg.nspecies) return fail(c, PIC_ERR_ARG, "species out of range");
+    *binned = c->sp_binned[s] ? 1 : 0;
     return PIC_OK;
 }
 

@@ -175,10 +175,10 @@ cudaError_t launch_window_inject3(const SortArrays<R> &src, int m_upper, const S
 template <typename R>
 cudaError_t launch_window_append(const SortArrays<R> &src, int m_upper, const SortArrays<R> &dst, int32_t *n_dst,
                                  int cap, bool d3, unsigned *err, cudaStream_t st);
-// live particles after a sort into host-mapped memory (split: the binned
-// layout's tile counts, nullptr for the compact layout's *n_dev)
-cudaError_t launch_live_sample(const int32_t *n_dev, const int32_t *split, int nt, volatile long long *out,
-                               cudaStream_t st);
+// live particles into host-mapped memory: *n_dev (tile_start == nullptr,
+// the compact layout) or the sum of the nr binned ranges' lengths
+cudaError_t launch_live_sample(const int32_t *n_dev, const int32_t *tile_start, const int32_t *cnt, int nr,
+                               volatile long long *out, cudaStream_t st);
 template <typename A, typename B>
 cudaError_t launch_convert(const A *src, B *dst, size_t n, cudaStream_t st);
 

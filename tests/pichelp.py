@@ -10,10 +10,10 @@ import workloads as W
 
 
 def make_pair(wl, fields=None, step=0, capacity_factor=1.0, sort_every=0, tile=None, parts=None,
-              precision=32, bins=None):
+              precision=32, bins=None, window_cells=0):
     parts = W.generate_particles(wl) if parts is None else parts
     cfg = pic.config_from_workload(wl, capacity_factor=capacity_factor, sort_every=sort_every, tile=tile,
-                                   precision=precision, bins=bins)
+                                   precision=precision, bins=bins, window_cells=window_cells)
     sim = pic.Simulation(cfg)
     for s, d in enumerate(parts):
         sim.set_particles(s, d)
@@ -119,3 +119,44 @@ def compare_fields(sim, orc, keys, tol, region=None, f64=False, max_tol=None):
         errs[k] = (d2 / vnorm if vnorm > 0 else d2, rel_max(a, b, vmax))
         assert errs[k][0] <= tol and errs[k][1] <= max_tol, (k, errs)
     return errs
+
+
+# co-moving window on the stepping path -------------------------------------
+def window_schedule(start, steps, n0, dt, dx, speed, ncells):
+    """Step indices before which the rule moves the box, one entry per move."""
+    out, moved = [], 0
+    for n in range(n0, n0 + steps):
+        while n >= start and moved + ncells <= math.floor((n - start) * dt * speed / dx):
+            out.append(n)
+            moved += ncells
+    return out
+
+
+def window_plasmas(wl, ncells, count, ids, seed0=300):
+    """count plasmas of the uncovered columns; the ids continue each species'."""
+    out = []
+    for k in range(count):
+        inj = W.injection_particles(wl, ncells, seed=seed0 + k, id_base=ids[0])
+        if len(wl.species) > 1:
+            inj2 = W.injection_particles(wl, ncells, seed=seed0 + k, id_base=ids[1])
+            inj = [inj[0], inj2[1]]
+        for s in range(len(ids)):
+            ids[s] += len(inj[s]["ix"])
+        out.append(inj)
+    return out
+
+
+def window_oracle_run(orc, steps, start, dt, dx, speed, ncells, slabs):
+    """steps oracle steps with the co-moving window's rule: before the step
+    from index n, while n >= start and moved + ncells <= floor((n - start) dt
+    speed / dx), one orc.shift_window(ncells, next plasma or None).  Returns
+    the cells moved."""
+    moved, k = 0, 0
+    for _ in range(steps):
+        n = orc.step_index
+        while n >= start and moved + ncells <= math.floor((n - start) * dt * speed / dx):
+            orc.shift_window(ncells, slabs[k] if k < len(slabs) else None)
+            k += 1
+            moved += ncells
+        orc.step(1)
+    return moved

@@ -8,7 +8,7 @@ step where the envelope of the pulse is near its peak at x = 0, so within a
 few steps the laser drives the plasma: particles cross cells and tiles in
 every direction and arrive in other tiles' ranges.
 
-Two checks, the tolerances of the parity tests:
+Three checks, the tolerances of the parity tests:
   - per step: at three points of the run the oracle's state is loaded into a
     second context, and one step of each is compared: every particle's u
     (relative, floor 1e-3), s and x at 1e-5, and J, E, B and the left
@@ -16,16 +16,22 @@ Two checks, the tolerances of the parity tests:
   - over the run: a context started from the same seeded state as the oracle
     runs 120 steps beside it, and the Eq. (4) polarization, the mean and the
     variance of the kinetic energy agree within 1 %, the live counts within
-    0.1 %.
+    0.1 %;
+  - the same with the co-moving window on (moves of one 16-cell tile column
+    from 10 steps into the run, the plasma of each move staged): the ranges
+    are relabelled in place across several moves and a re-bin, and the run
+    still follows the oracle's window within those bounds.
 """
 import math
 
 import numpy as np
 import pytest
 
+import oracle
 import paper_2002_02211_gb300 as pic
 import workloads as W
-from pichelp import compare_fields, compare_particles, make_pair
+from pichelp import (compare_fields, compare_particles, make_pair, window_oracle_run, window_plasmas,
+                     window_schedule)
 
 pytestmark = pytest.mark.gpu
 
@@ -109,4 +115,39 @@ def test_binned_layout_at_scale_with_the_laser_in_the_plasma():
         assert g["ekin_var"] == pytest.approx(om[6], rel=1e-2)
     finally:
         chk.close()
+        sim.close()
+
+
+def test_binned_layout_at_scale_co_moving():
+    wl = _cut()
+    dt = 0.95 / math.sqrt(sum((1 / (d * 2 * math.pi)) ** 2 for d in (wl.dx_lambda, wl.dy_lambda, wl.dz_lambda)))
+    start = int(round(wl.t_peak_periods * 2 * math.pi / dt)) - 30
+    sim, orc, parts = make_pair(wl, step=start, sort_every=SORT_EVERY, bins=BINS, window_cells=16)
+    try:
+        dt, dx = sim.grid()[:2]
+        ncells, w0 = 16, start + 10
+        moves = window_schedule(w0, STEPS, start, dt, dx, 1.0, ncells)
+        assert len(moves) >= 5, moves
+        plasmas = window_plasmas(wl, ncells, len(moves), [len(parts[0]["ix"])])
+        for pl in plasmas:
+            sim.stage_injection(pl)
+        sim.set_window(ncells, w0, 1.0)
+        for k in range(STEPS):
+            sim.step(1)
+            # the moves and the re-bin keep the binned layout (no fallback to the compact one)
+            assert sim.binned(0), k
+        sim.sync()
+        with oracle.parallel():
+            moved = window_oracle_run(orc, STEPS, w0, dt, dx, 1.0, ncells, plasmas)
+        assert moved == sim.window() == len(moves) * ncells
+        assert sim.staged_injections() == 0
+        assert np.abs(orc.f["ey"]).max() > 1.0
+        g = sim.polarization(0)
+        om = orc.moments(0)
+        assert abs(g["count"] - om[4]) <= 1e-3 * om[4]
+        np.testing.assert_allclose(g["P"], om[:3], atol=1e-2)
+        assert g["ekin_mean"] == pytest.approx(om[5], rel=1e-2)
+        assert g["ekin_var"] == pytest.approx(om[6], rel=1e-2)
+        compare_fields(sim, orc, ("ex", "ey", "ez", "bx", "by", "bz"), 1e-2)
+    finally:
         sim.close()

@@ -4,11 +4,12 @@ laser through the plasma).
 
 pic_step moves the box before the step from index n whenever
 n >= start and moved + ncells <= floor((n - start) dt speed / dx); the oracle
-run below applies the same rule, written out here, with orc.shift_window and
-the same staged plasma in the same order.  Cases:
+run (pichelp.window_oracle_run) applies the same rule, written out there, with
+orc.shift_window and the same staged plasma in the same order.  Cases:
   - 3D3V binned layout, moves of one tile column (16-wide and 8-wide tiles):
     the ranges are relabelled, no sort; the launch count of a step with a
-    move shows that path (six kernels more than a step without);
+    move shows that path (seven kernels more than a step without), and the
+    layout is still binned at the end;
   - 3D3V binned layout with moves that are not tile multiples, and the
     compact layout: the compact path (append, sort);
   - 2D3V with CUDA graphs (stretches end where a move is due), FP32 and FP64
@@ -25,58 +26,22 @@ import pytest
 
 import paper_2002_02211_gb300 as pic
 import workloads as W
-from pichelp import compare_fields, compare_particles, make_pair
+from pichelp import compare_fields, compare_particles, make_pair, window_oracle_run, window_plasmas, window_schedule
 
 pytestmark = pytest.mark.gpu
 
 
-def _schedule(start, steps, n0, dt, dx, speed, ncells):
-    """Step indices before which the rule moves the box, one entry per move."""
-    out, moved = [], 0
-    for n in range(n0, n0 + steps):
-        while n >= start and moved + ncells <= math.floor((n - start) * dt * speed / dx):
-            out.append(n)
-            moved += ncells
-    return out
-
-
-def _slabs(wl, ncells, count, ids, seed0=300):
-    """count plasmas of the uncovered columns; the ids continue each species'."""
-    out = []
-    for k in range(count):
-        inj = W.injection_particles(wl, ncells, seed=seed0 + k, id_base=ids[0])
-        if len(wl.species) > 1:
-            inj2 = W.injection_particles(wl, ncells, seed=seed0 + k, id_base=ids[1])
-            inj = [inj[0], inj2[1]]
-        for s in range(len(ids)):
-            ids[s] += len(inj[s]["ix"])
-        out.append(inj)
-    return out
-
-
-def _oracle_run(orc, steps, start, dt, dx, speed, ncells, slabs):
-    moved, k = 0, 0
-    for _ in range(steps):
-        n = orc.step_index
-        while n >= start and moved + ncells <= math.floor((n - start) * dt * speed / dx):
-            orc.shift_window(ncells, slabs[k] if k < len(slabs) else None)
-            k += 1
-            moved += ncells
-        orc.step(1)
-    return moved
-
-
 def _run(wl, steps, ncells, speed, start, *, tile=None, bins=None, sort_every=64, precision=32,
          staged_short=0, graphs=None):
-    sim, orc, parts = make_pair(wl, capacity_factor=1.6, sort_every=sort_every, tile=tile, bins=bins,
-                                precision=precision)
+    sim, orc, parts = make_pair(wl, sort_every=sort_every, tile=tile, bins=bins, precision=precision,
+                                window_cells=ncells)
     if graphs is not None:
         sim.set_graphs(graphs)
     dt, dx = sim.grid()[0], sim.grid()[1]
-    moves = _schedule(start, steps, 0, dt, dx, speed, ncells)
+    moves = window_schedule(start, steps, 0, dt, dx, speed, ncells)
     assert len(moves) >= 3, moves
     ids = [len(p["ix"]) for p in parts]
-    slabs = _slabs(wl, ncells, len(moves) - staged_short, ids)
+    slabs = window_plasmas(wl, ncells, len(moves) - staged_short, ids)
     for sl in slabs:
         sim.stage_injection(sl)
     assert sim.staged_injections() == len(slabs)
@@ -85,7 +50,7 @@ def _run(wl, steps, ncells, speed, start, *, tile=None, bins=None, sort_every=64
 
 
 def _finish(sim, orc, steps, start, grid, speed, ncells, slabs, moves, tol=1e-4, f64=False):
-    moved = _oracle_run(orc, steps, start, grid[0], grid[1], speed, ncells, slabs)
+    moved = window_oracle_run(orc, steps, start, grid[0], grid[1], speed, ncells, slabs)
     assert moved == len(moves) * ncells
     assert sim.window() == moved
     assert sim.get_step() == orc.step_index
@@ -124,11 +89,13 @@ def test_window_in_pic_step_3d(case):
             assert moves[1] > k0 + 1
             sim.step(1)
             l2 = sim.launch_count()
-            # the move: rows, cells, vacate, inject, counters, background
-            assert (l1 - l0) - (l2 - l1) == 6, (l0, l1, l2)
+            # the move: rows, cells, vacate, inject, counters, live count, background
+            assert (l1 - l0) - (l2 - l1) == 7, (l0, l1, l2)
             sim.step(steps - k0 - 2)
         else:
             sim.step(steps)
+        if bins and ncells % tile[0] == 0:
+            assert sim.binned(0), "the moves relabel ranges: the layout stays binned"
         _finish(sim, orc, steps, start, grid, speed, ncells, slabs, moves)
         assert (~orc.p[0]["alive"].astype(bool)).sum() > 0, "the moves should have removed particles"
     finally:
