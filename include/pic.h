@@ -196,7 +196,11 @@ pic_status_t pic_get_grid(void *ctx, double *dt, double *dx, double *dy, double 
 
 /* Loads the particles of one species from host float32 arrays (widened
  * exactly with precision 64; replacing what was there) and sorts them by tile.  n <= capacity (else PIC_ERR_OVERFLOW).
- * Cells must lie in the particle region (else PIC_ERR_ARG).  Synchronous. */
+ * Cells must lie in the particle region (else PIC_ERR_ARG).  Synchronous.
+ * When every array is pinned (page-locked, device-mapped) host memory, one
+ * kernel reads them in place over the host link and writes the particle
+ * buffer, cells packed on the way; other arrays are copied (cudaMemcpyAsync)
+ * and packed on the device.  Both give the same state. */
 pic_status_t pic_set_particles(void *ctx, int species, const pic_particles_t *p, void *stream);
 
 /* The same from float64 host arrays (exact with precision 64; rounded to

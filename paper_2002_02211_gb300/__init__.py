@@ -343,6 +343,13 @@ class Simulation:
         p = pic_particles_t(n=int(n), **kw)
         self._c(load().pic_set_particles(self.h, s, C.byref(p), self._s))
 
+    def set_particles_f64_raw(self, s, n, ptrs):
+        """set_particles_f64 from raw host addresses (float64 record arrays)."""
+        kw = {k: C.cast(C.c_void_p(int(v)), _I32P if k in _INT_KEYS else _F64P)
+              for k, v in ptrs.items()}
+        p = pic_particles_f64_t(n=int(n), **kw)
+        self._c(load().pic_set_particles_f64(self.h, s, C.byref(p), self._s))
+
     def count(self, s):
         n = C.c_int64()
         self._c(load().pic_get_count(self.h, s, C.byref(n)))

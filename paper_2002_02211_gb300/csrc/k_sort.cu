@@ -50,6 +50,24 @@ __global__ void k_pack3(const int32_t *ix, const int32_t *iy, const int32_t *iz,
     }
 }
 
+// Host particle arrays read in place (pinned, device-mapped memory) over the
+// host link and written into a particle buffer: cells packed and range
+// checked as k_pack / k_pack3 do, records converted to the buffer's real type.
+template <typename HostT, typename R, bool D3>
+__global__ void k_upload(const UploadSrc<HostT> s, const SortArrays<R> d, int n, int xlo, int xhi, int ny, int nz,
+                         unsigned *err) {
+    constexpr int NF = D3 ? 10 : 9;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+        const int x = s.ix[p], y = s.iy[p], z = D3 ? s.iz[p] : 0;
+        const bool bad = x < xlo || x > xhi || y < 0 || y >= ny || (D3 && (z < 0 || z >= nz));
+        if (bad) atomicOr(err, PIC_EF_RANGE);
+        d.cell[p] = bad ? PIC_DEAD : (D3 ? pack_cell3(x, y, z) : (((uint32_t)y << 16) | (uint32_t)x));
+#pragma unroll
+        for (int k = 0; k < NF; ++k) d.f[k][p] = (R)s.f[k][p];
+        d.id[p] = s.id[p];
+    }
+}
+
 __global__ void k_unpack3(const uint32_t *cell, int32_t *ix, int32_t *iy, int32_t *iz, int n) {
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
         const uint32_t c = cell[p];
@@ -302,6 +320,25 @@ cudaError_t launch_unpack_cells3(const uint32_t *cell, int32_t *ix, int32_t *iy,
     k_unpack3<<<grid_for(n), 256, 0, st>>>(cell, ix, iy, iz, n);
     return cudaGetLastError();
 }
+
+template <typename HostT, typename R>
+cudaError_t launch_upload(const UploadSrc<HostT> &src, const SortArrays<R> &dst, int n, int xlo, int xhi, int ny,
+                          int nz, bool d3, unsigned *err, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    if (d3)
+        k_upload<HostT, R, true><<<152 * 16, 256, 0, st>>>(src, dst, n, xlo, xhi, ny, nz, err);
+    else
+        k_upload<HostT, R, false><<<152 * 16, 256, 0, st>>>(src, dst, n, xlo, xhi, ny, nz, err);
+    return cudaGetLastError();
+}
+template cudaError_t launch_upload<float, float>(const UploadSrc<float> &, const SortArrays<float> &, int, int, int,
+                                                 int, int, bool, unsigned *, cudaStream_t);
+template cudaError_t launch_upload<float, double>(const UploadSrc<float> &, const SortArrays<double> &, int, int, int,
+                                                  int, int, bool, unsigned *, cudaStream_t);
+template cudaError_t launch_upload<double, float>(const UploadSrc<double> &, const SortArrays<float> &, int, int, int,
+                                                  int, int, bool, unsigned *, cudaStream_t);
+template cudaError_t launch_upload<double, double>(const UploadSrc<double> &, const SortArrays<double> &, int, int,
+                                                   int, int, int, bool, unsigned *, cudaStream_t);
 
 // Binned layout, per range r of each species:
 //  - counters: record the range's arrival base for the next step and clear

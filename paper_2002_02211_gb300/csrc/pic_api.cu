@@ -545,6 +545,35 @@ pic_status_t read_count(Ctx *c, int s, cudaStream_t st, int32_t *n) {
     return PIC_OK;
 }
 
+// the arrays of species s in buffer `which`, records in SortArrays order
+template <typename T>
+SortArrays<T> buf_arrays(Ctx *c, int s, int which) {
+    const SpeciesBuf &B = c->buf[s][which];
+    SortArrays<T> a{};
+    a.cell = B.cell;
+    a.id = B.id;
+    a.n = c->n_dev + s;
+    T *const *f = reinterpret_cast<T *const *>(B.f);
+    if (c->dim == 3) {
+        T *g[10] = {f[0], f[1], static_cast<T *>(B.oz), f[2], f[3], f[4], f[5], f[6], f[7], f[8]};
+        for (int k = 0; k < 10; ++k) a.f[k] = g[k];
+    } else {
+        for (int k = 0; k < 9; ++k) a.f[k] = f[k];
+    }
+    return a;
+}
+
+// device address of a pinned (device-mapped) host array, nullptr for pageable
+// memory or when the query fails
+const void *mapped_host(const void *p) {
+    cudaPointerAttributes a{};
+    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 // Host particles p of species s into slots [base, base + p->n) of the current
 // buffer (float or double host arrays; converted on the device when the
 // context's precision differs), cells packed and range checked; the slot
@@ -566,11 +595,42 @@ pic_status_t upload_particles(Ctx *c, int s, const PT *p, int64_t base, cudaStre
         pic_status_t r = seal_pending(c, st);  // appended after sealed slots
         if (r != PIC_OK) return r;
     }
+    const int xlo = c->cfg.bc_x == PIC_BC_OPEN ? 2 : 0;
+    const int xhi = c->cfg.bc_x == PIC_BC_OPEN ? c->cfg.nx - 3 : c->cfg.nx - 1;
+    // pinned host arrays: one kernel reads them in place over the host link
+    // and writes the buffer (cells packed, precision converted on the way)
+    UploadSrc<HostT> us{};
+    bool direct = n > 0;
+    if (direct) {
+        us.ix = static_cast<const int32_t *>(mapped_host(p->ix));
+        us.iy = static_cast<const int32_t *>(mapped_host(p->iy));
+        us.iz = d3 ? static_cast<const int32_t *>(mapped_host(p->iz)) : nullptr;
+        us.id = static_cast<const int32_t *>(mapped_host(p->id));
+        direct = us.ix && us.iy && us.id && (!d3 || us.iz);
+        const HostT *rec3[10] = {p->ox, p->oy, p->oz, p->ux, p->uy, p->uz, p->sx, p->sy, p->sz, p->w};
+        for (int k = 0; k < (d3 ? 10 : 9) && direct; ++k) {
+            us.f[k] = static_cast<const HostT *>(mapped_host(d3 ? rec3[k] : src[k]));
+            direct = us.f[k] != nullptr;
+        }
+    }
+    if (direct) {
+        CK(with_real(c, [&](auto z) {
+            using T = decltype(z);
+            SortArrays<T> d = buf_arrays<T>(c, s, c->cur[s]);
+            d.cell += base;
+            d.id += base;
+            for (int k = 0; k < 10; ++k)
+                if (d.f[k]) d.f[k] += base;
+            return launch_upload<HostT, T>(us, d, (int)n, xlo, xhi, c->cfg.ny, c->dim == 3 ? c->cfg.nz : 1, d3,
+                                           c->err, st);
+        }));
+        c->launches += 1;
+    }
     SpeciesBuf &B = c->buf[s][c->cur[s]];
     const size_t cap = (size_t)c->cfg.sp[s].capacity;
     int32_t *dix = c->scratch_i32, *diy = c->scratch_i32 + cap, *diz = c->scratch_i32 + 2 * cap;
     const size_t rb = c->rb;
-    if (n) {
+    if (n && !direct) {
         CK(cudaMemcpyAsync(dix, p->ix, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(diy, p->iy, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         if (d3) CK(cudaMemcpyAsync(diz, p->iz, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
@@ -590,13 +650,13 @@ pic_status_t upload_particles(Ctx *c, int s, const PT *p, int64_t base, cudaStre
         }
         CK(cudaMemcpyAsync(B.id + base, p->id, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     }
-    const int xlo = c->cfg.bc_x == PIC_BC_OPEN ? 2 : 0;
-    const int xhi = c->cfg.bc_x == PIC_BC_OPEN ? c->cfg.nx - 3 : c->cfg.nx - 1;
-    if (d3)
-        CK(launch_pack_cells3(dix, diy, diz, B.cell + base, (int)n, xlo, xhi, c->cfg.ny, c->cfg.nz, c->err, st));
-    else
-        CK(launch_pack_cells(dix, diy, B.cell + base, (int)n, xlo, xhi, c->cfg.ny, c->err, st));
-    c->launches += n ? 1 : 0;
+    if (!direct) {
+        if (d3)
+            CK(launch_pack_cells3(dix, diy, diz, B.cell + base, (int)n, xlo, xhi, c->cfg.ny, c->cfg.nz, c->err, st));
+        else
+            CK(launch_pack_cells(dix, diy, B.cell + base, (int)n, xlo, xhi, c->cfg.ny, c->err, st));
+        c->launches += n ? 1 : 0;
+    }
     const int32_t nn = (int32_t)(base + (int64_t)n);
     CK(cudaMemcpyAsync(c->n_dev + s, &nn, sizeof(int32_t), cudaMemcpyHostToDevice, st));
     c->n_upper[s] = (int)nn;
@@ -668,24 +728,6 @@ pic_status_t alloc_old(Ctx *c, int s) {
 // ---------------------------------------------------------------------------
 // co-moving window (Sec. 2): staged plasma and the device-side move
 // ---------------------------------------------------------------------------
-
-// the arrays of species s in buffer `which`, records in SortArrays order
-template <typename T>
-SortArrays<T> buf_arrays(Ctx *c, int s, int which) {
-    const SpeciesBuf &B = c->buf[s][which];
-    SortArrays<T> a{};
-    a.cell = B.cell;
-    a.id = B.id;
-    a.n = c->n_dev + s;
-    T *const *f = reinterpret_cast<T *const *>(B.f);
-    if (c->dim == 3) {
-        T *g[10] = {f[0], f[1], static_cast<T *>(B.oz), f[2], f[3], f[4], f[5], f[6], f[7], f[8]};
-        for (int k = 0; k < 10; ++k) a.f[k] = g[k];
-    } else {
-        for (int k = 0; k < 9; ++k) a.f[k] = f[k];
-    }
-    return a;
-}
 
 template <typename T>
 SortArrays<T> slab_arrays(const Slab &b, int s) {

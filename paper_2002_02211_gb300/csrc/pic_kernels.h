@@ -92,6 +92,16 @@ struct SortArrays {
     int32_t *id;
     const int32_t *n;
 };
+// host particle arrays a kernel reads in place (device-mapped pointers),
+// records in SortArrays order
+template <typename HostT>
+struct UploadSrc {
+    const int32_t *ix, *iy, *iz, *id;
+    const HostT *f[10];
+};
+template <typename HostT, typename R>
+cudaError_t launch_upload(const UploadSrc<HostT> &src, const SortArrays<R> &dst, int n, int xlo, int xhi, int ny,
+                          int nz, bool d3, unsigned *err, cudaStream_t st);
 struct SortScratch {
     int32_t *cell_count, *cell_off;  // [ntiles * TX * TY]
     int32_t *tile_R, *tile_total;    // [ntiles], tile_total [ntiles + 1]
