@@ -375,6 +375,48 @@ pic_status_t pic_staged_injections(void *ctx, int64_t *count);
  * counts every particle staged into it since the last completed count). */
 pic_status_t pic_get_layout(void *ctx, int species, int *binned);
 
+/* Caller-owned device memory for a context's state (e.g. torch tensors,
+ * which then are the state, with no copy).  Per species the two particle
+ * buffers the steps and sorts
+ * alternate between: the cell words (0xFFFFFFFF = removed), the record
+ * arrays in the context's real type (float for precision 32, double for 64;
+ * oz in 3D3V only) and the ids, each of at least `capacity` entries; and the
+ * mesh: eb = E then B, [6][nz][ny][ld] reals, j = [3][nz][ny][ld] reals (nz = 1
+ * in 2D3V; ld and the sizes from pic_buffer_sizes).  A NULL member keeps the
+ * context's own array. */
+typedef struct {
+    uint32_t *cell;
+    void *ox, *oy, *oz, *ux, *uy, *uz, *sx, *sy, *sz, *w;
+    int32_t *id;
+} pic_particle_buffer_t;
+
+typedef struct {
+    pic_particle_buffer_t sp[PIC_MAX_SPECIES][2];
+    void *eb;
+    void *j;
+} pic_buffers_t;
+
+/* Sizes a caller needs to allocate pic_buffers_t memory: the mesh row pitch
+ * ld (reals; >= nx), the reals of one mesh component (plane = ld ny nz), the
+ * bytes of one real (4 or 8), and each species' capacity (slots of every
+ * particle array; unused entries 0). */
+pic_status_t pic_buffer_sizes(void *ctx, int64_t *ld, int64_t *plane, int *real_bytes,
+                              int64_t capacity[PIC_MAX_SPECIES]);
+
+/* Moves the context's state into the caller's memory: each non-NULL member of
+ * b receives a copy of the array it replaces, the context frees its own and
+ * uses the caller's from then on (the caller keeps ownership: the memory must
+ * stay allocated, on the context's device, until pic_destroy).  Every pointer
+ * must be device (or managed) memory of the context's device, 16-byte aligned
+ * (else PIC_ERR_ARG and nothing changes); sizes are the caller's
+ * responsibility.  Captured step graphs are dropped and the field window's
+ * tensor map is re-encoded.  Synchronous. */
+pic_status_t pic_bind_buffers(void *ctx, const pic_buffers_t *b, void *stream);
+
+/* Which of species s's two particle buffers holds its particles now (0 or 1;
+ * the other is scratch for the next step or sort). */
+pic_status_t pic_current_buffer(void *ctx, int species, int *which);
+
 /* Cells the window has moved since pic_create. */
 pic_status_t pic_get_window(void *ctx, int64_t *offset_cells);
 

@@ -64,6 +64,17 @@ class pic_particles_t(C.Structure):
 
 _F64P = C.POINTER(C.c_double)
 
+# record arrays of one particle buffer, in pic_particle_buffer_t order
+_BUF_REALS = ("ox", "oy", "oz", "ux", "uy", "uz", "sx", "sy", "sz", "w")
+
+
+class pic_particle_buffer_t(C.Structure):
+    _fields_ = [("cell", C.c_void_p)] + [(k, C.c_void_p) for k in _BUF_REALS] + [("id", C.c_void_p)]
+
+
+class pic_buffers_t(C.Structure):
+    _fields_ = [("sp", (pic_particle_buffer_t * 2) * 4), ("eb", C.c_void_p), ("j", C.c_void_p)]
+
 
 class pic_particles_f64_t(C.Structure):
     _fields_ = [("n", C.c_int64), ("ix", _I32P), ("iy", _I32P)] + \
@@ -138,6 +149,10 @@ _SIGS = {
     "pic_stage_injection": [C.c_void_p, C.c_void_p, C.c_void_p],
     "pic_staged_injections": [C.c_void_p, C.POINTER(C.c_int64)],
     "pic_get_layout": [C.c_void_p, C.c_int, C.POINTER(C.c_int)],
+    "pic_buffer_sizes": [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int),
+                         C.POINTER(C.c_int64)],
+    "pic_bind_buffers": [C.c_void_p, C.c_void_p, C.c_void_p],
+    "pic_current_buffer": [C.c_void_p, C.c_int, C.POINTER(C.c_int)],
     "pic_set_diagnostics": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
     "pic_get_diagnostics": [C.c_void_p, C.c_void_p, C.POINTER(C.c_int64), C.c_void_p],
     "pic_moments_noalloc": [C.c_int64] + [C.c_void_p] * 8 + [C.c_double, C.c_double, C.c_double,
@@ -541,6 +556,57 @@ class Simulation:
         arr, keep = self._inject_arr(inject)
         self._c(load().pic_stage_injection(self.h, arr, self._s))
         del keep
+
+    def buffer_sizes(self):
+        """pic_buffer_sizes: (ld, plane, real bytes, [capacity per species])."""
+        ld, plane, rb = C.c_int64(), C.c_int64(), C.c_int()
+        cap = (C.c_int64 * 4)()
+        self._c(load().pic_buffer_sizes(self.h, C.byref(ld), C.byref(plane), C.byref(rb), cap))
+        return ld.value, plane.value, rb.value, list(cap)[:self.nspecies]
+
+    def bind_torch(self, mesh=True, particles=True):
+        """pic_bind_buffers with torch tensors allocated here on the current
+        CUDA device: from then on they are the context's state (no copies).
+        Returns {"eb": [6][nz][ny][ld], "j": [3][nz][ny][ld],
+        "sp": [[buffer 0 dict, buffer 1 dict] per species]} (cell words as
+        int32 bit patterns)."""
+        import torch
+        ld, plane, rb, caps = self.buffer_sizes()
+        dt = torch.float32 if rb == 4 else torch.float64
+        dev = torch.device("cuda", torch.cuda.current_device())
+        b = pic_buffers_t()
+        out = {"eb": None, "j": None, "sp": []}
+        if mesh:
+            out["eb"] = torch.zeros((6, self.nz, self.ny, ld), dtype=dt, device=dev)
+            out["j"] = torch.zeros((3, self.nz, self.ny, ld), dtype=dt, device=dev)
+            b.eb, b.j = out["eb"].data_ptr(), out["j"].data_ptr()
+        for s in range(self.nspecies):
+            pair = []
+            for q in range(2):
+                if not particles:
+                    pair.append(None)
+                    continue
+                t = {"cell": torch.empty(caps[s], dtype=torch.int32, device=dev),
+                     "id": torch.empty(caps[s], dtype=torch.int32, device=dev)}
+                for k in _BUF_REALS:
+                    if k != "oz" or self.dim == 3:
+                        t[k] = torch.empty(caps[s], dtype=dt, device=dev)
+                slot = b.sp[s][q]
+                for k, v in t.items():
+                    setattr(slot, k, v.data_ptr())
+                pair.append(t)
+            out["sp"].append(pair)
+        self._c(load().pic_bind_buffers(self.h, C.byref(b), self._s))
+        self._bound = out
+        return out
+
+    def particle_views(self, s):
+        """Species s's particles in bound memory (bind_torch), no copy: the
+        current buffer's tensors cut to pic_get_count slots."""
+        which = C.c_int()
+        self._c(load().pic_current_buffer(self.h, int(s), C.byref(which)))
+        n = self.count(s)
+        return {k: v[:n] for k, v in self._bound["sp"][s][which.value].items()}
 
     def binned(self, s):
         """pic_get_layout: True when species s is in the binned 3D3V layout."""

@@ -161,8 +161,18 @@ struct Ctx {
     cudaEvent_t gev[2] = {};
     double *laser_tab = nullptr;  // device [2 * graph_max]: (fz, fy) of each step of a replayed stretch
     const double *lf_capture = nullptr;  // while capturing: this step's slot of laser_tab
+    // device arrays the caller owns (pic_bind_buffers): never freed here
+    std::vector<void *> borrowed;
     std::string last_error;
 };
+
+// cudaFree unless the caller owns the array
+void free_own(Ctx *c, void *p) {
+    if (!p) return;
+    for (void *b : c->borrowed)
+        if (b == p) return;
+    cudaFree(p);
+}
 
 void drop_step_graphs(Ctx *c) {
     for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
@@ -1174,18 +1184,18 @@ pic_status_t pic_create(const pic_config_t *cfg, void *stream, void **ctx_out) {
 void pic_destroy(void *ctx) {
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return;
-    cudaFree(c->EB);
-    cudaFree(c->J);
+    free_own(c, c->EB);
+    free_own(c, c->J);
     cudaFree(c->bnd);
     cudaFree(c->rho);
     cudaFree(c->rho_bg);
     cudaFree(c->stage);
     for (int s = 0; s < PIC_MAX_SPECIES; ++s) {
         for (int b = 0; b < 2; ++b) {
-            cudaFree(c->buf[s][b].cell);
-            for (int k = 0; k < 9; ++k) cudaFree(c->buf[s][b].f[k]);
-            cudaFree(c->buf[s][b].oz);
-            cudaFree(c->buf[s][b].id);
+            free_own(c, c->buf[s][b].cell);
+            for (int k = 0; k < 9; ++k) free_own(c, c->buf[s][b].f[k]);
+            free_own(c, c->buf[s][b].oz);
+            free_own(c, c->buf[s][b].id);
         }
         cudaFree(c->tile_start[s]);
         cudaFree(c->bin_cnt[s][0]);
@@ -2004,6 +2014,79 @@ pic_status_t pic_staged_injections(void *ctx, int64_t *count) {
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c || !count) return fail(c, PIC_ERR_ARG, "null argument");
     *count = (int64_t)c->inj_queue.size();
+    return PIC_OK;
+}
+
+pic_status_t pic_buffer_sizes(void *ctx, int64_t *ld, int64_t *plane, int *real_bytes,
+                              int64_t capacity[PIC_MAX_SPECIES]) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c || !ld || !plane || !real_bytes || !capacity) return fail(c, PIC_ERR_ARG, "null argument");
+    *ld = c->ld;
+    *plane = (int64_t)c->plane;
+    *real_bytes = c->rb;
+    for (int s = 0; s < PIC_MAX_SPECIES; ++s) capacity[s] = s < c->cfg.nspecies ? c->cfg.sp[s].capacity : 0;
+    return PIC_OK;
+}
+
+pic_status_t pic_bind_buffers(void *ctx, const pic_buffers_t *b, void *stream) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c || !b) return fail(c, PIC_ERR_ARG, "null argument");
+    if (c->pending_deposit) return fail(c, PIC_ERR_STATE, "a move is waiting for pic_deposit");
+    cudaStream_t st = S(stream);
+    // (slot in the context, caller's array, bytes)
+    struct Swap {
+        void **own;
+        void *mine;
+        size_t bytes;
+    };
+    std::vector<Swap> sw;
+    const size_t rb = c->rb;
+    auto add = [&](void **own, void *mine, size_t bytes) {
+        if (mine) sw.push_back(Swap{own, mine, bytes});
+    };
+    add(&c->EB, b->eb, 6 * c->plane * rb);
+    add(&c->J, b->j, 3 * c->plane * rb);
+    for (int s = 0; s < c->cfg.nspecies; ++s) {
+        const size_t cap = (size_t)c->cfg.sp[s].capacity;
+        for (int q = 0; q < 2; ++q) {
+            const pic_particle_buffer_t &u = b->sp[s][q];
+            SpeciesBuf &B = c->buf[s][q];
+            add(reinterpret_cast<void **>(&B.cell), u.cell, cap * sizeof(uint32_t));
+            void *rec[9] = {u.ox, u.oy, u.ux, u.uy, u.uz, u.sx, u.sy, u.sz, u.w};
+            for (int k = 0; k < 9; ++k) add(&B.f[k], rec[k], cap * rb);
+            if (c->dim == 3) add(&B.oz, u.oz, cap * rb);
+            add(reinterpret_cast<void **>(&B.id), u.id, cap * sizeof(int32_t));
+        }
+    }
+    for (const Swap &w : sw) {
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, w.mine) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, PIC_ERR_ARG, "bound array: not a CUDA pointer");
+        }
+        const bool dev = a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+        if (!dev || a.device != c->device)
+            return fail(c, PIC_ERR_ARG, "bound array: not memory of the context's device");
+        if (reinterpret_cast<uintptr_t>(w.mine) % 16 != 0)
+            return fail(c, PIC_ERR_ARG, "bound array: not 16-byte aligned");
+    }
+    if (sw.empty()) return PIC_OK;
+    for (const Swap &w : sw) CK(cudaMemcpyAsync(w.mine, *w.own, w.bytes, cudaMemcpyDeviceToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    for (const Swap &w : sw) {
+        free_own(c, *w.own);
+        *w.own = w.mine;
+        c->borrowed.push_back(w.mine);
+    }
+    drop_step_graphs(c);
+    return make_tensor_map(c);
+}
+
+pic_status_t pic_current_buffer(void *ctx, int s, int *which) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c || !which) return fail(c, PIC_ERR_ARG, "null argument");
+    if (s < 0 || s >= c->cfg.nspecies) return fail(c, PIC_ERR_ARG, "species out of range");
+    *which = c->cur[s];
     return PIC_OK;
 }
 
