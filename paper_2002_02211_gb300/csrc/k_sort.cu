@@ -4,13 +4,16 @@
 // With C = TX * TY cells per tile and R = the smallest particle count of any
 // cell of the tile, slot r * C + c of the tile holds the r-th particle of
 // local cell c for r < R (every cell has at least R, so the layers have no
-// holes); the remaining particles follow in a tail, cell by cell.  A CTA of
-// C (or a divisor of C) threads walking the tile therefore meets the same
-// cell on every pass through the layers, which the fused kernel uses to sum
+// holes); the remaining particles follow in a tail, cell by cell (2D3V) or
+// dealt cell by cell into four interleaved runs (3D3V, where after motion
+// most tiles have an empty cell, R = 0, and the whole tile is tail: a warp's
+// 32 consecutive slots then rarely hold two particles of one cell).  A CTA
+// of C (or a divisor of C) threads walking the tile meets the same cell on
+// every pass through the layers, which the 2D3V fused kernel uses to sum
 // the in-cell currents in registers.  Steps: rank of each particle in its
 // cell (atomics), per-tile layout (block min and scan over the cells),
 // exclusive scan of the tile totals, scatter.  The 2D3V and 3D3V layouts
-// differ only in the cell packing and the tile key.
+// differ in the cell packing, the tile key and the tail order.
 #include "pic_device3.cuh"
 #include "pic_kernels.h"
 
@@ -84,6 +87,7 @@ __global__ void k_unpack3(const uint32_t *cell, int32_t *ix, int32_t *iy, int32_
 __host__ __device__ constexpr int log2i(int v) { return v <= 1 ? 0 : 1 + log2i(v >> 1); }
 
 struct Key2 {
+    static constexpr bool kSpread = false;  // tail kept cell by cell (see k_scatter)
     int sx, sy, ntx, nt;  // log2 of the tile sizes, tiles along x, tiles
     explicit Key2(const TileGeom &t) : sx(log2i(t.TX)), sy(log2i(t.TY)), ntx(t.ntx), nt(t.ntx * t.nty) {}
     __device__ __forceinline__ int operator()(uint32_t c, int &tile) const {
@@ -96,6 +100,7 @@ struct Key2 {
 };
 
 struct Key3 {
+    static constexpr bool kSpread = true;
     int sx, sy, sz, ntx, nty, nt;
     explicit Key3(const TileGeom3 &t)
         : sx(log2i(t.TX)), sy(log2i(t.TY)), sz(log2i(t.TZ)), ntx(t.ntx), nty(t.nty), nt(t.ntx * t.nty * t.ntz) {}
@@ -270,7 +275,8 @@ cudaError_t scan_tiles(const int32_t *count, int nt, int32_t *start, int32_t *sc
 
 template <typename R, int NF, class K>
 __global__ void k_scatter(const SortArrays<R> src, const SortArrays<R> dst, const K kf, const int32_t *rank,
-                          const int32_t *tile_start, const int32_t *tile_R, const int32_t *cell_off, int C) {
+                          const int32_t *tile_start, const int32_t *tile_R, const int32_t *cell_off,
+                          const int32_t *cell_count, int C) {
     const int n = *src.n;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
         const int r = rank[p];
@@ -279,7 +285,28 @@ __global__ void k_scatter(const SortArrays<R> src, const SortArrays<R> dst, cons
         int tile;
         const int key = kf(c, tile);
         const int lc = key - tile * C, Rl = tile_R[tile];
-        const int pos = tile_start[tile] + (r < Rl ? r * C + lc : Rl * C + cell_off[key] + (r - Rl));
+        int pos;
+        if (r < Rl) {
+            pos = r * C + lc;
+        } else {
+            int i = cell_off[key] + (r - Rl);  // place in the tail, cell by cell
+            if constexpr (K::kSpread) {
+                // the tail dealt into S interleaved runs, so that the particles
+                // of one cell (consecutive in the tail) land in different warps
+                // and a warp's lanes rarely share a cell: their shared-memory
+                // atomics then do not collide on one address.  S = 4 was the
+                // fastest of 2, 3, 4, 6, 8, 16 on the 3D3V workload at 2 per cell
+                constexpr int S = 4;
+                const int last = (tile + 1) * C - 1;
+                const int T = cell_off[last] + cell_count[last] - Rl;
+                if (T >= 64 * S) {
+                    const int m = i % S, q = i / S;
+                    i = m * (T / S) + min(m, T % S) + q;
+                }
+            }
+            pos = Rl * C + i;
+        }
+        pos += tile_start[tile];
         dst.cell[pos] = c;
 #pragma unroll
         for (int k = 0; k < NF; ++k) dst.f[k][pos] = src.f[k][p];
@@ -409,7 +436,8 @@ cudaError_t tile_sort(const SortArrays<R> &src, const SortArrays<R> &dst, const 
     k_layout<<<nt, C, 0, st>>>(w.cell_count, C, w.cell_off, w.tile_R, w.tile_total, bins);
     e = scan_tiles(w.tile_total, bins.cnt_to ? nt + 1 : nt, tile_start, w.cursor, n_tmp, st);
     if (e != cudaSuccess) return e;
-    k_scatter<R, NF, K><<<g, 256, 0, st>>>(src, dst, key, w.rank, tile_start, w.tile_R, w.cell_off, C);
+    k_scatter<R, NF, K><<<g, 256, 0, st>>>(src, dst, key, w.rank, tile_start, w.tile_R, w.cell_off, w.cell_count,
+                                           C);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (bins.cnt_to) {
