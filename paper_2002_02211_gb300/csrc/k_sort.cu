@@ -4,16 +4,16 @@
 // With C = TX * TY cells per tile and R = the smallest particle count of any
 // cell of the tile, slot r * C + c of the tile holds the r-th particle of
 // local cell c for r < R (every cell has at least R, so the layers have no
-// holes); the remaining particles follow in a tail, cell by cell (2D3V) or
-// dealt cell by cell into four interleaved runs (3D3V, where after motion
-// most tiles have an empty cell, R = 0, and the whole tile is tail: a warp's
-// 32 consecutive slots then rarely hold two particles of one cell).  A CTA
-// of C (or a divisor of C) threads walking the tile meets the same cell on
-// every pass through the layers, which the 2D3V fused kernel uses to sum
-// the in-cell currents in registers.  Steps: rank of each particle in its
-// cell (atomics), per-tile layout (block min and scan over the cells),
-// exclusive scan of the tile totals, scatter.  The 2D3V and 3D3V layouts
-// differ in the cell packing, the tile key and the tail order.
+// holes); the remaining particles follow in a tail, taken cell by cell and
+// dealt into a few interleaved runs, so that a warp's 32 consecutive slots
+// rarely hold two particles of one cell (after some motion most 3D3V tiles
+// have an empty cell, R = 0, and the whole tile is tail).  A CTA of C (or a
+// divisor of C) threads walking the tile meets the same cell on every pass
+// through the layers, which the 2D3V fused kernel uses to sum the in-cell
+// currents in registers.  Steps: rank of each particle in its cell
+// (atomics), per-tile layout (block min and scan over the cells), exclusive
+// scan of the tile totals, scatter.  The 2D3V and 3D3V layouts differ only
+// in the cell packing and the tile key.
 #include "pic_device3.cuh"
 #include "pic_kernels.h"
 
@@ -87,7 +87,7 @@ __global__ void k_unpack3(const uint32_t *cell, int32_t *ix, int32_t *iy, int32_
 __host__ __device__ constexpr int log2i(int v) { return v <= 1 ? 0 : 1 + log2i(v >> 1); }
 
 struct Key2 {
-    static constexpr bool kSpread = false;  // tail kept cell by cell (see k_scatter)
+    static constexpr int kTailRuns = 8;  // interleaved runs of the tail (k_scatter)
     int sx, sy, ntx, nt;  // log2 of the tile sizes, tiles along x, tiles
     explicit Key2(const TileGeom &t) : sx(log2i(t.TX)), sy(log2i(t.TY)), ntx(t.ntx), nt(t.ntx * t.nty) {}
     __device__ __forceinline__ int operator()(uint32_t c, int &tile) const {
@@ -100,7 +100,7 @@ struct Key2 {
 };
 
 struct Key3 {
-    static constexpr bool kSpread = true;
+    static constexpr int kTailRuns = 4;
     int sx, sy, sz, ntx, nty, nt;
     explicit Key3(const TileGeom3 &t)
         : sx(log2i(t.TX)), sy(log2i(t.TY)), sz(log2i(t.TZ)), ntx(t.ntx), nty(t.nty), nt(t.ntx * t.nty * t.ntz) {}
@@ -290,19 +290,18 @@ __global__ void k_scatter(const SortArrays<R> src, const SortArrays<R> dst, cons
             pos = r * C + lc;
         } else {
             int i = cell_off[key] + (r - Rl);  // place in the tail, cell by cell
-            if constexpr (K::kSpread) {
-                // the tail dealt into S interleaved runs, so that the particles
-                // of one cell (consecutive in the tail) land in different warps
-                // and a warp's lanes rarely share a cell: their shared-memory
-                // atomics then do not collide on one address.  S = 4 was the
-                // fastest of 2, 3, 4, 6, 8, 16 on the 3D3V workload at 2 per cell
-                constexpr int S = 4;
-                const int last = (tile + 1) * C - 1;
-                const int T = cell_off[last] + cell_count[last] - Rl;
-                if (T >= 64 * S) {
-                    const int m = i % S, q = i / S;
-                    i = m * (T / S) + min(m, T % S) + q;
-                }
+            // the tail dealt into S interleaved runs, so that the particles
+            // of one cell (consecutive in the tail) land in different warps
+            // and a warp's lanes rarely share a cell: their shared-memory
+            // atomics then do not collide on one address.  Measured fastest:
+            // S = 4 of 2, 3, 4, 6, 8, 16 for 3D3V at 2 per cell, S = 8 of 2,
+            // 4, 8 for 2D3V at 8 + 8 per cell (a fifth off its fused kernel)
+            constexpr int S = K::kTailRuns;
+            const int last = (tile + 1) * C - 1;
+            const int T = cell_off[last] + cell_count[last] - Rl;
+            if (T >= 64 * S) {
+                const int m = i % S, q = i / S;
+                i = m * (T / S) + min(m, T % S) + q;
             }
             pos = Rl * C + i;
         }
