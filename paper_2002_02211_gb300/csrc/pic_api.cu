@@ -2710,11 +2710,23 @@ pic_status_t pic_adjoint(void *ctx, int nsteps, int checkpoint_every, const pic_
     }
     const Snap L = snap_layout(c, n);
     const int nck = (nsteps + K - 1) / K;
-    const size_t nsnap = (size_t)nck + (size_t)K + 1;  // checkpoints, one stretch, the final state
+    // checkpoints, two stretches (the backward of one stretch reads one while
+    // the recompute of the stretch before it fills the other), the final state
+    const size_t nsnap = (size_t)nck + 2 * (size_t)K + 1;
     char *store = nullptr;
     void *LEB = nullptr, *LJ = nullptr, *Lbnd = nullptr;
     double *sums = nullptr, *dla0 = nullptr;
+    cudaStream_t s2 = nullptr;  // the recompute stream
+    cudaEvent_t ready[2] = {}, freed[2] = {};
     auto cleanup = [&]() {
+        if (s2) {
+            cudaStreamSynchronize(s2);
+            cudaStreamDestroy(s2);
+        }
+        for (int b = 0; b < 2; ++b) {
+            if (ready[b]) cudaEventDestroy(ready[b]);
+            if (freed[b]) cudaEventDestroy(freed[b]);
+        }
         cudaFree(store);
         cudaFree(LEB);
         cudaFree(LJ);
@@ -2759,11 +2771,20 @@ pic_status_t pic_adjoint(void *ctx, int nsteps, int checkpoint_every, const pic_
         c->adj_n[s] = n[s];
     }
     auto snap = [&](size_t k) { return store + k * L.bytes; };
-    char *final_state = snap(nck + K);
+    auto stretch = [&](int b, int j) { return snap((size_t)nck + (size_t)b * K + j); };
+    char *final_state = snap((size_t)nck + 2 * (size_t)K);
+    ACK(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; ++b) {
+        ACK(cudaEventCreateWithFlags(&ready[b], cudaEventDisableTiming));
+        ACK(cudaEventCreateWithFlags(&freed[b], cudaEventDisableTiming));
+    }
     const long long step0 = c->step;
-    // forward with checkpoints
+    // forward with checkpoints; the states of the last stretch are kept as
+    // they pass (its backward comes first and needs no recompute)
+    const int klast = (nck - 1) * K;
     for (int k = 0; k < nsteps; ++k) {
         if (k % K == 0) ARET(snap_copy(c, L, n, snap(k / K), true, st));
+        if (k >= klast) ARET(snap_copy(c, L, n, stretch((nck - 1) & 1, k - klast), true, st));
         ARET(forward_adjoint_step(c, st));
     }
     ARET(snap_copy(c, L, n, final_state, true, st));
@@ -2781,18 +2802,38 @@ pic_status_t pic_adjoint(void *ctx, int nsteps, int checkpoint_every, const pic_
     ACK(cudaMemsetAsync(dla0, 0, sizeof(double), st));
     LaserParams unit = laser(c);
     unit.a0 = 1.0;  // time factors per unit a0: the source is linear in a0
-    // backward, one stretch at a time
-    for (int i = nck - 1; i >= 0; --i) {
-        const int k0 = i * K, k1 = std::min(nsteps, k0 + K);
-        // restore the checkpoint and store every state of the stretch
-        ARET(snap_copy(c, L, n, snap(i), false, st));
+    // backward, one stretch at a time.  The recompute of stretch i - 1 (from
+    // its checkpoint, in the context's buffers, on stream s2) and the backward
+    // of stretch i (from stored states and the lambda buffers, on st) touch
+    // disjoint memory, so they run at the same time; events order each
+    // stretch buffer's fill before its backward and its backward before the
+    // next fill.
+    ACK(cudaEventRecord(freed[0], st));  // the forward pass above, done on st
+    ACK(cudaStreamWaitEvent(s2, freed[0], 0));
+    auto recompute = [&](int i) -> pic_status_t {
+        const int b = i & 1, k0 = i * K, k1 = std::min(nsteps, k0 + K);
+        pic_status_t q = snap_copy(c, L, n, snap(i), false, s2);
         c->step = step0 + k0;
-        for (int k = k0; k < k1; ++k) {
-            ARET(snap_copy(c, L, n, snap(nck + (k - k0)), true, st));
-            if (k + 1 < k1) ARET(forward_adjoint_step(c, st));
+        for (int k = k0; k < k1 && q == PIC_OK; ++k) {
+            q = snap_copy(c, L, n, stretch(b, k - k0), true, s2);
+            if (q == PIC_OK && k + 1 < k1) q = forward_adjoint_step(c, s2);
+        }
+        if (q == PIC_OK && cudaEventRecord(ready[b], s2) != cudaSuccess)
+            q = fail(c, PIC_ERR_CUDA, "adjoint: event record failed");
+        return q;
+    };
+    ACK(cudaEventRecord(ready[(nck - 1) & 1], st));
+    for (int i = nck - 1; i >= 0; --i) {
+        const int b = i & 1, k0 = i * K, k1 = std::min(nsteps, k0 + K);
+        ACK(cudaStreamWaitEvent(st, ready[b], 0));
+        if (i > 0) {
+            // stretch i - 1 goes into the other buffer once its last reader
+            // (the backward of stretch i + 1) is done
+            if (i + 1 < nck) ACK(cudaStreamWaitEvent(s2, freed[(i + 1) & 1], 0));
+            ARET(recompute(i - 1));
         }
         for (int k = k1 - 1; k >= k0; --k) {
-            const char *state = snap(nck + (k - k0));
+            const char *state = stretch(b, k - k0);
             double phz = 0.0, phy = 0.0;
             laser_time_factors(unit, ((double)(step0 + k) + 0.5) * c->dt, &phz, &phy);
             ACK(with_real(c, [&](auto z) -> cudaError_t {
@@ -2805,8 +2846,11 @@ pic_status_t pic_adjoint(void *ctx, int nsteps, int checkpoint_every, const pic_
             }));
             c->launches += 4 + nsp;
         }
+        ACK(cudaEventRecord(freed[b], st));
     }
-    // the context ends in the final forward state
+    // the context ends in the final forward state (after the last recompute)
+    ACK(cudaEventRecord(ready[0], s2));
+    ACK(cudaStreamWaitEvent(st, ready[0], 0));
     ARET(snap_copy(c, L, n, final_state, false, st));
     c->step = step0 + nsteps;
     double g = 0.0;
