@@ -79,8 +79,11 @@ DEFAULT_SORT_EVERY = {2: 32, 3: 2}
 # tile range), re-binned every DEFAULT_REBIN_EVERY steps
 DEFAULT_BINS = (25, 16)
 DEFAULT_REBIN_EVERY = 64
-KERNEL = {2: ("k_step_fused", ("k_particles.cu", "pic_device.cuh", "pic_ptx.cuh")),
-          3: ("k_step_fused3", ("k_particles3.cu", "pic_device3.cuh", "pic_step3.cuh", "pic_device.cuh", "pic_ptx.cuh"))}
+# the fused kernel of each dimension and the sources its DRAM traffic depends
+# on (the kernel, its headers, and the sort, whose in-tile order it reads in)
+KERNEL = {2: ("k_step_fused", ("k_particles.cu", "pic_device.cuh", "pic_ptx.cuh", "k_sort.cu")),
+          3: ("k_step_fused3", ("k_particles3.cu", "pic_device3.cuh", "pic_step3.cuh", "pic_device.cuh", "pic_ptx.cuh",
+                                "k_sort.cu"))}
 
 
 def parse(argv=None):
