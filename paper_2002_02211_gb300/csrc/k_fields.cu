@@ -31,6 +31,55 @@ __global__ void __launch_bounds__(256) k_b_half(const MeshParams<R> m, R hdx, R 
     if (i < m.nx) b_half_cell(m, i, blockIdx.y, hdx, hdy);
 }
 
+// The same for float, four cells of a row per thread with 16-byte loads and
+// stores (ld is a multiple of 32; cells past nx keep their values).  The x + 1
+// neighbour of the group's last cell is the next group's first, or at the
+// row's end the wrapped column 0 (periodic x; By, Bz of the last column are
+// left to the boundary stage otherwise).
+__global__ void __launch_bounds__(128) k_b_half_f4(const MeshParams<float> m, float hdx, float hdy) {
+    const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int j = blockIdx.y;
+    if (i0 >= m.nx) return;
+    const int jp = j + 1 == m.ny ? 0 : j + 1;
+    const size_t P = m.plane, r0 = (size_t)j * m.ld;
+    const size_t c = r0 + i0, cjp = (size_t)jp * m.ld + i0;
+    float *EB = m.EB;
+    auto ld4 = [&](size_t o) { return *reinterpret_cast<const float4 *>(EB + o); };
+    auto arr = [](const float4 v, float a[4]) { a[0] = v.x, a[1] = v.y, a[2] = v.z, a[3] = v.w; };
+    float ex[4], ey[4], ez[4], ezjp[4], exjp[4], bx[4], by[4], bz[4];
+    arr(ld4(c), ex);
+    arr(ld4(P + c), ey);
+    arr(ld4(2 * P + c), ez);
+    arr(ld4(2 * P + cjp), ezjp);
+    arr(ld4(cjp), exjp);
+    arr(ld4(3 * P + c), bx);
+    arr(ld4(4 * P + c), by);
+    arr(ld4(5 * P + c), bz);
+    const bool periodic = m.bc_x == 1;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int i = i0 + q;
+        if (i >= m.nx) break;
+        bx[q] -= hdy * (ezjp[q] - ez[q]);
+        if (i < m.nx - 1 || periodic) {
+            float eyn, ezn;  // Ey, Ez at the x + 1 neighbour
+            if (i + 1 < m.nx && q < 3) {
+                eyn = ey[q + 1];
+                ezn = ez[q + 1];
+            } else {
+                const size_t cn = r0 + (i + 1 < m.nx ? i + 1 : 0);
+                eyn = EB[P + cn];
+                ezn = EB[2 * P + cn];
+            }
+            by[q] += hdx * (ezn - ez[q]);
+            bz[q] -= hdx * (eyn - ey[q]) - hdy * (exjp[q] - ex[q]);
+        }
+    }
+    *reinterpret_cast<float4 *>(EB + 3 * P + c) = make_float4(bx[0], bx[1], bx[2], bx[3]);
+    *reinterpret_cast<float4 *>(EB + 4 * P + c) = make_float4(by[0], by[1], by[2], by[3]);
+    *reinterpret_cast<float4 *>(EB + 5 * P + c) = make_float4(bz[0], bz[1], bz[2], bz[3]);
+}
+
 // boundary B at t^{n+1/2}: the incoming characteristic is the laser at x_min
 // and zero at x_max, imposed on time-centred values with E^{n+1} from its own
 // update including the transverse term dBx = Bx(j+1/2) - Bx(j-1/2) (r = dt/dx,
@@ -159,6 +208,64 @@ __global__ void k_batch_advance(long long *step, const long long *nsteps, int nr
     if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0;
 }
 
+// E <- E + dt (curl B - J), then J <- 0, for float: four cells of a row per
+// thread as k_b_half_f4; each cell's x - 1 neighbour is the previous cell of
+// the group, the previous group's last, or for column 0 the row's last cell
+// (periodic x) or the boundary value.
+__global__ void __launch_bounds__(128) k_e_full_f4(const MeshParams<float> m, const float *bnd, float dt,
+                                                   float dtdx, float dtdy) {
+    const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int j = blockIdx.y;
+    if (i0 >= m.nx) return;
+    const int jm = j == 0 ? m.ny - 1 : j - 1;
+    const size_t P = m.plane, r0 = (size_t)j * m.ld;
+    const size_t c = r0 + i0, cjm = (size_t)jm * m.ld + i0;
+    float *EB = m.EB, *J = m.J;
+    auto ld4 = [](const float *p) { return *reinterpret_cast<const float4 *>(p); };
+    auto arr = [](const float4 v, float a[4]) { a[0] = v.x, a[1] = v.y, a[2] = v.z, a[3] = v.w; };
+    float bx[4], by[4], bz[4], bzjm[4], bxjm[4], ex[4], ey[4], ez[4], jx[4], jy[4], jz[4];
+    arr(ld4(EB + 3 * P + c), bx);
+    arr(ld4(EB + 4 * P + c), by);
+    arr(ld4(EB + 5 * P + c), bz);
+    arr(ld4(EB + 5 * P + cjm), bzjm);
+    arr(ld4(EB + 3 * P + cjm), bxjm);
+    arr(ld4(EB + c), ex);
+    arr(ld4(EB + P + c), ey);
+    arr(ld4(EB + 2 * P + c), ez);
+    arr(ld4(J + c), jx);
+    arr(ld4(J + P + c), jy);
+    arr(ld4(J + 2 * P + c), jz);
+    float by_im, bz_im;  // By, Bz at the x - 1 neighbour of the group's first cell
+    if (i0 > 0) {
+        by_im = EB[4 * P + c - 1];
+        bz_im = EB[5 * P + c - 1];
+    } else if (m.bc_x == 1) {
+        by_im = EB[4 * P + r0 + m.nx - 1];
+        bz_im = EB[5 * P + r0 + m.nx - 1];
+    } else {
+        by_im = bnd[j];
+        bz_im = bnd[m.ny + j];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (i0 + q >= m.nx) break;
+        if (q > 0) {
+            by_im = by[q - 1];
+            bz_im = bz[q - 1];
+        }
+        ex[q] += dtdy * (bz[q] - bzjm[q]) - dt * jx[q];
+        ey[q] += -dtdx * (bz[q] - bz_im) - dt * jy[q];
+        ez[q] += dtdx * (by[q] - by_im) - dtdy * (bx[q] - bxjm[q]) - dt * jz[q];
+        jx[q] = jy[q] = jz[q] = 0.f;
+    }
+    *reinterpret_cast<float4 *>(EB + c) = make_float4(ex[0], ex[1], ex[2], ex[3]);
+    *reinterpret_cast<float4 *>(EB + P + c) = make_float4(ey[0], ey[1], ey[2], ey[3]);
+    *reinterpret_cast<float4 *>(EB + 2 * P + c) = make_float4(ez[0], ez[1], ez[2], ez[3]);
+    *reinterpret_cast<float4 *>(J + c) = make_float4(jx[0], jx[1], jx[2], jx[3]);
+    *reinterpret_cast<float4 *>(J + P + c) = make_float4(jy[0], jy[1], jy[2], jy[3]);
+    *reinterpret_cast<float4 *>(J + 2 * P + c) = make_float4(jz[0], jz[1], jz[2], jz[3]);
+}
+
 }  // namespace
 
 template <typename R>
@@ -195,15 +302,25 @@ cudaError_t launch_field_update(const MeshParams<R> &m, R *bnd, const double *pr
                                 double dt, double dx, double dy, long long step, cudaStream_t st,
                                 const double *lf_dev) {
     const dim3 blk(256), grd((m.nx + 255) / 256, m.ny);
+    const dim3 blk4(128), grd4((m.nx + 4 * 128 - 1) / (4 * 128), m.ny);
     const R hdx = (R)(0.5 * dt / dx), hdy = (R)(0.5 * dt / dy);
-    k_b_half<R><<<grd, blk, 0, st>>>(m, hdx, hdy);
+    auto b_half = [&]() {
+        if constexpr (sizeof(R) == 4)
+            k_b_half_f4<<<grd4, blk4, 0, st>>>(m, hdx, hdy);
+        else
+            k_b_half<R><<<grd, blk, 0, st>>>(m, hdx, hdy);
+    };
+    b_half();
     if (m.bc_x == 0) {
         double fz, fy;
         laser_time_factors(L, ((double)step + 0.5) * dt, &fz, &fy);
         k_boundary<R><<<(m.ny + 127) / 128, 128, 0, st>>>(m, bnd, prof, fz, fy, dt / dx, dt / dy, lf_dev);
     }
-    k_e_full<R><<<grd, blk, 0, st>>>(m, bnd, (R)dt, (R)(dt / dx), (R)(dt / dy));
-    k_b_half<R><<<grd, blk, 0, st>>>(m, hdx, hdy);
+    if constexpr (sizeof(R) == 4)
+        k_e_full_f4<<<grd4, blk4, 0, st>>>(m, bnd, (R)dt, (R)(dt / dx), (R)(dt / dy));
+    else
+        k_e_full<R><<<grd, blk, 0, st>>>(m, bnd, (R)dt, (R)(dt / dx), (R)(dt / dy));
+    b_half();
     return cudaGetLastError();
 }
 
