@@ -185,18 +185,18 @@ __device__ __forceinline__ bool fused_tile(const StepParams<R> &P, const CUtenso
         if (!S.mobile) continue;
         const int beg = S.tile_start[tile], len = S.tile_start[tile + 1] - beg;
         const R qm = S.qm, a = S.a, q = S.q;
-        R dacc[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
-        R dlo = R(0), dhi = R(0), dm = R(0), dshift = R(0);
+        double *drow = sdiag[tid >> 5];  // this warp's Eq. (4) sums of the species (lanes 4 q add sum q)
         if (diag) {
-            dlo = (R)P.diag.lo[sp];
-            dhi = (R)P.diag.hi[sp];
-            dm = (R)P.diag.m_mev[sp];
-            dshift = (R)P.diag.shift[sp];
+            if ((tid & 31) < 8) drow[tid & 31] = 0.0;
+            __syncwarp();
         }
         if (sp != first) prefetch(S, beg + tid, tid < len);
         for (int k0 = 0; k0 < len; k0 += kFusedThreads) {
             const int k = k0 + tid;
             cp_async_wait0();
+            // this lane's contribution to the Eq. (4) sums, summed over the warp below
+            bool dhas = false;
+            R dw = R(0), du[3] = {R(0), R(0), R(0)}, ds[3] = {R(0), R(0), R(0)};
             if (k < len) {
                 const int slot = beg + k;
                 const R *r = ring0;
@@ -247,17 +247,10 @@ __device__ __forceinline__ bool fused_tile(const StepParams<R> &P, const CUtenso
                                   spn[1] * spn[1] + spn[2] * spn[2];
                     bad |= !isfinite(chk);
                     if (diag && alive) {
-                        const R e = ekin_mev(dm, u[0], u[1], u[2]);
-                        if (e >= dlo && e < dhi) {
-                            const R ep = e - dshift;
-                            dacc[0] += w;
-                            dacc[1] += w * spn[0];
-                            dacc[2] += w * spn[1];
-                            dacc[3] += w * spn[2];
-                            dacc[4] += w * ep;
-                            dacc[5] += w * ep * ep;
-                            dacc[6] += R(1);
-                        }
+                        dhas = true;
+                        dw = w;
+#pragma unroll
+                        for (int d3 = 0; d3 < 3; ++d3) du[d3] = u[d3], ds[d3] = spn[d3];
                     }
                     S.cell[slot] = alive ? pack_cell(ix1, iy1) : PIC_DEAD;
                     S.ox[slot] = ox1;
@@ -270,24 +263,10 @@ __device__ __forceinline__ bool fused_tile(const StepParams<R> &P, const CUtenso
                     S.sz[slot] = spn[2];
                 }
             }
+            if (diag) diag_warp(P.diag, sp, dhas, dw, du, ds, drow);
         }
         cp_async_wait0();
-        if (diag) {
-            // converged here: warp shuffles in double, then one row per CTA
-            const int lane = tid & 31, wid = tid >> 5;
-            for (int qd = 0; qd < 7; ++qd) {
-                double v = (double)dacc[qd];
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
-                if (lane == 0) sdiag[wid][qd] = v;
-            }
-            __syncthreads();
-            if (tid < 7) {
-                double t = 0.0;
-                for (int w8 = 0; w8 < kFusedThreads / 32; ++w8) t += sdiag[w8][tid];
-                P.diag.rows[((size_t)sp * 8 + tid) * ntiles + tile] = t;
-            }
-            __syncthreads();
-        }
+        if (diag) store_diag_sums(P.diag, sp, sdiag, kFusedThreads / 32, tile, ntiles);
     }
     acc_flush();
     if (bad) atomicOr(P.err, PIC_EF_NAN);
@@ -308,8 +287,7 @@ __device__ __forceinline__ bool fused_tile(const StepParams<R> &P, const CUtenso
 }
 
 template <int TX, int TY, typename R, bool DIAG>
-__global__ void __launch_bounds__(kFusedThreads,
-                                  DIAG ? (sizeof(R) == 4 ? PIC_FUSED_MINB : 2) : TileConst<TX, TY, R>::minb_nodiag)
+__global__ void __launch_bounds__(kFusedThreads, TileConst<TX, TY, R>::minb_nodiag)
     k_step_fused(const __grid_constant__ StepParams<R> P, const __grid_constant__ CUtensorMap tmapEB) {
     extern __shared__ __align__(1024) unsigned char dsm[];
     __shared__ __align__(8) uint64_t bar;

@@ -36,19 +36,6 @@ struct TileConst3 : WinConst3<TX, TY, TZ, R> {
         sizeof(R) == 8 ? 1 : (smem_ctas >= PIC3_MINB ? PIC3_MINB : (smem_ctas >= 3 ? 3 : 2));
 };
 
-// column `col` of the CTA's FP64 sums of species sp, kept per warp in sdiag
-// (ncols columns per row); the whole CTA calls it
-__device__ __forceinline__ void store_diag_sums3(const DiagParams &D, int sp, double (*sdiag)[8], int col, int ncols) {
-    __syncthreads();
-    const int tid = threadIdx.x;
-    if (tid < 7) {
-        double t = 0.0;
-        for (int w8 = 0; w8 < kThreads3 / 32; ++w8) t += sdiag[w8][tid];
-        D.rows[((size_t)sp * 8 + tid) * ncols + col] = t;
-    }
-    __syncthreads();
-}
-
 // column `col` of the per-CTA sums of species sp (FP64 warp shuffles), ncols
 // columns per row; the whole CTA calls it
 template <typename R>
@@ -131,7 +118,7 @@ __global__ void __launch_bounds__(kThreads3) k_overflow3(const StepParams3<R> P)
                 }
                 bad |= !finite3(u) || !finite3(spn);
                 if (finish_move3(m, ix1, iy1, iz1)) {
-                    if (diag) diag_add3(dacc, dm, dlo, dhi, dshift, w, u, spn);
+                    if (diag) diag_add(dacc, dm, dlo, dhi, dshift, w, u, spn);
                     dest = bin_dest3<TX, TY, TZ>(m, P.t, ix1, iy1, iz1, P.err, P.bin[sp].txo);
                     cw = pack_cell3(ix1, iy1, iz1);
                     v[0] = ox1, v[1] = oy1, v[2] = oz1, v[3] = u[0], v[4] = u[1], v[5] = u[2];
@@ -307,9 +294,11 @@ __global__ void __launch_bounds__(kThreads3, (TileConst3<TX, TY, TZ, R>::minb))
         const BinRange rg = range(sp);
         const int len = rg.len;
         const R qm = S.qm, a = S.a, q = S.q;
-        double *drow = sdiag[tid >> 5];  // this warp's Eq. (4) sums of the species (lane 0 only)
-        if (diag && (tid & 31) == 0)
-            for (int q = 0; q < 8; ++q) drow[q] = 0.0;
+        double *drow = sdiag[tid >> 5];  // this warp's Eq. (4) sums of the species (lanes 4 q add sum q)
+        if (diag) {
+            if ((tid & 31) < 8) drow[tid & 31] = 0.0;
+            __syncwarp();
+        }
         if (sp != first) prefetch(S, tid < len ? bin_slot(rg, tid) : 0, tid < len);
         for (int k0 = 0; k0 < len; k0 += kThreads3) {
             const int k = k0 + tid;
@@ -380,7 +369,7 @@ __global__ void __launch_bounds__(kThreads3, (TileConst3<TX, TY, TZ, R>::minb))
                         bv[6] = spn[0], bv[7] = spn[1], bv[8] = spn[2], bv[9] = w;
                     }
                 }
-                if constexpr (DIAG) diag_warp3(P.diag, sp, dhas, w, u, spn, drow);
+                if constexpr (DIAG) diag_warp(P.diag, sp, dhas, w, u, spn, drow);
                 bin_store3(P.bin[sp], S.tile_start, (int)gridDim.x, own(sp), &s_front[sp], dest, bcell, bv, id, P.err,
                            rg.beg);
             } else {
@@ -458,12 +447,12 @@ __global__ void __launch_bounds__(kThreads3, (TileConst3<TX, TY, TZ, R>::minb))
                         S.sz[slot] = spn[2];
                     }
                 }
-                if constexpr (DIAG) diag_warp3(P.diag, sp, dhas, dw, du, ds, drow);
+                if constexpr (DIAG) diag_warp(P.diag, sp, dhas, dw, du, ds, drow);
             }
         }
         cp_async_wait0();
         if (diag)  // diagnostic columns: the tiles, then (binned) the overflow CTAs
-            store_diag_sums3(P.diag, sp, sdiag, (int)blockIdx.x, (int)gridDim.x + (BIN ? P.nextra : 0));
+            store_diag_sums(P.diag, sp, sdiag, kThreads3 / 32, (int)blockIdx.x, (int)gridDim.x + (BIN ? P.nextra : 0));
     }
     if (bad) atomicOr(P.err, PIC_EF_NAN);
     __syncthreads();

@@ -63,56 +63,4 @@ __device__ __forceinline__ int bin_dest3(const MeshParams3<R> &m, const TileGeom
     return tile_of3<TX, TY, TZ>(t, ix, iy, iz, txo);
 }
 
-// Eq. (4) sums of the particles in the window [dlo, dhi) MeV
-template <typename R>
-__device__ __forceinline__ void diag_add3(R dacc[7], R dm, R dlo, R dhi, R dshift, R w, const R u[3],
-                                          const R spn[3]) {
-    const R e = ekin_mev(dm, u[0], u[1], u[2]);
-    if (e >= dlo && e < dhi) {
-        const R ep = e - dshift;
-        dacc[0] += w;
-        dacc[1] += w * spn[0];
-        dacc[2] += w * spn[1];
-        dacc[3] += w * spn[2];
-        dacc[4] += w * ep;
-        dacc[5] += w * ep * ep;
-        dacc[6] += R(1);
-    }
-}
-
-// Fused kernel, steps with the Eq. (4) sums: one record per lane, summed
-// over the warp at once (float shuffles) and added to the warp's FP64 row of
-// sdiag, so no accumulator stays live across the particle loop.  All 32 lanes
-// of the warp call it together.
-template <typename R>
-__device__ __forceinline__ void diag_warp3(const DiagParams &D, int sp, bool has, R w, const R u[3], const R spn[3],
-                                           double *row) {
-    constexpr unsigned kAll = 0xFFFFFFFFu;
-    R c[8] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
-    if (has) diag_add3(c, (R)D.m_mev[sp], (R)D.lo[sp], (R)D.hi[sp], (R)D.shift[sp], w, u, spn);
-    if (!__any_sync(kAll, c[6] != R(0))) return;
-    // the 8 slots (7 sums and a zero) over the warp in 9 shuffles: across lane
-    // bits 4, 3 and 2 each lane keeps the half of its slots that bit selects
-    // and adds its partner's copy of that half; then bits 1 and 0 sum the one
-    // slot left, which lane 4 q ends up holding for slot q
-    const int lane = threadIdx.x & 31;
-    const bool h4 = (lane >> 4) & 1, h3 = (lane >> 3) & 1, h2 = (lane >> 2) & 1;
-    R c4[4], c2[2];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const R keep = h4 ? c[4 + k] : c[k], give = h4 ? c[k] : c[4 + k];
-        c4[k] = keep + __shfl_xor_sync(kAll, give, 16);
-    }
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const R keep = h3 ? c4[2 + k] : c4[k], give = h3 ? c4[k] : c4[2 + k];
-        c2[k] = keep + __shfl_xor_sync(kAll, give, 8);
-    }
-    R v = (h2 ? c2[1] : c2[0]) + __shfl_xor_sync(kAll, h2 ? c2[0] : c2[1], 4);
-    v += __shfl_xor_sync(kAll, v, 2);
-    v += __shfl_xor_sync(kAll, v, 1);
-    const int q = lane >> 2;  // = 4 h4 + 2 h3 + h2
-    if ((lane & 3) == 0 && q < 7) row[q] += (double)v;
-}
-
 }  // namespace
