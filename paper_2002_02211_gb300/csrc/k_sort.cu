@@ -97,6 +97,7 @@ struct Key2 {
     }
     int cells() const { return 1 << (sx + sy); }
     int tiles() const { return nt; }
+    int ntiles_x() const { return ntx; }
 };
 
 struct Key3 {
@@ -118,6 +119,7 @@ struct Key3 {
     }
     int cells() const { return 1 << (sx + sy + sz); }
     int tiles() const { return nt; }
+    int ntiles_x() const { return ntx; }
 };
 
 // per-cell counts and each particle's rank inside its cell (-1: removed)
@@ -273,43 +275,110 @@ cudaError_t scan_tiles(const int32_t *count, int nt, int32_t *start, int32_t *sc
     return cudaGetLastError();
 }
 
+// slot of the r-th particle of cell `key` within its tile's range
+template <class K>
+__device__ __forceinline__ int slot_in_tile(int key, int tile, int r, const int32_t *tile_R, const int32_t *cell_off,
+                                            const int32_t *cell_count, int C) {
+    const int lc = key - tile * C, Rl = tile_R[tile];
+    if (r < Rl) return r * C + lc;
+    int i = cell_off[key] + (r - Rl);  // place in the tail, cell by cell
+    // the tail dealt into S interleaved runs, so that the particles of one
+    // cell (consecutive in the tail) land in different warps and a warp's
+    // lanes rarely share a cell: their shared-memory atomics then do not
+    // collide on one address.  Measured fastest: S = 4 of 2, 3, 4, 6, 8, 16
+    // for 3D3V at 2 per cell, S = 8 of 2, 4, 8 for 2D3V at 8 + 8 per cell (a
+    // fifth off its fused kernel)
+    constexpr int S = K::kTailRuns;
+    const int last = (tile + 1) * C - 1;
+    const int T = cell_off[last] + cell_count[last] - Rl;
+    if (T >= 64 * S) {
+        const int m = i % S, q = i / S;
+        i = m * (T / S) + min(m, T % S) + q;
+    }
+    return Rl * C + i;
+}
+
+// every particle to its slot; range: nullptr (all *src.n slots) or a device
+// pair [range[0], range[1]) of source slots
 template <typename R, int NF, class K>
 __global__ void k_scatter(const SortArrays<R> src, const SortArrays<R> dst, const K kf, const int32_t *rank,
                           const int32_t *tile_start, const int32_t *tile_R, const int32_t *cell_off,
-                          const int32_t *cell_count, int C) {
-    const int n = *src.n;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+                          const int32_t *cell_count, int C, const int32_t *range) {
+    const long long p0 = range ? range[0] : 0, n = range ? range[1] : *src.n;
+    for (long long p = p0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
         const int r = rank[p];
         if (r < 0) continue;
         const uint32_t c = src.cell[p];
         int tile;
         const int key = kf(c, tile);
-        const int lc = key - tile * C, Rl = tile_R[tile];
-        int pos;
-        if (r < Rl) {
-            pos = r * C + lc;
-        } else {
-            int i = cell_off[key] + (r - Rl);  // place in the tail, cell by cell
-            // the tail dealt into S interleaved runs, so that the particles
-            // of one cell (consecutive in the tail) land in different warps
-            // and a warp's lanes rarely share a cell: their shared-memory
-            // atomics then do not collide on one address.  Measured fastest:
-            // S = 4 of 2, 3, 4, 6, 8, 16 for 3D3V at 2 per cell, S = 8 of 2,
-            // 4, 8 for 2D3V at 8 + 8 per cell (a fifth off its fused kernel)
-            constexpr int S = K::kTailRuns;
-            const int last = (tile + 1) * C - 1;
-            const int T = cell_off[last] + cell_count[last] - Rl;
-            if (T >= 64 * S) {
-                const int m = i % S, q = i / S;
-                i = m * (T / S) + min(m, T % S) + q;
-            }
-            pos = Rl * C + i;
-        }
-        pos += tile_start[tile];
+        const int pos = tile_start[tile] + slot_in_tile<K>(key, tile, r, tile_R, cell_off, cell_count, C);
         dst.cell[pos] = c;
 #pragma unroll
         for (int k = 0; k < NF; ++k) dst.f[k][pos] = src.f[k][p];
         dst.id[pos] = src.id[p];
+    }
+}
+
+// Re-bin of a sealed binned source, one CTA per tile t: the particles of its
+// source range (old_start, relabelled by txo) go into shared memory at their
+// slots, and the tile's new range is written in slot order (coalesced).  A
+// tile with more than cap particles, or a particle of another tile (none in
+// a sealed binned layout), is written directly.  Slots the CTA did not fill
+// (the tile's particles in the overflow range, scattered after this kernel)
+// are not written.
+// (no cell word takes this value: 3D3V needs nz <= 1020, 2D3V ix, iy < 2^15)
+constexpr uint32_t kSlotEmpty = 0xFFFFFFFEu;
+
+template <typename R, int NF, class K>
+__global__ void __launch_bounds__(256) k_scatter_tiles(const SortArrays<R> src, const SortArrays<R> dst, const K kf,
+                                                       const int32_t *rank, const int32_t *old_start, int txo,
+                                                       int ntx, const int32_t *tile_start, const int32_t *tile_R,
+                                                       const int32_t *cell_off, const int32_t *cell_count, int C,
+                                                       int cap) {
+    extern __shared__ __align__(16) unsigned char sm_rec[];
+    uint32_t *scell = reinterpret_cast<uint32_t *>(sm_rec);
+    int32_t *sid = reinterpret_cast<int32_t *>(scell + cap);
+    R *sf = reinterpret_cast<R *>(sid + cap);  // cap is a multiple of 4: 16-byte aligned
+    const int t = blockIdx.x, tx = t % ntx;
+    const int r = t - tx + bin_rot_x(tx, ntx, txo);
+    const int os = old_start[r], oe = old_start[r + 1];
+    const int ns = tile_start[t];
+    const int last = (t + 1) * C - 1, Rl = tile_R[t];
+    const int cnt = Rl * C + cell_off[last] + cell_count[last] - Rl;
+    const bool staged = cnt <= cap;
+    if (staged)
+        for (int j = threadIdx.x; j < cnt; j += blockDim.x) scell[j] = kSlotEmpty;
+    __syncthreads();
+    for (int i = os + threadIdx.x; i < oe; i += blockDim.x) {
+        const int rk = rank[i];
+        if (rk < 0) continue;
+        const uint32_t c = src.cell[i];
+        int tile;
+        const int key = kf(c, tile);
+        const int pos = slot_in_tile<K>(key, tile, rk, tile_R, cell_off, cell_count, C);
+        if (staged && tile == t) {
+            scell[pos] = c;
+            sid[pos] = src.id[i];
+#pragma unroll
+            for (int k = 0; k < NF; ++k) sf[k * cap + pos] = src.f[k][i];
+        } else {
+            const int g = tile_start[tile] + pos;
+            dst.cell[g] = c;
+            dst.id[g] = src.id[i];
+#pragma unroll
+            for (int k = 0; k < NF; ++k) dst.f[k][g] = src.f[k][i];
+        }
+    }
+    if (!staged) return;
+    __syncthreads();
+    for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+        const uint32_t c = scell[j];
+        if (c == kSlotEmpty) continue;
+        dst.cell[ns + j] = c;
+        dst.id[ns + j] = sid[j];
+#pragma unroll
+        for (int k = 0; k < NF; ++k) dst.f[k][ns + j] = sf[k * cap + j];
     }
 }
 
@@ -431,12 +500,41 @@ cudaError_t tile_sort(const SortArrays<R> &src, const SortArrays<R> &dst, const 
     cudaError_t e = cudaMemsetAsync(w.cell_count, 0, sizeof(int32_t) * (size_t)nt * C, st);
     if (e != cudaSuccess) return e;
     const int g = grid_for(n_upper);
+    const bool tiled = bins.cnt_to && bins.from_binned && bins.old_start;
+    if (tiled) {
+        // the source ranges, before the scan below replaces them
+        e = cudaMemcpyAsync(bins.old_start, tile_start, sizeof(int32_t) * (size_t)(nt + 2), cudaMemcpyDeviceToDevice,
+                            st);
+        if (e != cudaSuccess) return e;
+    }
     k_rank<K><<<g, 256, 0, st>>>(src.cell, src.n, key, w.cell_count, w.rank);
     k_layout<<<nt, C, 0, st>>>(w.cell_count, C, w.cell_off, w.tile_R, w.tile_total, bins);
     e = scan_tiles(w.tile_total, bins.cnt_to ? nt + 1 : nt, tile_start, w.cursor, n_tmp, st);
     if (e != cudaSuccess) return e;
-    k_scatter<R, NF, K><<<g, 256, 0, st>>>(src, dst, key, w.rank, tile_start, w.tile_R, w.cell_off, w.cell_count,
-                                           C);
+    if (tiled) {
+        // tiles through shared memory (96 KB: 2 CTAs per SM), then the
+        // overflow range's particles directly
+        constexpr int kRecBytes = 8 + NF * (int)sizeof(R);
+        const int cap = (96 * 1024 / kRecBytes) / 4 * 4;
+        const size_t smem = (size_t)cap * kRecBytes;
+        static bool attr_set = false;
+        if (!attr_set) {
+            e = cudaFuncSetAttribute(k_scatter_tiles<R, NF, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
+            if (e != cudaSuccess) return e;
+            attr_set = true;
+        }
+        k_scatter_tiles<R, NF, K><<<nt, 256, smem, st>>>(src, dst, key, w.rank, bins.old_start, bins.txo,
+                                                         key.ntiles_x(), tile_start, w.tile_R, w.cell_off,
+                                                         w.cell_count, C, cap);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_scatter<R, NF, K><<<g, 256, 0, st>>>(src, dst, key, w.rank, tile_start, w.tile_R, w.cell_off,
+                                               w.cell_count, C, bins.old_start + nt);
+    } else {
+        k_scatter<R, NF, K><<<g, 256, 0, st>>>(src, dst, key, w.rank, tile_start, w.tile_R, w.cell_off,
+                                               w.cell_count, C, nullptr);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (bins.cnt_to) {

@@ -133,6 +133,7 @@ struct Ctx {
     cudaEvent_t ahead_ev[kAhead] = {};
     long long ahead_k = 0;
     int32_t *bin_cnt[PIC_MAX_SPECIES][2] = {};
+    int32_t *old_start = nullptr;  // [ntiles + 2]: a re-bin's source ranges
     int64_t n_live[PIC_MAX_SPECIES] = {};
     // CTAs of the overflow-range kernel: one per 256 slots of the largest
     // overflow range, between kBinCtasMin and kBinCtasMax
@@ -519,6 +520,10 @@ pic_status_t sort_species(Ctx *c, int s, cudaStream_t st, bool compact_only = fa
         bins.extra = c->cfg.bin_min_extra;
         bins.cnt_to = c->bin_cnt[s][to];
         bins.cnt_from = c->bin_cnt[s][from];
+        // sealed above: a binned source re-bins tile by tile
+        bins.from_binned = c->sp_binned[s];
+        bins.txo = c->bin_txo[s];
+        bins.old_start = c->old_start;
     }
     CK(with_real(c, [&](auto z) {
         using T = decltype(z);
@@ -528,7 +533,9 @@ pic_status_t sort_species(Ctx *c, int s, cudaStream_t st, bool compact_only = fa
         return launch_tile_sort<T>(dev_species<T>(c, s, from), dev_species<T>(c, s, to), c->tg, w, c->tile_start[s],
                                    c->n_dev + PIC_MAX_SPECIES, c->n_upper[s], st);
     }));
-    c->launches += bin ? 7 : 6;  // rank, layout, three scan passes, scatter (, seal)
+    // rank, layout, three scan passes, scatter (binned: + seal; from a binned
+    // source the scatter is the per-tile one and the overflow range's)
+    c->launches += bin ? (bins.from_binned ? 8 : 7) : 6;
     c->cur[s] = to;
     c->bin_txo[s] = 0;
     if (bin) {
@@ -598,6 +605,9 @@ pic_status_t upload_particles(Ctx *c, int s, const PT *p, int64_t base, cudaStre
             if (!src[k]) return fail(c, PIC_ERR_ARG, "null particle array");
     }
     const size_t n = (size_t)p->n;
+    // the uploaded slots are in no tile order: the species is in the compact
+    // layout until the sort that follows an upload
+    c->sp_binned[s] = false;
     if (base == 0) {
         c->unsealed[s] = false;  // the upload replaces the layout
         c->live_pending[s] = false;
@@ -1138,6 +1148,8 @@ pic_status_t pic_create(const pic_config_t *cfg, void *stream, void **ctx_out) {
             c->ovf_alert = h;
             CKC(cudaHostGetDevicePointer(reinterpret_cast<void **>(&c->ovf_alert_dev), h, 0));
         }
+        if (c->binned && cfg->sp[s].mobile && !c->old_start)
+            CKC(cudaMalloc(&c->old_start, (c->ntiles + 2) * sizeof(int32_t)));
         if (c->binned && cfg->sp[s].mobile)
             for (int b = 0; b < 2; ++b) {
                 CKC(cudaMalloc(&c->bin_cnt[s][b], 4 * (c->ntiles + 1) * sizeof(int32_t)));
@@ -1198,6 +1210,7 @@ void pic_destroy(void *ctx) {
             free_own(c, c->buf[s][b].id);
         }
         cudaFree(c->tile_start[s]);
+        if (s == 0) cudaFree(c->old_start);
         cudaFree(c->bin_cnt[s][0]);
         cudaFree(c->bin_cnt[s][1]);
         cudaFree(c->cell_old[s]);

@@ -116,6 +116,13 @@ struct BinSort {
     int pct = 0, extra = 0, ovf_cap = 0;
     int32_t *cnt_to = nullptr;    // [4 (ntiles + 1)] range counters (Bin3) of the sorted buffer
     int32_t *cnt_from = nullptr;  // [4 (ntiles + 1)] of the source buffer, cleared
+    // a re-bin of a sealed binned source: every particle of source range r
+    // belongs to one tile (the tile-column relabelling txo maps it), so each
+    // tile is gathered by one CTA through shared memory and written in order;
+    // old_start ([ntiles + 2] scratch) keeps the source ranges
+    bool from_binned = false;
+    int txo = 0;
+    int32_t *old_start = nullptr;
 };
 // seal of the binned layout: slots outside each range's two segments ->
 // PIC_DEAD, and the other buffer's range counters cleared
