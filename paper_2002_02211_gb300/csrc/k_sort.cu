@@ -500,7 +500,7 @@ cudaError_t tile_sort(const SortArrays<R> &src, const SortArrays<R> &dst, const 
     cudaError_t e = cudaMemsetAsync(w.cell_count, 0, sizeof(int32_t) * (size_t)nt * C, st);
     if (e != cudaSuccess) return e;
     const int g = grid_for(n_upper);
-    const bool tiled = bins.cnt_to && bins.from_binned && bins.old_start;
+    const bool tiled = bins.src_ordered && bins.old_start;
     if (tiled) {
         // the source ranges, before the scan below replaces them
         e = cudaMemcpyAsync(bins.old_start, tile_start, sizeof(int32_t) * (size_t)(nt + 2), cudaMemcpyDeviceToDevice,
@@ -512,8 +512,8 @@ cudaError_t tile_sort(const SortArrays<R> &src, const SortArrays<R> &dst, const 
     e = scan_tiles(w.tile_total, bins.cnt_to ? nt + 1 : nt, tile_start, w.cursor, n_tmp, st);
     if (e != cudaSuccess) return e;
     if (tiled) {
-        // tiles through shared memory (96 KB: 2 CTAs per SM), then the
-        // overflow range's particles directly
+        // tiles through shared memory (96 KB: 2 CTAs per SM), then a binned
+        // source's overflow range directly
         constexpr int kRecBytes = 8 + NF * (int)sizeof(R);
         const int cap = (96 * 1024 / kRecBytes) / 4 * 4;
         const size_t smem = (size_t)cap * kRecBytes;
@@ -529,8 +529,9 @@ cudaError_t tile_sort(const SortArrays<R> &src, const SortArrays<R> &dst, const 
                                                          w.cell_count, C, cap);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        k_scatter<R, NF, K><<<g, 256, 0, st>>>(src, dst, key, w.rank, tile_start, w.tile_R, w.cell_off,
-                                               w.cell_count, C, bins.old_start + nt);
+        if (bins.src_binned)
+            k_scatter<R, NF, K><<<g, 256, 0, st>>>(src, dst, key, w.rank, tile_start, w.tile_R, w.cell_off,
+                                                   w.cell_count, C, bins.old_start + nt);
     } else {
         k_scatter<R, NF, K><<<g, 256, 0, st>>>(src, dst, key, w.rank, tile_start, w.tile_R, w.cell_off,
                                                w.cell_count, C, nullptr);
@@ -568,8 +569,8 @@ SortArrays<R> arrays3(const DevSpecies3<R> &S) {
 template <typename R>
 cudaError_t launch_tile_sort(const DevSpecies<R> &src, const DevSpecies<R> &dst, const TileGeom &t,
                              const SortScratch &w, int32_t *tile_start, int32_t *n_tmp, int n_upper,
-                             cudaStream_t st) {
-    return tile_sort<R, 9>(arrays2(src), arrays2(dst), Key2(t), w, tile_start, n_tmp, n_upper, BinSort{}, st);
+                             const BinSort &order, cudaStream_t st) {
+    return tile_sort<R, 9>(arrays2(src), arrays2(dst), Key2(t), w, tile_start, n_tmp, n_upper, order, st);
 }
 
 template <typename R>
@@ -588,10 +589,10 @@ template cudaError_t launch_tile_sort3<double>(const DevSpecies3<double> &, cons
 
 template cudaError_t launch_tile_sort<float>(const DevSpecies<float> &, const DevSpecies<float> &,
                                              const TileGeom &, const SortScratch &, int32_t *, int32_t *, int,
-                                             cudaStream_t);
+                                             const BinSort &, cudaStream_t);
 template cudaError_t launch_tile_sort<double>(const DevSpecies<double> &, const DevSpecies<double> &,
                                               const TileGeom &, const SortScratch &, int32_t *, int32_t *, int,
-                                              cudaStream_t);
+                                              const BinSort &, cudaStream_t);
 
 // element-wise precision conversion (host transfers of the FP64 instantiation)
 namespace {

@@ -133,7 +133,10 @@ struct Ctx {
     cudaEvent_t ahead_ev[kAhead] = {};
     long long ahead_k = 0;
     int32_t *bin_cnt[PIC_MAX_SPECIES][2] = {};
-    int32_t *old_start = nullptr;  // [ntiles + 2]: a re-bin's source ranges
+    int32_t *old_start = nullptr;  // [ntiles + 2]: a sort's source ranges
+    // the current buffer is the compact layout of the species' last sort, its
+    // slots unchanged since (the next sort can gather tile by tile)
+    bool tile_ordered[PIC_MAX_SPECIES] = {};
     int64_t n_live[PIC_MAX_SPECIES] = {};
     // CTAs of the overflow-range kernel: one per 256 slots of the largest
     // overflow range, between kBinCtasMin and kBinCtasMax
@@ -520,22 +523,25 @@ pic_status_t sort_species(Ctx *c, int s, cudaStream_t st, bool compact_only = fa
         bins.extra = c->cfg.bin_min_extra;
         bins.cnt_to = c->bin_cnt[s][to];
         bins.cnt_from = c->bin_cnt[s][from];
-        // sealed above: a binned source re-bins tile by tile
-        bins.from_binned = c->sp_binned[s];
-        bins.txo = c->bin_txo[s];
-        bins.old_start = c->old_start;
     }
+    // a source in the layout of the last sort (binned and sealed above, or
+    // compact with its slots unchanged) is gathered tile by tile
+    bins.src_binned = c->sp_binned[s];
+    bins.src_ordered = c->sp_binned[s] || c->tile_ordered[s];
+    bins.txo = c->bin_txo[s];
+    bins.old_start = c->old_start;
     CK(with_real(c, [&](auto z) {
         using T = decltype(z);
         if (c->dim == 3)
             return launch_tile_sort3<T>(dev_species3<T>(c, s, from), dev_species3<T>(c, s, to), c->tg3, w,
                                         c->tile_start[s], c->n_dev + PIC_MAX_SPECIES, c->n_upper[s], bins, st);
         return launch_tile_sort<T>(dev_species<T>(c, s, from), dev_species<T>(c, s, to), c->tg, w, c->tile_start[s],
-                                   c->n_dev + PIC_MAX_SPECIES, c->n_upper[s], st);
+                                   c->n_dev + PIC_MAX_SPECIES, c->n_upper[s], bins, st);
     }));
-    // rank, layout, three scan passes, scatter (binned: + seal; from a binned
-    // source the scatter is the per-tile one and the overflow range's)
-    c->launches += bin ? (bins.from_binned ? 8 : 7) : 6;
+    // rank, layout, three scan passes, scatter (a binned source's tiles and
+    // then its overflow range), the seal of a binned result
+    c->launches += 6 + (bins.src_binned ? 1 : 0) + (bin ? 1 : 0);
+    c->tile_ordered[s] = !bin;
     c->cur[s] = to;
     c->bin_txo[s] = 0;
     if (bin) {
@@ -608,6 +614,7 @@ pic_status_t upload_particles(Ctx *c, int s, const PT *p, int64_t base, cudaStre
     // the uploaded slots are in no tile order: the species is in the compact
     // layout until the sort that follows an upload
     c->sp_binned[s] = false;
+    c->tile_ordered[s] = false;
     if (base == 0) {
         c->unsealed[s] = false;  // the upload replaces the layout
         c->live_pending[s] = false;
@@ -712,6 +719,9 @@ pic_status_t retile(Ctx *c, int tx, int ty, cudaStream_t st) {
     cudaFree(c->tile_R);
     cudaFree(c->tile_cursor);
     cudaFree(c->diag_rows);
+    cudaFree(c->old_start);
+    c->old_start = nullptr;
+    for (int s = 0; s < PIC_MAX_SPECIES; ++s) c->tile_ordered[s] = false;  // the old tiles' order
     c->cfg.tile_x = tx;
     c->cfg.tile_y = ty;
     choose_tiles(c);
@@ -725,6 +735,7 @@ pic_status_t retile(Ctx *c, int tx, int ty, cudaStream_t st) {
     CK(cudaMalloc(&c->cell_off, cells * sizeof(int32_t)));
     CK(cudaMalloc(&c->tile_R, c->ntiles * sizeof(int32_t)));
     CK(cudaMalloc(&c->tile_cursor, c->ntiles * sizeof(int32_t)));
+    CK(cudaMalloc(&c->old_start, (c->ntiles + 2) * sizeof(int32_t)));
     CK(cudaMalloc(&c->diag_rows, (size_t)(c->ntiles + Ctx::kBinCtasMax) * PIC_MAX_SPECIES * 8 * sizeof(double)));
     pic_status_t r = make_tensor_map(c);
     if (r != PIC_OK) return r;
@@ -947,6 +958,7 @@ pic_status_t window_move(Ctx *c, int ncells, const Slab *slab, cudaStream_t st) 
                 }));
                 c->launches += 2;
                 c->n_upper[s] = (int)std::min<int64_t>((int64_t)c->n_upper[s] + m, c->cfg.sp[s].capacity);
+                c->tile_ordered[s] = false;  // appended after the last tile's range
             }
             sort[s] = true;
         }
@@ -1148,8 +1160,7 @@ pic_status_t pic_create(const pic_config_t *cfg, void *stream, void **ctx_out) {
             c->ovf_alert = h;
             CKC(cudaHostGetDevicePointer(reinterpret_cast<void **>(&c->ovf_alert_dev), h, 0));
         }
-        if (c->binned && cfg->sp[s].mobile && !c->old_start)
-            CKC(cudaMalloc(&c->old_start, (c->ntiles + 2) * sizeof(int32_t)));
+        if (!c->old_start) CKC(cudaMalloc(&c->old_start, (c->ntiles + 2) * sizeof(int32_t)));
         if (c->binned && cfg->sp[s].mobile)
             for (int b = 0; b < 2; ++b) {
                 CKC(cudaMalloc(&c->bin_cnt[s][b], 4 * (c->ntiles + 1) * sizeof(int32_t)));

@@ -116,11 +116,14 @@ struct BinSort {
     int pct = 0, extra = 0, ovf_cap = 0;
     int32_t *cnt_to = nullptr;    // [4 (ntiles + 1)] range counters (Bin3) of the sorted buffer
     int32_t *cnt_from = nullptr;  // [4 (ntiles + 1)] of the source buffer, cleared
-    // a re-bin of a sealed binned source: every particle of source range r
-    // belongs to one tile (the tile-column relabelling txo maps it), so each
-    // tile is gathered by one CTA through shared memory and written in order;
-    // old_start ([ntiles + 2] scratch) keeps the source ranges
-    bool from_binned = false;
+    // The source is the layout of the previous sort (its slots unchanged
+    // since, particles moved only within them): its tile ranges (relabelled
+    // by txo in the binned layout) hold that tile's particles, but for those
+    // that drifted, so each tile is gathered by one CTA through shared memory
+    // and its new range written in order; old_start ([ntiles + 2] scratch)
+    // keeps the source ranges.  src_binned: a sealed binned source, whose
+    // overflow range is scattered after the tiles.
+    bool src_ordered = false, src_binned = false;
     int txo = 0;
     int32_t *old_start = nullptr;
 };
@@ -149,7 +152,7 @@ cudaError_t launch_unpack_cells(const uint32_t *cell, int32_t *ix, int32_t *iy, 
 template <typename R>
 cudaError_t launch_tile_sort(const DevSpecies<R> &src, const DevSpecies<R> &dst, const TileGeom &t,
                              const SortScratch &w, int32_t *tile_start, int32_t *n_tmp, int n_upper,
-                             cudaStream_t st);
+                             const BinSort &order, cudaStream_t st);
 cudaError_t launch_pack_cells3(const int32_t *ix, const int32_t *iy, const int32_t *iz, uint32_t *cell, int n,
                                int xlo, int xhi, int ny, int nz, unsigned *err, cudaStream_t st);
 cudaError_t launch_unpack_cells3(const uint32_t *cell, int32_t *ix, int32_t *iy, int32_t *iz, int n,
