@@ -887,7 +887,7 @@ def main_latency(args):
     out = {}
     clk = None
     for mode, graphs in (("graphs", 32), ("launched", 0)):
-        with pic.Simulation(pic.config_from_workload(wl, sort_every=sort_every), stream=stream) as sim:
+        with pic.Simulation(pic.config_from_workload(wl, sort_every=sort_every, tile=args.tile), stream=stream) as sim:
             for s, d in enumerate(parts):
                 sim.set_particles(s, d)
             if wl.neutralizing_background:

@@ -94,7 +94,8 @@ typedef struct {
     pic_species_t sp[PIC_MAX_SPECIES];
     int sort_every;              /* steps between tile sorts in pic_step (0: 32)   */
     int tile_x, tile_y;          /* cells per tile: 8x4, 16x8, 32x8, 32x16 or 64x16 (0, 0: chosen
-                                    from the mesh size)                            */
+                                    from the mesh size: 32x8 from 2^19 cells, 16x8
+                                    from 77,824 (4 tiles per SM), else 8x4)         */
     int precision;               /* arithmetic of particles and mesh: 32 (the
                                     production path) or 64 (the FP64 instantiation
                                     of the same kernels); 0 means 32.  Reductions

@@ -376,9 +376,12 @@ void choose_tiles(Ctx *c) {
     }
     int tx = c->cfg.tile_x, ty = c->cfg.tile_y;
     if (tx <= 0 || ty <= 0) {
+        // large meshes: 32 x 8; small ones: 16 x 8, and below 4 CTAs of 16 x 8
+        // per SM, 8 x 4 (the L2-resident 256 x 128 run: 42.8 against 56.2 us
+        // a step replayed from graphs)
         const long long cells = (long long)c->cfg.nx * c->cfg.ny;
-        tx = cells >= (1LL << 19) ? 32 : 16;
-        ty = 8;
+        tx = cells >= (1LL << 19) ? 32 : (cells >= 152LL * 4 * 16 * 8 ? 16 : 8);
+        ty = tx == 8 ? 4 : 8;
     }
     // tile shapes the fused kernel is compiled for (pic_validate_config checks)
     c->tg.TX = tx;
