@@ -500,7 +500,9 @@ cudaError_t tile_sort(const SortArrays<R> &src, const SortArrays<R> &dst, const 
     cudaError_t e = cudaMemsetAsync(w.cell_count, 0, sizeof(int32_t) * (size_t)nt * C, st);
     if (e != cudaSuccess) return e;
     const int g = grid_for(n_upper);
-    const bool tiled = bins.src_ordered && bins.old_start;
+    // (one CTA a tile: a mesh of few tiles scatters faster over all slots,
+    // e.g. the small runs of a batch)
+    const bool tiled = bins.src_ordered && bins.old_start && nt >= 4 * 152;
     if (tiled) {
         // the source ranges, before the scan below replaces them
         e = cudaMemcpyAsync(bins.old_start, tile_start, sizeof(int32_t) * (size_t)(nt + 2), cudaMemcpyDeviceToDevice,

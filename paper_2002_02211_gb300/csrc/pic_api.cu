@@ -543,7 +543,7 @@ pic_status_t sort_species(Ctx *c, int s, cudaStream_t st, bool compact_only = fa
     }));
     // rank, layout, three scan passes, scatter (a binned source's tiles and
     // then its overflow range), the seal of a binned result
-    c->launches += 6 + (bins.src_binned ? 1 : 0) + (bin ? 1 : 0);
+    c->launches += 6 + (bins.src_binned && c->ntiles >= 4 * 152 ? 1 : 0) + (bin ? 1 : 0);
     c->tile_ordered[s] = !bin;
     c->cur[s] = to;
     c->bin_txo[s] = 0;
