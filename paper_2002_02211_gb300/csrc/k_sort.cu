@@ -1,19 +1,22 @@
 // k_sort.cu -- a7: counting sort of the particles of one species by tile,
 // laid out in layers inside each tile.  Removed particles are dropped.
 //
-// With C = TX * TY cells per tile and R = the smallest particle count of any
-// cell of the tile, slot r * C + c of the tile holds the r-th particle of
-// local cell c for r < R (every cell has at least R, so the layers have no
-// holes); the remaining particles follow in a tail, taken cell by cell and
-// dealt into a few interleaved runs, so that a warp's 32 consecutive slots
-// rarely hold two particles of one cell (after some motion most 3D3V tiles
-// have an empty cell, R = 0, and the whole tile is tail).  A CTA of C (or a
-// divisor of C) threads walking the tile meets the same cell on every pass
-// through the layers, which the 2D3V fused kernel uses to sum the in-cell
+// With C cells per tile and R = the smallest particle count of any cell of
+// the tile, slot r * C + c of the tile holds the r-th particle of local cell c
+// for r < R (every cell has at least R, so the layers have no holes).  The
+// remaining particles follow in a tail: first L depth layers (2D3V: L = 3),
+// layer d holding the (R + d)-th particle of every cell that has more than
+// R + d, in cell order, so a warp's 32 consecutive slots hold particles of 32
+// distinct cells of one or two rows; then the rest, cell by cell, dealt into
+// a few interleaved runs, so that a warp's lanes rarely share a cell there
+// either (3D3V: the whole tail, L = 0; after some motion most 3D3V tiles have
+// an empty cell, R = 0, and the whole tile is tail).  A CTA of C (or a divisor
+// of C) threads walking the tile meets the same cell on every pass through
+// the full layers, which the 2D3V fused kernel uses to sum the in-cell
 // currents in registers.  Steps: rank of each particle in its cell
-// (atomics), per-tile layout (block min and scan over the cells), exclusive
-// scan of the tile totals, scatter.  The 2D3V and 3D3V layouts differ only
-// in the cell packing and the tile key.
+// (atomics), per-tile layout (block minimum and scans over the cells),
+// exclusive scan of the tile totals, scatter.  The 2D3V and 3D3V layouts
+// differ in the cell packing, the tile key and the tail.
 #include "pic_device3.cuh"
 #include "pic_kernels.h"
 
@@ -87,7 +90,11 @@ __global__ void k_unpack3(const uint32_t *cell, int32_t *ix, int32_t *iy, int32_
 __host__ __device__ constexpr int log2i(int v) { return v <= 1 ? 0 : 1 + log2i(v >> 1); }
 
 struct Key2 {
-    static constexpr int kTailRuns = 8;  // interleaved runs of the tail (k_scatter)
+    // the tail: three depth layers (config 3's fused kernel 1.552 -> 1.520 ms
+    // against the whole tail dealt, 39.6 -> 40.3 G particle-steps/s; two: the
+    // same), then the rest dealt into eight runs
+    static constexpr int kTailLayers = 3;
+    static constexpr int kTailRuns = 8;
     int sx, sy, ntx, nt;  // log2 of the tile sizes, tiles along x, tiles
     explicit Key2(const TileGeom &t) : sx(log2i(t.TX)), sy(log2i(t.TY)), ntx(t.ntx), nt(t.ntx * t.nty) {}
     __device__ __forceinline__ int operator()(uint32_t c, int &tile) const {
@@ -101,6 +108,9 @@ struct Key2 {
 };
 
 struct Key3 {
+    // the whole tail dealt into four runs: depth layers left config 2's fused
+    // kernel unchanged (3.815 ms with three layers or none) and cost 0.3 ms a sort
+    static constexpr int kTailLayers = 0;
     static constexpr int kTailRuns = 4;
     int sx, sy, sz, ntx, nty, nt;
     explicit Key3(const TileGeom3 &t)
@@ -138,14 +148,22 @@ __global__ void k_rank(const uint32_t *cell, const int32_t *n_src, const K key, 
     }
 }
 
-// one CTA per tile, one thread per cell (C <= 1024): layer depth R (block
-// minimum of the counts), tail offset of each cell (exclusive scan of the
-// counts above R), tile total
-__global__ void __launch_bounds__(1024) k_layout(const int32_t *cell_count, int C, int32_t *cell_off,
-                                                 int32_t *tile_R, int32_t *tile_total, BinSort bins) {
-    __shared__ int32_t wmin[32], wsum[32];
+// one CTA per tile, one thread per cell (C <= 1024, a multiple of 32): the
+// full layers' depth R (block minimum of the counts); the tail's L depth
+// layers (layer d: the cells with more than R + d particles, an exclusive
+// scan over the cells each) and the rest (counts above R + L, an exclusive
+// scan).  Per cell: its places in the L layers, 10 bits each, written over
+// its count in cell_count, and its offset in the rest (cell_off).  Per tile
+// (tile_info, kTileInfo entries): R, the tile's particle count, the rest's
+// size and start, the layers' starts.
+template <int L>
+__global__ void __launch_bounds__(1024) k_layout(int32_t *cell_count, int C, int32_t *cell_off, int32_t *tile_info,
+                                                 int32_t *tile_total, BinSort bins) {
+    static_assert(L >= 0 && L <= 3 && 4 + L <= kTileInfo, "three 10-bit places per cell, kTileInfo entries");
+    __shared__ int32_t wmin[32], wsum[L + 1][32];
     const int t = blockIdx.x, c = threadIdx.x, lane = c & 31, wid = c >> 5, nw = (C + 31) >> 5;
-    const int cnt = cell_count[(size_t)t * C + c];
+    const size_t at = (size_t)t * C + c;
+    const int cnt = cell_count[at];
     int m = cnt;
     for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
     if (lane == 0) wmin[wid] = m;
@@ -153,19 +171,52 @@ __global__ void __launch_bounds__(1024) k_layout(const int32_t *cell_count, int 
     int R = wmin[0];
     for (int w = 1; w < nw; ++w) R = min(R, wmin[w]);
     const int ex = cnt - R;
-    int incl = ex;  // inclusive warp scan
-    for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= o) incl += v;
+    // v[q < L]: the cell has a particle in tail layer q; v[L]: its particles after them
+    int v[L + 1], incl[L + 1];
+#pragma unroll
+    for (int q = 0; q <= L; ++q) {
+        v[q] = q < L ? (ex > q ? 1 : 0) : max(ex - L, 0);
+        incl[q] = v[q];  // inclusive warp scan
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xFFFFFFFFu, incl[q], o);
+            if (lane >= o) incl[q] += u;
+        }
+        if (lane == 31) wsum[q][wid] = incl[q];
     }
-    if (lane == 31) wsum[wid] = incl;
     __syncthreads();
-    int base = 0;
-    for (int w = 0; w < wid; ++w) base += wsum[w];
-    cell_off[(size_t)t * C + c] = base + incl - ex;
+    int base[L + 1], tot[L + 1];
+#pragma unroll
+    for (int q = 0; q <= L; ++q) {
+        base[q] = tot[q] = 0;
+        for (int w = 0; w < nw; ++w) {
+            const int ws = wsum[q][w];
+            base[q] += w < wid ? ws : 0;
+            tot[q] += ws;
+        }
+    }
+    uint32_t places = 0;
+#pragma unroll
+    for (int q = 0; q < L; ++q) places |= (uint32_t)(base[q] + incl[q] - v[q]) << (10 * q);
+    cell_count[at] = (int32_t)places;
+    cell_off[at] = base[L] + incl[L] - v[L];
+    int lstart = 0;
+#pragma unroll
+    for (int q = 0; q < L; ++q) lstart += tot[q];
+    const int total = R * C + lstart + tot[L];
+    if (c == 0) {
+        int32_t *ti = tile_info + (size_t)t * kTileInfo;
+        ti[0] = R;
+        ti[1] = total;
+        ti[2] = tot[L];
+        ti[3] = lstart;
+        int ls = 0;
+#pragma unroll
+        for (int q = 0; q < L; ++q) {
+            ti[4 + q] = ls;
+            ls += tot[q];
+        }
+    }
     if (c == C - 1) {
-        const int total = R * C + base + incl;
-        tile_R[t] = R;
         if (bins.cnt_to) {
             // binned layout: the range holds the tile's particles (one front
             // segment) and its spare slots; the range after the last tile is
@@ -275,35 +326,40 @@ cudaError_t scan_tiles(const int32_t *count, int nt, int32_t *start, int32_t *sc
     return cudaGetLastError();
 }
 
-// slot of the r-th particle of cell `key` within its tile's range
+// slot of the r-th particle of cell `key` within its tile's range, from the
+// tile's layout (k_layout: tile_info, the cell's places in the tail layers
+// in cell_pos, its offset in the rest in cell_off)
 template <class K>
-__device__ __forceinline__ int slot_in_tile(int key, int tile, int r, const int32_t *tile_R, const int32_t *cell_off,
-                                            const int32_t *cell_count, int C) {
-    const int lc = key - tile * C, Rl = tile_R[tile];
-    if (r < Rl) return r * C + lc;
-    int i = cell_off[key] + (r - Rl);  // place in the tail, cell by cell
-    // the tail dealt into S interleaved runs, so that the particles of one
-    // cell (consecutive in the tail) land in different warps and a warp's
-    // lanes rarely share a cell: their shared-memory atomics then do not
-    // collide on one address.  Measured fastest: S = 4 of 2, 3, 4, 6, 8, 16
-    // for 3D3V at 2 per cell, S = 8 of 2, 4, 8 for 2D3V at 8 + 8 per cell (a
-    // fifth off its fused kernel)
+__device__ __forceinline__ int slot_in_tile(int key, int tile, int r, const int32_t *tile_info, const int32_t *cell_off,
+                                            const int32_t *cell_pos, int C) {
+    constexpr int L = K::kTailLayers;
+    const int32_t *ti = tile_info + (size_t)tile * kTileInfo;
+    const int Rl = ti[0];
+    if (r < Rl) return r * C + key - tile * C;
+    const int d = r - Rl;
+    if (d < L) return Rl * C + ti[4 + d] + (int)(((uint32_t)cell_pos[key] >> (10 * d)) & 1023u);
+    int i = cell_off[key] + (d - L);  // place in the rest, cell by cell
+    // the rest dealt into S interleaved runs, so that the particles of one
+    // cell (consecutive there) land in different warps and a warp's lanes
+    // rarely share a cell: their shared-memory atomics then do not collide on
+    // one address.  Measured fastest for the whole tail: S = 4 of 2, 3, 4, 6,
+    // 8, 16 for 3D3V at 2 per cell, S = 8 of 2, 4, 8 for 2D3V at 8 + 8 per
+    // cell (a fifth off its fused kernel)
     constexpr int S = K::kTailRuns;
-    const int last = (tile + 1) * C - 1;
-    const int T = cell_off[last] + cell_count[last] - Rl;
+    const int T = ti[2];
     if (T >= 64 * S) {
         const int m = i % S, q = i / S;
         i = m * (T / S) + min(m, T % S) + q;
     }
-    return Rl * C + i;
+    return Rl * C + ti[3] + i;
 }
 
 // every particle to its slot; range: nullptr (all *src.n slots) or a device
 // pair [range[0], range[1]) of source slots
 template <typename R, int NF, class K>
 __global__ void k_scatter(const SortArrays<R> src, const SortArrays<R> dst, const K kf, const int32_t *rank,
-                          const int32_t *tile_start, const int32_t *tile_R, const int32_t *cell_off,
-                          const int32_t *cell_count, int C, const int32_t *range) {
+                          const int32_t *tile_start, const int32_t *tile_info, const int32_t *cell_off,
+                          const int32_t *cell_pos, int C, const int32_t *range) {
     const long long p0 = range ? range[0] : 0, n = range ? range[1] : *src.n;
     for (long long p = p0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
          p += (long long)gridDim.x * blockDim.x) {
@@ -312,7 +368,7 @@ __global__ void k_scatter(const SortArrays<R> src, const SortArrays<R> dst, cons
         const uint32_t c = src.cell[p];
         int tile;
         const int key = kf(c, tile);
-        const int pos = tile_start[tile] + slot_in_tile<K>(key, tile, r, tile_R, cell_off, cell_count, C);
+        const int pos = tile_start[tile] + slot_in_tile<K>(key, tile, r, tile_info, cell_off, cell_pos, C);
         dst.cell[pos] = c;
 #pragma unroll
         for (int k = 0; k < NF; ++k) dst.f[k][pos] = src.f[k][p];
@@ -333,8 +389,8 @@ constexpr uint32_t kSlotEmpty = 0xFFFFFFFEu;
 template <typename R, int NF, class K>
 __global__ void __launch_bounds__(256) k_scatter_tiles(const SortArrays<R> src, const SortArrays<R> dst, const K kf,
                                                        const int32_t *rank, const int32_t *old_start, int txo,
-                                                       int ntx, const int32_t *tile_start, const int32_t *tile_R,
-                                                       const int32_t *cell_off, const int32_t *cell_count, int C,
+                                                       int ntx, const int32_t *tile_start, const int32_t *tile_info,
+                                                       const int32_t *cell_off, const int32_t *cell_pos, int C,
                                                        int cap) {
     extern __shared__ __align__(16) unsigned char sm_rec[];
     uint32_t *scell = reinterpret_cast<uint32_t *>(sm_rec);
@@ -344,8 +400,7 @@ __global__ void __launch_bounds__(256) k_scatter_tiles(const SortArrays<R> src, 
     const int r = t - tx + bin_rot_x(tx, ntx, txo);
     const int os = old_start[r], oe = old_start[r + 1];
     const int ns = tile_start[t];
-    const int last = (t + 1) * C - 1, Rl = tile_R[t];
-    const int cnt = Rl * C + cell_off[last] + cell_count[last] - Rl;
+    const int cnt = tile_info[(size_t)t * kTileInfo + 1];
     const bool staged = cnt <= cap;
     if (staged)
         for (int j = threadIdx.x; j < cnt; j += blockDim.x) scell[j] = kSlotEmpty;
@@ -356,7 +411,7 @@ __global__ void __launch_bounds__(256) k_scatter_tiles(const SortArrays<R> src, 
         const uint32_t c = src.cell[i];
         int tile;
         const int key = kf(c, tile);
-        const int pos = slot_in_tile<K>(key, tile, rk, tile_R, cell_off, cell_count, C);
+        const int pos = slot_in_tile<K>(key, tile, rk, tile_info, cell_off, cell_pos, C);
         if (staged && tile == t) {
             scell[pos] = c;
             sid[pos] = src.id[i];
@@ -510,7 +565,7 @@ cudaError_t tile_sort(const SortArrays<R> &src, const SortArrays<R> &dst, const 
         if (e != cudaSuccess) return e;
     }
     k_rank<K><<<g, 256, 0, st>>>(src.cell, src.n, key, w.cell_count, w.rank);
-    k_layout<<<nt, C, 0, st>>>(w.cell_count, C, w.cell_off, w.tile_R, w.tile_total, bins);
+    k_layout<K::kTailLayers><<<nt, C, 0, st>>>(w.cell_count, C, w.cell_off, w.tile_info, w.tile_total, bins);
     e = scan_tiles(w.tile_total, bins.cnt_to ? nt + 1 : nt, tile_start, w.cursor, n_tmp, st);
     if (e != cudaSuccess) return e;
     if (tiled) {
@@ -527,15 +582,15 @@ cudaError_t tile_sort(const SortArrays<R> &src, const SortArrays<R> &dst, const 
             attr_set = true;
         }
         k_scatter_tiles<R, NF, K><<<nt, 256, smem, st>>>(src, dst, key, w.rank, bins.old_start, bins.txo,
-                                                         key.ntiles_x(), tile_start, w.tile_R, w.cell_off,
+                                                         key.ntiles_x(), tile_start, w.tile_info, w.cell_off,
                                                          w.cell_count, C, cap);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         if (bins.src_binned)
-            k_scatter<R, NF, K><<<g, 256, 0, st>>>(src, dst, key, w.rank, tile_start, w.tile_R, w.cell_off,
+            k_scatter<R, NF, K><<<g, 256, 0, st>>>(src, dst, key, w.rank, tile_start, w.tile_info, w.cell_off,
                                                    w.cell_count, C, bins.old_start + nt);
     } else {
-        k_scatter<R, NF, K><<<g, 256, 0, st>>>(src, dst, key, w.rank, tile_start, w.tile_R, w.cell_off,
+        k_scatter<R, NF, K><<<g, 256, 0, st>>>(src, dst, key, w.rank, tile_start, w.tile_info, w.cell_off,
                                                w.cell_count, C, nullptr);
     }
     e = cudaGetLastError();
@@ -566,8 +621,8 @@ SortArrays<R> arrays3(const DevSpecies3<R> &S) {
 
 // n_upper bounds the source count (sizes the grids); the device counter
 // *src.n is read by the kernels and replaced by the sorted count at the end.
-// Scratch: cell_count and cell_off [ntiles * C], tile_R and tile_total
-// [ntiles], rank [n_upper].
+// Scratch: cell_count and cell_off [ntiles * C], tile_info [ntiles *
+// kTileInfo], tile_total [ntiles + 1], rank [n_upper].
 template <typename R>
 cudaError_t launch_tile_sort(const DevSpecies<R> &src, const DevSpecies<R> &dst, const TileGeom &t,
                              const SortScratch &w, int32_t *tile_start, int32_t *n_tmp, int n_upper,

@@ -63,7 +63,7 @@ struct Ctx {
     uint32_t *cell_old[PIC_MAX_SPECIES] = {};
     void *old_f[PIC_MAX_SPECIES][3] = {};  // ox_old, oy_old, then vz (2D3V) or oz_old (3D3V)
     int32_t *tile_count = nullptr, *tile_cursor = nullptr;
-    int32_t *cell_count = nullptr, *cell_off = nullptr, *tile_R = nullptr;
+    int32_t *cell_count = nullptr, *cell_off = nullptr, *tile_info = nullptr;
     int32_t *n_dev = nullptr;  // [PIC_MAX_SPECIES + 1] slot counts; the last entry is sort scratch
     int32_t *scratch_i32 = nullptr;  // 3 * max capacity, for ix / iy / iz transfers
     unsigned *err = nullptr;
@@ -517,7 +517,7 @@ pic_status_t sort_species(Ctx *c, int s, cudaStream_t st, bool compact_only = fa
     if (sr != PIC_OK) return sr;
     refresh_live(c, s);
     const int from = c->cur[s], to = 1 - from;
-    SortScratch w{c->cell_count, c->cell_off, c->tile_R, c->tile_count, c->tile_cursor, c->scratch_i32};
+    SortScratch w{c->cell_count, c->cell_off, c->tile_info, c->tile_count, c->tile_cursor, c->scratch_i32};
     BinSort bins{};
     int64_t span = 0;
     const bool bin = c->dim == 3 && !compact_only && bin_plan(c, s, &bins.ovf_cap, &span);
@@ -719,7 +719,7 @@ pic_status_t retile(Ctx *c, int tx, int ty, cudaStream_t st) {
     cudaFree(c->tile_count);
     cudaFree(c->cell_count);
     cudaFree(c->cell_off);
-    cudaFree(c->tile_R);
+    cudaFree(c->tile_info);
     cudaFree(c->tile_cursor);
     cudaFree(c->diag_rows);
     cudaFree(c->old_start);
@@ -736,7 +736,7 @@ pic_status_t retile(Ctx *c, int tx, int ty, cudaStream_t st) {
     CK(cudaMalloc(&c->tile_count, (c->ntiles + 1) * sizeof(int32_t)));
     CK(cudaMalloc(&c->cell_count, cells * sizeof(int32_t)));
     CK(cudaMalloc(&c->cell_off, cells * sizeof(int32_t)));
-    CK(cudaMalloc(&c->tile_R, c->ntiles * sizeof(int32_t)));
+    CK(cudaMalloc(&c->tile_info, (size_t)c->ntiles * kTileInfo * sizeof(int32_t)));
     CK(cudaMalloc(&c->tile_cursor, c->ntiles * sizeof(int32_t)));
     CK(cudaMalloc(&c->old_start, (c->ntiles + 2) * sizeof(int32_t)));
     CK(cudaMalloc(&c->diag_rows, (size_t)(c->ntiles + Ctx::kBinCtasMax) * PIC_MAX_SPECIES * 8 * sizeof(double)));
@@ -1173,7 +1173,7 @@ pic_status_t pic_create(const pic_config_t *cfg, void *stream, void **ctx_out) {
     CKC(cudaMalloc(&c->tile_count, (c->ntiles + 1) * sizeof(int32_t)));
     CKC(cudaMalloc(&c->cell_count, (size_t)c->ntiles * tile_cells(c) * sizeof(int32_t)));
     CKC(cudaMalloc(&c->cell_off, (size_t)c->ntiles * tile_cells(c) * sizeof(int32_t)));
-    CKC(cudaMalloc(&c->tile_R, c->ntiles * sizeof(int32_t)));
+    CKC(cudaMalloc(&c->tile_info, (size_t)c->ntiles * kTileInfo * sizeof(int32_t)));
     CKC(cudaMalloc(&c->tile_cursor, c->ntiles * sizeof(int32_t)));
     CKC(cudaMalloc(&c->n_dev, (PIC_MAX_SPECIES + 1) * sizeof(int32_t)));
     CKC(cudaMemsetAsync(c->n_dev, 0, (PIC_MAX_SPECIES + 1) * sizeof(int32_t), st));
@@ -1235,7 +1235,7 @@ void pic_destroy(void *ctx) {
     cudaFree(c->tile_count);
     cudaFree(c->cell_count);
     cudaFree(c->cell_off);
-    cudaFree(c->tile_R);
+    cudaFree(c->tile_info);
     cudaFree(c->tile_cursor);
     cudaFree(c->n_dev);
     cudaFree(c->scratch_i32);

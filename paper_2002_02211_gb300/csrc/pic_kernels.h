@@ -102,9 +102,14 @@ struct UploadSrc {
 template <typename HostT, typename R>
 cudaError_t launch_upload(const UploadSrc<HostT> &src, const SortArrays<R> &dst, int n, int xlo, int xhi, int ny,
                           int nz, bool d3, unsigned *err, cudaStream_t st);
+// per-tile layout record of a sort (k_layout): the full layers' depth, the
+// tile's particle count, the size and start of the tail's rest, the starts
+// of the tail's depth layers
+constexpr int kTileInfo = 8;
 struct SortScratch {
-    int32_t *cell_count, *cell_off;  // [ntiles * TX * TY]
-    int32_t *tile_R, *tile_total;    // [ntiles], tile_total [ntiles + 1]
+    int32_t *cell_count, *cell_off;  // [ntiles * cells per tile]
+    int32_t *tile_info;              // [ntiles * kTileInfo]
+    int32_t *tile_total;             // [ntiles + 1]
     int32_t *cursor;                 // [ntiles] scan scratch
     int32_t *rank;                   // [n]
 };
