@@ -101,7 +101,9 @@ typedef struct {
                                     of the same kernels); 0 means 32.  Reductions
                                     are FP64 in both.                              */
     int dim;                     /* 2 (or 0): 2D3V; 3: 3D3V                        */
-    int nz;                      /* 3D3V: cells along z, 4 <= nz <= 1020; nx, ny <= 2044 */
+    int nz;                      /* 3D3V: cells along z, 4 <= nz <= 1020; nx, ny <= 2044;
+                                    the mesh padded to whole tiles holds at most
+                                    2^31 - 1 cells (the tile sort's cell index)    */
     double dz_lambda;            /* 3D3V: cell size along z [lambda]; then
                                     dt = cfl / sqrt(1/dx^2 + 1/dy^2 + 1/dz^2)      */
     int tile_z;                  /* 3D3V tiles (tile_x, tile_y, tile_z): 16x4x4,

@@ -1083,6 +1083,16 @@ pic_status_t pic_validate_config(const pic_config_t *cfg) {
     if (d3 && (cfg->tile_x != 0 || cfg->tile_y != 0 || cfg->tile_z != 0) &&
         !fused3_tile_supported(cfg->tile_x, cfg->tile_y, cfg->tile_z))
         return fail(c, PIC_ERR_ARG, "3D3V tile must be one of 16x4x4, 8x8x4, 8x4x4, 16x8x4, 32x4x4 cells");
+    if (d3) {
+        // the tile sort keys every cell of the tile-padded mesh with a 32-bit
+        // signed index (tile, cell inside the tile)
+        const bool dflt = cfg->tile_x == 0 && cfg->tile_y == 0 && cfg->tile_z == 0;
+        const int64_t tx = dflt ? 16 : cfg->tile_x, ty = dflt ? 4 : cfg->tile_y, tz = dflt ? 4 : cfg->tile_z;
+        const int64_t padded = (cfg->nx + tx - 1) / tx * tx * ((cfg->ny + ty - 1) / ty * ty) *
+                               ((cfg->nz + tz - 1) / tz * tz);
+        if (padded > INT_MAX)
+            return fail(c, PIC_ERR_ARG, "3D3V mesh padded to whole tiles must hold at most 2^31 - 1 cells");
+    }
     if (cfg->sort_every < 0) return fail(c, PIC_ERR_ARG, "sort_every must be >= 0");
     if (cfg->bin_headroom_pct < 0 || cfg->bin_headroom_pct > 400 || cfg->bin_min_extra < 0 ||
         cfg->bin_min_extra > 4096)

@@ -77,6 +77,36 @@ def test_validate_config_rejects_bad_tiles_and_species():
     assert _status(cfg) == -1
 
 
+def test_validate_config_mesh_size_limits():
+    # smallest accepted meshes, the largest per-axis sizes, and the 3D3V
+    # bound on the mesh padded to whole tiles (the tile sort indexes its
+    # cells with 32-bit signed keys)
+    def cfg2(nx, ny):
+        return pic.config_from_workload(W.small_case(nx=nx, ny=ny, ppc=1))
+
+    def cfg3(nx, ny, nz, tile=None):
+        return pic.config_from_workload(W.small_case3(nx=nx, ny=ny, nz=nz, ppc=1), tile=tile)
+
+    assert _status(cfg2(8, 4)) == 0
+    assert _status(cfg2(32767, 32767)) == 0
+    for nx, ny in ((7, 4), (8, 3), (32768, 4), (8, 32768)):
+        assert _status(cfg2(nx, ny)) == -1, (nx, ny)
+    assert _status(cfg3(8, 4, 4)) == 0
+    for dims in ((7, 4, 4), (8, 3, 4), (8, 4, 3), (2045, 4, 4), (8, 2045, 4), (8, 4, 1021)):
+        assert _status(cfg3(*dims)) == -1, dims
+    # default 16x4x4 tiles: 2044 x 1028 x 1020 pads to 2048 x 1028 x 1020 =
+    # 2,147,450,880 cells (accepted), 2044 x 1029 x 1020 to 2048 x 1032 x 1020
+    # = 2,155,806,720 > 2^31 - 1 (refused)
+    assert _status(cfg3(2044, 1028, 1020)) == 0
+    assert _status(cfg3(2044, 1029, 1020)) == -1
+    assert "2^31" in pic.load().pic_last_error(None).decode()
+    assert _status(cfg3(2044, 2044, 1020)) == -1
+    # the padding follows the tile: 2020 columns pad to 2032 with 16-wide
+    # tiles (2,138,964,480 cells with 1032 x 1020) and to 2048 with 32-wide ones
+    assert _status(cfg3(2020, 1032, 1020)) == 0
+    assert _status(cfg3(2020, 1032, 1020, tile=(32, 4, 4))) == -1
+
+
 def test_validate_config_binned_layout():
     # binned layout: 3D3V only, headroom in [0, 400] %, spare slots in [0, 4096]
     cfg = pic.config_from_workload(W.small_case3(), bins=(25, 16))
