@@ -410,8 +410,9 @@ pic_status_t pic_buffer_sizes(void *ctx, int64_t *ld, int64_t *plane, int *real_
  * b receives a copy of the array it replaces, the context frees its own and
  * uses the caller's from then on (the caller keeps ownership: the memory must
  * stay allocated, on the context's device, until pic_destroy).  Every pointer
- * must be device (or managed) memory of the context's device, 16-byte aligned
- * (else PIC_ERR_ARG and nothing changes); sizes are the caller's
+ * must be device (or managed) memory of the context's device, 16-byte aligned,
+ * and no two arrays of the context (bound, or its own) may share a byte once
+ * bound (else PIC_ERR_ARG and nothing changes); sizes are the caller's
  * responsibility.  Captured step graphs are dropped and the field window's
  * tensor map is re-encoded.  Synchronous. */
 pic_status_t pic_bind_buffers(void *ctx, const pic_buffers_t *b, void *stream);

@@ -2076,9 +2076,10 @@ pic_status_t pic_bind_buffers(void *ctx, const pic_buffers_t *b, void *stream) {
         void *mine;
         size_t bytes;
     };
-    std::vector<Swap> sw;
+    std::vector<Swap> sw, all;  // the arrays replaced; every array slot of the context
     const size_t rb = c->rb;
     auto add = [&](void **own, void *mine, size_t bytes) {
+        all.push_back(Swap{own, mine, bytes});
         if (mine) sw.push_back(Swap{own, mine, bytes});
     };
     add(&c->EB, b->eb, 6 * c->plane * rb);
@@ -2094,6 +2095,17 @@ pic_status_t pic_bind_buffers(void *ctx, const pic_buffers_t *b, void *stream) {
             if (c->dim == 3) add(&B.oz, u.oz, cap * rb);
             add(reinterpret_cast<void **>(&B.id), u.id, cap * sizeof(int32_t));
         }
+    }
+    {
+        // after the bind no two arrays of the context may share a byte
+        std::vector<std::pair<uintptr_t, uintptr_t>> iv;
+        for (const Swap &w : all) {
+            const uintptr_t p = reinterpret_cast<uintptr_t>(w.mine ? w.mine : *w.own);
+            if (p && w.bytes) iv.emplace_back(p, p + w.bytes);
+        }
+        std::sort(iv.begin(), iv.end());
+        for (size_t k = 1; k < iv.size(); ++k)
+            if (iv[k].first < iv[k - 1].second) return fail(c, PIC_ERR_ARG, "bound arrays overlap");
     }
     for (const Swap &w : sw) {
         cudaPointerAttributes a{};

@@ -92,7 +92,7 @@ def test_bound_mid_run_3d_binned():
         b.close()
 
 
-def test_bind_refuses_foreign_or_misaligned_memory():
+def test_bind_refuses_foreign_misaligned_or_overlapping_memory():
     wl = W.small_case(nx=32, ny=16, ppc=1)
     sim, orc, _ = make_pair(wl)
     try:
@@ -107,6 +107,22 @@ def test_bind_refuses_foreign_or_misaligned_memory():
             with pytest.raises(pic.PicError) as e:
                 sim._c(pic.load().pic_bind_buffers(sim.h, C.byref(b), sim._s))
             assert e.value.status == -1
+        # arrays that would share bytes once bound: E/B and J from one
+        # tensor 16 bytes apart, and E/B over a species array
+        big = torch.zeros(9 * plane + 64, dtype=torch.float32, device="cuda")
+        rec = torch.zeros(caps[0] + 64, dtype=torch.float32, device="cuda")
+        b = pic.pic_buffers_t()
+        b.eb, b.j = big.data_ptr(), big.data_ptr() + 16
+        with pytest.raises(pic.PicError) as e:
+            sim._c(pic.load().pic_bind_buffers(sim.h, C.byref(b), sim._s))
+        assert e.value.status == -1 and "overlap" in str(e.value)
+        b = pic.pic_buffers_t()
+        b.eb = big.data_ptr()
+        b.sp[0][1].ux = big.data_ptr() + 4 * plane
+        b.sp[0][1].uy = rec.data_ptr()
+        with pytest.raises(pic.PicError) as e:
+            sim._c(pic.load().pic_bind_buffers(sim.h, C.byref(b), sim._s))
+        assert e.value.status == -1 and "overlap" in str(e.value)
         after = sim.get_fields()
         for k in FIELDS:
             assert np.array_equal(before[k], after[k])
