@@ -20,8 +20,11 @@ exactly zero; that catches a write at a wrapped index anywhere.
 Tolerances as in the one-step parity tests.
 
 Device memory: about 210 GB at the peak of the 3D3V binding (the context's
-130 GB plus the bound E, B and J), so torch's cache is emptied first.
+130 GB plus the bound E, B and J), so unreferenced contexts are collected
+and torch's cache is emptied first.
 """
+import gc
+
 import numpy as np
 import pytest
 
@@ -98,6 +101,7 @@ def _abs_sum(torch, t):
 def test_largest_mesh_far_corner_step_against_oracle(dim):
     torch = pytest.importorskip("torch")
     assert torch.cuda.is_available()
+    gc.collect()                 # contexts of earlier tests awaiting collection free their memory
     torch.cuda.empty_cache()
     big, small, origin = _cases(dim)
     rng = np.random.default_rng(61 + dim)
