@@ -1,0 +1,70 @@
+"""Host-side arithmetic of bench.py's roofline line, against the algorithmic
+bytes the method fixes for the fused a1-a5 kernel: per particle read cell,
+offsets, u (3), s (3), w and write cell, offsets, u, s; per cell the E, B
+window and the current added to J.  Also: the DRAM traffic record is used
+only for the kernel source it was measured on."""
+import json
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+import workloads as W  # noqa: E402
+
+
+def _count(dim, real):
+    """Algorithmic bytes per particle and per cell, counted field by field."""
+    offsets = dim                   # ox, oy (, oz)
+    read = 4 + real * (offsets + 3 + 3 + 1)
+    write = 4 + real * (offsets + 3 + 3)
+    cell = real * (6 + 3)           # E, B read (6 components), J added (3)
+    return read + write, cell
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("precision", [32, 64])
+def test_fused_bytes_follow_the_field_count(dim, precision):
+    per_p, per_c = _count(dim, precision // 8)
+    alg, lay = bench.fused_bytes(dim, 1000, 10, precision, False)
+    assert alg == per_p * 1000 + per_c * 10
+    assert lay == 0
+
+
+def test_fused_bytes_fp32_values():
+    # 76 B (2D3V) and 84 B (3D3V) a particle, 36 B a cell; the binned layout's
+    # id read and w, id writes (12 B) reported apart
+    assert bench.fused_bytes(2, 1, 0, 32, False) == (76, 0)
+    assert bench.fused_bytes(3, 1, 0, 32, False) == (84, 0)
+    assert bench.fused_bytes(3, 0, 1, 32, False) == (36, 0)
+    assert bench.fused_bytes(3, 1, 0, 32, True) == (84, 12)
+    assert bench.fused_bytes(3, 1, 0, 64, True) == (160, 16)
+
+
+def test_config2_launch_bytes():
+    # 66,584,576 electrons on 512 x 256 x 256 cells: 6.80 GB a launch
+    n = 2 * (512 - 4) * 256 * 256
+    alg, _ = bench.fused_bytes(3, n, 512 * 256 * 256, 32, True)
+    assert n == 66_584_576
+    assert alg == 84 * n + 36 * 33_554_432
+    assert alg / 1e9 == pytest.approx(6.80, abs=0.005)
+
+
+def test_traffic_record_only_for_its_source(tmp_path, monkeypatch):
+    wl = W.CONFIG2
+    rec = {"kernel": "k_step_fused3", "workload": wl.name, "dram_bytes_per_launch": 123,
+           "source_sha256": bench.kernel_source_hash(3)}
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "k_step_fused3_binned.traffic.json").write_text(json.dumps(rec))
+    # the hash covers the sources under the repository; only the record moves
+    real_hash = bench.kernel_source_hash(3)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda dim: real_hash)
+    assert bench.traffic_record(3, wl, True)["dram_bytes_per_launch"] == 123
+    assert bench.traffic_record(3, W.CONFIG3, True) is None          # another workload
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda dim: "0" * 64)
+    assert bench.traffic_record(3, wl, True) is None                  # another kernel source
