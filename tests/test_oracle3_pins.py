@@ -253,6 +253,9 @@ def test_laser3_transverse_profile_is_centred_gaussian(oracle_mod):
     # node 0.5 cells, so the ratio is exp(-(7.5^2 - 0.5^2) / 8^2)
     ratio = best[nz // 2, ny // 2 - 1 + 8] / centre
     assert ratio == pytest.approx(math.exp(-(7.5 ** 2 - 0.5 ** 2) / 64), rel=0.05)
+    # and along z: the node 8 cells off axis in z (the same 0.5 cells in y)
+    ratio_z = best[nz // 2 + 8, ny // 2 - 1] / centre
+    assert ratio_z == pytest.approx(math.exp(-(8.0 ** 2) / 64), rel=0.05)
 
 
 # ---------------------------------------------------------------------------

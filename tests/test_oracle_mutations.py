@@ -60,6 +60,55 @@ MUTATIONS = [
     ("moments unweighted mean", "swy += p->w[i] * p->sy[i];", "swy += p->sy[i];"),
     ("energy uses total energy", "double ek = (sqrt(1.0 + dot3(u, u)) - 1.0) * sp->m * MEC2_MEV;\n        if (ek < emin_mev",
      "double ek = (sqrt(1.0 + dot3(u, u))) * sp->m * MEC2_MEV;\n        if (ek < emin_mev"),
+    # the position advance, the deposit's v_z, Ampere's J, div E, the moments'
+    # weights and window, the open-x removal and the laser source's placement
+    ("advance uses old momentum", "double X1 = p->x[i] + g->dt * u[0] / gam / g->dx;",
+     "double X1 = p->x[i] + g->dt * u0[0] / gam / g->dx;"),
+    ("vz from old momentum", "vz[i] = u[2] / gam;", "vz[i] = u0[2] / gam;"),
+    ("Jy half term dropped", "acc += dSy[l] * (S0x[k] + 0.5 * dSx[k]);", "acc += dSy[l] * S0x[k];"),
+    ("Jz drops vz", "+= qw * vz * wz;", "+= qw * wz;"),
+    ("Jy on the next half node", "f->jy[yj(g, j0 + l) * g->nx + xi(g, i0 + k)] += cy * acc;",
+     "f->jy[yj(g, j0 + l + 1) * g->nx + xi(g, i0 + k)] += cy * acc;"),
+    ("Ez ignores Jz", "(f->bx[c] - f->bx[jm * nx + i]) / g->dy - f->jz[c]);",
+     "(f->bx[c] - f->bx[jm * nx + i]) / g->dy);"),
+    ("By half-step sign", "f->by[c] += h / g->dx * (f->ez[j * nx + ip] - f->ez[c]);",
+     "f->by[c] -= h / g->dx * (f->ez[j * nx + ip] - f->ez[c]);"),
+    ("boris drops first half kick", "um[k] = u[k] + 0.5 * qm * dt * E[k];", "um[k] = u[k];"),
+    ("spin angle halved", "double th = om * dt;", "double th = 0.5 * om * dt;"),
+    ("omega at the new momentum",
+     "double ubar[3] = {0.5 * (u0[0] + u[0]), 0.5 * (u0[1] + u[1]), 0.5 * (u0[2] + u[2])};",
+     "double ubar[3] = {u[0], u[1], u[2]};"),
+    ("gather stagger of Ey", "E[1] = interp(g, f->ey, X, Y, 0.0, 0.5);", "E[1] = interp(g, f->ey, X, Y, 0.5, 0.0);"),
+    ("gather stagger of Bx", "B[0] = interp(g, f->bx, X, Y, 0.0, 0.5);", "B[0] = interp(g, f->bx, X, Y, 0.5, 0.0);"),
+    ("gather stagger of By", "B[1] = interp(g, f->by, X, Y, 0.5, 0.0);", "B[1] = interp(g, f->by, X, Y, 0.0, 0.5);"),
+    ("periodic unwrap sign", "        return X1 - n;", "        return X1 + n;"),
+    ("rho y shape uses x", "shape1(p->y[i] - (double)(j0 + dj));", "shape1(p->x[i] - (double)(j0 + dj));"),
+    ("div E y difference uses dx", "(f->ey[c] - f->ey[jm * nx + i]) / g->dy;",
+     "(f->ey[c] - f->ey[jm * nx + i]) / g->dx;"),
+    ("energy variance unweighted", "var += p->w[i] * (ek - mean) * (ek - mean);",
+     "var += (ek - mean) * (ek - mean);"),
+    ("count sums weights", "cnt += 1.0;", "cnt += p->w[i];"),
+    ("energy window closed above", "if (ek < emin_mev || ek >= emax_mev)\n            continue;\n        sw",
+     "if (ek < emin_mev || ek > emax_mev)\n            continue;\n        sw"),
+    ("histogram count weighted", "out[5 * b + 0] += 1.0;", "out[5 * b + 0] += p->w[i];"),
+    ("log bins linear", "double f = log_bins ? log(ek / emin_mev) / log(emax_mev / emin_mev)",
+     "double f = log_bins ? (ek - emin_mev) / (emax_mev - emin_mev)"),
+    ("removal at x_min from x = 1", "if (g->bc_x == OR_BC_OPEN && (p->x[i] < 2.0 ||",
+     "if (g->bc_x == OR_BC_OPEN && (p->x[i] < 1.0 ||"),
+    ("removal at x_max from nx - 1", "p->x[i] >= (double)(g->nx - 2)))\n            p->alive[i] = 0;",
+     "p->x[i] >= (double)(g->nx - 1)))\n            p->alive[i] = 0;"),
+    ("laser time at the integer step", "t = ((double)step + 0.5) * dt;", "t = (double)step * dt;"),
+    ("laser envelope of the intensity",
+     "double env = exp(-((t - g->t_peak) / g->tau) * ((t - g->t_peak) / g->tau));",
+     "double env = exp(-0.5 * ((t - g->t_peak) / g->tau) * ((t - g->t_peak) / g->tau));"),
+    ("laser centred at y = 0", "double yc = 0.5 * g->ny * g->dy;", "double yc = 0.0;"),
+    ("laser phase counted from t = 0", "double ph = t - g->t_peak;", "double ph = t;"),
+    ("CP at full amplitude per component", "v = g->a0 / sqrt(2.0) * env * tr", "v = g->a0 * env * tr"),
+    ("laser Ez source at the Ey height", "or_laser(g, t, (double)j * g->dy, 1, &fin);",
+     "or_laser(g, t, ((double)j + 0.5) * g->dy, 1, &fin);"),
+    ("x_max absorber uses Ey one column in",
+     "f->bz[cl] = (2.0 * f->ey[cl] - (1.0 - r) * f->bz[cl - 1]) / (1.0 + r);",
+     "f->bz[cl] = (2.0 * f->ey[cl - 1] - (1.0 - r) * f->bz[cl - 1]) / (1.0 + r);"),
 ]
 
 
@@ -92,6 +141,32 @@ MUTATIONS3 = [
     ("3d div E uses dy for z", "(f->ez[c] - f->ez[at3(g, i, j, k - 1)]) / g->dz;",
      "(f->ez[c] - f->ez[at3(g, i, j, k - 1)]) / g->dy;"),
     ("3d rho z weight", "shape1_3(p->z[n] - (double)(k0 + c));", "shape1_3(p->z[n] - (double)(k0));"),
+    ("3d z advance uses old momentum", "double Z1 = p->z[i] + g->dt * u[2] / gam / g->dz;",
+     "double Z1 = p->z[i] + g->dt * u0[2] / gam / g->dz;"),
+    ("3d Wy drops the dSz half term", "0.5 * S0x[i] * dSz[k] +\n                        dSx[i] * dSz[k] / 3.0;",
+     "dSx[i] * dSz[k] / 3.0;"),
+    ("3d Jz scaled by dy", "f->jz[at3(g, i0 + i, j0 + j, k0 + k)] += cz * acc;",
+     "f->jz[at3(g, i0 + i, j0 + j, k0 + k)] += cy * acc;"),
+    ("3d laser radius without z",
+     "double r2 = ((y - yc) * (y - yc) + (z - zc) * (z - zc)) / (g->w0 * g->w0);",
+     "double r2 = ((y - yc) * (y - yc)) / (g->w0 * g->w0);"),
+    ("3d Ey z-curl sign", "f->ey[c] += dt * ((f->bx[c] - f->bx[ckm]) / g->dz",
+     "f->ey[c] += dt * (-(f->bx[c] - f->bx[ckm]) / g->dz"),
+    ("3d Bz y-curl uses Ey", "- (f->ex[cjp] - f->ex[c]) / g->dy);\n                }",
+     "- (f->ey[cjp] - f->ey[c]) / g->dy);\n                }"),
+    ("3d z wrap one cell short", "p->z[i] = wrap_pos3(Z1, (double)g->nz);",
+     "p->z[i] = wrap_pos3(Z1, (double)(g->nz - 1));"),
+    ("3d gather stagger of By", "B[1] = interp3(g, f->by, X, Y, Z, 0.5, 0.0, 0.5);",
+     "B[1] = interp3(g, f->by, X, Y, Z, 0.5, 0.0, 0.0);"),
+    ("3d gather stagger of Ey", "E[1] = interp3(g, f->ey, X, Y, Z, 0.0, 0.5, 0.0);",
+     "E[1] = interp3(g, f->ey, X, Y, Z, 0.0, 0.5, 0.5);"),
+    ("3d x_max By without transverse term",
+     "f->by[cl] = (-2.0 * f->ez[cl] - (1.0 - r) * f->by[cl - 1] + qy * dybl) / (1.0 + r);",
+     "f->by[cl] = (-2.0 * f->ez[cl] - (1.0 - r) * f->by[cl - 1]) / (1.0 + r);"),
+    ("3d div B z difference uses dy", "(f->bz[at3(g, i, j, k + 1)] - f->bz[c]) / g->dz;",
+     "(f->bz[at3(g, i, j, k + 1)] - f->bz[c]) / g->dy;"),
+    ("3d removal at x_min from x = 1", "if (g->bc_x == OR_BC_OPEN && (p->x[i] < 2.0 ||",
+     "if (g->bc_x == OR_BC_OPEN && (p->x[i] < 1.0 ||"),
 ]
 
 CASES = ([("pic_oracle.c", "test_oracle_pins.py") + m for m in MUTATIONS] +

@@ -4,6 +4,7 @@ Every test here checks the oracle against a closed form, an invariant, a
 special case with a textbook answer, brute force, or values worked by hand
 from Eq. (4) (tests/golden/).  None re-types the oracle's own formula.
 """
+import dataclasses
 import math
 import os
 
@@ -621,3 +622,168 @@ def test_histogram_sums_to_the_eq4_moments(oracle_mod, log_bins):
     mb = sim.moments(0, edges[b], edges[b + 1])
     assert h[b, 0] == mb[4]
     np.testing.assert_allclose(h[b, 2:5] / h[b, 1], mb[:3], atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# a4 and the current's v_z use the new momentum u^{n+1/2}
+# ---------------------------------------------------------------------------
+def test_advance_and_vz_use_the_new_momentum(oracle_mod):
+    # from rest in uniform E (B = 0) one push gives u^{n+1/2} = (q/m) E dt
+    # exactly (Boris' kick); the particle then moves by dt u / gamma(u) and the
+    # out-of-plane velocity handed to the deposit is u_z / gamma(u)
+    E = (0.4, -0.3, 0.7)
+    sim = _one_particle_sim(oracle_mod, {"ex": E[0], "ey": E[1], "ez": E[2]})
+    g = sim.grid
+    x0, y0 = float(sim.p[0]["x"][0]), float(sim.p[0]["y"][0])
+    _, _, vz = sim.push(0)
+    u = -1.0 * g.dt * np.asarray(E)
+    gam = math.sqrt(1.0 + u @ u)
+    p = sim.p[0]
+    np.testing.assert_allclose([p["ux"][0], p["uy"][0], p["uz"][0]], u, rtol=1e-14)
+    assert p["x"][0] == pytest.approx(x0 + g.dt * u[0] / gam / g.dx, rel=1e-14)
+    assert p["y"][0] == pytest.approx(y0 + g.dt * u[1] / gam / g.dy, rel=1e-14)
+    assert vz[0] == pytest.approx(u[2] / gam, rel=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# a6 with a current: Ampere's law, and div E with unequal cells
+# ---------------------------------------------------------------------------
+def test_uniform_current_drives_e_by_minus_dt_j(oracle_mod):
+    # dE/dt = curl B - J: with no fields and a uniform current every E
+    # component changes by exactly -dt J in one update, and B stays zero
+    wl = _vacuum(12, 10)
+    sim = oracle_mod.OracleSim(wl, _empty())
+    J = {"jx": 0.3, "jy": -0.7, "jz": 1.1}
+    for k, v in J.items():
+        sim.f[k][...] = v
+    sim.field_update()
+    dt = sim.grid.dt
+    for e, j in (("ex", "jx"), ("ey", "jy"), ("ez", "jz")):
+        np.testing.assert_allclose(sim.f[e], -dt * J[j], rtol=1e-15)
+    for b in ("bx", "by", "bz"):
+        assert np.all(sim.f[b] == 0.0)
+
+
+def test_div_e_of_a_linear_field_with_unequal_cells(oracle_mod):
+    # E = (alpha x, beta y) sampled at the Yee positions has div E = alpha +
+    # beta at every node whose stencil does not cross the periodic seam
+    wl = _vacuum(12, 10)                          # dx = lambda/16, dy = lambda/10
+    sim = oracle_mod.OracleSim(wl, _empty())
+    g = sim.grid
+    assert g.dx != g.dy
+    alpha, beta = 0.37, -1.9
+    i = np.arange(wl.nx)[None, :]
+    j = np.arange(wl.ny)[:, None]
+    sim.f["ex"][...] = alpha * (i + 0.5) * g.dx + 0.0 * j
+    sim.f["ey"][...] = beta * (j + 0.5) * g.dy + 0.0 * i
+    d = sim.div_e()
+    np.testing.assert_allclose(d[1:, 1:], alpha + beta, rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Eq. (4) moments: the energy window and the weighted spread
+# ---------------------------------------------------------------------------
+def _energy_particles(k_list, w_list):
+    # particles along x with gamma = 1 + k, so (gamma - 1) m c^2 = k m c^2
+    n = len(k_list)
+    ux = np.array([math.sqrt((1 + k) ** 2 - 1) for k in k_list])
+    f32 = np.float32
+    return dict(ix=np.full(n, 3, np.int32), iy=np.full(n, 3, np.int32),
+                ox=np.full(n, 0.5, f32), oy=np.full(n, 0.5, f32),
+                ux=ux.astype(np.float64), uy=np.zeros(n), uz=np.zeros(n),
+                sx=np.zeros(n, f32), sy=np.ones(n, f32), sz=np.zeros(n, f32),
+                w=np.array(w_list, f32), id=np.arange(n, dtype=np.int32))
+
+
+def _moments_of(oracle_mod, d, emin=-np.inf, emax=np.inf):
+    sp = W.Species("e", q=-1.0, m=1.0, a=0.0, n0=0.01, ppc=1, u_th=0.0, s0=(0, 1, 0))
+    wl = W.Workload(name="m", nx=8, ny=8, dx_lambda=1 / 16, dy_lambda=1 / 16, cfl=0.95,
+                    steps=1, species=(sp,), pol="none", bc_x="periodic")
+    sim = oracle_mod.OracleSim(wl, [d])    # keeps the float64 momenta (gamma = 1 + k to rounding)
+    return sim.moments(0, emin, emax)
+
+
+def test_energy_moments_are_weight_weighted(oracle_mod):
+    # kinetic energies 1, 2, 4 (units of m_e c^2) with weights 1, 1, 2:
+    # mean (1 + 2 + 8) / 4 = 2.75; variance
+    # (1.75^2 + 0.75^2 + 2 * 1.25^2) / 4 = 6.75 / 4 = 1.6875
+    mec2 = 0.51099895
+    m = _moments_of(oracle_mod, _energy_particles([1.0, 2.0, 4.0], [1.0, 1.0, 2.0]))
+    assert m[3] == pytest.approx(4.0)
+    assert m[4] == 3
+    assert m[5] == pytest.approx(2.75 * mec2, rel=1e-12)
+    assert m[6] == pytest.approx(1.6875 * mec2 ** 2, rel=1e-12)
+
+
+def test_energy_window_is_closed_below_and_open_above(oracle_mod):
+    # a particle at rest has kinetic energy exactly 0: it is in [0, 1) and
+    # not in [-1, 0)
+    d = _energy_particles([0.0, 0.0], [1.0, 3.0])
+    assert _moments_of(oracle_mod, d, 0.0, 1.0)[4] == 2
+    assert _moments_of(oracle_mod, d, -1.0, 0.0)[4] == 0
+
+
+# ---------------------------------------------------------------------------
+# open x: particles live in [2, nx - 2)
+# ---------------------------------------------------------------------------
+def test_open_x_removes_particles_leaving_the_plasma_region(oracle_mod):
+    # four free particles (no fields) cross or approach the two edges of the
+    # plasma region [2, nx - 2); the ones whose new x lies outside it are
+    # removed after the step, the others stay
+    nx, ny = 16, 8
+    wl = _vacuum(nx, ny, bc="open", pol="none")
+    sp = W.Species("e", q=-1.0, m=1.0, a=0.0, n0=0.01, ppc=1, u_th=0.0, s0=(1, 0, 0))
+    wl = dataclasses.replace(wl, species=(sp,))
+    sim0 = oracle_mod.OracleSim(wl, _empty())
+    g = sim0.grid
+    v = 0.6 * g.dx / g.dt                        # 0.6 cells a step
+    ux = v / math.sqrt(1 - v * v)
+    x = np.array([2.3, 2.9, nx - 2.3, nx - 2.9])
+    u = np.array([-ux, -ux, ux, ux])
+    f32 = np.float32
+    d = dict(ix=np.floor(x).astype(np.int32), iy=np.full(4, 3, np.int32),
+             ox=(x - np.floor(x)).astype(f32), oy=np.full(4, 0.5, f32),
+             ux=u.astype(f32), uy=np.zeros(4, f32), uz=np.zeros(4, f32),
+             sx=np.ones(4, f32), sy=np.zeros(4, f32), sz=np.zeros(4, f32),
+             w=np.full(4, 0.01, f32), id=np.arange(4, dtype=np.int32))
+    sim = oracle_mod.OracleSim(wl, [d])
+    sim.step(1)
+    # new x: 1.7 (out), 2.3 (in), nx - 1.7 (out), nx - 2.3 (in)
+    np.testing.assert_array_equal(sim.p[0]["alive"], [0, 1, 0, 1])
+
+
+# ---------------------------------------------------------------------------
+# laser source: centred on the box axis, staggered like E, phase at the peak
+# ---------------------------------------------------------------------------
+def test_laser_source_is_centred_and_staggered(oracle_mod):
+    # CP beam of waist 4 cells: after a few steps E_z (nodes, y = j dy) is
+    # mirror symmetric about the node j = ny/2 on the box axis, E_y (y =
+    # (j + 1/2) dy) about the half node between j = ny/2 - 1 and ny/2
+    nx, ny = 24, 32
+    wl = _vacuum(nx, ny, bc="open", pol="cp", a0=1.0, waist_lambda=0.4, fwhm_periods=2.0,
+                 t_peak_periods=0.5)
+    sim = oracle_mod.OracleSim(wl, _empty())
+    sim.step(12)
+    ez, ey = sim.f["ez"][:, 3], sim.f["ey"][:, 3]
+    jz = (ny - np.arange(ny)) % ny                # node mirror about j = ny/2
+    jy = ny - 1 - np.arange(ny)                   # half-node mirror
+    assert np.abs(ez).max() > 0.05 and np.abs(ey).max() > 0.05
+    np.testing.assert_allclose(ez[jz], ez, atol=1e-12 * np.abs(ez).max())
+    np.testing.assert_allclose(ey[jy], ey, atol=1e-12 * np.abs(ey).max())
+
+
+def test_laser_carrier_phase_is_zero_at_the_envelope_peak(oracle_mod):
+    # the LP source sin(t - t_peak) a0 envelope(t) profile(y): zero at the
+    # envelope peak and a0 a quarter period later on the axis (envelope
+    # 1/e time tau = FWHM / sqrt(2 ln 2)); t_peak of 1.25 periods is not a
+    # whole number of periods, so a phase counted from t = 0 would differ
+    wl = _vacuum(16, 8, bc="open", pol="lp-y", a0=2.0, waist_lambda=1e6, fwhm_periods=4.0,
+                 t_peak_periods=1.25)
+    sim = oracle_mod.OracleSim(wl, _empty())
+    tp = 1.25 * 2 * math.pi
+    tau = 4.0 * 2 * math.pi / math.sqrt(2 * math.log(2))
+    yc = 0.5 * wl.ny * sim.grid.dy
+    assert abs(sim.laser(tp, yc, 0)) < 1e-12
+    q = tp + 0.5 * math.pi
+    assert sim.laser(q, yc, 0) == pytest.approx(2.0 * math.exp(-((0.5 * math.pi) / tau) ** 2), rel=1e-9)
+    assert sim.laser(q, yc, 1) == 0.0
