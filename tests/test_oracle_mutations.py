@@ -1,6 +1,8 @@
 """Plant plausible mistakes in copies of the oracle (on the CPU) and check that
 the pins catch every one of them: test_oracle_pins.py for the 2D3V source,
-test_oracle3_pins.py for the 3D3V source."""
+test_oracle3_pins.py for the 3D3V source, and for the Python layer (the
+units derived from a workload, the beam loss, the co-moving window) the pins
+file of each."""
 import os
 import subprocess
 import sys
@@ -209,9 +211,10 @@ MUTATIONS_PY = [
 ]
 
 
-def _run_window_pins(old=None, new=None):
-    """Run the window pins against a copy of the oracle package (sources
-    included), optionally with one planted mistake; returns the pytest run."""
+def _run_py_pins(pins, old=None, new=None):
+    """Run one pins file against a copy of the oracle package (sources
+    included), optionally with one planted mistake in its Python layer;
+    returns the pytest run."""
     with tempfile.TemporaryDirectory() as td:
         pkg = os.path.join(td, "oracle")
         os.makedirs(pkg)
@@ -227,8 +230,12 @@ def _run_window_pins(old=None, new=None):
         env = dict(os.environ, PYTHONPATH=td + os.pathsep + ROOT)
         env.pop("PIC_ORACLE_LIB", None)
         return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                               os.path.join(ROOT, "tests", "test_oracle_window_pins.py")],
+                               os.path.join(ROOT, "tests", pins)],
                               cwd=td, env=env, capture_output=True, text=True, timeout=600)
+
+
+def _run_window_pins(old=None, new=None):
+    return _run_py_pins("test_oracle_window_pins.py", old, new)
 
 
 def test_window_pins_pass_on_an_unmodified_copy():
@@ -240,5 +247,67 @@ def test_window_pins_pass_on_an_unmodified_copy():
 def test_window_pins_catch_planted_mistake(name, old, new):
     r = _run_window_pins(old, new)
     # caught = a pin failed (not an error while collecting or building)
+    assert r.returncode == 1 and "failed" in r.stdout.splitlines()[-1], \
+        f"pins did not catch: {name}\n{r.stdout[-2000:]}"
+
+
+# planted mistakes in the rest of the Python layer: the oracle's units (the
+# grid it derives from a workload), the beam loss and more of the window;
+# each with the pins file that catches it
+MUTATIONS_PY_MORE = [
+    ("dx in wavelengths", "test_oracle_pins.py", "dx, dy = wl.dx_lambda * two_pi, wl.dy_lambda * two_pi",
+     "dx, dy = wl.dx_lambda, wl.dy_lambda * two_pi"),
+    ("dt without the Courant factor", "test_oracle_pins.py",
+     "dt = wl.cfl / math.sqrt(1.0 / dx ** 2 + 1.0 / dy ** 2)\n", "dt = 1.0 / math.sqrt(1.0 / dx ** 2 + 1.0 / dy ** 2)\n"),
+    ("tau from the field FWHM", "test_oracle_pins.py",
+     "tau = wl.fwhm_periods * two_pi / math.sqrt(2.0 * math.log(2.0))\n    return Grid(",
+     "tau = wl.fwhm_periods * two_pi / (2.0 * math.sqrt(math.log(2.0)))\n    return Grid("),
+    ("2d waist in wavelengths", "test_oracle_pins.py",
+     "w0=wl.waist_lambda * two_pi, tau=tau, t_peak=wl.t_peak_periods * two_pi)\n\n\ndef derive_grid3",
+     "w0=wl.waist_lambda, tau=tau, t_peak=wl.t_peak_periods * two_pi)\n\n\ndef derive_grid3"),
+    ("2d t_peak in periods", "test_oracle_pins.py",
+     "w0=wl.waist_lambda * two_pi, tau=tau, t_peak=wl.t_peak_periods * two_pi)\n\n\ndef derive_grid3",
+     "w0=wl.waist_lambda * two_pi, tau=tau, t_peak=wl.t_peak_periods)\n\n\ndef derive_grid3"),
+    ("3d dt without dz", "test_oracle3_pins.py",
+     "dt = wl.cfl / math.sqrt(1.0 / dx ** 2 + 1.0 / dy ** 2 + 1.0 / dz ** 2)",
+     "dt = wl.cfl / math.sqrt(1.0 / dx ** 2 + 1.0 / dy ** 2)"),
+    ("3d dz in wavelengths", "test_oracle3_pins.py", "wl.dz_lambda * two_pi\n", "wl.dz_lambda\n"),
+    ("3d waist in wavelengths", "test_oracle3_pins.py",
+     "w0=wl.waist_lambda * two_pi, tau=tau, t_peak=wl.t_peak_periods * two_pi)\n\n\nclass OracleSim",
+     "w0=wl.waist_lambda, tau=tau, t_peak=wl.t_peak_periods * two_pi)\n\n\nclass OracleSim"),
+    ("loss sigmoid sign", "test_oracle_loss_pins.py",
+     "a = d[\"w\"][live] * e / (1.0 + np.exp(-(e - e_cut_mev) / e_width_mev))",
+     "a = d[\"w\"][live] * e / (1.0 + np.exp((e - e_cut_mev) / e_width_mev))"),
+    ("loss not energy weighted", "test_oracle_loss_pins.py", "a = d[\"w\"][live] * e / (1.0",
+     "a = d[\"w\"][live] / (1.0"),
+    ("loss of the total energy", "test_oracle_loss_pins.py",
+     "e = (np.sqrt(1.0 + u2) - 1.0) * self.spec[s].m * MEC2_MEV\n        a =",
+     "e = np.sqrt(1.0 + u2) * self.spec[s].m * MEC2_MEV\n        a ="),
+    ("loss of a fixed spin axis", "test_oracle_loss_pins.py", "spin = d[(\"sx\", \"sy\", \"sz\")[axis]][live]",
+     "spin = d[\"sy\"][live]"),
+    ("loss counts removed particles", "test_oracle_loss_pins.py", "live = d[\"alive\"] > 0\n        u2",
+     "live = d[\"alive\"] >= 0\n        u2"),
+    ("loss energy without the mass", "test_oracle_loss_pins.py",
+     "e = (np.sqrt(1.0 + u2) - 1.0) * self.spec[s].m * MEC2_MEV\n        a =",
+     "e = (np.sqrt(1.0 + u2) - 1.0) * MEC2_MEV\n        a ="),
+    ("window boundary values from column n", "test_oracle_window_pins.py",
+     "self.f[\"byL\"][...] = self.f[\"by\"][..., n - 1]", "self.f[\"byL\"][...] = self.f[\"by\"][..., n]"),
+    ("window keeps the old Bz boundary", "test_oracle_window_pins.py",
+     "self.f[\"bzL\"][...] = self.f[\"bz\"][..., n - 1]", "pass"),
+    ("window renumbers injected plasma", "test_oracle_window_pins.py",
+     "alive=np.ones(len(d[\"ix\"]), np.int32),\n                   id=d[\"id\"].copy())",
+     "alive=np.ones(len(d[\"ix\"]), np.int32),\n                   id=np.arange(len(d[\"ix\"]), dtype=np.int32))"),
+]
+
+
+@pytest.mark.parametrize("pins", sorted({m[1] for m in MUTATIONS_PY_MORE}))
+def test_python_layer_pins_pass_on_an_unmodified_copy(pins):
+    r = _run_py_pins(pins)
+    assert r.returncode == 0, r.stdout[-2000:]
+
+
+@pytest.mark.parametrize("name,pins,old,new", MUTATIONS_PY_MORE, ids=[m[0] for m in MUTATIONS_PY_MORE])
+def test_python_layer_pins_catch_planted_mistake(name, pins, old, new):
+    r = _run_py_pins(pins, old, new)
     assert r.returncode == 1 and "failed" in r.stdout.splitlines()[-1], \
         f"pins did not catch: {name}\n{r.stdout[-2000:]}"

@@ -787,3 +787,18 @@ def test_laser_carrier_phase_is_zero_at_the_envelope_peak(oracle_mod):
     q = tp + 0.5 * math.pi
     assert sim.laser(q, yc, 0) == pytest.approx(2.0 * math.exp(-((0.5 * math.pi) / tau) ** 2), rel=1e-9)
     assert sim.laser(q, yc, 1) == 0.0
+
+
+def test_laser_waist_is_the_field_1_over_e_radius(oracle_mod):
+    # the LP source at a quarter period after the envelope peak: on the axis
+    # a0 times the envelope; w0 = waist off axis e^-1 times that (the waist
+    # is the 1/e radius of the field, in wavelengths: lambda = 2 pi c/omega0)
+    waist = 0.4
+    wl = _vacuum(16, 8, bc="open", pol="lp-y", a0=1.0, waist_lambda=waist, fwhm_periods=4.0,
+                 t_peak_periods=1.0)
+    sim = oracle_mod.OracleSim(wl, _empty())
+    t = 2 * math.pi + 0.5 * math.pi
+    yc = 0.5 * wl.ny * sim.grid.dy
+    w0 = waist * 2 * math.pi
+    assert sim.laser(t, yc + w0, 0) / sim.laser(t, yc, 0) == pytest.approx(math.exp(-1.0), rel=1e-12)
+    assert sim.laser(t, yc - 0.5 * w0, 0) / sim.laser(t, yc, 0) == pytest.approx(math.exp(-0.25), rel=1e-12)

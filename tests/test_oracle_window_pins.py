@@ -105,3 +105,27 @@ def test_gauss_law_across_shifts_with_injected_plasma(oracle_mod, dim):
     assert np.abs(sim.f["ey"]).max() > 0.3
     assert np.abs(sim.gauss_residual()).max() < 1e-11
     assert len(sim.p[0]["x"]) == idb
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_shift_relabels_columns_and_keeps_injected_ids(oracle_mod, dim):
+    # with every mesh value equal to its column index, a shift by n leaves
+    # column i holding i + n (the uncovered n columns at zero), and the left
+    # boundary values By(-1/2), Bz(-1/2) are those of the column that now sits
+    # at x = -1/2: old column n - 1.  Injected plasma keeps the ids it was
+    # given.
+    wl = _pulse_case(dim)
+    sim = oracle_mod.OracleSim(wl, _empty(dim))
+    n = 10
+    col = np.arange(wl.nx, dtype=float)
+    for k in sim.FIELD_KEYS:
+        sim.f[k][...] = col
+    inj = W.injection_particles(dataclasses.replace(wl, species=(dataclasses.replace(wl.species[0], ppc=1),)),
+                                n, seed=3, id_base=5000)
+    sim.shift_window(n, inj)
+    for k in sim.FIELD_KEYS:
+        np.testing.assert_array_equal(sim.f[k][..., :-n], np.broadcast_to(col[n:], sim.f[k][..., :-n].shape))
+        assert np.all(sim.f[k][..., -n:] == 0.0)
+    assert np.all(sim.f["byL"] == n - 1) and np.all(sim.f["bzL"] == n - 1)
+    ids = np.sort(sim.p[0]["id"])
+    np.testing.assert_array_equal(ids, 5000 + np.arange(len(inj[0]["id"])))
