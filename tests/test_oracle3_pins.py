@@ -378,3 +378,20 @@ def test_free_streaming_particle_3d(oracle_mod):
     assert p["y"][0] == pytest.approx((3.5 + 30 * g.dt * uu[1] / gam / g.dy) % 9, rel=1e-12)
     assert p["z"][0] == pytest.approx((5.75 + 30 * g.dt * uu[2] / gam / g.dz) % 8, rel=1e-12)
     assert p["ux"][0] == uu[0] and p["sx"][0] == 1.0
+
+
+def test_laser3_cp_components_are_staggered_like_e(oracle_mod):
+    # CP beam: E_y sits at (j+1/2, k) and E_z at (j, k+1/2), so near x_min E_y
+    # is mirror symmetric under j -> ny-1-j, k -> nz-k and E_z under
+    # j -> ny-j, k -> nz-1-k (both about the box axis)
+    ny = nz = 16
+    wl = _vacuum3(24, ny, nz, bc="open", pol="cp", a0=1.0, waist_lambda=0.5, fwhm_periods=2.0,
+                  t_peak_periods=0.5, dx=1 / 16, dy=1 / 8, dz=1 / 8)
+    sim = oracle_mod.OracleSim(wl, _empty3())
+    sim.step(10)
+    ey, ez = sim.f["ey"][:, :, 2], sim.f["ez"][:, :, 2]
+    assert np.abs(ey).max() > 0.05 and np.abs(ez).max() > 0.05
+    jh, jn = ny - 1 - np.arange(ny), (ny - np.arange(ny)) % ny
+    kh, kn = nz - 1 - np.arange(nz), (nz - np.arange(nz)) % nz
+    np.testing.assert_allclose(ey[np.ix_(kn, jh)], ey, atol=1e-12 * np.abs(ey).max())
+    np.testing.assert_allclose(ez[np.ix_(kh, jn)], ez, atol=1e-12 * np.abs(ez).max())

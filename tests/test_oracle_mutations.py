@@ -111,6 +111,32 @@ MUTATIONS = [
     ("x_max absorber uses Ey one column in",
      "f->bz[cl] = (2.0 * f->ey[cl] - (1.0 - r) * f->bz[cl - 1]) / (1.0 + r);",
      "f->bz[cl] = (2.0 * f->ey[cl - 1] - (1.0 - r) * f->bz[cl - 1]) / (1.0 + r);"),
+    ("Bx half step uses dx", "f->bx[c] -= h / g->dy * (f->ez[jp * nx + i] - f->ez[c]);",
+     "f->bx[c] -= h / g->dx * (f->ez[jp * nx + i] - f->ez[c]);"),
+    ("Ey source at node height", "or_laser(g, t, ((double)j + 0.5) * g->dy, 0, &gin);",
+     "or_laser(g, t, (double)j * g->dy, 0, &gin);"),
+    ("x_max By transverse term dropped", "f->by[cl] = (-2.0 * f->ez[cl] - (1.0 - r) * f->by[cl - 1] + q * dbxl) / (1.0 + r);",
+     "f->by[cl] = (-2.0 * f->ez[cl] - (1.0 - r) * f->by[cl - 1]) / (1.0 + r);"),
+    ("CP second component sin", "v = g->a0 / sqrt(2.0) * env * tr * (comp == 0 ? sin(ph) : cos(ph));",
+     "v = g->a0 / sqrt(2.0) * env * tr * (comp == 0 ? sin(ph) : sin(ph));"),
+    ("interp truncates", "long i0 = (long)floor(xs), j0 = (long)floor(ys);\n    double v = 0.0;",
+     "long i0 = (long)xs, j0 = (long)ys;\n    double v = 0.0;"),
+    ("Ex ignores Jx", "(f->bz[c] - f->bz[jm * nx + i]) / g->dy - f->jx[c]);",
+     "(f->bz[c] - f->bz[jm * nx + i]) / g->dy);"),
+    ("Ez By difference sign", "f->ez[c] += dt * ((f->by[c] - by_im) / g->dx -",
+     "f->ez[c] += dt * ((by_im - f->by[c]) / g->dx -"),
+    ("left boundary uses periodic values", "} else {\n                bz_im = f->bzL[j];\n                by_im = f->byL[j];",
+     "} else {\n                bz_im = f->bz[j * nx + nx - 1];\n                by_im = f->byL[j];"),
+    ("histogram sx unweighted", "out[5 * b + 2] += p->w[i] * p->sx[i];",
+     "out[5 * b + 2] += p->sx[i];"),
+    ("moments sz unweighted", "swz += p->w[i] * p->sz[i];",
+     "swz += p->sz[i];"),
+    ("div B y uses dx", "(f->by[jp * nx + i] - f->by[c]) / g->dy;",
+     "(f->by[jp * nx + i] - f->by[c]) / g->dx;"),
+    ("rho uses charge only", "rho[yj(g, j0 + dj) * g->nx + xi(g, i0 + di)] += sp->q * p->w[i] * wgt;",
+     "rho[yj(g, j0 + dj) * g->nx + xi(g, i0 + di)] += sp->q * wgt;"),
+    ("removal ignores the deposit", "or_deposit_one(g, f, sp->q * p->w[i], x_old[i], y_old[i], X1, Y1, vz[i]);\n        if (g->bc_x",
+     "if (g->bc_x == OR_BC_OPEN && (p->x[i] < 2.0 || p->x[i] >= (double)(g->nx - 2))) { p->alive[i] = 0; continue; }\n        or_deposit_one(g, f, sp->q * p->w[i], x_old[i], y_old[i], X1, Y1, vz[i]);\n        if (g->bc_x"),
 ]
 
 
@@ -169,6 +195,32 @@ MUTATIONS3 = [
      "(f->bz[at3(g, i, j, k + 1)] - f->bz[c]) / g->dy;"),
     ("3d removal at x_min from x = 1", "if (g->bc_x == OR_BC_OPEN && (p->x[i] < 2.0 ||",
      "if (g->bc_x == OR_BC_OPEN && (p->x[i] < 1.0 ||"),
+    ("3d Jx on next node", "f->jx[at3(g, i0 + i, j0 + j, k0 + k)] += cx * acc;",
+     "f->jx[at3(g, i0 + i + 1, j0 + j, k0 + k)] += cx * acc;"),
+    ("3d Ez source z height", "or3_laser(g, t, (double)j * g->dy, ((double)k + 0.5) * g->dz, 1, &fin);",
+     "or3_laser(g, t, (double)j * g->dy, (double)k * g->dz, 1, &fin);"),
+    ("3d left By source sign", "f->byL[b] = (2.0 * f->ez[c0] - (1.0 - r) * f->by[c0] - qy * dyb0 - 4.0 * fin) / (1.0 + r);",
+     "f->byL[b] = (2.0 * f->ez[c0] - (1.0 - r) * f->by[c0] - qy * dyb0 + 4.0 * fin) / (1.0 + r);"),
+    ("3d left Bz source factor", "f->bzL[b] = (4.0 * gin - 2.0 * f->ey[c0]",
+     "f->bzL[b] = (2.0 * gin - 2.0 * f->ey[c0]"),
+    ("3d Ex ignores Jx", "- (f->by[c] - f->by[ckm]) / g->dz - f->jx[c]);",
+     "- (f->by[c] - f->by[ckm]) / g->dz);"),
+    ("3d Ey z difference uses dx", "f->ey[c] += dt * ((f->bx[c] - f->bx[ckm]) / g->dz",
+     "f->ey[c] += dt * ((f->bx[c] - f->bx[ckm]) / g->dx"),
+    ("3d gather y weight uses x", "double w = shape1_3(xs - (double)i) * shape1_3(ys - (double)j) *",
+     "double w = shape1_3(xs - (double)i) * shape1_3(xs - (double)j) *"),
+    ("3d rho y weight", "shape1_3(p->y[n] - (double)(j0 + b)) *",
+     "shape1_3(p->y[n] - (double)(j0)) *"),
+    ("3d div E x uses dy", "div[c] = (f->ex[c] - f->ex[at3(g, i - 1, j, k)]) / g->dx +",
+     "div[c] = (f->ex[c] - f->ex[at3(g, i - 1, j, k)]) / g->dy +"),
+    ("3d Bx y curl uses Ey", "f->bx[c] -= h * ((f->ez[cjp] - f->ez[c]) / g->dy",
+     "f->bx[c] -= h * ((f->ey[cjp] - f->ez[c]) / g->dy"),
+    ("3d deposit z not unwrapped", "double Z1 = unwrap3(p->z[i], z_old[i], (double)g->nz);",
+     "double Z1 = p->z[i];"),
+    ("3d left dzBx sign", "double dzb0 = f->bx[c0] - f->bx[at3(g, 0, j, k - 1)];",
+     "double dzb0 = f->bx[at3(g, 0, j, k - 1)] - f->bx[c0];"),
+    ("3d right dyBx from the first column", "double dybl = f->bx[cl] - f->bx[at3(g, nx - 1, j - 1, k)];",
+     "double dybl = f->bx[cl] - f->bx[at3(g, 0, j - 1, k)];"),
 ]
 
 CASES = ([("pic_oracle.c", "test_oracle_pins.py") + m for m in MUTATIONS] +

@@ -802,3 +802,55 @@ def test_laser_waist_is_the_field_1_over_e_radius(oracle_mod):
     w0 = waist * 2 * math.pi
     assert sim.laser(t, yc + w0, 0) / sim.laser(t, yc, 0) == pytest.approx(math.exp(-1.0), rel=1e-12)
     assert sim.laser(t, yc - 0.5 * w0, 0) / sim.laser(t, yc, 0) == pytest.approx(math.exp(-0.25), rel=1e-12)
+
+
+def test_cp_components_are_a_quarter_period_apart(oracle_mod):
+    # CP (a0/sqrt 2 in each of Ey and Ez): on the axis of a wide beam, at the
+    # envelope peak the Ey source is 0 and the Ez source a0/sqrt 2; a quarter
+    # period later (envelope e^-((pi/2)/tau)^2) the roles swap
+    wl = _vacuum(16, 8, bc="open", pol="cp", a0=2.0, waist_lambda=1e6, fwhm_periods=4.0,
+                 t_peak_periods=1.0)
+    sim = oracle_mod.OracleSim(wl, _empty())
+    tp = 2 * math.pi
+    tau = 4.0 * 2 * math.pi / math.sqrt(2 * math.log(2))
+    yc = 0.5 * wl.ny * sim.grid.dy
+    amp = 2.0 / math.sqrt(2.0)
+    assert abs(sim.laser(tp, yc, 0)) < 1e-12
+    assert sim.laser(tp, yc, 1) == pytest.approx(amp, rel=1e-12)
+    q = tp + 0.5 * math.pi
+    env = math.exp(-((0.5 * math.pi) / tau) ** 2)
+    assert sim.laser(q, yc, 0) == pytest.approx(amp * env, rel=1e-12)
+    assert abs(sim.laser(q, yc, 1)) < 1e-12
+
+
+def test_gather_of_uniform_fields_everywhere(oracle_mod):
+    # the CIC weights of every staggered component sum to one at any position,
+    # within half a cell of the periodic seams too: uniform fields are
+    # gathered exactly
+    vals = {"ex": 0.3, "ey": -1.1, "ez": 0.7, "bx": 2.0, "by": -0.4, "bz": 1.3}
+    sim = _one_particle_sim(oracle_mod, vals, nx=8, ny=8)
+    rng = np.random.default_rng(9)
+    pts = [(0.1, 0.2), (0.45, 7.9), (7.95, 0.05), (3.3, 0.4)] + [tuple(v) for v in rng.uniform(0, 8, (20, 2))]
+    import ctypes as C
+    for X, Y in pts:
+        E, B = (C.c_double * 3)(), (C.c_double * 3)()
+        oracle_mod.lib().or_gather(C.byref(sim.grid), C.byref(sim._fields()), X, Y, E, B)
+        np.testing.assert_allclose(list(E), [vals["ex"], vals["ey"], vals["ez"]], rtol=1e-14)
+        np.testing.assert_allclose(list(B), [vals["bx"], vals["by"], vals["bz"]], rtol=1e-14)
+
+
+def test_div_b_of_a_linear_field_with_unequal_cells(oracle_mod):
+    # B = (alpha x, beta y) at the Yee positions of Bx (i, j+1/2) and By
+    # (i+1/2, j): div B on the cell centres is alpha + beta wherever the
+    # stencil does not cross the periodic seam
+    wl = _vacuum(12, 10)
+    sim = oracle_mod.OracleSim(wl, _empty())
+    g = sim.grid
+    assert g.dx != g.dy
+    alpha, beta = -0.8, 1.7
+    i = np.arange(wl.nx)[None, :]
+    j = np.arange(wl.ny)[:, None]
+    sim.f["bx"][...] = alpha * i * g.dx + 0.0 * j
+    sim.f["by"][...] = beta * j * g.dy + 0.0 * i
+    d = sim.div_b()
+    np.testing.assert_allclose(d[:-1, :-1], alpha + beta, rtol=1e-12)
