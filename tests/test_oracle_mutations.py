@@ -137,6 +137,30 @@ MUTATIONS = [
      "rho[yj(g, j0 + dj) * g->nx + xi(g, i0 + di)] += sp->q * wgt;"),
     ("removal ignores the deposit", "or_deposit_one(g, f, sp->q * p->w[i], x_old[i], y_old[i], X1, Y1, vz[i]);\n        if (g->bc_x",
      "if (g->bc_x == OR_BC_OPEN && (p->x[i] < 2.0 || p->x[i] >= (double)(g->nx - 2))) { p->alive[i] = 0; continue; }\n        or_deposit_one(g, f, sp->q * p->w[i], x_old[i], y_old[i], X1, Y1, vz[i]);\n        if (g->bc_x"),
+    ("Ey curl uses Bz at i+1", "f->ey[c] += dt * (-(f->bz[c] - bz_im) / g->dx - f->jy[c]);",
+     "f->ey[c] += dt * (-(f->bz[j * nx + xi(g, i + 1)] - f->bz[c]) / g->dx - f->jy[c]);"),
+    ("Bz half step y term sign", "h / g->dy * (f->ex[jp * nx + i] - f->ex[c]);\n            }",
+     "h / g->dy * (f->ex[c] - f->ex[jp * nx + i]);\n            }"),
+    ("mean energy unweighted", "swe += p->w[i] * ek;",
+     "swe += ek;"),
+    ("histogram top bin clamp dropped", "if (b >= nbins)\n            b = nbins - 1;",
+     "if (b > nbins)\n            b = nbins - 1;"),
+    ("moments P x from sy", "swx += p->w[i] * p->sx[i];",
+     "swx += p->w[i] * p->sy[i];"),
+    ("Jx stencil row offset", "f->jx[yj(g, j0 + l) * g->nx + xi(g, i0 + k)] += cx * acc;",
+     "f->jx[yj(g, j0 + l) * g->nx + xi(g, i0 + k + 1)] += cx * acc;"),
+    ("Wz first-order term", "0.5 * dSx[k] * S0y[l] +",
+     "dSx[k] * S0y[l] +"),
+    ("spin rotation cos/sin swapped", "s[k] = s[k] * c + nxs[k] * sn + n[k] * ns * (1.0 - c);",
+     "s[k] = s[k] * sn + nxs[k] * c + n[k] * ns * (1.0 - sn);"),
+    ("omega E term sign", "Om[k] = qm * (omB * B[k] - omv * vB * v[k] - omE * vxE[k]);",
+     "Om[k] = qm * (omB * B[k] - omv * vB * v[k] + omE * vxE[k]);"),
+    ("boris t uses gamma of u0", "double gm = sqrt(1.0 + dot3(um, um));",
+     "double gm = sqrt(1.0 + dot3(u, u));"),
+    ("periodic x wrap missing", "if (g->bc_x == OR_BC_PERIODIC)\n            X1 = wrap_pos(X1, (double)g->nx);\n        Y1",
+     "if (0)\n            X1 = wrap_pos(X1, (double)g->nx);\n        Y1"),
+    ("div E x uses the wrong neighbour", "div[c] = (f->ex[c] - f->ex[j * nx + im]) / g->dx +",
+     "div[c] = (f->ex[j * nx + xi(g, i + 1)] - f->ex[c]) / g->dx +"),
 ]
 
 
@@ -221,21 +245,45 @@ MUTATIONS3 = [
      "double dzb0 = f->bx[at3(g, 0, j, k - 1)] - f->bx[c0];"),
     ("3d right dyBx from the first column", "double dybl = f->bx[cl] - f->bx[at3(g, nx - 1, j - 1, k)];",
      "double dybl = f->bx[cl] - f->bx[at3(g, 0, j - 1, k)];"),
+    ("3d By x curl sign", "- (f->ez[cip] - f->ez[c]) / g->dx);",
+     "+ (f->ez[cip] - f->ez[c]) / g->dx);"),
+    ("3d Ez x difference uses dy", "f->ez[c] += dt * ((f->by[c] - by_im) / g->dx",
+     "f->ez[c] += dt * ((f->by[c] - by_im) / g->dy"),
+    ("3d Ex y term uses Bx", "f->ex[c] += dt * ((f->bz[c] - f->bz[cjm]) / g->dy",
+     "f->ex[c] += dt * ((f->bx[c] - f->bx[cjm]) / g->dy"),
+    ("3d rho x weight", "double w = shape1_3(p->x[n] - (double)(i0 + a)) *",
+     "double w = shape1_3(p->x[n] - (double)(i0)) *"),
+    ("3d div B y uses dz", "(f->by[at3(g, i, j + 1, k)] - f->by[c]) / g->dy +",
+     "(f->by[at3(g, i, j + 1, k)] - f->by[c]) / g->dz +"),
+    ("3d laser LP into Ez", "v = comp == 0 ? g->a0 * env * sin(ph) : 0.0;",
+     "v = comp == 1 ? g->a0 * env * sin(ph) : 0.0;"),
+    ("3d Jy running sum drops Wy", "acc += dSy[j] * xz;",
+     "acc += dSy[j] * S0x[i];"),
+    ("3d Jz prefix over the wrong axis", "f->jz[at3(g, i0 + i, j0 + j, k0 + k)] += cz * acc;",
+     "f->jz[at3(g, i0 + i, j0 + k, k0 + j)] += cz * acc;"),
+    ("3d left Bz uses Ey at x=1", "f->bzL[b] = (4.0 * gin - 2.0 * f->ey[c0]",
+     "f->bzL[b] = (4.0 * gin - 2.0 * f->ey[c0 + 1]"),
+    ("3d gather z weight uses y", "shape1_3(zs - (double)k);",
+     "shape1_3(ys - (double)k);"),
+    ("3d E update x periodic neighbour", "by_im = f->by[at3(g, nx - 1, j, k)];",
+     "by_im = f->by[at3(g, 0, j, k)];"),
 ]
 
 CASES = ([("pic_oracle.c", "test_oracle_pins.py") + m for m in MUTATIONS] +
          [("pic_oracle3.c", "test_oracle3_pins.py") + m for m in MUTATIONS3])
 
 
-@pytest.mark.parametrize("src_name,pins,name,old,new", CASES, ids=[c[2] for c in CASES])
-def test_pins_catch_planted_mistake(src_name, pins, name, old, new):
+def _c_caught(src_name, pins, name, old, new):
+    """(caught, detail): the pins file run against a copy of the C oracle with
+    one planted mistake."""
     import shutil
     with tempfile.TemporaryDirectory() as td:
         srcs = []
         for f in ("pic_oracle.c", "pic_oracle3.c"):
             text = open(os.path.join(ROOT, "oracle", f)).read()
             if f == src_name:
-                assert text.count(old) >= 1, f"mutation anchor not found: {name}"
+                if text.count(old) < 1:
+                    return False, f"mutation anchor not found: {name}"
                 text = text.replace(old, new, 1)
             srcs.append(os.path.join(td, f))
             with open(srcs[-1], "w") as fh:
@@ -248,7 +296,13 @@ def test_pins_catch_planted_mistake(src_name, pins, name, old, new):
         r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                             os.path.join(ROOT, "tests", pins)],
                            cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
-        assert r.returncode != 0, f"pins did not catch: {name}\n{r.stdout[-2000:]}"
+        return r.returncode != 0, f"pins did not catch: {name}\n{r.stdout[-2000:]}"
+
+
+@pytest.mark.parametrize("src_name,pins,name,old,new", CASES, ids=[c[2] for c in CASES])
+def test_pins_catch_planted_mistake(outcomes, src_name, pins, name, old, new):
+    caught, detail = outcomes[("c", name)]
+    assert caught, detail
 
 
 # planted mistakes in the oracle's Python layer (the co-moving window), caught
@@ -295,12 +349,18 @@ def test_window_pins_pass_on_an_unmodified_copy():
     assert r.returncode == 0, r.stdout[-2000:]
 
 
+def _py_caught(pins, name, old, new):
+    """(caught, detail) for one planted mistake in the Python layer: caught =
+    a pin failed (not an error while collecting or building)."""
+    r = _run_py_pins(pins, old, new)
+    last = r.stdout.splitlines()[-1] if r.stdout.strip() else ""
+    return r.returncode == 1 and "failed" in last, f"pins did not catch: {name}\n{r.stdout[-2000:]}"
+
+
 @pytest.mark.parametrize("name,old,new", MUTATIONS_PY, ids=[m[0] for m in MUTATIONS_PY])
-def test_window_pins_catch_planted_mistake(name, old, new):
-    r = _run_window_pins(old, new)
-    # caught = a pin failed (not an error while collecting or building)
-    assert r.returncode == 1 and "failed" in r.stdout.splitlines()[-1], \
-        f"pins did not catch: {name}\n{r.stdout[-2000:]}"
+def test_window_pins_catch_planted_mistake(outcomes, name, old, new):
+    caught, detail = outcomes[("window", name)]
+    assert caught, detail
 
 
 # planted mistakes in the rest of the Python layer: the oracle's units (the
@@ -359,7 +419,19 @@ def test_python_layer_pins_pass_on_an_unmodified_copy(pins):
 
 
 @pytest.mark.parametrize("name,pins,old,new", MUTATIONS_PY_MORE, ids=[m[0] for m in MUTATIONS_PY_MORE])
-def test_python_layer_pins_catch_planted_mistake(name, pins, old, new):
-    r = _run_py_pins(pins, old, new)
-    assert r.returncode == 1 and "failed" in r.stdout.splitlines()[-1], \
-        f"pins did not catch: {name}\n{r.stdout[-2000:]}"
+def test_python_layer_pins_catch_planted_mistake(outcomes, name, pins, old, new):
+    caught, detail = outcomes[("python", name)]
+    assert caught, detail
+
+
+@pytest.fixture(scope="module")
+def outcomes():
+    """Every planted mistake's pins run, once, on all host cores at a time
+    (each in its own temporary copy of the oracle and its own process)."""
+    from concurrent.futures import ThreadPoolExecutor
+    jobs = {("c", c[2]): (_c_caught, c) for c in CASES}
+    jobs.update({("window", m[0]): (_py_caught, ("test_oracle_window_pins.py",) + m) for m in MUTATIONS_PY})
+    jobs.update({("python", m[0]): (_py_caught, (m[1], m[0], m[2], m[3])) for m in MUTATIONS_PY_MORE})
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        futs = {k: ex.submit(f, *a) for k, (f, a) in jobs.items()}
+        return {k: fut.result() for k, fut in futs.items()}

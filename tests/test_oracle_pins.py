@@ -854,3 +854,26 @@ def test_div_b_of_a_linear_field_with_unequal_cells(oracle_mod):
     sim.f["by"][...] = beta * j * g.dy + 0.0 * i
     d = sim.div_b()
     np.testing.assert_allclose(d[:-1, :-1], alpha + beta, rtol=1e-12)
+
+
+def test_histogram_keeps_a_particle_just_below_emax_in_the_last_bin(oracle_mod):
+    # a particle one ulp below emax is inside [emin, emax); with log bins its
+    # bin coordinate log(e/emin)/log(emax/emin) rounds to exactly 1.0, one bin
+    # past the last, and must still be counted in the last bin
+    sp = W.Species("e", q=-1.0, m=1.0, a=0.0, n0=0.01, ppc=1, u_th=0.0, s0=(1, 0, 0))
+    wl = W.Workload(name="h", nx=8, ny=8, dx_lambda=1 / 16, dy_lambda=1 / 16, cfl=0.95,
+                    steps=1, species=(sp,), pol="none", bc_x="periodic")
+    f32 = np.float32
+    d = dict(ix=np.array([3], np.int32), iy=np.array([3], np.int32), ox=np.array([0.5], f32),
+             oy=np.array([0.5], f32), ux=np.array([3.0], f32), uy=np.zeros(1, f32), uz=np.zeros(1, f32),
+             sx=np.zeros(1, f32), sy=np.ones(1, f32), sz=np.zeros(1, f32), w=np.ones(1, f32),
+             id=np.zeros(1, np.int32))
+    sim = oracle_mod.OracleSim(wl, [d])
+    ek = sim.moments(0)[5]                      # the particle's kinetic energy (weight 1)
+    emax = float(np.nextafter(ek, np.inf))
+    emin, nbins = ek / 100.0, 8
+    # the case is the one the clamp exists for: the bin coordinate rounds to 1
+    assert math.floor(math.log(ek / emin) / math.log(emax / emin) * nbins) == nbins
+    assert sim.moments(0, emin, emax)[4] == 1
+    h = sim.histogram(0, emin, emax, nbins, True)
+    assert h[:, 0].sum() == 1 and h[-1, 0] == 1 and h[-1, 3] == 1.0
