@@ -24,7 +24,12 @@
  *     pic_create, freed at pic_destroy); host pointers passed in are only
  *     read or written during the call;
  *   - a context is bound to the CUDA device that was current at pic_create;
- *     calls on one context must not overlap (one host thread at a time).
+ *     calls on one context must not overlap (one host thread at a time);
+ *   - each compute entry point names the equation, section or published
+ *     method it follows (a1-a8 are the steps of one PIC step with spin);
+ *     the calls that only configure a context, move state between host and
+ *     device, bind memory, report sizes, counters or errors, or replay steps
+ *     from CUDA graphs have no counterpart in the paper.
  *
  * Mesh layout (host arrays are row-major [ny][nx] float32).  Element [j][i] of
  *   Ex sits at (i+1/2, j)   Ey at (i, j+1/2)   Ez at (i, j)
