@@ -395,3 +395,55 @@ def test_laser3_cp_components_are_staggered_like_e(oracle_mod):
     kh, kn = nz - 1 - np.arange(nz), (nz - np.arange(nz)) % nz
     np.testing.assert_allclose(ey[np.ix_(kn, jh)], ey, atol=1e-12 * np.abs(ey).max())
     np.testing.assert_allclose(ez[np.ix_(kh, jn)], ez, atol=1e-12 * np.abs(ez).max())
+
+
+def test_split_calls_equal_the_whole_step_3d(oracle_mod):
+    # as in 2D3V: the calls one by one are the whole step, bit for bit, with
+    # the laser entering (the field update reads the step index for it)
+    wl = W.small_case3(nx=20, ny=8, nz=6, ppc=1, u_th=0.3, two_species=True)
+    parts = W.generate_particles(wl)
+    a, b = oracle_mod.OracleSim(wl, parts, step=3), oracle_mod.OracleSim(wl, parts, step=3)
+    a.step(3)
+    for _ in range(3):
+        b.zero_current()
+        saved = [b.push(s) for s in range(len(b.p))]
+        for s, old in enumerate(saved):
+            b.deposit(s, *old)
+        b.field_update()
+    assert np.abs(a.f["ey"]).max() > 0
+    for k in a.f:
+        assert np.array_equal(a.f[k], b.f[k]), k
+    for s in range(2):
+        for k in a.p[s]:
+            assert np.array_equal(a.p[s][k], b.p[s][k]), (s, k)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_immobile_species_is_never_moved(oracle_mod, dim):
+    # an immobile species (the ions) keeps its particles bit for bit through
+    # whole steps in strong fields, while the mobile one moves
+    wl = (W.small_case(nx=20, ny=8, ppc=1, u_th=0.3, two_species=True, bc_x="periodic", pol="none") if dim == 2
+          else W.small_case3(nx=12, ny=8, nz=6, ppc=1, u_th=0.3, two_species=True, bc_x="periodic", pol="none"))
+    wl = dataclasses.replace(wl, species=(wl.species[0], dataclasses.replace(wl.species[1], mobile=False)))
+    parts = W.generate_particles(wl)
+    sim = oracle_mod.OracleSim(wl, parts, fields=W.random_fields(wl, seed=8, e_amp=0.5, b_amp=0.5))
+    before = {k: v.copy() for k, v in sim.p[1].items()}
+    x0 = sim.p[0]["x"].copy()
+    sim.step(3)
+    for k, v in before.items():
+        assert np.array_equal(sim.p[1][k], v), k
+    assert not np.array_equal(sim.p[0]["x"], x0)
+
+
+def test_spectra_of_3d_particles_are_those_of_their_momenta(oracle_mod):
+    # the spectra read only u, s, w and the alive flag: a 3D3V species gives
+    # the (pinned) 2D3V spectra of the same momenta, linear and log bins
+    wl3 = W.small_case3(nx=12, ny=8, nz=6, ppc=2, u_th=0.8, bc_x="periodic")
+    wl2 = W.small_case(nx=12, ny=8 * 6, ppc=2, u_th=0.8, bc_x="periodic")
+    p3 = W.generate_particles(wl3)[0]
+    p2 = {k: v for k, v in p3.items() if k not in ("iz", "oz")}
+    p2["iy"] = (p3["iy"] + 8 * p3["iz"]).astype(np.int32)
+    s3, s2 = oracle_mod.OracleSim(wl3, [p3]), oracle_mod.OracleSim(wl2, [p2])
+    for log_bins, (lo, hi) in ((False, (0.0, 0.5)), (True, (0.01, 0.5))):
+        np.testing.assert_array_equal(s3.histogram(0, lo, hi, 9, log_bins), s2.histogram(0, lo, hi, 9, log_bins))
+    np.testing.assert_array_equal(s3.moments(0, 0.01, 0.5), s2.moments(0, 0.01, 0.5))

@@ -409,6 +409,36 @@ MUTATIONS_PY_MORE = [
     ("window renumbers injected plasma", "test_oracle_window_pins.py",
      "alive=np.ones(len(d[\"ix\"]), np.int32),\n                   id=d[\"id\"].copy())",
      "alive=np.ones(len(d[\"ix\"]), np.int32),\n                   id=np.arange(len(d[\"ix\"]), dtype=np.int32))"),
+    ("2d positions drop the offsets", "test_oracle3_pins.py",
+     "x=d[\"ix\"].astype(np.float64) + d[\"ox\"].astype(np.float64),\n                y=d[\"iy\"].astype(np.float64) + d[\"oy\"].astype(np.float64),\n                ux",
+     "x=d[\"ix\"].astype(np.float64) + d[\"ox\"].astype(np.float64),\n                y=d[\"iy\"].astype(np.float64) + 0.5,\n                ux"),
+    ("2d background with the wrong sign", "test_oracle_pins.py",
+     "        self.rho_bg = np.zeros((ny, nx))\n        if wl.neutralizing_background:\n            self.rho_bg = -self.rho()",
+     "        self.rho_bg = np.zeros((ny, nx))\n        if wl.neutralizing_background:\n            self.rho_bg = self.rho()"),
+    ("3d background with the wrong sign", "test_oracle3_pins.py",
+     "        self.rho_bg = np.zeros(shape)\n        if wl.neutralizing_background:\n            self.rho_bg = -self.rho()",
+     "        self.rho_bg = np.zeros(shape)\n        if wl.neutralizing_background:\n            self.rho_bg = self.rho()"),
+    ("2d gauss residual leaves out the background", "test_oracle_pins.py",
+     "        r = self.div_e() - self.rho() - self.rho_bg\n        if self.wl.bc_x == \"open\":\n            r = r[:, 3:",
+     "        r = self.div_e() - self.rho()\n        if self.wl.bc_x == \"open\":\n            r = r[:, 3:"),
+    ("3d z offsets dropped", "test_oracle3_pins.py",
+     "z=d[\"iz\"].astype(np.float64) + d[\"oz\"].astype(np.float64),",
+     "z=d[\"iz\"].astype(np.float64) + 0.5,"),
+    ("3d field update without the step index", "test_oracle3_pins.py",
+     "lib().or3_field_update(C.byref(self.grid), C.byref(self._fields()), self.step_index)",
+     "lib().or3_field_update(C.byref(self.grid), C.byref(self._fields()), 0)"),
+    ("2d step index not advanced", "test_oracle_pins.py",
+     "lib().or_field_update(C.byref(self.grid), C.byref(self._fields()), self.step_index)\n        self.step_index += 1",
+     "lib().or_field_update(C.byref(self.grid), C.byref(self._fields()), self.step_index)"),
+    ("3d immobile species pushed", "test_oracle3_pins.py",
+     "        for _ in range(nsteps):\n            parts = (Parts3 * nsp)",
+     "        self.mobile[...] = 1\n        for _ in range(nsteps):\n            parts = (Parts3 * nsp)"),
+    ("window injected offsets dropped", "test_oracle_window_pins.py",
+     "out[a] = d[\"i\" + a].astype(np.float64) + d[\"o\" + a].astype(np.float64)",
+     "out[a] = d[\"i\" + a].astype(np.float64)"),
+    ("3d histogram log flag ignored", "test_oracle3_pins.py",
+     "1 if log_bins else 0, _dp(out))\n        return out.reshape(nbins, 5)\n\n    def laser(self, t, y, z, comp):",
+     "0, _dp(out))\n        return out.reshape(nbins, 5)\n\n    def laser(self, t, y, z, comp):"),
 ]
 
 

@@ -877,3 +877,26 @@ def test_histogram_keeps_a_particle_just_below_emax_in_the_last_bin(oracle_mod):
     assert sim.moments(0, emin, emax)[4] == 1
     h = sim.histogram(0, emin, emax, nbins, True)
     assert h[:, 0].sum() == 1 and h[-1, 0] == 1 and h[-1, 3] == 1.0
+
+
+def test_split_calls_equal_the_whole_step(oracle_mod):
+    # push + deposit of every species and then the field update, called one
+    # by one, is the whole step (whose laser injection is pinned above): the
+    # same state bit for bit after several steps with the laser entering
+    wl = W.small_case(nx=24, ny=12, ppc=2, u_th=0.3, two_species=True)
+    parts = W.generate_particles(wl)
+    a, b = oracle_mod.OracleSim(wl, parts, step=3), oracle_mod.OracleSim(wl, parts, step=3)
+    a.step(4)
+    for _ in range(4):
+        b.zero_current()
+        saved = [b.push(s) for s in range(len(b.p))]
+        for s, old in enumerate(saved):
+            b.deposit(s, *old)
+        b.field_update()
+    assert a.step_index == b.step_index == 7
+    assert np.abs(a.f["ey"]).max() > 0
+    for k in a.f:
+        assert np.array_equal(a.f[k], b.f[k]), k
+    for s in range(2):
+        for k in a.p[s]:
+            assert np.array_equal(a.p[s][k], b.p[s][k]), (s, k)

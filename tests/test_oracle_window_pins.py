@@ -129,3 +129,7 @@ def test_shift_relabels_columns_and_keeps_injected_ids(oracle_mod, dim):
     assert np.all(sim.f["byL"] == n - 1) and np.all(sim.f["bzL"] == n - 1)
     ids = np.sort(sim.p[0]["id"])
     np.testing.assert_array_equal(ids, 5000 + np.arange(len(inj[0]["id"])))
+    # and sit where they were given, cell plus offset, in the moved box
+    o = np.argsort(sim.p[0]["id"])
+    np.testing.assert_array_equal(sim.p[0]["x"][o], inj[0]["ix"] + inj[0]["ox"].astype(np.float64))
+    np.testing.assert_array_equal(sim.p[0]["y"][o], inj[0]["iy"] + inj[0]["oy"].astype(np.float64))
