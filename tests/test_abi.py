@@ -144,3 +144,15 @@ def test_moments_noalloc_checks_its_arguments_on_the_host():
     nulls = [None] * 8 + args[8:]
     assert L.pic_moments_noalloc(10, *nulls) == -1
     assert b"null" in L.pic_last_error(None)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    # without libpic.so the binding raises; there is no other implementation
+    # to fall back to
+    missing = str(tmp_path / "libpic.so")
+    monkeypatch.setattr(pic, "_lib", None)
+    monkeypatch.setattr(pic, "LIB_PATH", missing)
+    with pytest.raises(OSError, match="CUDA library not built"):
+        pic.load(build=False)
+    with pytest.raises(OSError):
+        pic._check(-1)                      # any status lookup needs the library too
