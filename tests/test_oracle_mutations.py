@@ -161,6 +161,28 @@ MUTATIONS = [
      "if (0)\n            X1 = wrap_pos(X1, (double)g->nx);\n        Y1"),
     ("div E x uses the wrong neighbour", "div[c] = (f->ex[c] - f->ex[j * nx + im]) / g->dx +",
      "div[c] = (f->ex[j * nx + xi(g, i + 1)] - f->ex[c]) / g->dx +"),
+    ("stencil origin off by one", "long i0 = (long)floor(X0) - 1, j0 = (long)floor(Y0) - 1;",
+     "long i0 = (long)floor(X0) - 1, j0 = (long)floor(Y0);"),
+    ("Wz first term from S1", "double wz = S0x[k] * S0y[l] + 0.5 * dSx[k] * S0y[l] +",
+     "double wz = S1x[k] * S1y[l] + 0.5 * dSx[k] * S0y[l] +"),
+    ("Wx uses dSy fully", "acc += dSx[k] * (S0y[l] + 0.5 * dSy[l]);",
+     "acc += dSx[k] * (S0y[l] + dSy[l]);"),
+    ("rotation n.s term sign", "s[k] = s[k] * c + nxs[k] * sn + n[k] * ns * (1.0 - c);",
+     "s[k] = s[k] * c + nxs[k] * sn - n[k] * ns * (1.0 - c);"),
+    ("boris s without t2", "s[k] = 2.0 * t[k] / (1.0 + t2);",
+     "s[k] = 2.0 * t[k];"),
+    ("boris up uses s", "cross3(um, t, c);\n    for (int k = 0; k < 3; ++k)\n        up[k] = um[k] + c[k];",
+     "cross3(um, s, c);\n    for (int k = 0; k < 3; ++k)\n        up[k] = um[k] + c[k];"),
+    ("omega v from u not gamma", "double v[3] = {ubar[0] / gam, ubar[1] / gam, ubar[2] / gam};",
+     "double v[3] = {ubar[0], ubar[1], ubar[2]};"),
+    ("interp sy ignored", "double xs = X - sx, ys = Y - sy;",
+     "double xs = X - sx, ys = Y;"),
+    ("shape wider", "return a < 1.0 ? 1.0 - a : 0.0;\n}\n\nstatic double dot3",
+     "return a < 1.0 ? 1.0 - 0.5 * a : 0.0;\n}\n\nstatic double dot3"),
+    ("E step uses half dt", "    double dt = g->dt;\n    b_half(g, f, 0.5 * dt);",
+     "    double dt = 0.5 * g->dt;\n    b_half(g, f, dt);"),
+    ("second B half skipped", "    b_half(g, f, 0.5 * dt);\n}\n\nvoid or_step",
+     "}\n\nvoid or_step"),
 ]
 
 
@@ -267,6 +289,16 @@ MUTATIONS3 = [
      "shape1_3(ys - (double)k);"),
     ("3d E update x periodic neighbour", "by_im = f->by[at3(g, nx - 1, j, k)];",
      "by_im = f->by[at3(g, 0, j, k)];"),
+    ("3d stencil origin z", "k0 = (long)floor(Z0) - 1;",
+     "k0 = (long)floor(Z0);"),
+    ("3d Wx yz uses S1 for dSz term", "double yz = S0y[j] * S0z[k] + 0.5 * dSy[j] * S0z[k] + 0.5 * S0y[j] * dSz[k] +",
+     "double yz = S0y[j] * S0z[k] + 0.5 * dSy[j] * S0z[k] + 0.5 * S0y[j] * S0z[k] +"),
+    ("3d interp sz ignored", "double xs = X - sx, ys = Y - sy, zs = Z - sz;",
+     "double xs = X - sx, ys = Y - sy, zs = Z;"),
+    ("3d E step uses dt/2", "    double dt = g->dt;\n    b_half3(g, f, 0.5 * dt);",
+     "    double dt = 0.5 * g->dt;\n    b_half3(g, f, dt);"),
+    ("3d Jz accumulates dSy", "acc += dSz[k] * xy;",
+     "acc += dSy[k] * xy;"),
 ]
 
 CASES = ([("pic_oracle.c", "test_oracle_pins.py") + m for m in MUTATIONS] +
