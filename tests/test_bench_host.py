@@ -68,3 +68,26 @@ def test_traffic_record_only_for_its_source(tmp_path, monkeypatch):
     assert bench.traffic_record(3, W.CONFIG3, True) is None          # another workload
     monkeypatch.setattr(bench, "kernel_source_hash", lambda dim: "0" * 64)
     assert bench.traffic_record(3, wl, True) is None                  # another kernel source
+
+
+def _dt(wl):
+    import math
+    d = [wl.dx_lambda, wl.dy_lambda] + ([wl.dz_lambda] if wl.dim == 3 else [])
+    return wl.cfl / math.sqrt(sum((1.0 / (2 * math.pi * v)) ** 2 for v in d))
+
+
+def test_timed_region_starts_in_the_interaction_phase():
+    # 40 steps after the envelope peak reaches x = 0: t_peak = 15 periods,
+    # config 2 dt = 0.2597/omega0 -> step 363 + 40; config 3 dt = 0.1319 -> 715 + 40
+    assert _dt(W.CONFIG2) == pytest.approx(0.2598, abs=1e-4)
+    assert bench.interaction_start(W.CONFIG2, _dt(W.CONFIG2)) == 403
+    assert bench.interaction_start(W.CONFIG3, _dt(W.CONFIG3)) == 755
+    # no laser, no interaction phase to wait for
+    import dataclasses
+    assert bench.interaction_start(dataclasses.replace(W.CONFIG2, pol="none"), 0.26) == 0
+
+
+def test_window_follows_the_envelope_peak():
+    # the co-moving leg starts when the envelope peak reaches 3/4 of the box
+    # (x = 384 cells of dx = lambda/20 in config 2): step 828
+    assert bench.window_start(W.CONFIG2, _dt(W.CONFIG2), 0.75) == 828
