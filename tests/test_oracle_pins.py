@@ -66,14 +66,21 @@ def test_boris_crossed_fields_drift(oracle_mod):
 def test_boris_plane_wave_drift_velocity(oracle_mod):
     # electron starting at rest at a zero of the vector potential of a linearly
     # polarised plane wave (E_y = B_z = a0 cos(t - x)) drifts along x at
-    # a0^2 / (4 + a0^2)  (textbook figure-of-eight orbit)
+    # a0^2 / (4 + a0^2), with the figure-of-eight amplitudes of the textbook
+    # orbit
     a0, qm, dt = 1.5, -1.0, 2 * math.pi / 600
-    u, x, t = np.zeros(3), 0.0, 0.0
+    x, t = 0.0, 0.0
     x_half = 0.0
-    # positions at integer times, momentum at half times: start u^{-1/2} = 0
+    # positions at integer times, momentum at half times: u^{-1/2} is the
+    # exact orbit of the electron at rest at t = 0, taken at t = -dt/2
+    # (u_y = -a0 sin(phi), u_x = u_y^2 / 2); starting from u^{-1/2} = 0 would
+    # leave the canonical momentum off by a0 dt / 2 and y drifting
+    uy0 = a0 * math.sin(0.5 * dt)
+    u = np.array([0.5 * uy0 ** 2, uy0, 0.0])
     periods = 0
     t0 = x0 = None
     phi_prev = 0.0
+    y, ys, uxs = 0.0, [0.0], [0.0]
     while periods < 6:
         ph = t - x
         E = (0.0, a0 * math.cos(ph), 0.0)
@@ -81,6 +88,9 @@ def test_boris_plane_wave_drift_velocity(oracle_mod):
         u = oracle_mod.boris(qm, dt, E, Bf, u)
         g = math.sqrt(1 + u @ u)
         x += dt * u[0] / g
+        y += dt * u[1] / g
+        ys.append(y)
+        uxs.append(u[0])
         t += dt
         phi = t - x
         if math.floor(phi / (2 * math.pi)) > math.floor(phi_prev / (2 * math.pi)):
@@ -94,6 +104,11 @@ def test_boris_plane_wave_drift_velocity(oracle_mod):
         phi_prev = phi
     vd = (xc - x0) / (tc - t0)
     assert vd == pytest.approx(a0 ** 2 / (4 + a0 ** 2), rel=2e-3)
+    # the figure of eight: u_y = -a0 sin(phi) (canonical momentum), so
+    # y = a0 (cos(phi) - 1), a transverse excursion of 2 a0, and
+    # u_x = u_y^2 / 2 peaks at a0^2 / 2
+    assert max(ys) - min(ys) == pytest.approx(2 * a0, rel=2e-3)
+    assert max(uxs) == pytest.approx(a0 ** 2 / 2, rel=2e-3)
 
 
 # ---------------------------------------------------------------------------
