@@ -915,3 +915,23 @@ def test_split_calls_equal_the_whole_step(oracle_mod):
     for s in range(2):
         for k in a.p[s]:
             assert np.array_equal(a.p[s][k], b.p[s][k]), (s, k)
+
+
+@pytest.mark.parametrize("u0", [0.3, 4.0])
+def test_boris_gyro_radius(oracle_mod, u0):
+    # pure B_z: the orbit is a circle of radius u_perp / (|q/m| B) (gyration
+    # frequency |q/m| B / gamma, speed u / gamma), here to O((omega dt)^2)
+    qm, B0 = -1.0, 0.8
+    gam = math.sqrt(1 + u0 * u0)
+    omega = abs(qm) * B0 / gam
+    dt = 0.1 / omega
+    u = np.array([u0, 0.0, 0.0])
+    x = np.zeros(2)
+    xs = []
+    for _ in range(int(2 * math.pi / (omega * dt)) + 2):
+        u = oracle_mod.boris(qm, dt, (0, 0, 0), (0, 0, B0), u)
+        x += dt * u[:2] / gam
+        xs.append(x.copy())
+    xs = np.array(xs)
+    r = 0.25 * (xs[:, 0].max() - xs[:, 0].min() + xs[:, 1].max() - xs[:, 1].min())
+    assert r == pytest.approx(u0 / (abs(qm) * B0), rel=(omega * dt) ** 2)
