@@ -935,3 +935,29 @@ def test_boris_gyro_radius(oracle_mod, u0):
     xs = np.array(xs)
     r = 0.25 * (xs[:, 0].max() - xs[:, 0].min() + xs[:, 1].max() - xs[:, 1].min())
     assert r == pytest.approx(u0 / (abs(qm) * B0), rel=(omega * dt) ** 2)
+
+
+@pytest.mark.parametrize("u0", [0.5, 5.0])
+def test_spin_gains_on_the_momentum_at_the_anomaly_rate(oracle_mod, u0):
+    # moving across a uniform B_z with the spin along the momentum: the spin
+    # turns at (q/m)(a + 1/gamma) B, the momentum at (q/m) B / gamma, so the
+    # angle between them grows at |q/m| a B per unit time (the spin tune a
+    # gamma per turn) whatever the energy; a = 1 keeps the O((omega dt)^2)
+    # terms of the discrete steps small against it
+    sp = W.Species("x", q=-1.0, m=1.0, a=1.0, n0=0.01, ppc=1, u_th=0.0, s0=(1, 0, 0))
+    B0 = 0.02
+    sim = _one_particle_sim(oracle_mod, {"bz": B0}, u=(u0, 0, 0), s=(1, 0, 0), species=sp, nx=64, ny=64)
+    dt = sim.grid.dt
+    n = 200
+    rel = 0.0
+    for _ in range(n):
+        p = sim.p[0]
+        a_u = math.atan2(p["uy"][0], p["ux"][0])
+        a_s = math.atan2(p["sy"][0], p["sx"][0])
+        sim.push(0)
+        p = sim.p[0]
+        d_u = math.atan2(p["uy"][0], p["ux"][0]) - a_u
+        d_s = math.atan2(p["sy"][0], p["sx"][0]) - a_s
+        rel += (d_s - d_u + math.pi) % (2 * math.pi) - math.pi
+    # an electron: both turn counter-clockwise about +z, the spin ahead
+    assert rel == pytest.approx(n * 1.0 * B0 * dt, rel=1e-3)
