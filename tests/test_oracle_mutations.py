@@ -488,12 +488,14 @@ def test_python_layer_pins_catch_planted_mistake(outcomes, name, pins, old, new)
 
 @pytest.fixture(scope="module")
 def outcomes():
-    """Every planted mistake's pins run, once, on all host cores at a time
-    (each in its own temporary copy of the oracle and its own process)."""
+    """Every planted mistake's pins run, once, on the host cores this process
+    may use (at most 16 at a time; each in its own temporary copy of the
+    oracle and its own process)."""
     from concurrent.futures import ThreadPoolExecutor
     jobs = {("c", c[2]): (_c_caught, c) for c in CASES}
     jobs.update({("window", m[0]): (_py_caught, ("test_oracle_window_pins.py",) + m) for m in MUTATIONS_PY})
     jobs.update({("python", m[0]): (_py_caught, (m[1], m[0], m[2], m[3])) for m in MUTATIONS_PY_MORE})
-    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 4)
+    with ThreadPoolExecutor(max_workers=max(1, min(16, cores))) as ex:
         futs = {k: ex.submit(f, *a) for k, (f, a) in jobs.items()}
         return {k: fut.result() for k, fut in futs.items()}
