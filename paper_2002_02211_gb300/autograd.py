@@ -92,12 +92,15 @@ def _function():
             gs[idx, 0], gs[idx, 1], gs[idx, 2] = g["sx"], g["sy"], g["sz"]
             ctx.save_for_backward(torch.tensor(dla0, dtype=torch.float64), torch.from_numpy(gw),
                                   torch.from_numpy(gs))
+            ctx.devices = (a0.device, weights.device, spins.device)   # each gradient goes back there
             return torch.tensor(value, dtype=torch.float64)
 
         @staticmethod
         def backward(ctx, gout):
             dla0, gw, gs = ctx.saved_tensors
-            return gout * dla0, gout * gw, gout * gs, None
+            gout = gout.cpu()
+            d0, dw, ds = ctx.devices
+            return (gout * dla0).to(d0), (gout * gw).to(dw), (gout * gs).to(ds), None
 
     return _PolarizationLoss
 
