@@ -91,3 +91,20 @@ def test_window_follows_the_envelope_peak():
     # the co-moving leg starts when the envelope peak reaches 3/4 of the box
     # (x = 384 cells of dx = lambda/20 in config 2): step 828
     assert bench.window_start(W.CONFIG2, _dt(W.CONFIG2), 0.75) == 828
+
+
+def test_workload_particle_counts():
+    # every cell but the two vacuum columns at each open x end, ppc per cell
+    # and species: config 1 (256 x 128, 4 ppc) 129,024 electrons; config 2
+    # (512 x 256 x 256, 2 ppc) 66,584,576; config 3 (4096 x 1024, 8 + 8 ppc)
+    # 67,043,328 particles
+    def count(wl):
+        cols = wl.nx if wl.bc_x == "periodic" else wl.nx - 4
+        return sum(sp.ppc * cols * wl.ny * (wl.nz if wl.dim == 3 else 1) for sp in wl.species)
+
+    assert count(W.CONFIG1) == 129_024
+    assert count(W.CONFIG2) == 66_584_576
+    assert count(W.CONFIG3) == 67_043_328
+    # and the generator draws exactly that many on a small cut of each
+    for wl in (W.CONFIG1, W.scaled(W.CONFIG2, ny=8, nz=4), W.scaled(W.CONFIG3, nx=64, ny=8)):
+        assert sum(len(d["ix"]) for d in W.generate_particles(wl)) == count(wl)
